@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Throughput benchmark: Q+Tw values per second on one GB300.
+
+Workload (the synthetic active-region configuration): a 256x256x128 FP32 cube,
+the potential field of 24 buried monopoles (seeded), unit spacing, curl by
+central differences; Q (Method I, RKF45, tol_perp = 10^-3.2) and Tw on the z=0
+plane at 4x oversampling (1024x1024 seeds), both directions. A "step" is one
+Q+Tw map (tracer + Q assembly launches). The headline ``value`` is the FP32
+tracer (FP64 error-norm/Tw/Q assembly); the plain FP64 tracer is timed beside
+it. ``e2e`` is the same map through the C ABI from host memory: copy of B,
+curl+pack, map, copy of Q and Tw back.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fqsl|reference]
+N>1 runs as torchrun ranks, one GPU each, each rank mapping its own cube
+(weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NU = NV = 1024
+TOL = 10 ** -3.2
+CUBE = (256, 256, 128)
+SEED = 2208
+WORKLOAD = "monopole24_256x256x128_f32_z0plane_1024x1024_methodI_rkf45"
+METRIC = "Q+Tw values/sec on 1 GB300 (FP32 vs FP64) at stated rel-err vs oracle"
+# Algorithmic work of one RKF45 trial step of the FP32 tracer, counted from the
+# kernel source (trace.cuh): 6 right-hand-side evaluations of 145 flops each
+# (trilinear weights 18, 8-corner x 6-component accumulation 96, normalisation
+# and twist integrand 31) plus 222 flops of stage combination; and 6 x 8
+# corner records of 32 bytes requested from L1.
+FLOPS_PER_TRIAL = 6 * 145 + 222
+GATHER_BYTES_PER_TRIAL = 6 * 8 * 32
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def c2_inputs(rank: int = 0):
+    import synth
+
+    B, grid, _ = synth.c2_monopole(seed=SEED + rank, n=CUBE)
+    u = (float(CUBE[0] - 1) / NU, 0.0, 0.0)
+    v = (0.0, float(CUBE[1] - 1) / NV, 0.0)
+    return B, grid, u, v
+
+
+def cpu_baseline(B, grid, u, v, target_s=12.0, seed=5):
+    """The oracle as it stands, on a seeded random sample of the same lattice,
+    all host cores; rate in Q+Tw values per second."""
+    import oracle
+
+    oracle.build()
+    B64 = B.astype(np.float64)
+    J = oracle.curl(B64, grid)
+    rng = np.random.default_rng(seed)
+    p = oracle.params(tol=TOL)
+    calib = np.sort(rng.choice(NU * NV, 512, replace=False))
+    t0 = time.perf_counter()
+    oracle.plane(B64, grid, (0.0, 0.0, 0.0), u, v, NU, NV, p, sample=calib, J=J)
+    rate0 = len(calib) / max(time.perf_counter() - t0, 1e-6)
+    m = int(min(NU * NV, max(1024, rate0 * target_s)))
+    sample = np.sort(rng.choice(NU * NV, m, replace=False))
+    t0 = time.perf_counter()
+    ref = oracle.plane(B64, grid, (0.0, 0.0, 0.0), u, v, NU, NV, p, sample=sample, J=J)
+    dt = time.perf_counter() - t0
+    return {"value": m / dt, "unit": "Q+Tw values/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": "%d seeded-random seeds of the 1024x1024 lattice (%.1f s)" % (m, dt)}, sample, ref
+
+
+def err_stats(g, ref, sample):
+    """Relative Q and Tw error of a GPU map against the oracle on the sample."""
+    gq, rq = g["Q"][sample], ref["Q"]
+    ok = np.isfinite(rq) & np.isfinite(gq) & (rq < 1e6)
+    rel = np.abs(gq[ok] / rq[ok] - 1)
+    gt, rt = g["Tw"][sample], ref["Tw"]
+    okt = np.isfinite(rt) & np.isfinite(gt)
+    twr = np.abs(gt[okt] - rt[okt]) / np.maximum(np.abs(rt[okt]), 1e-3)
+    return {"q_rel_median": float(np.median(rel)), "q_rel_p99": float(np.percentile(rel, 99)),
+            "tw_rel_median": float(np.median(twr)), "tw_rel_p99": float(np.percentile(twr, 99)),
+            "faces_equal": float(np.mean((g["face1"][sample] == ref["face1"]) & (g["face2"][sample] == ref["face2"]))),
+            "status_equal": float(np.mean(g["status"][sample] == ref["status"])), "n": int(len(sample))}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    B, grid, u, v = c2_inputs(0)
+    import oracle
+
+    oracle.build()
+    B64 = B.astype(np.float64)
+    J = oracle.curl(B64, grid)
+    p = oracle.params(tol=TOL)
+    rng = np.random.default_rng(17)
+    per_step = 4096
+    times = []
+    for it in range(args.warmup + args.steps):
+        sample = np.sort(rng.choice(NU * NV, per_step, replace=False))
+        t0 = time.perf_counter()
+        oracle.plane(B64, grid, (0.0, 0.0, 0.0), u, v, NU, NV, p, sample=sample, J=J)
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1000.0 * float(np.mean(times))
+    value = per_step / (ms / 1000.0)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Q+Tw values/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": "Q+Tw values/s", "cores": oracle.max_threads(),
+                             "kind": "oracle", "sample": "%d seeded-random seeds per step" % per_step},
+            "e2e": {"value": value, "unit": "Q+Tw values/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fqsl", choices=["fqsl", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    ws, rank, local = _dist()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+
+    __graft_entry__._builder().build()
+    import paper_2208_12569_gb300 as fq
+
+    B, grid, u, v = c2_inputs(rank)
+    Bd = torch.from_numpy(B).to(dev)
+    field = fq.Field(Bd, grid.origin, grid.spacing, pack=("f32", "f64"))
+    field.set_timing(True)
+    n = NU * NV
+    out = fq.alloc_out(n, device=dev)
+    p32 = fq.params(precision="f32", tol=TOL)
+    p64 = fq.params(precision="f64", tol=TOL)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step(p):
+        fq.qmap_plane(field, (0.0, 0.0, 0.0), u, v, NU, NV, p, out=out)
+
+    def timed(p, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        kern = []
+        for e0, e1 in ev:
+            flush.fill_(1.0)
+            e0.record(stream)
+            step(p)
+            e1.record(stream)
+            kern.append(field.times())
+        torch.cuda.synchronize()
+        return [e0.elapsed_time(e1) for e0, e1 in ev], kern
+
+    for _ in range(args.warmup):
+        step(p32)
+    field.check()
+    clocks = ClockSampler(torch.cuda.current_device())
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ms32, kern32 = timed(p32, args.steps)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    res32 = {k: t.cpu().numpy() for k, t in out.items() if t is not None}
+    step(p64)
+    torch.cuda.synchronize()
+    ms64, kern64 = timed(p64, args.fp64_steps)
+    res64 = {k: t.cpu().numpy() for k, t in out.items() if t is not None}
+
+    ms_step = float(np.mean(ms32))
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = n * ws / (ms_step / 1000.0)
+    value64 = n / (float(np.mean(ms64)) / 1000.0)
+
+    # end to end through the C ABI from pinned host memory
+    Bh = torch.from_numpy(B).pin_memory()
+    Bdev = torch.empty_like(Bd)
+    Qh = torch.empty(n, dtype=torch.float64).pin_memory()
+    Twh = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Bdev.copy_(Bh, non_blocking=True)
+        field.update(Bdev)
+        step(p32)
+        Qh.copy_(out["Q"], non_blocking=True)
+        Twh.copy_(out["Tw"], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_value = n * ws / (float(np.mean(e2e_ms)) / 1000.0)
+    assert np.array_equal(np.isnan(Qh.numpy()), np.isnan(res32["Q"]))
+
+    # roofline of the dominant kernel (the FP32 tracer)
+    peaks, peak_kind = _measured_peaks()
+    trials = float(res32["steps"].astype(np.int64).sum())
+    trace_ms = float(np.mean([k[0] for k in kern32]))
+    asm_ms = float(np.mean([k[2] for k in kern32]))
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    achieved = trials * FLOPS_PER_TRIAL / (trace_ms / 1000.0) / 1e12
+    gather_tbs = trials * GATHER_BYTES_PER_TRIAL / (trace_ms / 1000.0) / 1e12
+    l1_peak = NUM_SMS * 128 * sm_mhz * 1e6 / 1e12
+
+    line = {"metric": METRIC, "value": value, "unit": "Q+Tw values/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cube": list(CUBE), "seeds": [NU, NV], "tol_perp": TOL,
+                       "method": 1, "l2": "flushed between steps (256 MB write)", "inputs_resident": True},
+            "fp64": {"value": value64, "unit": "Q+Tw values/s", "ms_per_step": float(np.mean(ms64)),
+                     "trace_ms": float(np.mean([k[0] for k in kern64])),
+                     "speedup_fp32_over_fp64": value / ws / value64},
+            "kernels_ms": {"trace_f32": trace_ms, "assemble": asm_ms},
+            "work": {"trial_steps_per_map": trials, "mean_trials_per_line": trials / n},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved / alu_peak, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, peak_kind),
+                         "gather": {"achieved_TBs": gather_tbs, "l1_nominal_TBs": l1_peak,
+                                    "frac": gather_tbs / l1_peak}},
+            "e2e": {"value": e2e_value, "unit": "Q+Tw values/s", "ms_per_step": float(np.mean(e2e_ms)),
+                    "h2d_bytes_per_step": int(B.nbytes), "d2h_bytes_per_step": int(2 * n * 8)},
+            "gpu_launches": 2 * args.steps, "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb, sample, ref = cpu_baseline(B, grid, u, v)
+        line["cpu_baseline"] = cb
+        line["error_vs_oracle"] = {"f32": err_stats(res32, ref, sample), "f64": err_stats(res64, ref, sample)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * fqsl -- squashing factor Q and twist number Tw of magnetic field lines
+ * traced through a gridded 3D field on one NVIDIA GB300 (sm_103a).
+ *
+ * The operations follow Zhang, Chen, Liu & Wang (2022), "FastQSL: A Fast
+ * Computation Method for Quasi-separatrix Layers" (ApJL; arXiv:2208.12569):
+ *   - field lines dr/ds = B/|B| (Sec. 2.1, Eq. rb), traced from every seed of
+ *     a plane or a volume lattice in both directions until they leave the box,
+ *     with trilinear interpolation (Sec. 2.2, Eqs. interp, w0, w1) and the
+ *     step-adaptive RKF45 scheme whose tolerance is in grid cells (Sec. 2.3);
+ *   - Q = (a^2+b^2+c^2+d^2)/|det D| with |det D| -> |Bn1/Bn2| (Sec. 1, Eqs.
+ *     D+-, Q+-, Bn1), D from neighbouring footpoints on an auxiliary plane S0
+ *     (Method I, Sec. 2.1, Eqs. D+-2, D+-3; obliquity-scaled tolerance and
+ *     local rotation of S0, Sec. 4, Eq. tol) or from deviation vectors
+ *     (Method II, Sec. 2.1, Eqs. rb2, q_scott);
+ *   - Tw = int (curl B . B)/(4 pi B^2) dl (Sec. 1, Eq. tw) from a curl grid,
+ *     and the field-line length (Sec. 2.4).
+ *
+ * Conventions shared by every entry point
+ *   - Every call is asynchronous on the CUDA stream it is given (a
+ *     cudaStream_t passed as void*, NULL = the legacy default stream) and
+ *     returns a status; no exception crosses this boundary. Argument errors are
+ *     detected on the host before anything is launched. A thread-local message
+ *     for the last error is available from fqsl_last_error().
+ *   - Pointers named *_dev are device pointers. Caller-owned buffers must be
+ *     contiguous, 16-byte aligned and stay valid until the stream has run the
+ *     call. The library never frees caller memory.
+ *   - B layout: nx*ny*nz nodes, x fastest then y then z, three components per
+ *     node innermost: B[((k*ny + j)*nx + i)*3 + c], node (i,j,k) at physical
+ *     origin + (i*dx, j*dy, k*dz).
+ *   - Per-line problems are not errors: they are reported in status[] (the
+ *     FQSL_LINE_* bits) and give NaN in Q (and Tw) as documented below.
+ *   - Index coordinates xi = (r - origin)/spacing are used internally; step
+ *     sizes and tolerances are in cells.
+ */
+#ifndef FQSL_H
+#define FQSL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* symbols exported from libfqsl.so */
+#if defined(__GNUC__)
+#define FQSL_API __attribute__((visibility("default")))
+#else
+#define FQSL_API
+#endif
+
+typedef struct fqsl_field_s *fqsl_field;
+
+typedef enum {
+    FQSL_OK = 0,
+    FQSL_ERR_ARG = 1,         /* invalid argument; nothing was launched */
+    FQSL_ERR_CUDA = 2,        /* a CUDA runtime call failed (message has the CUDA error) */
+    FQSL_ERR_OOM = 3,         /* device memory could not be allocated */
+    FQSL_ERR_TIMEOUT = 4,     /* a bounded device loop gave up (see fqsl_field_check) */
+    FQSL_ERR_UNSUPPORTED = 5  /* valid request the library does not implement */
+} fqsl_status;
+
+typedef enum { FQSL_F32 = 0, FQSL_F64 = 1 } fqsl_dtype;
+
+/* fqsl_field_create flags: which packed node records to build. */
+#define FQSL_PACK_F32 1u   /* 32-byte records {Bx,By,Bz,Jx | Jy,Jz,0,0} in float */
+#define FQSL_PACK_F64 2u   /* 64-byte records {Bx,By | Bz,Jx | Jy,Jz | 0,0} in double */
+
+/* per-line status bits (status[] output) */
+#define FQSL_LINE_MAXSTEPS 1u  /* max_steps trial steps used before both ends were found */
+#define FQSL_LINE_NULL_B   2u  /* |B| = 0 (or not finite) at an evaluation */
+#define FQSL_LINE_STALL    4u  /* a step was accepted at h_min above tolerance */
+#define FQSL_LINE_MIXED    8u  /* Method I: no valid difference along one lattice axis at one end */
+#define FQSL_LINE_OUTSIDE 16u  /* seed outside the box */
+#define FQSL_LINE_ROTATED 32u  /* Method I: S0 rotated perpendicular to B at this seed */
+#define FQSL_LINE_CHORD   64u  /* an end was placed on the chord after grazing the face */
+
+/* Tracing and Q parameters. fqsl_params_default() fills the documented
+ * defaults; all lengths are in cells. */
+typedef struct {
+    int method;           /* 1 = neighbour differences (Method I), 2 = deviation vectors (Method II) */
+    int gradb_way;        /* Method II gradient of B/|B|: 1 = node grid (Eq. grad_B), 2 = +-eps differences */
+    int precision;        /* fqsl_dtype: arithmetic of the traced state (FQSL_F64 or FQSL_F32) */
+    int reserved0;
+    double tol;           /* tol_perp (Method I; scaled per line by |Bn0/B|^tol_exp) or tol (Method II, twist); default 10^-3.2 */
+    double h0;            /* initial step, default 0.5 */
+    double h_min;         /* smallest step, default 1e-6 */
+    double h_max;         /* largest step, default 4 */
+    long long max_steps;  /* trial steps per line over both directions, default 100000 (< 2^31) */
+    double rot_thresh;    /* rotate S0 below this |Bn0/B| (interior planes), default 0.05 */
+    double tol_exp;       /* obliquity exponent of Eq. tol, default 1.5 */
+    double graze;         /* smallest outward face-normal velocity of the exit step, default 1e-3 */
+    double eps_way2;      /* Method II way-2 offset, default 1e-3 */
+} fqsl_params;
+
+/* Output buffers of one call (caller-owned device memory, n = number of
+ * seeds; any pointer may be NULL to skip that output).
+ *   Q        double[n]   squashing factor (NaN if status has MAXSTEPS, NULL_B,
+ *                        OUTSIDE or MIXED)
+ *   Tw       double[n]   twist number over the whole line (NaN if MAXSTEPS,
+ *                        NULL_B or OUTSIDE)
+ *   length   double[n]   physical field-line length (same NaN rule as Tw)
+ *   r1, r2   double[3n]  physical footpoints. End 1 is the footpoint on the
+ *                        side of S0 opposite to its normal n0 = unit(u x v)
+ *                        (for a seed list: the backward end); end 2 the other.
+ *   face1, face2 int8[n] exit face of each end: 0 x-min, 1 x-max, 2 y-min,
+ *                        3 y-max, 4 z-min, 5 z-max, -1 none
+ *   status   uint8[n]    FQSL_LINE_* bits
+ *   steps    int32[n]    RKF45 trial steps (accepted, rejected and exit steps) */
+typedef struct {
+    double *Q, *Tw, *length, *r1, *r2;
+    int8_t *face1, *face2;
+    uint8_t *status;
+    int32_t *steps;
+} fqsl_out;
+
+/* Fill *p with the defaults documented in fqsl_params. */
+FQSL_API void fqsl_params_default(fqsl_params *p);
+
+/* Library version string. */
+FQSL_API const char *fqsl_version(void);
+
+/* Message of the last failing call on this host thread ("" if none). */
+FQSL_API const char *fqsl_last_error(void);
+
+/* Build a field handle from a B cube (Sec. 2.2: B known at every node of a
+ * uniform Cartesian grid). B_dev: device array in the layout above, of
+ * b_dtype (FQSL_F32 or FQSL_F64); nx, ny, nz >= 2; spacing > 0. The library
+ * computes curl B at the nodes (2nd-order central differences inside,
+ * 2nd-order one-sided on the faces, first order on a 2-node axis: the curl grid
+ * of Eq. tw) and packs B with it into node records of the precisions asked for
+ * in flags (FQSL_PACK_F32 and/or FQSL_PACK_F64). The handle owns those
+ * records and its scratch memory; the caller may free B_dev once the stream has
+ * run the call. Errors: FQSL_ERR_ARG (null pointers, sizes, flags),
+ * FQSL_ERR_OOM, FQSL_ERR_CUDA. */
+FQSL_API fqsl_status fqsl_field_create(const void *B_dev, fqsl_dtype b_dtype, long long nx, long long ny,
+                              long long nz, const double origin[3], const double spacing[3],
+                              unsigned flags, void *cuda_stream, fqsl_field *out);
+
+/* Replace the field's B by a new cube of the same shape and spacing (for a
+ * time series of snapshots): recomputes curl B and repacks every record
+ * precision the handle holds, asynchronously on cuda_stream, without
+ * allocating. Errors: FQSL_ERR_ARG, FQSL_ERR_CUDA. */
+FQSL_API fqsl_status fqsl_field_update(fqsl_field field, const void *B_dev, fqsl_dtype b_dtype, void *cuda_stream);
+
+/* Release a field handle and everything it owns (synchronises the device). */
+FQSL_API fqsl_status fqsl_field_destroy(fqsl_field field);
+
+/* Q, Tw, length and footpoints on the cell-centred plane lattice
+ *   seed(i,j) = origin + (i + 1/2) u + (j + 1/2) v,  0 <= i < nu, 0 <= j < nv,
+ * output index i + nu*j. S0 is the plane spanned by u and v (u . v = 0
+ * required), with normal n0 = unit(u x v); the refined lattice spacing delta
+ * of Method I is |u| along u and |v| along v (Sec. 2.1). On a plane that lies
+ * on a box face no rotation of S0 is done; elsewhere seeds with |Bn0/B| <
+ * rot_thresh use S0 perpendicular to B and four extra lines at +-delta along
+ * its axes, delta = min(|u|,|v|) (Sec. 4). The field must have been packed in
+ * params->precision. Errors: FQSL_ERR_ARG, FQSL_ERR_UNSUPPORTED (precision not
+ * packed), FQSL_ERR_OOM, FQSL_ERR_CUDA. */
+FQSL_API fqsl_status fqsl_qmap_plane(fqsl_field field, const double origin[3], const double u[3],
+                            const double v[3], long long nu, long long nv,
+                            const fqsl_params *params, const fqsl_out *out, void *cuda_stream);
+
+/* The same on the 3D lattice seed(i,j,k) = origin + ((i+1/2) sx, (j+1/2) sy,
+ * (k+1/2) sz), output index i + nx*(j + ny*k); every z-layer is its own
+ * horizontal S0 (Q extended to 3D by being constant along a line, Eq. qline). */
+FQSL_API fqsl_status fqsl_qmap_volume(fqsl_field field, const double origin[3], const double step[3],
+                             long long nx, long long ny, long long nz, const fqsl_params *params,
+                             const fqsl_out *out, void *cuda_stream);
+
+/* Tw, length, footpoints, faces, status and steps (no Q; out->Q ignored) for
+ * an explicit list of physical seeds seeds_dev[3*n] (double), traced with
+ * tol = params->tol (Sec. 2.4: Tw needs little or no refinement). */
+FQSL_API fqsl_status fqsl_twist(fqsl_field field, const double *seeds_dev, long long n,
+                       const fqsl_params *params, const fqsl_out *out, void *cuda_stream);
+
+/* Per-kernel timing. With timing enabled, every later call on this field
+ * records CUDA events on its own stream around its kernels; fqsl_field_times
+ * waits for the events of the last call and returns their durations in
+ * milliseconds: ms[0] line tracer (lattice or seed list), ms[1] tracer of the
+ * rotated-S0 extra lines (0 if not launched), ms[2] Q assembly. Errors:
+ * FQSL_ERR_ARG (NULL, or no timed call yet), FQSL_ERR_CUDA. */
+FQSL_API fqsl_status fqsl_field_set_timing(fqsl_field field, int enable);
+FQSL_API fqsl_status fqsl_field_times(fqsl_field field, float ms[3]);
+
+/* Synchronise cuda_stream and report device-side failures recorded by earlier
+ * calls on this field (FQSL_ERR_TIMEOUT if a bounded loop gave up). The
+ * record is cleared. */
+FQSL_API fqsl_status fqsl_field_check(fqsl_field field, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FQSL_H */

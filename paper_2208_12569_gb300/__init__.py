@@ -1,0 +1,8 @@
+"""fqsl: squashing factor Q and twist number Tw of magnetic field lines on one
+GB300 (sm_103a), after Zhang et al. (2022), FastQSL. The computation lives in
+the CUDA library libfqsl.so (C ABI in include/fqsl.h); ``fqsl`` is its Python
+binding."""
+from .fqsl import (  # noqa: F401
+    F32, F64, LINE_BAD, LINE_CHORD, LINE_MAXSTEPS, LINE_MIXED, LINE_NULL_B, LINE_OUTSIDE, LINE_ROTATED, LINE_STALL,
+    Field, FqslError, alloc_out, params, qmap_plane, qmap_volume, twist, version,
+)

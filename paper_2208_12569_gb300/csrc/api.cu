@@ -1,0 +1,561 @@
+// C ABI of the fqsl library (declared in include/fqsl.h): argument checks,
+// handle and scratch management, and the launch sequence of each call.
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+
+#include "fqsl_internal.cuh"
+
+using namespace fqsl;
+
+namespace {
+
+thread_local std::string g_err;
+
+fqsl_status fail(fqsl_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+fqsl_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(FQSL_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(FQSL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool finite3(const double *v) { return v && isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// sequential carve of one scratch allocation
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <typename P>
+    P *take(size_t count)
+    {
+        P *p = base ? (P *)(base + off) : nullptr;
+        off = align_up(off + count * sizeof(P));
+        return p;
+    }
+};
+
+}  // namespace
+
+struct fqsl_field_s {
+    int device = 0;
+    int sms = 0;
+    FieldView g{};
+    void *rec32 = nullptr, *rec64 = nullptr;
+    void *scratch = nullptr;
+    size_t scratch_cap = 0;
+    unsigned long long *counters = nullptr;  // [0] primary head, [1] extra head, [2] rotated count (low 32 bits)
+    int blocks_f32[3] = {0, 0, 0}, blocks_f64[3] = {0, 0, 0};
+    bool timing = false, timed = false, extra_timed = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::mutex mu;
+};
+
+namespace {
+void mark(fqsl_field f, int i, cudaStream_t s)
+{
+    if (f->timing) cudaEventRecord(f->ev[i], s);
+}
+}  // namespace
+
+extern "C" {
+
+void fqsl_params_default(fqsl_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->method = 1;
+    p->gradb_way = 1;
+    p->precision = FQSL_F32;
+    p->tol = pow(10.0, -3.2);
+    p->h0 = 0.5;
+    p->h_min = 1e-6;
+    p->h_max = 4.0;
+    p->max_steps = 100000;
+    p->rot_thresh = 0.05;
+    p->tol_exp = 1.5;
+    p->graze = 1e-3;
+    p->eps_way2 = 1e-3;
+}
+
+const char *fqsl_version(void) { return "fqsl 0.1.0 (sm_103a)"; }
+
+const char *fqsl_last_error(void) { return g_err.c_str(); }
+
+fqsl_status fqsl_field_create(const void *B_dev, fqsl_dtype b_dtype, long long nx, long long ny, long long nz,
+                              const double origin[3], const double spacing[3], unsigned flags, void *cuda_stream,
+                              fqsl_field *out)
+{
+    g_err.clear();
+    if (!out) return fail(FQSL_ERR_ARG, "fqsl_field_create: out is NULL");
+    *out = nullptr;
+    if (!B_dev) return fail(FQSL_ERR_ARG, "fqsl_field_create: B_dev is NULL");
+    if (b_dtype != FQSL_F32 && b_dtype != FQSL_F64)
+        return fail(FQSL_ERR_ARG, "fqsl_field_create: b_dtype must be FQSL_F32 or FQSL_F64");
+    if (nx < 2 || ny < 2 || nz < 2) return fail(FQSL_ERR_ARG, "fqsl_field_create: need nx, ny, nz >= 2");
+    if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30) || nx * ny * nz > (1LL << 34))
+        return fail(FQSL_ERR_ARG, "fqsl_field_create: grid too large");
+    if (!finite3(origin) || !finite3(spacing))
+        return fail(FQSL_ERR_ARG, "fqsl_field_create: origin/spacing must be finite");
+    if (!(spacing[0] > 0 && spacing[1] > 0 && spacing[2] > 0))
+        return fail(FQSL_ERR_ARG, "fqsl_field_create: spacing must be > 0");
+    if (flags == 0 || (flags & ~(FQSL_PACK_F32 | FQSL_PACK_F64)))
+        return fail(FQSL_ERR_ARG, "fqsl_field_create: flags must be a non-empty set of FQSL_PACK_*");
+    if (((uintptr_t)B_dev) % 16) return fail(FQSL_ERR_ARG, "fqsl_field_create: B_dev must be 16-byte aligned");
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, B_dev);
+    if (e != cudaSuccess || (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return fail(FQSL_ERR_ARG, "fqsl_field_create: B_dev is not device memory");
+    }
+    fqsl_field f = new (std::nothrow) fqsl_field_s();
+    if (!f) return fail(FQSL_ERR_OOM, "fqsl_field_create: host allocation failed");
+    cudaGetDevice(&f->device);
+    cudaDeviceGetAttribute(&f->sms, cudaDevAttrMultiProcessorCount, f->device);
+    f->g.nx = (int)nx;
+    f->g.ny = (int)ny;
+    f->g.nz = (int)nz;
+    for (int a = 0; a < 3; a++) {
+        f->g.o[a] = origin[a];
+        f->g.d[a] = spacing[a];
+    }
+    const size_t nodes = (size_t)nx * ny * nz;
+    if (flags & FQSL_PACK_F32) {
+        e = cudaMalloc(&f->rec32, nodes * 32);
+        if (e != cudaSuccess) {
+            delete f;
+            return cuda_fail(e, "fqsl_field_create: FP32 records");
+        }
+    }
+    if (flags & FQSL_PACK_F64) {
+        e = cudaMalloc(&f->rec64, nodes * 64);
+        if (e != cudaSuccess) {
+            cudaFree(f->rec32);
+            delete f;
+            return cuda_fail(e, "fqsl_field_create: FP64 records");
+        }
+    }
+    e = cudaMalloc(&f->counters, 4 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFree(f->rec32);
+        cudaFree(f->rec64);
+        delete f;
+        return cuda_fail(e, "fqsl_field_create: counters");
+    }
+    e = launch_curl_pack(B_dev, b_dtype, f->g, f->rec32, f->rec64, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) {
+        cudaFree(f->rec32);
+        cudaFree(f->rec64);
+        cudaFree(f->counters);
+        delete f;
+        return cuda_fail(e, "fqsl_field_create: curl_pack launch");
+    }
+    *out = f;
+    return FQSL_OK;
+}
+
+fqsl_status fqsl_field_update(fqsl_field f, const void *B_dev, fqsl_dtype b_dtype, void *cuda_stream)
+{
+    g_err.clear();
+    if (!f) return fail(FQSL_ERR_ARG, "fqsl_field_update: NULL handle");
+    if (!B_dev) return fail(FQSL_ERR_ARG, "fqsl_field_update: B_dev is NULL");
+    if (b_dtype != FQSL_F32 && b_dtype != FQSL_F64)
+        return fail(FQSL_ERR_ARG, "fqsl_field_update: b_dtype must be FQSL_F32 or FQSL_F64");
+    if (((uintptr_t)B_dev) % 16) return fail(FQSL_ERR_ARG, "fqsl_field_update: B_dev must be 16-byte aligned");
+    std::lock_guard<std::mutex> lock(f->mu);
+    cudaError_t e = launch_curl_pack(B_dev, b_dtype, f->g, f->rec32, f->rec64, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fqsl_field_update: curl_pack launch");
+    return FQSL_OK;
+}
+
+fqsl_status fqsl_field_set_timing(fqsl_field f, int enable)
+{
+    g_err.clear();
+    if (!f) return fail(FQSL_ERR_ARG, "fqsl_field_set_timing: NULL handle");
+    std::lock_guard<std::mutex> lock(f->mu);
+    if (enable && !f->ev[0]) {
+        for (int i = 0; i < 4; i++) {
+            cudaError_t e = cudaEventCreate(&f->ev[i]);
+            if (e != cudaSuccess) return cuda_fail(e, "fqsl_field_set_timing");
+        }
+    }
+    f->timing = enable != 0;
+    f->timed = false;
+    return FQSL_OK;
+}
+
+fqsl_status fqsl_field_times(fqsl_field f, float ms[3])
+{
+    g_err.clear();
+    if (!f || !ms) return fail(FQSL_ERR_ARG, "fqsl_field_times: NULL argument");
+    std::lock_guard<std::mutex> lock(f->mu);
+    if (!f->timed) return fail(FQSL_ERR_ARG, "fqsl_field_times: no timed call yet");
+    cudaError_t e = cudaEventSynchronize(f->ev[3]);
+    if (e != cudaSuccess) return cuda_fail(e, "fqsl_field_times");
+    ms[0] = ms[1] = ms[2] = 0.f;
+    cudaEventElapsedTime(&ms[0], f->ev[0], f->ev[1]);
+    if (f->extra_timed) cudaEventElapsedTime(&ms[1], f->ev[1], f->ev[2]);
+    cudaEventElapsedTime(&ms[2], f->ev[2], f->ev[3]);
+    return FQSL_OK;
+}
+
+fqsl_status fqsl_field_destroy(fqsl_field f)
+{
+    g_err.clear();
+    if (!f) return fail(FQSL_ERR_ARG, "fqsl_field_destroy: NULL handle");
+    cudaDeviceSynchronize();
+    for (int i = 0; i < 4; i++)
+        if (f->ev[i]) cudaEventDestroy(f->ev[i]);
+    cudaFree(f->rec32);
+    cudaFree(f->rec64);
+    cudaFree(f->scratch);
+    cudaFree(f->counters);
+    delete f;
+    return FQSL_OK;
+}
+
+fqsl_status fqsl_field_check(fqsl_field f, void *cuda_stream)
+{
+    g_err.clear();
+    if (!f) return fail(FQSL_ERR_ARG, "fqsl_field_check: NULL handle");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fqsl_field_check");
+    return FQSL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *who)
+{
+    if (!f) return fail(FQSL_ERR_ARG, "%s: NULL field", who);
+    if (!p) return fail(FQSL_ERR_ARG, "%s: NULL params", who);
+    if (p->method != 1 && p->method != 2) return fail(FQSL_ERR_ARG, "%s: method must be 1 or 2", who);
+    if (p->gradb_way != 1 && p->gradb_way != 2) return fail(FQSL_ERR_ARG, "%s: gradb_way must be 1 or 2", who);
+    if (p->precision != FQSL_F32 && p->precision != FQSL_F64)
+        return fail(FQSL_ERR_ARG, "%s: precision must be FQSL_F32 or FQSL_F64", who);
+    if (!(p->tol > 0) || !isfinite(p->tol)) return fail(FQSL_ERR_ARG, "%s: tol must be > 0", who);
+    if (!(p->h_min > 0) || !(p->h_max >= p->h_min) || !(p->h0 >= p->h_min) || !(p->h0 <= p->h_max) ||
+        !isfinite(p->h_max))
+        return fail(FQSL_ERR_ARG, "%s: need 0 < h_min <= h0 <= h_max", who);
+    if (p->max_steps < 1 || p->max_steps > 2000000000LL)
+        return fail(FQSL_ERR_ARG, "%s: max_steps must be in [1, 2e9]", who);
+    if (!(p->rot_thresh >= 0) || !(p->rot_thresh < 1)) return fail(FQSL_ERR_ARG, "%s: rot_thresh in [0,1)", who);
+    if (!(p->tol_exp >= 0) || !isfinite(p->tol_exp)) return fail(FQSL_ERR_ARG, "%s: tol_exp >= 0", who);
+    if (!(p->graze > 0) || !(p->graze < 1)) return fail(FQSL_ERR_ARG, "%s: graze in (0,1)", who);
+    if (!(p->eps_way2 > 0) || !(p->eps_way2 < 0.5)) return fail(FQSL_ERR_ARG, "%s: eps_way2 in (0,0.5)", who);
+    if (p->precision == FQSL_F32 && !f->rec32)
+        return fail(FQSL_ERR_UNSUPPORTED, "%s: field was not packed in FP32 (FQSL_PACK_F32)", who);
+    if (p->precision == FQSL_F64 && !f->rec64)
+        return fail(FQSL_ERR_UNSUPPORTED, "%s: field was not packed in FP64 (FQSL_PACK_F64)", who);
+    if (p->method == 2) return fail(FQSL_ERR_UNSUPPORTED, "%s: Method II is not built yet", who);
+    return FQSL_OK;
+}
+
+DevParams dev_params(const fqsl_params *p)
+{
+    DevParams d;
+    d.tol = p->tol;
+    d.h0 = p->h0;
+    d.hmin = p->h_min;
+    d.hmax = p->h_max;
+    d.rot = p->rot_thresh;
+    d.texp = p->tol_exp;
+    d.graze = p->graze;
+    d.eps2 = p->eps_way2;
+    d.max_steps = p->max_steps;
+    d.method = p->method;
+    d.way = p->gradb_way;
+    return d;
+}
+
+struct Scratch {
+    LineRecs rec{}, ext{};
+    int32_t *rot_seed = nullptr, *rot_slot = nullptr;
+    size_t bytes = 0;
+};
+
+// Lay out the per-call scratch for n primary lines (and 4 n extra lines when
+// rotation is possible). With base == NULL only the size is computed.
+Scratch layout(char *base, long long n, bool rot, bool want_bn)
+{
+    Carver c{base};
+    Scratch s;
+    LineRecs &r = s.rec;
+    r.r1 = c.take<double>(3 * n);
+    r.r2 = c.take<double>(3 * n);
+    r.bn1 = want_bn ? c.take<double>(n) : nullptr;
+    r.bn2 = want_bn ? c.take<double>(n) : nullptr;
+    r.bn0 = want_bn ? c.take<double>(n) : nullptr;
+    r.tw = c.take<double>(n);
+    r.len = c.take<double>(n);
+    r.f1 = c.take<int8_t>(n);
+    r.f2 = c.take<int8_t>(n);
+    r.st = c.take<uint8_t>(n);
+    r.steps = c.take<int32_t>(n);
+    if (rot) {
+        s.rot_seed = c.take<int32_t>(n);
+        s.rot_slot = c.take<int32_t>(n);
+        LineRecs &x = s.ext;
+        x.r1 = c.take<double>(12 * n);
+        x.r2 = c.take<double>(12 * n);
+        x.f1 = c.take<int8_t>(4 * n);
+        x.f2 = c.take<int8_t>(4 * n);
+        x.st = c.take<uint8_t>(4 * n);
+        x.steps = c.take<int32_t>(4 * n);
+    }
+    s.bytes = c.off;
+    return s;
+}
+
+fqsl_status ensure_scratch(fqsl_field f, size_t bytes)
+{
+    if (bytes <= f->scratch_cap) return FQSL_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "scratch: synchronize");
+    cudaFree(f->scratch);
+    f->scratch = nullptr;
+    f->scratch_cap = 0;
+    e = cudaMalloc(&f->scratch, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e, "scratch allocation");
+    }
+    f->scratch_cap = bytes;
+    return FQSL_OK;
+}
+
+int blocks_per_sm(fqsl_field f, int precision, int src)
+{
+    int *cache = precision == FQSL_F32 ? f->blocks_f32 : f->blocks_f64;
+    if (!cache[src]) cache[src] = precision == FQSL_F32 ? trace_blocks_per_sm_f32(src) : trace_blocks_per_sm_f64(src);
+    return cache[src];
+}
+
+cudaError_t launch_trace(fqsl_field f, const fqsl_params *p, const TraceArgs &a, int src, long long items,
+                         cudaStream_t s)
+{
+    const long long warps_needed = (items + 31) / 32;
+    long long grid = (long long)f->sms * blocks_per_sm(f, p->precision, src);
+    const long long need = (warps_needed * 32 + kTraceBlock - 1) / kTraceBlock;
+    if (src != kSrcExtra && need < grid) grid = need;
+    if (grid < 1) grid = 1;
+    return p->precision == FQSL_F32 ? launch_trace_f32(a, src, (int)grid, kTraceBlock, s)
+                                    : launch_trace_f64(a, src, (int)grid, kTraceBlock, s);
+}
+
+void cross(const double *a, const double *b, double *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Shared body of the plane and volume Q maps.
+fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, const fqsl_out *out,
+                     cudaStream_t stream, bool face_plane, const char *who)
+{
+    Lattice lat = lat0;
+    const long long n = lat.n1 * lat.n2 * lat.n3;
+    lat.tiles_u = (lat.n1 + kTileU - 1) / kTileU;
+    lat.tiles_v = (lat.n2 + kTileV - 1) / kTileV;
+    lat.allow_rot = (p->method == 1 && !face_plane) ? 1 : 0;
+    std::lock_guard<std::mutex> lock(f->mu);
+    Scratch sz = layout(nullptr, n, lat.allow_rot, true);
+    fqsl_status st = ensure_scratch(f, sz.bytes);
+    if (st != FQSL_OK) return st;
+    Scratch s = layout((char *)f->scratch, n, lat.allow_rot, true);
+
+    cudaError_t e = cudaMemsetAsync(f->counters, 0, 4 * sizeof(unsigned long long), stream);
+    if (e == cudaSuccess && lat.allow_rot) e = cudaMemsetAsync(s.rot_slot, 0, (size_t)n * sizeof(int32_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+
+    TraceArgs a{};
+    a.f = f->g;
+    a.f.rec = p->precision == FQSL_F32 ? f->rec32 : f->rec64;
+    a.p = dev_params(p);
+    a.lat = lat;
+    a.rec = s.rec;
+    a.ext = s.ext;
+    a.q.head = f->counters;
+    a.q.rot_count = (unsigned int *)(f->counters + 2);
+    a.q.rot_seed = s.rot_seed;
+    a.q.rot_slot = s.rot_slot;
+    a.nitems = lat.n3 * lat.tiles_u * lat.tiles_v * (long long)(kTileU * kTileV);
+    mark(f, 0, stream);
+    e = launch_trace(f, p, a, kSrcLattice, a.nitems, stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    mark(f, 1, stream);
+    if (lat.allow_rot) {
+        a.q.head = f->counters + 1;
+        e = launch_trace(f, p, a, kSrcExtra, 4 * n, stream);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+    }
+    mark(f, 2, stream);
+    AssembleArgs g{};
+    g.lat = lat;
+    g.rec = s.rec;
+    g.ext = s.ext;
+    g.rot_slot = lat.allow_rot ? s.rot_slot : nullptr;
+    g.out = *out;
+    g.n = n;
+    g.want_q = 1;
+    e = launch_assemble(g, stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    mark(f, 3, stream);
+    f->timed = f->timing;
+    f->extra_timed = lat.allow_rot != 0;
+    return FQSL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fqsl_status fqsl_qmap_plane(fqsl_field f, const double origin[3], const double u[3], const double v[3],
+                            long long nu, long long nv, const fqsl_params *p, const fqsl_out *out, void *cuda_stream)
+{
+    g_err.clear();
+    const char *who = "fqsl_qmap_plane";
+    fqsl_status st = check_params(f, p, who);
+    if (st != FQSL_OK) return st;
+    if (!out) return fail(FQSL_ERR_ARG, "%s: out is NULL", who);
+    if (!finite3(origin) || !finite3(u) || !finite3(v)) return fail(FQSL_ERR_ARG, "%s: non-finite plane", who);
+    if (nu < 1 || nv < 1 || nu * nv > (1LL << 31) - 1) return fail(FQSL_ERR_ARG, "%s: need 1 <= nu*nv < 2^31", who);
+    double n0[3];
+    cross(u, v, n0);
+    const double nn = sqrt(n0[0] * n0[0] + n0[1] * n0[1] + n0[2] * n0[2]);
+    const double nuu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const double nvv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (!(nuu > 0) || !(nvv > 0) || !(nn > 0)) return fail(FQSL_ERR_ARG, "%s: u and v must span a plane", who);
+    if (fabs(u[0] * v[0] + u[1] * v[1] + u[2] * v[2]) > 1e-12 * nuu * nvv)
+        return fail(FQSL_ERR_ARG, "%s: u and v must be orthogonal", who);
+    Lattice lat{};
+    for (int a = 0; a < 3; a++) {
+        lat.o[a] = origin[a];
+        lat.a1[a] = u[a];
+        lat.a2[a] = v[a];
+        lat.a3[a] = 0.0;
+        lat.n0[a] = n0[a] / nn;
+    }
+    lat.n1 = nu;
+    lat.n2 = nv;
+    lat.n3 = 1;
+    lat.du = nuu;
+    lat.dv = nvv;
+    lat.drot = fmin(nuu, nvv);
+    int zeros = 0, axis = -1;
+    for (int a = 0; a < 3; a++) {
+        if (lat.n0[a] == 0.0) zeros++;
+        else axis = a;
+    }
+    lat.normal_axis = zeros == 2 ? axis : -1;
+    bool face_plane = false;
+    if (lat.normal_axis >= 0) {
+        const int a = lat.normal_axis;
+        const int na = a == 0 ? f->g.nx : (a == 1 ? f->g.ny : f->g.nz);
+        const double xi = (origin[a] - f->g.o[a]) / f->g.d[a];
+        face_plane = (xi == 0.0) || (xi == (double)(na - 1));
+    }
+    return run_qmap(f, lat, p, out, (cudaStream_t)cuda_stream, face_plane, who);
+}
+
+fqsl_status fqsl_qmap_volume(fqsl_field f, const double origin[3], const double step[3], long long nx, long long ny,
+                             long long nz, const fqsl_params *p, const fqsl_out *out, void *cuda_stream)
+{
+    g_err.clear();
+    const char *who = "fqsl_qmap_volume";
+    fqsl_status st = check_params(f, p, who);
+    if (st != FQSL_OK) return st;
+    if (!out) return fail(FQSL_ERR_ARG, "%s: out is NULL", who);
+    if (!finite3(origin) || !finite3(step)) return fail(FQSL_ERR_ARG, "%s: non-finite lattice", who);
+    if (!(step[0] > 0 && step[1] > 0 && step[2] > 0)) return fail(FQSL_ERR_ARG, "%s: steps must be > 0", who);
+    if (nx < 1 || ny < 1 || nz < 1 || nx * ny * nz > (1LL << 31) - 1)
+        return fail(FQSL_ERR_ARG, "%s: need 1 <= nx*ny*nz < 2^31", who);
+    Lattice lat{};
+    for (int a = 0; a < 3; a++) {
+        lat.o[a] = origin[a];
+        lat.a1[a] = a == 0 ? step[0] : 0.0;
+        lat.a2[a] = a == 1 ? step[1] : 0.0;
+        lat.a3[a] = a == 2 ? step[2] : 0.0;
+        lat.n0[a] = a == 2 ? 1.0 : 0.0;
+    }
+    lat.n1 = nx;
+    lat.n2 = ny;
+    lat.n3 = nz;
+    lat.du = step[0];
+    lat.dv = step[1];
+    lat.drot = fmin(step[0], step[1]);
+    lat.normal_axis = 2;
+    return run_qmap(f, lat, p, out, (cudaStream_t)cuda_stream, false, who);
+}
+
+fqsl_status fqsl_twist(fqsl_field f, const double *seeds_dev, long long n, const fqsl_params *p, const fqsl_out *out,
+                       void *cuda_stream)
+{
+    g_err.clear();
+    const char *who = "fqsl_twist";
+    fqsl_status st = check_params(f, p, who);
+    if (st != FQSL_OK) return st;
+    if (!out) return fail(FQSL_ERR_ARG, "%s: out is NULL", who);
+    if (n < 0 || n > (1LL << 31) - 1) return fail(FQSL_ERR_ARG, "%s: n out of range", who);
+    if (n == 0) return FQSL_OK;
+    if (!seeds_dev) return fail(FQSL_ERR_ARG, "%s: seeds_dev is NULL", who);
+    if (((uintptr_t)seeds_dev) % 8) return fail(FQSL_ERR_ARG, "%s: seeds_dev must be 8-byte aligned", who);
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    std::lock_guard<std::mutex> lock(f->mu);
+    Scratch sz = layout(nullptr, n, false, false);
+    st = ensure_scratch(f, sz.bytes);
+    if (st != FQSL_OK) return st;
+    Scratch s = layout((char *)f->scratch, n, false, false);
+    cudaError_t e = cudaMemsetAsync(f->counters, 0, 4 * sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    TraceArgs a{};
+    a.f = f->g;
+    a.f.rec = p->precision == FQSL_F32 ? f->rec32 : f->rec64;
+    a.p = dev_params(p);
+    a.seeds = seeds_dev;
+    a.nitems = n;
+    a.rec = s.rec;
+    a.q.head = f->counters;
+    mark(f, 0, stream);
+    e = launch_trace(f, p, a, kSrcList, n, stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    mark(f, 1, stream);
+    mark(f, 2, stream);
+    AssembleArgs g{};
+    g.lat.n1 = n;
+    g.lat.n2 = 1;
+    g.lat.n3 = 1;
+    g.rec = s.rec;
+    g.out = *out;
+    g.out.Q = nullptr;
+    g.n = n;
+    g.want_q = 0;
+    e = launch_assemble(g, stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    mark(f, 3, stream);
+    f->timed = f->timing;
+    f->extra_timed = false;
+    return FQSL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// curl_pack: curl B at the nodes and the packed B+J node records.
+//
+// The twist number Tw = int (curl B . B)/(4 pi B^2) dl (Sec. 1, Eq. tw) needs
+// curl B along the line; it is precomputed once per field on the node grid
+// with 2nd-order central differences inside (the stencil of Eq. grad_B),
+// 2nd-order one-sided differences on the faces and first order on a 2-node
+// axis, and packed next to B so that one trilinear gather (Sec. 2.2, Eq.
+// interp) fetches both. The stencil arithmetic is done in FP64 for both record
+// precisions. One thread per node, grid-stride; streaming and HBM-bound.
+#include "fqsl_internal.cuh"
+
+namespace fqsl {
+namespace {
+
+template <typename TI>
+__device__ __forceinline__ double node_diff(const TI *__restrict__ B, int c, long long node, long long stride,
+                                            long long i, long long n, double h)
+{
+    // value of component c at index kk along the axis (node is at index i)
+    auto F = [&](long long kk) -> double { return (double)B[(node + (kk - i) * stride) * 3 + c]; };
+    if (n == 2) return (F(1) - F(0)) / h;
+    if (i == 0) return (-3.0 * F(0) + 4.0 * F(1) - F(2)) / (2.0 * h);
+    if (i == n - 1) return (3.0 * F(n - 1) - 4.0 * F(n - 2) + F(n - 3)) / (2.0 * h);
+    return (F(i + 1) - F(i - 1)) / (2.0 * h);
+}
+
+template <typename TI>
+__global__ void __launch_bounds__(256) k_curl_pack(const TI *__restrict__ B, int nx, int ny, int nz, double dx,
+                                                   double dy, double dz, float4 *__restrict__ rec32,
+                                                   double2 *__restrict__ rec64)
+{
+    const long long total = (long long)nx * ny * nz;
+    const long long sy = nx, sz = (long long)nx * ny;
+    for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < total;
+         node += (long long)gridDim.x * blockDim.x) {
+        const long long i = node % nx;
+        const long long j = (node / nx) % ny;
+        const long long k = node / sz;
+        const double dyBz = node_diff(B, 2, node, sy, j, ny, dy);
+        const double dzBy = node_diff(B, 1, node, sz, k, nz, dz);
+        const double dzBx = node_diff(B, 0, node, sz, k, nz, dz);
+        const double dxBz = node_diff(B, 2, node, 1, i, nx, dx);
+        const double dxBy = node_diff(B, 1, node, 1, i, nx, dx);
+        const double dyBx = node_diff(B, 0, node, sy, j, ny, dy);
+        const double Jx = dyBz - dzBy, Jy = dzBx - dxBz, Jz = dxBy - dyBx;
+        const double Bx = (double)B[node * 3 + 0], By = (double)B[node * 3 + 1], Bz = (double)B[node * 3 + 2];
+        if (rec32) {
+            rec32[2 * node + 0] = make_float4((float)Bx, (float)By, (float)Bz, (float)Jx);
+            rec32[2 * node + 1] = make_float4((float)Jy, (float)Jz, 0.f, 0.f);
+        }
+        if (rec64) {
+            rec64[4 * node + 0] = make_double2(Bx, By);
+            rec64[4 * node + 1] = make_double2(Bz, Jx);
+            rec64[4 * node + 2] = make_double2(Jy, Jz);
+            rec64[4 * node + 3] = make_double2(0.0, 0.0);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_curl_pack(const void *B, fqsl_dtype bt, const FieldView &g, void *rec32, void *rec64,
+                             cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    long long blocks = (total + 255) / 256;
+    const long long cap = (long long)sms * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (bt == FQSL_F32)
+        k_curl_pack<float><<<(unsigned)blocks, 256, 0, s>>>((const float *)B, g.nx, g.ny, g.nz, g.d[0], g.d[1],
+                                                           g.d[2], (float4 *)rec32, (double2 *)rec64);
+    else
+        k_curl_pack<double><<<(unsigned)blocks, 256, 0, s>>>((const double *)B, g.nx, g.ny, g.nz, g.d[0], g.d[1],
+                                                            g.d[2], (float4 *)rec32, (double2 *)rec64);
+    return cudaGetLastError();
+}
+
+}  // namespace fqsl

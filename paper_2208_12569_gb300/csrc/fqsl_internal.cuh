@@ -1,0 +1,110 @@
+// Internal types shared by the fqsl CUDA translation units (not part of the
+// public C ABI in include/fqsl.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fqsl.h"
+
+namespace fqsl {
+
+// ---------------------------------------------------------------------------
+// Packed node records (one gather fetches B and curl B of a node).
+//   FP32: 32 B  = float4 {Bx, By, Bz, Jx}, float4 {Jy, Jz, 0, 0}
+//   FP64: 64 B  = double2 {Bx, By}, {Bz, Jx}, {Jy, Jz}, {0, 0}
+// Node (i,j,k) is record (k*ny + j)*nx + i.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct RecTraits;
+template <>
+struct RecTraits<float> {
+    static constexpr int kVec = 2;  // float4 per record
+};
+template <>
+struct RecTraits<double> {
+    static constexpr int kVec = 4;  // double2 per record
+};
+
+struct FieldView {
+    const void *rec;  // float4* (FP32) or double2* (FP64)
+    int nx, ny, nz;
+    double o[3];  // origin
+    double d[3];  // spacing
+};
+
+struct DevParams {
+    double tol, h0, hmin, hmax, rot, texp, graze, eps2;
+    long long max_steps;
+    int method, way;
+};
+
+// Cell-centred lattice seed(i,j,k) = o + (i+1/2) a1 + (j+1/2) a2 + (k+1/2) a3.
+// Work items walk it in tiles of kTileU x kTileV seeds per layer so that a
+// warp traces neighbouring seeds together.
+constexpr int kTileU = 8;
+constexpr int kTileV = 4;
+
+struct Lattice {
+    double o[3], a1[3], a2[3], a3[3];
+    double n0[3];      // unit(a1 x a2)
+    long long n1, n2, n3;
+    long long tiles_u, tiles_v;
+    double du, dv, drot;
+    int normal_axis;   // axis of n0 if it is a coordinate axis, else -1
+    int allow_rot;     // Method I and some layer may be interior
+};
+
+// Per-line results in structure-of-arrays form (library scratch).
+struct LineRecs {
+    double *r1, *r2;    // physical footpoints, 3 per line
+    double *bn1, *bn2;  // B . n at each end
+    double *bn0;        // B0 . n0 (or |B0| when S0 is perpendicular to B)
+    double *tw, *len;
+    int8_t *f1, *f2;
+    uint8_t *st;
+    int32_t *steps;
+};
+
+struct Queue {
+    unsigned long long *head;  // work counter of the launch
+    unsigned int *rot_count;   // number of rotated seeds
+    int32_t *rot_seed;         // rotated slot -> lattice index
+    int32_t *rot_slot;         // lattice index -> slot + 1 (0 = not rotated)
+};
+
+enum Source { kSrcLattice = 0, kSrcExtra = 1, kSrcList = 2 };
+
+struct TraceArgs {
+    FieldView f;
+    DevParams p;
+    Lattice lat;
+    const double *seeds;  // kSrcList: 3 per seed
+    long long nitems;     // work items (kSrcExtra: read from rot_count)
+    LineRecs rec;         // primary lines (lattice or list)
+    LineRecs ext;         // rotated extra lines, 4 per slot
+    Queue q;
+};
+
+struct AssembleArgs {
+    Lattice lat;
+    LineRecs rec, ext;
+    const int32_t *rot_slot;  // may be NULL
+    fqsl_out out;
+    long long n;
+    int want_q;
+};
+
+constexpr unsigned kBad = FQSL_LINE_MAXSTEPS | FQSL_LINE_NULL_B | FQSL_LINE_OUTSIDE;
+
+// launch helpers implemented in the .cu files
+cudaError_t launch_curl_pack(const void *B, fqsl_dtype bt, const FieldView &g, void *rec32, void *rec64,
+                             cudaStream_t s);
+cudaError_t launch_trace_f32(const TraceArgs &a, int src, int grid, int block, cudaStream_t s);
+cudaError_t launch_trace_f64(const TraceArgs &a, int src, int grid, int block, cudaStream_t s);
+int trace_blocks_per_sm_f32(int src);
+int trace_blocks_per_sm_f64(int src);
+constexpr int kTraceBlock = 128;
+cudaError_t launch_assemble(const AssembleArgs &a, cudaStream_t s);
+
+}  // namespace fqsl

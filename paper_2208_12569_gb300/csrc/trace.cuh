@@ -1,0 +1,740 @@
+// Persistent field-line tracer (templated on the traced precision T).
+//
+// Method (Zhang et al. 2022):
+//   - field-line equation dr/ds = B/|B| (Sec. 2.1, Eq. rb), integrated in index
+//     coordinates xi = (r - o)/d with d xi/d tau = bt/|bt|, bt_a = B_a/d_a, so
+//     tau, step and tol are in cells (Sec. 2.3); physical length dl/dtau =
+//     |B|/|bt| and the twist integrand (curl B . B)/(4 pi B^2) dl/dtau (Eq. tw)
+//     ride along as two extra components;
+//   - B and curl B between nodes by trilinear interpolation with a floor cell
+//     lookup clamped to [0, n-2] (Sec. 2.2, Eqs. interp, w0, w1);
+//   - Fehlberg's RKF45 pair with the 4th-order solution propagated; a trial is
+//     accepted when the position error (cells) is <= the line's tolerance;
+//     step growth min(4, 0.9 (tol/err)^(1/5)), shrink max(0.1, 0.9
+//     (tol/err)^(1/4)), h in [h_min, h_max], a reject at h_min is accepted and
+//     flagged (Sec. 2.3);
+//   - at the box exit the accepted step is discarded and one RKF45 step is
+//     taken from the previous point with the face-normal index coordinate as
+//     the independent variable, landing exactly on the face (the paper's "move
+//     one step back", Sec. 2.1); grazing exits halve h and retry;
+//   - per-line tolerance tol_perp max(|Bn0/B|, rot_thresh)^1.5 (Sec. 4, Eq.
+//     tol); seeds of an interior S0 below rot_thresh are queued for the rotated
+//     S0 and traced with tol_perp.
+//
+// GPU design: one lane per line; a warp takes tiles of 8x4 neighbouring seeds
+// from a device work counter (persistent grid) so that the 32 lines of a warp
+// gather from the same cells; a lane whose line is done takes the next seed
+// before the next trial step. Normal trials and exit steps share one 6-stage
+// code path, so a warp only diverges at line start and end. The state is
+// stepped in T; the error norm, the tolerance and the Tw/length sums are FP64.
+#pragma once
+
+#include <math.h>
+
+#include "fqsl_internal.cuh"
+
+namespace fqsl {
+namespace trace {
+
+constexpr int kChunk = kTileU * kTileV;  // work items per queue grab
+
+// Fehlberg 4(5) coefficients.
+template <typename T>
+struct Fehlberg {
+    static __device__ __forceinline__ T a(int s, int r)
+    {
+        // lower-triangular stage matrix, row s (1..5), column r < s
+        const double A[6][5] = {{0, 0, 0, 0, 0},
+                                {1.0 / 4.0, 0, 0, 0, 0},
+                                {3.0 / 32.0, 9.0 / 32.0, 0, 0, 0},
+                                {1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0, 0, 0},
+                                {439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0, 0},
+                                {-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0}};
+        return (T)A[s][r];
+    }
+    static __device__ __forceinline__ T b4(int s)
+    {
+        const double B[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0};
+        return (T)B[s];
+    }
+    // 5th minus 4th order weights (error estimate)
+    static __device__ __forceinline__ T e(int s)
+    {
+        const double E[6] = {16.0 / 135.0 - 25.0 / 216.0,
+                             0.0,
+                             6656.0 / 12825.0 - 1408.0 / 2565.0,
+                             28561.0 / 56430.0 - 2197.0 / 4104.0,
+                             -9.0 / 50.0 + 1.0 / 5.0,
+                             2.0 / 55.0};
+        return (T)E[s];
+    }
+};
+
+// ---------------------------------------------------------------------------
+// trilinear gather of B and curl B at index position (x, y, z)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_node(const FieldView &f, long long node, float &bx, float &by, float &bz,
+                                          float &jx, float &jy, float &jz)
+{
+    const float4 *r = (const float4 *)f.rec + 2 * node;
+    const float4 a = __ldg(r);
+    const float4 b = __ldg(r + 1);
+    bx = a.x;
+    by = a.y;
+    bz = a.z;
+    jx = a.w;
+    jy = b.x;
+    jz = b.y;
+}
+
+__device__ __forceinline__ void load_node(const FieldView &f, long long node, double &bx, double &by, double &bz,
+                                          double &jx, double &jy, double &jz)
+{
+    const double2 *r = (const double2 *)f.rec + 4 * node;
+    const double2 a = __ldg(r);
+    const double2 b = __ldg(r + 1);
+    const double2 c = __ldg(r + 2);
+    bx = a.x;
+    by = a.y;
+    bz = b.x;
+    jx = b.y;
+    jy = c.x;
+    jz = c.y;
+}
+
+template <typename T>
+__device__ __forceinline__ T tfloor(T v);
+template <>
+__device__ __forceinline__ float tfloor<float>(float v) { return floorf(v); }
+template <>
+__device__ __forceinline__ double tfloor<double>(double v) { return floor(v); }
+
+template <typename T>
+__device__ __forceinline__ T clampcell(T c, int n)
+{
+    // fmax/fmin return the non-NaN operand: a NaN position maps to cell 0
+    return fmin(fmax(c, (T)0), (T)(n - 2));
+}
+
+template <typename T>
+__device__ __forceinline__ void gather(const FieldView &f, T x, T y, T z, T B[3], T J[3])
+{
+    const T cx = clampcell<T>(tfloor<T>(x), f.nx);
+    const T cy = clampcell<T>(tfloor<T>(y), f.ny);
+    const T cz = clampcell<T>(tfloor<T>(z), f.nz);
+    const T wx = x - cx, wy = y - cy, wz = z - cz;
+    const T ux = (T)1 - wx, uy = (T)1 - wy, uz = (T)1 - wz;
+    const long long sy = f.nx, sz = (long long)f.nx * f.ny;
+    const long long base = (long long)cz * sz + (long long)cy * sy + (long long)cx;
+    const T wyz[4] = {uy * uz, wy * uz, uy * wz, wy * wz};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        B[c] = (T)0;
+        J[c] = (T)0;
+    }
+#pragma unroll
+    for (int qp = 0; qp < 4; qp++) {
+        const long long node = base + (qp & 1) * sy + (qp >> 1) * sz;
+#pragma unroll
+        for (int m = 0; m < 2; m++) {
+            T bx, by, bz, jx, jy, jz;
+            load_node(f, node + m, bx, by, bz, jx, jy, jz);
+            const T w = (m ? wx : ux) * wyz[qp];
+            B[0] += w * bx;
+            B[1] += w * by;
+            B[2] += w * bz;
+            J[0] += w * jx;
+            J[1] += w * jy;
+            J[2] += w * jz;
+        }
+    }
+}
+
+// Right-hand side in index space: out = {F (3), dl/dtau, dTw/dtau}.
+// Returns false on a null / non-finite field.
+__device__ __forceinline__ bool rhs(const FieldView &f, const float invd[3], float sgn, float x, float y, float z,
+                                    float out[5])
+{
+    float B[3], J[3];
+    gather<float>(f, x, y, z, B, J);
+    const float b0 = B[0] * invd[0], b1 = B[1] * invd[1], b2 = B[2] * invd[2];
+    const float bb = b0 * b0 + b1 * b1 + b2 * b2;
+    const float BB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    if (!(bb > 0.f) || !(bb < INFINITY)) return false;
+    const float inv = rsqrtf(bb);
+    const float s = sgn * inv;
+    out[0] = b0 * s;
+    out[1] = b1 * s;
+    out[2] = b2 * s;
+    const float dl = sqrtf(BB) * inv;
+    out[3] = dl;
+    const float JB = J[0] * B[0] + J[1] * B[1] + J[2] * B[2];
+    out[4] = __fdividef(JB * dl, 12.566370614359172f * BB);
+    return true;
+}
+
+__device__ __forceinline__ bool rhs(const FieldView &f, const double invd[3], double sgn, double x, double y,
+                                    double z, double out[5])
+{
+    double B[3], J[3];
+    gather<double>(f, x, y, z, B, J);
+    const double b0 = B[0] * invd[0], b1 = B[1] * invd[1], b2 = B[2] * invd[2];
+    const double bb = b0 * b0 + b1 * b1 + b2 * b2;
+    const double BB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    if (!(bb > 0.0) || !(bb < INFINITY)) return false;
+    const double nbt = sqrt(bb);
+    const double inv = 1.0 / nbt;
+    const double s = sgn * inv;
+    out[0] = b0 * s;
+    out[1] = b1 * s;
+    out[2] = b2 * s;
+    const double dl = sqrt(BB) * inv;
+    out[3] = dl;
+    const double JB = J[0] * B[0] + J[1] * B[1] + J[2] * B[2];
+    out[4] = JB / (12.566370614359172 * BB) * dl;
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T tpow(T a, T b);
+template <>
+__device__ __forceinline__ float tpow<float>(float a, float b) { return __powf(a, b); }
+template <>
+__device__ __forceinline__ double tpow<double>(double a, double b) { return pow(a, b); }
+
+// physical coordinate of an index coordinate, without contraction so that the
+// value matches a plain multiply-then-add
+__device__ __forceinline__ double to_phys(double o, double d, double xi) { return __dadd_rn(o, __dmul_rn(d, xi)); }
+
+template <typename T>
+__device__ __forceinline__ T sel3(int a, T v0, T v1, T v2)
+{
+    return a == 0 ? v0 : (a == 1 ? v1 : v2);
+}
+
+// Seed position of lattice index (i, j, k) in physical coordinates, evaluated
+// as o + t1 + t2 + t3 left to right without contraction.
+__device__ __forceinline__ void lattice_seed(const Lattice &L, long long i, long long j, long long k, double r[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        double v = __dadd_rn(L.o[a], __dmul_rn((double)i + 0.5, L.a1[a]));
+        v = __dadd_rn(v, __dmul_rn((double)j + 0.5, L.a2[a]));
+        v = __dadd_rn(v, __dmul_rn((double)k + 0.5, L.a3[a]));
+        r[a] = v;
+    }
+}
+
+// Orthonormal u, v perpendicular to bhat: u = unit(bhat x e_m) with m the axis
+// of smallest |bhat_m| (lowest index on ties), v = bhat x u.
+__device__ __forceinline__ void perp_frame(const double bh[3], double u[3], double v[3])
+{
+    int m = 0;
+    if (fabs(bh[1]) < fabs(bh[m])) m = 1;
+    if (fabs(bh[2]) < fabs(bh[m])) m = 2;
+    double t[3];
+    // bh x e_m
+    t[0] = (m == 0) ? 0.0 : (m == 1 ? -bh[2] : bh[1]);
+    t[1] = (m == 0) ? bh[2] : (m == 1 ? 0.0 : -bh[0]);
+    t[2] = (m == 0) ? -bh[1] : (m == 1 ? bh[0] : 0.0);
+    const double nt = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    u[0] = t[0] / nt;
+    u[1] = t[1] / nt;
+    u[2] = t[2] / nt;
+    v[0] = bh[1] * u[2] - bh[2] * u[1];
+    v[1] = bh[2] * u[0] - bh[0] * u[2];
+    v[2] = bh[0] * u[1] - bh[1] * u[0];
+}
+
+// B at an index position in double (for seeds, frames and end normals)
+template <typename T>
+__device__ __forceinline__ void b_at(const FieldView &f, double x, double y, double z, double B[3])
+{
+    T Bt[3], Jt[3];
+    gather<T>(f, (T)x, (T)y, (T)z, Bt, Jt);
+    B[0] = (double)Bt[0];
+    B[1] = (double)Bt[1];
+    B[2] = (double)Bt[2];
+}
+
+// ---------------------------------------------------------------------------
+// lane state
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Lane {
+    long long line;   // record index
+    T x, y, z;        // current position (cells)
+    T sx, sy, sz;     // seed position
+    T h;              // current step
+    T s0;             // end 1 is traced along -s0 B
+    T ox, oy, oz;     // end of the exiting step (chord fallback)
+    T t0;             // chord parameter of the first crossed face
+    double tol;
+    double lacc, twacc;  // length / Tw of the current direction
+    double l1, tw1;      // totals of end 1
+    float ol, otw;       // length / Tw increments of the exiting step
+    int steps, st, end, mode, hface, tries, fc0;
+};
+
+template <typename T>
+__device__ __forceinline__ void write_end(const TraceArgs &A, const LineRecs &R, const Lane<T> &L, int e,
+                                          double px, double py, double pz, int face, double bn)
+{
+    double *r = (e == 0 ? R.r1 : R.r2) + 3 * L.line;
+    r[0] = px;
+    r[1] = py;
+    r[2] = pz;
+    (e == 0 ? R.f1 : R.f2)[L.line] = (int8_t)face;
+    double *bnp = (e == 0 ? R.bn1 : R.bn2);
+    if (bnp) bnp[L.line] = bn;
+}
+
+// Finish the line with a bad status (MAXSTEPS or NULL_B): the unfinished end
+// is the current position, an untraced end the seed, their faces -1.
+template <typename T>
+__device__ __forceinline__ void finish_bad(const TraceArgs &A, const LineRecs &R, Lane<T> &L, unsigned bit)
+{
+    const FieldView &f = A.f;
+    L.st |= bit;
+    write_end(A, R, L, L.end, to_phys(f.o[0], f.d[0], (double)L.x), to_phys(f.o[1], f.d[1], (double)L.y),
+              to_phys(f.o[2], f.d[2], (double)L.z), -1, 0.0);
+    if (L.end == 0)
+        write_end(A, R, L, 1, to_phys(f.o[0], f.d[0], (double)L.sx), to_phys(f.o[1], f.d[1], (double)L.sy),
+                  to_phys(f.o[2], f.d[2], (double)L.sz), -1, 0.0);
+    R.st[L.line] = (uint8_t)L.st;
+    R.steps[L.line] = L.steps;
+    if (R.tw) R.tw[L.line] = NAN;
+    if (R.len) R.len[L.line] = NAN;
+}
+
+// A direction reached a face at index position (x, y, z).
+template <typename T>
+__device__ __forceinline__ bool finish_dir(const TraceArgs &A, const LineRecs &R, Lane<T> &L, T x, T y, T z,
+                                           int face)
+{
+    const FieldView &f = A.f;
+    double B[3];
+    b_at<T>(f, (double)x, (double)y, (double)z, B);
+    const int ax = face >> 1;
+    write_end(A, R, L, L.end, to_phys(f.o[0], f.d[0], (double)x), to_phys(f.o[1], f.d[1], (double)y),
+              to_phys(f.o[2], f.d[2], (double)z), face, sel3<double>(ax, B[0], B[1], B[2]));
+    if (L.end == 0) {
+        L.l1 = L.lacc;
+        L.tw1 = L.twacc;
+        L.end = 1;
+        L.x = L.sx;
+        L.y = L.sy;
+        L.z = L.sz;
+        L.h = (T)A.p.h0;
+        L.mode = 0;
+        L.lacc = 0.0;
+        L.twacc = 0.0;
+        return true;
+    }
+    R.st[L.line] = (uint8_t)L.st;
+    R.steps[L.line] = L.steps;
+    if (R.tw) R.tw[L.line] = L.tw1 + L.twacc;
+    if (R.len) R.len[L.line] = L.l1 + L.lacc;
+    return false;
+}
+
+template <typename T>
+__device__ __forceinline__ bool inside(const FieldView &f, T x, T y, T z)
+{
+    return x >= (T)0 && x <= (T)(f.nx - 1) && y >= (T)0 && y <= (T)(f.ny - 1) && z >= (T)0 &&
+           z <= (T)(f.nz - 1);
+}
+
+// Start a line at physical seed r0 with orientation vector n (NULL: end 1 is
+// the backward end). Returns false if the line ends at once (outside / null).
+template <typename T>
+__device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R, Lane<T> &L, const double r0[3],
+                                           const double *n, double tol, int st0)
+{
+    const FieldView &f = A.f;
+    double xi[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) xi[a] = (r0[a] - f.o[a]) / f.d[a];
+    L.sx = (T)xi[0];
+    L.sy = (T)xi[1];
+    L.sz = (T)xi[2];
+    L.x = L.sx;
+    L.y = L.sy;
+    L.z = L.sz;
+    L.st = st0;
+    L.steps = 0;
+    L.end = 0;
+    L.mode = 0;
+    L.lacc = L.twacc = 0.0;
+    L.h = (T)A.p.h0;
+    L.tol = tol;
+    const bool in = xi[0] >= 0.0 && xi[0] <= (double)(f.nx - 1) && xi[1] >= 0.0 && xi[1] <= (double)(f.ny - 1) &&
+                    xi[2] >= 0.0 && xi[2] <= (double)(f.nz - 1);
+    unsigned bad = 0;
+    double B0[3] = {0, 0, 0};
+    if (!in) {
+        bad = FQSL_LINE_OUTSIDE;
+    } else {
+        b_at<T>(f, xi[0], xi[1], xi[2], B0);
+        const double b0 = B0[0] / f.d[0], b1 = B0[1] / f.d[1], b2 = B0[2] / f.d[2];
+        const double bb = b0 * b0 + b1 * b1 + b2 * b2;
+        if (!(bb > 0.0) || !(bb < INFINITY)) bad = FQSL_LINE_NULL_B;
+    }
+    if (bad) {
+        L.st |= bad;
+        const double px = r0[0], py = r0[1], pz = r0[2];
+        // footpoints of a line that never started: its seed (index round trip)
+        const double qx = to_phys(f.o[0], f.d[0], xi[0]), qy = to_phys(f.o[1], f.d[1], xi[1]),
+                     qz = to_phys(f.o[2], f.d[2], xi[2]);
+        (void)px;
+        (void)py;
+        (void)pz;
+        write_end(A, R, L, 0, qx, qy, qz, -1, 0.0);
+        write_end(A, R, L, 1, qx, qy, qz, -1, 0.0);
+        R.st[L.line] = (uint8_t)L.st;
+        R.steps[L.line] = 0;
+        if (R.tw) R.tw[L.line] = NAN;
+        if (R.len) R.len[L.line] = NAN;
+        return false;
+    }
+    L.s0 = (T)1;
+    if (n && (B0[0] * n[0] + B0[1] * n[1] + B0[2] * n[2] < 0.0)) L.s0 = (T)-1;
+    return true;
+}
+
+// Lattice seed: frame, tolerance and rotation decision (Sec. 4).
+template <typename T>
+__device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, long long item)
+{
+    const Lattice &G = A.lat;
+    const long long per_tile = kTileU * kTileV;
+    const long long w = item % per_tile;
+    long long t = item / per_tile;
+    const long long tu = t % G.tiles_u;
+    t /= G.tiles_u;
+    const long long tv = t % G.tiles_v;
+    const long long k = t / G.tiles_v;
+    const long long i = tu * kTileU + (w % kTileU);
+    const long long j = tv * kTileV + (w / kTileU);
+    if (i >= G.n1 || j >= G.n2 || k >= G.n3) return false;
+    const long long idx = i + G.n1 * (j + G.n2 * k);
+    L.line = idx;
+    double r0[3];
+    lattice_seed(G, i, j, k, r0);
+    const FieldView &f = A.f;
+    const LineRecs &R = A.rec;
+    // B at the seed, S0 obliquity and tolerance
+    double xi[3], B0[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) xi[a] = (r0[a] - f.o[a]) / f.d[a];
+    double tol = A.p.tol;
+    int st0 = 0;
+    double bn0 = 0.0;
+    const bool in = xi[0] >= 0.0 && xi[0] <= (double)(f.nx - 1) && xi[1] >= 0.0 && xi[1] <= (double)(f.ny - 1) &&
+                    xi[2] >= 0.0 && xi[2] <= (double)(f.nz - 1);
+    if (in) {
+        b_at<T>(f, xi[0], xi[1], xi[2], B0);
+        const double nB = sqrt(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
+        if (nB > 0.0 && nB < INFINITY) {
+            const double bn = B0[0] * G.n0[0] + B0[1] * G.n0[1] + B0[2] * G.n0[2];
+            if (A.p.method == 2) {
+                bn0 = nB;
+            } else {
+                const double ratio = fabs(bn) / nB;
+                bool on_face = false;
+                if (G.normal_axis >= 0) {
+                    const double xa = xi[G.normal_axis];
+                    const int na = G.normal_axis == 0 ? f.nx : (G.normal_axis == 1 ? f.ny : f.nz);
+                    on_face = (xa == 0.0) || (xa == (double)(na - 1));
+                }
+                if (G.allow_rot && ratio < A.p.rot && !on_face) {
+                    st0 = FQSL_LINE_ROTATED;
+                    bn0 = nB;
+                    const unsigned slot = atomicAdd(A.q.rot_count, 1u);
+                    A.q.rot_seed[slot] = (int32_t)idx;
+                    A.q.rot_slot[idx] = (int32_t)slot + 1;
+                } else {
+                    bn0 = bn;
+                    tol = A.p.tol * pow(fmax(ratio, A.p.rot), A.p.texp);
+                }
+            }
+        }
+    }
+    R.bn0[idx] = bn0;
+    return start_line<T>(A, R, L, r0, G.n0, tol, st0);
+}
+
+// Rotated extra line q (0: +u, 1: -u, 2: +v, 3: -v) of rotated slot s (Sec. 4).
+template <typename T>
+__device__ __forceinline__ bool init_extra(const TraceArgs &A, Lane<T> &L, long long item)
+{
+    const Lattice &G = A.lat;
+    const long long s = item >> 2;
+    const int q = (int)(item & 3);
+    const long long idx = A.q.rot_seed[s];
+    const long long i = idx % G.n1, j = (idx / G.n1) % G.n2, k = idx / (G.n1 * G.n2);
+    double r0[3];
+    lattice_seed(G, i, j, k, r0);
+    const FieldView &f = A.f;
+    double xi[3], B0[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) xi[a] = (r0[a] - f.o[a]) / f.d[a];
+    b_at<T>(f, xi[0], xi[1], xi[2], B0);
+    const double nB = sqrt(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
+    double bh[3] = {B0[0] / nB, B0[1] / nB, B0[2] / nB}, u[3], v[3];
+    perp_frame(bh, u, v);
+    const double sc = (B0[0] * G.n0[0] + B0[1] * G.n0[1] + B0[2] * G.n0[2] < 0.0) ? -1.0 : 1.0;
+    const double nrot[3] = {sc * bh[0], sc * bh[1], sc * bh[2]};
+    const double *dir = (q < 2) ? u : v;
+    const double sg = (q & 1) ? -1.0 : 1.0;
+    double rr[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) rr[a] = r0[a] + sg * G.drot * dir[a];
+    L.line = item;
+    return start_line<T>(A, A.ext, L, rr, nrot, A.p.tol, 0);
+}
+
+template <typename T>
+__device__ __forceinline__ bool init_list(const TraceArgs &A, Lane<T> &L, long long item)
+{
+    L.line = item;
+    const double r0[3] = {A.seeds[3 * item], A.seeds[3 * item + 1], A.seeds[3 * item + 2]};
+    return start_line<T>(A, A.rec, L, r0, nullptr, A.p.tol, 0);
+}
+
+// ---------------------------------------------------------------------------
+// the persistent kernel body
+// ---------------------------------------------------------------------------
+template <typename T, int SRC>
+__device__ __forceinline__ void trace_body(const TraceArgs &A)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const FieldView &f = A.f;
+    const LineRecs &R = (SRC == kSrcExtra) ? A.ext : A.rec;
+    const T invd[3] = {(T)(1.0 / f.d[0]), (T)(1.0 / f.d[1]), (T)(1.0 / f.d[2])};
+    const T hmin = (T)A.p.hmin, hmax = (T)A.p.hmax;
+    const T graze = (T)A.p.graze;
+    const int max_steps = (int)A.p.max_steps;
+
+    long long nitems = A.nitems;
+    if (SRC == kSrcExtra) nitems = 4LL * (long long)(*(volatile unsigned *)A.q.rot_count);
+
+    long long ck_cur = 0, ck_end = 0;
+    bool exhausted = false;
+    bool active = false;
+    Lane<T> L;
+    L.line = 0;
+
+    for (;;) {
+        // refill idle lanes from the warp's chunk / the global counter
+        unsigned idle = __ballot_sync(FULL, !active);
+        while (idle != 0u && !exhausted) {
+            if (ck_cur >= ck_end) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(A.q.head, (unsigned long long)kChunk);
+                base = __shfl_sync(FULL, base, 0);
+                if ((long long)base >= nitems) {
+                    exhausted = true;
+                    break;
+                }
+                ck_cur = (long long)base;
+                ck_end = min(ck_cur + (long long)kChunk, nitems);
+            }
+            const long long avail = ck_end - ck_cur;
+            const int rank = __popc(idle & lt_mask);
+            if (!active && rank < avail) {
+                const long long item = ck_cur + rank;
+                if (SRC == kSrcLattice) active = init_lattice<T>(A, L, item);
+                else if (SRC == kSrcExtra) active = init_extra<T>(A, L, item);
+                else active = init_list<T>(A, L, item);
+            }
+            ck_cur += min((long long)__popc(idle), avail);
+            idle = __ballot_sync(FULL, !active);
+        }
+        if (__ballot_sync(FULL, active) == 0u) break;
+        if (!active) continue;
+
+        // ---- one trial: normal RKF45 step or exit (Henon) step ----
+        const bool henon = L.mode != 0;
+        const int hax = L.hface >> 1;
+        const int hmaxside = L.hface & 1;
+        const T hsign = hmaxside ? (T)1 : (T)-1;
+        const int nax = hax == 0 ? f.nx : (hax == 1 ? f.ny : f.nz);
+        const T target = hmaxside ? (T)(nax - 1) : (T)0;
+        const T sgn = (L.end == 0) ? -L.s0 : L.s0;
+        T hh;
+        if (!henon) {
+            if (L.steps >= max_steps) {
+                finish_bad(A, R, L, FQSL_LINE_MAXSTEPS);
+                active = false;
+                continue;
+            }
+            hh = L.h;
+        } else {
+            hh = target - sel3<T>(hax, L.x, L.y, L.z);
+        }
+        L.steps++;
+
+        T k0[5], k1[5], k2[5];  // position derivatives of stages 1..5
+        T a4[3] = {0, 0, 0}, e5[3] = {0, 0, 0};
+        T l4 = 0, tw4 = 0;
+        bool nul = false, grz = false;
+#pragma unroll
+        for (int s = 0; s < 6; s++) {
+            T px = 0, py = 0, pz = 0;
+#pragma unroll
+            for (int r = 0; r < s; r++) {
+                const T c = Fehlberg<T>::a(s, r);
+                px += c * k0[r];
+                py += c * k1[r];
+                pz += c * k2[r];
+            }
+            px = L.x + hh * px;
+            py = L.y + hh * py;
+            pz = L.z + hh * pz;
+            T o[5];
+            nul |= !rhs(f, invd, sgn, px, py, pz, o);
+            if (henon) {
+                const T fa = sel3<T>(hax, o[0], o[1], o[2]);
+                const bool bad = !(fa * hsign >= graze);
+                grz |= bad;
+                const T inv = bad ? (T)0 : (T)1 / fa;
+#pragma unroll
+                for (int c = 0; c < 5; c++) o[c] *= inv;
+            }
+            if (s < 5) {
+                k0[s] = o[0];
+                k1[s] = o[1];
+                k2[s] = o[2];
+            }
+            const T b = Fehlberg<T>::b4(s), e = Fehlberg<T>::e(s);
+            a4[0] += b * o[0];
+            a4[1] += b * o[1];
+            a4[2] += b * o[2];
+            e5[0] += e * o[0];
+            e5[1] += e * o[1];
+            e5[2] += e * o[2];
+            l4 += b * o[3];
+            tw4 += b * o[4];
+        }
+
+        if (nul) {
+            finish_bad(A, R, L, FQSL_LINE_NULL_B);
+            active = false;
+            continue;
+        }
+        if (!henon) {
+            const double ex = (double)e5[0], ey = (double)e5[1], ez = (double)e5[2];
+            const double err = (double)hh * sqrt(ex * ex + ey * ey + ez * ez);
+            if (err > L.tol) {
+                if (L.h > hmin) {
+                    T hn = L.h * (T)fmax(0.1, 0.9 * (double)tpow<T>((T)(L.tol / err), (T)0.25));
+                    L.h = hn < hmin ? hmin : hn;
+                    continue;
+                }
+                L.st |= FQSL_LINE_STALL;
+            }
+            T hn = (err > 0.0) ? L.h * (T)fmin(4.0, 0.9 * (double)tpow<T>((T)(L.tol / err), (T)0.2)) : (T)4 * L.h;
+            hn = hn < hmin ? hmin : (hn > hmax ? hmax : hn);
+            const T nx = L.x + hh * a4[0], ny = L.y + hh * a4[1], nz = L.z + hh * a4[2];
+            if (inside<T>(f, nx, ny, nz)) {
+                L.x = nx;
+                L.y = ny;
+                L.z = nz;
+                L.lacc += (double)(hh * l4);
+                L.twacc += (double)(hh * tw4);
+                L.h = hn;
+                continue;
+            }
+            // exit: the first face the chord crosses (ties: lower axis first)
+            int best = -1;
+            T tb = (T)INFINITY;
+            const T cur[3] = {L.x, L.y, L.z}, nxt[3] = {nx, ny, nz};
+            const int nn[3] = {f.nx, f.ny, f.nz};
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const T hi = (T)(nn[a] - 1);
+                T t;
+                int fc;
+                if (nxt[a] < (T)0) {
+                    t = ((T)0 - cur[a]) / (nxt[a] - cur[a]);
+                    fc = 2 * a;
+                } else if (nxt[a] > hi) {
+                    t = (hi - cur[a]) / (nxt[a] - cur[a]);
+                    fc = 2 * a + 1;
+                } else {
+                    continue;
+                }
+                if (t < tb) {
+                    tb = t;
+                    best = fc;
+                }
+            }
+            L.ox = nx;
+            L.oy = ny;
+            L.oz = nz;
+            L.ol = (float)(hh * l4);
+            L.otw = (float)(hh * tw4);
+            L.t0 = tb;
+            L.fc0 = best;
+            L.hface = best;
+            L.tries = 0;
+            L.mode = 1;
+            continue;
+        }
+        // exit step
+        if (grz) {
+            L.mode = 0;
+            if ((T)0.5 * L.h >= hmin) {
+                L.h = (T)0.5 * L.h;
+                continue;
+            }
+            // chord fallback onto the first crossed face
+            T ex = L.x + L.t0 * (L.ox - L.x), ey = L.y + L.t0 * (L.oy - L.y), ez = L.z + L.t0 * (L.oz - L.z);
+            const int a0 = L.fc0 >> 1;
+            const int n0 = a0 == 0 ? f.nx : (a0 == 1 ? f.ny : f.nz);
+            const T v0 = (L.fc0 & 1) ? (T)(n0 - 1) : (T)0;
+            if (a0 == 0) ex = v0;
+            else if (a0 == 1) ey = v0;
+            else ez = v0;
+            L.lacc += (double)L.t0 * (double)L.ol;
+            L.twacc += (double)L.t0 * (double)L.otw;
+            L.st |= FQSL_LINE_CHORD;
+            active = finish_dir<T>(A, R, L, ex, ey, ez, L.fc0);
+            continue;
+        }
+        T tx = L.x + hh * a4[0], ty = L.y + hh * a4[1], tz = L.z + hh * a4[2];
+        if (hax == 0) tx = target;
+        else if (hax == 1) ty = target;
+        else tz = target;
+        int nf = -1;
+        {
+            const T tt[3] = {tx, ty, tz};
+            const int nn[3] = {f.nx, f.ny, f.nz};
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                if (b == hax || nf >= 0) continue;
+                if (tt[b] < (T)0) nf = 2 * b;
+                else if (tt[b] > (T)(nn[b] - 1)) nf = 2 * b + 1;
+            }
+        }
+        if (nf >= 0 && L.tries < 2) {
+            L.hface = nf;
+            L.tries++;
+            continue;
+        }
+        if (nf >= 0) {
+            tx = fmin(fmax(tx, (T)0), (T)(f.nx - 1));
+            ty = fmin(fmax(ty, (T)0), (T)(f.ny - 1));
+            tz = fmin(fmax(tz, (T)0), (T)(f.nz - 1));
+        }
+        L.lacc += (double)(hh * l4);
+        L.twacc += (double)(hh * tw4);
+        active = finish_dir<T>(A, R, L, tx, ty, tz, L.hface);
+    }
+}
+
+}  // namespace trace
+}  // namespace fqsl

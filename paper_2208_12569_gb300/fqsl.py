@@ -1,0 +1,214 @@
+"""Thin Python binding of libfqsl.so (include/fqsl.h).
+
+Argument marshalling only: torch supplies device memory and the current CUDA
+stream; every step of the computation runs in the library's CUDA kernels. If
+the library is missing this module raises at import time -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfqsl.so")
+
+F32, F64 = 0, 1
+PACK_F32, PACK_F64 = 1, 2
+LINE_MAXSTEPS, LINE_NULL_B, LINE_STALL, LINE_MIXED, LINE_OUTSIDE, LINE_ROTATED, LINE_CHORD = 1, 2, 4, 8, 16, 32, 64
+LINE_BAD = LINE_MAXSTEPS | LINE_NULL_B | LINE_OUTSIDE
+EXPORTS = ("fqsl_params_default", "fqsl_version", "fqsl_last_error", "fqsl_field_create", "fqsl_field_destroy",
+           "fqsl_qmap_plane", "fqsl_qmap_volume", "fqsl_twist", "fqsl_field_check", "fqsl_field_set_timing",
+           "fqsl_field_times", "fqsl_field_update")
+
+
+class FqslError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("fqsl status %d: %s" % (status, msg))
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("method", C.c_int), ("gradb_way", C.c_int), ("precision", C.c_int), ("reserved0", C.c_int),
+                ("tol", C.c_double), ("h0", C.c_double), ("h_min", C.c_double), ("h_max", C.c_double),
+                ("max_steps", C.c_longlong), ("rot_thresh", C.c_double), ("tol_exp", C.c_double),
+                ("graze", C.c_double), ("eps_way2", C.c_double)]
+
+
+class Out(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("Q", "Tw", "length", "r1", "r2", "face1", "face2", "status", "steps")]
+
+
+def load(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError("libfqsl.so not found at %s: build it with __graft_entry__.build() "
+                          "(the fqsl library has no CPU fallback)" % path)
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.fqsl_params_default.argtypes = [C.POINTER(Params)]
+    lib.fqsl_params_default.restype = None
+    lib.fqsl_version.restype = C.c_char_p
+    lib.fqsl_last_error.restype = C.c_char_p
+    lib.fqsl_field_create.argtypes = [P, C.c_int, C.c_longlong, C.c_longlong, C.c_longlong, P, P, C.c_uint, P,
+                                      C.POINTER(P)]
+    lib.fqsl_field_destroy.argtypes = [P]
+    lib.fqsl_qmap_plane.argtypes = [P, P, P, P, C.c_longlong, C.c_longlong, C.POINTER(Params), C.POINTER(Out), P]
+    lib.fqsl_qmap_volume.argtypes = [P, P, P, C.c_longlong, C.c_longlong, C.c_longlong, C.POINTER(Params),
+                                     C.POINTER(Out), P]
+    lib.fqsl_twist.argtypes = [P, P, C.c_longlong, C.POINTER(Params), C.POINTER(Out), P]
+    lib.fqsl_field_check.argtypes = [P, P]
+    lib.fqsl_field_set_timing.argtypes = [P, C.c_int]
+    lib.fqsl_field_update.argtypes = [P, P, C.c_int, P]
+    lib.fqsl_field_times.argtypes = [P, C.POINTER(C.c_float * 3)]
+    for name in EXPORTS:
+        if name not in ("fqsl_params_default", "fqsl_version", "fqsl_last_error"):
+            getattr(lib, name).restype = C.c_int
+    return lib
+
+
+_lib = load()
+
+
+def version() -> str:
+    return _lib.fqsl_version().decode()
+
+
+def _check(status):
+    if status != 0:
+        raise FqslError(status, _lib.fqsl_last_error().decode())
+
+
+def params(**kw) -> Params:
+    """fqsl_params with the library defaults, overridden by keyword
+    (method, gradb_way, precision ('f32'/'f64' or 0/1), tol, h0, h_min, h_max,
+    max_steps, rot_thresh, tol_exp, graze, eps_way2)."""
+    p = Params()
+    _lib.fqsl_params_default(C.byref(p))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"f32": F32, "f64": F64}[v]
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _vec3(v):
+    return (C.c_double * 3)(*[float(x) for x in v])
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Field:
+    """A field handle: B (torch CUDA tensor (nz, ny, nx, 3), float32 or float64)
+    packed with its curl into node records (pack: 'f32', 'f64' or both)."""
+
+    def __init__(self, B: torch.Tensor, origin, spacing, pack=("f32", "f64"), stream=None):
+        if not (isinstance(B, torch.Tensor) and B.is_cuda and B.dim() == 4 and B.shape[-1] == 3):
+            raise ValueError("B must be a CUDA tensor of shape (nz, ny, nx, 3)")
+        if B.dtype not in (torch.float32, torch.float64):
+            raise ValueError("B must be float32 or float64")
+        B = B.contiguous()
+        nz, ny, nx, _ = B.shape
+        flags = (PACK_F32 if "f32" in pack else 0) | (PACK_F64 if "f64" in pack else 0)
+        h = C.c_void_p()
+        _check(_lib.fqsl_field_create(C.c_void_p(B.data_ptr()), F32 if B.dtype == torch.float32 else F64, nx, ny,
+                                      nz, _vec3(origin), _vec3(spacing), flags, _stream(stream), C.byref(h)))
+        self._h = h
+        self.n = (nx, ny, nz)
+        self.origin = tuple(float(v) for v in origin)
+        self.spacing = tuple(float(v) for v in spacing)
+        self._keep = B  # the packing kernel reads B asynchronously
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, stream=None):
+        _check(_lib.fqsl_field_check(self._h, _stream(stream)))
+
+    def update(self, B: torch.Tensor, stream=None):
+        """Repack a new B of the same shape (a later snapshot) into this handle."""
+        if not (isinstance(B, torch.Tensor) and B.is_cuda and tuple(B.shape) == (self.n[2], self.n[1], self.n[0], 3)):
+            raise ValueError("B must be a CUDA tensor of shape (nz, ny, nx, 3) matching the field")
+        B = B.contiguous()
+        _check(_lib.fqsl_field_update(self._h, C.c_void_p(B.data_ptr()), F32 if B.dtype == torch.float32 else F64,
+                                      _stream(stream)))
+        self._keep = B
+
+    def set_timing(self, enable: bool = True):
+        """Record CUDA events around this field's kernels on each call's stream."""
+        _check(_lib.fqsl_field_set_timing(self._h, 1 if enable else 0))
+
+    def times(self):
+        """(tracer ms, rotated-extra tracer ms, assembly ms) of the last call."""
+        ms = (C.c_float * 3)()
+        _check(_lib.fqsl_field_times(self._h, C.byref(ms)))
+        return tuple(float(v) for v in ms)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.fqsl_field_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def alloc_out(n: int, device="cuda", q=True):
+    """Device output buffers for n seeds."""
+    f64 = dict(dtype=torch.float64, device=device)
+    return dict(Q=torch.empty(n, **f64) if q else None, Tw=torch.empty(n, **f64), length=torch.empty(n, **f64),
+                r1=torch.empty((n, 3), **f64), r2=torch.empty((n, 3), **f64),
+                face1=torch.empty(n, dtype=torch.int8, device=device),
+                face2=torch.empty(n, dtype=torch.int8, device=device),
+                status=torch.empty(n, dtype=torch.uint8, device=device),
+                steps=torch.empty(n, dtype=torch.int32, device=device))
+
+
+def _out_struct(out):
+    o = Out()
+    for name, _ in Out._fields_:
+        t = out.get(name)
+        setattr(o, name, None if t is None else t.data_ptr())
+    return o
+
+
+def qmap_plane(field: Field, origin, u, v, nu: int, nv: int, p: Params | None = None, out=None, stream=None):
+    """Q, Tw, length, footpoints, faces, status, steps on the plane lattice
+    origin + (i+1/2) u + (j+1/2) v (index i + nu j)."""
+    p = p or params()
+    out = out or alloc_out(nu * nv)
+    _check(_lib.fqsl_qmap_plane(field.handle, _vec3(origin), _vec3(u), _vec3(v), nu, nv, C.byref(p),
+                                C.byref(_out_struct(out)), _stream(stream)))
+    return out
+
+
+def qmap_volume(field: Field, origin, step, nx: int, ny: int, nz: int, p: Params | None = None, out=None,
+                stream=None):
+    """The same on the volume lattice origin + (i+1/2, j+1/2, k+1/2) * step."""
+    p = p or params()
+    out = out or alloc_out(nx * ny * nz)
+    _check(_lib.fqsl_qmap_volume(field.handle, _vec3(origin), _vec3(step), nx, ny, nz, C.byref(p),
+                                 C.byref(_out_struct(out)), _stream(stream)))
+    return out
+
+
+def twist(field: Field, seeds: torch.Tensor, p: Params | None = None, out=None, stream=None):
+    """Tw, length, footpoints for explicit seeds (CUDA float64 tensor (n, 3))."""
+    p = p or params()
+    seeds = seeds.to(torch.float64).contiguous()
+    n = seeds.shape[0]
+    out = out or alloc_out(n, q=False)
+    _check(_lib.fqsl_twist(field.handle, C.c_void_p(seeds.data_ptr()), n, C.byref(p), C.byref(_out_struct(out)),
+                           _stream(stream)))
+    return out

@@ -1,0 +1,215 @@
+"""CUDA path vs the FP64 oracle on the same seeded inputs, through the C ABI.
+
+FP64 tracer: Q and Tw within the parity bars (median relative error <= 1e-9,
+99th percentile <= 1e-4 for Q < 1e6), exit faces, status bits and footpoint
+cells bit-exact. FP32 tracer: its error against the oracle is measured and
+bounded loosely (it is reported, not gated at FP64 level)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import assert_exact_ints, assert_fp64_parity, footpoint_cells_exact, q_rel, to_np, tw_rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2208_12569_gb300 as m
+
+    return m
+
+
+def _field(fq, B, grid):
+    return fq.Field(torch.from_numpy(np.ascontiguousarray(B)).cuda(), grid.origin, grid.spacing)
+
+
+def _gpu_plane(fq, field, origin, u, v, nu, nv, **kw):
+    out = fq.qmap_plane(field, origin, u, v, nu, nv, fq.params(**kw))
+    field.check()
+    return to_np(out)
+
+
+G1 = synth.C1_GRID
+D1 = 2.0 / 128
+
+
+@pytest.mark.parametrize("kind", ["hyperbolic", "rotation", "uniform", "shear", "expanding"])
+@pytest.mark.parametrize("tol", [1e-10, 10 ** -3.2])
+def test_c1_analytic_fp64_parity(fq, oracle_lib, kind, tol):
+    """Analytic 64^3 fields, 128x128 cell-centred seeds on z=0."""
+    B = synth.analytic_cube(kind)
+    field = _field(fq, B, G1)
+    args = ((-1.0, -1.0, 0.0), (D1, 0, 0), (0, D1, 0), 128, 128)
+    g = _gpu_plane(fq, field, *args, precision="f64", tol=tol)
+    r = oracle.plane(B, G1, *args, oracle.params(tol=tol))
+    assert_fp64_parity(g, r)
+    footpoint_cells_exact(g, r, G1)
+
+
+def test_c1_closed_forms_on_gpu(fq, oracle_lib):
+    """The closed forms themselves, on the FP64 and FP32 paths."""
+    X, Y = np.meshgrid(-1 + (np.arange(128) + 0.5) * D1, -1 + (np.arange(128) + 0.5) * D1, indexing="xy")
+    X, Y = X.ravel(), Y.ravel()
+    args = ((-1.0, -1.0, 0.0), (D1, 0, 0), (0, D1, 0), 128, 128)
+    e2 = math.e ** 2 + math.e ** -2
+    for prec, tolq in (("f64", 1e-8), ("f32", 2e-3)):
+        field = _field(fq, synth.analytic_cube("hyperbolic"), G1)
+        g = _gpu_plane(fq, field, *args, precision=prec, tol=1e-10 if prec == "f64" else 1e-5)
+        top = np.abs(X) < 1 / math.e - 2 * D1
+        assert np.max(np.abs(g["Q"][top] / e2 - 1)) < tolq
+        field = _field(fq, synth.analytic_cube("rotation"), G1)
+        g = _gpu_plane(fq, field, *args, precision=prec, tol=1e-10 if prec == "f64" else 1e-5)
+        R = np.hypot(X, Y)
+        inn = R < 0.95
+        q = 2 * math.pi
+        assert np.max(np.abs(g["Q"][inn] - 2)) < 2 * tolq
+        assert np.max(np.abs(g["Tw"][inn] - q / (2 * math.pi * np.sqrt(1 + q * q * R[inn] ** 2)))) < tolq
+        field = _field(fq, synth.analytic_cube("uniform"), G1)
+        g = _gpu_plane(fq, field, *args, precision=prec)
+        assert np.max(np.abs(g["Q"] - 2)) < 1e-6 and np.max(np.abs(g["Tw"])) < 1e-7
+
+
+@pytest.fixture(scope="module")
+def mono():
+    grid = synth.Grid((64, 56, 32), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    ch = synth.random_charges(np.random.default_rng(2208), 10, ((0.0, 63.0), (0.0, 55.0)), depth=(4.0, 12.0))
+    B = synth.monopole_cube(grid, ch, dtype=np.float32)
+    return B, grid
+
+
+def test_monopole_plane_fp64_parity_ragged(fq, oracle_lib, mono):
+    """Several tiles and ragged tails (101 x 75 seeds, 8x4 tiles)."""
+    B, grid = mono
+    field = _field(fq, B, grid)
+    nu, nv = 101, 75
+    args = ((0.0, 0.0, 0.0), (63.0 / nu, 0, 0), (0, 55.0 / nv, 0), nu, nv)
+    g = _gpu_plane(fq, field, *args, precision="f64")
+    r = oracle.plane(B.astype(np.float64), grid, *args, oracle.params())
+    assert_fp64_parity(g, r)
+    footpoint_cells_exact(g, r, grid)
+    assert np.array_equal(g["steps"], r["steps"]) or np.mean(g["steps"] == r["steps"]) > 0.99
+
+
+def test_monopole_plane_fp32_error_stated(fq, oracle_lib, mono):
+    B, grid = mono
+    field = _field(fq, B, grid)
+    nu, nv = 101, 75
+    args = ((0.0, 0.0, 0.0), (63.0 / nu, 0, 0), (0, 55.0 / nv, 0), nu, nv)
+    g = _gpu_plane(fq, field, *args, precision="f32")
+    r = oracle.plane(B.astype(np.float64), grid, *args, oracle.params())
+    assert np.mean(g["face2"] == r["face2"]) > 0.99
+    rel = q_rel(g, r)
+    both = np.isfinite(g["Q"]) & np.isfinite(r["Q"])
+    assert np.mean(both) > 0.95
+    assert np.median(rel[np.isfinite(rel)]) < 1e-3
+    assert np.median(tw_rel(g, r)[np.isfinite(tw_rel(g, r))]) < 1e-4
+
+
+def test_interior_plane_rotation_parity(fq, oracle_lib, mono):
+    """A vertical interior plane (xz at mid-y): near-tangent seeds rotate S0
+    and trace four extra lines (Sec. 4)."""
+    B, grid = mono
+    field = _field(fq, B, grid)
+    nu, nv = 70, 36
+    args = ((0.0, 27.5, 0.0), (63.0 / nu, 0, 0), (0, 0, 31.0 / nv), nu, nv)
+    g = _gpu_plane(fq, field, *args, precision="f64")
+    r = oracle.plane(B.astype(np.float64), grid, *args, oracle.params())
+    assert (r["status"] & oracle.ROTATED).sum() > 5
+    assert_fp64_parity(g, r)
+
+
+def test_tilted_field_rotation_q2(fq, oracle_lib):
+    B = synth.analytic_cube("tilted")
+    field = _field(fq, B, G1)
+    d = 2.0 / 32
+    g = _gpu_plane(fq, field, (-1.0, -1.0, 0.5), (d, 0, 0), (0, d, 0), 32, 32, precision="f64", tol=1e-10)
+    assert np.all(g["status"] & 32)
+    assert np.max(np.abs(g["Q"] - 2)) < 1e-10
+
+
+def test_volume_parity(fq, oracle_lib, mono):
+    B, grid = mono
+    field = _field(fq, B, grid)
+    step = (63.0 / 20, 55.0 / 18, 31.0 / 6)
+    g = to_np(fq.qmap_volume(field, (0.0, 0.0, 0.0), step, 20, 18, 6, fq.params(precision="f64")))
+    field.check()
+    r = oracle.qmap(B.astype(np.float64), grid, (0.0, 0.0, 0.0), (step[0], 0, 0), (0, step[1], 0), (0, 0, step[2]),
+                    (20, 18, 6), oracle.params())
+    assert_fp64_parity(g, r)
+
+
+def test_twist_list_parity(fq, oracle_lib, mono):
+    B, grid = mono
+    field = _field(fq, B, grid)
+    rng = np.random.default_rng(3)
+    seeds = np.concatenate([rng.uniform([0, 0, 0], [63, 55, 31], size=(500, 3)),
+                            [[70.0, 1.0, 1.0], [-0.5, 3.0, 3.0]]])  # two outside the box
+    g = to_np(fq.twist(field, torch.from_numpy(seeds).cuda(), fq.params(precision="f64")))
+    field.check()
+    r = oracle.twist(B.astype(np.float64), grid, seeds, oracle.params())
+    assert_fp64_parity(g, r)
+    assert np.all(g["status"][-2:] == 16)
+    for k in ("r1", "r2"):
+        ok = (r["status"] & 19) == 0
+        assert np.max(np.abs(g[k][ok] - r[k][ok])) < 1e-6
+
+
+def test_edge_cases(fq, oracle_lib):
+    # closed loops stop at max_steps; zero field is NULL_B; single-seed lattice; empty list
+    B = synth.analytic_cube("loops")
+    field = _field(fq, B, G1)
+    seeds = torch.tensor([[0.5, 0.0, 0.5]], dtype=torch.float64, device="cuda")
+    for prec in ("f64", "f32"):
+        g = to_np(fq.twist(field, seeds, fq.params(precision=prec, tol=1e-6, max_steps=2000)))
+        assert g["status"][0] & 1 and np.isnan(g["Tw"][0]) and g["steps"][0] == 2000
+    field = _field(fq, synth.analytic_cube("zero"), G1)
+    g = _gpu_plane(fq, field, (-1.0, -1.0, 0.0), (D1, 0, 0), (0, D1, 0), 4, 4, precision="f64")
+    assert np.all(g["status"] == 2) and np.all(np.isnan(g["Q"]))
+    field = _field(fq, synth.analytic_cube("uniform"), G1)
+    g = _gpu_plane(fq, field, (-0.5, -0.5, 0.0), (1.0, 0, 0), (0, 1.0, 0), 1, 1, precision="f64")
+    assert g["status"][0] == 8 and np.isnan(g["Q"][0]) and abs(g["Tw"][0]) < 1e-12
+    out = fq.twist(field, torch.zeros((0, 3), dtype=torch.float64, device="cuda"))
+    assert out["Tw"].numel() == 0
+    # a plane partly outside the box
+    g = _gpu_plane(fq, field, (0.9, -0.1, 0.0), (0.1, 0, 0), (0, 0.1, 0), 4, 2, precision="f64")
+    assert list(g["status"][:4]) == [0, 16, 16, 16]
+
+
+def test_argument_errors(fq):
+    field = _field(fq, synth.analytic_cube("uniform"), G1)
+    with pytest.raises(fq.FqslError):
+        fq.qmap_plane(field, (0, 0, 0), (1, 0, 0), (1, 0, 0), 2, 2)  # u parallel to v
+    with pytest.raises(fq.FqslError):
+        fq.qmap_plane(field, (0, 0, 0), (0.1, 0, 0), (0, 0.1, 0), 2, 2, fq.params(tol=-1.0))
+    f32only = fq.Field(torch.from_numpy(synth.analytic_cube("uniform")).cuda(), G1.origin, G1.spacing,
+                       pack=("f32",))
+    with pytest.raises(fq.FqslError) as ei:
+        fq.qmap_plane(f32only, (0, 0, 0), (0.1, 0, 0), (0, 0.1, 0), 2, 2, fq.params(precision="f64"))
+    assert ei.value.status == 5
+
+
+def test_c2_full_size_sampled_parity(fq, oracle_lib):
+    """The benchmark workload at full size (256x256x128 FP32 monopole cube,
+    1024x1024 seeds on z=0) in the benchmark's launch configuration; the oracle
+    recomputes a seeded random sample of seeds one by one."""
+    B, grid, _ = synth.c2_monopole()
+    field = _field(fq, B, grid)
+    n = 1024
+    args = ((0.0, 0.0, 0.0), (255.0 / n, 0, 0), (0, 255.0 / n, 0), n, n)
+    g64 = _gpu_plane(fq, field, *args, precision="f64")
+    g32 = _gpu_plane(fq, field, *args, precision="f32")
+    sample = np.sort(np.random.default_rng(11).choice(n * n, 400, replace=False))
+    r = oracle.plane(B.astype(np.float64), grid, *args, oracle.params(), sample=sample)
+    gs = {k: v[sample] for k, v in g64.items()}
+    assert_fp64_parity(gs, r)
+    g32s = {k: v[sample] for k, v in g32.items()}
+    assert np.mean(g32s["face2"] == r["face2"]) > 0.98
+    rel = q_rel(g32s, r)
+    assert np.median(rel[np.isfinite(rel)]) < 1e-3
