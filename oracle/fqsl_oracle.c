@@ -28,11 +28,16 @@
  *       dl/dtau; length and Tw are two extra ODE components.
  *   R2  RKF45 = Fehlberg's 4(5) pair; the 4th-order solution is propagated; err =
  *       Euclidean norm of the position difference of the two solutions (cells).
- *       Accept if err <= tol. Accept: h *= min(4, 0.9 (tol/err)^(1/5)) (x4 if
- *       err = 0). Reject: h *= max(0.1, 0.9 (tol/err)^(1/4)). h stays in
- *       [h_min, h_max]; a reject at h_min is accepted and flagged STALL. Every
- *       trial (and every exit attempt) counts toward max_steps over both
- *       directions of a line.
+ *       Accept if err <= tol. With q = (tol/err)^(1/4), computed as
+ *       sqrt(sqrt(tol/err)): accept: h *= min(4, 0.9 q) (x4 if err = 0);
+ *       reject: h *= max(0.1, 0.9 q). h stays in [h_min, h_max]; a reject at
+ *       h_min is accepted and flagged STALL. Every trial (and every exit
+ *       attempt) counts toward max_steps over both directions of a line. The
+ *       paper does not give the controller; the fourth root is taken with the
+ *       correctly rounded square root because the adaptive step sequence
+ *       amplifies a one-ulp difference in h by orders of magnitude per step, so
+ *       a pow() that differs between math libraries would make the sequence
+ *       unreproducible.
  *   R3  Interpolation clamps the cell index to [0, n-2]; outside the box this is
  *       linear extrapolation from the boundary cell.
  *   R4  Curl and the B/B gradient use 2nd-order central differences inside and
@@ -70,7 +75,8 @@
  *       Q = |J2 adj(J1)|_F^2 |Bn1 Bn2| / Bn0^2, which is Eqs. D+-2, D+-3, Q+-
  *       with det D replaced by |Bn1/Bn2| (Eq. Bn1).
  *   R9  Per-line tolerance (Sec. 4, Eq. tol): tol_line = tol_perp
- *       max(|Bn0/B|, rot_thresh)^1.5. On an interior S0 with |Bn0/B| <
+ *       max(|Bn0/B|, rot_thresh)^1.5 (the power 1.5 as x sqrt(x), for the
+ *       reason given in R2; other exponents use pow). On an interior S0 with |Bn0/B| <
  *       rot_thresh, S0 is rotated perpendicular to B (n0 = B/|B|, u = unit(b x
  *       e_m) for the axis m of smallest |b_m|, v = b x u), four extra lines
  *       are traced at r0 +- delta u, r0 +- delta v (delta = min(|a1|,|a2|)), all
@@ -407,13 +413,13 @@ static int o_trace_dir(const OField *f, const OParams *p, double tol, double sig
         double err = sqrt(e2);
         if (err > tol) {
             if (h > p->hmin) {
-                h = h * fmax(0.1, 0.9 * pow(tol / err, 0.25));
+                h = h * fmax(0.1, 0.9 * sqrt(sqrt(tol / err)));
                 if (h < p->hmin) h = p->hmin;
                 continue;
             }
             *status |= ST_STALL;
         }
-        double hn = (err > 0.0) ? h * fmin(4.0, 0.9 * pow(tol / err, 0.2)) : 4.0 * h;
+        double hn = (err > 0.0) ? h * fmin(4.0, 0.9 * sqrt(sqrt(tol / err))) : 4.0 * h;
         if (hn < p->hmin) hn = p->hmin;
         if (hn > p->hmax) hn = p->hmax;
         if (o_inside(f, y4)) {
@@ -678,7 +684,8 @@ static void o_seed_setup(const OField *f, const OParams *p, const OLattice *L, l
         S->tol = p->tol;
     } else {
         S->bn0 = o_dot(B, S->n0);
-        S->tol = p->tol * pow(fmax(ratio, p->rot_thresh), p->tol_exp);
+        double x = fmax(ratio, p->rot_thresh);
+        S->tol = p->tol * (p->tol_exp == 1.5 ? x * sqrt(x) : pow(x, p->tol_exp));
     }
 }
 

@@ -16,7 +16,11 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libfqsl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-              "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+              "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+# Translation units whose FP64 arithmetic must round like a plain evaluation
+# of the method (no fused multiply-add contraction): the FP64 tracer, the curl
+# grid and the Q assembly. The FP32 tracer keeps contraction.
+NO_FMAD = {"trace_f64.cu", "field.cu", "assemble.cu"}
 
 
 def nvcc() -> str:
@@ -28,7 +32,7 @@ def nvcc() -> str:
 
 def _deps():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
-                  [os.path.join(INCLUDE, "fqsl.h")])
+                  [os.path.join(INCLUDE, "fqsl.h"), os.path.abspath(__file__)])
 
 
 def _stale(target: str, deps) -> bool:
@@ -49,7 +53,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [exe, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
+        fmad = ["--fmad=false"] if os.path.basename(src) in NO_FMAD else []
+        cmd = [exe, *ARCH, *NVCC_FLAGS, *fmad, *extra_flags, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

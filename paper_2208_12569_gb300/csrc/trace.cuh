@@ -10,9 +10,9 @@
 //     lookup clamped to [0, n-2] (Sec. 2.2, Eqs. interp, w0, w1);
 //   - Fehlberg's RKF45 pair with the 4th-order solution propagated; a trial is
 //     accepted when the position error (cells) is <= the line's tolerance;
-//     step growth min(4, 0.9 (tol/err)^(1/5)), shrink max(0.1, 0.9
-//     (tol/err)^(1/4)), h in [h_min, h_max], a reject at h_min is accepted and
-//     flagged (Sec. 2.3);
+//     with q = (tol/err)^(1/4) taken as two correctly rounded square roots,
+//     growth min(4, 0.9 q), shrink max(0.1, 0.9 q), h in [h_min, h_max], a
+//     reject at h_min is accepted and flagged (Sec. 2.3);
 //   - at the box exit the accepted step is discarded and one RKF45 step is
 //     taken from the previous point with the face-normal index coordinate as
 //     the independent variable, landing exactly on the face (the paper's "move
@@ -27,6 +27,12 @@
 // before the next trial step. Normal trials and exit steps share one 6-stage
 // code path, so a warp only diverges at line start and end. The state is
 // stepped in T; the error norm, the tolerance and the Tw/length sums are FP64.
+// The FP64 instantiation is built without floating-point contraction and
+// evaluates every expression in the order of its definition (Eq. interp term
+// by term, the 4th- and 5th-order solutions formed separately), because the
+// adaptive step sequence amplifies any rounding difference by orders of
+// magnitude per step: that way it reproduces a plain evaluation of the method
+// to the last bit. The FP32 instantiation uses the fast forms.
 #pragma once
 
 #include <math.h>
@@ -55,6 +61,11 @@ struct Fehlberg {
     static __device__ __forceinline__ T b4(int s)
     {
         const double B[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0};
+        return (T)B[s];
+    }
+    static __device__ __forceinline__ T b5(int s)
+    {
+        const double B[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
         return (T)B[s];
     }
     // 5th minus 4th order weights (error estimate)
@@ -116,30 +127,30 @@ __device__ __forceinline__ T clampcell(T c, int n)
     return fmin(fmax(c, (T)0), (T)(n - 2));
 }
 
-template <typename T>
-__device__ __forceinline__ void gather(const FieldView &f, T x, T y, T z, T B[3], T J[3])
+// FP32: weights as products of per-axis weights, corners grouped by (y, z).
+__device__ __forceinline__ void gather(const FieldView &f, float x, float y, float z, float B[3], float J[3])
 {
-    const T cx = clampcell<T>(tfloor<T>(x), f.nx);
-    const T cy = clampcell<T>(tfloor<T>(y), f.ny);
-    const T cz = clampcell<T>(tfloor<T>(z), f.nz);
-    const T wx = x - cx, wy = y - cy, wz = z - cz;
-    const T ux = (T)1 - wx, uy = (T)1 - wy, uz = (T)1 - wz;
+    const float cx = clampcell<float>(floorf(x), f.nx);
+    const float cy = clampcell<float>(floorf(y), f.ny);
+    const float cz = clampcell<float>(floorf(z), f.nz);
+    const float wx = x - cx, wy = y - cy, wz = z - cz;
+    const float ux = 1.f - wx, uy = 1.f - wy, uz = 1.f - wz;
     const long long sy = f.nx, sz = (long long)f.nx * f.ny;
     const long long base = (long long)cz * sz + (long long)cy * sy + (long long)cx;
-    const T wyz[4] = {uy * uz, wy * uz, uy * wz, wy * wz};
+    const float wyz[4] = {uy * uz, wy * uz, uy * wz, wy * wz};
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        B[c] = (T)0;
-        J[c] = (T)0;
+        B[c] = 0.f;
+        J[c] = 0.f;
     }
 #pragma unroll
     for (int qp = 0; qp < 4; qp++) {
         const long long node = base + (qp & 1) * sy + (qp >> 1) * sz;
 #pragma unroll
         for (int m = 0; m < 2; m++) {
-            T bx, by, bz, jx, jy, jz;
+            float bx, by, bz, jx, jy, jz;
             load_node(f, node + m, bx, by, bz, jx, jy, jz);
-            const T w = (m ? wx : ux) * wyz[qp];
+            const float w = (m ? wx : ux) * wyz[qp];
             B[0] += w * bx;
             B[1] += w * by;
             B[2] += w * bz;
@@ -150,13 +161,52 @@ __device__ __forceinline__ void gather(const FieldView &f, T x, T y, T z, T B[3]
     }
 }
 
+// FP64: Eq. interp term by term, omega_0 = (i+1) - xi and omega_1 = 1 - omega_0
+// (Eqs. w0, w1 in cells), summed over m (x), n (y), p (z) in that nesting.
+// Built without contraction, this is the plain evaluation of the definition.
+__device__ __forceinline__ void gather(const FieldView &f, double x, double y, double z, double B[3], double J[3])
+{
+    const double c[3] = {clampcell<double>(floor(x), f.nx), clampcell<double>(floor(y), f.ny),
+                         clampcell<double>(floor(z), f.nz)};
+    const double xi[3] = {x, y, z};
+    double w[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        w[a][0] = (c[a] + 1.0) - xi[a];
+        w[a][1] = 1.0 - w[a][0];
+    }
+    const long long sy = f.nx, sz = (long long)f.nx * f.ny;
+    const long long base = (long long)c[2] * sz + (long long)c[1] * sy + (long long)c[0];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        B[k] = 0.0;
+        J[k] = 0.0;
+    }
+#pragma unroll
+    for (int m = 0; m < 2; m++)
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+#pragma unroll
+            for (int p = 0; p < 2; p++) {
+                const double wt = w[0][m] * w[1][q] * w[2][p];
+                double bx, by, bz, jx, jy, jz;
+                load_node(f, base + p * sz + q * sy + m, bx, by, bz, jx, jy, jz);
+                B[0] += wt * bx;
+                B[1] += wt * by;
+                B[2] += wt * bz;
+                J[0] += wt * jx;
+                J[1] += wt * jy;
+                J[2] += wt * jz;
+            }
+}
+
 // Right-hand side in index space: out = {F (3), dl/dtau, dTw/dtau}.
 // Returns false on a null / non-finite field.
 __device__ __forceinline__ bool rhs(const FieldView &f, const float invd[3], float sgn, float x, float y, float z,
                                     float out[5])
 {
     float B[3], J[3];
-    gather<float>(f, x, y, z, B, J);
+    gather(f, x, y, z, B, J);
     const float b0 = B[0] * invd[0], b1 = B[1] * invd[1], b2 = B[2] * invd[2];
     const float bb = b0 * b0 + b1 * b1 + b2 * b2;
     const float BB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
@@ -173,34 +223,33 @@ __device__ __forceinline__ bool rhs(const FieldView &f, const float invd[3], flo
     return true;
 }
 
-__device__ __forceinline__ bool rhs(const FieldView &f, const double invd[3], double sgn, double x, double y,
+// FP64: bt_a = B_a / d_a, F = sigma bt / |bt|, dl/dtau = |B| / |bt|,
+// dTw/dtau = (J.B) / (4 pi B^2) dl/dtau, each as written.
+__device__ __forceinline__ bool rhs(const FieldView &f, const double d[3], double sgn, double x, double y,
                                     double z, double out[5])
 {
     double B[3], J[3];
-    gather<double>(f, x, y, z, B, J);
-    const double b0 = B[0] * invd[0], b1 = B[1] * invd[1], b2 = B[2] * invd[2];
-    const double bb = b0 * b0 + b1 * b1 + b2 * b2;
+    gather(f, x, y, z, B, J);
+    const double bt[3] = {B[0] / d[0], B[1] / d[1], B[2] / d[2]};
+    const double bb = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
     const double BB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
     if (!(bb > 0.0) || !(bb < INFINITY)) return false;
-    const double nbt = sqrt(bb);
-    const double inv = 1.0 / nbt;
-    const double s = sgn * inv;
-    out[0] = b0 * s;
-    out[1] = b1 * s;
-    out[2] = b2 * s;
-    const double dl = sqrt(BB) * inv;
+    const double nbt = sqrt(bb), nB = sqrt(BB);
+    out[0] = sgn * bt[0] / nbt;
+    out[1] = sgn * bt[1] / nbt;
+    out[2] = sgn * bt[2] / nbt;
+    const double dl = nB / nbt;
     out[3] = dl;
-    const double JB = J[0] * B[0] + J[1] * B[1] + J[2] * B[2];
-    out[4] = JB / (12.566370614359172 * BB) * dl;
+    out[4] = (J[0] * B[0] + J[1] * B[1] + J[2] * B[2]) / (12.566370614359172 * BB) * dl;
     return true;
 }
 
-template <typename T>
-__device__ __forceinline__ T tpow(T a, T b);
-template <>
-__device__ __forceinline__ float tpow<float>(float a, float b) { return __powf(a, b); }
-template <>
-__device__ __forceinline__ double tpow<double>(double a, double b) { return pow(a, b); }
+// fourth root through the correctly rounded square root
+__device__ __forceinline__ float root4(float v) { return sqrtf(sqrtf(v)); }
+__device__ __forceinline__ double root4(double v) { return sqrt(sqrt(v)); }
+
+// x^e for the obliquity factor of Eq. tol (x sqrt(x) for the usual e = 1.5)
+__device__ __forceinline__ double obliq_pow(double x, double e) { return e == 1.5 ? x * sqrt(x) : pow(x, e); }
 
 // physical coordinate of an index coordinate, without contraction so that the
 // value matches a plain multiply-then-add
@@ -232,11 +281,8 @@ __device__ __forceinline__ void perp_frame(const double bh[3], double u[3], doub
     int m = 0;
     if (fabs(bh[1]) < fabs(bh[m])) m = 1;
     if (fabs(bh[2]) < fabs(bh[m])) m = 2;
-    double t[3];
-    // bh x e_m
-    t[0] = (m == 0) ? 0.0 : (m == 1 ? -bh[2] : bh[1]);
-    t[1] = (m == 0) ? bh[2] : (m == 1 ? 0.0 : -bh[0]);
-    t[2] = (m == 0) ? -bh[1] : (m == 1 ? bh[0] : 0.0);
+    const double e[3] = {m == 0 ? 1.0 : 0.0, m == 1 ? 1.0 : 0.0, m == 2 ? 1.0 : 0.0};
+    const double t[3] = {bh[1] * e[2] - bh[2] * e[1], bh[2] * e[0] - bh[0] * e[2], bh[0] * e[1] - bh[1] * e[0]};
     const double nt = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
     u[0] = t[0] / nt;
     u[1] = t[1] / nt;
@@ -251,7 +297,7 @@ template <typename T>
 __device__ __forceinline__ void b_at(const FieldView &f, double x, double y, double z, double B[3])
 {
     T Bt[3], Jt[3];
-    gather<T>(f, (T)x, (T)y, (T)z, Bt, Jt);
+    gather(f, (T)x, (T)y, (T)z, Bt, Jt);
     B[0] = (double)Bt[0];
     B[1] = (double)Bt[1];
     B[2] = (double)Bt[2];
@@ -272,7 +318,7 @@ struct Lane {
     double tol;
     double lacc, twacc;  // length / Tw of the current direction
     double l1, tw1;      // totals of end 1
-    float ol, otw;       // length / Tw increments of the exiting step
+    double ol, otw;      // length / Tw at the end of the exiting step
     int steps, st, end, mode, hface, tries, fc0;
 };
 
@@ -455,7 +501,7 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
                     A.q.rot_slot[idx] = (int32_t)slot + 1;
                 } else {
                     bn0 = bn;
-                    tol = A.p.tol * pow(fmax(ratio, A.p.rot), A.p.texp);
+                    tol = A.p.tol * obliq_pow(fmax(ratio, A.p.rot), A.p.texp);
                 }
             }
         }
@@ -513,7 +559,10 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
     const unsigned lt_mask = (1u << lane) - 1u;
     const FieldView &f = A.f;
     const LineRecs &R = (SRC == kSrcExtra) ? A.ext : A.rec;
-    const T invd[3] = {(T)(1.0 / f.d[0]), (T)(1.0 / f.d[1]), (T)(1.0 / f.d[2])};
+    constexpr bool kF64 = sizeof(T) == 8;
+    // FP32 multiplies by 1/d, FP64 divides by d (see rhs)
+    const T dd[3] = {kF64 ? (T)f.d[0] : (T)(1.0 / f.d[0]), kF64 ? (T)f.d[1] : (T)(1.0 / f.d[1]),
+                     kF64 ? (T)f.d[2] : (T)(1.0 / f.d[2])};
     const T hmin = (T)A.p.hmin, hmax = (T)A.p.hmax;
     const T graze = (T)A.p.graze;
     const int max_steps = (int)A.p.max_steps;
@@ -578,9 +627,9 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
         L.steps++;
 
         T k0[5], k1[5], k2[5];  // position derivatives of stages 1..5
-        T a4[3] = {0, 0, 0}, e5[3] = {0, 0, 0};
+        T a4[3] = {0, 0, 0}, a5[3] = {0, 0, 0};  // FP64: 5th-order sums; FP32: 5th - 4th
         T l4 = 0, tw4 = 0;
-        bool nul = false, grz = false;
+        int fail = 0;  // first failing stage: 1 null field, 2 grazing exit step
 #pragma unroll
         for (int s = 0; s < 6; s++) {
             T px = 0, py = 0, pz = 0;
@@ -595,56 +644,79 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             py = L.y + hh * py;
             pz = L.z + hh * pz;
             T o[5];
-            nul |= !rhs(f, invd, sgn, px, py, pz, o);
+            const bool ok = rhs(f, dd, sgn, px, py, pz, o);
+            if (!ok && !fail) fail = 1;
             if (henon) {
                 const T fa = sel3<T>(hax, o[0], o[1], o[2]);
                 const bool bad = !(fa * hsign >= graze);
-                grz |= bad;
-                const T inv = bad ? (T)0 : (T)1 / fa;
+                if (bad && !fail) fail = 2;
+                if (kF64) {
+                    const T den = bad ? (T)1 : fa;
 #pragma unroll
-                for (int c = 0; c < 5; c++) o[c] *= inv;
+                    for (int c = 0; c < 5; c++) o[c] = o[c] / den;
+                } else {
+                    const T inv = bad ? (T)0 : (T)1 / fa;
+#pragma unroll
+                    for (int c = 0; c < 5; c++) o[c] *= inv;
+                }
             }
             if (s < 5) {
                 k0[s] = o[0];
                 k1[s] = o[1];
                 k2[s] = o[2];
             }
-            const T b = Fehlberg<T>::b4(s), e = Fehlberg<T>::e(s);
+            const T b = Fehlberg<T>::b4(s);
+            const T e = kF64 ? Fehlberg<T>::b5(s) : Fehlberg<T>::e(s);
             a4[0] += b * o[0];
             a4[1] += b * o[1];
             a4[2] += b * o[2];
-            e5[0] += e * o[0];
-            e5[1] += e * o[1];
-            e5[2] += e * o[2];
+            a5[0] += e * o[0];
+            a5[1] += e * o[1];
+            a5[2] += e * o[2];
             l4 += b * o[3];
             tw4 += b * o[4];
         }
 
-        if (nul) {
+        if (fail == 1) {
             finish_bad(A, R, L, FQSL_LINE_NULL_B);
             active = false;
             continue;
         }
         if (!henon) {
-            const double ex = (double)e5[0], ey = (double)e5[1], ez = (double)e5[2];
-            const double err = (double)hh * sqrt(ex * ex + ey * ey + ez * ez);
+            const T nx = L.x + hh * a4[0], ny = L.y + hh * a4[1], nz = L.z + hh * a4[2];
+            double err;
+            if (kF64) {
+                // error = |y5 - y4| with both solutions formed as written
+                const double d0 = (double)((L.x + hh * a5[0]) - nx), d1 = (double)((L.y + hh * a5[1]) - ny),
+                             d2 = (double)((L.z + hh * a5[2]) - nz);
+                err = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+            } else {
+                const double ex = (double)a5[0], ey = (double)a5[1], ez = (double)a5[2];
+                err = (double)hh * sqrt(ex * ex + ey * ey + ez * ez);
+            }
             if (err > L.tol) {
                 if (L.h > hmin) {
-                    T hn = L.h * (T)fmax(0.1, 0.9 * (double)tpow<T>((T)(L.tol / err), (T)0.25));
+                    const T q = kF64 ? (T)root4(L.tol / err) : (T)root4((float)(L.tol / err));
+                    T hn = L.h * fmax((T)0.1, (T)0.9 * q);
                     L.h = hn < hmin ? hmin : hn;
                     continue;
                 }
                 L.st |= FQSL_LINE_STALL;
             }
-            T hn = (err > 0.0) ? L.h * (T)fmin(4.0, 0.9 * (double)tpow<T>((T)(L.tol / err), (T)0.2)) : (T)4 * L.h;
+            T hn;
+            if (err > 0.0) {
+                const T q = kF64 ? (T)root4(L.tol / err) : (T)root4((float)(L.tol / err));
+                hn = L.h * fmin((T)4, (T)0.9 * q);
+            } else {
+                hn = (T)4 * L.h;
+            }
             hn = hn < hmin ? hmin : (hn > hmax ? hmax : hn);
-            const T nx = L.x + hh * a4[0], ny = L.y + hh * a4[1], nz = L.z + hh * a4[2];
             if (inside<T>(f, nx, ny, nz)) {
                 L.x = nx;
                 L.y = ny;
                 L.z = nz;
-                L.lacc += (double)(hh * l4);
-                L.twacc += (double)(hh * tw4);
+                L.lacc = L.lacc + (double)(hh * l4);
+                L.twacc = L.twacc + (double)(hh * tw4);
                 L.h = hn;
                 continue;
             }
@@ -675,8 +747,8 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             L.ox = nx;
             L.oy = ny;
             L.oz = nz;
-            L.ol = (float)(hh * l4);
-            L.otw = (float)(hh * tw4);
+            L.ol = L.lacc + (double)(hh * l4);
+            L.otw = L.twacc + (double)(hh * tw4);
             L.t0 = tb;
             L.fc0 = best;
             L.hface = best;
@@ -685,7 +757,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             continue;
         }
         // exit step
-        if (grz) {
+        if (fail == 2) {
             L.mode = 0;
             if ((T)0.5 * L.h >= hmin) {
                 L.h = (T)0.5 * L.h;
@@ -699,8 +771,8 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             if (a0 == 0) ex = v0;
             else if (a0 == 1) ey = v0;
             else ez = v0;
-            L.lacc += (double)L.t0 * (double)L.ol;
-            L.twacc += (double)L.t0 * (double)L.otw;
+            L.lacc = L.lacc + (double)L.t0 * (L.ol - L.lacc);
+            L.twacc = L.twacc + (double)L.t0 * (L.otw - L.twacc);
             L.st |= FQSL_LINE_CHORD;
             active = finish_dir<T>(A, R, L, ex, ey, ez, L.fc0);
             continue;
@@ -730,8 +802,8 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             ty = fmin(fmax(ty, (T)0), (T)(f.ny - 1));
             tz = fmin(fmax(tz, (T)0), (T)(f.nz - 1));
         }
-        L.lacc += (double)(hh * l4);
-        L.twacc += (double)(hh * tw4);
+        L.lacc = L.lacc + (double)(hh * l4);
+        L.twacc = L.twacc + (double)(hh * tw4);
         active = finish_dir<T>(A, R, L, tx, ty, tz, L.hface);
     }
 }

@@ -61,3 +61,18 @@ def footpoint_cells_exact(g, r, grid, margin=1e-9):
         same = np.floor(xr) == np.floor(xg)
         assert np.all(same | near), "footpoint cell differs at %d coordinates" % int((~(same | near)).sum())
     return excluded
+
+
+def assert_bitwise(g, r, keys=("Q", "Tw", "length", "r1", "r2", "face1", "face2", "status", "steps")):
+    """Every output identical to the last bit (NaN where the oracle has NaN)."""
+    for k in keys:
+        if k not in r or k not in g:
+            continue
+        gg, rr = np.asarray(g[k]), np.asarray(r[k])
+        if rr.dtype.kind == "f":
+            same = (gg == rr) | (np.isnan(gg) & np.isnan(rr))
+        else:
+            same = gg.astype(np.int64) == rr.astype(np.int64)
+        bad = np.nonzero(~same.reshape(len(rr), -1).all(axis=1))[0]
+        assert bad.size == 0, "%s differs at %d of %d seeds, first %s: gpu %s oracle %s" % (
+            k, bad.size, len(rr), bad[:3], gg[bad[:3]], rr[bad[:3]])
