@@ -182,6 +182,33 @@ FQSL_API fqsl_status fqsl_twist(fqsl_field field, const double *seeds_dev, long 
 FQSL_API fqsl_status fqsl_field_set_timing(fqsl_field field, int enable);
 FQSL_API fqsl_status fqsl_field_times(fqsl_field field, float ms[3]);
 
+/* Largest nu*nv accepted by fqsl_qmap_plane_static. */
+#define FQSL_STATIC_MAX_SEEDS 65536
+
+/* fqsl_qmap_plane without any memory allocation (the paper has no counterpart;
+ * this is a deployment variant). Some callers cannot call cudaMalloc: for
+ * example an application whose device memory is owned entirely by its own
+ * fixed arena or pool allocator, or a latency-critical loop that cannot afford
+ * the device-wide synchronisation that growing library scratch (cudaFree +
+ * cudaMalloc) implies. This entry point computes exactly what fqsl_qmap_plane
+ * computes, with the same arguments, outputs and errors, but keeps its
+ * per-line scratch (line records, work counters, rotated-S0 buffers) in one
+ * static device array of about 22 MiB that is part of the library: every GPU
+ * that loads the library holds that array until the process exits, and this
+ * call allocates nothing. Limits and rules:
+ *   - nu*nv <= FQSL_STATIC_MAX_SEEDS, else FQSL_ERR_ARG with a message;
+ *   - the first call on a device (with that device current) looks up the
+ *     array's device address once; make that first call before any stream
+ *     capture;
+ *   - all calls share the one array: the call clears what must start at zero,
+ *     and calls whose work overlaps on the GPU (other streams, other host
+ *     threads) race on it, so serialise them;
+ *   - the field handle (created beforehand by fqsl_field_create) is only read.
+ */
+FQSL_API fqsl_status fqsl_qmap_plane_static(fqsl_field field, const double origin[3], const double u[3],
+                                            const double v[3], long long nu, long long nv,
+                                            const fqsl_params *params, const fqsl_out *out, void *cuda_stream);
+
 /* Synchronise cuda_stream and report device-side failures recorded by earlier
  * calls on this field (FQSL_ERR_TIMEOUT if a bounded loop gave up). The
  * record is cleared. */

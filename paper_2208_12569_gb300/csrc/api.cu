@@ -559,3 +559,141 @@ fqsl_status fqsl_twist(fqsl_field f, const double *seeds_dev, long long n, const
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// fqsl_qmap_plane_static: the plane map with its scratch in a static device
+// array, for callers that cannot allocate device memory.
+// ---------------------------------------------------------------------------
+namespace {
+
+// 323 bytes per seed for 65536 seeds with rotation buffers, plus counters and
+// the 256-byte alignment of each carved array
+constexpr size_t kStaticScratchBytes = (size_t)22 << 20;
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+char *g_static_addr[kMaxDevices] = {};
+
+// Device address of the static array on the current device (looked up once).
+fqsl_status static_scratch(char **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "fqsl_qmap_plane_static: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(FQSL_ERR_UNSUPPORTED, "fqsl_qmap_plane_static: device %d", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "fqsl_qmap_plane_static: cudaGetSymbolAddress");
+        g_static_addr[dev] = (char *)ptr;
+    }
+    *out = g_static_addr[dev];
+    return FQSL_OK;
+}
+
+}  // namespace
+
+extern "C" fqsl_status fqsl_qmap_plane_static(fqsl_field f, const double origin[3], const double u[3],
+                                              const double v[3], long long nu, long long nv, const fqsl_params *p,
+                                              const fqsl_out *out, void *cuda_stream)
+{
+    g_err.clear();
+    const char *who = "fqsl_qmap_plane_static";
+    fqsl_status st = check_params(f, p, who);
+    if (st != FQSL_OK) return st;
+    if (!out) return fail(FQSL_ERR_ARG, "%s: out is NULL", who);
+    if (!finite3(origin) || !finite3(u) || !finite3(v)) return fail(FQSL_ERR_ARG, "%s: non-finite plane", who);
+    if (nu < 1 || nv < 1) return fail(FQSL_ERR_ARG, "%s: need nu, nv >= 1", who);
+    if (nu * nv > FQSL_STATIC_MAX_SEEDS)
+        return fail(FQSL_ERR_ARG, "%s: nu*nv = %lld exceeds FQSL_STATIC_MAX_SEEDS = %d", who, nu * nv,
+                    FQSL_STATIC_MAX_SEEDS);
+    double n0[3];
+    cross(u, v, n0);
+    const double nn = sqrt(n0[0] * n0[0] + n0[1] * n0[1] + n0[2] * n0[2]);
+    const double nuu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const double nvv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (!(nuu > 0) || !(nvv > 0) || !(nn > 0)) return fail(FQSL_ERR_ARG, "%s: u and v must span a plane", who);
+    if (fabs(u[0] * v[0] + u[1] * v[1] + u[2] * v[2]) > 1e-12 * nuu * nvv)
+        return fail(FQSL_ERR_ARG, "%s: u and v must be orthogonal", who);
+    Lattice lat{};
+    for (int a = 0; a < 3; a++) {
+        lat.o[a] = origin[a];
+        lat.a1[a] = u[a];
+        lat.a2[a] = v[a];
+        lat.a3[a] = 0.0;
+        lat.n0[a] = n0[a] / nn;
+    }
+    lat.n1 = nu;
+    lat.n2 = nv;
+    lat.n3 = 1;
+    lat.du = nuu;
+    lat.dv = nvv;
+    lat.drot = fmin(nuu, nvv);
+    int zeros = 0, axis = -1;
+    for (int a = 0; a < 3; a++) {
+        if (lat.n0[a] == 0.0) zeros++;
+        else axis = a;
+    }
+    lat.normal_axis = zeros == 2 ? axis : -1;
+    bool face_plane = false;
+    if (lat.normal_axis >= 0) {
+        const int a = lat.normal_axis;
+        const int na = a == 0 ? f->g.nx : (a == 1 ? f->g.ny : f->g.nz);
+        const double xi = (origin[a] - f->g.o[a]) / f->g.d[a];
+        face_plane = (xi == 0.0) || (xi == (double)(na - 1));
+    }
+    const long long n = nu * nv;
+    lat.tiles_u = (lat.n1 + kTileU - 1) / kTileU;
+    lat.tiles_v = (lat.n2 + kTileV - 1) / kTileV;
+    lat.allow_rot = (p->method == 1 && !face_plane) ? 1 : 0;
+
+    char *base = nullptr;
+    st = static_scratch(&base);
+    if (st != FQSL_OK) return st;
+    // counters first, then the line records
+    unsigned long long *counters = (unsigned long long *)base;
+    const size_t head = 256;
+    Scratch need = layout(nullptr, n, lat.allow_rot, true);
+    if (head + need.bytes > kStaticScratchBytes)
+        return fail(FQSL_ERR_ARG, "%s: %lld seeds need %zu scratch bytes, the static array holds %zu", who, n,
+                    head + need.bytes, kStaticScratchBytes);
+    Scratch s = layout(base + head, n, lat.allow_rot, true);
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+    std::lock_guard<std::mutex> lock(f->mu);
+    cudaError_t e = cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), stream);
+    if (e == cudaSuccess && lat.allow_rot) e = cudaMemsetAsync(s.rot_slot, 0, (size_t)n * sizeof(int32_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    TraceArgs a{};
+    a.f = f->g;
+    a.f.rec = p->precision == FQSL_F32 ? f->rec32 : f->rec64;
+    a.p = dev_params(p);
+    a.lat = lat;
+    a.rec = s.rec;
+    a.ext = s.ext;
+    a.q.head = counters;
+    a.q.rot_count = (unsigned int *)(counters + 2);
+    a.q.rot_seed = s.rot_seed;
+    a.q.rot_slot = s.rot_slot;
+    a.nitems = lat.n3 * lat.tiles_u * lat.tiles_v * (long long)(kTileU * kTileV);
+    e = launch_trace(f, p, a, kSrcLattice, a.nitems, stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    if (lat.allow_rot) {
+        a.q.head = counters + 1;
+        e = launch_trace(f, p, a, kSrcExtra, 4 * n, stream);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+    }
+    AssembleArgs g{};
+    g.lat = lat;
+    g.rec = s.rec;
+    g.ext = s.ext;
+    g.rot_slot = lat.allow_rot ? s.rot_slot : nullptr;
+    g.out = *out;
+    g.n = n;
+    g.want_q = 1;
+    e = launch_assemble(g, stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return FQSL_OK;
+}

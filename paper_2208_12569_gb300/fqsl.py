@@ -21,7 +21,8 @@ LINE_MAXSTEPS, LINE_NULL_B, LINE_STALL, LINE_MIXED, LINE_OUTSIDE, LINE_ROTATED, 
 LINE_BAD = LINE_MAXSTEPS | LINE_NULL_B | LINE_OUTSIDE
 EXPORTS = ("fqsl_params_default", "fqsl_version", "fqsl_last_error", "fqsl_field_create", "fqsl_field_destroy",
            "fqsl_qmap_plane", "fqsl_qmap_volume", "fqsl_twist", "fqsl_field_check", "fqsl_field_set_timing",
-           "fqsl_field_times", "fqsl_field_update")
+           "fqsl_field_times", "fqsl_field_update", "fqsl_qmap_plane_static")
+STATIC_MAX_SEEDS = 65536
 
 
 class FqslError(RuntimeError):
@@ -55,6 +56,8 @@ def load(path: str = LIB_PATH):
                                       C.POINTER(P)]
     lib.fqsl_field_destroy.argtypes = [P]
     lib.fqsl_qmap_plane.argtypes = [P, P, P, P, C.c_longlong, C.c_longlong, C.POINTER(Params), C.POINTER(Out), P]
+    lib.fqsl_qmap_plane_static.argtypes = [P, P, P, P, C.c_longlong, C.c_longlong, C.POINTER(Params),
+                                           C.POINTER(Out), P]
     lib.fqsl_qmap_volume.argtypes = [P, P, P, C.c_longlong, C.c_longlong, C.c_longlong, C.POINTER(Params),
                                      C.POINTER(Out), P]
     lib.fqsl_twist.argtypes = [P, P, C.c_longlong, C.POINTER(Params), C.POINTER(Out), P]
@@ -190,6 +193,19 @@ def qmap_plane(field: Field, origin, u, v, nu: int, nv: int, p: Params | None = 
     out = out or alloc_out(nu * nv)
     _check(_lib.fqsl_qmap_plane(field.handle, _vec3(origin), _vec3(u), _vec3(v), nu, nv, C.byref(p),
                                 C.byref(_out_struct(out)), _stream(stream)))
+    return out
+
+
+def qmap_plane_static(field: Field, origin, u, v, nu: int, nv: int, p: Params | None = None, out=None,
+                      stream=None):
+    """qmap_plane through fqsl_qmap_plane_static: the library allocates no device
+    memory for the call (its scratch is a fixed static array; nu*nv <=
+    STATIC_MAX_SEEDS; calls must not overlap on the GPU). The output buffers
+    are the caller's: pass ``out`` to avoid allocating them here."""
+    p = p or params()
+    out = out or alloc_out(nu * nv)
+    _check(_lib.fqsl_qmap_plane_static(field.handle, _vec3(origin), _vec3(u), _vec3(v), nu, nv, C.byref(p),
+                                       C.byref(_out_struct(out)), _stream(stream)))
     return out
 
 
