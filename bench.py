@@ -201,6 +201,8 @@ def main():
     ap.add_argument("--impl", default="fqsl", choices=["fqsl", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--only-f32", action="store_true",
+                    help="time only the FP32 map (no FP64, e2e or CPU legs); used for ncu captures")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -262,6 +264,13 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     res32 = {k: t.cpu().numpy() for k, t in out.items() if t is not None}
+    if args.only_f32:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": n * ws / (float(np.mean(ms32)) / 1000.0),
+                              "unit": "Q+Tw values/s", "ms_per_step": float(np.mean(ms32)),
+                              "kernels_ms": {"trace_f32": float(np.mean([k[0] for k in kern32]))},
+                              "config": {"workload": WORKLOAD}, "partial": "only-f32"}), flush=True)
+        return
     step(p64)
     torch.cuda.synchronize()
     ms64, kern64 = timed(p64, args.fp64_steps)

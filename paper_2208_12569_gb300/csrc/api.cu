@@ -369,11 +369,23 @@ void cross(const double *a, const double *b, double *c)
     c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
+// The lattice in index coordinates (used by the FP32 tracer's seed set-up).
+void index_lattice(const fqsl_field f, Lattice &lat)
+{
+    for (int a = 0; a < 3; a++) {
+        lat.xo[a] = (lat.o[a] - f->g.o[a]) / f->g.d[a];
+        lat.xa1[a] = lat.a1[a] / f->g.d[a];
+        lat.xa2[a] = lat.a2[a] / f->g.d[a];
+        lat.xa3[a] = lat.a3[a] / f->g.d[a];
+    }
+}
+
 // Shared body of the plane and volume Q maps.
 fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, const fqsl_out *out,
                      cudaStream_t stream, bool face_plane, const char *who)
 {
     Lattice lat = lat0;
+    index_lattice(f, lat);
     const long long n = lat.n1 * lat.n2 * lat.n3;
     lat.tiles_u = (lat.n1 + kTileU - 1) / kTileU;
     lat.tiles_v = (lat.n2 + kTileV - 1) / kTileV;
@@ -645,6 +657,7 @@ extern "C" fqsl_status fqsl_qmap_plane_static(fqsl_field f, const double origin[
         face_plane = (xi == 0.0) || (xi == (double)(na - 1));
     }
     const long long n = nu * nv;
+    index_lattice(f, lat);
     lat.tiles_u = (lat.n1 + kTileU - 1) / kTileU;
     lat.tiles_v = (lat.n2 + kTileV - 1) / kTileV;
     lat.allow_rot = (p->method == 1 && !face_plane) ? 1 : 0;

@@ -47,6 +47,8 @@ constexpr int kTileV = 4;
 
 struct Lattice {
     double o[3], a1[3], a2[3], a3[3];
+    // the same lattice in index coordinates: (o - origin)/d and a/d
+    double xo[3], xa1[3], xa2[3], xa3[3];
     double n0[3];      // unit(a1 x a2)
     long long n1, n2, n3;
     long long tiles_u, tiles_v;

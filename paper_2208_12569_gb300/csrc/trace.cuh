@@ -315,7 +315,8 @@ struct Lane {
     T s0;             // end 1 is traced along -s0 B
     T ox, oy, oz;     // end of the exiting step (chord fallback)
     T t0;             // chord parameter of the first crossed face
-    double tol;
+    double tol;          // FP64: the line's tolerance; FP32: its square
+    float tolf2;         // FP32: tol^2 for the step factor
     double lacc, twacc;  // length / Tw of the current direction
     double l1, tw1;      // totals of end 1
     double ol, otw;      // length / Tw at the end of the exiting step
@@ -391,16 +392,15 @@ __device__ __forceinline__ bool inside(const FieldView &f, T x, T y, T z)
            z <= (T)(f.nz - 1);
 }
 
-// Start a line at physical seed r0 with orientation vector n (NULL: end 1 is
-// the backward end). Returns false if the line ends at once (outside / null).
+// Start a line at index position xi (FP64: (r0 - o)/d as written) with
+// orientation vector n (NULL: end 1 is the backward end). Returns false if the
+// line ends at once (outside / null).
 template <typename T>
-__device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R, Lane<T> &L, const double r0[3],
+__device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R, Lane<T> &L, const double xi[3],
                                            const double *n, double tol, int st0)
 {
     const FieldView &f = A.f;
-    double xi[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) xi[a] = (r0[a] - f.o[a]) / f.d[a];
+    constexpr bool kF64 = sizeof(T) == 8;
     L.sx = (T)xi[0];
     L.sy = (T)xi[1];
     L.sz = (T)xi[2];
@@ -413,28 +413,36 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
     L.mode = 0;
     L.lacc = L.twacc = 0.0;
     L.h = (T)A.p.h0;
-    L.tol = tol;
+    if (kF64) {
+        L.tol = tol;
+    } else {
+        L.tol = tol * tol;
+        L.tolf2 = (float)L.tol;
+    }
     const bool in = xi[0] >= 0.0 && xi[0] <= (double)(f.nx - 1) && xi[1] >= 0.0 && xi[1] <= (double)(f.ny - 1) &&
                     xi[2] >= 0.0 && xi[2] <= (double)(f.nz - 1);
     unsigned bad = 0;
-    double B0[3] = {0, 0, 0};
+    T B0[3] = {0, 0, 0};
     if (!in) {
         bad = FQSL_LINE_OUTSIDE;
     } else {
-        b_at<T>(f, xi[0], xi[1], xi[2], B0);
-        const double b0 = B0[0] / f.d[0], b1 = B0[1] / f.d[1], b2 = B0[2] / f.d[2];
-        const double bb = b0 * b0 + b1 * b1 + b2 * b2;
-        if (!(bb > 0.0) || !(bb < INFINITY)) bad = FQSL_LINE_NULL_B;
+        T J0[3];
+        gather(f, L.sx, L.sy, L.sz, B0, J0);
+        T bb;
+        if (kF64) {
+            const T b0 = B0[0] / (T)f.d[0], b1 = B0[1] / (T)f.d[1], b2 = B0[2] / (T)f.d[2];
+            bb = b0 * b0 + b1 * b1 + b2 * b2;
+        } else {
+            const T b0 = B0[0] * (T)(1.0 / f.d[0]), b1 = B0[1] * (T)(1.0 / f.d[1]), b2 = B0[2] * (T)(1.0 / f.d[2]);
+            bb = b0 * b0 + b1 * b1 + b2 * b2;
+        }
+        if (!(bb > (T)0) || !(bb < (T)INFINITY)) bad = FQSL_LINE_NULL_B;
     }
     if (bad) {
         L.st |= bad;
-        const double px = r0[0], py = r0[1], pz = r0[2];
-        // footpoints of a line that never started: its seed (index round trip)
+        // footpoints of a line that never started: its seed
         const double qx = to_phys(f.o[0], f.d[0], xi[0]), qy = to_phys(f.o[1], f.d[1], xi[1]),
                      qz = to_phys(f.o[2], f.d[2], xi[2]);
-        (void)px;
-        (void)py;
-        (void)pz;
         write_end(A, R, L, 0, qx, qy, qz, -1, 0.0);
         write_end(A, R, L, 1, qx, qy, qz, -1, 0.0);
         R.st[L.line] = (uint8_t)L.st;
@@ -444,7 +452,7 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
         return false;
     }
     L.s0 = (T)1;
-    if (n && (B0[0] * n[0] + B0[1] * n[1] + B0[2] * n[2] < 0.0)) L.s0 = (T)-1;
+    if (n && (B0[0] * (T)n[0] + B0[1] * (T)n[1] + B0[2] * (T)n[2] < (T)0)) L.s0 = (T)-1;
     return true;
 }
 
@@ -452,6 +460,7 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
 template <typename T>
 __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, long long item)
 {
+    constexpr bool kF64 = sizeof(T) == 8;
     const Lattice &G = A.lat;
     const long long per_tile = kTileU * kTileV;
     const long long w = item % per_tile;
@@ -465,49 +474,63 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
     if (i >= G.n1 || j >= G.n2 || k >= G.n3) return false;
     const long long idx = i + G.n1 * (j + G.n2 * k);
     L.line = idx;
-    double r0[3];
-    lattice_seed(G, i, j, k, r0);
     const FieldView &f = A.f;
     const LineRecs &R = A.rec;
-    // B at the seed, S0 obliquity and tolerance
-    double xi[3], B0[3];
+    double xi[3];
+    if (kF64) {
+        // physical seed, then (r0 - o)/d, as written
+        double r0[3];
+        lattice_seed(G, i, j, k, r0);
 #pragma unroll
-    for (int a = 0; a < 3; a++) xi[a] = (r0[a] - f.o[a]) / f.d[a];
+        for (int a = 0; a < 3; a++) xi[a] = (r0[a] - f.o[a]) / f.d[a];
+    } else {
+        const double fi = (double)i + 0.5, fj = (double)j + 0.5, fk = (double)k + 0.5;
+#pragma unroll
+        for (int a = 0; a < 3; a++) xi[a] = fma(fk, G.xa3[a], fma(fj, G.xa2[a], fma(fi, G.xa1[a], G.xo[a])));
+    }
+    // B at the seed, S0 obliquity and tolerance
     double tol = A.p.tol;
     int st0 = 0;
     double bn0 = 0.0;
     const bool in = xi[0] >= 0.0 && xi[0] <= (double)(f.nx - 1) && xi[1] >= 0.0 && xi[1] <= (double)(f.ny - 1) &&
                     xi[2] >= 0.0 && xi[2] <= (double)(f.nz - 1);
     if (in) {
-        b_at<T>(f, xi[0], xi[1], xi[2], B0);
-        const double nB = sqrt(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
-        if (nB > 0.0 && nB < INFINITY) {
-            const double bn = B0[0] * G.n0[0] + B0[1] * G.n0[1] + B0[2] * G.n0[2];
+        T B0[3], J0[3];
+        gather(f, (T)xi[0], (T)xi[1], (T)xi[2], B0, J0);
+        const T nB = sqrt(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
+        if (nB > (T)0 && nB < (T)INFINITY) {
+            const T bn = B0[0] * (T)G.n0[0] + B0[1] * (T)G.n0[1] + B0[2] * (T)G.n0[2];
             if (A.p.method == 2) {
-                bn0 = nB;
+                bn0 = (double)nB;
             } else {
-                const double ratio = fabs(bn) / nB;
+                const T ratio = fabs(bn) / nB;
                 bool on_face = false;
                 if (G.normal_axis >= 0) {
                     const double xa = xi[G.normal_axis];
                     const int na = G.normal_axis == 0 ? f.nx : (G.normal_axis == 1 ? f.ny : f.nz);
                     on_face = (xa == 0.0) || (xa == (double)(na - 1));
                 }
-                if (G.allow_rot && ratio < A.p.rot && !on_face) {
+                if (G.allow_rot && ratio < (T)A.p.rot && !on_face) {
                     st0 = FQSL_LINE_ROTATED;
-                    bn0 = nB;
+                    bn0 = (double)nB;
                     const unsigned slot = atomicAdd(A.q.rot_count, 1u);
                     A.q.rot_seed[slot] = (int32_t)idx;
                     A.q.rot_slot[idx] = (int32_t)slot + 1;
                 } else {
-                    bn0 = bn;
-                    tol = A.p.tol * obliq_pow(fmax(ratio, A.p.rot), A.p.texp);
+                    bn0 = (double)bn;
+                    if (kF64) {
+                        tol = A.p.tol * obliq_pow(fmax((double)ratio, A.p.rot), A.p.texp);
+                    } else {
+                        const float x = fmaxf((float)ratio, (float)A.p.rot);
+                        const float g = A.p.texp == 1.5 ? x * sqrtf(x) : __powf(x, (float)A.p.texp);
+                        tol = A.p.tol * (double)g;
+                    }
                 }
             }
         }
     }
     R.bn0[idx] = bn0;
-    return start_line<T>(A, R, L, r0, G.n0, tol, st0);
+    return start_line<T>(A, R, L, xi, G.n0, tol, st0);
 }
 
 // Rotated extra line q (0: +u, 1: -u, 2: +v, 3: -v) of rotated slot s (Sec. 4).
@@ -536,16 +559,22 @@ __device__ __forceinline__ bool init_extra(const TraceArgs &A, Lane<T> &L, long 
     double rr[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) rr[a] = r0[a] + sg * G.drot * dir[a];
+    double xr[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) xr[a] = (rr[a] - f.o[a]) / f.d[a];
     L.line = item;
-    return start_line<T>(A, A.ext, L, rr, nrot, A.p.tol, 0);
+    return start_line<T>(A, A.ext, L, xr, nrot, A.p.tol, 0);
 }
 
 template <typename T>
 __device__ __forceinline__ bool init_list(const TraceArgs &A, Lane<T> &L, long long item)
 {
     L.line = item;
-    const double r0[3] = {A.seeds[3 * item], A.seeds[3 * item + 1], A.seeds[3 * item + 2]};
-    return start_line<T>(A, A.rec, L, r0, nullptr, A.p.tol, 0);
+    const FieldView &f = A.f;
+    double xi[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) xi[a] = (A.seeds[3 * item + a] - f.o[a]) / f.d[a];
+    return start_line<T>(A, A.rec, L, xi, nullptr, A.p.tol, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -684,19 +713,27 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
         }
         if (!henon) {
             const T nx = L.x + hh * a4[0], ny = L.y + hh * a4[1], nz = L.z + hh * a4[2];
-            double err;
+            // err > tol (FP64: err = |y5 - y4| with both solutions formed as
+            // written; FP32: err^2 = h^2 |sum (b5 - b4) k|^2 accumulated in FP64
+            // and compared with tol^2, the step factor (tol/err)^(1/4) =
+            // (tol^2/err^2)^(1/8) in float)
+            double err = 0.0;
+            float rf = 0.f;
+            bool over;
             if (kF64) {
-                // error = |y5 - y4| with both solutions formed as written
                 const double d0 = (double)((L.x + hh * a5[0]) - nx), d1 = (double)((L.y + hh * a5[1]) - ny),
                              d2 = (double)((L.z + hh * a5[2]) - nz);
                 err = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                over = err > L.tol;
             } else {
                 const double ex = (double)a5[0], ey = (double)a5[1], ez = (double)a5[2];
-                err = (double)hh * sqrt(ex * ex + ey * ey + ez * ez);
+                err = (double)(hh * hh) * (ex * ex + ey * ey + ez * ez);  // err^2
+                over = err > L.tol;
+                rf = __fdividef(L.tolf2, (float)err);
             }
-            if (err > L.tol) {
+            if (over) {
                 if (L.h > hmin) {
-                    const T q = kF64 ? (T)root4(L.tol / err) : (T)root4((float)(L.tol / err));
+                    const T q = kF64 ? (T)root4(L.tol / err) : (T)sqrtf(root4(rf));
                     T hn = L.h * fmax((T)0.1, (T)0.9 * q);
                     L.h = hn < hmin ? hmin : hn;
                     continue;
@@ -705,7 +742,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             }
             T hn;
             if (err > 0.0) {
-                const T q = kF64 ? (T)root4(L.tol / err) : (T)root4((float)(L.tol / err));
+                const T q = kF64 ? (T)root4(L.tol / err) : (T)sqrtf(root4(rf));
                 hn = L.h * fmin((T)4, (T)0.9 * q);
             } else {
                 hn = (T)4 * L.h;

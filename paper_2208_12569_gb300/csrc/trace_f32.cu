@@ -3,12 +3,17 @@
 // are in double.
 #include "trace.cuh"
 
+// minimum resident blocks per SM requested from the register allocator
+#ifndef FQSL_TRACE_F32_MINB
+#define FQSL_TRACE_F32_MINB 4
+#endif
+
 namespace fqsl {
 namespace {
 constexpr int kBlock = 128;
 
 template <int SRC>
-__global__ void __launch_bounds__(kBlock) k_trace_f32(const TraceArgs A)
+__global__ void __launch_bounds__(kBlock, FQSL_TRACE_F32_MINB) k_trace_f32(const TraceArgs A)
 {
     trace::trace_body<float, SRC>(A);
 }
