@@ -6,8 +6,9 @@ the potential field of 24 buried monopoles (seeded), unit spacing, curl by
 central differences; Q (Method I, RKF45, tol_perp = 10^-3.2) and Tw on the z=0
 plane at 4x oversampling (1024x1024 seeds), both directions. A "step" is one
 Q+Tw map (tracer + Q assembly launches). The headline ``value`` is the FP32
-tracer (FP64 error-norm/Tw/Q assembly); the plain FP64 tracer is timed beside
-it. ``e2e`` is the same map through the C ABI from host memory: copy of B,
+tracer (FP32 error norm, compensated FP32 length/Tw sums, FP64 tolerance,
+footpoints and Q assembly); the FP32 tracer with FP64 accumulation at every
+step and the plain FP64 tracer are timed beside it. ``e2e`` is the same map through the C ABI from host memory: copy of B,
 curl+pack, map, copy of Q and Tw back.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fqsl|reference]
@@ -231,6 +232,7 @@ def main():
     n = NU * NV
     out = fq.alloc_out(n, device=dev)
     p32 = fq.params(precision="f32", tol=TOL)
+    pacc = fq.params(precision="f32acc64", tol=TOL)
     p64 = fq.params(precision="f64", tol=TOL)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream()
@@ -271,6 +273,10 @@ def main():
                               "kernels_ms": {"trace_f32": float(np.mean([k[0] for k in kern32]))},
                               "config": {"workload": WORKLOAD}, "partial": "only-f32"}), flush=True)
         return
+    step(pacc)
+    torch.cuda.synchronize()
+    msacc, kernacc = timed(pacc, args.steps)
+    resacc = {k: t.cpu().numpy() for k, t in out.items() if t is not None}
     step(p64)
     torch.cuda.synchronize()
     ms64, kern64 = timed(p64, args.fp64_steps)
@@ -322,6 +328,10 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "cube": list(CUBE), "seeds": [NU, NV], "tol_perp": TOL,
                        "method": 1, "l2": "flushed between steps (256 MB write)", "inputs_resident": True},
+            "f32_acc64": {"value": n / (float(np.mean(msacc)) / 1000.0), "unit": "Q+Tw values/s",
+                          "ms_per_step": float(np.mean(msacc)),
+                          "trace_ms": float(np.mean([k[0] for k in kernacc])),
+                          "note": "error norm and length/Tw sums accumulated in FP64 every step"},
             "fp64": {"value": value64, "unit": "Q+Tw values/s", "ms_per_step": float(np.mean(ms64)),
                      "trace_ms": float(np.mean([k[0] for k in kern64])),
                      "speedup_fp32_over_fp64": value / ws / value64},
@@ -338,7 +348,8 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, sample, ref = cpu_baseline(B, grid, u, v)
         line["cpu_baseline"] = cb
-        line["error_vs_oracle"] = {"f32": err_stats(res32, ref, sample), "f64": err_stats(res64, ref, sample)}
+        line["error_vs_oracle"] = {"f32": err_stats(res32, ref, sample), "f32_acc64": err_stats(resacc, ref, sample),
+                                   "f64": err_stats(res64, ref, sample)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

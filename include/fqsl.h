@@ -60,7 +60,15 @@ typedef enum {
     FQSL_ERR_UNSUPPORTED = 5  /* valid request the library does not implement */
 } fqsl_status;
 
-typedef enum { FQSL_F32 = 0, FQSL_F64 = 1 } fqsl_dtype;
+/* Element types of B, and tracing precisions (fqsl_params.precision):
+ *   FQSL_F32        FP32 cube and stepping; error norm in FP32; length and Tw
+ *                   as compensated FP32 sums formed in FP64 per direction;
+ *                   tolerance, footpoints, Bn and Q assembly in FP64
+ *   FQSL_F64        FP64 throughout; reproduces a plain FP64 evaluation of the
+ *                   method bit for bit
+ *   FQSL_F32_ACC64  as FQSL_F32 but the error norm and the length/Tw sums are
+ *                   accumulated in FP64 at every step (precision only) */
+typedef enum { FQSL_F32 = 0, FQSL_F64 = 1, FQSL_F32_ACC64 = 2 } fqsl_dtype;
 
 /* fqsl_field_create flags: which packed node records to build. */
 #define FQSL_PACK_F32 1u   /* 32-byte records {Bx,By,Bz,Jx | Jy,Jz,0,0} in float */
@@ -80,7 +88,7 @@ typedef enum { FQSL_F32 = 0, FQSL_F64 = 1 } fqsl_dtype;
 typedef struct {
     int method;           /* 1 = neighbour differences (Method I), 2 = deviation vectors (Method II) */
     int gradb_way;        /* Method II gradient of B/|B|: 1 = node grid (Eq. grad_B), 2 = +-eps differences */
-    int precision;        /* fqsl_dtype: arithmetic of the traced state (FQSL_F64 or FQSL_F32) */
+    int precision;        /* FQSL_F32 (default), FQSL_F64 or FQSL_F32_ACC64 (see fqsl_dtype) */
     int reserved0;
     double tol;           /* tol_perp (Method I; scaled per line by |Bn0/B|^tol_exp) or tol (Method II, twist); default 10^-3.2 */
     double h0;            /* initial step, default 0.5 */

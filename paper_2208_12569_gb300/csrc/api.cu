@@ -62,7 +62,7 @@ struct fqsl_field_s {
     void *scratch = nullptr;
     size_t scratch_cap = 0;
     unsigned long long *counters = nullptr;  // [0] primary head, [1] extra head, [2] rotated count (low 32 bits)
-    int blocks_f32[3] = {0, 0, 0}, blocks_f64[3] = {0, 0, 0};
+    int blocks_cache[3][3] = {};  // [precision][source] resident blocks per SM
     bool timing = false, timed = false, extra_timed = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::mutex mu;
@@ -250,8 +250,8 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
     if (!p) return fail(FQSL_ERR_ARG, "%s: NULL params", who);
     if (p->method != 1 && p->method != 2) return fail(FQSL_ERR_ARG, "%s: method must be 1 or 2", who);
     if (p->gradb_way != 1 && p->gradb_way != 2) return fail(FQSL_ERR_ARG, "%s: gradb_way must be 1 or 2", who);
-    if (p->precision != FQSL_F32 && p->precision != FQSL_F64)
-        return fail(FQSL_ERR_ARG, "%s: precision must be FQSL_F32 or FQSL_F64", who);
+    if (p->precision != FQSL_F32 && p->precision != FQSL_F64 && p->precision != FQSL_F32_ACC64)
+        return fail(FQSL_ERR_ARG, "%s: precision must be FQSL_F32, FQSL_F64 or FQSL_F32_ACC64", who);
     if (!(p->tol > 0) || !isfinite(p->tol)) return fail(FQSL_ERR_ARG, "%s: tol must be > 0", who);
     if (!(p->h_min > 0) || !(p->h_max >= p->h_min) || !(p->h0 >= p->h_min) || !(p->h0 <= p->h_max) ||
         !isfinite(p->h_max))
@@ -262,7 +262,7 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
     if (!(p->tol_exp >= 0) || !isfinite(p->tol_exp)) return fail(FQSL_ERR_ARG, "%s: tol_exp >= 0", who);
     if (!(p->graze > 0) || !(p->graze < 1)) return fail(FQSL_ERR_ARG, "%s: graze in (0,1)", who);
     if (!(p->eps_way2 > 0) || !(p->eps_way2 < 0.5)) return fail(FQSL_ERR_ARG, "%s: eps_way2 in (0,0.5)", who);
-    if (p->precision == FQSL_F32 && !f->rec32)
+    if (p->precision != FQSL_F64 && !f->rec32)
         return fail(FQSL_ERR_UNSUPPORTED, "%s: field was not packed in FP32 (FQSL_PACK_F32)", who);
     if (p->precision == FQSL_F64 && !f->rec64)
         return fail(FQSL_ERR_UNSUPPORTED, "%s: field was not packed in FP64 (FQSL_PACK_F64)", who);
@@ -345,9 +345,11 @@ fqsl_status ensure_scratch(fqsl_field f, size_t bytes)
 
 int blocks_per_sm(fqsl_field f, int precision, int src)
 {
-    int *cache = precision == FQSL_F32 ? f->blocks_f32 : f->blocks_f64;
-    if (!cache[src]) cache[src] = precision == FQSL_F32 ? trace_blocks_per_sm_f32(src) : trace_blocks_per_sm_f64(src);
-    return cache[src];
+    int &c = f->blocks_cache[precision][src];
+    if (!c)
+        c = precision == FQSL_F64 ? trace_blocks_per_sm_f64(src)
+                                  : trace_blocks_per_sm_f32(src, precision == FQSL_F32_ACC64);
+    return c;
 }
 
 cudaError_t launch_trace(fqsl_field f, const fqsl_params *p, const TraceArgs &a, int src, long long items,
@@ -358,8 +360,9 @@ cudaError_t launch_trace(fqsl_field f, const fqsl_params *p, const TraceArgs &a,
     const long long need = (warps_needed * 32 + kTraceBlock - 1) / kTraceBlock;
     if (src != kSrcExtra && need < grid) grid = need;
     if (grid < 1) grid = 1;
-    return p->precision == FQSL_F32 ? launch_trace_f32(a, src, (int)grid, kTraceBlock, s)
-                                    : launch_trace_f64(a, src, (int)grid, kTraceBlock, s);
+    return p->precision == FQSL_F64 ? launch_trace_f64(a, src, (int)grid, kTraceBlock, s)
+                                    : launch_trace_f32(a, src, (int)grid, kTraceBlock, s,
+                                                       p->precision == FQSL_F32_ACC64);
 }
 
 void cross(const double *a, const double *b, double *c)
@@ -402,7 +405,7 @@ fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, co
 
     TraceArgs a{};
     a.f = f->g;
-    a.f.rec = p->precision == FQSL_F32 ? f->rec32 : f->rec64;
+    a.f.rec = p->precision == FQSL_F64 ? f->rec64 : f->rec32;
     a.p = dev_params(p);
     a.lat = lat;
     a.rec = s.rec;
@@ -542,7 +545,7 @@ fqsl_status fqsl_twist(fqsl_field f, const double *seeds_dev, long long n, const
     if (e != cudaSuccess) return cuda_fail(e, who);
     TraceArgs a{};
     a.f = f->g;
-    a.f.rec = p->precision == FQSL_F32 ? f->rec32 : f->rec64;
+    a.f.rec = p->precision == FQSL_F64 ? f->rec64 : f->rec32;
     a.p = dev_params(p);
     a.seeds = seeds_dev;
     a.nitems = n;
@@ -681,7 +684,7 @@ extern "C" fqsl_status fqsl_qmap_plane_static(fqsl_field f, const double origin[
     if (e != cudaSuccess) return cuda_fail(e, who);
     TraceArgs a{};
     a.f = f->g;
-    a.f.rec = p->precision == FQSL_F32 ? f->rec32 : f->rec64;
+    a.f.rec = p->precision == FQSL_F64 ? f->rec64 : f->rec32;
     a.p = dev_params(p);
     a.lat = lat;
     a.rec = s.rec;

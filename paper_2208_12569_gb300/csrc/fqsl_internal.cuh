@@ -102,9 +102,9 @@ constexpr unsigned kBad = FQSL_LINE_MAXSTEPS | FQSL_LINE_NULL_B | FQSL_LINE_OUTS
 // launch helpers implemented in the .cu files
 cudaError_t launch_curl_pack(const void *B, fqsl_dtype bt, const FieldView &g, void *rec32, void *rec64,
                              cudaStream_t s);
-cudaError_t launch_trace_f32(const TraceArgs &a, int src, int grid, int block, cudaStream_t s);
+cudaError_t launch_trace_f32(const TraceArgs &a, int src, int grid, int block, cudaStream_t s, bool acc64);
 cudaError_t launch_trace_f64(const TraceArgs &a, int src, int grid, int block, cudaStream_t s);
-int trace_blocks_per_sm_f32(int src);
+int trace_blocks_per_sm_f32(int src, bool acc64);
 int trace_blocks_per_sm_f64(int src);
 constexpr int kTraceBlock = 128;
 cudaError_t launch_assemble(const AssembleArgs &a, cudaStream_t s);

@@ -317,11 +317,58 @@ struct Lane {
     T t0;             // chord parameter of the first crossed face
     double tol;          // FP64: the line's tolerance; FP32: its square
     float tolf2;         // FP32: tol^2 for the step factor
-    double lacc, twacc;  // length / Tw of the current direction
+    double lacc, twacc;  // length / Tw of the current direction (FP64 sums)
+    float ls, lc, ts, tc;  // the same as compensated FP32 sums and their carries
     double l1, tw1;      // totals of end 1
-    double ol, otw;      // length / Tw at the end of the exiting step
+    double ol, otw;      // exiting step: FP64 sums at its end / FP32 its increments
     int steps, st, end, mode, hface, tries, fc0;
 };
+
+// Length and Tw of the current direction: FP64 sums (ACC, and the FP64
+// tracer) or compensated FP32 sums (Kahan 1965) whose total is formed in FP64
+// once per direction.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v)
+{
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+template <typename T, bool ACC>
+__device__ __forceinline__ void acc_reset(Lane<T> &L)
+{
+    if (ACC) {
+        L.lacc = 0.0;
+        L.twacc = 0.0;
+    } else {
+        L.ls = L.lc = L.ts = L.tc = 0.f;
+    }
+}
+
+template <typename T, bool ACC>
+__device__ __forceinline__ void acc_add(Lane<T> &L, T dl, T dtw)
+{
+    if (ACC) {
+        L.lacc = L.lacc + (double)dl;
+        L.twacc = L.twacc + (double)dtw;
+    } else {
+        kahan_add(L.ls, L.lc, (float)dl);
+        kahan_add(L.ts, L.tc, (float)dtw);
+    }
+}
+
+template <typename T, bool ACC>
+__device__ __forceinline__ double acc_len(const Lane<T> &L)
+{
+    return ACC ? L.lacc : (double)L.ls - (double)L.lc;
+}
+
+template <typename T, bool ACC>
+__device__ __forceinline__ double acc_tw(const Lane<T> &L)
+{
+    return ACC ? L.twacc : (double)L.ts - (double)L.tc;
+}
 
 template <typename T>
 __device__ __forceinline__ void write_end(const TraceArgs &A, const LineRecs &R, const Lane<T> &L, int e,
@@ -355,7 +402,7 @@ __device__ __forceinline__ void finish_bad(const TraceArgs &A, const LineRecs &R
 }
 
 // A direction reached a face at index position (x, y, z).
-template <typename T>
+template <typename T, bool ACC>
 __device__ __forceinline__ bool finish_dir(const TraceArgs &A, const LineRecs &R, Lane<T> &L, T x, T y, T z,
                                            int face)
 {
@@ -366,22 +413,21 @@ __device__ __forceinline__ bool finish_dir(const TraceArgs &A, const LineRecs &R
     write_end(A, R, L, L.end, to_phys(f.o[0], f.d[0], (double)x), to_phys(f.o[1], f.d[1], (double)y),
               to_phys(f.o[2], f.d[2], (double)z), face, sel3<double>(ax, B[0], B[1], B[2]));
     if (L.end == 0) {
-        L.l1 = L.lacc;
-        L.tw1 = L.twacc;
+        L.l1 = acc_len<T, ACC>(L);
+        L.tw1 = acc_tw<T, ACC>(L);
         L.end = 1;
         L.x = L.sx;
         L.y = L.sy;
         L.z = L.sz;
         L.h = (T)A.p.h0;
         L.mode = 0;
-        L.lacc = 0.0;
-        L.twacc = 0.0;
+        acc_reset<T, ACC>(L);
         return true;
     }
     R.st[L.line] = (uint8_t)L.st;
     R.steps[L.line] = L.steps;
-    if (R.tw) R.tw[L.line] = L.tw1 + L.twacc;
-    if (R.len) R.len[L.line] = L.l1 + L.lacc;
+    if (R.tw) R.tw[L.line] = L.tw1 + acc_tw<T, ACC>(L);
+    if (R.len) R.len[L.line] = L.l1 + acc_len<T, ACC>(L);
     return false;
 }
 
@@ -395,7 +441,7 @@ __device__ __forceinline__ bool inside(const FieldView &f, T x, T y, T z)
 // Start a line at index position xi (FP64: (r0 - o)/d as written) with
 // orientation vector n (NULL: end 1 is the backward end). Returns false if the
 // line ends at once (outside / null).
-template <typename T>
+template <typename T, bool ACC>
 __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R, Lane<T> &L, const double xi[3],
                                            const double *n, double tol, int st0)
 {
@@ -411,7 +457,7 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
     L.steps = 0;
     L.end = 0;
     L.mode = 0;
-    L.lacc = L.twacc = 0.0;
+    acc_reset<T, ACC>(L);
     L.h = (T)A.p.h0;
     if (kF64) {
         L.tol = tol;
@@ -457,7 +503,7 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
 }
 
 // Lattice seed: frame, tolerance and rotation decision (Sec. 4).
-template <typename T>
+template <typename T, bool ACC>
 __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, long long item)
 {
     constexpr bool kF64 = sizeof(T) == 8;
@@ -530,11 +576,11 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
         }
     }
     R.bn0[idx] = bn0;
-    return start_line<T>(A, R, L, xi, G.n0, tol, st0);
+    return start_line<T, ACC>(A, R, L, xi, G.n0, tol, st0);
 }
 
 // Rotated extra line q (0: +u, 1: -u, 2: +v, 3: -v) of rotated slot s (Sec. 4).
-template <typename T>
+template <typename T, bool ACC>
 __device__ __forceinline__ bool init_extra(const TraceArgs &A, Lane<T> &L, long long item)
 {
     const Lattice &G = A.lat;
@@ -563,10 +609,10 @@ __device__ __forceinline__ bool init_extra(const TraceArgs &A, Lane<T> &L, long 
 #pragma unroll
     for (int a = 0; a < 3; a++) xr[a] = (rr[a] - f.o[a]) / f.d[a];
     L.line = item;
-    return start_line<T>(A, A.ext, L, xr, nrot, A.p.tol, 0);
+    return start_line<T, ACC>(A, A.ext, L, xr, nrot, A.p.tol, 0);
 }
 
-template <typename T>
+template <typename T, bool ACC>
 __device__ __forceinline__ bool init_list(const TraceArgs &A, Lane<T> &L, long long item)
 {
     L.line = item;
@@ -574,13 +620,15 @@ __device__ __forceinline__ bool init_list(const TraceArgs &A, Lane<T> &L, long l
     double xi[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) xi[a] = (A.seeds[3 * item + a] - f.o[a]) / f.d[a];
-    return start_line<T>(A, A.rec, L, xi, nullptr, A.p.tol, 0);
+    return start_line<T, ACC>(A, A.rec, L, xi, nullptr, A.p.tol, 0);
 }
 
 // ---------------------------------------------------------------------------
 // the persistent kernel body
 // ---------------------------------------------------------------------------
-template <typename T, int SRC>
+// ACC: FP64 sums for the error norm and for length/Tw (always true for the
+// FP64 tracer); false: FP32 error norm and compensated FP32 sums.
+template <typename T, int SRC, bool ACC>
 __device__ __forceinline__ void trace_body(const TraceArgs &A)
 {
     constexpr unsigned FULL = 0xffffffffu;
@@ -624,9 +672,9 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             const int rank = __popc(idle & lt_mask);
             if (!active && rank < avail) {
                 const long long item = ck_cur + rank;
-                if (SRC == kSrcLattice) active = init_lattice<T>(A, L, item);
-                else if (SRC == kSrcExtra) active = init_extra<T>(A, L, item);
-                else active = init_list<T>(A, L, item);
+                if (SRC == kSrcLattice) active = init_lattice<T, ACC>(A, L, item);
+                else if (SRC == kSrcExtra) active = init_extra<T, ACC>(A, L, item);
+                else active = init_list<T, ACC>(A, L, item);
             }
             ck_cur += min((long long)__popc(idle), avail);
             idle = __ballot_sync(FULL, !active);
@@ -725,11 +773,16 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
                              d2 = (double)((L.z + hh * a5[2]) - nz);
                 err = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
                 over = err > L.tol;
-            } else {
+            } else if (ACC) {
                 const double ex = (double)a5[0], ey = (double)a5[1], ez = (double)a5[2];
                 err = (double)(hh * hh) * (ex * ex + ey * ey + ez * ez);  // err^2
                 over = err > L.tol;
                 rf = __fdividef(L.tolf2, (float)err);
+            } else {
+                const float e2 = (float)(hh * hh) * (float)(a5[0] * a5[0] + a5[1] * a5[1] + a5[2] * a5[2]);
+                over = e2 > L.tolf2;
+                err = e2 > 0.f ? 1.0 : 0.0;  // only its sign is used below
+                rf = __fdividef(L.tolf2, e2);
             }
             if (over) {
                 if (L.h > hmin) {
@@ -752,8 +805,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
                 L.x = nx;
                 L.y = ny;
                 L.z = nz;
-                L.lacc = L.lacc + (double)(hh * l4);
-                L.twacc = L.twacc + (double)(hh * tw4);
+                acc_add<T, ACC>(L, hh * l4, hh * tw4);
                 L.h = hn;
                 continue;
             }
@@ -784,8 +836,13 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             L.ox = nx;
             L.oy = ny;
             L.oz = nz;
-            L.ol = L.lacc + (double)(hh * l4);
-            L.otw = L.twacc + (double)(hh * tw4);
+            if (ACC) {
+                L.ol = L.lacc + (double)(hh * l4);
+                L.otw = L.twacc + (double)(hh * tw4);
+            } else {
+                L.ol = (double)(hh * l4);
+                L.otw = (double)(hh * tw4);
+            }
             L.t0 = tb;
             L.fc0 = best;
             L.hface = best;
@@ -808,10 +865,14 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             if (a0 == 0) ex = v0;
             else if (a0 == 1) ey = v0;
             else ez = v0;
-            L.lacc = L.lacc + (double)L.t0 * (L.ol - L.lacc);
-            L.twacc = L.twacc + (double)L.t0 * (L.otw - L.twacc);
+            if (ACC) {
+                L.lacc = L.lacc + (double)L.t0 * (L.ol - L.lacc);
+                L.twacc = L.twacc + (double)L.t0 * (L.otw - L.twacc);
+            } else {
+                acc_add<T, ACC>(L, (T)((double)L.t0 * L.ol), (T)((double)L.t0 * L.otw));
+            }
             L.st |= FQSL_LINE_CHORD;
-            active = finish_dir<T>(A, R, L, ex, ey, ez, L.fc0);
+            active = finish_dir<T, ACC>(A, R, L, ex, ey, ez, L.fc0);
             continue;
         }
         T tx = L.x + hh * a4[0], ty = L.y + hh * a4[1], tz = L.z + hh * a4[2];
@@ -839,9 +900,8 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             ty = fmin(fmax(ty, (T)0), (T)(f.ny - 1));
             tz = fmin(fmax(tz, (T)0), (T)(f.nz - 1));
         }
-        L.lacc = L.lacc + (double)(hh * l4);
-        L.twacc = L.twacc + (double)(hh * tw4);
-        active = finish_dir<T>(A, R, L, tx, ty, tz, L.hface);
+        acc_add<T, ACC>(L, hh * l4, hh * tw4);
+        active = finish_dir<T, ACC>(A, R, L, tx, ty, tz, L.hface);
     }
 }
 

@@ -1,6 +1,8 @@
-// FP32 instantiation of the persistent tracer: the cube and the line state are
-// in float; the error norm, the per-line tolerance and the Tw / length sums
-// are in double.
+// FP32 instantiations of the persistent tracer: the cube and the line state
+// are in float. ACC = false (precision FQSL_F32): error norm in float, length
+// and Tw as compensated float sums formed in double per direction. ACC = true
+// (FQSL_F32_ACC64): error norm and length/Tw sums accumulated in double. The
+// per-line tolerance, footpoints and Bn are double in both.
 #include "trace.cuh"
 
 // minimum resident blocks per SM requested from the register allocator
@@ -12,29 +14,44 @@ namespace fqsl {
 namespace {
 constexpr int kBlock = 128;
 
-template <int SRC>
+template <int SRC, bool ACC>
 __global__ void __launch_bounds__(kBlock, FQSL_TRACE_F32_MINB) k_trace_f32(const TraceArgs A)
 {
-    trace::trace_body<float, SRC>(A);
+    trace::trace_body<float, SRC, ACC>(A);
 }
 }  // namespace
 
-cudaError_t launch_trace_f32(const TraceArgs &a, int src, int grid, int block, cudaStream_t s)
+namespace {
+template <bool ACC>
+void launch(const TraceArgs &a, int src, int grid, int block, cudaStream_t s)
+{
+    if (src == kSrcLattice) k_trace_f32<kSrcLattice, ACC><<<grid, block, 0, s>>>(a);
+    else if (src == kSrcExtra) k_trace_f32<kSrcExtra, ACC><<<grid, block, 0, s>>>(a);
+    else k_trace_f32<kSrcList, ACC><<<grid, block, 0, s>>>(a);
+}
+
+template <bool ACC>
+int blocks(int src)
+{
+    int b = 0;
+    if (src == kSrcLattice)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_f32<kSrcLattice, ACC>, kBlock, 0);
+    else if (src == kSrcExtra)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_f32<kSrcExtra, ACC>, kBlock, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_f32<kSrcList, ACC>, kBlock, 0);
+    return b > 0 ? b : 1;
+}
+}  // namespace
+
+cudaError_t launch_trace_f32(const TraceArgs &a, int src, int grid, int block, cudaStream_t s, bool acc64)
 {
     if (block != kBlock) return cudaErrorInvalidValue;
-    if (src == kSrcLattice) k_trace_f32<kSrcLattice><<<grid, block, 0, s>>>(a);
-    else if (src == kSrcExtra) k_trace_f32<kSrcExtra><<<grid, block, 0, s>>>(a);
-    else k_trace_f32<kSrcList><<<grid, block, 0, s>>>(a);
+    if (acc64) launch<true>(a, src, grid, block, s);
+    else launch<false>(a, src, grid, block, s);
     return cudaGetLastError();
 }
 
-int trace_blocks_per_sm_f32(int src)
-{
-    int b = 0;
-    if (src == kSrcLattice) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_f32<kSrcLattice>, kBlock, 0);
-    else if (src == kSrcExtra) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_f32<kSrcExtra>, kBlock, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_f32<kSrcList>, kBlock, 0);
-    return b > 0 ? b : 1;
-}
+int trace_blocks_per_sm_f32(int src, bool acc64) { return acc64 ? blocks<true>(src) : blocks<false>(src); }
 
 }  // namespace fqsl

@@ -9,7 +9,7 @@ constexpr int kBlock = 128;
 template <int SRC>
 __global__ void __launch_bounds__(kBlock) k_trace_f64(const TraceArgs A)
 {
-    trace::trace_body<double, SRC>(A);
+    trace::trace_body<double, SRC, true>(A);
 }
 }  // namespace
 

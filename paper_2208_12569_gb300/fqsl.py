@@ -15,7 +15,7 @@ import torch
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfqsl.so")
 
-F32, F64 = 0, 1
+F32, F64, F32_ACC64 = 0, 1, 2
 PACK_F32, PACK_F64 = 1, 2
 LINE_MAXSTEPS, LINE_NULL_B, LINE_STALL, LINE_MIXED, LINE_OUTSIDE, LINE_ROTATED, LINE_CHORD = 1, 2, 4, 8, 16, 32, 64
 LINE_BAD = LINE_MAXSTEPS | LINE_NULL_B | LINE_OUTSIDE
@@ -85,13 +85,13 @@ def _check(status):
 
 def params(**kw) -> Params:
     """fqsl_params with the library defaults, overridden by keyword
-    (method, gradb_way, precision ('f32'/'f64' or 0/1), tol, h0, h_min, h_max,
+    (method, gradb_way, precision ('f32'/'f64'/'f32acc64' or 0/1/2), tol, h0, h_min, h_max,
     max_steps, rot_thresh, tol_exp, graze, eps_way2)."""
     p = Params()
     _lib.fqsl_params_default(C.byref(p))
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
-            v = {"f32": F32, "f64": F64}[v]
+            v = {"f32": F32, "f64": F64, "f32acc64": F32_ACC64}[v]
         if not hasattr(p, k):
             raise KeyError(k)
         setattr(p, k, v)

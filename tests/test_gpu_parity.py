@@ -101,12 +101,13 @@ def test_monopole_plane_fp64_parity_ragged(fq, oracle_lib, mono):
     assert_bitwise(g, r)
 
 
-def test_monopole_plane_fp32_error_stated(fq, oracle_lib, mono):
+@pytest.mark.parametrize("precision", ["f32", "f32acc64"])
+def test_monopole_plane_fp32_error_stated(fq, oracle_lib, mono, precision):
     B, grid = mono
     field = _field(fq, B, grid)
     nu, nv = 101, 75
     args = ((0.0, 0.0, 0.0), (63.0 / nu, 0, 0), (0, 55.0 / nv, 0), nu, nv)
-    g = _gpu_plane(fq, field, *args, precision="f32")
+    g = _gpu_plane(fq, field, *args, precision=precision)
     r = oracle.plane(B.astype(np.float64), grid, *args, oracle.params())
     assert np.mean(g["face2"] == r["face2"]) > 0.99
     rel = q_rel(g, r)
