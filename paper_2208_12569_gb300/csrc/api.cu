@@ -110,8 +110,8 @@ fqsl_status fqsl_field_create(const void *B_dev, fqsl_dtype b_dtype, long long n
     if (b_dtype != FQSL_F32 && b_dtype != FQSL_F64)
         return fail(FQSL_ERR_ARG, "fqsl_field_create: b_dtype must be FQSL_F32 or FQSL_F64");
     if (nx < 2 || ny < 2 || nz < 2) return fail(FQSL_ERR_ARG, "fqsl_field_create: need nx, ny, nz >= 2");
-    if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30) || nx * ny * nz > (1LL << 34))
-        return fail(FQSL_ERR_ARG, "fqsl_field_create: grid too large");
+    if (nx >= (1 << 23) || ny >= (1 << 23) || nz >= (1 << 23) || nx * ny * nz >= (1LL << 31))
+        return fail(FQSL_ERR_ARG, "fqsl_field_create: grid too large (each axis < 2^23 nodes, < 2^31 nodes)");
     if (!finite3(origin) || !finite3(spacing))
         return fail(FQSL_ERR_ARG, "fqsl_field_create: origin/spacing must be finite");
     if (!(spacing[0] > 0 && spacing[1] > 0 && spacing[2] > 0))
@@ -136,6 +136,11 @@ fqsl_status fqsl_field_create(const void *B_dev, fqsl_dtype b_dtype, long long n
         f->g.o[a] = origin[a];
         f->g.d[a] = spacing[a];
     }
+    f->g.cmax[0] = (float)(nx - 2);
+    f->g.cmax[1] = (float)(ny - 2);
+    f->g.cmax[2] = (float)(nz - 2);
+    f->g.sy32 = (unsigned)(nx * 32);
+    f->g.sz32 = (unsigned)(nx * ny * 32 <= 0xffffffffLL ? nx * ny * 32 : 0);
     const size_t nodes = (size_t)nx * ny * nz;
     if (flags & FQSL_PACK_F32) {
         e = cudaMalloc(&f->rec32, nodes * 32);

@@ -31,6 +31,8 @@ struct FieldView {
     int nx, ny, nz;
     double o[3];  // origin
     double d[3];  // spacing
+    float cmax[3];            // largest cell index per axis, n - 2, as float
+    unsigned sy32, sz32;      // FP32 record byte strides along y and z
 };
 
 struct DevParams {

@@ -127,16 +127,39 @@ __device__ __forceinline__ T clampcell(T c, int n)
     return fmin(fmax(c, (T)0), (T)(n - 2));
 }
 
-// FP32: weights as products of per-axis weights, corners grouped by (y, z).
+// One 32-byte FP32 node record in a single 256-bit read-only load (records are
+// 32-byte aligned: the allocation is, and every record offset is a multiple of
+// 32). Returns Bx, By, Bz, Jx, Jy, Jz.
+__device__ __forceinline__ void load_rec32(const char *p, float &b0, float &b1, float &b2, float &j0, float &j1,
+                                           float &j2)
+{
+    float pad0, pad1;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(b0), "=f"(b1), "=f"(b2), "=f"(j0), "=f"(j1), "=f"(j2), "=f"(pad0), "=f"(pad1)
+        : "l"(p));
+}
+
+// Exact integer value of a float that holds an integer in [0, 2^23): adding
+// 2^23 puts it in the low mantissa bits. (A float -> 64-bit integer conversion
+// runs on GB300's narrow FP64 pipe; this is one FADD and one integer op.)
+__device__ __forceinline__ int small_int(float c) { return __float_as_int(c + 8388608.f) - 0x4B000000; }
+
+// FP32: weights as products of per-axis weights, corners grouped by (y, z);
+// 32-bit cell arithmetic and byte strides (field_create keeps every axis below
+// 2^23 nodes and the cube below 2^31 nodes; sz32 = 0 marks a z stride that
+// does not fit 32 bits).
 __device__ __forceinline__ void gather(const FieldView &f, float x, float y, float z, float B[3], float J[3])
 {
-    const float cx = clampcell<float>(floorf(x), f.nx);
-    const float cy = clampcell<float>(floorf(y), f.ny);
-    const float cz = clampcell<float>(floorf(z), f.nz);
+    const float cx = fminf(fmaxf(floorf(x), 0.f), f.cmax[0]);
+    const float cy = fminf(fmaxf(floorf(y), 0.f), f.cmax[1]);
+    const float cz = fminf(fmaxf(floorf(z), 0.f), f.cmax[2]);
     const float wx = x - cx, wy = y - cy, wz = z - cz;
     const float ux = 1.f - wx, uy = 1.f - wy, uz = 1.f - wz;
-    const long long sy = f.nx, sz = (long long)f.nx * f.ny;
-    const long long base = (long long)cz * sz + (long long)cy * sy + (long long)cx;
+    const unsigned node = ((unsigned)small_int(cz) * (unsigned)f.ny + (unsigned)small_int(cy)) * (unsigned)f.nx +
+                          (unsigned)small_int(cx);
+    const char *p00 = (const char *)f.rec + (size_t)node * 32u;
+    const size_t szb = f.sz32 ? (size_t)f.sz32 : (size_t)f.nx * (size_t)f.ny * 32u;
+    const char *pc[4] = {p00, p00 + f.sy32, p00 + szb, p00 + szb + f.sy32};
     const float wyz[4] = {uy * uz, wy * uz, uy * wz, wy * wz};
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -145,18 +168,17 @@ __device__ __forceinline__ void gather(const FieldView &f, float x, float y, flo
     }
 #pragma unroll
     for (int qp = 0; qp < 4; qp++) {
-        const long long node = base + (qp & 1) * sy + (qp >> 1) * sz;
 #pragma unroll
         for (int m = 0; m < 2; m++) {
-            float bx, by, bz, jx, jy, jz;
-            load_node(f, node + m, bx, by, bz, jx, jy, jz);
+            float r0, r1, r2, r3, r4, r5;
+            load_rec32(pc[qp] + 32 * m, r0, r1, r2, r3, r4, r5);
             const float w = (m ? wx : ux) * wyz[qp];
-            B[0] += w * bx;
-            B[1] += w * by;
-            B[2] += w * bz;
-            J[0] += w * jx;
-            J[1] += w * jy;
-            J[2] += w * jz;
+            B[0] += w * r0;
+            B[1] += w * r1;
+            B[2] += w * r2;
+            J[0] += w * r3;
+            J[1] += w * r4;
+            J[2] += w * r5;
         }
     }
 }
@@ -767,21 +789,23 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             // (tol^2/err^2)^(1/8) in float)
             double err = 0.0;
             float rf = 0.f;
-            bool over;
+            bool over, pos;
             if (kF64) {
                 const double d0 = (double)((L.x + hh * a5[0]) - nx), d1 = (double)((L.y + hh * a5[1]) - ny),
                              d2 = (double)((L.z + hh * a5[2]) - nz);
                 err = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
                 over = err > L.tol;
+                pos = err > 0.0;
             } else if (ACC) {
                 const double ex = (double)a5[0], ey = (double)a5[1], ez = (double)a5[2];
                 err = (double)(hh * hh) * (ex * ex + ey * ey + ez * ez);  // err^2
                 over = err > L.tol;
+                pos = err > 0.0;
                 rf = __fdividef(L.tolf2, (float)err);
             } else {
                 const float e2 = (float)(hh * hh) * (float)(a5[0] * a5[0] + a5[1] * a5[1] + a5[2] * a5[2]);
                 over = e2 > L.tolf2;
-                err = e2 > 0.f ? 1.0 : 0.0;  // only its sign is used below
+                pos = e2 > 0.f;
                 rf = __fdividef(L.tolf2, e2);
             }
             if (over) {
@@ -794,7 +818,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
                 L.st |= FQSL_LINE_STALL;
             }
             T hn;
-            if (err > 0.0) {
+            if (pos) {
                 const T q = kF64 ? (T)root4(L.tol / err) : (T)sqrtf(root4(rf));
                 hn = L.h * fmin((T)4, (T)0.9 * q);
             } else {
