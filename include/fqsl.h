@@ -184,7 +184,8 @@ FQSL_API fqsl_status fqsl_twist(fqsl_field field, const double *seeds_dev, long 
 /* Per-kernel timing. With timing enabled, every later call on this field
  * records CUDA events on its own stream around its kernels; fqsl_field_times
  * waits for the events of the last call and returns their durations in
- * milliseconds: ms[0] line tracer (lattice or seed list), ms[1] tracer of the
+ * milliseconds: ms[0] line tracer (lattice or seed list; the FP32 seed
+ * pre-pass runs just before it and is not included), ms[1] tracer of the
  * rotated-S0 extra lines (0 if not launched), ms[2] Q assembly. Errors:
  * FQSL_ERR_ARG (NULL, or no timed call yet), FQSL_ERR_CUDA. */
 FQSL_API fqsl_status fqsl_field_set_timing(fqsl_field field, int enable);

@@ -294,34 +294,52 @@ DevParams dev_params(const fqsl_params *p)
 
 struct Scratch {
     LineRecs rec{}, ext{};
+    SeedPrep prep{};
     int32_t *rot_seed = nullptr, *rot_slot = nullptr;
     size_t bytes = 0;
 };
 
 // Lay out the per-call scratch for n primary lines (and 4 n extra lines when
-// rotation is possible). With base == NULL only the size is computed.
-Scratch layout(char *base, long long n, bool rot, bool want_bn)
+// rotation is possible): FP64 records for the FP64 tracer, index-space
+// records and the seed pre-pass arrays for the FP32 tracers. With base == NULL
+// only the size is computed.
+Scratch layout(char *base, long long n, bool rot, bool lattice, bool f32)
 {
     Carver c{base};
     Scratch s;
     LineRecs &r = s.rec;
-    r.r1 = c.take<double>(3 * n);
-    r.r2 = c.take<double>(3 * n);
-    r.bn1 = want_bn ? c.take<double>(n) : nullptr;
-    r.bn2 = want_bn ? c.take<double>(n) : nullptr;
-    r.bn0 = want_bn ? c.take<double>(n) : nullptr;
-    r.tw = c.take<double>(n);
-    r.len = c.take<double>(n);
+    if (f32) {
+        r.xi1 = c.take<float>(3 * n);
+        r.xi2 = c.take<float>(3 * n);
+        r.kacc = c.take<float4>(2 * n);
+    } else {
+        r.r1 = c.take<double>(3 * n);
+        r.r2 = c.take<double>(3 * n);
+        r.bn1 = lattice ? c.take<double>(n) : nullptr;
+        r.bn2 = lattice ? c.take<double>(n) : nullptr;
+        r.tw = c.take<double>(n);
+        r.len = c.take<double>(n);
+    }
+    r.bn0 = lattice ? c.take<double>(n) : nullptr;
     r.f1 = c.take<int8_t>(n);
     r.f2 = c.take<int8_t>(n);
     r.st = c.take<uint8_t>(n);
     r.steps = c.take<int32_t>(n);
+    if (f32 && lattice) {
+        s.prep.seed = c.take<float4>(n);
+        s.prep.flags = c.take<uint8_t>(n);
+    }
     if (rot) {
         s.rot_seed = c.take<int32_t>(n);
         s.rot_slot = c.take<int32_t>(n);
         LineRecs &x = s.ext;
-        x.r1 = c.take<double>(12 * n);
-        x.r2 = c.take<double>(12 * n);
+        if (f32) {
+            x.xi1 = c.take<float>(12 * n);
+            x.xi2 = c.take<float>(12 * n);
+        } else {
+            x.r1 = c.take<double>(12 * n);
+            x.r2 = c.take<double>(12 * n);
+        }
         x.f1 = c.take<int8_t>(4 * n);
         x.f2 = c.take<int8_t>(4 * n);
         x.st = c.take<uint8_t>(4 * n);
@@ -398,11 +416,12 @@ fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, co
     lat.tiles_u = (lat.n1 + kTileU - 1) / kTileU;
     lat.tiles_v = (lat.n2 + kTileV - 1) / kTileV;
     lat.allow_rot = (p->method == 1 && !face_plane) ? 1 : 0;
+    const bool f32 = p->precision != FQSL_F64;
     std::lock_guard<std::mutex> lock(f->mu);
-    Scratch sz = layout(nullptr, n, lat.allow_rot, true);
+    Scratch sz = layout(nullptr, n, lat.allow_rot, true, f32);
     fqsl_status st = ensure_scratch(f, sz.bytes);
     if (st != FQSL_OK) return st;
-    Scratch s = layout((char *)f->scratch, n, lat.allow_rot, true);
+    Scratch s = layout((char *)f->scratch, n, lat.allow_rot, true, f32);
 
     cudaError_t e = cudaMemsetAsync(f->counters, 0, 4 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess && lat.allow_rot) e = cudaMemsetAsync(s.rot_slot, 0, (size_t)n * sizeof(int32_t), stream);
@@ -419,7 +438,12 @@ fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, co
     a.q.rot_count = (unsigned int *)(f->counters + 2);
     a.q.rot_seed = s.rot_seed;
     a.q.rot_slot = s.rot_slot;
+    a.prep = s.prep;
     a.nitems = lat.n3 * lat.tiles_u * lat.tiles_v * (long long)(kTileU * kTileV);
+    if (f32) {
+        e = launch_seed_prep_f32(a, n, stream);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+    }
     mark(f, 0, stream);
     e = launch_trace(f, p, a, kSrcLattice, a.nitems, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
@@ -431,6 +455,7 @@ fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, co
     }
     mark(f, 2, stream);
     AssembleArgs g{};
+    g.f = a.f;
     g.lat = lat;
     g.rec = s.rec;
     g.ext = s.ext;
@@ -438,7 +463,7 @@ fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, co
     g.out = *out;
     g.n = n;
     g.want_q = 1;
-    e = launch_assemble(g, stream);
+    e = f32 ? launch_assemble_f32(g, stream) : launch_assemble(g, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     mark(f, 3, stream);
     f->timed = f->timing;
@@ -541,11 +566,12 @@ fqsl_status fqsl_twist(fqsl_field f, const double *seeds_dev, long long n, const
     if (!seeds_dev) return fail(FQSL_ERR_ARG, "%s: seeds_dev is NULL", who);
     if (((uintptr_t)seeds_dev) % 8) return fail(FQSL_ERR_ARG, "%s: seeds_dev must be 8-byte aligned", who);
     cudaStream_t stream = (cudaStream_t)cuda_stream;
+    const bool f32 = p->precision != FQSL_F64;
     std::lock_guard<std::mutex> lock(f->mu);
-    Scratch sz = layout(nullptr, n, false, false);
+    Scratch sz = layout(nullptr, n, false, false, f32);
     st = ensure_scratch(f, sz.bytes);
     if (st != FQSL_OK) return st;
-    Scratch s = layout((char *)f->scratch, n, false, false);
+    Scratch s = layout((char *)f->scratch, n, false, false, f32);
     cudaError_t e = cudaMemsetAsync(f->counters, 0, 4 * sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     TraceArgs a{};
@@ -562,6 +588,7 @@ fqsl_status fqsl_twist(fqsl_field f, const double *seeds_dev, long long n, const
     mark(f, 1, stream);
     mark(f, 2, stream);
     AssembleArgs g{};
+    g.f = a.f;
     g.lat.n1 = n;
     g.lat.n2 = 1;
     g.lat.n3 = 1;
@@ -570,7 +597,7 @@ fqsl_status fqsl_twist(fqsl_field f, const double *seeds_dev, long long n, const
     g.out.Q = nullptr;
     g.n = n;
     g.want_q = 0;
-    e = launch_assemble(g, stream);
+    e = f32 ? launch_assemble_f32(g, stream) : launch_assemble(g, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     mark(f, 3, stream);
     f->timed = f->timing;
@@ -676,11 +703,12 @@ extern "C" fqsl_status fqsl_qmap_plane_static(fqsl_field f, const double origin[
     // counters first, then the line records
     unsigned long long *counters = (unsigned long long *)base;
     const size_t head = 256;
-    Scratch need = layout(nullptr, n, lat.allow_rot, true);
+    const bool f32 = p->precision != FQSL_F64;
+    Scratch need = layout(nullptr, n, lat.allow_rot, true, f32);
     if (head + need.bytes > kStaticScratchBytes)
         return fail(FQSL_ERR_ARG, "%s: %lld seeds need %zu scratch bytes, the static array holds %zu", who, n,
                     head + need.bytes, kStaticScratchBytes);
-    Scratch s = layout(base + head, n, lat.allow_rot, true);
+    Scratch s = layout(base + head, n, lat.allow_rot, true, f32);
     cudaStream_t stream = (cudaStream_t)cuda_stream;
 
     std::lock_guard<std::mutex> lock(f->mu);
@@ -698,7 +726,12 @@ extern "C" fqsl_status fqsl_qmap_plane_static(fqsl_field f, const double origin[
     a.q.rot_count = (unsigned int *)(counters + 2);
     a.q.rot_seed = s.rot_seed;
     a.q.rot_slot = s.rot_slot;
+    a.prep = s.prep;
     a.nitems = lat.n3 * lat.tiles_u * lat.tiles_v * (long long)(kTileU * kTileV);
+    if (f32) {
+        e = launch_seed_prep_f32(a, n, stream);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+    }
     e = launch_trace(f, p, a, kSrcLattice, a.nitems, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     if (lat.allow_rot) {
@@ -707,6 +740,7 @@ extern "C" fqsl_status fqsl_qmap_plane_static(fqsl_field f, const double origin[
         if (e != cudaSuccess) return cuda_fail(e, who);
     }
     AssembleArgs g{};
+    g.f = a.f;
     g.lat = lat;
     g.rec = s.rec;
     g.ext = s.ext;
@@ -714,7 +748,7 @@ extern "C" fqsl_status fqsl_qmap_plane_static(fqsl_field f, const double origin[
     g.out = *out;
     g.n = n;
     g.want_q = 1;
-    e = launch_assemble(g, stream);
+    e = f32 ? launch_assemble_f32(g, stream) : launch_assemble(g, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     return FQSL_OK;
 }

@@ -1,0 +1,142 @@
+// q_assemble for the FP32 tracers: the FP32 tracer leaves index-space
+// footpoints, exit faces and compensated length/Tw partial sums; this kernel
+// forms, in FP64 and with every thread of a warp busy, the physical
+// footpoints, Bn at both ends (trilinear B of the FP32 records, Sec. 2.2), the
+// length and Tw totals (Eq. tw), and Method I's Q (Eqs. D+-2, D+-3, Q+- with
+// |det D| -> |Bn1/Bn2|, Eq. Bn1): J_e = d(face coordinates)/d(S0
+// coordinates) by central differences when both neighbours end on the
+// centre's face, one-sided when one does, NaN and FQSL_LINE_MIXED otherwise.
+// Neighbouring footpoints are differenced in index space first (exact for
+// nearby values in float) and scaled by the spacing in FP64.
+#include <math.h>
+
+#include "trace.cuh"
+
+namespace fqsl {
+namespace {
+
+// the two non-normal axes of a face, in increasing order
+__device__ __forceinline__ void face_axes(int face, int &r0, int &r1)
+{
+    const int a = face >> 1;
+    r0 = (a == 0) ? 1 : 0;
+    r1 = (a == 2) ? 1 : 2;
+}
+
+__device__ __forceinline__ double bn_at(const FieldView &f, const float *xi, int face)
+{
+    float B[3], J[3];
+    trace::gather(f, xi[0], xi[1], xi[2], B, J);
+    const int a = face >> 1;
+    return (double)(a == 0 ? B[0] : (a == 1 ? B[1] : B[2]));
+}
+
+__global__ void __launch_bounds__(256) k_assemble_f32(const AssembleArgs A)
+{
+    const Lattice &G = A.lat;
+    const FieldView &f = A.f;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < A.n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const LineRecs &R = A.rec;
+        unsigned st = R.st[idx];
+        const bool bad = (st & kBad) != 0;
+        const float *x1 = R.xi1 + 3 * idx, *x2 = R.xi2 + 3 * idx;
+        const int f1 = R.f1[idx], f2 = R.f2[idx];
+        double Q = NAN;
+        if (A.want_q && !bad) {
+            const long long i = idx % G.n1, j = (idx / G.n1) % G.n2, k = idx / (G.n1 * G.n2);
+            const int slot = A.rot_slot ? A.rot_slot[idx] : 0;
+            const LineRecs *NR = slot > 0 ? &A.ext : &A.rec;
+            long long nid[4];
+            bool has[4];
+            double du = G.du, dv = G.dv;
+            if (slot > 0) {
+                for (int q = 0; q < 4; q++) {
+                    nid[q] = (long long)(slot - 1) * 4 + q;
+                    has[q] = true;
+                }
+                du = dv = G.drot;
+            } else {
+                const long long ni[4] = {i + 1, i - 1, i, i}, nj[4] = {j, j, j + 1, j - 1};
+                for (int q = 0; q < 4; q++) {
+                    has[q] = ni[q] >= 0 && ni[q] < G.n1 && nj[q] >= 0 && nj[q] < G.n2;
+                    nid[q] = ni[q] + G.n1 * (nj[q] + G.n2 * k);
+                }
+            }
+            double Jm[2][2][2];
+            bool mixed = false;
+            for (int e = 0; e < 2 && !mixed; e++) {
+                const int fe = e == 0 ? f1 : f2;
+                int ra[2];
+                face_axes(fe, ra[0], ra[1]);
+                const float *c0 = e == 0 ? x1 : x2;
+                for (int s = 0; s < 2 && !mixed; s++) {
+                    const int P = 2 * s, M = 2 * s + 1;
+                    const double del = s ? dv : du;
+                    const float *cp = nullptr, *cm = nullptr;
+                    if (has[P] && !(NR->st[nid[P]] & kBad) && (e == 0 ? NR->f1 : NR->f2)[nid[P]] == fe)
+                        cp = (e == 0 ? NR->xi1 : NR->xi2) + 3 * nid[P];
+                    if (has[M] && !(NR->st[nid[M]] & kBad) && (e == 0 ? NR->f1 : NR->f2)[nid[M]] == fe)
+                        cm = (e == 0 ? NR->xi1 : NR->xi2) + 3 * nid[M];
+                    for (int r = 0; r < 2; r++) {
+                        const int a = ra[r];
+                        if (cp && cm) Jm[e][r][s] = (double)(cp[a] - cm[a]) * f.d[a] / (2.0 * del);
+                        else if (cp) Jm[e][r][s] = (double)(cp[a] - c0[a]) * f.d[a] / del;
+                        else if (cm) Jm[e][r][s] = (double)(c0[a] - cm[a]) * f.d[a] / del;
+                        else mixed = true;
+                    }
+                }
+            }
+            if (mixed) {
+                st |= FQSL_LINE_MIXED;
+            } else {
+                const double adj[2][2] = {{Jm[0][1][1], -Jm[0][0][1]}, {-Jm[0][1][0], Jm[0][0][0]}};
+                double norm2 = 0.0;
+                for (int r = 0; r < 2; r++)
+                    for (int s = 0; s < 2; s++) {
+                        const double m = Jm[1][r][0] * adj[0][s] + Jm[1][r][1] * adj[1][s];
+                        norm2 += m * m;
+                    }
+                const double bn0 = R.bn0[idx];
+                Q = norm2 * fabs(bn_at(f, x1, f1) * bn_at(f, x2, f2)) / (bn0 * bn0);
+            }
+        }
+        const fqsl_out &o = A.out;
+        if (o.Q) o.Q[idx] = Q;
+        if (o.Tw || o.length) {
+            double tw = NAN, len = NAN;
+            if (!bad) {
+                const float4 k0 = R.kacc[2 * idx], k1 = R.kacc[2 * idx + 1];
+                len = ((double)k0.x - (double)k0.y) + ((double)k1.x - (double)k1.y);
+                tw = ((double)k0.z - (double)k0.w) + ((double)k1.z - (double)k1.w);
+            }
+            if (o.Tw) o.Tw[idx] = tw;
+            if (o.length) o.length[idx] = len;
+        }
+        if (o.r1)
+            for (int c = 0; c < 3; c++) o.r1[3 * idx + c] = fma(f.d[c], (double)x1[c], f.o[c]);
+        if (o.r2)
+            for (int c = 0; c < 3; c++) o.r2[3 * idx + c] = fma(f.d[c], (double)x2[c], f.o[c]);
+        if (o.face1) o.face1[idx] = (int8_t)f1;
+        if (o.face2) o.face2[idx] = (int8_t)f2;
+        if (o.status) o.status[idx] = (uint8_t)st;
+        if (o.steps) o.steps[idx] = R.steps[idx];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_assemble_f32(const AssembleArgs &a, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long blocks = (a.n + 255) / 256;
+    const long long cap = (long long)sms * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_assemble_f32<<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace fqsl

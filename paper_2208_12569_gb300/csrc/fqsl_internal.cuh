@@ -59,15 +59,29 @@ struct Lattice {
     int allow_rot;     // Method I and some layer may be interior
 };
 
-// Per-line results in structure-of-arrays form (library scratch).
+// Per-line results in structure-of-arrays form (library scratch). The FP64
+// tracer writes physical footpoints, Bn and the length/Tw totals; the FP32
+// tracer writes index-space footpoints and compensated partial sums, which the
+// FP32 assembly turns into the same quantities in FP64.
 struct LineRecs {
-    double *r1, *r2;    // physical footpoints, 3 per line
-    double *bn1, *bn2;  // B . n at each end
+    double *r1, *r2;    // FP64: physical footpoints, 3 per line
+    double *bn1, *bn2;  // FP64: B . n at each end
     double *bn0;        // B0 . n0 (or |B0| when S0 is perpendicular to B)
-    double *tw, *len;
+    double *tw, *len;   // FP64: totals
+    float *xi1, *xi2;   // FP32: index-space footpoints, 3 per line
+    float4 *kacc;       // FP32: per direction {length sum, its carry, Tw sum, its carry}, 2 per line
     int8_t *f1, *f2;
     uint8_t *st;
     int32_t *steps;
+};
+
+// FP32 seed pre-pass output: index-space seed and tol^2, and flags.
+constexpr uint8_t kSeedNegS0 = 1;   // end 1 is traced along +B (B0 . n0 < 0)
+constexpr uint8_t kSeedDone = 2;    // the line's record is final (outside / null seed)
+constexpr uint8_t kSeedRotated = 4; // S0 rotated (Sec. 4)
+struct SeedPrep {
+    float4 *seed;     // {xi_x, xi_y, xi_z, tol^2}
+    uint8_t *flags;
 };
 
 struct Queue {
@@ -88,9 +102,11 @@ struct TraceArgs {
     LineRecs rec;         // primary lines (lattice or list)
     LineRecs ext;         // rotated extra lines, 4 per slot
     Queue q;
+    SeedPrep prep;        // FP32 lattice: filled by the seed pre-pass
 };
 
 struct AssembleArgs {
+    FieldView f;          // FP32 records (FP32 assembly: Bn at the footpoints)
     Lattice lat;
     LineRecs rec, ext;
     const int32_t *rot_slot;  // may be NULL
@@ -110,5 +126,7 @@ int trace_blocks_per_sm_f32(int src, bool acc64);
 int trace_blocks_per_sm_f64(int src);
 constexpr int kTraceBlock = 128;
 cudaError_t launch_assemble(const AssembleArgs &a, cudaStream_t s);
+cudaError_t launch_assemble_f32(const AssembleArgs &a, cudaStream_t s);
+cudaError_t launch_seed_prep_f32(const TraceArgs &a, long long n, cudaStream_t s);
 
 }  // namespace fqsl

@@ -137,6 +137,8 @@ __device__ __forceinline__ void load_rec32(const char *p, float &b0, float &b1, 
     asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=f"(b0), "=f"(b1), "=f"(b2), "=f"(j0), "=f"(j1), "=f"(j2), "=f"(pad0), "=f"(pad1)
         : "l"(p));
+    (void)pad0;
+    (void)pad1;
 }
 
 // Exact integer value of a float that holds an integer in [0, 2^23): adding
@@ -392,6 +394,7 @@ __device__ __forceinline__ double acc_tw(const Lane<T> &L)
     return ACC ? L.twacc : (double)L.ts - (double)L.tc;
 }
 
+// FP64 end record: physical footpoint, face and Bn.
 template <typename T>
 __device__ __forceinline__ void write_end(const TraceArgs &A, const LineRecs &R, const Lane<T> &L, int e,
                                           double px, double py, double pz, int face, double bn)
@@ -405,6 +408,18 @@ __device__ __forceinline__ void write_end(const TraceArgs &A, const LineRecs &R,
     if (bnp) bnp[L.line] = bn;
 }
 
+// FP32 end record: index-space footpoint and face (the assembly forms the
+// physical footpoint and Bn).
+__device__ __forceinline__ void write_end32(const LineRecs &R, long long line, int e, float x, float y, float z,
+                                            int face)
+{
+    float *r = (e == 0 ? R.xi1 : R.xi2) + 3 * line;
+    r[0] = x;
+    r[1] = y;
+    r[2] = z;
+    (e == 0 ? R.f1 : R.f2)[line] = (int8_t)face;
+}
+
 // Finish the line with a bad status (MAXSTEPS or NULL_B): the unfinished end
 // is the current position, an untraced end the seed, their faces -1.
 template <typename T>
@@ -412,15 +427,20 @@ __device__ __forceinline__ void finish_bad(const TraceArgs &A, const LineRecs &R
 {
     const FieldView &f = A.f;
     L.st |= bit;
-    write_end(A, R, L, L.end, to_phys(f.o[0], f.d[0], (double)L.x), to_phys(f.o[1], f.d[1], (double)L.y),
-              to_phys(f.o[2], f.d[2], (double)L.z), -1, 0.0);
-    if (L.end == 0)
-        write_end(A, R, L, 1, to_phys(f.o[0], f.d[0], (double)L.sx), to_phys(f.o[1], f.d[1], (double)L.sy),
-                  to_phys(f.o[2], f.d[2], (double)L.sz), -1, 0.0);
+    if constexpr (sizeof(T) == 8) {
+        write_end(A, R, L, L.end, to_phys(f.o[0], f.d[0], (double)L.x), to_phys(f.o[1], f.d[1], (double)L.y),
+                  to_phys(f.o[2], f.d[2], (double)L.z), -1, 0.0);
+        if (L.end == 0)
+            write_end(A, R, L, 1, to_phys(f.o[0], f.d[0], (double)L.sx), to_phys(f.o[1], f.d[1], (double)L.sy),
+                      to_phys(f.o[2], f.d[2], (double)L.sz), -1, 0.0);
+        if (R.tw) R.tw[L.line] = NAN;
+        if (R.len) R.len[L.line] = NAN;
+    } else {
+        write_end32(R, L.line, L.end, (float)L.x, (float)L.y, (float)L.z, -1);
+        if (L.end == 0) write_end32(R, L.line, 1, (float)L.sx, (float)L.sy, (float)L.sz, -1);
+    }
     R.st[L.line] = (uint8_t)L.st;
     R.steps[L.line] = L.steps;
-    if (R.tw) R.tw[L.line] = NAN;
-    if (R.len) R.len[L.line] = NAN;
 }
 
 // A direction reached a face at index position (x, y, z).
@@ -429,14 +449,31 @@ __device__ __forceinline__ bool finish_dir(const TraceArgs &A, const LineRecs &R
                                            int face)
 {
     const FieldView &f = A.f;
-    double B[3];
-    b_at<T>(f, (double)x, (double)y, (double)z, B);
-    const int ax = face >> 1;
-    write_end(A, R, L, L.end, to_phys(f.o[0], f.d[0], (double)x), to_phys(f.o[1], f.d[1], (double)y),
-              to_phys(f.o[2], f.d[2], (double)z), face, sel3<double>(ax, B[0], B[1], B[2]));
+    if constexpr (sizeof(T) == 8) {
+        double B[3];
+        b_at<T>(f, (double)x, (double)y, (double)z, B);
+        const int ax = face >> 1;
+        write_end(A, R, L, L.end, to_phys(f.o[0], f.d[0], (double)x), to_phys(f.o[1], f.d[1], (double)y),
+                  to_phys(f.o[2], f.d[2], (double)z), face, sel3<double>(ax, B[0], B[1], B[2]));
+    } else {
+        write_end32(R, L.line, L.end, (float)x, (float)y, (float)z, face);
+        if (R.kacc) {
+            float4 k;
+            if (ACC) {
+                // FP64 sums: carry the value and its float residue
+                const float lh = (float)L.lacc, th = (float)L.twacc;
+                k = make_float4(lh, -(float)(L.lacc - (double)lh), th, -(float)(L.twacc - (double)th));
+            } else {
+                k = make_float4(L.ls, L.lc, L.ts, L.tc);
+            }
+            R.kacc[2 * L.line + L.end] = k;
+        }
+    }
     if (L.end == 0) {
-        L.l1 = acc_len<T, ACC>(L);
-        L.tw1 = acc_tw<T, ACC>(L);
+        if constexpr (sizeof(T) == 8) {
+            L.l1 = acc_len<T, ACC>(L);
+            L.tw1 = acc_tw<T, ACC>(L);
+        }
         L.end = 1;
         L.x = L.sx;
         L.y = L.sy;
@@ -448,8 +485,10 @@ __device__ __forceinline__ bool finish_dir(const TraceArgs &A, const LineRecs &R
     }
     R.st[L.line] = (uint8_t)L.st;
     R.steps[L.line] = L.steps;
-    if (R.tw) R.tw[L.line] = L.tw1 + acc_tw<T, ACC>(L);
-    if (R.len) R.len[L.line] = L.l1 + acc_len<T, ACC>(L);
+    if constexpr (sizeof(T) == 8) {
+        if (R.tw) R.tw[L.line] = L.tw1 + acc_tw<T, ACC>(L);
+        if (R.len) R.len[L.line] = L.l1 + acc_len<T, ACC>(L);
+    }
     return false;
 }
 
@@ -509,14 +548,19 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
     if (bad) {
         L.st |= bad;
         // footpoints of a line that never started: its seed
-        const double qx = to_phys(f.o[0], f.d[0], xi[0]), qy = to_phys(f.o[1], f.d[1], xi[1]),
-                     qz = to_phys(f.o[2], f.d[2], xi[2]);
-        write_end(A, R, L, 0, qx, qy, qz, -1, 0.0);
-        write_end(A, R, L, 1, qx, qy, qz, -1, 0.0);
+        if constexpr (sizeof(T) == 8) {
+            const double qx = to_phys(f.o[0], f.d[0], xi[0]), qy = to_phys(f.o[1], f.d[1], xi[1]),
+                         qz = to_phys(f.o[2], f.d[2], xi[2]);
+            write_end(A, R, L, 0, qx, qy, qz, -1, 0.0);
+            write_end(A, R, L, 1, qx, qy, qz, -1, 0.0);
+            if (R.tw) R.tw[L.line] = NAN;
+            if (R.len) R.len[L.line] = NAN;
+        } else {
+            write_end32(R, L.line, 0, (float)xi[0], (float)xi[1], (float)xi[2], -1);
+            write_end32(R, L.line, 1, (float)xi[0], (float)xi[1], (float)xi[2], -1);
+        }
         R.st[L.line] = (uint8_t)L.st;
         R.steps[L.line] = 0;
-        if (R.tw) R.tw[L.line] = NAN;
-        if (R.len) R.len[L.line] = NAN;
         return false;
     }
     L.s0 = (T)1;
@@ -544,6 +588,26 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
     L.line = idx;
     const FieldView &f = A.f;
     const LineRecs &R = A.rec;
+    if constexpr (!kF64) {
+        // FP32: the seed pre-pass did the set-up (and wrote final records of
+        // seeds outside the box or on a null)
+        const uint8_t fl = A.prep.flags[idx];
+        if (fl & kSeedDone) return false;
+        const float4 sd = A.prep.seed[idx];
+        L.sx = L.x = sd.x;
+        L.sy = L.y = sd.y;
+        L.sz = L.z = sd.z;
+        L.tolf2 = sd.w;
+        L.tol = (double)sd.w;
+        L.s0 = (fl & kSeedNegS0) ? (T)-1 : (T)1;
+        L.st = (fl & kSeedRotated) ? FQSL_LINE_ROTATED : 0;
+        L.steps = 0;
+        L.end = 0;
+        L.mode = 0;
+        acc_reset<T, ACC>(L);
+        L.h = (T)A.p.h0;
+        return true;
+    }
     double xi[3];
     if (kF64) {
         // physical seed, then (r0 - o)/d, as written
@@ -927,6 +991,77 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
         acc_add<T, ACC>(L, hh * l4, hh * tw4);
         active = finish_dir<T, ACC>(A, R, L, tx, ty, tz, L.hface);
     }
+}
+
+// FP32 seed set-up for every lattice seed, one thread each (convergent): the
+// index-space seed, Bn0, the S0 rotation decision and the per-line tolerance
+// (Sec. 4, Eq. tol), or the final record of a seed outside the box or on a
+// null field.
+__device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
+{
+    const Lattice &G = A.lat;
+    const FieldView &f = A.f;
+    const LineRecs &R = A.rec;
+    const long long i = idx % G.n1, j = (idx / G.n1) % G.n2, k = idx / (G.n1 * G.n2);
+    const double fi = (double)i + 0.5, fj = (double)j + 0.5, fk = (double)k + 0.5;
+    double xi[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) xi[a] = fma(fk, G.xa3[a], fma(fj, G.xa2[a], fma(fi, G.xa1[a], G.xo[a])));
+    const float x = (float)xi[0], y = (float)xi[1], z = (float)xi[2];
+    uint8_t fl = 0;
+    unsigned bad = 0;
+    double bn0 = 0.0, tol = A.p.tol;
+    const bool in = xi[0] >= 0.0 && xi[0] <= (double)(f.nx - 1) && xi[1] >= 0.0 && xi[1] <= (double)(f.ny - 1) &&
+                    xi[2] >= 0.0 && xi[2] <= (double)(f.nz - 1);
+    if (!in) {
+        bad = FQSL_LINE_OUTSIDE;
+    } else {
+        float B0[3], J0[3];
+        gather(f, x, y, z, B0, J0);
+        const float b0 = B0[0] * (float)(1.0 / f.d[0]), b1 = B0[1] * (float)(1.0 / f.d[1]),
+                    b2 = B0[2] * (float)(1.0 / f.d[2]);
+        const float bb = b0 * b0 + b1 * b1 + b2 * b2;
+        const float nB = sqrtf(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
+        if (!(bb > 0.f) || !(bb < INFINITY) || !(nB > 0.f)) {
+            bad = FQSL_LINE_NULL_B;
+        } else {
+            const float bn = B0[0] * (float)G.n0[0] + B0[1] * (float)G.n0[1] + B0[2] * (float)G.n0[2];
+            if (bn < 0.f) fl |= kSeedNegS0;
+            if (A.p.method == 2) {
+                bn0 = (double)nB;
+            } else {
+                const float ratio = fabsf(bn) / nB;
+                bool on_face = false;
+                if (G.normal_axis >= 0) {
+                    const double xa = xi[G.normal_axis];
+                    const int na = G.normal_axis == 0 ? f.nx : (G.normal_axis == 1 ? f.ny : f.nz);
+                    on_face = (xa == 0.0) || (xa == (double)(na - 1));
+                }
+                if (G.allow_rot && ratio < (float)A.p.rot && !on_face) {
+                    fl |= kSeedRotated;
+                    bn0 = (double)nB;
+                    const unsigned slot = atomicAdd(A.q.rot_count, 1u);
+                    A.q.rot_seed[slot] = (int32_t)idx;
+                    A.q.rot_slot[idx] = (int32_t)slot + 1;
+                } else {
+                    bn0 = (double)bn;
+                    const float xr = fmaxf(ratio, (float)A.p.rot);
+                    const float g = A.p.texp == 1.5 ? xr * sqrtf(xr) : __powf(xr, (float)A.p.texp);
+                    tol = A.p.tol * (double)g;
+                }
+            }
+        }
+    }
+    R.bn0[idx] = bn0;
+    if (bad) {
+        fl |= kSeedDone;
+        write_end32(R, idx, 0, x, y, z, -1);
+        write_end32(R, idx, 1, x, y, z, -1);
+        R.st[idx] = (uint8_t)bad;
+        R.steps[idx] = 0;
+    }
+    A.prep.seed[idx] = make_float4(x, y, z, (float)(tol * tol));
+    A.prep.flags[idx] = fl;
 }
 
 }  // namespace trace

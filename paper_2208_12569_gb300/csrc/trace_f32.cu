@@ -55,3 +55,27 @@ cudaError_t launch_trace_f32(const TraceArgs &a, int src, int grid, int block, c
 int trace_blocks_per_sm_f32(int src, bool acc64) { return acc64 ? blocks<true>(src) : blocks<false>(src); }
 
 }  // namespace fqsl
+
+namespace fqsl {
+namespace {
+__global__ void __launch_bounds__(256) k_seed_prep_f32(const TraceArgs A, long long n)
+{
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x)
+        trace::seed_prep_f32(A, idx);
+}
+}  // namespace
+
+cudaError_t launch_seed_prep_f32(const TraceArgs &a, long long n, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long blocks = (n + 255) / 256;
+    if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+    if (blocks < 1) blocks = 1;
+    k_seed_prep_f32<<<(unsigned)blocks, 256, 0, s>>>(a, n);
+    return cudaGetLastError();
+}
+
+}  // namespace fqsl
