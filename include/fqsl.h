@@ -89,7 +89,8 @@ typedef struct {
     int method;           /* 1 = neighbour differences (Method I), 2 = deviation vectors (Method II) */
     int gradb_way;        /* Method II gradient of B/|B|: 1 = node grid (Eq. grad_B), 2 = +-eps differences */
     int precision;        /* FQSL_F32 (default), FQSL_F64 or FQSL_F32_ACC64 (see fqsl_dtype) */
-    int reserved0;
+    int refill_lanes;     /* scheduling: a warp takes new seeds once this many of its 32 lanes are idle
+                             (1..32; 0 = library default). Results do not depend on it. */
     double tol;           /* tol_perp (Method I; scaled per line by |Bn0/B|^tol_exp) or tol (Method II, twist); default 10^-3.2 */
     double h0;            /* initial step, default 0.5 */
     double h_min;         /* smallest step, default 1e-6 */
@@ -99,6 +100,9 @@ typedef struct {
     double tol_exp;       /* obliquity exponent of Eq. tol, default 1.5 */
     double graze;         /* smallest outward face-normal velocity of the exit step, default 1e-3 */
     double eps_way2;      /* Method II way-2 offset, default 1e-3 */
+    int sync_dirs;        /* scheduling: 1 = the lanes of a warp start their second directions together,
+                             0 = each lane at once, -1 = library default. Results do not depend on it. */
+    int reserved1;
 } fqsl_params;
 
 /* Output buffers of one call (caller-owned device memory, n = number of

@@ -93,6 +93,7 @@ void fqsl_params_default(fqsl_params *p)
     p->tol_exp = 1.5;
     p->graze = 1e-3;
     p->eps_way2 = 1e-3;
+    p->sync_dirs = -1;
 }
 
 const char *fqsl_version(void) { return "fqsl 0.1.0 (sm_103a)"; }
@@ -267,6 +268,8 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
     if (!(p->tol_exp >= 0) || !isfinite(p->tol_exp)) return fail(FQSL_ERR_ARG, "%s: tol_exp >= 0", who);
     if (!(p->graze > 0) || !(p->graze < 1)) return fail(FQSL_ERR_ARG, "%s: graze in (0,1)", who);
     if (!(p->eps_way2 > 0) || !(p->eps_way2 < 0.5)) return fail(FQSL_ERR_ARG, "%s: eps_way2 in (0,0.5)", who);
+    if (p->refill_lanes < 0 || p->refill_lanes > 32) return fail(FQSL_ERR_ARG, "%s: refill_lanes in [0, 32]", who);
+    if (p->sync_dirs < -1 || p->sync_dirs > 1) return fail(FQSL_ERR_ARG, "%s: sync_dirs in {-1, 0, 1}", who);
     if (p->precision != FQSL_F64 && !f->rec32)
         return fail(FQSL_ERR_UNSUPPORTED, "%s: field was not packed in FP32 (FQSL_PACK_F32)", who);
     if (p->precision == FQSL_F64 && !f->rec64)
@@ -274,6 +277,10 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
     if (p->method == 2) return fail(FQSL_ERR_UNSUPPORTED, "%s: Method II is not built yet", who);
     return FQSL_OK;
 }
+
+// scheduling defaults (measured on GB300)
+constexpr int kDefaultRefill = 32;
+constexpr int kDefaultSyncDirs = 0;
 
 DevParams dev_params(const fqsl_params *p)
 {
@@ -289,6 +296,8 @@ DevParams dev_params(const fqsl_params *p)
     d.max_steps = p->max_steps;
     d.method = p->method;
     d.way = p->gradb_way;
+    d.refill = p->refill_lanes > 0 ? p->refill_lanes : kDefaultRefill;
+    d.sync_dirs = p->sync_dirs >= 0 ? p->sync_dirs : kDefaultSyncDirs;
     return d;
 }
 

@@ -63,6 +63,8 @@ __global__ void __launch_bounds__(256) k_assemble_f32(const AssembleArgs A)
                     nid[q] = ni[q] + G.n1 * (nj[q] + G.n2 * k);
                 }
             }
+            // reciprocal lattice steps: one division per axis instead of one per entry
+            const double inv[2] = {1.0 / du, 1.0 / dv};
             double Jm[2][2][2];
             bool mixed = false;
             for (int e = 0; e < 2 && !mixed; e++) {
@@ -72,7 +74,7 @@ __global__ void __launch_bounds__(256) k_assemble_f32(const AssembleArgs A)
                 const float *c0 = e == 0 ? x1 : x2;
                 for (int s = 0; s < 2 && !mixed; s++) {
                     const int P = 2 * s, M = 2 * s + 1;
-                    const double del = s ? dv : du;
+                    const double rdel = inv[s];
                     const float *cp = nullptr, *cm = nullptr;
                     if (has[P] && !(NR->st[nid[P]] & kBad) && (e == 0 ? NR->f1 : NR->f2)[nid[P]] == fe)
                         cp = (e == 0 ? NR->xi1 : NR->xi2) + 3 * nid[P];
@@ -80,9 +82,9 @@ __global__ void __launch_bounds__(256) k_assemble_f32(const AssembleArgs A)
                         cm = (e == 0 ? NR->xi1 : NR->xi2) + 3 * nid[M];
                     for (int r = 0; r < 2; r++) {
                         const int a = ra[r];
-                        if (cp && cm) Jm[e][r][s] = (double)(cp[a] - cm[a]) * f.d[a] / (2.0 * del);
-                        else if (cp) Jm[e][r][s] = (double)(cp[a] - c0[a]) * f.d[a] / del;
-                        else if (cm) Jm[e][r][s] = (double)(c0[a] - cm[a]) * f.d[a] / del;
+                        if (cp && cm) Jm[e][r][s] = (double)(cp[a] - cm[a]) * (0.5 * f.d[a] * rdel);
+                        else if (cp) Jm[e][r][s] = (double)(cp[a] - c0[a]) * (f.d[a] * rdel);
+                        else if (cm) Jm[e][r][s] = (double)(c0[a] - cm[a]) * (f.d[a] * rdel);
                         else mixed = true;
                     }
                 }

@@ -5,8 +5,9 @@
 // with 2nd-order central differences inside (the stencil of Eq. grad_B),
 // 2nd-order one-sided differences on the faces and first order on a 2-node
 // axis, and packed next to B so that one trilinear gather (Sec. 2.2, Eq.
-// interp) fetches both. The stencil arithmetic is done in FP64 for both record
-// precisions. One thread per node, grid-stride; streaming and HBM-bound.
+// interp) fetches both. FP64 records (and FP32 records of an FP64 cube) use
+// FP64 stencils written as plain expressions; FP32 records of an FP32 cube use
+// float stencils. One thread per node, grid-stride; streaming and HBM-bound.
 #include "fqsl_internal.cuh"
 
 namespace fqsl {
@@ -57,6 +58,39 @@ __global__ void __launch_bounds__(256) k_curl_pack(const TI *__restrict__ B, int
     }
 }
 
+// FP32 records only: the same stencils in float with reciprocal spacings (the
+// FP64 kernel above is the one whose rounding matches a plain evaluation).
+__device__ __forceinline__ float node_diff32(const float *__restrict__ B, int c, long long node, long long stride,
+                                             long long i, long long n, float rh, float rh2)
+{
+    auto F = [&](long long kk) -> float { return B[(node + (kk - i) * stride) * 3 + c]; };
+    if (n == 2) return (F(1) - F(0)) * rh;
+    if (i == 0) return (-3.f * F(0) + 4.f * F(1) - F(2)) * rh2;
+    if (i == n - 1) return (3.f * F(n - 1) - 4.f * F(n - 2) + F(n - 3)) * rh2;
+    return (F(i + 1) - F(i - 1)) * rh2;
+}
+
+__global__ void __launch_bounds__(256) k_curl_pack32(const float *__restrict__ B, int nx, int ny, int nz, float rx,
+                                                     float ry, float rz, float4 *__restrict__ rec32)
+{
+    const long long total = (long long)nx * ny * nz;
+    const long long sy = nx, sz = (long long)nx * ny;
+    for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < total;
+         node += (long long)gridDim.x * blockDim.x) {
+        const long long i = node % nx;
+        const long long j = (node / nx) % ny;
+        const long long k = node / sz;
+        const float dyBz = node_diff32(B, 2, node, sy, j, ny, ry, 0.5f * ry);
+        const float dzBy = node_diff32(B, 1, node, sz, k, nz, rz, 0.5f * rz);
+        const float dzBx = node_diff32(B, 0, node, sz, k, nz, rz, 0.5f * rz);
+        const float dxBz = node_diff32(B, 2, node, 1, i, nx, rx, 0.5f * rx);
+        const float dxBy = node_diff32(B, 1, node, 1, i, nx, rx, 0.5f * rx);
+        const float dyBx = node_diff32(B, 0, node, sy, j, ny, ry, 0.5f * ry);
+        rec32[2 * node + 0] = make_float4(B[node * 3 + 0], B[node * 3 + 1], B[node * 3 + 2], dyBz - dzBy);
+        rec32[2 * node + 1] = make_float4(dzBx - dxBz, dxBy - dyBx, 0.f, 0.f);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_curl_pack(const void *B, fqsl_dtype bt, const FieldView &g, void *rec32, void *rec64,
@@ -70,7 +104,16 @@ cudaError_t launch_curl_pack(const void *B, fqsl_dtype bt, const FieldView &g, v
     const long long cap = (long long)sms * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    if (bt == FQSL_F32)
+    if (bt == FQSL_F32 && rec32) {
+        // FP32 records from an FP32 cube: float stencils (the FP64 records, if
+        // also wanted, come from the FP64 stencils below)
+        k_curl_pack32<<<(unsigned)blocks, 256, 0, s>>>((const float *)B, g.nx, g.ny, g.nz, (float)(1.0 / g.d[0]),
+                                                       (float)(1.0 / g.d[1]), (float)(1.0 / g.d[2]),
+                                                       (float4 *)rec32);
+        if (rec64)
+            k_curl_pack<float><<<(unsigned)blocks, 256, 0, s>>>((const float *)B, g.nx, g.ny, g.nz, g.d[0], g.d[1],
+                                                               g.d[2], nullptr, (double2 *)rec64);
+    } else if (bt == FQSL_F32)
         k_curl_pack<float><<<(unsigned)blocks, 256, 0, s>>>((const float *)B, g.nx, g.ny, g.nz, g.d[0], g.d[1],
                                                            g.d[2], (float4 *)rec32, (double2 *)rec64);
     else

@@ -39,6 +39,8 @@ struct DevParams {
     double tol, h0, hmin, hmax, rot, texp, graze, eps2;
     long long max_steps;
     int method, way;
+    int refill;     // minimum idle lanes before a warp takes new seeds
+    int sync_dirs;  // lanes wait for each other before their second direction
 };
 
 // Cell-centred lattice seed(i,j,k) = o + (i+1/2) a1 + (j+1/2) a2 + (k+1/2) a3.

@@ -736,13 +736,16 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
     long long ck_cur = 0, ck_end = 0;
     bool exhausted = false;
     bool active = false;
+    bool waiting = false;  // sync_dirs: first direction done, second not started
     Lane<T> L;
     L.line = 0;
 
     for (;;) {
-        // refill idle lanes from the warp's chunk / the global counter
+        // refill idle lanes from the warp's chunk / the global counter, once
+        // at least p.refill lanes are idle (or none is busy)
         unsigned idle = __ballot_sync(FULL, !active);
-        while (idle != 0u && !exhausted) {
+        const bool refill = __popc(idle) >= A.p.refill || idle == FULL;
+        while (refill && idle != 0u && !exhausted) {
             if (ck_cur >= ck_end) {
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(A.q.head, (unsigned long long)kChunk);
@@ -766,7 +769,11 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             idle = __ballot_sync(FULL, !active);
         }
         if (__ballot_sync(FULL, active) == 0u) break;
-        if (!active) continue;
+        if (A.p.sync_dirs) {
+            // lanes that finished their first direction wait until none is left in it
+            if (__ballot_sync(FULL, active && !waiting && L.end == 0) == 0u) waiting = false;
+        }
+        if (!active || waiting) continue;
 
         // ---- one trial: normal RKF45 step or exit (Henon) step ----
         const bool henon = L.mode != 0;
@@ -961,6 +968,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             }
             L.st |= FQSL_LINE_CHORD;
             active = finish_dir<T, ACC>(A, R, L, ex, ey, ez, L.fc0);
+            waiting = active && A.p.sync_dirs;
             continue;
         }
         T tx = L.x + hh * a4[0], ty = L.y + hh * a4[1], tz = L.z + hh * a4[2];
@@ -990,6 +998,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
         }
         acc_add<T, ACC>(L, hh * l4, hh * tw4);
         active = finish_dir<T, ACC>(A, R, L, tx, ty, tz, L.hface);
+        waiting = active && A.p.sync_dirs;
     }
 }
 
