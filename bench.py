@@ -46,6 +46,21 @@ FLOPS_PER_TRIAL = 6 * 145 + 222
 GATHER_BYTES_PER_TRIAL = 6 * 8 * 32
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
+# DRAM bytes (read + write) of one k_trace_f32 launch on this workload, from
+# the ncu capture summarised in profiles/trace_f32_c2_monopole_1024x1024.md,
+# valid while the tracer sources hash to TRACE_F32_SRC_HASH.
+TRACE_F32_DRAM_BYTES = 308.808448e6 + 59.993856e6
+TRACE_F32_SRC_HASH = "efc172667b648b79"
+
+
+def _trace_src_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in ("trace.cuh", "trace_f32.cu"):
+        with open(os.path.join(ROOT, "paper_2208_12569_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _measured_peaks():
@@ -342,10 +357,14 @@ def main():
             "kernels_ms": {"trace_f32": trace_ms, "assemble": asm_ms},
             "work": {"trial_steps_per_map": trials, "mean_trials_per_line": trials / n},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": achieved / alu_peak, "traffic": None,
+                         "frac": achieved / alu_peak,
+                         "traffic": TRACE_F32_DRAM_BYTES if _trace_src_hash() == TRACE_F32_SRC_HASH else None,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, peak_kind),
                          "gather": {"achieved_TBs": gather_tbs, "l1_nominal_TBs": l1_peak,
-                                    "frac": gather_tbs / l1_peak}},
+                                    "frac": gather_tbs / l1_peak,
+                                    "note": "bytes requested by the trilinear gathers over the nominal L1 byte "
+                                            "rate; the binding unit is the L1 data pipe's wavefronts "
+                                            "(ncu: 76% of peak, profiles/trace_f32_c2_monopole_1024x1024.md)"}},
             "e2e": {"value": e2e_value, "unit": "Q+Tw values/s", "ms_per_step": float(np.mean(e2e_ms)),
                     "h2d_bytes_per_step": int(B.nbytes), "d2h_bytes_per_step": int(2 * n * 8)},
             "gpu_launches": 3 * args.steps, "clocks": clk}
