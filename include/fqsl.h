@@ -73,6 +73,8 @@ typedef enum { FQSL_F32 = 0, FQSL_F64 = 1, FQSL_F32_ACC64 = 2 } fqsl_dtype;
 /* fqsl_field_create flags: which packed node records to build. */
 #define FQSL_PACK_F32 1u   /* 32-byte records {Bx,By,Bz,Jx | Jy,Jz,0,0} in float */
 #define FQSL_PACK_F64 2u   /* 64-byte records {Bx,By | Bz,Jx | Jy,Jz | 0,0} in double */
+#define FQSL_PACK_GRADB 4u /* also the grad(B/|B|) node grid for Method II way 1 (Sec. 4, Eq. grad_B):
+                              48-byte FP32 and/or 80-byte FP64 records, for the precisions packed */
 
 /* per-line status bits (status[] output) */
 #define FQSL_LINE_MAXSTEPS 1u  /* max_steps trial steps used before both ends were found */
@@ -141,7 +143,8 @@ FQSL_API const char *fqsl_last_error(void);
  * computes curl B at the nodes (2nd-order central differences inside,
  * 2nd-order one-sided on the faces, first order on a 2-node axis: the curl grid
  * of Eq. tw) and packs B with it into node records of the precisions asked for
- * in flags (FQSL_PACK_F32 and/or FQSL_PACK_F64). The handle owns those
+ * in flags (FQSL_PACK_F32 and/or FQSL_PACK_F64; FQSL_PACK_GRADB adds the
+ * gradient grid of B/|B| for Method II way 1). The handle owns those
  * records and its scratch memory; the caller may free B_dev once the stream has
  * run the call. Errors: FQSL_ERR_ARG (null pointers, sizes, flags),
  * FQSL_ERR_OOM, FQSL_ERR_CUDA. */
@@ -165,9 +168,12 @@ FQSL_API fqsl_status fqsl_field_destroy(fqsl_field field);
  * of Method I is |u| along u and |v| along v (Sec. 2.1). On a plane that lies
  * on a box face no rotation of S0 is done; elsewhere seeds with |Bn0/B| <
  * rot_thresh use S0 perpendicular to B and four extra lines at +-delta along
- * its axes, delta = min(|u|,|v|) (Sec. 4). The field must have been packed in
- * params->precision. Errors: FQSL_ERR_ARG, FQSL_ERR_UNSUPPORTED (precision not
- * packed), FQSL_ERR_OOM, FQSL_ERR_CUDA. */
+ * its axes, delta = min(|u|,|v|) (Sec. 4). With params->method = 2 every line
+ * carries the deviation vectors U, V of the frame perpendicular to B at its
+ * seed (Sec. 2.1, Eq. rb2) and Q follows Eq. q_scott; gradb_way 1 needs a
+ * field packed with FQSL_PACK_GRADB. The field must have been packed in
+ * params->precision. Errors: FQSL_ERR_ARG, FQSL_ERR_UNSUPPORTED (precision or
+ * gradient grid not packed), FQSL_ERR_OOM, FQSL_ERR_CUDA. */
 FQSL_API fqsl_status fqsl_qmap_plane(fqsl_field field, const double origin[3], const double u[3],
                             const double v[3], long long nu, long long nv,
                             const fqsl_params *params, const fqsl_out *out, void *cuda_stream);
@@ -216,7 +222,8 @@ FQSL_API fqsl_status fqsl_field_times(fqsl_field field, float ms[3]);
  *   - all calls share the one array: the call clears what must start at zero,
  *     and calls whose work overlaps on the GPU (other streams, other host
  *     threads) race on it, so serialise them;
- *   - the field handle (created beforehand by fqsl_field_create) is only read.
+ *   - the field handle (created beforehand by fqsl_field_create) is only read;
+ *   - Method I only (params->method = 2 gives FQSL_ERR_UNSUPPORTED).
  */
 FQSL_API fqsl_status fqsl_qmap_plane_static(fqsl_field field, const double origin[3], const double u[3],
                                             const double v[3], long long nu, long long nv,

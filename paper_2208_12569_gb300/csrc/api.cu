@@ -59,10 +59,12 @@ struct fqsl_field_s {
     int sms = 0;
     FieldView g{};
     void *rec32 = nullptr, *rec64 = nullptr;
+    void *grad32 = nullptr, *grad64 = nullptr;  // Method II way 1 gradient grid
     void *scratch = nullptr;
     size_t scratch_cap = 0;
     unsigned long long *counters = nullptr;  // [0] primary head, [1] extra head, [2] rotated count (low 32 bits)
     int blocks_cache[3][3] = {};  // [precision][source] resident blocks per SM
+    int blocks_cache_m2[2][2] = {};  // Method II: [fp64][way - 1]
     bool timing = false, timed = false, extra_timed = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::mutex mu;
@@ -117,8 +119,9 @@ fqsl_status fqsl_field_create(const void *B_dev, fqsl_dtype b_dtype, long long n
         return fail(FQSL_ERR_ARG, "fqsl_field_create: origin/spacing must be finite");
     if (!(spacing[0] > 0 && spacing[1] > 0 && spacing[2] > 0))
         return fail(FQSL_ERR_ARG, "fqsl_field_create: spacing must be > 0");
-    if (flags == 0 || (flags & ~(FQSL_PACK_F32 | FQSL_PACK_F64)))
-        return fail(FQSL_ERR_ARG, "fqsl_field_create: flags must be a non-empty set of FQSL_PACK_*");
+    if (!(flags & (FQSL_PACK_F32 | FQSL_PACK_F64)) || (flags & ~(FQSL_PACK_F32 | FQSL_PACK_F64 | FQSL_PACK_GRADB)))
+        return fail(FQSL_ERR_ARG, "fqsl_field_create: flags must hold FQSL_PACK_F32 and/or FQSL_PACK_F64 "
+                                  "(and optionally FQSL_PACK_GRADB)");
     if (((uintptr_t)B_dev) % 16) return fail(FQSL_ERR_ARG, "fqsl_field_create: B_dev must be 16-byte aligned");
     cudaPointerAttributes attr;
     cudaError_t e = cudaPointerGetAttributes(&attr, B_dev);
@@ -158,17 +161,34 @@ fqsl_status fqsl_field_create(const void *B_dev, fqsl_dtype b_dtype, long long n
             return cuda_fail(e, "fqsl_field_create: FP64 records");
         }
     }
+    if (flags & FQSL_PACK_GRADB) {
+        if (f->rec32) e = cudaMalloc(&f->grad32, nodes * 48);
+        if (e == cudaSuccess && f->rec64) e = cudaMalloc(&f->grad64, nodes * 80);
+        if (e != cudaSuccess) {
+            cudaFree(f->rec32);
+            cudaFree(f->rec64);
+            cudaFree(f->grad32);
+            delete f;
+            return cuda_fail(e, "fqsl_field_create: gradient records");
+        }
+    }
     e = cudaMalloc(&f->counters, 4 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         cudaFree(f->rec32);
         cudaFree(f->rec64);
+        cudaFree(f->grad32);
+        cudaFree(f->grad64);
         delete f;
         return cuda_fail(e, "fqsl_field_create: counters");
     }
     e = launch_curl_pack(B_dev, b_dtype, f->g, f->rec32, f->rec64, (cudaStream_t)cuda_stream);
+    if (e == cudaSuccess && (f->grad32 || f->grad64))
+        e = launch_gradb_pack(B_dev, b_dtype, f->g, f->grad32, f->grad64, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) {
         cudaFree(f->rec32);
         cudaFree(f->rec64);
+        cudaFree(f->grad32);
+        cudaFree(f->grad64);
         cudaFree(f->counters);
         delete f;
         return cuda_fail(e, "fqsl_field_create: curl_pack launch");
@@ -187,6 +207,8 @@ fqsl_status fqsl_field_update(fqsl_field f, const void *B_dev, fqsl_dtype b_dtyp
     if (((uintptr_t)B_dev) % 16) return fail(FQSL_ERR_ARG, "fqsl_field_update: B_dev must be 16-byte aligned");
     std::lock_guard<std::mutex> lock(f->mu);
     cudaError_t e = launch_curl_pack(B_dev, b_dtype, f->g, f->rec32, f->rec64, (cudaStream_t)cuda_stream);
+    if (e == cudaSuccess && (f->grad32 || f->grad64))
+        e = launch_gradb_pack(B_dev, b_dtype, f->g, f->grad32, f->grad64, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return cuda_fail(e, "fqsl_field_update: curl_pack launch");
     return FQSL_OK;
 }
@@ -231,6 +253,8 @@ fqsl_status fqsl_field_destroy(fqsl_field f)
         if (f->ev[i]) cudaEventDestroy(f->ev[i]);
     cudaFree(f->rec32);
     cudaFree(f->rec64);
+    cudaFree(f->grad32);
+    cudaFree(f->grad64);
     cudaFree(f->scratch);
     cudaFree(f->counters);
     delete f;
@@ -274,7 +298,8 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
         return fail(FQSL_ERR_UNSUPPORTED, "%s: field was not packed in FP32 (FQSL_PACK_F32)", who);
     if (p->precision == FQSL_F64 && !f->rec64)
         return fail(FQSL_ERR_UNSUPPORTED, "%s: field was not packed in FP64 (FQSL_PACK_F64)", who);
-    if (p->method == 2) return fail(FQSL_ERR_UNSUPPORTED, "%s: Method II is not built yet", who);
+    if (p->method == 2 && p->gradb_way == 1 && !(p->precision == FQSL_F64 ? f->grad64 : f->grad32))
+        return fail(FQSL_ERR_UNSUPPORTED, "%s: Method II way 1 needs a field packed with FQSL_PACK_GRADB", who);
     return FQSL_OK;
 }
 
@@ -312,11 +337,21 @@ struct Scratch {
 // rotation is possible): FP64 records for the FP64 tracer, index-space
 // records and the seed pre-pass arrays for the FP32 tracers. With base == NULL
 // only the size is computed.
-Scratch layout(char *base, long long n, bool rot, bool lattice, bool f32)
+Scratch layout(char *base, long long n, bool rot, bool lattice, bool f32, bool m2 = false)
 {
     Carver c{base};
     Scratch s;
     LineRecs &r = s.rec;
+    if (m2) {
+        if (f32) {
+            r.dev32 = c.take<float>(12 * n);
+            s.prep.fu = c.take<float4>(n);
+            s.prep.fv = c.take<float4>(n);
+        } else {
+            r.dev64 = c.take<double>(12 * n);
+            r.be64 = c.take<double>(6 * n);
+        }
+    }
     if (f32) {
         r.xi1 = c.take<float>(3 * n);
         r.xi2 = c.take<float>(3 * n);
@@ -397,6 +432,20 @@ cudaError_t launch_trace(fqsl_field f, const fqsl_params *p, const TraceArgs &a,
                                                        p->precision == FQSL_F32_ACC64);
 }
 
+cudaError_t launch_trace_m2(fqsl_field f, const fqsl_params *p, const TraceArgs &a, cudaStream_t s)
+{
+    int &c = f->blocks_cache_m2[p->precision == FQSL_F64 ? 1 : 0][p->gradb_way - 1];
+    if (!c)
+        c = p->precision == FQSL_F64 ? trace_dev_blocks_per_sm_f64(p->gradb_way)
+                                     : trace_dev_blocks_per_sm_f32(p->gradb_way);
+    long long grid = (long long)f->sms * c;
+    const long long need = (a.nitems + kTraceBlock - 1) / kTraceBlock;
+    if (need < grid) grid = need;
+    if (grid < 1) grid = 1;
+    return p->precision == FQSL_F64 ? launch_trace_dev_f64(a, p->gradb_way, (int)grid, kTraceBlock, s)
+                                    : launch_trace_dev_f32(a, p->gradb_way, (int)grid, kTraceBlock, s);
+}
+
 void cross(const double *a, const double *b, double *c)
 {
     c[0] = a[1] * b[2] - a[2] * b[1];
@@ -426,11 +475,12 @@ fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, co
     lat.tiles_v = (lat.n2 + kTileV - 1) / kTileV;
     lat.allow_rot = (p->method == 1 && !face_plane) ? 1 : 0;
     const bool f32 = p->precision != FQSL_F64;
+    const bool m2 = p->method == 2;
     std::lock_guard<std::mutex> lock(f->mu);
-    Scratch sz = layout(nullptr, n, lat.allow_rot, true, f32);
+    Scratch sz = layout(nullptr, n, lat.allow_rot, true, f32, m2);
     fqsl_status st = ensure_scratch(f, sz.bytes);
     if (st != FQSL_OK) return st;
-    Scratch s = layout((char *)f->scratch, n, lat.allow_rot, true, f32);
+    Scratch s = layout((char *)f->scratch, n, lat.allow_rot, true, f32, m2);
 
     cudaError_t e = cudaMemsetAsync(f->counters, 0, 4 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess && lat.allow_rot) e = cudaMemsetAsync(s.rot_slot, 0, (size_t)n * sizeof(int32_t), stream);
@@ -439,6 +489,7 @@ fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, co
     TraceArgs a{};
     a.f = f->g;
     a.f.rec = p->precision == FQSL_F64 ? f->rec64 : f->rec32;
+    a.f.grad = p->precision == FQSL_F64 ? f->grad64 : f->grad32;
     a.p = dev_params(p);
     a.lat = lat;
     a.rec = s.rec;
@@ -454,6 +505,25 @@ fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, co
         if (e != cudaSuccess) return cuda_fail(e, who);
     }
     mark(f, 0, stream);
+    if (m2) {
+        e = launch_trace_m2(f, p, a, stream);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+        mark(f, 1, stream);
+        mark(f, 2, stream);
+        AssembleArgs g{};
+        g.f = a.f;
+        g.lat = lat;
+        g.rec = s.rec;
+        g.out = *out;
+        g.n = n;
+        g.want_q = 1;
+        e = f32 ? launch_assemble_m2_f32(g, stream) : launch_assemble_m2_f64(g, stream);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+        mark(f, 3, stream);
+        f->timed = f->timing;
+        f->extra_timed = false;
+        return FQSL_OK;
+    }
     e = launch_trace(f, p, a, kSrcLattice, a.nitems, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     mark(f, 1, stream);
@@ -659,6 +729,7 @@ extern "C" fqsl_status fqsl_qmap_plane_static(fqsl_field f, const double origin[
     const char *who = "fqsl_qmap_plane_static";
     fqsl_status st = check_params(f, p, who);
     if (st != FQSL_OK) return st;
+    if (p->method != 1) return fail(FQSL_ERR_UNSUPPORTED, "%s: Method I only", who);
     if (!out) return fail(FQSL_ERR_ARG, "%s: out is NULL", who);
     if (!finite3(origin) || !finite3(u) || !finite3(v)) return fail(FQSL_ERR_ARG, "%s: non-finite plane", who);
     if (nu < 1 || nv < 1) return fail(FQSL_ERR_ARG, "%s: need nu, nv >= 1", who);

@@ -110,7 +110,64 @@ __global__ void __launch_bounds__(256) k_assemble(const AssembleArgs A)
     }
 }
 
+__device__ __forceinline__ double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// Method II (Sec. 2.1, Eq. q_scott with absolute values): at each end the
+// deviation vectors are projected onto the exit face along B, U~ = U -
+// (U.n)/(B.n) B, and Q = |U~1^2 V~2^2 + U~2^2 V~1^2 - 2 (U~1.V~1)(U~2.V~2)|
+// |Bn1 Bn2| / Bn0^2 with Bn0 = |B| at the seed (S0 perpendicular to B).
+__global__ void __launch_bounds__(256) k_assemble_m2(const AssembleArgs A)
+{
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < A.n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const LineRecs &R = A.rec;
+        const unsigned st = R.st[idx];
+        const bool bad = (st & kBad) != 0;
+        double Q = NAN;
+        if (!bad) {
+            double Ut[2][3], Vt[2][3], bn[2];
+            for (int e = 0; e < 2; e++) {
+                const int a = (e == 0 ? R.f1 : R.f2)[idx] >> 1;
+                const double *U = R.dev64 + 12 * idx + 6 * e, *V = U + 3, *B = R.be64 + 6 * idx + 3 * e;
+                bn[e] = B[a];
+                for (int b = 0; b < 3; b++) {
+                    Ut[e][b] = U[b] - U[a] / B[a] * B[b];
+                    Vt[e][b] = V[b] - V[a] / B[a] * B[b];
+                }
+            }
+            const double num = dot3(Ut[0], Ut[0]) * dot3(Vt[1], Vt[1]) + dot3(Ut[1], Ut[1]) * dot3(Vt[0], Vt[0]) -
+                               2.0 * dot3(Ut[0], Vt[0]) * dot3(Ut[1], Vt[1]);
+            const double bn0 = R.bn0[idx];
+            Q = fabs(num) * fabs(bn[0] * bn[1]) / (bn0 * bn0);
+        }
+        const fqsl_out &o = A.out;
+        if (o.Q) o.Q[idx] = Q;
+        if (o.Tw) o.Tw[idx] = bad ? NAN : R.tw[idx];
+        if (o.length) o.length[idx] = bad ? NAN : R.len[idx];
+        if (o.r1)
+            for (int c = 0; c < 3; c++) o.r1[3 * idx + c] = R.r1[3 * idx + c];
+        if (o.r2)
+            for (int c = 0; c < 3; c++) o.r2[3 * idx + c] = R.r2[3 * idx + c];
+        if (o.face1) o.face1[idx] = R.f1[idx];
+        if (o.face2) o.face2[idx] = R.f2[idx];
+        if (o.status) o.status[idx] = (uint8_t)st;
+        if (o.steps) o.steps[idx] = R.steps[idx];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_assemble_m2_f64(const AssembleArgs &a, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long blocks = (a.n + 255) / 256;
+    if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+    if (blocks < 1) blocks = 1;
+    k_assemble_m2<<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_assemble(const AssembleArgs &a, cudaStream_t s)
 {

@@ -126,7 +126,77 @@ __global__ void __launch_bounds__(256) k_assemble_f32(const AssembleArgs A)
     }
 }
 
+// Method II from the FP32 tracer's end deviation vectors (Eq. q_scott), in FP64.
+__global__ void __launch_bounds__(256) k_assemble_m2_f32(const AssembleArgs A)
+{
+    const FieldView &f = A.f;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < A.n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const LineRecs &R = A.rec;
+        const unsigned st = R.st[idx];
+        const bool bad = (st & kBad) != 0;
+        const float *x1 = R.xi1 + 3 * idx, *x2 = R.xi2 + 3 * idx;
+        const int f1 = R.f1[idx], f2 = R.f2[idx];
+        double Q = NAN;
+        if (!bad) {
+            double Ut[2][3], Vt[2][3], bn[2];
+            for (int e = 0; e < 2; e++) {
+                const int a = (e == 0 ? f1 : f2) >> 1;
+                const float *xe = e == 0 ? x1 : x2;
+                float Bf[3], Jf[3];
+                trace::gather(f, xe[0], xe[1], xe[2], Bf, Jf);
+                const double B[3] = {Bf[0], Bf[1], Bf[2]};
+                const float *dv = R.dev32 + 12 * idx + 6 * e;
+                const double U[3] = {dv[0], dv[1], dv[2]}, V[3] = {dv[3], dv[4], dv[5]};
+                bn[e] = B[a];
+                const double ru = U[a] / B[a], rv = V[a] / B[a];
+                for (int b = 0; b < 3; b++) {
+                    Ut[e][b] = U[b] - ru * B[b];
+                    Vt[e][b] = V[b] - rv * B[b];
+                }
+            }
+            auto dot = [](const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
+            const double num = dot(Ut[0], Ut[0]) * dot(Vt[1], Vt[1]) + dot(Ut[1], Ut[1]) * dot(Vt[0], Vt[0]) -
+                               2.0 * dot(Ut[0], Vt[0]) * dot(Ut[1], Vt[1]);
+            const double bn0 = R.bn0[idx];
+            Q = fabs(num) * fabs(bn[0] * bn[1]) / (bn0 * bn0);
+        }
+        const fqsl_out &o = A.out;
+        if (o.Q) o.Q[idx] = Q;
+        if (o.Tw || o.length) {
+            double tw = NAN, len = NAN;
+            if (!bad) {
+                const float4 k0 = R.kacc[2 * idx], k1 = R.kacc[2 * idx + 1];
+                len = ((double)k0.x - (double)k0.y) + ((double)k1.x - (double)k1.y);
+                tw = ((double)k0.z - (double)k0.w) + ((double)k1.z - (double)k1.w);
+            }
+            if (o.Tw) o.Tw[idx] = tw;
+            if (o.length) o.length[idx] = len;
+        }
+        if (o.r1)
+            for (int c = 0; c < 3; c++) o.r1[3 * idx + c] = fma(f.d[c], (double)x1[c], f.o[c]);
+        if (o.r2)
+            for (int c = 0; c < 3; c++) o.r2[3 * idx + c] = fma(f.d[c], (double)x2[c], f.o[c]);
+        if (o.face1) o.face1[idx] = (int8_t)f1;
+        if (o.face2) o.face2[idx] = (int8_t)f2;
+        if (o.status) o.status[idx] = (uint8_t)st;
+        if (o.steps) o.steps[idx] = R.steps[idx];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_assemble_m2_f32(const AssembleArgs &a, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long blocks = (a.n + 255) / 256;
+    if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+    if (blocks < 1) blocks = 1;
+    k_assemble_m2_f32<<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_assemble_f32(const AssembleArgs &a, cudaStream_t s)
 {

@@ -91,7 +91,72 @@ __global__ void __launch_bounds__(256) k_curl_pack32(const float *__restrict__ B
     }
 }
 
+// Component c of B/|B| at a node (0 where |B| = 0), as written.
+template <typename TI>
+__device__ __forceinline__ double bhat(const TI *__restrict__ B, long long q, int c)
+{
+    const double b0 = (double)B[3 * q], b1 = (double)B[3 * q + 1], b2 = (double)B[3 * q + 2];
+    const double m = sqrt(b0 * b0 + b1 * b1 + b2 * b2);
+    const double bc = c == 0 ? b0 : (c == 1 ? b1 : b2);
+    return m > 0 ? bc / m : 0.0;
+}
+
+template <typename TI>
+__device__ __forceinline__ double bhat_diff(const TI *__restrict__ B, int c, long long node, long long stride,
+                                            long long i, long long n, double h)
+{
+    auto F = [&](long long kk) -> double { return bhat(B, node + (kk - i) * stride, c); };
+    if (n == 2) return (F(1) - F(0)) / h;
+    if (i == 0) return (-3.0 * F(0) + 4.0 * F(1) - F(2)) / (2.0 * h);
+    if (i == n - 1) return (3.0 * F(n - 1) - 4.0 * F(n - 2) + F(n - 3)) / (2.0 * h);
+    return (F(i + 1) - F(i - 1)) / (2.0 * h);
+}
+
+// grad(B/|B|) at the nodes for Method II way 1 (Sec. 4, Eq. grad_B): G[a*3+b]
+// = d(B_b/|B|)/dx_a with the stencils of the curl grid.
+template <typename TI>
+__global__ void __launch_bounds__(256) k_gradb_pack(const TI *__restrict__ B, int nx, int ny, int nz, double dx,
+                                                    double dy, double dz, float *__restrict__ g32,
+                                                    double *__restrict__ g64)
+{
+    const long long total = (long long)nx * ny * nz;
+    const long long stride[3] = {1, nx, (long long)nx * ny};
+    const double d[3] = {dx, dy, dz};
+    const long long n[3] = {nx, ny, nz};
+    for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < total;
+         node += (long long)gridDim.x * blockDim.x) {
+        const long long idx[3] = {node % nx, (node / nx) % ny, node / stride[2]};
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) {
+                const double g = bhat_diff(B, b, node, stride[a], idx[a], n[a], d[a]);
+                if (g64) g64[node * 10 + a * 3 + b] = g;
+                if (g32) g32[node * 12 + a * 3 + b] = (float)g;
+            }
+        if (g64) g64[node * 10 + 9] = 0.0;
+        if (g32) g32[node * 12 + 9] = g32[node * 12 + 10] = g32[node * 12 + 11] = 0.f;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_gradb_pack(const void *B, fqsl_dtype bt, const FieldView &g, void *grad32, void *grad64,
+                              cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    long long blocks = (total + 255) / 256;
+    if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+    if (blocks < 1) blocks = 1;
+    if (bt == FQSL_F32)
+        k_gradb_pack<float><<<(unsigned)blocks, 256, 0, s>>>((const float *)B, g.nx, g.ny, g.nz, g.d[0], g.d[1],
+                                                            g.d[2], (float *)grad32, (double *)grad64);
+    else
+        k_gradb_pack<double><<<(unsigned)blocks, 256, 0, s>>>((const double *)B, g.nx, g.ny, g.nz, g.d[0], g.d[1],
+                                                             g.d[2], (float *)grad32, (double *)grad64);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_curl_pack(const void *B, fqsl_dtype bt, const FieldView &g, void *rec32, void *rec64,
                              cudaStream_t s)

@@ -33,6 +33,8 @@ struct FieldView {
     double d[3];  // spacing
     float cmax[3];            // largest cell index per axis, n - 2, as float
     unsigned sy32, sz32;      // FP32 record byte strides along y and z
+    const void *grad;         // grad(B/|B|) node records (Method II way 1) or NULL:
+                              // FP32 48 B {g0..g8, 0, 0, 0}, FP64 80 B {g0..g8, 0}
 };
 
 struct DevParams {
@@ -72,6 +74,9 @@ struct LineRecs {
     double *tw, *len;   // FP64: totals
     float *xi1, *xi2;   // FP32: index-space footpoints, 3 per line
     float4 *kacc;       // FP32: per direction {length sum, its carry, Tw sum, its carry}, 2 per line
+    double *dev64;      // Method II, FP64: U1, V1, U2, V2 (12 per line)
+    double *be64;       // Method II, FP64: B at end 1 and end 2 (6 per line)
+    float *dev32;       // Method II, FP32: U1, V1, U2, V2 (12 per line)
     int8_t *f1, *f2;
     uint8_t *st;
     int32_t *steps;
@@ -84,6 +89,7 @@ constexpr uint8_t kSeedRotated = 4; // S0 rotated (Sec. 4)
 struct SeedPrep {
     float4 *seed;     // {xi_x, xi_y, xi_z, tol^2}
     uint8_t *flags;
+    float4 *fu, *fv;  // Method II: initial deviation vectors U0, V0
 };
 
 struct Queue {
@@ -126,6 +132,15 @@ cudaError_t launch_trace_f32(const TraceArgs &a, int src, int grid, int block, c
 cudaError_t launch_trace_f64(const TraceArgs &a, int src, int grid, int block, cudaStream_t s);
 int trace_blocks_per_sm_f32(int src, bool acc64);
 int trace_blocks_per_sm_f64(int src);
+// Method II tracers (deviation vectors; way 1 = gradient grid, 2 = +-eps)
+cudaError_t launch_trace_dev_f32(const TraceArgs &a, int way, int grid, int block, cudaStream_t s);
+cudaError_t launch_trace_dev_f64(const TraceArgs &a, int way, int grid, int block, cudaStream_t s);
+int trace_dev_blocks_per_sm_f32(int way);
+int trace_dev_blocks_per_sm_f64(int way);
+cudaError_t launch_gradb_pack(const void *B, fqsl_dtype bt, const FieldView &g, void *grad32, void *grad64,
+                              cudaStream_t s);
+cudaError_t launch_assemble_m2_f64(const AssembleArgs &a, cudaStream_t s);
+cudaError_t launch_assemble_m2_f32(const AssembleArgs &a, cudaStream_t s);
 constexpr int kTraceBlock = 128;
 cudaError_t launch_assemble(const AssembleArgs &a, cudaStream_t s);
 cudaError_t launch_assemble_f32(const AssembleArgs &a, cudaStream_t s);

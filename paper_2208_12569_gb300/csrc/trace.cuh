@@ -130,6 +130,7 @@ __device__ __forceinline__ T clampcell(T c, int n)
 // One 32-byte FP32 node record in a single 256-bit read-only load (records are
 // 32-byte aligned: the allocation is, and every record offset is a multiple of
 // 32). Returns Bx, By, Bz, Jx, Jy, Jz.
+#pragma nv_diag_suppress 550  // the two padding floats of the record are loaded and dropped
 __device__ __forceinline__ void load_rec32(const char *p, float &b0, float &b1, float &b2, float &j0, float &j1,
                                            float &j2)
 {
@@ -137,9 +138,8 @@ __device__ __forceinline__ void load_rec32(const char *p, float &b0, float &b1, 
     asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=f"(b0), "=f"(b1), "=f"(b2), "=f"(j0), "=f"(j1), "=f"(j2), "=f"(pad0), "=f"(pad1)
         : "l"(p));
-    (void)pad0;
-    (void)pad1;
 }
+#pragma nv_diag_default 550
 
 // Exact integer value of a float that holds an integer in [0, 2^23): adding
 // 2^23 puts it in the low mantissa bits. (A float -> 64-bit integer conversion
@@ -268,6 +268,117 @@ __device__ __forceinline__ bool rhs(const FieldView &f, const double d[3], doubl
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// Method II: grad(B/|B|) at a point (Sec. 4): way 1 interpolates the node grid
+// of Eq. grad_B trilinearly, way 2 differences B/|B| at xi +- eps e_a.
+// G[a][b] = d(B_b/|B|)/dx_a in physical units. Returns false on a null field.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void gather_grad(const FieldView &f, float x, float y, float z, float G[3][3])
+{
+    const float cx = fminf(fmaxf(floorf(x), 0.f), f.cmax[0]);
+    const float cy = fminf(fmaxf(floorf(y), 0.f), f.cmax[1]);
+    const float cz = fminf(fmaxf(floorf(z), 0.f), f.cmax[2]);
+    const float wx = x - cx, wy = y - cy, wz = z - cz;
+    const float ux = 1.f - wx, uy = 1.f - wy, uz = 1.f - wz;
+    const long long base = ((long long)small_int(cz) * f.ny + small_int(cy)) * f.nx + small_int(cx);
+    const long long sy = f.nx, sz = (long long)f.nx * f.ny;
+    const float4 *g = (const float4 *)f.grad;
+    const float wyz[4] = {uy * uz, wy * uz, uy * wz, wy * wz};
+    float acc[9];
+#pragma unroll
+    for (int c = 0; c < 9; c++) acc[c] = 0.f;
+#pragma unroll
+    for (int qp = 0; qp < 4; qp++)
+#pragma unroll
+        for (int m = 0; m < 2; m++) {
+            const long long node = base + (qp & 1) * sy + (qp >> 1) * sz + m;
+            const float4 r0 = __ldg(g + 3 * node), r1 = __ldg(g + 3 * node + 1), r2 = __ldg(g + 3 * node + 2);
+            const float w = (m ? wx : ux) * wyz[qp];
+            const float v[9] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x};
+#pragma unroll
+            for (int c = 0; c < 9; c++) acc[c] += w * v[c];
+        }
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) G[a][b] = acc[a * 3 + b];
+}
+
+// FP64: Eq. interp term by term on the 9 gradient components
+__device__ __forceinline__ void gather_grad(const FieldView &f, double x, double y, double z, double G[3][3])
+{
+    const double c[3] = {clampcell<double>(floor(x), f.nx), clampcell<double>(floor(y), f.ny),
+                         clampcell<double>(floor(z), f.nz)};
+    const double xi[3] = {x, y, z};
+    double w[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        w[a][0] = (c[a] + 1.0) - xi[a];
+        w[a][1] = 1.0 - w[a][0];
+    }
+    const long long sy = f.nx, sz = (long long)f.nx * f.ny;
+    const long long base = (long long)c[2] * sz + (long long)c[1] * sy + (long long)c[0];
+    const double2 *g = (const double2 *)f.grad;
+    double acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) acc[k] = 0.0;
+#pragma unroll
+    for (int m = 0; m < 2; m++)
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+#pragma unroll
+            for (int p = 0; p < 2; p++) {
+                const double wt = w[0][m] * w[1][q] * w[2][p];
+                const long long node = base + p * sz + q * sy + m;
+                const double2 r0 = __ldg(g + 5 * node), r1 = __ldg(g + 5 * node + 1), r2 = __ldg(g + 5 * node + 2),
+                              r3 = __ldg(g + 5 * node + 3), r4 = __ldg(g + 5 * node + 4);
+                const double v[9] = {r0.x, r0.y, r1.x, r1.y, r2.x, r2.y, r3.x, r3.y, r4.x};
+#pragma unroll
+                for (int k = 0; k < 9; k++) acc[k] += wt * v[k];
+            }
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) G[a][b] = acc[a * 3 + b];
+}
+
+template <typename T>
+__device__ __forceinline__ bool unit_b(const FieldView &f, T x, T y, T z, T bh[3])
+{
+    T B[3], J[3];
+    gather(f, x, y, z, B, J);
+    const T m = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+    if (!(m > (T)0) || !(m < (T)INFINITY)) return false;
+    bh[0] = B[0] / m;
+    bh[1] = B[1] / m;
+    bh[2] = B[2] / m;
+    return true;
+}
+
+template <typename T, int WAY>
+__device__ __forceinline__ bool grad_bhat(const FieldView &f, T eps, T x, T y, T z, T G[3][3])
+{
+    if constexpr (WAY == 1) {
+        gather_grad(f, x, y, z, G);
+        return true;
+    } else {
+        const T p[3] = {x, y, z};
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            T xp[3] = {p[0], p[1], p[2]}, xm[3] = {p[0], p[1], p[2]};
+            xp[a] += eps;
+            xm[a] -= eps;
+            T bp[3], bm[3];
+            ok &= unit_b(f, xp[0], xp[1], xp[2], bp);
+            ok &= unit_b(f, xm[0], xm[1], xm[2], bm);
+#pragma unroll
+            for (int b = 0; b < 3; b++) G[a][b] = (bp[b] - bm[b]) / ((T)2 * eps * (T)f.d[a]);
+        }
+        return ok;
+    }
+}
+
 // fourth root through the correctly rounded square root
 __device__ __forceinline__ float root4(float v) { return sqrtf(sqrtf(v)); }
 __device__ __forceinline__ double root4(double v) { return sqrt(sqrt(v)); }
@@ -346,6 +457,8 @@ struct Lane {
     double l1, tw1;      // totals of end 1
     double ol, otw;      // exiting step: FP64 sums at its end / FP32 its increments
     int steps, st, end, mode, hface, tries, fc0;
+    // Method II: deviation vectors (current, at the seed, at the end of the exiting step)
+    T u[3], v[3], u0[3], v0[3], ou[3], ov[3];
 };
 
 // Length and Tw of the current direction: FP64 sums (ACC, and the FP64
@@ -443,18 +556,42 @@ __device__ __forceinline__ void finish_bad(const TraceArgs &A, const LineRecs &R
     R.steps[L.line] = L.steps;
 }
 
-// A direction reached a face at index position (x, y, z).
-template <typename T, bool ACC>
+// A direction reached a face at index position (x, y, z) with deviation
+// vectors (du, dv) (Method II only).
+template <typename T, bool ACC, int DEV = 0>
 __device__ __forceinline__ bool finish_dir(const TraceArgs &A, const LineRecs &R, Lane<T> &L, T x, T y, T z,
-                                           int face)
+                                           int face, const T *du = nullptr, const T *dv = nullptr)
 {
     const FieldView &f = A.f;
+    if constexpr (DEV != 0) {
+        if constexpr (sizeof(T) == 8) {
+            double *d = R.dev64 + 12 * L.line + 6 * L.end;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                d[c] = du[c];
+                d[3 + c] = dv[c];
+            }
+        } else {
+            float *d = R.dev32 + 12 * L.line + 6 * L.end;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                d[c] = du[c];
+                d[3 + c] = dv[c];
+            }
+        }
+    }
     if constexpr (sizeof(T) == 8) {
         double B[3];
         b_at<T>(f, (double)x, (double)y, (double)z, B);
         const int ax = face >> 1;
         write_end(A, R, L, L.end, to_phys(f.o[0], f.d[0], (double)x), to_phys(f.o[1], f.d[1], (double)y),
                   to_phys(f.o[2], f.d[2], (double)z), face, sel3<double>(ax, B[0], B[1], B[2]));
+        if (R.be64) {
+            double *be = R.be64 + 6 * L.line + 3 * L.end;
+            be[0] = B[0];
+            be[1] = B[1];
+            be[2] = B[2];
+        }
     } else {
         write_end32(R, L.line, L.end, (float)x, (float)y, (float)z, face);
         if (R.kacc) {
@@ -478,6 +615,13 @@ __device__ __forceinline__ bool finish_dir(const TraceArgs &A, const LineRecs &R
         L.x = L.sx;
         L.y = L.sy;
         L.z = L.sz;
+        if constexpr (DEV != 0) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                L.u[c] = L.u0[c];
+                L.v[c] = L.v0[c];
+            }
+        }
         L.h = (T)A.p.h0;
         L.mode = 0;
         acc_reset<T, ACC>(L);
@@ -569,7 +713,7 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
 }
 
 // Lattice seed: frame, tolerance and rotation decision (Sec. 4).
-template <typename T, bool ACC>
+template <typename T, bool ACC, int DEV = 0>
 __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, long long item)
 {
     constexpr bool kF64 = sizeof(T) == 8;
@@ -606,6 +750,15 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
         L.mode = 0;
         acc_reset<T, ACC>(L);
         L.h = (T)A.p.h0;
+        if constexpr (DEV != 0) {
+            const float4 fu = A.prep.fu[idx], fv = A.prep.fv[idx];
+            L.u[0] = L.u0[0] = fu.x;
+            L.u[1] = L.u0[1] = fu.y;
+            L.u[2] = L.u0[2] = fu.z;
+            L.v[0] = L.v0[0] = fv.x;
+            L.v[1] = L.v0[1] = fv.y;
+            L.v[2] = L.v0[2] = fv.z;
+        }
         return true;
     }
     double xi[3];
@@ -662,7 +815,23 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
         }
     }
     R.bn0[idx] = bn0;
-    return start_line<T, ACC>(A, R, L, xi, G.n0, tol, st0);
+    const bool started = start_line<T, ACC>(A, R, L, xi, G.n0, tol, st0);
+    if constexpr (DEV != 0) {
+        if (started) {
+            // S0 perpendicular to B: U0, V0 = the frame of B/|B| at the seed (Sec. 4)
+            double B0[3], u[3], v[3];
+            b_at<T>(f, xi[0], xi[1], xi[2], B0);
+            const double nB = sqrt(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
+            const double bh[3] = {B0[0] / nB, B0[1] / nB, B0[2] / nB};
+            perp_frame(bh, u, v);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                L.u[c] = L.u0[c] = (T)u[c];
+                L.v[c] = L.v0[c] = (T)v[c];
+            }
+        }
+    }
+    return started;
 }
 
 // Rotated extra line q (0: +u, 1: -u, 2: +v, 3: -v) of rotated slot s (Sec. 4).
@@ -714,7 +883,9 @@ __device__ __forceinline__ bool init_list(const TraceArgs &A, Lane<T> &L, long l
 // ---------------------------------------------------------------------------
 // ACC: FP64 sums for the error norm and for length/Tw (always true for the
 // FP64 tracer); false: FP32 error norm and compensated FP32 sums.
-template <typename T, int SRC, bool ACC>
+// DEV: 0 = positions only (Method I, twist); 1, 2 = Method II deviation
+// vectors with grad(B/|B|) by way 1 or way 2 (lattice source only).
+template <typename T, int SRC, bool ACC, int DEV = 0>
 __device__ __forceinline__ void trace_body(const TraceArgs &A)
 {
     constexpr unsigned FULL = 0xffffffffu;
@@ -761,7 +932,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             const int rank = __popc(idle & lt_mask);
             if (!active && rank < avail) {
                 const long long item = ck_cur + rank;
-                if (SRC == kSrcLattice) active = init_lattice<T, ACC>(A, L, item);
+                if (SRC == kSrcLattice) active = init_lattice<T, ACC, DEV>(A, L, item);
                 else if (SRC == kSrcExtra) active = init_extra<T, ACC>(A, L, item);
                 else active = init_list<T, ACC>(A, L, item);
             }
@@ -796,8 +967,11 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
         }
         L.steps++;
 
+        constexpr int NS = DEV ? 11 : 5;  // xi (3), length, Tw [, U (3), V (3)]
         T k0[5], k1[5], k2[5];  // position derivatives of stages 1..5
+        T kd[DEV ? 5 : 1][6];   // deviation derivatives of stages 1..5 (Method II)
         T a4[3] = {0, 0, 0}, a5[3] = {0, 0, 0};  // FP64: 5th-order sums; FP32: 5th - 4th
+        T ad[6] = {0, 0, 0, 0, 0, 0};           // Method II: 4th-order sums of U, V
         T l4 = 0, tw4 = 0;
         int fail = 0;  // first failing stage: 1 null field, 2 grazing exit step
 #pragma unroll
@@ -813,8 +987,33 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             px = L.x + hh * px;
             py = L.y + hh * py;
             pz = L.z + hh * pz;
-            T o[5];
-            const bool ok = rhs(f, dd, sgn, px, py, pz, o);
+            T o[NS];
+            bool ok = rhs(f, dd, sgn, px, py, pz, o);
+            if constexpr (DEV != 0) {
+                // stage deviation vectors and Eq. rb2: dU/dtau = sigma (ds/dtau) (U . grad)(B/|B|)
+                T us[6];
+#pragma unroll
+                for (int c = 0; c < 6; c++) {
+                    T acc = 0;
+#pragma unroll
+                    for (int r = 0; r < s; r++) acc += Fehlberg<T>::a(s, r) * kd[r][c];
+                    us[c] = (c < 3 ? L.u[c] : L.v[c - 3]) + hh * acc;
+                }
+                T G[3][3];
+                ok = grad_bhat<T, DEV>(f, (T)A.p.eps2, px, py, pz, G) && ok;
+                const T sdl = sgn * o[3];
+#pragma unroll
+                for (int b = 0; b < 3; b++) {
+                    T su = 0, sv = 0;
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        su += us[a] * G[a][b];
+                        sv += us[3 + a] * G[a][b];
+                    }
+                    o[5 + b] = sdl * su;
+                    o[8 + b] = sdl * sv;
+                }
+            }
             if (!ok && !fail) fail = 1;
             if (henon) {
                 const T fa = sel3<T>(hax, o[0], o[1], o[2]);
@@ -823,17 +1022,25 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
                 if (kF64) {
                     const T den = bad ? (T)1 : fa;
 #pragma unroll
-                    for (int c = 0; c < 5; c++) o[c] = o[c] / den;
+                    for (int c = 0; c < NS; c++) o[c] = o[c] / den;
                 } else {
                     const T inv = bad ? (T)0 : (T)1 / fa;
 #pragma unroll
-                    for (int c = 0; c < 5; c++) o[c] *= inv;
+                    for (int c = 0; c < NS; c++) o[c] *= inv;
                 }
             }
             if (s < 5) {
                 k0[s] = o[0];
                 k1[s] = o[1];
                 k2[s] = o[2];
+                if constexpr (DEV != 0) {
+#pragma unroll
+                    for (int c = 0; c < 6; c++) kd[s][c] = o[5 + c];
+                }
+            }
+            if constexpr (DEV != 0) {
+#pragma unroll
+                for (int c = 0; c < 6; c++) ad[c] += Fehlberg<T>::b4(s) * o[5 + c];
             }
             const T b = Fehlberg<T>::b4(s);
             const T e = kF64 ? Fehlberg<T>::b5(s) : Fehlberg<T>::e(s);
@@ -900,6 +1107,13 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
                 L.x = nx;
                 L.y = ny;
                 L.z = nz;
+                if constexpr (DEV != 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        L.u[c] = L.u[c] + hh * ad[c];
+                        L.v[c] = L.v[c] + hh * ad[3 + c];
+                    }
+                }
                 acc_add<T, ACC>(L, hh * l4, hh * tw4);
                 L.h = hn;
                 continue;
@@ -931,6 +1145,13 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             L.ox = nx;
             L.oy = ny;
             L.oz = nz;
+            if constexpr (DEV != 0) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    L.ou[c] = L.u[c] + hh * ad[c];
+                    L.ov[c] = L.v[c] + hh * ad[3 + c];
+                }
+            }
             if (ACC) {
                 L.ol = L.lacc + (double)(hh * l4);
                 L.otw = L.twacc + (double)(hh * tw4);
@@ -967,7 +1188,15 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
                 acc_add<T, ACC>(L, (T)((double)L.t0 * L.ol), (T)((double)L.t0 * L.otw));
             }
             L.st |= FQSL_LINE_CHORD;
-            active = finish_dir<T, ACC>(A, R, L, ex, ey, ez, L.fc0);
+            T eu[3], ev[3];
+            if constexpr (DEV != 0) {
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    eu[c] = L.u[c] + L.t0 * (L.ou[c] - L.u[c]);
+                    ev[c] = L.v[c] + L.t0 * (L.ov[c] - L.v[c]);
+                }
+            }
+            active = finish_dir<T, ACC, DEV>(A, R, L, ex, ey, ez, L.fc0, eu, ev);
             waiting = active && A.p.sync_dirs;
             continue;
         }
@@ -997,7 +1226,15 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             tz = fmin(fmax(tz, (T)0), (T)(f.nz - 1));
         }
         acc_add<T, ACC>(L, hh * l4, hh * tw4);
-        active = finish_dir<T, ACC>(A, R, L, tx, ty, tz, L.hface);
+        T eu[3], ev[3];
+        if constexpr (DEV != 0) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                eu[c] = L.u[c] + hh * ad[c];
+                ev[c] = L.v[c] + hh * ad[3 + c];
+            }
+        }
+        active = finish_dir<T, ACC, DEV>(A, R, L, tx, ty, tz, L.hface, eu, ev);
         waiting = active && A.p.sync_dirs;
     }
 }
@@ -1062,6 +1299,23 @@ __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
         }
     }
     R.bn0[idx] = bn0;
+    if (A.prep.fu) {
+        // Method II: S0 perpendicular to B, U0, V0 its frame (Sec. 4)
+        float4 fu = make_float4(0.f, 0.f, 0.f, 0.f), fv = fu;
+        if (!bad) {
+            float B0[3], J0[3];
+            gather(f, x, y, z, B0, J0);
+            const double b0 = B0[0], b1 = B0[1], b2 = B0[2];
+            const double nB = sqrt(b0 * b0 + b1 * b1 + b2 * b2);
+            const double bh[3] = {b0 / nB, b1 / nB, b2 / nB};
+            double u[3], v[3];
+            perp_frame(bh, u, v);
+            fu = make_float4((float)u[0], (float)u[1], (float)u[2], 0.f);
+            fv = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+        }
+        A.prep.fu[idx] = fu;
+        A.prep.fv[idx] = fv;
+    }
     if (bad) {
         fl |= kSeedDone;
         write_end32(R, idx, 0, x, y, z, -1);

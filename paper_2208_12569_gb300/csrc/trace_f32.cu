@@ -79,3 +79,29 @@ cudaError_t launch_seed_prep_f32(const TraceArgs &a, long long n, cudaStream_t s
 }
 
 }  // namespace fqsl
+
+namespace fqsl {
+namespace {
+template <int WAY>
+__global__ void __launch_bounds__(kBlock) k_trace_dev_f32(const TraceArgs A)
+{
+    trace::trace_body<float, kSrcLattice, false, WAY>(A);
+}
+}  // namespace
+
+cudaError_t launch_trace_dev_f32(const TraceArgs &a, int way, int grid, int block, cudaStream_t s)
+{
+    if (block != kBlock) return cudaErrorInvalidValue;
+    if (way == 1) k_trace_dev_f32<1><<<grid, block, 0, s>>>(a);
+    else k_trace_dev_f32<2><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int trace_dev_blocks_per_sm_f32(int way)
+{
+    int b = 0;
+    if (way == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_dev_f32<1>, kBlock, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_dev_f32<2>, kBlock, 0);
+    return b > 0 ? b : 1;
+}
+}  // namespace fqsl

@@ -32,3 +32,29 @@ int trace_blocks_per_sm_f64(int src)
 }
 
 }  // namespace fqsl
+
+namespace fqsl {
+namespace {
+template <int WAY>
+__global__ void __launch_bounds__(kBlock) k_trace_dev_f64(const TraceArgs A)
+{
+    trace::trace_body<double, kSrcLattice, true, WAY>(A);
+}
+}  // namespace
+
+cudaError_t launch_trace_dev_f64(const TraceArgs &a, int way, int grid, int block, cudaStream_t s)
+{
+    if (block != kBlock) return cudaErrorInvalidValue;
+    if (way == 1) k_trace_dev_f64<1><<<grid, block, 0, s>>>(a);
+    else k_trace_dev_f64<2><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int trace_dev_blocks_per_sm_f64(int way)
+{
+    int b = 0;
+    if (way == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_dev_f64<1>, kBlock, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_dev_f64<2>, kBlock, 0);
+    return b > 0 ? b : 1;
+}
+}  // namespace fqsl

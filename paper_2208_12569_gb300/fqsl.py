@@ -16,7 +16,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfqsl.so")
 
 F32, F64, F32_ACC64 = 0, 1, 2
-PACK_F32, PACK_F64 = 1, 2
+PACK_F32, PACK_F64, PACK_GRADB = 1, 2, 4
 LINE_MAXSTEPS, LINE_NULL_B, LINE_STALL, LINE_MIXED, LINE_OUTSIDE, LINE_ROTATED, LINE_CHORD = 1, 2, 4, 8, 16, 32, 64
 LINE_BAD = LINE_MAXSTEPS | LINE_NULL_B | LINE_OUTSIDE
 EXPORTS = ("fqsl_params_default", "fqsl_version", "fqsl_last_error", "fqsl_field_create", "fqsl_field_destroy",
@@ -110,7 +110,8 @@ def _stream(stream):
 
 class Field:
     """A field handle: B (torch CUDA tensor (nz, ny, nx, 3), float32 or float64)
-    packed with its curl into node records (pack: 'f32', 'f64' or both)."""
+    packed with its curl into node records (pack: 'f32', 'f64' or both, plus
+    'gradb' for the grad(B/|B|) grid of Method II way 1)."""
 
     def __init__(self, B: torch.Tensor, origin, spacing, pack=("f32", "f64"), stream=None):
         if not (isinstance(B, torch.Tensor) and B.is_cuda and B.dim() == 4 and B.shape[-1] == 3):
@@ -119,7 +120,8 @@ class Field:
             raise ValueError("B must be float32 or float64")
         B = B.contiguous()
         nz, ny, nx, _ = B.shape
-        flags = (PACK_F32 if "f32" in pack else 0) | (PACK_F64 if "f64" in pack else 0)
+        flags = ((PACK_F32 if "f32" in pack else 0) | (PACK_F64 if "f64" in pack else 0) |
+                 (PACK_GRADB if "gradb" in pack else 0))
         h = C.c_void_p()
         _check(_lib.fqsl_field_create(C.c_void_p(B.data_ptr()), F32 if B.dtype == torch.float32 else F64, nx, ny,
                                       nz, _vec3(origin), _vec3(spacing), flags, _stream(stream), C.byref(h)))

@@ -224,3 +224,74 @@ def test_c2_full_size_sampled_parity(fq, oracle_lib):
     assert np.mean(g32s["face2"] == r["face2"]) > 0.98
     rel = q_rel(g32s, r)
     assert np.median(rel[np.isfinite(rel)]) < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# Method II (deviation vectors, Sec. 2.1 Eqs. rb2, q_scott; S0 perpendicular to
+# B, Sec. 4), both ways of grad(B/|B|)
+# ---------------------------------------------------------------------------
+def _field_m2(fq, B, grid):
+    return fq.Field(torch.from_numpy(np.ascontiguousarray(B)).cuda(), grid.origin, grid.spacing,
+                    pack=("f32", "f64", "gradb"))
+
+
+@pytest.mark.parametrize("way", [1, 2])
+@pytest.mark.parametrize("kind,z", [("hyperbolic", 0.0), ("shear", 0.5), ("rotation", 0.0)])
+def test_method2_analytic_fp64_bitwise(fq, oracle_lib, kind, z, way):
+    B = synth.analytic_cube(kind)
+    field = _field_m2(fq, B, G1)
+    d = 2.0 / 64
+    args = ((-1.0, -1.0, z), (d, 0, 0), (0, d, 0), 64, 64)
+    g = _gpu_plane(fq, field, *args, precision="f64", method=2, gradb_way=way, tol=1e-9)
+    r = oracle.plane(B, G1, *args, oracle.params(method=2, way=way, tol=1e-9))
+    assert_fp64_parity(g, r)
+    assert_bitwise(g, r)
+
+
+@pytest.mark.parametrize("way", [1, 2])
+def test_method2_monopole_fp64_bitwise_and_fp32(fq, oracle_lib, mono, way):
+    B, grid = mono
+    field = _field_m2(fq, B, grid)
+    nu, nv = 61, 43
+    args = ((0.0, 0.0, 0.0), (63.0 / nu, 0, 0), (0, 55.0 / nv, 0), nu, nv)
+    g = _gpu_plane(fq, field, *args, precision="f64", method=2, gradb_way=way)
+    r = oracle.plane(B.astype(np.float64), grid, *args, oracle.params(method=2, way=way))
+    assert_fp64_parity(g, r)
+    assert_bitwise(g, r)
+    g32 = _gpu_plane(fq, field, *args, precision="f32", method=2, gradb_way=way)
+    assert np.mean(g32["face2"] == r["face2"]) > 0.99
+    rel = q_rel(g32, r)
+    assert np.median(rel[np.isfinite(rel)]) < 1e-3
+
+
+def test_method2_closed_form_on_gpu(fq, oracle_lib):
+    """Deviation vectors carry no finite-difference error: on B=(x,-y,1) the
+    top-exit Q is e^2 + e^-2 (way 2) on both precisions."""
+    B = synth.analytic_cube("hyperbolic")
+    field = _field_m2(fq, B, G1)
+    X, Y = np.meshgrid(-1 + (np.arange(64) + 0.5) / 32, -1 + (np.arange(64) + 0.5) / 32, indexing="xy")
+    X = X.ravel()
+    top = np.abs(X) < 1 / math.e - 1e-3
+    e2 = math.e ** 2 + math.e ** -2
+    for prec, tol, bound in (("f64", 1e-10, 1e-8), ("f32", 1e-6, 2e-3)):
+        g = _gpu_plane(fq, field, (-1.0, -1.0, 0.0), (1 / 32, 0, 0), (0, 1 / 32, 0), 64, 64, precision=prec,
+                       method=2, gradb_way=2, tol=tol)
+        assert np.max(np.abs(g["Q"][top] / e2 - 1)) < bound
+
+
+def test_method2_volume_fp64_bitwise(fq, oracle_lib, mono):
+    B, grid = mono
+    field = _field_m2(fq, B, grid)
+    step = (63.0 / 12, 55.0 / 10, 31.0 / 4)
+    g = to_np(fq.qmap_volume(field, (0.0, 0.0, 0.0), step, 12, 10, 4, fq.params(precision="f64", method=2)))
+    field.check()
+    r = oracle.qmap(B.astype(np.float64), grid, (0.0, 0.0, 0.0), (step[0], 0, 0), (0, step[1], 0), (0, 0, step[2]),
+                    (12, 10, 4), oracle.params(method=2))
+    assert_bitwise(g, r)
+
+
+def test_method2_way1_needs_gradient_grid(fq):
+    field = _field(fq, synth.analytic_cube("uniform"), G1)
+    with pytest.raises(fq.FqslError) as ei:
+        fq.qmap_plane(field, (-1, -1, 0), (0.1, 0, 0), (0, 0.1, 0), 4, 4, fq.params(method=2, gradb_way=1))
+    assert ei.value.status == 5
