@@ -292,6 +292,25 @@ def main():
                               "kernels_ms": {"trace_f32": float(np.mean([k[0] for k in kern32]))},
                               "config": {"workload": WORKLOAD}, "partial": "only-f32"}), flush=True)
         return
+    # Method II (deviation vectors) on the same map, both ways of grad(B/|B|)
+    fieldg = fq.Field(Bd, grid.origin, grid.spacing, pack=("f32", "gradb"))
+    m2 = {}
+    for way in (1, 2):
+        pm2 = fq.params(precision="f32", tol=TOL, method=2, gradb_way=way)
+        fq.qmap_plane(fieldg, (0.0, 0.0, 0.0), u, v, NU, NV, pm2, out=out)
+        torch.cuda.synchronize()
+        tms = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fq.qmap_plane(fieldg, (0.0, 0.0, 0.0), u, v, NU, NV, pm2, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tms.append(e0.elapsed_time(e1))
+        m2["way%d" % way] = {"value": n / (float(np.mean(tms)) / 1000.0), "unit": "Q+Tw values/s",
+                             "ms_per_step": float(np.mean(tms))}
+    fieldg.close()
     step(pacc)
     torch.cuda.synchronize()
     msacc, kernacc = timed(pacc, args.steps)
@@ -351,6 +370,7 @@ def main():
                           "ms_per_step": float(np.mean(msacc)),
                           "trace_ms": float(np.mean([k[0] for k in kernacc])),
                           "note": "error norm and length/Tw sums accumulated in FP64 every step"},
+            "method2_f32": dict(m2, note="deviation vectors (Method II), tol = tol_perp, same map"),
             "fp64": {"value": value64, "unit": "Q+Tw values/s", "ms_per_step": float(np.mean(ms64)),
                      "trace_ms": float(np.mean([k[0] for k in kern64])),
                      "speedup_fp32_over_fp64": value / ws / value64},
