@@ -209,6 +209,83 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_volume(args):
+    """Large volume: 1024x1024x512 FP32 monopole cube (64 sources); Q and Tw on
+    the 512x512x256 cell-centred seed volume spanning the cube (every z-layer
+    its own S0) and on a 4096x4096 z=0 map; FP32 and FP64 tracing of the same
+    cube; error against the oracle on a seeded 1% sample of the volume."""
+    import torch
+
+    import __graft_entry__
+    import oracle
+    import synth
+
+    __graft_entry__._builder().build()
+    import paper_2208_12569_gb300 as fq
+
+    dev = torch.device("cuda", 0)
+    n = (1024, 1024, 512)
+    t0 = time.perf_counter()
+    Bd, grid, _ = synth.large_monopole(n=n, device=dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    vol = (512, 512, 256)
+    step = tuple((n[a] - 1.0) / vol[a] for a in range(3))
+    plane = (4096, 4096)
+    u = ((n[0] - 1.0) / plane[0], 0.0, 0.0)
+    v = (0.0, (n[1] - 1.0) / plane[1], 0.0)
+    res = {}
+    outs = {}
+    for prec in ("f32", "f64"):
+        field = fq.Field(Bd, grid.origin, grid.spacing, pack=(prec,))
+        field.set_timing(True)
+        p = fq.params(precision=prec, tol=TOL)
+        nv = vol[0] * vol[1] * vol[2]
+        out = fq.alloc_out(nv, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fq.qmap_volume(field, (0.0, 0.0, 0.0), step, *vol, p, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        field.check()
+        ms_v = e0.elapsed_time(e1)
+        kern = field.times()
+        outs[prec] = {k: t.cpu().numpy() for k, t in out.items() if t is not None}
+        steps_total = float(outs[prec]["steps"].astype(np.int64).sum())
+        del out
+        outp = fq.alloc_out(plane[0] * plane[1], device=dev)
+        e0.record()
+        fq.qmap_plane(field, (0.0, 0.0, 0.0), u, v, *plane, p, out=outp)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_p = e0.elapsed_time(e1)
+        del outp
+        field.close()
+        res[prec] = {"volume": {"value": nv / (ms_v / 1000.0), "ms": ms_v, "kernels_ms": kern,
+                                "mean_trials_per_line": steps_total / nv},
+                     "plane_4096": {"value": plane[0] * plane[1] / (ms_p / 1000.0), "ms": ms_p}}
+        torch.cuda.empty_cache()
+    # oracle on a 1% seeded sample of the volume
+    nvol = vol[0] * vol[1] * vol[2]
+    sample = np.sort(np.random.default_rng(19).choice(nvol, nvol // 100, replace=False))
+    B64 = Bd.cpu().numpy().astype(np.float64)
+    del Bd
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    ref = oracle.qmap(B64, grid, (0.0, 0.0, 0.0), (step[0], 0, 0), (0, step[1], 0), (0, 0, step[2]), vol,
+                      oracle.params(tol=TOL), sample=sample)
+    ora_s = time.perf_counter() - t0
+    line = {"metric": METRIC, "workload": "large_volume", "unit": "Q+Tw values/s",
+            "config": {"workload": "monopole64_1024x1024x512_f32_volume512x512x256_plane4096x4096_methodI",
+                       "tol_perp": TOL},
+            "value": res["f32"]["volume"]["value"], "f32": res["f32"], "f64": res["f64"],
+            "error_vs_oracle": {"f32": err_stats(outs["f32"], ref, sample), "f64": err_stats(outs["f64"], ref, sample)},
+            "cpu_baseline": {"value": len(sample) / ora_s, "unit": "Q+Tw values/s", "cores": oracle.max_threads(),
+                             "kind": "oracle", "sample": "%d seeded-random seeds of the volume (1%%)" % len(sample)},
+            "generation_s": gen_s}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,9 +296,14 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--only-f32", action="store_true",
                     help="time only the FP32 map (no FP64, e2e or CPU legs); used for ncu captures")
+    ap.add_argument("--workload", default="plane", choices=["plane", "volume"],
+                    help="plane: the benchmark line; volume: the large-volume configuration")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "volume":
+        run_volume(args)
         return
 
     import torch

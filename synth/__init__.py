@@ -19,4 +19,5 @@ from .fields import (  # noqa: F401
     batch_specs,
     C1_GRID,
     c2_monopole,
+    large_monopole,
 )

@@ -176,6 +176,16 @@ def c2_monopole(seed: int = 2208, n=(256, 256, 128), count: int = 24, dtype=np.f
     return monopole_cube(grid, ch, dtype=dtype, device=device), grid, ch
 
 
+def large_monopole(seed: int = 2208, n=(1024, 1024, 512), count: int = 64, device=None):
+    """The large-volume workload: ``count`` buried monopoles (depths 4..16
+    cells) on an FP32 cube of ``n`` nodes with unit spacing. Sampled on
+    ``device`` (torch) when given. Returns (B, grid, charges)."""
+    grid = Grid(tuple(n), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    rng = np.random.default_rng(seed)
+    ch = random_charges(rng, count, ((0.0, n[0] - 1.0), (0.0, n[1] - 1.0)))
+    return monopole_cube(grid, ch, dtype=np.float32, device=device), grid, ch
+
+
 def quadrupole_charges():
     """The four unit charges of the paper's quadrupole (Sec. 3.2, Eq. quadrapole):
     +1, -1, +1, -1 at x = -1.5, -0.5, 0.5, 1.5, y = 0, z = -0.5."""
