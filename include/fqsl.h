@@ -201,6 +201,37 @@ FQSL_API fqsl_status fqsl_twist(fqsl_field field, const double *seeds_dev, long 
 FQSL_API fqsl_status fqsl_field_set_timing(fqsl_field field, int enable);
 FQSL_API fqsl_status fqsl_field_times(fqsl_field field, float ms[3]);
 
+/* One seed plane of a batch: seed(i,j) = origin + (i+1/2) u + (j+1/2) v as in
+ * fqsl_qmap_plane. */
+typedef struct {
+    double origin[3], u[3], v[3];
+    long long nu, nv;
+} fqsl_plane;
+
+typedef struct fqsl_batch_s *fqsl_batch;
+
+/* A batch plan: n (field, plane, outputs) entries of uneven sizes mapped
+ * together (Method I; the paper has no counterpart, it maps one plane at a
+ * time). Every entry computes exactly what fqsl_qmap_plane computes for it.
+ * Creation validates the entries like fqsl_qmap_plane, allocates the scratch
+ * of all entries and uploads the entry descriptors (it synchronises the
+ * device). fields must share the current device and be packed in
+ * params->precision; outs[k] receives entry k's nu*nv results and must stay
+ * valid for the plan's lifetime. Errors: FQSL_ERR_ARG, FQSL_ERR_UNSUPPORTED,
+ * FQSL_ERR_OOM, FQSL_ERR_CUDA. */
+FQSL_API fqsl_status fqsl_batch_create(const fqsl_field *fields, const fqsl_plane *planes, const fqsl_out *outs,
+                                       int n, const fqsl_params *params, fqsl_batch *out);
+
+/* Run a batch plan on cuda_stream: one seed pre-pass (FP32), one persistent
+ * tracer launch over the work items of all entries (a device counter hands
+ * out 8x4-seed tiles of any entry), one launch for the rotated-S0 extra lines
+ * of all entries (if any plane is interior) and one assembly launch. No
+ * allocation and no host synchronisation happen here. */
+FQSL_API fqsl_status fqsl_batch_run(fqsl_batch batch, void *cuda_stream);
+
+/* Release a batch plan (synchronises the device; the fields stay). */
+FQSL_API fqsl_status fqsl_batch_destroy(fqsl_batch batch);
+
 /* Largest nu*nv accepted by fqsl_qmap_plane_static. */
 #define FQSL_STATIC_MAX_SEEDS 65536
 

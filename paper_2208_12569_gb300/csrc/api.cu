@@ -8,6 +8,7 @@
 
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "fqsl_internal.cuh"
 
@@ -140,6 +141,7 @@ fqsl_status fqsl_field_create(const void *B_dev, fqsl_dtype b_dtype, long long n
         f->g.o[a] = origin[a];
         f->g.d[a] = spacing[a];
     }
+    for (int a = 0; a < 3; a++) f->g.rd[a] = (float)(1.0 / spacing[a]);
     f->g.cmax[0] = (float)(nx - 2);
     f->g.cmax[1] = (float)(ny - 2);
     f->g.cmax[2] = (float)(nz - 2);
@@ -830,5 +832,250 @@ extern "C" fqsl_status fqsl_qmap_plane_static(fqsl_field f, const double origin[
     g.want_q = 1;
     e = f32 ? launch_assemble_f32(g, stream) : launch_assemble(g, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
+    return FQSL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+struct fqsl_batch_s {
+    int nent = 0;
+    int sms = 0;
+    fqsl_params params{};
+    long long total_seeds = 0, total_items = 0;
+    bool any_rot = false;
+    void *mem = nullptr;  // scratch of all entries, descriptors and prefixes
+    TraceArgs *d_desc = nullptr;
+    AssembleArgs *d_adesc = nullptr;
+    long long *d_ibase = nullptr, *d_nbase = nullptr, *d_xbase = nullptr;
+    unsigned long long *d_heads = nullptr;
+    unsigned *d_rot_counts = nullptr;
+    int32_t *d_rot_slots = nullptr;
+    size_t rot_slot_bytes = 0;
+    int grid = 0;
+};
+
+namespace {
+
+// Lattice of one plane entry (the checks of fqsl_qmap_plane).
+fqsl_status plane_lattice(const fqsl_field f, const fqsl_plane &pl, const fqsl_params *p, Lattice &lat,
+                          const char *who)
+{
+    const double *origin = pl.origin, *u = pl.u, *v = pl.v;
+    const long long nu = pl.nu, nv = pl.nv;
+    if (!finite3(origin) || !finite3(u) || !finite3(v)) return fail(FQSL_ERR_ARG, "%s: non-finite plane", who);
+    if (nu < 1 || nv < 1 || nu * nv > (1LL << 31) - 1) return fail(FQSL_ERR_ARG, "%s: need 1 <= nu*nv < 2^31", who);
+    double n0[3];
+    cross(u, v, n0);
+    const double nn = sqrt(n0[0] * n0[0] + n0[1] * n0[1] + n0[2] * n0[2]);
+    const double nuu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const double nvv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (!(nuu > 0) || !(nvv > 0) || !(nn > 0)) return fail(FQSL_ERR_ARG, "%s: u and v must span a plane", who);
+    if (fabs(u[0] * v[0] + u[1] * v[1] + u[2] * v[2]) > 1e-12 * nuu * nvv)
+        return fail(FQSL_ERR_ARG, "%s: u and v must be orthogonal", who);
+    lat = Lattice{};
+    for (int a = 0; a < 3; a++) {
+        lat.o[a] = origin[a];
+        lat.a1[a] = u[a];
+        lat.a2[a] = v[a];
+        lat.a3[a] = 0.0;
+        lat.n0[a] = n0[a] / nn;
+    }
+    lat.n1 = nu;
+    lat.n2 = nv;
+    lat.n3 = 1;
+    lat.du = nuu;
+    lat.dv = nvv;
+    lat.drot = fmin(nuu, nvv);
+    int zeros = 0, axis = -1;
+    for (int a = 0; a < 3; a++) {
+        if (lat.n0[a] == 0.0) zeros++;
+        else axis = a;
+    }
+    lat.normal_axis = zeros == 2 ? axis : -1;
+    bool face_plane = false;
+    if (lat.normal_axis >= 0) {
+        const int a = lat.normal_axis;
+        const int na = a == 0 ? f->g.nx : (a == 1 ? f->g.ny : f->g.nz);
+        const double xi = (origin[a] - f->g.o[a]) / f->g.d[a];
+        face_plane = (xi == 0.0) || (xi == (double)(na - 1));
+    }
+    index_lattice(f, lat);
+    lat.tiles_u = (lat.n1 + kTileU - 1) / kTileU;
+    lat.tiles_v = (lat.n2 + kTileV - 1) / kTileV;
+    lat.allow_rot = (p->method == 1 && !face_plane) ? 1 : 0;
+    return FQSL_OK;
+}
+
+void batch_free(fqsl_batch b)
+{
+    if (!b) return;
+    cudaFree(b->mem);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" fqsl_status fqsl_batch_create(const fqsl_field *fields, const fqsl_plane *planes, const fqsl_out *outs,
+                                         int n, const fqsl_params *p, fqsl_batch *out)
+{
+    g_err.clear();
+    const char *who = "fqsl_batch_create";
+    if (!out) return fail(FQSL_ERR_ARG, "%s: out is NULL", who);
+    *out = nullptr;
+    if (!fields || !planes || !outs || n < 1) return fail(FQSL_ERR_ARG, "%s: need n >= 1 fields, planes, outs", who);
+    if (!p) return fail(FQSL_ERR_ARG, "%s: NULL params", who);
+    if (p->method != 1) return fail(FQSL_ERR_UNSUPPORTED, "%s: batches run Method I", who);
+    const bool f32 = p->precision != FQSL_F64;
+    std::vector<Lattice> lats(n);
+    std::vector<size_t> off(n);
+    size_t bytes = 0;
+    fqsl_batch b = new (std::nothrow) fqsl_batch_s();
+    if (!b) return fail(FQSL_ERR_OOM, "%s: host allocation", who);
+    b->nent = n;
+    b->params = *p;
+    std::vector<long long> ibase(n + 1), nbase(n + 1);
+    for (int k = 0; k < n; k++) {
+        fqsl_status st = check_params(fields[k], p, who);
+        if (st != FQSL_OK) {
+            delete b;
+            return st;
+        }
+        st = plane_lattice(fields[k], planes[k], p, lats[k], who);
+        if (st != FQSL_OK) {
+            delete b;
+            return st;
+        }
+        const long long nk = lats[k].n1 * lats[k].n2;
+        ibase[k] = b->total_items;
+        nbase[k] = b->total_seeds;
+        b->total_items += lats[k].tiles_u * lats[k].tiles_v * (long long)(kTileU * kTileV);
+        b->total_seeds += nk;
+        off[k] = bytes;
+        bytes += layout(nullptr, nk, lats[k].allow_rot, true, f32).bytes;
+        if (lats[k].allow_rot) b->any_rot = true;
+    }
+    ibase[n] = b->total_items;
+    nbase[n] = b->total_seeds;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    // one allocation: entry scratch, contiguous rot_slot arrays, descriptors, prefixes, counters
+    const size_t rot_off = align_up(bytes);
+    b->rot_slot_bytes = b->any_rot ? align_up((size_t)b->total_seeds * sizeof(int32_t)) : 0;
+    const size_t desc_off = align_up(rot_off + b->rot_slot_bytes);
+    const size_t adesc_off = align_up(desc_off + n * sizeof(TraceArgs));
+    const size_t ib_off = align_up(adesc_off + n * sizeof(AssembleArgs));
+    const size_t nb_off = align_up(ib_off + (n + 1) * sizeof(long long));
+    const size_t xb_off = align_up(nb_off + (n + 1) * sizeof(long long));
+    const size_t rc_off = align_up(xb_off + (n + 1) * sizeof(long long));
+    const size_t hd_off = align_up(rc_off + n * sizeof(unsigned));
+    const size_t total = align_up(hd_off + 4 * sizeof(unsigned long long));
+    cudaError_t e = cudaMalloc(&b->mem, total);
+    if (e != cudaSuccess) {
+        delete b;
+        cudaGetLastError();
+        return cuda_fail(e, who);
+    }
+    char *base = (char *)b->mem;
+    b->d_rot_slots = b->any_rot ? (int32_t *)(base + rot_off) : nullptr;
+    b->d_desc = (TraceArgs *)(base + desc_off);
+    b->d_adesc = (AssembleArgs *)(base + adesc_off);
+    b->d_ibase = (long long *)(base + ib_off);
+    b->d_nbase = (long long *)(base + nb_off);
+    b->d_xbase = (long long *)(base + xb_off);
+    b->d_rot_counts = (unsigned *)(base + rc_off);
+    b->d_heads = (unsigned long long *)(base + hd_off);
+    std::vector<TraceArgs> desc(n);
+    std::vector<AssembleArgs> adesc(n);
+    for (int k = 0; k < n; k++) {
+        const fqsl_field f = fields[k];
+        const long long nk = lats[k].n1 * lats[k].n2;
+        Scratch s = layout(base + off[k], nk, lats[k].allow_rot, true, f32);
+        if (lats[k].allow_rot) s.rot_slot = b->d_rot_slots + nbase[k];
+        TraceArgs &a = desc[k];
+        a = TraceArgs{};
+        a.f = f->g;
+        a.f.rec = p->precision == FQSL_F64 ? f->rec64 : f->rec32;
+        a.p = dev_params(p);
+        a.lat = lats[k];
+        a.rec = s.rec;
+        a.ext = s.ext;
+        a.q.rot_count = b->d_rot_counts + k;
+        a.q.rot_seed = s.rot_seed;
+        a.q.rot_slot = s.rot_slot;
+        a.prep = s.prep;
+        a.nitems = ibase[k + 1] - ibase[k];
+        AssembleArgs &g = adesc[k];
+        g = AssembleArgs{};
+        g.f = a.f;
+        g.lat = lats[k];
+        g.rec = s.rec;
+        g.ext = s.ext;
+        g.rot_slot = lats[k].allow_rot ? s.rot_slot : nullptr;
+        g.out = outs[k];
+        g.n = nk;
+        g.want_q = 1;
+    }
+    e = cudaMemcpy(b->d_desc, desc.data(), n * sizeof(TraceArgs), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_adesc, adesc.data(), n * sizeof(AssembleArgs), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_ibase, ibase.data(), (n + 1) * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_nbase, nbase.data(), (n + 1) * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(e, who);
+    }
+    const int bps = p->precision == FQSL_F64 ? batch_trace_blocks_per_sm_f64()
+                                             : batch_trace_blocks_per_sm_f32(p->precision == FQSL_F32_ACC64);
+    b->grid = b->sms * bps;
+    *out = b;
+    return FQSL_OK;
+}
+
+extern "C" fqsl_status fqsl_batch_run(fqsl_batch b, void *cuda_stream)
+{
+    g_err.clear();
+    const char *who = "fqsl_batch_run";
+    if (!b) return fail(FQSL_ERR_ARG, "%s: NULL batch", who);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const fqsl_params *p = &b->params;
+    const bool f32 = p->precision != FQSL_F64;
+    cudaError_t e = cudaMemsetAsync(b->d_heads, 0, 4 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_rot_counts, 0, b->nent * sizeof(unsigned), s);
+    if (e == cudaSuccess && b->any_rot) e = cudaMemsetAsync(b->d_rot_slots, 0, b->rot_slot_bytes, s);
+    if (e == cudaSuccess && f32) e = launch_batch_seed_prep_f32(b->d_desc, b->d_nbase, b->nent, b->total_seeds, s);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    TraceArgs a0{};
+    a0.p = dev_params(p);
+    a0.q.head = b->d_heads;
+    a0.nitems = b->total_items;
+    BatchArgs ba{b->d_desc, b->d_ibase, b->nent};
+    long long grid = b->grid;
+    const long long need = (b->total_items + kTraceBlock - 1) / kTraceBlock;
+    if (need < grid) grid = need;
+    e = f32 ? launch_batch_trace_f32(a0, ba, kSrcLattice, p->precision == FQSL_F32_ACC64, (int)grid, s)
+            : launch_batch_trace_f64(a0, ba, kSrcLattice, (int)grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    if (b->any_rot) {
+        e = launch_batch_extra_prefix(b->d_rot_counts, b->nent, b->d_xbase, s);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+        a0.q.head = b->d_heads + 1;
+        BatchArgs bx{b->d_desc, b->d_xbase, b->nent};
+        e = f32 ? launch_batch_trace_f32(a0, bx, kSrcExtra, p->precision == FQSL_F32_ACC64, b->grid, s)
+                : launch_batch_trace_f64(a0, bx, kSrcExtra, b->grid, s);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+    }
+    e = f32 ? launch_batch_assemble_f32(b->d_adesc, b->d_nbase, b->nent, b->total_seeds, s)
+            : launch_batch_assemble_f64(b->d_adesc, b->d_nbase, b->nent, b->total_seeds, s);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return FQSL_OK;
+}
+
+extern "C" fqsl_status fqsl_batch_destroy(fqsl_batch b)
+{
+    g_err.clear();
+    if (!b) return fail(FQSL_ERR_ARG, "fqsl_batch_destroy: NULL batch");
+    cudaDeviceSynchronize();
+    batch_free(b);
     return FQSL_OK;
 }

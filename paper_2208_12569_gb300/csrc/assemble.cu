@@ -23,11 +23,12 @@ __device__ __forceinline__ void face_coords(const double *r, int face, double fc
     fc[1] = (a == 2) ? r[1] : r[2];
 }
 
-__global__ void __launch_bounds__(256) k_assemble(const AssembleArgs A)
+}  // namespace
+
+__device__ __forceinline__ void assemble_one_f64(const AssembleArgs &A, long long idx)
 {
     const Lattice &G = A.lat;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < A.n;
-         idx += (long long)gridDim.x * blockDim.x) {
+    {
         const LineRecs &R = A.rec;
         unsigned st = R.st[idx];
         double Q = NAN;
@@ -110,6 +111,15 @@ __global__ void __launch_bounds__(256) k_assemble(const AssembleArgs A)
     }
 }
 
+namespace {
+
+__global__ void __launch_bounds__(256) k_assemble(const AssembleArgs A)
+{
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < A.n;
+         idx += (long long)gridDim.x * blockDim.x)
+        assemble_one_f64(A, idx);
+}
+
 __device__ __forceinline__ double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
 // Method II (Sec. 2.1, Eq. q_scott with absolute values): at each end the
@@ -166,6 +176,44 @@ cudaError_t launch_assemble_m2_f64(const AssembleArgs &a, cudaStream_t s)
     if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
     if (blocks < 1) blocks = 1;
     k_assemble_m2<<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+namespace {
+// entry b of a batch holding item idx: nbase[b] <= idx < nbase[b + 1]
+__device__ __forceinline__ int batch_entry(const long long *__restrict__ base, int nent, long long idx)
+{
+    int lo = 0, hi = nent - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= idx) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_batch_assemble_f64(const AssembleArgs *__restrict__ desc,
+                                                            const long long *__restrict__ nbase, int nent)
+{
+    const long long total = nbase[nent];
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int b = batch_entry(nbase, nent, idx);
+        assemble_one_f64(desc[b], idx - nbase[b]);
+    }
+}
+}  // namespace
+
+cudaError_t launch_batch_assemble_f64(const AssembleArgs *desc, const long long *nbase, int nent, long long total,
+                                      cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long blocks = (total + 255) / 256;
+    if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+    if (blocks < 1) blocks = 1;
+    k_batch_assemble_f64<<<(unsigned)blocks, 256, 0, s>>>(desc, nbase, nent);
     return cudaGetLastError();
 }
 

@@ -31,12 +31,13 @@ __device__ __forceinline__ double bn_at(const FieldView &f, const float *xi, int
     return (double)(a == 0 ? B[0] : (a == 1 ? B[1] : B[2]));
 }
 
-__global__ void __launch_bounds__(256) k_assemble_f32(const AssembleArgs A)
+}  // namespace
+
+__device__ __forceinline__ void assemble_one_f32(const AssembleArgs &A, long long idx)
 {
     const Lattice &G = A.lat;
     const FieldView &f = A.f;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < A.n;
-         idx += (long long)gridDim.x * blockDim.x) {
+    {
         const LineRecs &R = A.rec;
         unsigned st = R.st[idx];
         const bool bad = (st & kBad) != 0;
@@ -126,6 +127,15 @@ __global__ void __launch_bounds__(256) k_assemble_f32(const AssembleArgs A)
     }
 }
 
+namespace {
+
+__global__ void __launch_bounds__(256) k_assemble_f32(const AssembleArgs A)
+{
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < A.n;
+         idx += (long long)gridDim.x * blockDim.x)
+        assemble_one_f32(A, idx);
+}
+
 // Method II from the FP32 tracer's end deviation vectors (Eq. q_scott), in FP64.
 __global__ void __launch_bounds__(256) k_assemble_m2_f32(const AssembleArgs A)
 {
@@ -195,6 +205,43 @@ cudaError_t launch_assemble_m2_f32(const AssembleArgs &a, cudaStream_t s)
     if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
     if (blocks < 1) blocks = 1;
     k_assemble_m2_f32<<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+namespace {
+__device__ __forceinline__ int batch_entry(const long long *__restrict__ base, int nent, long long idx)
+{
+    int lo = 0, hi = nent - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= idx) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_batch_assemble_f32(const AssembleArgs *__restrict__ desc,
+                                                            const long long *__restrict__ nbase, int nent)
+{
+    const long long total = nbase[nent];
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int b = batch_entry(nbase, nent, idx);
+        assemble_one_f32(desc[b], idx - nbase[b]);
+    }
+}
+}  // namespace
+
+cudaError_t launch_batch_assemble_f32(const AssembleArgs *desc, const long long *nbase, int nent, long long total,
+                                      cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long blocks = (total + 255) / 256;
+    if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+    if (blocks < 1) blocks = 1;
+    k_batch_assemble_f32<<<(unsigned)blocks, 256, 0, s>>>(desc, nbase, nent);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,7 @@ struct FieldView {
     double o[3];  // origin
     double d[3];  // spacing
     float cmax[3];            // largest cell index per axis, n - 2, as float
+    float rd[3];              // 1 / spacing, as float
     unsigned sy32, sz32;      // FP32 record byte strides along y and z
     const void *grad;         // grad(B/|B|) node records (Method II way 1) or NULL:
                               // FP32 48 B {g0..g8, 0, 0, 0}, FP64 80 B {g0..g8, 0}
@@ -113,6 +114,15 @@ struct TraceArgs {
     SeedPrep prep;        // FP32 lattice: filled by the seed pre-pass
 };
 
+// A batch: many (field, lattice) entries traced by one launch. Work items are
+// numbered across entries; ibase[b] is the first item of entry b (a multiple
+// of 32, so a 32-item chunk never spans two entries), ibase[nent] the total.
+struct BatchArgs {
+    const TraceArgs *desc;  // per entry (device memory)
+    const long long *ibase;
+    int nent;
+};
+
 struct AssembleArgs {
     FieldView f;          // FP32 records (FP32 assembly: Bn at the footpoints)
     Lattice lat;
@@ -145,5 +155,19 @@ constexpr int kTraceBlock = 128;
 cudaError_t launch_assemble(const AssembleArgs &a, cudaStream_t s);
 cudaError_t launch_assemble_f32(const AssembleArgs &a, cudaStream_t s);
 cudaError_t launch_seed_prep_f32(const TraceArgs &a, long long n, cudaStream_t s);
+
+// batches
+cudaError_t launch_batch_seed_prep_f32(const TraceArgs *desc, const long long *nbase, int nent, long long total,
+                                       cudaStream_t s);
+cudaError_t launch_batch_extra_prefix(const unsigned *rot_counts, int nent, long long *xbase, cudaStream_t s);
+cudaError_t launch_batch_trace_f32(const TraceArgs &a0, const BatchArgs &b, int src, bool acc64, int grid,
+                                   cudaStream_t s);
+cudaError_t launch_batch_trace_f64(const TraceArgs &a0, const BatchArgs &b, int src, int grid, cudaStream_t s);
+int batch_trace_blocks_per_sm_f32(bool acc64);
+int batch_trace_blocks_per_sm_f64();
+cudaError_t launch_batch_assemble_f32(const AssembleArgs *desc, const long long *nbase, int nent, long long total,
+                                      cudaStream_t s);
+cudaError_t launch_batch_assemble_f64(const AssembleArgs *desc, const long long *nbase, int nent, long long total,
+                                      cudaStream_t s);
 
 }  // namespace fqsl

@@ -684,7 +684,7 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
             const T b0 = B0[0] / (T)f.d[0], b1 = B0[1] / (T)f.d[1], b2 = B0[2] / (T)f.d[2];
             bb = b0 * b0 + b1 * b1 + b2 * b2;
         } else {
-            const T b0 = B0[0] * (T)(1.0 / f.d[0]), b1 = B0[1] * (T)(1.0 / f.d[1]), b2 = B0[2] * (T)(1.0 / f.d[2]);
+            const T b0 = B0[0] * (T)f.rd[0], b1 = B0[1] * (T)f.rd[1], b2 = B0[2] * (T)f.rd[2];
             bb = b0 * b0 + b1 * b1 + b2 * b2;
         }
         if (!(bb > (T)0) || !(bb < (T)INFINITY)) bad = FQSL_LINE_NULL_B;
@@ -885,41 +885,46 @@ __device__ __forceinline__ bool init_list(const TraceArgs &A, Lane<T> &L, long l
 // FP64 tracer); false: FP32 error norm and compensated FP32 sums.
 // DEV: 0 = positions only (Method I, twist); 1, 2 = Method II deviation
 // vectors with grad(B/|B|) by way 1 or way 2 (lattice source only).
-template <typename T, int SRC, bool ACC, int DEV = 0>
-__device__ __forceinline__ void trace_body(const TraceArgs &A)
+// BATCH: the launch traces the entries of a batch (BatchArgs); each lane keeps
+// the entry of its line. A0 holds the launch-wide parameters and counter.
+template <typename T, int SRC, bool ACC, int DEV = 0, bool BATCH = false>
+__device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs &BA)
 {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const FieldView &f = A.f;
-    const LineRecs &R = (SRC == kSrcExtra) ? A.ext : A.rec;
     constexpr bool kF64 = sizeof(T) == 8;
-    // FP32 multiplies by 1/d, FP64 divides by d (see rhs)
-    const T dd[3] = {kF64 ? (T)f.d[0] : (T)(1.0 / f.d[0]), kF64 ? (T)f.d[1] : (T)(1.0 / f.d[1]),
-                     kF64 ? (T)f.d[2] : (T)(1.0 / f.d[2])};
-    const T hmin = (T)A.p.hmin, hmax = (T)A.p.hmax;
-    const T graze = (T)A.p.graze;
-    const int max_steps = (int)A.p.max_steps;
+    const T hmin = (T)A0.p.hmin, hmax = (T)A0.p.hmax;
+    const T graze = (T)A0.p.graze;
+    const int max_steps = (int)A0.p.max_steps;
 
-    long long nitems = A.nitems;
-    if (SRC == kSrcExtra) nitems = 4LL * (long long)(*(volatile unsigned *)A.q.rot_count);
+    long long nitems = A0.nitems;
+    if (BATCH) nitems = BA.ibase[BA.nent];
+    else if (SRC == kSrcExtra) nitems = 4LL * (long long)(*(volatile unsigned *)A0.q.rot_count);
 
-    long long ck_cur = 0, ck_end = 0;
+    long long ck_cur = 0, ck_end = 0, ck_base = 0;
+    int ck_ent = 0;
     bool exhausted = false;
     bool active = false;
     bool waiting = false;  // sync_dirs: first direction done, second not started
+    int eb = 0;            // BATCH: entry of this lane's line
     Lane<T> L;
     L.line = 0;
+    // the entry of this lane's line (the launch itself when not batched)
+    auto ent = [&]() -> const TraceArgs & {
+        if constexpr (BATCH) return BA.desc[eb];
+        else return A0;
+    };
 
     for (;;) {
         // refill idle lanes from the warp's chunk / the global counter, once
         // at least p.refill lanes are idle (or none is busy)
         unsigned idle = __ballot_sync(FULL, !active);
-        const bool refill = __popc(idle) >= A.p.refill || idle == FULL;
+        const bool refill = __popc(idle) >= A0.p.refill || idle == FULL;
         while (refill && idle != 0u && !exhausted) {
             if (ck_cur >= ck_end) {
                 unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(A.q.head, (unsigned long long)kChunk);
+                if (lane == 0) base = atomicAdd(A0.q.head, (unsigned long long)kChunk);
                 base = __shfl_sync(FULL, base, 0);
                 if ((long long)base >= nitems) {
                     exhausted = true;
@@ -927,24 +932,45 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
                 }
                 ck_cur = (long long)base;
                 ck_end = min(ck_cur + (long long)kChunk, nitems);
+                ck_base = 0;
+                if constexpr (BATCH) {
+                    // entry holding this chunk (chunks never span entries)
+                    int lo = 0, hi = BA.nent - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (BA.ibase[mid] <= ck_cur) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    ck_ent = lo;
+                    ck_base = BA.ibase[lo];
+                }
             }
             const long long avail = ck_end - ck_cur;
             const int rank = __popc(idle & lt_mask);
             if (!active && rank < avail) {
-                const long long item = ck_cur + rank;
-                if (SRC == kSrcLattice) active = init_lattice<T, ACC, DEV>(A, L, item);
-                else if (SRC == kSrcExtra) active = init_extra<T, ACC>(A, L, item);
-                else active = init_list<T, ACC>(A, L, item);
+                const long long item = ck_cur + rank - ck_base;
+                eb = ck_ent;
+                const TraceArgs &E = ent();
+                if (SRC == kSrcLattice) active = init_lattice<T, ACC, DEV>(E, L, item);
+                else if (SRC == kSrcExtra) active = item < 4LL * (long long)*E.q.rot_count && init_extra<T, ACC>(E, L, item);
+                else active = init_list<T, ACC>(E, L, item);
             }
             ck_cur += min((long long)__popc(idle), avail);
             idle = __ballot_sync(FULL, !active);
         }
         if (__ballot_sync(FULL, active) == 0u) break;
-        if (A.p.sync_dirs) {
+        if (A0.p.sync_dirs) {
             // lanes that finished their first direction wait until none is left in it
             if (__ballot_sync(FULL, active && !waiting && L.end == 0) == 0u) waiting = false;
         }
         if (!active || waiting) continue;
+
+        const TraceArgs &A = ent();
+        const FieldView &f = A.f;
+        const LineRecs &R = (SRC == kSrcExtra) ? A.ext : A.rec;
+        // FP32 multiplies by 1/d, FP64 divides by d (see rhs)
+        const T dd[3] = {kF64 ? (T)f.d[0] : (T)f.rd[0], kF64 ? (T)f.d[1] : (T)f.rd[1],
+                         kF64 ? (T)f.d[2] : (T)f.rd[2]};
 
         // ---- one trial: normal RKF45 step or exit (Henon) step ----
         const bool henon = L.mode != 0;
@@ -1000,7 +1026,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
                     us[c] = (c < 3 ? L.u[c] : L.v[c - 3]) + hh * acc;
                 }
                 T G[3][3];
-                ok = grad_bhat<T, DEV>(f, (T)A.p.eps2, px, py, pz, G) && ok;
+                ok = grad_bhat<T, DEV>(f, (T)A0.p.eps2, px, py, pz, G) && ok;
                 const T sdl = sgn * o[3];
 #pragma unroll
                 for (int b = 0; b < 3; b++) {
@@ -1197,7 +1223,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
                 }
             }
             active = finish_dir<T, ACC, DEV>(A, R, L, ex, ey, ez, L.fc0, eu, ev);
-            waiting = active && A.p.sync_dirs;
+            waiting = active && A0.p.sync_dirs;
             continue;
         }
         T tx = L.x + hh * a4[0], ty = L.y + hh * a4[1], tz = L.z + hh * a4[2];
@@ -1235,7 +1261,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A)
             }
         }
         active = finish_dir<T, ACC, DEV>(A, R, L, tx, ty, tz, L.hface, eu, ev);
-        waiting = active && A.p.sync_dirs;
+        waiting = active && A0.p.sync_dirs;
     }
 }
 
@@ -1264,8 +1290,7 @@ __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
     } else {
         float B0[3], J0[3];
         gather(f, x, y, z, B0, J0);
-        const float b0 = B0[0] * (float)(1.0 / f.d[0]), b1 = B0[1] * (float)(1.0 / f.d[1]),
-                    b2 = B0[2] * (float)(1.0 / f.d[2]);
+        const float b0 = B0[0] * f.rd[0], b1 = B0[1] * f.rd[1], b2 = B0[2] * f.rd[2];
         const float bb = b0 * b0 + b1 * b1 + b2 * b2;
         const float nB = sqrtf(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
         if (!(bb > 0.f) || !(bb < INFINITY) || !(nB > 0.f)) {

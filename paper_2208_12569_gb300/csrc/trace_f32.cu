@@ -17,7 +17,7 @@ constexpr int kBlock = 128;
 template <int SRC, bool ACC>
 __global__ void __launch_bounds__(kBlock, FQSL_TRACE_F32_MINB) k_trace_f32(const TraceArgs A)
 {
-    trace::trace_body<float, SRC, ACC>(A);
+    trace::trace_body<float, SRC, ACC>(A, BatchArgs{});
 }
 }  // namespace
 
@@ -85,7 +85,7 @@ namespace {
 template <int WAY>
 __global__ void __launch_bounds__(kBlock) k_trace_dev_f32(const TraceArgs A)
 {
-    trace::trace_body<float, kSrcLattice, false, WAY>(A);
+    trace::trace_body<float, kSrcLattice, false, WAY>(A, BatchArgs{});
 }
 }  // namespace
 
@@ -102,6 +102,88 @@ int trace_dev_blocks_per_sm_f32(int way)
     int b = 0;
     if (way == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_dev_f32<1>, kBlock, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_dev_f32<2>, kBlock, 0);
+    return b > 0 ? b : 1;
+}
+}  // namespace fqsl
+
+// ---------------------------------------------------------------------------
+// batches: many (field, plane) entries in one launch
+// ---------------------------------------------------------------------------
+namespace fqsl {
+namespace {
+template <int SRC, bool ACC>
+__global__ void __launch_bounds__(kBlock, FQSL_TRACE_F32_MINB) k_batch_trace_f32(const TraceArgs A0, const BatchArgs B)
+{
+    trace::trace_body<float, SRC, ACC, 0, true>(A0, B);
+}
+
+__global__ void __launch_bounds__(256) k_batch_seed_prep_f32(const TraceArgs *__restrict__ desc,
+                                                             const long long *__restrict__ nbase, int nent)
+{
+    const long long total = nbase[nent];
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nent - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (nbase[mid] <= idx) lo = mid;
+            else hi = mid - 1;
+        }
+        trace::seed_prep_f32(desc[lo], idx - nbase[lo]);
+    }
+}
+
+// work-item prefix of the rotated extra lines: 4 per rotated seed, padded to
+// whole 32-item chunks per entry
+__global__ void k_batch_extra_prefix(const unsigned *__restrict__ rot_counts, int nent, long long *xbase)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    long long acc = 0;
+    for (int b = 0; b < nent; b++) {
+        xbase[b] = acc;
+        acc += (4LL * rot_counts[b] + 31) / 32 * 32;
+    }
+    xbase[nent] = acc;
+}
+}  // namespace
+
+cudaError_t launch_batch_seed_prep_f32(const TraceArgs *desc, const long long *nbase, int nent, long long total,
+                                       cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long blocks = (total + 255) / 256;
+    if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+    if (blocks < 1) blocks = 1;
+    k_batch_seed_prep_f32<<<(unsigned)blocks, 256, 0, s>>>(desc, nbase, nent);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_extra_prefix(const unsigned *rot_counts, int nent, long long *xbase, cudaStream_t s)
+{
+    k_batch_extra_prefix<<<1, 32, 0, s>>>(rot_counts, nent, xbase);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_trace_f32(const TraceArgs &a0, const BatchArgs &b, int src, bool acc64, int grid,
+                                   cudaStream_t s)
+{
+    if (src == kSrcLattice) {
+        if (acc64) k_batch_trace_f32<kSrcLattice, true><<<grid, kBlock, 0, s>>>(a0, b);
+        else k_batch_trace_f32<kSrcLattice, false><<<grid, kBlock, 0, s>>>(a0, b);
+    } else {
+        if (acc64) k_batch_trace_f32<kSrcExtra, true><<<grid, kBlock, 0, s>>>(a0, b);
+        else k_batch_trace_f32<kSrcExtra, false><<<grid, kBlock, 0, s>>>(a0, b);
+    }
+    return cudaGetLastError();
+}
+
+int batch_trace_blocks_per_sm_f32(bool acc64)
+{
+    int b = 0;
+    if (acc64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_trace_f32<kSrcLattice, true>, kBlock, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_trace_f32<kSrcLattice, false>, kBlock, 0);
     return b > 0 ? b : 1;
 }
 }  // namespace fqsl

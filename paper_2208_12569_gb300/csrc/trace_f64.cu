@@ -9,7 +9,7 @@ constexpr int kBlock = 128;
 template <int SRC>
 __global__ void __launch_bounds__(kBlock) k_trace_f64(const TraceArgs A)
 {
-    trace::trace_body<double, SRC, true>(A);
+    trace::trace_body<double, SRC, true>(A, BatchArgs{});
 }
 }  // namespace
 
@@ -38,7 +38,7 @@ namespace {
 template <int WAY>
 __global__ void __launch_bounds__(kBlock) k_trace_dev_f64(const TraceArgs A)
 {
-    trace::trace_body<double, kSrcLattice, true, WAY>(A);
+    trace::trace_body<double, kSrcLattice, true, WAY>(A, BatchArgs{});
 }
 }  // namespace
 
@@ -55,6 +55,30 @@ int trace_dev_blocks_per_sm_f64(int way)
     int b = 0;
     if (way == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_dev_f64<1>, kBlock, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_dev_f64<2>, kBlock, 0);
+    return b > 0 ? b : 1;
+}
+}  // namespace fqsl
+
+namespace fqsl {
+namespace {
+template <int SRC>
+__global__ void __launch_bounds__(kBlock) k_batch_trace_f64(const TraceArgs A0, const BatchArgs B)
+{
+    trace::trace_body<double, SRC, true, 0, true>(A0, B);
+}
+}  // namespace
+
+cudaError_t launch_batch_trace_f64(const TraceArgs &a0, const BatchArgs &b, int src, int grid, cudaStream_t s)
+{
+    if (src == kSrcLattice) k_batch_trace_f64<kSrcLattice><<<grid, kBlock, 0, s>>>(a0, b);
+    else k_batch_trace_f64<kSrcExtra><<<grid, kBlock, 0, s>>>(a0, b);
+    return cudaGetLastError();
+}
+
+int batch_trace_blocks_per_sm_f64()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_trace_f64<kSrcLattice>, kBlock, 0);
     return b > 0 ? b : 1;
 }
 }  // namespace fqsl

@@ -21,7 +21,8 @@ LINE_MAXSTEPS, LINE_NULL_B, LINE_STALL, LINE_MIXED, LINE_OUTSIDE, LINE_ROTATED, 
 LINE_BAD = LINE_MAXSTEPS | LINE_NULL_B | LINE_OUTSIDE
 EXPORTS = ("fqsl_params_default", "fqsl_version", "fqsl_last_error", "fqsl_field_create", "fqsl_field_destroy",
            "fqsl_qmap_plane", "fqsl_qmap_volume", "fqsl_twist", "fqsl_field_check", "fqsl_field_set_timing",
-           "fqsl_field_times", "fqsl_field_update", "fqsl_qmap_plane_static")
+           "fqsl_field_times", "fqsl_field_update", "fqsl_qmap_plane_static", "fqsl_batch_create", "fqsl_batch_run",
+           "fqsl_batch_destroy")
 STATIC_MAX_SEEDS = 65536
 
 
@@ -36,6 +37,11 @@ class Params(C.Structure):
                 ("tol", C.c_double), ("h0", C.c_double), ("h_min", C.c_double), ("h_max", C.c_double),
                 ("max_steps", C.c_longlong), ("rot_thresh", C.c_double), ("tol_exp", C.c_double),
                 ("graze", C.c_double), ("eps_way2", C.c_double), ("sync_dirs", C.c_int), ("reserved1", C.c_int)]
+
+
+class Plane(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("u", C.c_double * 3), ("v", C.c_double * 3), ("nu", C.c_longlong),
+                ("nv", C.c_longlong)]
 
 
 class Out(C.Structure):
@@ -63,6 +69,9 @@ def load(path: str = LIB_PATH):
     lib.fqsl_twist.argtypes = [P, P, C.c_longlong, C.POINTER(Params), C.POINTER(Out), P]
     lib.fqsl_field_check.argtypes = [P, P]
     lib.fqsl_field_set_timing.argtypes = [P, C.c_int]
+    lib.fqsl_batch_create.argtypes = [P, P, P, C.c_int, C.POINTER(Params), C.POINTER(P)]
+    lib.fqsl_batch_run.argtypes = [P, P]
+    lib.fqsl_batch_destroy.argtypes = [P]
     lib.fqsl_field_update.argtypes = [P, P, C.c_int, P]
     lib.fqsl_field_times.argtypes = [P, C.POINTER(C.c_float * 3)]
     for name in EXPORTS:
@@ -230,3 +239,58 @@ def twist(field: Field, seeds: torch.Tensor, p: Params | None = None, out=None, 
     _check(_lib.fqsl_twist(field.handle, C.c_void_p(seeds.data_ptr()), n, C.byref(p), C.byref(_out_struct(out)),
                            _stream(stream)))
     return out
+
+
+class Batch:
+    """A batch plan: entries (field, plane) of uneven sizes mapped by one set of
+    launches (fqsl_batch_*). ``planes`` are dicts with origin, u, v, nu, nv.
+    Output buffers are allocated here (``outs[k]``) unless given. ``run()`` only
+    launches kernels on the stream, so it can be captured in a CUDA graph
+    (``graph()``)."""
+
+    def __init__(self, fields, planes, p: Params | None = None, outs=None, device="cuda"):
+        self.p = p or params()
+        self.fields = list(fields)
+        self.planes = [dict(pl) for pl in planes]
+        n = len(self.fields)
+        self.outs = outs or [alloc_out(pl["nu"] * pl["nv"], device=device) for pl in self.planes]
+        F = (C.c_void_p * n)(*[f.handle.value for f in self.fields])
+        PL = (Plane * n)()
+        for k, pl in enumerate(self.planes):
+            PL[k].origin = (C.c_double * 3)(*map(float, pl["origin"]))
+            PL[k].u = (C.c_double * 3)(*map(float, pl["u"]))
+            PL[k].v = (C.c_double * 3)(*map(float, pl["v"]))
+            PL[k].nu = int(pl["nu"])
+            PL[k].nv = int(pl["nv"])
+        O = (Out * n)(*[_out_struct(o) for o in self.outs])
+        h = C.c_void_p()
+        _check(_lib.fqsl_batch_create(F, PL, O, n, C.byref(self.p), C.byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        _check(_lib.fqsl_batch_run(self._h, _stream(stream)))
+        return self.outs
+
+    def graph(self, warmup: int = 1):
+        """Capture run() into a torch CUDA graph; replay it with .replay()."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self.run()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run()
+        return g
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.fqsl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
