@@ -286,6 +286,108 @@ def run_volume(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Batched uneven workload: 48 monopole cubes with sizes drawn from
+    {64^3, 128^2x64, 256^2x128, 384^2x192}, 8-64 sources each, each with the
+    z=0 plane or the mid-y vertical slice of 512x256 seeds (6.29 M lines).
+    Times per-cube launches, one batch run, its CUDA-graph replay and the
+    autotuned graph; checks a sample of seeds against the oracle."""
+    import torch
+
+    import __graft_entry__
+    import oracle
+    import synth
+
+    __graft_entry__._builder().build()
+    import paper_2208_12569_gb300 as fq
+    from paper_2208_12569_gb300 import autotune
+
+    dev = torch.device("cuda", 0)
+    specs = synth.batch_specs(seed=SEED)
+    t0 = time.perf_counter()
+    cubes = [synth.monopole_cube(sp["grid"], sp["charges"], dtype=np.float32, device=dev) for sp in specs]
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    fields = [fq.Field(B, sp["grid"].origin, sp["grid"].spacing, pack=("f32",)) for B, sp in zip(cubes, specs)]
+    planes = [sp["plane"] for sp in specs]
+    total = sum(pl["nu"] * pl["nv"] for pl in planes)
+    p = fq.params(precision="f32", tol=TOL)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    outs = [fq.alloc_out(pl["nu"] * pl["nv"], device=dev) for pl in planes]
+
+    def timed(fn, k):
+        ts = []
+        for _ in range(k):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    def per_cube(pp=p):
+        for fld, pl, o in zip(fields, planes, outs):
+            fq.qmap_plane(fld, pl["origin"], pl["u"], pl["v"], pl["nu"], pl["nv"], pp, out=o)
+
+    for _ in range(args.warmup):
+        per_cube()
+    ms_single = timed(per_cube, args.steps)
+    batch = fq.Batch(fields, planes, p, outs=outs)
+    for _ in range(args.warmup):
+        batch.run()
+    ms_batch = timed(batch.run, args.steps)
+    graph = batch.graph()
+    ms_graph = timed(graph.replay, args.steps)
+    # autotune the batch's scheduling knobs (results are identical for all)
+    space = {"refill_lanes": (1, 32), "sync_dirs": (0, 1), "blocks_per_sm": (0, 2, 3)}
+
+    def run_with(pp):
+        b = fq.Batch(fields, planes, pp, outs=outs)
+        b.run()
+        torch.cuda.synchronize()
+        b.close()
+
+    best, table = autotune.tune(run_with, p, key="batch48_512x256", space=space, reps=3, path="")
+    tuned = fq.Batch(fields, planes, best, outs=outs)
+    tuned.run()
+    tgraph = tuned.graph()
+    ms_tuned = timed(tgraph.replay, args.steps)
+    torch.cuda.synchronize()
+    res = [{k: t.cpu().numpy() for k, t in o.items() if t is not None} for o in outs]
+    # oracle on a sample of seeds of the four smallest cubes
+    order = sorted(range(len(specs)), key=lambda k: np.prod(specs[k]["grid"].n))[:4]
+    errs = []
+    ora_n, ora_s = 0, 0.0
+    for k in order:
+        sp, pl = specs[k], planes[k]
+        sample = np.sort(np.random.default_rng(k).choice(pl["nu"] * pl["nv"], 500, replace=False))
+        B64 = cubes[k].cpu().numpy().astype(np.float64)
+        t1 = time.perf_counter()
+        ref = oracle.plane(B64, sp["grid"], pl["origin"], pl["u"], pl["v"], pl["nu"], pl["nv"],
+                           oracle.params(tol=TOL), sample=sample)
+        ora_s += time.perf_counter() - t1
+        ora_n += len(sample)
+        errs.append(err_stats(res[k], ref, sample))
+    line = {"metric": METRIC, "workload": "batch", "unit": "Q+Tw values/s",
+            "config": {"workload": "batch48_monopole_mixed_sizes_512x256_seeds_methodI", "entries": len(specs),
+                       "lines": total, "tol_perp": TOL, "l2": "flushed between steps"},
+            "value": total / (ms_tuned / 1000.0),
+            "per_cube_launches": {"ms": ms_single, "value": total / (ms_single / 1000.0)},
+            "batch_run": {"ms": ms_batch, "value": total / (ms_batch / 1000.0)},
+            "batch_graph": {"ms": ms_graph, "value": total / (ms_graph / 1000.0)},
+            "batch_graph_autotuned": {"ms": ms_tuned, "value": total / (ms_tuned / 1000.0),
+                                      "best": {k: getattr(best, k) for k in space}, "table": table},
+            "error_vs_oracle_sample": errs,
+            "cpu_baseline": {"value": ora_n / ora_s, "unit": "Q+Tw values/s", "cores": oracle.max_threads(),
+                             "kind": "oracle", "sample": "500 seeds of each of the 4 smallest cubes"},
+            "generation_s": gen_s}
+    print(json.dumps(line), flush=True)
+    for b in (batch, tuned):
+        b.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -296,14 +398,18 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--only-f32", action="store_true",
                     help="time only the FP32 map (no FP64, e2e or CPU legs); used for ncu captures")
-    ap.add_argument("--workload", default="plane", choices=["plane", "volume"],
-                    help="plane: the benchmark line; volume: the large-volume configuration")
+    ap.add_argument("--workload", default="plane", choices=["plane", "volume", "batch"],
+                    help="plane: the benchmark line; volume: the large-volume configuration; "
+                         "batch: 48 uneven cubes in one launch")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.workload == "volume":
         run_volume(args)
+        return
+    if args.workload == "batch":
+        run_batch(args)
         return
 
     import torch

@@ -104,7 +104,10 @@ typedef struct {
     double eps_way2;      /* Method II way-2 offset, default 1e-3 */
     int sync_dirs;        /* scheduling: 1 = the lanes of a warp start their second directions together,
                              0 = each lane at once, -1 = library default. Results do not depend on it. */
-    int reserved1;
+    int chunk_tiles;      /* scheduling: 8x4-seed tiles a warp takes per grab of the work counter
+                             (1..64; 0 = default 1; batches always take 1). Results do not depend on it. */
+    int blocks_per_sm;    /* scheduling: resident 128-thread blocks per SM of the persistent tracer
+                             (0 = as many as fit). Results do not depend on it. */
 } fqsl_params;
 
 /* Output buffers of one call (caller-owned device memory, n = number of

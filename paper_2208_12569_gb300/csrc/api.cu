@@ -296,6 +296,8 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
     if (!(p->eps_way2 > 0) || !(p->eps_way2 < 0.5)) return fail(FQSL_ERR_ARG, "%s: eps_way2 in (0,0.5)", who);
     if (p->refill_lanes < 0 || p->refill_lanes > 32) return fail(FQSL_ERR_ARG, "%s: refill_lanes in [0, 32]", who);
     if (p->sync_dirs < -1 || p->sync_dirs > 1) return fail(FQSL_ERR_ARG, "%s: sync_dirs in {-1, 0, 1}", who);
+    if (p->chunk_tiles < 0 || p->chunk_tiles > 64) return fail(FQSL_ERR_ARG, "%s: chunk_tiles in [0, 64]", who);
+    if (p->blocks_per_sm < 0 || p->blocks_per_sm > 64) return fail(FQSL_ERR_ARG, "%s: blocks_per_sm in [0, 64]", who);
     if (p->precision != FQSL_F64 && !f->rec32)
         return fail(FQSL_ERR_UNSUPPORTED, "%s: field was not packed in FP32 (FQSL_PACK_F32)", who);
     if (p->precision == FQSL_F64 && !f->rec64)
@@ -325,6 +327,7 @@ DevParams dev_params(const fqsl_params *p)
     d.way = p->gradb_way;
     d.refill = p->refill_lanes > 0 ? p->refill_lanes : kDefaultRefill;
     d.sync_dirs = p->sync_dirs >= 0 ? p->sync_dirs : kDefaultSyncDirs;
+    d.chunk = (p->chunk_tiles > 0 ? p->chunk_tiles : 1) * kTileU * kTileV;
     return d;
 }
 
@@ -425,7 +428,9 @@ cudaError_t launch_trace(fqsl_field f, const fqsl_params *p, const TraceArgs &a,
                          cudaStream_t s)
 {
     const long long warps_needed = (items + 31) / 32;
-    long long grid = (long long)f->sms * blocks_per_sm(f, p->precision, src);
+    int bps = blocks_per_sm(f, p->precision, src);
+    if (p->blocks_per_sm > 0 && p->blocks_per_sm < bps) bps = p->blocks_per_sm;
+    long long grid = (long long)f->sms * bps;
     const long long need = (warps_needed * 32 + kTraceBlock - 1) / kTraceBlock;
     if (src != kSrcExtra && need < grid) grid = need;
     if (grid < 1) grid = 1;
@@ -440,7 +445,7 @@ cudaError_t launch_trace_m2(fqsl_field f, const fqsl_params *p, const TraceArgs 
     if (!c)
         c = p->precision == FQSL_F64 ? trace_dev_blocks_per_sm_f64(p->gradb_way)
                                      : trace_dev_blocks_per_sm_f32(p->gradb_way);
-    long long grid = (long long)f->sms * c;
+    long long grid = (long long)f->sms * (p->blocks_per_sm > 0 && p->blocks_per_sm < c ? p->blocks_per_sm : c);
     const long long need = (a.nitems + kTraceBlock - 1) / kTraceBlock;
     if (need < grid) grid = need;
     if (grid < 1) grid = 1;
@@ -1027,7 +1032,7 @@ extern "C" fqsl_status fqsl_batch_create(const fqsl_field *fields, const fqsl_pl
     }
     const int bps = p->precision == FQSL_F64 ? batch_trace_blocks_per_sm_f64()
                                              : batch_trace_blocks_per_sm_f32(p->precision == FQSL_F32_ACC64);
-    b->grid = b->sms * bps;
+    b->grid = b->sms * (p->blocks_per_sm > 0 && p->blocks_per_sm < bps ? p->blocks_per_sm : bps);
     *out = b;
     return FQSL_OK;
 }
@@ -1047,6 +1052,7 @@ extern "C" fqsl_status fqsl_batch_run(fqsl_batch b, void *cuda_stream)
     if (e != cudaSuccess) return cuda_fail(e, who);
     TraceArgs a0{};
     a0.p = dev_params(p);
+    a0.p.chunk = kTileU * kTileV;  // a grab never spans two entries
     a0.q.head = b->d_heads;
     a0.nitems = b->total_items;
     BatchArgs ba{b->d_desc, b->d_ibase, b->nent};

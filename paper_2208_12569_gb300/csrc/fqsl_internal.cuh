@@ -44,6 +44,7 @@ struct DevParams {
     int method, way;
     int refill;     // minimum idle lanes before a warp takes new seeds
     int sync_dirs;  // lanes wait for each other before their second direction
+    int chunk;      // work items per grab of the counter (a multiple of 32)
 };
 
 // Cell-centred lattice seed(i,j,k) = o + (i+1/2) a1 + (j+1/2) a2 + (k+1/2) a3.

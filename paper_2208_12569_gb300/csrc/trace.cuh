@@ -924,14 +924,15 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
         while (refill && idle != 0u && !exhausted) {
             if (ck_cur >= ck_end) {
                 unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(A0.q.head, (unsigned long long)kChunk);
+                const long long chunk = BATCH ? (long long)kChunk : (long long)A0.p.chunk;
+                if (lane == 0) base = atomicAdd(A0.q.head, (unsigned long long)chunk);
                 base = __shfl_sync(FULL, base, 0);
                 if ((long long)base >= nitems) {
                     exhausted = true;
                     break;
                 }
                 ck_cur = (long long)base;
-                ck_end = min(ck_cur + (long long)kChunk, nitems);
+                ck_end = min(ck_cur + chunk, nitems);
                 ck_base = 0;
                 if constexpr (BATCH) {
                     // entry holding this chunk (chunks never span entries)

@@ -36,7 +36,8 @@ class Params(C.Structure):
     _fields_ = [("method", C.c_int), ("gradb_way", C.c_int), ("precision", C.c_int), ("refill_lanes", C.c_int),
                 ("tol", C.c_double), ("h0", C.c_double), ("h_min", C.c_double), ("h_max", C.c_double),
                 ("max_steps", C.c_longlong), ("rot_thresh", C.c_double), ("tol_exp", C.c_double),
-                ("graze", C.c_double), ("eps_way2", C.c_double), ("sync_dirs", C.c_int), ("reserved1", C.c_int)]
+                ("graze", C.c_double), ("eps_way2", C.c_double), ("sync_dirs", C.c_int), ("chunk_tiles", C.c_int),
+                ("blocks_per_sm", C.c_int)]
 
 
 class Plane(C.Structure):

@@ -42,6 +42,9 @@ def test_params_defaults():
     assert p.method == 1 and p.precision == fq.F32
     assert abs(p.tol - 10 ** -3.2) < 1e-15 and p.h0 == 0.5 and p.h_max == 4.0 and p.max_steps == 100000
     assert fq.params(precision="f64").precision == fq.F64
+    # the tail of the struct (catches a layout mismatch with the header)
+    assert p.sync_dirs == -1 and p.chunk_tiles == 0 and p.blocks_per_sm == 0 and p.refill_lanes == 0
+    assert p.eps_way2 == 1e-3 and p.graze == 1e-3
 
 
 def test_host_argument_errors(lib):
