@@ -1,0 +1,389 @@
+"""FP64 CPU adjoint oracle -- TEST INFRASTRUCTURE ONLY.
+
+Reverse (and tangent-linear) derivatives of the plane-lattice Q and Tw maps
+(Method I) with respect to the field cube B, in plain PyTorch CPU float64.
+
+The C oracle traces every lattice line once and records its accepted steps
+(``oracle_lattice_log``): the step size of each accepted RKF45 step, and how
+each direction ended (exit step onto a face, the same with the point clamped
+into the box, or the chord fallback after an exiting step of a given size).
+This module replays exactly that step sequence with the step sizes, exit faces
+and exit kinds frozen, recomputing from the leaf tensor B everything else: the
+curl grid, every stage position and RHS value (Sec. 2.2 Eq. interp and the
+index-space line equation of Sec. 2.1 / 2.3), the exit-step length (distance
+to the face), the chord parameter, the footpoints, Tw (Eq. tw), Bn at the
+seed and at both ends (Eq. Bn1) and Method I's Q (Eqs. D+-2, D+-3, Q+-), with
+the finite-difference stencils the oracle chose (reading R8). Autograd (reverse
+mode) and forward-mode AD then give d(output)/dB of this frozen-sequence map,
+the discrete adjoint the CUDA reverse sweep implements.
+
+Only the tests and the benchmark's CPU leg use this module.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+import torch
+
+from . import BAD, ROTATED, _f64, _grid_args, _p, curl, lib, params, plane
+
+# Fehlberg 4(5) stage matrix and 4th-order weights (the propagated solution)
+_A = [[], [1 / 4], [3 / 32, 9 / 32], [1932 / 2197, -7200 / 2197, 7296 / 2197],
+      [439 / 216, -8.0, 3680 / 513, -845 / 4104], [-8 / 27, 2.0, -3544 / 2565, 1859 / 4104, -11 / 40]]
+_B4 = [25 / 216, 0.0, 1408 / 2565, 2197 / 4104, -1 / 5, 0.0]
+
+# step-record codes of oracle_lattice_log
+START, STEP, EXIT, EXIT_CLAMPED, CHORD = 99, 0, 16, 40, 48
+
+
+def lattice_log(B, grid, origin, u, v, nu, nv, p=None, cap=8192, J=None):
+    """Trace every line of the plane lattice once with the C oracle; return
+    its step records and per-line outcomes (numpy arrays)."""
+    p = p or params()
+    B = _f64(B)
+    J = _f64(curl(B, grid) if J is None else J)
+    n, o, d = _grid_args(grid)
+    m = nu * nv
+    out = dict(h=np.zeros((m, cap)), code=np.zeros((m, cap), np.int32), n=np.zeros(m, np.int32),
+               s0=np.zeros(m), tol=np.zeros(m), bn0=np.zeros(m), ends=np.zeros((m, 2, 11)),
+               faces=np.zeros((m, 2), np.int32), status=np.zeros(m, np.int32))
+    lo = np.array(origin, float)
+    a1, a2 = np.array(u, float), np.array(v, float)
+    ln = np.array([nu, nv], np.int64)
+    L = lib()
+    L.oracle_lattice_log.restype = C.c_int
+    rc = L.oracle_lattice_log(_p(B), _p(J), _p(n), _p(o), _p(d), _p(lo), _p(a1), _p(a2), _p(ln), C.byref(p),
+                              C.c_int(cap), _p(out["h"]), _p(out["code"]), _p(out["n"]), _p(out["s0"]),
+                              _p(out["tol"]), _p(out["bn0"]), _p(out["ends"]), _p(out["faces"]),
+                              _p(out["status"]))
+    if rc:
+        raise ValueError("oracle_lattice_log: error %d" % rc)
+    if np.any(out["n"] < 0):
+        raise ValueError("step record overflow: raise cap")
+    return out
+
+
+def curl_t(B, spacing):
+    """curl B at the nodes (B of shape (nz, ny, nx, 3)): 2nd-order central
+    differences inside, 2nd-order one-sided on the faces, first order on an
+    axis of 2 nodes -- the stencils of the oracle's curl grid, in torch."""
+    def deriv(f, dim, h):
+        n = f.shape[dim]
+        s = lambda a, b: f.narrow(dim, a, b - a)  # noqa: E731
+        if n == 2:
+            g = (s(1, 2) - s(0, 1)) / h
+            return torch.cat([g, g], dim=dim)
+        first = (-3.0 * s(0, 1) + 4.0 * s(1, 2) - s(2, 3)) / (2.0 * h)
+        mid = (s(2, n) - s(0, n - 2)) / (2.0 * h)
+        last = (3.0 * s(n - 1, n) - 4.0 * s(n - 2, n - 1) + s(n - 3, n - 2)) / (2.0 * h)
+        return torch.cat([first, mid, last], dim=dim)
+
+    dx, dy, dz = spacing
+    Bx, By, Bz = B[..., 0], B[..., 1], B[..., 2]
+    # tensor dims: 0 = z, 1 = y, 2 = x
+    Jx = deriv(Bz, 1, dy) - deriv(By, 0, dz)
+    Jy = deriv(Bx, 0, dz) - deriv(Bz, 2, dx)
+    Jz = deriv(By, 2, dx) - deriv(Bx, 1, dy)
+    return torch.stack([Jx, Jy, Jz], dim=-1)
+
+
+class _Field:
+    """B and curl B node values flattened to (nodes, 6), and trilinear
+    interpolation at index positions (Sec. 2.2): the cell is the floor of the
+    position clamped to [0, n-2] (chosen without a derivative), the weights
+    are linear in the position."""
+
+    def __init__(self, Bt, Jt, n, spacing):
+        self.n = n
+        self.BJ = torch.cat([Bt, Jt], dim=-1).reshape(-1, 6)
+        self.d = torch.tensor(spacing, dtype=torch.float64)
+        self.cmax = torch.tensor([n[0] - 2, n[1] - 2, n[2] - 2], dtype=torch.float64)
+        nx, ny, _ = n
+        self.off = [(m, q, p, (p * ny + q) * nx + m) for m in (0, 1) for q in (0, 1) for p in (0, 1)]
+
+    def interp(self, xi):
+        nx, ny, _ = self.n
+        with torch.no_grad():
+            c = torch.nan_to_num(torch.floor(xi), nan=0.0)
+            c = torch.minimum(torch.maximum(c, torch.zeros_like(c)), self.cmax)
+            ci = c.long()
+            base = (ci[:, 2] * ny + ci[:, 1]) * nx + ci[:, 0]
+            nodes = torch.stack([base + o for (_, _, _, o) in self.off], dim=1)
+        w1 = xi - c
+        w0 = 1.0 - w1
+        wts = torch.stack([(w1[:, 0] if m else w0[:, 0]) * (w1[:, 1] if q else w0[:, 1]) *
+                           (w1[:, 2] if p else w0[:, 2]) for (m, q, p, _) in self.off], dim=1)
+        vals = self.BJ[nodes]  # (k, 8, 6)
+        out = (wts[:, :, None] * vals).sum(1)
+        return out[:, :3], out[:, 3:]
+
+    def rhs(self, xi, sigma):
+        """Index-space line equation: F = sigma bt/|bt| (bt_a = B_a/d_a), and
+        the Tw integrand (J.B)/(4 pi B^2) dl/dtau with dl/dtau = |B|/|bt|."""
+        Bi, Ji = self.interp(xi)
+        bt = Bi / self.d
+        nbt = torch.sqrt((bt * bt).sum(-1))
+        BB = (Bi * Bi).sum(-1)
+        F = sigma[:, None] * bt / nbt[:, None]
+        dl = torch.sqrt(BB) / nbt
+        dtw = (Ji * Bi).sum(-1) / (4.0 * math.pi * BB) * dl
+        return F, dtw
+
+
+def _rk4(fld, x, h, sig, ax=None):
+    """One Fehlberg step of the 4th-order solution from x. With ax (face axis
+    per lane) the independent variable is that index coordinate (exit step):
+    the RHS is divided by its ax component."""
+    ks, ts = [], []
+    for s in range(6):
+        acc = sum(_A[s][r] * ks[r] for r in range(s)) if s else torch.zeros_like(x)
+        F, dtw = fld.rhs(x + h[:, None] * acc, sig)
+        if ax is not None:
+            fa = F.gather(1, ax[:, None])[:, 0]
+            F, dtw = F / fa[:, None], dtw / fa
+        ks.append(F)
+        ts.append(dtw)
+    x4 = x + h[:, None] * sum(_B4[s] * ks[s] for s in range(6))
+    dtw4 = h * sum(_B4[s] * ts[s] for s in range(6))
+    return x4, dtw4
+
+
+def half_lines(log):
+    """Split each line's record into its two directions (half-lines 2i, 2i+1,
+    i.e. end 1 and end 2): codes and step sizes, padded with code -1."""
+    m = len(log["n"])
+    seqs = []
+    for i in range(m):
+        codes, hs = log["code"][i, :log["n"][i]], log["h"][i, :log["n"][i]]
+        starts = [k for k in range(len(codes)) if codes[k] == START]
+        for e in range(2):
+            if e < len(starts):
+                k1 = starts[e + 1] if e + 1 < len(starts) else len(codes)
+                seqs.append((codes[starts[e] + 1:k1], hs[starts[e] + 1:k1]))
+            else:
+                seqs.append((np.zeros(0, np.int32), np.zeros(0)))
+    T = max((len(c) for c, _ in seqs), default=0)
+    code = np.full((2 * m, T), -1, np.int64)
+    hh = np.zeros((2 * m, T))
+    for k, (c, h) in enumerate(seqs):
+        code[k, :len(c)] = c
+        hh[k, :len(c)] = h
+    return code, hh
+
+
+def replay(fld, xi0, s0, log):
+    """Replay the frozen step sequences from the seeds xi0 (m, 3). Returns the
+    end positions (m, 2, 3) in index coordinates and Tw of each direction
+    (m, 2). End 1 (half-line 2i) is traced along -s0 B."""
+    m = xi0.shape[0]
+    code, hh = half_lines(log)
+    H, T = code.shape
+    sig = torch.stack([-s0, s0], dim=1).reshape(H)
+    n = fld.n
+    hi = torch.tensor([n[0] - 1.0, n[1] - 1.0, n[2] - 1.0], dtype=torch.float64)
+    xi = xi0.repeat_interleave(2, dim=0)
+    tw = torch.zeros(H, dtype=torch.float64)
+    for t in range(T):
+        ct = code[:, t]
+        # accepted steps inside the box
+        i_n = np.nonzero(ct == STEP)[0]
+        if len(i_n):
+            idx = torch.from_numpy(i_n)
+            x4, d4 = _rk4(fld, xi[idx], torch.from_numpy(hh[i_n, t]), sig[idx])
+            xi = xi.index_put((idx,), x4)
+            tw = tw.index_put((idx,), tw[idx] + d4)
+        # exit steps (independent variable = face-normal coordinate, Sec. 2.1)
+        i_e = np.nonzero(((ct >= EXIT) & (ct < EXIT + 6)) | ((ct >= EXIT_CLAMPED) & (ct < EXIT_CLAMPED + 6)))[0]
+        if len(i_e):
+            idx = torch.from_numpy(i_e)
+            face = torch.from_numpy(np.where(ct[i_e] >= EXIT_CLAMPED, ct[i_e] - EXIT_CLAMPED, ct[i_e] - EXIT))
+            ax = face // 2
+            target = torch.where(face % 2 == 1, hi[ax], torch.zeros(len(i_e), dtype=torch.float64))
+            x = xi[idx]
+            delta = target - x.gather(1, ax[:, None])[:, 0]
+            xe, de = _rk4(fld, x, delta, sig[idx], ax)
+            onehot = torch.nn.functional.one_hot(ax, 3).to(torch.bool)
+            xe = torch.where(onehot, target[:, None], xe)
+            xe = torch.minimum(torch.maximum(xe, torch.zeros_like(xe)), hi)  # the clamp of code 40+
+            xi = xi.index_put((idx,), xe)
+            tw = tw.index_put((idx,), tw[idx] + de)
+        # chord fallback after an exiting step of size h
+        i_c = np.nonzero((ct >= CHORD) & (ct < CHORD + 6))[0]
+        if len(i_c):
+            idx = torch.from_numpy(i_c)
+            face = torch.from_numpy(ct[i_c] - CHORD)
+            ax = face // 2
+            target = torch.where(face % 2 == 1, hi[ax], torch.zeros(len(i_c), dtype=torch.float64))
+            x = xi[idx]
+            x4, d4 = _rk4(fld, x, torch.from_numpy(hh[i_c, t]), sig[idx])
+            xa, x4a = x.gather(1, ax[:, None])[:, 0], x4.gather(1, ax[:, None])[:, 0]
+            t0 = (target - xa) / (x4a - xa)
+            onehot = torch.nn.functional.one_hot(ax, 3).to(torch.bool)
+            xc = torch.where(onehot, target[:, None], x + t0[:, None] * (x4 - x))
+            xi = xi.index_put((idx,), xc)
+            tw = tw.index_put((idx,), tw[idx] + t0 * d4)
+    return xi.reshape(m, 2, 3), tw.reshape(m, 2)
+
+
+def stencils(faces, status, nu, nv, du, dv):
+    """Method I difference coefficients (reading R8) chosen from the traced
+    faces: a list of (seed, end, lattice axis, line, coefficient) with
+    J_e[r][c](seed) = sum coefficient * face coordinate r of that line's end e;
+    and the seeds left MIXED (no usable neighbour on some axis)."""
+    m = nu * nv
+    ok = (status & BAD) == 0
+    entries = []
+    mixed = np.zeros(m, bool)
+    for s in range(m):
+        if not ok[s]:
+            continue
+        i, j = s % nu, s // nu
+        for e in range(2):
+            fe = faces[s, e]
+            for c, (di, dj, dl) in enumerate(((1, 0, du), (0, 1, dv))):
+                def usable(ii, jj):
+                    if not (0 <= ii < nu and 0 <= jj < nv):
+                        return None
+                    k = ii + nu * jj
+                    return k if ok[k] and faces[k, e] == fe else None
+                kp, km = usable(i + di, j + dj), usable(i - di, j - dj)
+                if kp is not None and km is not None:
+                    entries += [(s, e, c, kp, 0.5 / dl), (s, e, c, km, -0.5 / dl)]
+                elif kp is not None:
+                    entries += [(s, e, c, kp, 1.0 / dl), (s, e, c, s, -1.0 / dl)]
+                elif km is not None:
+                    entries += [(s, e, c, s, 1.0 / dl), (s, e, c, km, -1.0 / dl)]
+                else:
+                    mixed[s] = True
+    return entries, mixed
+
+
+_FACE_AXES = {0: (1, 2), 1: (0, 2), 2: (0, 1)}
+
+
+def seeds_index(grid, origin, u, v, nu, nv):
+    """Index-space lattice seeds o + (i+1/2) u + (j+1/2) v, i fastest."""
+    ii = np.arange(nu * nv) % nu
+    jj = np.arange(nu * nv) // nu
+    r0 = (np.asarray(origin, float)[None] + (ii + 0.5)[:, None] * np.asarray(u, float)[None]) + \
+        (jj + 0.5)[:, None] * np.asarray(v, float)[None]
+    return (r0 - np.asarray(grid.origin, float)) / np.asarray(grid.spacing, float)
+
+
+def qmap_t(Bt, grid, origin, u, v, nu, nv, log):
+    """Q and Tw of the lattice (differentiable in the tensor Bt) from the
+    frozen step sequence in log. Returns (Q, Tw, usable mask, end positions)."""
+    n = grid.n
+    Jt = curl_t(Bt, grid.spacing)
+    fld = _Field(Bt, Jt, n, grid.spacing)
+    m = nu * nv
+    xi0 = torch.from_numpy(seeds_index(grid, origin, u, v, nu, nv))
+    s0 = torch.from_numpy(log["s0"])
+    xi, tw = replay(fld, xi0, s0, log)
+    faces, status = log["faces"], log["status"]
+    good = (status & BAD) == 0
+    o = torch.tensor(grid.origin, dtype=torch.float64)
+    phys = o + fld.d * xi  # (m, 2, 3)
+    rows = []
+    for e in range(2):
+        for r in range(2):
+            idx = torch.from_numpy(np.array([_FACE_AXES[max(faces[s, e], 0) // 2][r] for s in range(m)]))
+            rows.append(phys[:, e, :].gather(1, idx[:, None])[:, 0])
+    fc = torch.stack(rows, dim=1).reshape(m, 2, 2)  # line, end, face row
+    du, dv = float(np.linalg.norm(u)), float(np.linalg.norm(v))
+    entries, mixed = stencils(faces, status, nu, nv, du, dv)
+    Jm = torch.zeros((m, 2, 2, 2), dtype=torch.float64)  # seed, end, face row r, lattice axis c
+    if entries:
+        es = np.array(entries, dtype=float)
+        s_i, e_i, c_i, l_i = (torch.from_numpy(es[:, k].astype(np.int64)) for k in range(4))
+        coef = torch.from_numpy(es[:, 4])
+        for r in range(2):
+            Jm = Jm.index_put((s_i, e_i, torch.full_like(s_i, r), c_i), coef * fc[l_i, e_i, r], accumulate=True)
+    J1, J2 = Jm[:, 0], Jm[:, 1]
+    adj = torch.stack([torch.stack([J1[:, 1, 1], -J1[:, 0, 1]], -1),
+                       torch.stack([-J1[:, 1, 0], J1[:, 0, 0]], -1)], 1)
+    M = torch.einsum("srk,skc->src", J2, adj)
+    norm2 = (M * M).sum((1, 2))
+    Bend, _ = fld.interp(xi.reshape(-1, 3))
+    Bend = Bend.reshape(m, 2, 3)
+    fax = torch.from_numpy(np.maximum(faces, 0) // 2)
+    bn1 = Bend[:, 0].gather(1, fax[:, 0:1])[:, 0]
+    bn2 = Bend[:, 1].gather(1, fax[:, 1:2])[:, 0]
+    n0 = np.cross(np.asarray(u, float), np.asarray(v, float))
+    n0 = torch.from_numpy(n0 / np.linalg.norm(n0))
+    B0, _ = fld.interp(xi0)
+    bn0 = (B0 * n0).sum(-1)
+    Q = norm2 * torch.abs(bn1 * bn2) / (bn0 * bn0)
+    usable = torch.from_numpy(good & ~mixed & ((status & ROTATED) == 0))
+    return Q, tw.sum(1), usable, xi
+
+
+def log_q_tw_loss(Q, Tw, Qt, Twt, usable, wtw=0.1):
+    """mean over usable seeds of (log10 Q - log10 Q_t)^2 + wtw (Tw - Tw_t)^2;
+    a seed counts when its line is good, not MIXED, and its Q, Q_t are
+    positive and finite and Tw, Tw_t finite."""
+    qt = torch.as_tensor(np.asarray(Qt, float))
+    twt = torch.as_tensor(np.asarray(Twt, float))
+    with torch.no_grad():
+        use = usable & torch.isfinite(qt) & (qt > 0) & torch.isfinite(Q) & (Q > 0) & torch.isfinite(Tw) & \
+            torch.isfinite(twt)
+    k = max(int(use.sum()), 1)
+    lq = torch.log10(Q[use]) - torch.log10(qt[use])
+    return (lq * lq + wtw * (Tw[use] - twt[use]) ** 2).sum() / k, use
+
+
+def loss_grad(B, grid, origin, u, v, nu, nv, Qt, Twt, p=None, wtw=0.1, log=None):
+    """Loss and d(loss)/dB (shape of B) of the frozen-sequence map."""
+    p = p or params()
+    B = _f64(B)
+    log = lattice_log(B, grid, origin, u, v, nu, nv, p) if log is None else log
+    Bt = torch.tensor(B, dtype=torch.float64, requires_grad=True)
+    Q, Tw, usable, _ = qmap_t(Bt, grid, origin, u, v, nu, nv, log)
+    loss, use = log_q_tw_loss(Q, Tw, Qt, Twt, usable, wtw)
+    loss.backward()
+    return float(loss.detach()), Bt.grad.numpy(), dict(Q=Q.detach().numpy(), Tw=Tw.detach().numpy(), use=use.numpy(),
+                                              log=log)
+
+
+def vjp(B, grid, origin, u, v, nu, nv, wQ, wTw, p=None, log=None):
+    """J^T w = d(sum of wQ Q + wTw Tw over usable seeds)/dB of the
+    frozen-sequence map."""
+    p = p or params()
+    B = _f64(B)
+    log = lattice_log(B, grid, origin, u, v, nu, nv, p) if log is None else log
+    Bt = torch.tensor(B, dtype=torch.float64, requires_grad=True)
+    Q, Tw, usable, _ = qmap_t(Bt, grid, origin, u, v, nu, nv, log)
+    wq = torch.as_tensor(np.asarray(wQ, float))
+    wt = torch.as_tensor(np.asarray(wTw, float))
+    s = (wq[usable] * Q[usable]).sum() + (wt[usable] * Tw[usable]).sum()
+    s.backward()
+    return Bt.grad.numpy(), log
+
+
+def jvp(B, grid, origin, u, v, nu, nv, dB, p=None, log=None):
+    """Tangent-linear mode J v: the directional derivatives (dQ, dTw) of the
+    frozen-sequence map along dB (forward-mode AD), and the usable mask."""
+    import torch.autograd.forward_ad as fwAD
+
+    p = p or params()
+    B = _f64(B)
+    log = lattice_log(B, grid, origin, u, v, nu, nv, p) if log is None else log
+    with fwAD.dual_level():
+        Bt = fwAD.make_dual(torch.tensor(B, dtype=torch.float64), torch.tensor(_f64(dB)))
+        Q, Tw, usable, _ = qmap_t(Bt, grid, origin, u, v, nu, nv, log)
+        dQ = fwAD.unpack_dual(Q).tangent
+        dTw = fwAD.unpack_dual(Tw).tangent
+        out = (dQ.numpy().copy(), dTw.numpy().copy(), usable.numpy())
+    return out + (log,)
+
+
+def free_loss(B, grid, origin, u, v, nu, nv, Qt, Twt, use, p=None, wtw=0.1):
+    """The same loss from a free re-trace with the C oracle (step sizes chosen
+    afresh), over a fixed seed mask: for finite differences of the true map."""
+    p = p or params()
+    o = plane(B, grid, origin, u, v, nu, nv, p)
+    q, tw = o["Q"][use], o["Tw"][use]
+    lq = np.log10(q) - np.log10(np.asarray(Qt)[use])
+    return float(np.sum(lq * lq + wtw * (tw - np.asarray(Twt)[use]) ** 2) / max(int(use.sum()), 1))

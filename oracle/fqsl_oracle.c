@@ -89,6 +89,15 @@
  *       evaluation), STALL 4, MIXED 8, OUTSIDE 16 (seed outside the box),
  *       ROTATED 32, CHORD 64. Q and Tw are NaN when MAXSTEPS, NULL_B or OUTSIDE
  *       is set; Q is NaN when MIXED is set.
+ *   R13 Derivatives (the paper has none; the adjoint tests): d(Q, Tw)/dB is
+ *       that of the traced computation with each line's accepted step sizes,
+ *       exit faces and exit kinds (exit step, clamped exit step, chord after
+ *       an exiting step of size h) frozen; rejected trials then contribute
+ *       nothing. Everything else -- the curl grid, stage positions, the exit
+ *       step's length to the face, the chord parameter, Bn at the seed and at
+ *       both ends, the finite-difference stencils' values -- varies with B.
+ *       oracle_lattice_log exports the frozen sequence; oracle/adjoint.py
+ *       replays and differentiates it.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -136,6 +145,29 @@ typedef struct {
     long long steps;
     int status;
 } OLine;
+
+/* Optional record of the accepted steps of a line (for the adjoint tests):
+ * code 99 starts a direction (h = its sign), 0 is an accepted step of size h,
+ * 16 + face the exit step onto that face, 40 + face the same when the point
+ * had to be clamped into the box, 48 + face a chord fallback after an exiting
+ * step of size h. */
+typedef struct {
+    double *h;
+    int *code;
+    int cap, n, overflow;
+} OLog;
+
+static void o_log(OLog *g, double h, int code)
+{
+    if (!g) return;
+    if (g->n >= g->cap) {
+        g->overflow = 1;
+        return;
+    }
+    g->h[g->n] = h;
+    g->code[g->n] = code;
+    g->n++;
+}
 
 /* ------------------------------------------------------------------ */
 /* node differences (R4) and the curl / B-hat gradient grids           */
@@ -390,8 +422,9 @@ static int o_chord_face(const OField *f, const double *y, const double *yn, doub
 /* Trace one direction from the seed state; writes the end state and face.
  * Returns nonzero when the line must stop with a bad status. */
 static int o_trace_dir(const OField *f, const OParams *p, double tol, double sigma, int ns, const double *yseed,
-                       double *yend, int *face, long long *steps, int *status)
+                       double *yend, int *face, long long *steps, int *status, OLog *log)
 {
+    o_log(log, sigma, 99);
     double y[NSTATE], y4[NSTATE], y5[NSTATE], yt[NSTATE];
     memcpy(y, yseed, sizeof(double) * ns);
     double h = p->h0;
@@ -423,6 +456,7 @@ static int o_trace_dir(const OField *f, const OParams *p, double tol, double sig
         if (hn < p->hmin) hn = p->hmin;
         if (hn > p->hmax) hn = p->hmax;
         if (o_inside(f, y4)) {
+            o_log(log, h, 0);
             memcpy(y, y4, sizeof(double) * ns);
             h = hn;
             continue;
@@ -453,6 +487,7 @@ static int o_trace_dir(const OField *f, const OParams *p, double tol, double sig
                 else if (yt[b] > (double)(f->n[b] - 1)) nf = 2 * b + 1;
             }
             if (nf < 0) {
+                o_log(log, 0.0, 16 + fc);
                 memcpy(yend, yt, sizeof(double) * ns);
                 *face = fc;
                 return 0;
@@ -462,6 +497,7 @@ static int o_trace_dir(const OField *f, const OParams *p, double tol, double sig
                     if (yt[b] < 0.0) yt[b] = 0.0;
                     if (yt[b] > (double)(f->n[b] - 1)) yt[b] = (double)(f->n[b] - 1);
                 }
+                o_log(log, 0.0, 40 + fc);
                 memcpy(yend, yt, sizeof(double) * ns);
                 *face = fc;
                 return 0;
@@ -475,6 +511,7 @@ static int o_trace_dir(const OField *f, const OParams *p, double tol, double sig
             }
             for (int c = 0; c < ns; c++) yend[c] = y[c] + t0 * (y4[c] - y[c]);
             yend[fc0 >> 1] = o_face_value(f, fc0);
+            o_log(log, h, 48 + fc0);
             *face = fc0;
             *status |= ST_CHORD;
             return 0;
@@ -486,8 +523,8 @@ static int o_trace_dir(const OField *f, const OParams *p, double tol, double sig
  * -n0 side of S0 (reached along -s0 B with s0 = sign(B(r0) . n0), +1 when the
  * product is 0 or n0 is NULL), end 2 the other one; end 1 is traced first.
  * U0/V0 may be NULL. */
-static void o_trace_line(const OField *f, const OParams *p, const double r0[3], const double *n0, double tol,
-                         const double *U0, const double *V0, OLine *L)
+static void o_trace_line_log(const OField *f, const OParams *p, const double r0[3], const double *n0, double tol,
+                             const double *U0, const double *V0, OLine *L, OLog *log, double *s0out)
 {
     int ns = (U0 && V0) ? NSTATE : 5;
     double y0[NSTATE];
@@ -517,9 +554,16 @@ static void o_trace_line(const OField *f, const OParams *p, const double r0[3], 
         o_interp(f, f->B, 3, y0, B0);
         if (B0[0] * n0[0] + B0[1] * n0[1] + B0[2] * n0[2] < 0.0) s0 = -1.0;
     }
-    if (o_trace_dir(f, p, tol, -s0, ns, y0, L->end[0], &L->face[0], &L->steps, &L->status)) return;
-    if (o_trace_dir(f, p, tol, +s0, ns, y0, L->end[1], &L->face[1], &L->steps, &L->status)) return;
+    if (s0out) *s0out = s0;
+    if (o_trace_dir(f, p, tol, -s0, ns, y0, L->end[0], &L->face[0], &L->steps, &L->status, log)) return;
+    if (o_trace_dir(f, p, tol, +s0, ns, y0, L->end[1], &L->face[1], &L->steps, &L->status, log)) return;
     for (int e = 0; e < 2; e++) o_interp(f, f->B, 3, L->end[e], L->Bend[e]);
+}
+
+static void o_trace_line(const OField *f, const OParams *p, const double r0[3], const double *n0, double tol,
+                         const double *U0, const double *V0, OLine *L)
+{
+    o_trace_line_log(f, p, r0, n0, tol, U0, V0, L, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------ */
@@ -850,4 +894,55 @@ int oracle_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* Every line of a plane lattice traced once, with the record of its accepted
+ * steps (OLog codes; at most cap entries per line, logn[s] = -1 on overflow),
+ * its orientation sign s0, tolerance, Bn0, end states (s x 2 x 11), faces and
+ * status. Used by the adjoint tests to replay the frozen step sequence. */
+int oracle_lattice_log(const double *B, const double *J, const long long n[3], const double o[3], const double d[3],
+                       const double lo[3], const double a1[3], const double a2[3], const long long ln[2],
+                       const OParams *p, int cap, double *logh, int *logc, int *logn, double *s0o, double *tolo,
+                       double *bn0o, double *ends, int *faces, int *st)
+{
+    OField f;
+    if (o_make_field(&f, B, J, NULL, n, o, d)) return 1;
+    if (p->method != 1) return 2;
+    OLattice L;
+    for (int a = 0; a < 3; a++) {
+        L.o[a] = lo[a];
+        L.a1[a] = a1[a];
+        L.a2[a] = a2[a];
+        L.a3[a] = 0.0;
+    }
+    L.n1 = ln[0];
+    L.n2 = ln[1];
+    L.n3 = 1;
+    long long total = L.n1 * L.n2;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long s = 0; s < total; s++) {
+        long long i = s % L.n1, j = s / L.n1;
+        OSeed S;
+        OLine c;
+        OLog g = {logh + s * cap, logc + s * cap, cap, 0, 0};
+        double s0 = 1.0;
+        o_seed_setup(&f, p, &L, i, j, 0, &S);
+        memset(&c, 0, sizeof c);
+        c.face[0] = c.face[1] = -1;
+        if (S.bad) {
+            c.status = S.bad;
+        } else {
+            o_trace_line_log(&f, p, S.r0, S.n0, S.tol, NULL, NULL, &c, &g, &s0);
+            if (S.rotated) c.status |= ST_ROTATED;
+        }
+        logn[s] = g.overflow ? -1 : g.n;
+        s0o[s] = s0;
+        tolo[s] = S.tol;
+        bn0o[s] = S.bn0;
+        memcpy(ends + s * 2 * NSTATE, c.end, sizeof c.end);
+        faces[2 * s] = c.face[0];
+        faces[2 * s + 1] = c.face[1];
+        st[s] = c.status;
+    }
+    return 0;
 }

@@ -20,4 +20,5 @@ from .fields import (  # noqa: F401
     C1_GRID,
     c2_monopole,
     large_monopole,
+    adjoint_cubes,
 )

@@ -267,3 +267,20 @@ def batch_specs(seed: int = 2208, count: int = 48, seeds_uv=(512, 256)):
                          v=(0.0, 0.0, (n[2] - 1.0) / nv), nu=nu, nv=nv)
         specs.append(dict(grid=grid, charges=ch, plane=plane))
     return specs
+
+
+def adjoint_cubes(seed: int = 2208, n=(128, 128, 64), count: int = 24, turns: float = 1.5,
+                  radius_cells: float = 10.0, rel: float = 0.05, dtype=np.float32):
+    """The differentiation workload: a monopole potential field (``count``
+    buried sources, depths 4..16 cells scaled by nx/128, unit spacing) plus a
+    vertical rigid-twist tube (``turns`` over the box height, radius
+    ``radius_cells``), and the target cube: the same sources with strengths
+    scaled by (1 + rel N(0,1)) under the same tube. Returns (B, B_target, grid)."""
+    grid = Grid(tuple(n), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    rng = np.random.default_rng(seed)
+    s = n[0] / 128.0
+    ch = random_charges(rng, count, ((0.0, n[0] - 1.0), (0.0, n[1] - 1.0)), depth=(4.0 * s, 16.0 * s))
+    cht = perturbed_charges(ch, rng, rel)
+    B, _ = twist_tube_cube(grid, ch, turns=turns, radius_cells=radius_cells, dtype=dtype)
+    Bt, _ = twist_tube_cube(grid, cht, turns=turns, radius_cells=radius_cells, dtype=dtype)
+    return B, Bt, grid
