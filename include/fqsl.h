@@ -108,6 +108,10 @@ typedef struct {
                              (1..64; 0 = default 1; batches always take 1). Results do not depend on it. */
     int blocks_per_sm;    /* scheduling: resident 128-thread blocks per SM of the persistent tracer
                              (0 = as many as fit). Results do not depend on it. */
+    int tape;             /* 1: fqsl_qmap_plane (Method I) also records the step tape that fqsl_backward
+                             differentiates (0 = default, no tape). Results do not depend on it. */
+    int tape_chunk;       /* steps per tape chunk, i.e. the checkpoint interval k of the reverse sweep
+                             (1..64; 0 = default 16) */
 } fqsl_params;
 
 /* Output buffers of one call (caller-owned device memory, n = number of
@@ -262,6 +266,53 @@ FQSL_API fqsl_status fqsl_batch_destroy(fqsl_batch batch);
 FQSL_API fqsl_status fqsl_qmap_plane_static(fqsl_field field, const double origin[3], const double u[3],
                                             const double v[3], long long nu, long long nv,
                                             const fqsl_params *params, const fqsl_out *out, void *cuda_stream);
+
+/* Reverse mode (the paper has no derivative; this is the discrete adjoint of
+ * the computation it defines). For the plane map that fqsl_qmap_plane last
+ * traced on this field with params->tape = 1 (Method I), accumulate
+ *   dB += d/dB ( sum_s dQ[s] Q[s] + dTw[s] Tw[s] )
+ * where the derivative is that of the traced computation with each line's
+ * accepted step sizes, exit faces and exit kinds (exit step onto a face, the
+ * same with the point clamped into the box, chord after an exiting step)
+ * frozen at their traced values -- so rejected trials contribute nothing --
+ * while every position, stage value (Sec. 2.3), trilinear weight (Sec. 2.2,
+ * Eq. interp), exit-step length, chord parameter, Bn at the seed and at both
+ * ends (Eq. Bn1), the Method I difference stencils' values (Eqs. D+-2, D+-3)
+ * and the curl grid (Eq. tw) vary with B.
+ *   dQ_dev, dTw_dev  double[nu*nv] per-seed weights in the map's output order
+ *                    (either may be NULL = 0). Seeds whose Q is NaN (status
+ *                    MAXSTEPS, NULL_B, OUTSIDE or MIXED) or whose S0 was
+ *                    rotated (ROTATED: their Q comes from four extra lines
+ *                    that are not taped) contribute nothing through Q; NaN
+ *                    or infinite weights count as 0.
+ *   dB_dev           B-shaped array (layout of fqsl_field_create) of db_dtype
+ *                    (FQSL_F32 or FQSL_F64), accumulated into, not cleared.
+ * The state is recomputed in the taped call's precision from checkpoints
+ * every params->tape_chunk accepted steps; the node adjoints accumulate in
+ * float (FQSL_F32) or double (FQSL_F32_ACC64, FQSL_F64). The field must not
+ * be updated between the taped call and this one. The call synchronises
+ * cuda_stream once (to confirm that the tape's chunk pool sufficed; if it did
+ * not, it traces the map again with a larger pool), so it cannot be captured
+ * in a CUDA graph. With timing enabled, fqsl_field_times reports ms[0] =
+ * reverse sweep, ms[1] = 0, ms[2] = curl transpose. Errors: FQSL_ERR_ARG (no
+ * taped map, NULL or misaligned pointers, db_dtype), FQSL_ERR_OOM,
+ * FQSL_ERR_CUDA. */
+FQSL_API fqsl_status fqsl_backward(fqsl_field field, const double *dQ_dev, const double *dTw_dev, void *dB_dev,
+                                   fqsl_dtype db_dtype, void *cuda_stream);
+
+/* The log-Q / Tw misfit of two maps and its gradient (a loss for
+ * fqsl_backward; the paper has no counterpart):
+ *   loss = (1/m) sum over usable seeds of (log10 Q - log10 Q_t)^2 + w_tw (Tw - Tw_t)^2,
+ * usable = Q, Q_t, Tw, Tw_t finite, Q > 0, Q_t > 0 and (status_dev given) no
+ * MAXSTEPS, NULL_B, OUTSIDE, MIXED or ROTATED bit; m = their number (1 if
+ * none). Writes *loss_dev and dQ_dev[s], dTw_dev[s] = d loss / d Q[s], Tw[s]
+ * (0 for seeds not usable; loss_dev, dQ_dev, dTw_dev may be NULL). sums_dev:
+ * double[2] scratch of the caller. All pointers are device pointers of n
+ * elements (status_dev may be NULL). Errors: FQSL_ERR_ARG, FQSL_ERR_CUDA. */
+FQSL_API fqsl_status fqsl_loss_logq_tw(long long n, const double *Q_dev, const double *Tw_dev,
+                                       const double *Qt_dev, const double *Twt_dev, const uint8_t *status_dev,
+                                       double w_tw, double *sums_dev, double *loss_dev, double *dQ_dev,
+                                       double *dTw_dev, void *cuda_stream);
 
 /* Synchronise cuda_stream and report device-side failures recorded by earlier
  * calls on this field (FQSL_ERR_TIMEOUT if a bounded loop gave up). The

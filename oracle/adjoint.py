@@ -348,16 +348,18 @@ def loss_grad(B, grid, origin, u, v, nu, nv, Qt, Twt, p=None, wtw=0.1, log=None)
 
 
 def vjp(B, grid, origin, u, v, nu, nv, wQ, wTw, p=None, log=None):
-    """J^T w = d(sum of wQ Q + wTw Tw over usable seeds)/dB of the
-    frozen-sequence map."""
+    """J^T w = d(sum of wQ Q over usable seeds + wTw Tw over good lines)/dB of
+    the frozen-sequence map (Q of MIXED or rotated seeds is not used; Tw of
+    every line without MAXSTEPS, NULL_B or OUTSIDE is)."""
     p = p or params()
     B = _f64(B)
     log = lattice_log(B, grid, origin, u, v, nu, nv, p) if log is None else log
     Bt = torch.tensor(B, dtype=torch.float64, requires_grad=True)
     Q, Tw, usable, _ = qmap_t(Bt, grid, origin, u, v, nu, nv, log)
+    good = torch.from_numpy((log["status"] & BAD) == 0)
     wq = torch.as_tensor(np.asarray(wQ, float))
     wt = torch.as_tensor(np.asarray(wTw, float))
-    s = (wq[usable] * Q[usable]).sum() + (wt[usable] * Tw[usable]).sum()
+    s = (wq[usable] * Q[usable]).sum() + (wt[good] * Tw[good]).sum()
     s.backward()
     return Bt.grad.numpy(), log
 

@@ -4,6 +4,6 @@ the CUDA library libfqsl.so (C ABI in include/fqsl.h); ``fqsl`` is its Python
 binding."""
 from .fqsl import (  # noqa: F401
     F32, F32_ACC64, F64, LINE_BAD, LINE_CHORD, LINE_MAXSTEPS, LINE_MIXED, LINE_NULL_B, LINE_OUTSIDE, LINE_ROTATED, LINE_STALL,
-    Batch, Field, FqslError, STATIC_MAX_SEEDS, alloc_out, params, qmap_plane, qmap_plane_static, qmap_volume, twist,
-    version,
+    Batch, Field, FqslError, QTwPlane, STATIC_MAX_SEEDS, alloc_out, backward, loss_logq_tw, params, qmap_plane,
+    qmap_plane_static, qmap_volume, twist, version,
 )

@@ -66,8 +66,21 @@ struct fqsl_field_s {
     unsigned long long *counters = nullptr;  // [0] primary head, [1] extra head, [2] rotated count (low 32 bits)
     int blocks_cache[3][3] = {};  // [precision][source] resident blocks per SM
     int blocks_cache_m2[2][2] = {};  // Method II: [fp64][way - 1]
+    int blocks_cache_tape[3] = {};   // taped lattice tracer: [precision]
+    int blocks_cache_rev[3] = {};    // adjoint reverse sweep: [precision]
     bool timing = false, timed = false, extra_timed = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // the last plane map traced with params->tape = 1 (for fqsl_backward): its
+    // records, step tape and adjoint buffers live in tape_buf
+    struct {
+        bool valid = false;
+        Lattice lat{};
+        fqsl_params p{};
+        bool face_plane = false;
+        long long pool = 0;  // tape chunks of the next taped call
+        void *buf = nullptr;
+        size_t cap = 0;
+    } tp;
     std::mutex mu;
 };
 
@@ -258,6 +271,7 @@ fqsl_status fqsl_field_destroy(fqsl_field f)
     cudaFree(f->grad32);
     cudaFree(f->grad64);
     cudaFree(f->scratch);
+    cudaFree(f->tp.buf);
     cudaFree(f->counters);
     delete f;
     return FQSL_OK;
@@ -298,6 +312,8 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
     if (p->sync_dirs < -1 || p->sync_dirs > 1) return fail(FQSL_ERR_ARG, "%s: sync_dirs in {-1, 0, 1}", who);
     if (p->chunk_tiles < 0 || p->chunk_tiles > 64) return fail(FQSL_ERR_ARG, "%s: chunk_tiles in [0, 64]", who);
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 64) return fail(FQSL_ERR_ARG, "%s: blocks_per_sm in [0, 64]", who);
+    if (p->tape != 0 && p->tape != 1) return fail(FQSL_ERR_ARG, "%s: tape must be 0 or 1", who);
+    if (p->tape_chunk < 0 || p->tape_chunk > 64) return fail(FQSL_ERR_ARG, "%s: tape_chunk in [0, 64]", who);
     if (p->precision != FQSL_F64 && !f->rec32)
         return fail(FQSL_ERR_UNSUPPORTED, "%s: field was not packed in FP32 (FQSL_PACK_F32)", who);
     if (p->precision == FQSL_F64 && !f->rec64)
@@ -471,9 +487,86 @@ void index_lattice(const fqsl_field f, Lattice &lat)
     }
 }
 
-// Shared body of the plane and volume Q maps.
-fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, const fqsl_out *out,
-                     cudaStream_t stream, bool face_plane, const char *who)
+// Layout of a taped plane map in the field's tape buffer: the line records
+// (as in layout()), counters, the step tape (pool chunks of k steps), the
+// footpoint adjoints, the loss sums and the adjoint node grid.
+struct TapeLayout {
+    Scratch s;
+    unsigned long long *ctr;  // [0] tape chunks handed out, [1] reverse-sweep work counter
+    Tape tape;
+    double *xbar, *sums;
+    void *acc;
+    size_t bytes;
+};
+
+constexpr int kDefaultTapeChunk = 16;
+
+TapeLayout tape_layout(char *base, long long n, bool rot, bool f32, long long pool, int k, size_t nodes,
+                       bool acc64)
+{
+    TapeLayout t{};
+    t.s = layout(base, n, rot, true, f32);
+    Carver c{base ? base + t.s.bytes : nullptr};
+    const size_t ts = f32 ? 4 : 8;
+    t.ctr = c.take<unsigned long long>(4);
+    t.tape.k = k;
+    t.tape.cap = pool;
+    t.tape.next = t.ctr;
+    t.tape.prev = c.take<int32_t>((size_t)pool);
+    t.tape.xi = c.take<char>((size_t)pool * 4 * ts);
+    t.tape.h = c.take<char>((size_t)pool * k * ts);
+    t.tape.head = c.take<int4>((size_t)(2 * n));
+    t.tape.xe = c.take<char>((size_t)(2 * n) * 4 * ts);
+    t.xbar = c.take<double>((size_t)(6 * n));
+    t.sums = c.take<double>(2);
+    t.acc = c.take<char>(nodes * 8 * (acc64 ? 8 : 4));
+    t.bytes = t.s.bytes + c.off;
+    return t;
+}
+
+bool acc64_of(int precision) { return precision != FQSL_F32; }
+
+// the taped map's layout in the field's tape buffer (base NULL: sizes only)
+TapeLayout field_tape_layout(const fqsl_field f, char *base, long long pool)
+{
+    const fqsl_params &p = f->tp.p;
+    const long long n = f->tp.lat.n1 * f->tp.lat.n2;
+    const int k = p.tape_chunk > 0 ? p.tape_chunk : kDefaultTapeChunk;
+    const size_t nodes = (size_t)f->g.nx * f->g.ny * f->g.nz;
+    return tape_layout(base, n, f->tp.lat.allow_rot, p.precision != FQSL_F64, pool, k, nodes,
+                       acc64_of(p.precision));
+}
+
+fqsl_status ensure_tape_buf(fqsl_field f, size_t bytes)
+{
+    if (bytes <= f->tp.cap) return FQSL_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "tape buffer: synchronize");
+    cudaFree(f->tp.buf);
+    f->tp.buf = nullptr;
+    f->tp.cap = 0;
+    e = cudaMalloc(&f->tp.buf, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e, "tape buffer allocation");
+    }
+    f->tp.cap = bytes;
+    return FQSL_OK;
+}
+
+int tape_blocks_per_sm(fqsl_field f, int precision)
+{
+    int &c = f->blocks_cache_tape[precision];
+    if (!c) c = precision == FQSL_F64 ? trace_tape_blocks_per_sm_f64()
+                                      : trace_tape_blocks_per_sm_f32(precision == FQSL_F32_ACC64);
+    return c;
+}
+
+// Shared body of the plane and volume Q maps (the caller holds f->mu). With
+// tape set (plane lattices, Method I) the records live in the field's tape
+// buffer and the lattice tracer also writes the step tape.
+fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params *p, const fqsl_out *out,
+                            cudaStream_t stream, bool face_plane, bool tape, const char *who)
 {
     Lattice lat = lat0;
     index_lattice(f, lat);
@@ -483,14 +576,31 @@ fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, co
     lat.allow_rot = (p->method == 1 && !face_plane) ? 1 : 0;
     const bool f32 = p->precision != FQSL_F64;
     const bool m2 = p->method == 2;
-    std::lock_guard<std::mutex> lock(f->mu);
-    Scratch sz = layout(nullptr, n, lat.allow_rot, true, f32, m2);
-    fqsl_status st = ensure_scratch(f, sz.bytes);
-    if (st != FQSL_OK) return st;
-    Scratch s = layout((char *)f->scratch, n, lat.allow_rot, true, f32, m2);
+    Scratch s;
+    TapeLayout tl{};
+    if (tape) {
+        f->tp.valid = false;
+        f->tp.lat = lat;
+        f->tp.p = *p;
+        f->tp.face_plane = face_plane;
+        const int k = p->tape_chunk > 0 ? p->tape_chunk : kDefaultTapeChunk;
+        // first guess: 128 accepted steps per direction on average
+        const long long guess = 2 * n * (128 / k + 1) + 1024;
+        if (f->tp.pool < guess) f->tp.pool = guess;
+        fqsl_status st = ensure_tape_buf(f, field_tape_layout(f, nullptr, f->tp.pool).bytes);
+        if (st != FQSL_OK) return st;
+        tl = field_tape_layout(f, (char *)f->tp.buf, f->tp.pool);
+        s = tl.s;
+    } else {
+        Scratch sz = layout(nullptr, n, lat.allow_rot, true, f32, m2);
+        fqsl_status st = ensure_scratch(f, sz.bytes);
+        if (st != FQSL_OK) return st;
+        s = layout((char *)f->scratch, n, lat.allow_rot, true, f32, m2);
+    }
 
     cudaError_t e = cudaMemsetAsync(f->counters, 0, 4 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess && lat.allow_rot) e = cudaMemsetAsync(s.rot_slot, 0, (size_t)n * sizeof(int32_t), stream);
+    if (e == cudaSuccess && tape) e = cudaMemsetAsync(tl.ctr, 0, 4 * sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
 
     TraceArgs a{};
@@ -506,6 +616,7 @@ fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, co
     a.q.rot_seed = s.rot_seed;
     a.q.rot_slot = s.rot_slot;
     a.prep = s.prep;
+    a.tape = tl.tape;
     a.nitems = lat.n3 * lat.tiles_u * lat.tiles_v * (long long)(kTileU * kTileV);
     if (f32) {
         e = launch_seed_prep_f32(a, n, stream);
@@ -531,7 +642,18 @@ fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, co
         f->extra_timed = false;
         return FQSL_OK;
     }
-    e = launch_trace(f, p, a, kSrcLattice, a.nitems, stream);
+    if (tape) {
+        int bps = tape_blocks_per_sm(f, p->precision);
+        if (p->blocks_per_sm > 0 && p->blocks_per_sm < bps) bps = p->blocks_per_sm;
+        long long grid = (long long)f->sms * bps;
+        const long long need = (a.nitems + kTraceBlock - 1) / kTraceBlock;
+        if (need < grid) grid = need;
+        if (grid < 1) grid = 1;
+        e = p->precision == FQSL_F64 ? launch_trace_tape_f64(a, (int)grid, stream)
+                                     : launch_trace_tape_f32(a, (int)grid, stream, p->precision == FQSL_F32_ACC64);
+    } else {
+        e = launch_trace(f, p, a, kSrcLattice, a.nitems, stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, who);
     mark(f, 1, stream);
     if (lat.allow_rot) {
@@ -554,7 +676,15 @@ fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, co
     mark(f, 3, stream);
     f->timed = f->timing;
     f->extra_timed = lat.allow_rot != 0;
+    if (tape) f->tp.valid = true;
     return FQSL_OK;
+}
+
+fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, const fqsl_out *out,
+                     cudaStream_t stream, bool face_plane, const char *who, bool tape = false)
+{
+    std::lock_guard<std::mutex> lock(f->mu);
+    return run_qmap_locked(f, lat0, p, out, stream, face_plane, tape, who);
 }
 
 }  // namespace
@@ -606,7 +736,8 @@ fqsl_status fqsl_qmap_plane(fqsl_field f, const double origin[3], const double u
         const double xi = (origin[a] - f->g.o[a]) / f->g.d[a];
         face_plane = (xi == 0.0) || (xi == (double)(na - 1));
     }
-    return run_qmap(f, lat, p, out, (cudaStream_t)cuda_stream, face_plane, who);
+    if (p->tape && p->method != 1) return fail(FQSL_ERR_UNSUPPORTED, "%s: the step tape needs Method I", who);
+    return run_qmap(f, lat, p, out, (cudaStream_t)cuda_stream, face_plane, who, p->tape != 0);
 }
 
 fqsl_status fqsl_qmap_volume(fqsl_field f, const double origin[3], const double step[3], long long nx, long long ny,
@@ -636,6 +767,7 @@ fqsl_status fqsl_qmap_volume(fqsl_field f, const double origin[3], const double 
     lat.dv = step[1];
     lat.drot = fmin(step[0], step[1]);
     lat.normal_axis = 2;
+    if (p->tape) return fail(FQSL_ERR_UNSUPPORTED, "%s: the step tape is recorded for plane maps only", who);
     return run_qmap(f, lat, p, out, (cudaStream_t)cuda_stream, false, who);
 }
 
@@ -646,6 +778,7 @@ fqsl_status fqsl_twist(fqsl_field f, const double *seeds_dev, long long n, const
     const char *who = "fqsl_twist";
     fqsl_status st = check_params(f, p, who);
     if (st != FQSL_OK) return st;
+    if (p->tape) return fail(FQSL_ERR_UNSUPPORTED, "%s: the step tape is recorded for plane maps only", who);
     if (!out) return fail(FQSL_ERR_ARG, "%s: out is NULL", who);
     if (n < 0 || n > (1LL << 31) - 1) return fail(FQSL_ERR_ARG, "%s: n out of range", who);
     if (n == 0) return FQSL_OK;
@@ -736,6 +869,7 @@ extern "C" fqsl_status fqsl_qmap_plane_static(fqsl_field f, const double origin[
     const char *who = "fqsl_qmap_plane_static";
     fqsl_status st = check_params(f, p, who);
     if (st != FQSL_OK) return st;
+    if (p->tape) return fail(FQSL_ERR_UNSUPPORTED, "%s: no step tape without allocation", who);
     if (p->method != 1) return fail(FQSL_ERR_UNSUPPORTED, "%s: Method I only", who);
     if (!out) return fail(FQSL_ERR_ARG, "%s: out is NULL", who);
     if (!finite3(origin) || !finite3(u) || !finite3(v)) return fail(FQSL_ERR_ARG, "%s: non-finite plane", who);
@@ -940,6 +1074,10 @@ extern "C" fqsl_status fqsl_batch_create(const fqsl_field *fields, const fqsl_pl
     b->nent = n;
     b->params = *p;
     std::vector<long long> ibase(n + 1), nbase(n + 1);
+    if (p->tape) {
+        delete b;
+        return fail(FQSL_ERR_UNSUPPORTED, "%s: batches record no step tape", who);
+    }
     for (int k = 0; k < n; k++) {
         fqsl_status st = check_params(fields[k], p, who);
         if (st != FQSL_OK) {
@@ -1083,5 +1221,104 @@ extern "C" fqsl_status fqsl_batch_destroy(fqsl_batch b)
     if (!b) return fail(FQSL_ERR_ARG, "fqsl_batch_destroy: NULL batch");
     cudaDeviceSynchronize();
     batch_free(b);
+    return FQSL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// fqsl_backward: reverse mode of the field's last taped plane map
+// ---------------------------------------------------------------------------
+extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const double *dTw_dev, void *dB_dev,
+                                     fqsl_dtype db_dtype, void *cuda_stream)
+{
+    g_err.clear();
+    const char *who = "fqsl_backward";
+    if (!f) return fail(FQSL_ERR_ARG, "%s: NULL field", who);
+    if (!dB_dev) return fail(FQSL_ERR_ARG, "%s: dB_dev is NULL", who);
+    if (db_dtype != FQSL_F32 && db_dtype != FQSL_F64)
+        return fail(FQSL_ERR_ARG, "%s: db_dtype must be FQSL_F32 or FQSL_F64", who);
+    if (((uintptr_t)dB_dev) % 16) return fail(FQSL_ERR_ARG, "%s: dB_dev must be 16-byte aligned", who);
+    if ((dQ_dev && ((uintptr_t)dQ_dev) % 8) || (dTw_dev && ((uintptr_t)dTw_dev) % 8))
+        return fail(FQSL_ERR_ARG, "%s: dQ_dev and dTw_dev must be 8-byte aligned", who);
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    std::lock_guard<std::mutex> lock(f->mu);
+    if (!f->tp.valid) return fail(FQSL_ERR_ARG, "%s: no taped plane map on this field (params.tape = 1)", who);
+    const fqsl_params p = f->tp.p;
+    // the pool of the taped call must have held every chunk; if not, trace the
+    // same map again with a larger pool (the map is deterministic)
+    for (int attempt = 0;; attempt++) {
+        TapeLayout tl = field_tape_layout(f, (char *)f->tp.buf, f->tp.pool);
+        unsigned long long used = 0;
+        cudaError_t e = cudaMemcpyAsync(&used, tl.ctr, sizeof used, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+        if (used <= (unsigned long long)f->tp.pool) break;
+        if (attempt >= 2) return fail(FQSL_ERR_CUDA, "%s: step tape pool still exhausted after re-tracing", who);
+        f->tp.pool = (long long)(used + used / 4 + 1024);
+        const Lattice lat = f->tp.lat;
+        const fqsl_out none{};
+        fqsl_status st = run_qmap_locked(f, lat, &p, &none, stream, f->tp.face_plane, true, who);
+        if (st != FQSL_OK) return st;
+    }
+    TapeLayout tl = field_tape_layout(f, (char *)f->tp.buf, f->tp.pool);
+    const Lattice &lat = f->tp.lat;
+    const long long n = lat.n1 * lat.n2;
+    const size_t nodes = (size_t)f->g.nx * f->g.ny * f->g.nz;
+    const bool acc64 = acc64_of(p.precision);
+    const int mode = p.precision == FQSL_F64 ? 2 : (acc64 ? 1 : 0);
+    cudaError_t e = cudaMemsetAsync(tl.xbar, 0, (size_t)(6 * n) * sizeof(double), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tl.acc, 0, nodes * 8 * (acc64 ? 8 : 4), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tl.ctr + 1, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    AdjArgs a{};
+    a.f = f->g;
+    a.f.rec = p.precision == FQSL_F64 ? f->rec64 : f->rec32;
+    a.f.grad = nullptr;
+    a.p = dev_params(&p);
+    a.lat = lat;
+    a.rec = tl.s.rec;
+    a.prep = tl.s.prep;
+    a.tape = tl.tape;
+    a.dQ = dQ_dev;
+    a.dTw = dTw_dev;
+    a.xbar = tl.xbar;
+    a.acc = tl.acc;
+    a.head = tl.ctr + 1;
+    a.n = n;
+    e = launch_q_vjp(a, mode, stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    mark(f, 0, stream);
+    int &bps = f->blocks_cache_rev[p.precision];
+    if (!bps) bps = reverse_blocks_per_sm(mode);
+    long long grid = (long long)f->sms * bps;
+    const long long units = lat.tiles_u * lat.tiles_v * 2;
+    const long long need = (units * 32 + 127) / 128;
+    if (need < grid) grid = need;
+    if (grid < 1) grid = 1;
+    e = launch_reverse(a, mode, (int)grid, stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    mark(f, 1, stream);
+    mark(f, 2, stream);
+    e = launch_curl_adjoint(tl.acc, acc64, f->g, dB_dev, db_dtype, stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    mark(f, 3, stream);
+    f->timed = f->timing;
+    f->extra_timed = false;
+    return FQSL_OK;
+}
+
+extern "C" fqsl_status fqsl_loss_logq_tw(long long n, const double *Q_dev, const double *Tw_dev,
+                                         const double *Qt_dev, const double *Twt_dev, const uint8_t *status_dev,
+                                         double w_tw, double *sums_dev, double *loss_dev, double *dQ_dev,
+                                         double *dTw_dev, void *cuda_stream)
+{
+    g_err.clear();
+    const char *who = "fqsl_loss_logq_tw";
+    if (n < 0) return fail(FQSL_ERR_ARG, "%s: n < 0", who);
+    if (!Q_dev || !Tw_dev || !Qt_dev || !Twt_dev || !sums_dev)
+        return fail(FQSL_ERR_ARG, "%s: Q, Tw, Q_target, Tw_target and sums are required", who);
+    if (!isfinite(w_tw)) return fail(FQSL_ERR_ARG, "%s: w_tw must be finite", who);
+    cudaError_t e = launch_loss(n, Q_dev, Tw_dev, Qt_dev, Twt_dev, status_dev, w_tw, sums_dev, loss_dev, dQ_dev,
+                                dTw_dev, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
     return FQSL_OK;
 }

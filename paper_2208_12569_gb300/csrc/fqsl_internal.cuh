@@ -103,6 +103,29 @@ struct Queue {
 
 enum Source { kSrcLattice = 0, kSrcExtra = 1, kSrcList = 2 };
 
+// Step tape of the adjoint's forward pass (lattice lines). Each direction of
+// a line (half-line 2 line + end) stores its accepted step sizes in chunks of
+// k steps taken from a pool by a device counter; a chunk holds the state at
+// its first step (the checkpoint the reverse sweep recomputes from) and the
+// index of the previous chunk of the same half-line. The head of a half-line
+// names its last chunk, the steps used in it, how the direction ended and its
+// orientation; the end record holds the footpoint and, for a chord end, the
+// size of the exiting step. A pool that runs out leaves the counter above cap
+// (the host re-runs with a larger pool).
+constexpr int kTapeExit = 16;         // + face: exit step onto that face
+constexpr int kTapeExitClamped = 40;  // + face: the same, other coordinates clamped into the box
+constexpr int kTapeChord = 48;        // + face: chord fallback after an exiting step of size hx
+struct Tape {
+    int k;                      // steps per chunk
+    long long cap;              // chunks in the pool
+    unsigned long long *next;   // chunks handed out
+    int32_t *prev;              // [cap] previous chunk of the half-line, -1 for its first
+    void *xi;                   // [cap] T[4]: state at the chunk's first step {x, y, z, 0}
+    void *h;                    // [cap * k] T: accepted step sizes
+    int4 *head;                 // [2 n] {last chunk, steps in it, end code, orientation sign}
+    void *xe;                   // [2 n] T[4]: {footpoint x, y, z, exiting step of a chord end}
+};
+
 struct TraceArgs {
     FieldView f;
     DevParams p;
@@ -113,6 +136,7 @@ struct TraceArgs {
     LineRecs ext;         // rotated extra lines, 4 per slot
     Queue q;
     SeedPrep prep;        // FP32 lattice: filled by the seed pre-pass
+    Tape tape;            // adjoint forward pass (lattice lines): the step tape
 };
 
 // A batch: many (field, lattice) entries traced by one launch. Work items are
@@ -136,11 +160,40 @@ struct AssembleArgs {
 
 constexpr unsigned kBad = FQSL_LINE_MAXSTEPS | FQSL_LINE_NULL_B | FQSL_LINE_OUTSIDE;
 
+// Reverse mode of a taped plane map (adjoint.cu).
+struct AdjArgs {
+    FieldView f;       // records of the traced precision
+    DevParams p;
+    Lattice lat;
+    LineRecs rec;      // the forward pass's line records
+    SeedPrep prep;     // FP32: seed positions
+    Tape tape;
+    const double *dQ, *dTw;    // per-seed weights (NULL = 0)
+    double *xbar;              // [2 n][3] adjoint of each footpoint (index coordinates)
+    void *acc;                 // [nodes][8] {dB (3), dJ (3), 0, 0}, float or double
+    unsigned long long *head;  // work counter of the reverse sweep
+    long long n;
+};
+// mode: 0 = FP32 state and float grid, 1 = FP32 state and double grid, 2 = FP64
+cudaError_t launch_q_vjp(const AdjArgs &a, int mode, cudaStream_t s);
+cudaError_t launch_reverse(const AdjArgs &a, int mode, int grid, cudaStream_t s);
+int reverse_blocks_per_sm(int mode);
+cudaError_t launch_curl_adjoint(const void *acc, bool acc64, const FieldView &g, void *dB, fqsl_dtype dt,
+                                cudaStream_t s);
+cudaError_t launch_loss(long long n, const double *Q, const double *Tw, const double *Qt, const double *Twt,
+                        const uint8_t *st, double wtw, double *sums, double *loss, double *dQ, double *dTw,
+                        cudaStream_t s);
+
 // launch helpers implemented in the .cu files
 cudaError_t launch_curl_pack(const void *B, fqsl_dtype bt, const FieldView &g, void *rec32, void *rec64,
                              cudaStream_t s);
 cudaError_t launch_trace_f32(const TraceArgs &a, int src, int grid, int block, cudaStream_t s, bool acc64);
 cudaError_t launch_trace_f64(const TraceArgs &a, int src, int grid, int block, cudaStream_t s);
+// lattice tracers that also write the step tape (a.tape)
+cudaError_t launch_trace_tape_f32(const TraceArgs &a, int grid, cudaStream_t s, bool acc64);
+cudaError_t launch_trace_tape_f64(const TraceArgs &a, int grid, cudaStream_t s);
+int trace_tape_blocks_per_sm_f32(bool acc64);
+int trace_tape_blocks_per_sm_f64();
 int trace_blocks_per_sm_f32(int src, bool acc64);
 int trace_blocks_per_sm_f64(int src);
 // Method II tracers (deviation vectors; way 1 = gradient grid, 2 = +-eps)

@@ -457,6 +457,7 @@ struct Lane {
     double l1, tw1;      // totals of end 1
     double ol, otw;      // exiting step: FP64 sums at its end / FP32 its increments
     int steps, st, end, mode, hface, tries, fc0;
+    int tcur, tn;        // step tape: current chunk (-1 none yet, -2 pool exhausted), steps in it
     // Method II: deviation vectors (current, at the seed, at the end of the exiting step)
     T u[3], v[3], u0[3], v0[3], ou[3], ov[3];
 };
@@ -531,6 +532,56 @@ __device__ __forceinline__ void write_end32(const LineRecs &R, long long line, i
     r[1] = y;
     r[2] = z;
     (e == 0 ? R.f1 : R.f2)[line] = (int8_t)face;
+}
+
+// ---------------------------------------------------------------------------
+// step tape (adjoint forward pass; see Tape)
+// ---------------------------------------------------------------------------
+// Open a new chunk whose checkpoint is the current state. Returns false when
+// the pool is exhausted (the half-line is then no longer taped).
+template <typename T>
+__device__ __forceinline__ bool tape_chunk(const Tape &tp, Lane<T> &L)
+{
+    const unsigned long long c = atomicAdd(tp.next, 1ull);
+    if (c >= (unsigned long long)tp.cap) {
+        L.tcur = -2;
+        return false;
+    }
+    tp.prev[c] = L.tcur;
+    T *x = (T *)tp.xi + 4 * c;
+    x[0] = L.x;
+    x[1] = L.y;
+    x[2] = L.z;
+    x[3] = (T)0;
+    L.tcur = (int)c;
+    L.tn = 0;
+    return true;
+}
+
+// An accepted step of size h from the current state.
+template <typename T>
+__device__ __forceinline__ void tape_step(const Tape &tp, Lane<T> &L, T h)
+{
+    if (L.tcur == -2) return;
+    if ((L.tcur < 0 || L.tn == tp.k) && !tape_chunk(tp, L)) return;
+    ((T *)tp.h)[(long long)L.tcur * tp.k + L.tn] = h;
+    L.tn++;
+}
+
+// The current direction ends at (x, y, z) by end code `code` (hx: the
+// exiting step of a chord end).
+template <typename T>
+__device__ __forceinline__ void tape_end(const Tape &tp, Lane<T> &L, int code, T x, T y, T z, T hx)
+{
+    if (L.tcur == -1) tape_chunk(tp, L);  // no accepted step: the checkpoint is the seed
+    const long long hl = 2 * L.line + L.end;
+    const int sg = (L.end == 0) == (L.s0 > (T)0) ? -1 : 1;
+    tp.head[hl] = make_int4(L.tcur, L.tn, L.tcur >= 0 ? code : -2, sg);
+    T *e = (T *)tp.xe + 4 * hl;
+    e[0] = x;
+    e[1] = y;
+    e[2] = z;
+    e[3] = hx;
 }
 
 // Finish the line with a bad status (MAXSTEPS or NULL_B): the unfinished end
@@ -624,6 +675,8 @@ __device__ __forceinline__ bool finish_dir(const TraceArgs &A, const LineRecs &R
         }
         L.h = (T)A.p.h0;
         L.mode = 0;
+        L.tcur = -1;
+        L.tn = 0;
         acc_reset<T, ACC>(L);
         return true;
     }
@@ -662,6 +715,8 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
     L.steps = 0;
     L.end = 0;
     L.mode = 0;
+    L.tcur = -1;
+    L.tn = 0;
     acc_reset<T, ACC>(L);
     L.h = (T)A.p.h0;
     if (kF64) {
@@ -748,6 +803,8 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
         L.steps = 0;
         L.end = 0;
         L.mode = 0;
+        L.tcur = -1;
+        L.tn = 0;
         acc_reset<T, ACC>(L);
         L.h = (T)A.p.h0;
         if constexpr (DEV != 0) {
@@ -887,7 +944,8 @@ __device__ __forceinline__ bool init_list(const TraceArgs &A, Lane<T> &L, long l
 // vectors with grad(B/|B|) by way 1 or way 2 (lattice source only).
 // BATCH: the launch traces the entries of a batch (BatchArgs); each lane keeps
 // the entry of its line. A0 holds the launch-wide parameters and counter.
-template <typename T, int SRC, bool ACC, int DEV = 0, bool BATCH = false>
+// TAPE: also write the step tape A0.tape (lattice lines, Method I).
+template <typename T, int SRC, bool ACC, int DEV = 0, bool BATCH = false, bool TAPE = false>
 __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs &BA)
 {
     constexpr unsigned FULL = 0xffffffffu;
@@ -1131,6 +1189,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
             }
             hn = hn < hmin ? hmin : (hn > hmax ? hmax : hn);
             if (inside<T>(f, nx, ny, nz)) {
+                if constexpr (TAPE) tape_step(A.tape, L, hh);
                 L.x = nx;
                 L.y = ny;
                 L.z = nz;
@@ -1215,6 +1274,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                 acc_add<T, ACC>(L, (T)((double)L.t0 * L.ol), (T)((double)L.t0 * L.otw));
             }
             L.st |= FQSL_LINE_CHORD;
+            if constexpr (TAPE) tape_end(A.tape, L, kTapeChord + L.fc0, ex, ey, ez, L.h);
             T eu[3], ev[3];
             if constexpr (DEV != 0) {
 #pragma unroll
@@ -1253,6 +1313,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
             tz = fmin(fmax(tz, (T)0), (T)(f.nz - 1));
         }
         acc_add<T, ACC>(L, hh * l4, hh * tw4);
+        if constexpr (TAPE) tape_end(A.tape, L, (nf >= 0 ? kTapeExitClamped : kTapeExit) + L.hface, tx, ty, tz, (T)0);
         T eu[3], ev[3];
         if constexpr (DEV != 0) {
 #pragma unroll

@@ -82,3 +82,26 @@ int batch_trace_blocks_per_sm_f64()
     return b > 0 ? b : 1;
 }
 }  // namespace fqsl
+
+namespace fqsl {
+namespace {
+// adjoint forward pass: the lattice tracer that also writes the step tape
+__global__ void __launch_bounds__(kBlock) k_trace_tape_f64(const TraceArgs A)
+{
+    trace::trace_body<double, kSrcLattice, true, 0, false, true>(A, BatchArgs{});
+}
+}  // namespace
+
+cudaError_t launch_trace_tape_f64(const TraceArgs &a, int grid, cudaStream_t s)
+{
+    k_trace_tape_f64<<<grid, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int trace_tape_blocks_per_sm_f64()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_f64, kBlock, 0);
+    return b > 0 ? b : 1;
+}
+}  // namespace fqsl

@@ -22,7 +22,7 @@ LINE_BAD = LINE_MAXSTEPS | LINE_NULL_B | LINE_OUTSIDE
 EXPORTS = ("fqsl_params_default", "fqsl_version", "fqsl_last_error", "fqsl_field_create", "fqsl_field_destroy",
            "fqsl_qmap_plane", "fqsl_qmap_volume", "fqsl_twist", "fqsl_field_check", "fqsl_field_set_timing",
            "fqsl_field_times", "fqsl_field_update", "fqsl_qmap_plane_static", "fqsl_batch_create", "fqsl_batch_run",
-           "fqsl_batch_destroy")
+           "fqsl_batch_destroy", "fqsl_backward", "fqsl_loss_logq_tw")
 STATIC_MAX_SEEDS = 65536
 
 
@@ -37,7 +37,7 @@ class Params(C.Structure):
                 ("tol", C.c_double), ("h0", C.c_double), ("h_min", C.c_double), ("h_max", C.c_double),
                 ("max_steps", C.c_longlong), ("rot_thresh", C.c_double), ("tol_exp", C.c_double),
                 ("graze", C.c_double), ("eps_way2", C.c_double), ("sync_dirs", C.c_int), ("chunk_tiles", C.c_int),
-                ("blocks_per_sm", C.c_int)]
+                ("blocks_per_sm", C.c_int), ("tape", C.c_int), ("tape_chunk", C.c_int)]
 
 
 class Plane(C.Structure):
@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
     lib.fqsl_batch_destroy.argtypes = [P]
     lib.fqsl_field_update.argtypes = [P, P, C.c_int, P]
     lib.fqsl_field_times.argtypes = [P, C.POINTER(C.c_float * 3)]
+    lib.fqsl_backward.argtypes = [P, P, P, P, C.c_int, P]
+    lib.fqsl_loss_logq_tw.argtypes = [C.c_longlong, P, P, P, P, P, C.c_double, P, P, P, P, P]
     for name in EXPORTS:
         if name not in ("fqsl_params_default", "fqsl_version", "fqsl_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -295,3 +297,69 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def backward(field: Field, dQ=None, dTw=None, dB=None, dtype=None, stream=None):
+    """Accumulate (d(Q,Tw)/dB)^T (dQ, dTw) of the field's last taped plane map
+    (qmap_plane with params(tape=1)) into dB (a B-shaped CUDA tensor; allocated
+    as zeros of ``dtype``, default float32, when not given). dQ, dTw: CUDA
+    float64 tensors of the map's seed count, or None."""
+    nx, ny, nz = field.n
+    if dB is None:
+        dB = torch.zeros((nz, ny, nx, 3), dtype=dtype or torch.float32, device="cuda")
+    if not (dB.is_cuda and dB.is_contiguous() and tuple(dB.shape) == (nz, ny, nx, 3)):
+        raise ValueError("dB must be a contiguous CUDA tensor of shape (nz, ny, nx, 3)")
+    if dB.dtype not in (torch.float32, torch.float64):
+        raise ValueError("dB must be float32 or float64")
+    dQ = None if dQ is None else dQ.to(torch.float64).contiguous()
+    dTw = None if dTw is None else dTw.to(torch.float64).contiguous()
+    _check(_lib.fqsl_backward(field.handle, _ptr(dQ), _ptr(dTw), C.c_void_p(dB.data_ptr()),
+                              F32 if dB.dtype == torch.float32 else F64, _stream(stream)))
+    return dB
+
+
+def loss_logq_tw(Q, Tw, Q_target, Tw_target, status=None, w_tw: float = 0.1, stream=None, out=None):
+    """mean over usable seeds of (log10 Q - log10 Q_t)^2 + w_tw (Tw - Tw_t)^2 and
+    its gradient (fqsl_loss_logq_tw). Returns (loss (0-d CUDA tensor), dQ, dTw)."""
+    n = Q.numel()
+    dev = Q.device
+    if out is None:
+        out = dict(sums=torch.empty(2, dtype=torch.float64, device=dev),
+                   loss=torch.empty((), dtype=torch.float64, device=dev),
+                   dQ=torch.empty(n, dtype=torch.float64, device=dev),
+                   dTw=torch.empty(n, dtype=torch.float64, device=dev))
+    args = [t.contiguous() for t in (Q, Tw, Q_target, Tw_target)]
+    if any(t.dtype != torch.float64 for t in args):
+        raise ValueError("Q, Tw and the targets must be float64")
+    st = None if status is None else status.contiguous()
+    _check(_lib.fqsl_loss_logq_tw(n, *[_ptr(t) for t in args], _ptr(st), float(w_tw), _ptr(out["sums"]),
+                                  _ptr(out["loss"]), _ptr(out["dQ"]), _ptr(out["dTw"]), _stream(stream)))
+    return out["loss"], out["dQ"], out["dTw"]
+
+
+class QTwPlane(torch.autograd.Function):
+    """(Q, Tw) of a plane map as a differentiable function of B:
+    ``Q, Tw = QTwPlane.apply(B, field, origin, u, v, nu, nv, p)``. The forward
+    repacks B into ``field`` and traces the map with the step tape; the backward
+    runs fqsl_backward (frozen step sequence; Method I). Q of rotated or
+    NaN seeds carries no gradient."""
+
+    @staticmethod
+    def forward(ctx, B, field, origin, u, v, nu, nv, p=None):
+        p = p or params()
+        q = Params.from_buffer_copy(p)
+        q.tape = 1
+        field.update(B.detach())
+        out = qmap_plane(field, origin, u, v, nu, nv, q)
+        ctx.field = field
+        ctx.b_dtype = B.dtype
+        return out["Q"], out["Tw"]
+
+    @staticmethod
+    def backward(ctx, gQ, gTw):
+        dB = backward(ctx.field, gQ, gTw, dtype=ctx.b_dtype)
+        return dB, None, None, None, None, None, None, None

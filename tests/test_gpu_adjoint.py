@@ -1,0 +1,256 @@
+"""The CUDA adjoint (fqsl_backward) against the FP64 CPU adjoint oracle
+(oracle/adjoint.py) on the same seeded inputs, through the C ABI.
+
+The derivative is that of the traced computation with each line's accepted
+step sizes and exit kinds frozen. The FP64 tracer takes exactly the oracle's
+steps (its forward is bit-identical), so its gradient must match the oracle's
+to rounding; the FP32 tracer takes its own steps in float, and its gradient is
+compared with a stated relative bound."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+adj = pytest.importorskip("oracle.adjoint")
+pytestmark = pytest.mark.gpu
+
+SMALL = dict(n=(24, 24, 24), count=6, radius_cells=4.0, dtype=np.float64)
+PLANE16 = ((0.0, 0.0, 0.0), (23.0 / 16, 0.0, 0.0), (0.0, 23.0 / 16, 0.0), 16, 16)
+# an interior xz plane (some seeds rotate S0; their Q carries no gradient)
+XZ = ((0.0, 11.3, 0.0), (23.0 / 20, 0.0, 0.0), (0.0, 0.0, 23.0 / 12), 20, 12)
+PATCH = ((-0.3, -0.3, 0.0), (0.1, 0.0, 0.0), (0.0, 0.1, 0.0), 6, 6)
+
+
+@pytest.fixture(scope="module")
+def fq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2208_12569_gb300 as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def small():
+    B, Bt, grid = synth.adjoint_cubes(**SMALL)
+    return B, Bt, grid
+
+
+def _field(fq, B, grid):
+    return fq.Field(torch.from_numpy(np.ascontiguousarray(B)).cuda(), grid.origin, grid.spacing)
+
+
+def _weights(seed, m):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(m), rng.standard_normal(m)
+
+
+def _gpu_vjp(fq, field, plane, wq, wt, dtype=torch.float64, **kw):
+    out = fq.qmap_plane(field, *plane, fq.params(tape=1, **kw))
+    st = out["status"].cpu().numpy()
+    dB = fq.backward(field, torch.from_numpy(wq).cuda(), torch.from_numpy(wt).cuda(), dtype=dtype)
+    field.check()
+    return dB.cpu().numpy().astype(np.float64), st
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("plane", [PLANE16, XZ], ids=["z0_plane", "interior_xz_plane"])
+def test_fp64_gradient_matches_oracle_adjoint(fq, small, plane):
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    m = plane[3] * plane[4]
+    wq, wt = _weights(11, m)
+    g, st = _gpu_vjp(fq, field, plane, wq, wt, precision="f64")
+    ref, log = adj.vjp(B, grid, *plane, wq, wt, oracle.params())
+    assert np.array_equal(st & oracle.BAD, log["status"] & oracle.BAD)
+    assert np.linalg.norm(ref) > 0
+    assert _rel(g, ref) < 1e-10
+    assert np.abs(g - ref).max() < 1e-10 * np.abs(ref).max()
+    if plane is XZ:
+        assert (st & fq.LINE_ROTATED).any()
+
+
+@pytest.mark.parametrize("precision,bound", [("f32", 2e-2), ("f32acc64", 2e-2)])
+def test_fp32_gradient_against_oracle_adjoint(fq, small, precision, bound):
+    # the FP32 tracer's own frozen step sequence, in float; the bound is stated
+    B, _, grid = small
+    field = _field(fq, B.astype(np.float32), grid)
+    m = PLANE16[3] * PLANE16[4]
+    wq, wt = _weights(12, m)
+    g, st = _gpu_vjp(fq, field, PLANE16, wq, wt, dtype=torch.float32, precision=precision)
+    ref, _ = adj.vjp(B.astype(np.float32).astype(np.float64), grid, *PLANE16, wq, wt, oracle.params())
+    assert _rel(g, ref) < bound
+
+
+def test_dot_product_with_oracle_tangent_mode(fq, small):
+    # <J v, w> from the oracle's forward-mode derivative = <v, J^T w> from the GPU
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    m = PLANE16[3] * PLANE16[4]
+    wq, wt = _weights(13, m)
+    v = np.random.default_rng(14).standard_normal(B.shape)
+    g, st = _gpu_vjp(fq, field, PLANE16, wq, wt, precision="f64")
+    dQ, dTw, us, log = adj.jvp(B, grid, *PLANE16, v, oracle.params())
+    good = (log["status"] & oracle.BAD) == 0
+    lhs = np.sum(wq[us] * dQ[us]) + np.sum(wt[good] * dTw[good])
+    rhs = np.sum(v * g)
+    assert abs(lhs - rhs) < 1e-10 * (abs(lhs) + 1e-3 * np.linalg.norm(g) * np.linalg.norm(v))
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-11), ("f32", 1e-4)])
+def test_gradient_orthogonal_to_B(fq, small, precision, tol):
+    # the map is invariant under B -> c B, so <J^T w, B> = 0
+    B, _, grid = small
+    Bp = B if precision == "f64" else B.astype(np.float32)
+    field = _field(fq, Bp, grid)
+    m = PLANE16[3] * PLANE16[4]
+    wq, wt = _weights(15, m)
+    g, _ = _gpu_vjp(fq, field, PLANE16, wq, wt, precision=precision)
+    Bd = Bp.astype(np.float64)
+    assert abs(np.sum(g * Bd)) < tol * np.linalg.norm(g) * np.linalg.norm(Bd)
+
+
+def _mesh(grid):
+    x, y, z = (grid.axis(a) for a in range(3))
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return X, Y, Z
+
+
+@pytest.mark.parametrize("precision,rtol", [("f64", 1e-5), ("f32", 1e-3)])
+def test_hyperbolic_closed_form(fq, precision, rtol):
+    # B = (x, -y, 1): sum_s w_s dQ_s/da along dB = (x, -y, 0) = sum w * 2L(e^2L - e^-2L)
+    grid = synth.C1_GRID
+    B = synth.analytic_cube("hyperbolic", grid)
+    field = _field(fq, B if precision == "f64" else B.astype(np.float32), grid)
+    X, Y, Z = _mesh(grid)
+    dB = np.stack([X, -Y, 0 * X], -1)
+    w = np.random.default_rng(3).uniform(0.5, 1.5, 36)
+    g, st = _gpu_vjp(fq, field, PATCH, w, 0 * w, precision=precision)
+    assert not (st & (oracle.BAD | oracle.MIXED)).any()
+    closed = 2.0 * (math.exp(2.0) - math.exp(-2.0))
+    np.testing.assert_allclose(np.sum(g * dB), np.sum(w) * closed, rtol=rtol)
+
+
+@pytest.mark.parametrize("precision,rtol", [("f64", 1e-3), ("f32", 2e-3)])
+def test_rotation_closed_form(fq, precision, rtol):
+    # B = (-q y, q x, 1): sum_s w_s dTw_s/dq along dB = (-y, x, 0)
+    grid = synth.C1_GRID
+    q = 2.0 * math.pi
+    B = synth.analytic_cube("rotation", grid, q=q)
+    field = _field(fq, B if precision == "f64" else B.astype(np.float32), grid)
+    X, Y, Z = _mesh(grid)
+    dB = np.stack([-Y, X, 0 * X], -1)
+    w = np.random.default_rng(4).uniform(0.5, 1.5, 36)
+    g, _ = _gpu_vjp(fq, field, PATCH, 0 * w, w, precision=precision)
+    r0 = np.asarray(grid.origin) + np.asarray(grid.spacing) * adj.seeds_index(grid, *PATCH)
+    r2 = r0[:, 0] ** 2 + r0[:, 1] ** 2
+    closed = (1.0 + q * q * r2) ** -1.5 / (2.0 * math.pi)
+    np.testing.assert_allclose(np.sum(g * dB), np.sum(w * closed), rtol=rtol)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(fq, small):
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    m = PLANE16[3] * PLANE16[4]
+    wq, wt = _weights(16, m)
+    gs = [_gpu_vjp(fq, field, PLANE16, wq, wt, precision="f64", tape_chunk=k)[0] for k in (1, 3, 16, 64)]
+    for g in gs[1:]:
+        assert _rel(g, gs[0]) < 1e-12
+
+
+def test_tape_pool_grows_when_exhausted(fq, small):
+    # tight tolerance and one step per chunk: the first pool guess is too small,
+    # fqsl_backward traces the map again with a larger pool
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    m = PLANE16[3] * PLANE16[4]
+    wq, wt = _weights(17, m)
+    kw = dict(precision="f64", tol=1e-7, max_steps=1000000)
+    g1, _ = _gpu_vjp(fq, field, PLANE16, wq, wt, tape_chunk=1, **kw)
+    g16, _ = _gpu_vjp(fq, field, PLANE16, wq, wt, tape_chunk=16, **kw)
+    assert _rel(g1, g16) < 1e-12
+    ref, _ = adj.vjp(B, grid, *PLANE16, wq, wt, oracle.params(tol=1e-7, max_steps=1000000))
+    assert _rel(g1, ref) < 1e-10
+
+
+def test_loss_kernel_matches_oracle_loss(fq, small):
+    B, Bt, grid = small
+    field = _field(fq, B, grid)
+    ftgt = _field(fq, Bt, grid)
+    p = fq.params(precision="f64")
+    out = fq.qmap_plane(field, *PLANE16, p)
+    tgt = fq.qmap_plane(ftgt, *PLANE16, p)
+    loss, dQ, dTw = fq.loss_logq_tw(out["Q"], out["Tw"], tgt["Q"], tgt["Tw"], out["status"], 0.1)
+    Q = torch.tensor(out["Q"].cpu().numpy(), requires_grad=True)
+    Tw = torch.tensor(out["Tw"].cpu().numpy(), requires_grad=True)
+    st = out["status"].cpu().numpy()
+    usable = torch.from_numpy((st & (oracle.BAD | oracle.MIXED | oracle.ROTATED)) == 0)
+    ref, use = adj.log_q_tw_loss(Q, Tw, tgt["Q"].cpu().numpy(), tgt["Tw"].cpu().numpy(), usable, 0.1)
+    ref.backward()
+    assert int(use.sum()) > 200
+    np.testing.assert_allclose(float(loss), float(ref), rtol=1e-12)
+    np.testing.assert_allclose(dQ.cpu().numpy(), Q.grad.numpy(), rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(dTw.cpu().numpy(), Tw.grad.numpy(), rtol=1e-12, atol=1e-300)
+
+
+def test_loss_gradient_end_to_end_matches_oracle(fq, small):
+    # loss -> dQ, dTw (loss kernel) -> dB (fqsl_backward), FP64, against the
+    # oracle's autograd of the same loss over the frozen step sequence
+    B, Bt, grid = small
+    field = _field(fq, B, grid)
+    tgt = oracle.plane(Bt, grid, *PLANE16, oracle.params())
+    p = fq.params(precision="f64", tape=1)
+    out = fq.qmap_plane(field, *PLANE16, p)
+    qt = torch.from_numpy(tgt["Q"]).cuda()
+    twt = torch.from_numpy(tgt["Tw"]).cuda()
+    loss, dQ, dTw = fq.loss_logq_tw(out["Q"], out["Tw"], qt, twt, out["status"], 0.1)
+    dB = fq.backward(field, dQ, dTw, dtype=torch.float64).cpu().numpy()
+    ref_loss, ref_g, _ = adj.loss_grad(B, grid, *PLANE16, tgt["Q"], tgt["Tw"], oracle.params())
+    np.testing.assert_allclose(float(loss), ref_loss, rtol=1e-11)
+    assert _rel(dB, ref_g) < 1e-10
+
+
+def test_autograd_function(fq, small):
+    B, Bt, grid = small
+    Bd = torch.from_numpy(B).cuda()
+    field = _field(fq, B, grid)
+    tgt = oracle.plane(Bt, grid, *PLANE16, oracle.params())
+    p = fq.params(precision="f64")
+    Bv = Bd.clone().requires_grad_(True)
+    Q, Tw = fq.QTwPlane.apply(Bv, field, *PLANE16, p)
+    st = fq.qmap_plane(field, *PLANE16, p)["status"]
+    loss, dQ, dTw = fq.loss_logq_tw(Q.detach(), Tw.detach(), torch.from_numpy(tgt["Q"]).cuda(),
+                                    torch.from_numpy(tgt["Tw"]).cuda(), st, 0.1)
+    torch.autograd.backward([Q, Tw], [dQ, dTw])
+    _, ref_g, _ = adj.loss_grad(B, grid, *PLANE16, tgt["Q"], tgt["Tw"], oracle.params())
+    assert Bv.grad is not None and Bv.grad.dtype == torch.float64
+    assert _rel(Bv.grad.cpu().numpy(), ref_g) < 1e-10
+
+
+def test_backward_argument_errors(fq, small):
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    with pytest.raises(fq.FqslError) as ei:
+        fq.backward(field, None, None)
+    assert ei.value.status == 1 and "taped" in str(ei.value)
+    with pytest.raises(fq.FqslError) as ei:
+        fq.qmap_plane(field, *PLANE16, fq.params(tape=1, method=2))
+    assert ei.value.status == 5
+    with pytest.raises(fq.FqslError) as ei:
+        fq.qmap_volume(field, (0.0, 0.0, 0.0), (2.0, 2.0, 2.0), 4, 4, 4, fq.params(tape=1))
+    assert ei.value.status == 5
+    with pytest.raises(fq.FqslError) as ei:
+        fq.qmap_plane(field, *PLANE16, fq.params(tape=1, tape_chunk=65))
+    assert ei.value.status == 1
+    # zero weights give a zero gradient
+    fq.qmap_plane(field, *PLANE16, fq.params(tape=1))
+    dB = fq.backward(field, None, None)
+    field.check()
+    assert float(dB.abs().max()) == 0.0
