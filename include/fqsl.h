@@ -112,6 +112,9 @@ typedef struct {
                              differentiates (0 = default, no tape). Results do not depend on it. */
     int tape_chunk;       /* steps per tape chunk, i.e. the checkpoint interval k of the reverse sweep
                              (1..64; 0 = default 16) */
+    int reverse_precision; /* precision of fqsl_backward's reverse sweep for this taped map: -1 (default)
+                             = precision; FQSL_F32, FQSL_F32_ACC64 (float state, double node grid) or
+                             FQSL_F64; the field must be packed in it */
 } fqsl_params;
 
 /* Output buffers of one call (caller-owned device memory, n = number of
@@ -287,9 +290,10 @@ FQSL_API fqsl_status fqsl_qmap_plane_static(fqsl_field field, const double origi
  *                    or infinite weights count as 0.
  *   dB_dev           B-shaped array (layout of fqsl_field_create) of db_dtype
  *                    (FQSL_F32 or FQSL_F64), accumulated into, not cleared.
- * The state is recomputed in the taped call's precision from checkpoints
- * every params->tape_chunk accepted steps; the node adjoints accumulate in
- * float (FQSL_F32) or double (FQSL_F32_ACC64, FQSL_F64). The field must not
+ * The state is recomputed from checkpoints every params->tape_chunk accepted
+ * steps, in the taped call's params->reverse_precision (default: its
+ * precision); the node adjoints accumulate in float (FQSL_F32) or double
+ * (FQSL_F32_ACC64, FQSL_F64). The field must not
  * be updated between the taped call and this one. The call synchronises
  * cuda_stream once (to confirm that the tape's chunk pool sufficed; if it did
  * not, it traces the map again with a larger pool), so it cannot be captured
@@ -299,6 +303,20 @@ FQSL_API fqsl_status fqsl_qmap_plane_static(fqsl_field field, const double origi
  * FQSL_ERR_CUDA. */
 FQSL_API fqsl_status fqsl_backward(fqsl_field field, const double *dQ_dev, const double *dTw_dev, void *dB_dev,
                                    fqsl_dtype db_dtype, void *cuda_stream);
+
+/* The step sequence of the field's last taped plane map (the paper has no
+ * counterpart; for inspection and for replaying a map's exact steps
+ * elsewhere). For half-line hl = 2 s + e (seed s, end e = 0 for end 1):
+ * nsteps_dev[hl] accepted steps (-1 if more than cap; 0 with code -1 for a
+ * line with MAXSTEPS, NULL_B or OUTSIDE), h_dev[hl * cap + i] their sizes in
+ * cells in order, code_dev[hl] how the direction ended (16 + face: exit step
+ * onto that face; 40 + face: the same with the other coordinates clamped into
+ * the box; 48 + face: chord onto that face after an exiting step of size
+ * hx_dev[hl], which is 0 otherwise). Device arrays of 2 nu nv elements
+ * (h_dev: 2 nu nv cap). The pool must have sufficed (run fqsl_backward first
+ * if unsure). Errors: FQSL_ERR_ARG, FQSL_ERR_CUDA. */
+FQSL_API fqsl_status fqsl_tape_export(fqsl_field field, int cap, int32_t *nsteps_dev, int32_t *code_dev,
+                                      double *hx_dev, double *h_dev, void *cuda_stream);
 
 /* The log-Q / Tw misfit of two maps and its gradient (a loss for
  * fqsl_backward; the paper has no counterpart):

@@ -440,8 +440,8 @@ __device__ __forceinline__ void chord_reverse(const FieldView &f, T sgn, const T
 
 constexpr int kMaxChunk = 64;  // largest steps per tape chunk
 
-// Reverse sweep of half-line hl = 2 line + e.
-template <typename T, typename AccT>
+// Reverse sweep of half-line hl = 2 line + e (TT: the tape's scalar type).
+template <typename T, typename AccT, typename TT>
 __device__ __forceinline__ void reverse_half_line(const AdjArgs &A, long long line, int e, T (*xs)[3])
 {
     const Tape &tp = A.tape;
@@ -458,21 +458,21 @@ __device__ __forceinline__ void reverse_half_line(const AdjArgs &A, long long li
     AccT *acc = (AccT *)A.acc;
     const FieldView &f = A.f;
     const T sgn = (T)hd.w;
-    const T *H = (const T *)tp.h;
-    const T *X = (const T *)tp.xi;
+    const TT *H = (const TT *)tp.h;
+    const TT *X = (const TT *)tp.xi;
     // last chunk: its states up to the exit step
     int c = hd.x;
     int n = hd.y;
-    xs[0][0] = X[4 * (long long)c];
-    xs[0][1] = X[4 * (long long)c + 1];
-    xs[0][2] = X[4 * (long long)c + 2];
+    xs[0][0] = (T)X[4 * (long long)c];
+    xs[0][1] = (T)X[4 * (long long)c + 1];
+    xs[0][2] = (T)X[4 * (long long)c + 2];
     for (int i = 0; i < n; i++) {
         T k[5][3];
-        advance(f, sgn, xs[i], H[(long long)c * tp.k + i], xs[i + 1], k, (T *)nullptr);
+        advance(f, sgn, xs[i], (T)H[(long long)c * tp.k + i], xs[i + 1], k, (T *)nullptr);
     }
     const int code = hd.z;
     if (code >= kTapeChord) {
-        const T hx = ((const T *)tp.xe)[4 * hl + 3];
+        const T hx = (T)((const TT *)tp.xe)[4 * hl + 3];
         chord_reverse<T, AccT>(f, sgn, xs[n], code - kTapeChord, hx, xb, wb, acc);
     } else if (code >= kTapeExitClamped) {
         exit_reverse<T, AccT>(f, sgn, xs[n], code - kTapeExitClamped, true, xb, wb, acc);
@@ -480,22 +480,23 @@ __device__ __forceinline__ void reverse_half_line(const AdjArgs &A, long long li
         exit_reverse<T, AccT>(f, sgn, xs[n], code - kTapeExit, false, xb, wb, acc);
     }
     for (;;) {
-        for (int i = n - 1; i >= 0; i--) step_reverse<T, AccT>(f, sgn, xs[i], H[(long long)c * tp.k + i], xb, wb, acc);
+        for (int i = n - 1; i >= 0; i--)
+            step_reverse<T, AccT>(f, sgn, xs[i], (T)H[(long long)c * tp.k + i], xb, wb, acc);
         const int pc = tp.prev[c];
         if (pc < 0 || pc >= c) break;  // chunks of a half-line are taken in increasing order
         c = pc;
         n = tp.k;
-        xs[0][0] = X[4 * (long long)c];
-        xs[0][1] = X[4 * (long long)c + 1];
-        xs[0][2] = X[4 * (long long)c + 2];
+        xs[0][0] = (T)X[4 * (long long)c];
+        xs[0][1] = (T)X[4 * (long long)c + 1];
+        xs[0][2] = (T)X[4 * (long long)c + 2];
         for (int i = 0; i + 1 < n; i++) {
             T k[5][3];
-            advance(f, sgn, xs[i], H[(long long)c * tp.k + i], xs[i + 1], k, (T *)nullptr);
+            advance(f, sgn, xs[i], (T)H[(long long)c * tp.k + i], xs[i + 1], k, (T *)nullptr);
         }
     }
 }
 
-template <typename T, typename AccT>
+template <typename T, typename AccT, typename TT>
 __global__ void __launch_bounds__(128) k_reverse(const AdjArgs A)
 {
     constexpr unsigned FULL = 0xffffffffu;
@@ -514,7 +515,7 @@ __global__ void __launch_bounds__(128) k_reverse(const AdjArgs A)
         const long long j = (t / G.tiles_u) * kTileV + (lane / kTileU);
         if (i < G.n1 && j < G.n2) {
             const long long line = i + G.n1 * j;
-            if (!(A.rec.st[line] & kBad)) reverse_half_line<T, AccT>(A, line, e, xs);
+            if (!(A.rec.st[line] & kBad)) reverse_half_line<T, AccT, TT>(A, line, e, xs);
         }
         __syncwarp();
     }
@@ -549,13 +550,13 @@ __device__ __forceinline__ double bn_vjp(const FieldView &f, const T p[3], int a
     return (double)V[ax];
 }
 
-template <typename T, typename AccT>
+template <typename T, typename AccT, typename TT>
 __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
 {
     const Lattice &G = A.lat;
     const FieldView &f = A.f;
     const LineRecs &R = A.rec;
-    const T *XE = (const T *)A.tape.xe;
+    const TT *XE = (const TT *)A.tape.xe;
     AccT *acc = (AccT *)A.acc;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < A.n;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
             }
         T pe[2][3];
         for (int e = 0; e < 2; e++)
-            for (int a = 0; a < 3; a++) pe[e][a] = XE[4 * (2 * idx + e) + a];
+            for (int a = 0; a < 3; a++) pe[e][a] = (T)XE[4 * (2 * idx + e) + a];
         double g1[3], g2[3];
         const int ax1 = fe2[0] >> 1, ax2 = fe2[1] >> 1;
         const double bn1 = bn_vjp<T, AccT>(f, pe[0], ax1, 0.0, g1, acc);
@@ -669,15 +670,17 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
         }
         // Bn0 = B(seed) . n0
         T p0[3];
-        if constexpr (sizeof(T) == 4) {
+        if (A.prep.seed) {
+            // the FP32 tracer's seed (its pre-pass)
             const float4 sd = A.prep.seed[idx];
-            p0[0] = sd.x;
-            p0[1] = sd.y;
-            p0[2] = sd.z;
+            p0[0] = (T)sd.x;
+            p0[1] = (T)sd.y;
+            p0[2] = (T)sd.z;
         } else {
+            // the FP64 tracer's seed: (r0 - o)/d as written
             double r0[3];
             trace::lattice_seed(G, i, j, 0, r0);
-            for (int a = 0; a < 3; a++) p0[a] = (r0[a] - f.o[a]) / f.d[a];
+            for (int a = 0; a < 3; a++) p0[a] = (T)((r0[a] - f.o[a]) / f.d[a]);
         }
         const Cell<T> c0 = cell_of(f, p0[0], p0[1], p0[2]);
         const T Vb[6] = {(T)(bn0b * G.n0[0]), (T)(bn0b * G.n0[1]), (T)(bn0b * G.n0[2]), 0, 0, 0};
@@ -798,6 +801,48 @@ __global__ void __launch_bounds__(256) k_loss_grad(long long n, const double *Q,
     }
 }
 
+// The step sequence of every half-line, in order: ns[hl] steps (-1: more
+// than cap; 0 with code -1: line not traced), h[hl * cap + i], end code and the
+// chord's exiting step.
+template <typename T>
+__global__ void __launch_bounds__(256) k_tape_export(const Tape tp, const uint8_t *__restrict__ st, long long halves,
+                                                     int cap, int32_t *ns, int32_t *code, double *hx, double *h)
+{
+    const T *H = (const T *)tp.h;
+    for (long long hl = blockIdx.x * (long long)blockDim.x + threadIdx.x; hl < halves;
+         hl += (long long)gridDim.x * blockDim.x) {
+        ns[hl] = 0;
+        code[hl] = -1;
+        hx[hl] = 0.0;
+        if (st[hl >> 1] & kBad) continue;
+        const int4 hd = tp.head[hl];
+        if (hd.x < 0 || hd.z < 0) continue;
+        long long total = hd.y;
+        for (int c = hd.x;;) {
+            const int pc = tp.prev[c];
+            if (pc < 0 || pc >= c) break;
+            total += tp.k;
+            c = pc;
+        }
+        code[hl] = hd.z;
+        hx[hl] = (double)((const T *)tp.xe)[4 * hl + 3];
+        if (total > cap) {
+            ns[hl] = -1;
+            continue;
+        }
+        ns[hl] = (int32_t)total;
+        long long pos = total;
+        int c = hd.x, m = hd.y;
+        for (;;) {
+            for (int i = m - 1; i >= 0; i--) h[hl * cap + --pos] = (double)H[(long long)c * tp.k + i];
+            const int pc = tp.prev[c];
+            if (pc < 0 || pc >= c) break;
+            c = pc;
+            m = tp.k;
+        }
+    }
+}
+
 int sm_count()
 {
     int dev = 0, sms = 0;
@@ -816,30 +861,53 @@ unsigned grid_for(long long n, int per_block, int cap_per_sm)
 
 }  // namespace adj
 
-// precision: 0 = float state / float grid, 1 = float state / double grid, 2 = double / double
-cudaError_t launch_q_vjp(const AdjArgs &a, int mode, cudaStream_t s)
+// mode: 0 = float state and float grid, 1 = float state and double grid, 2 =
+// double; tape_f64: the tape holds doubles (FP64 forward) or floats
+namespace {
+template <typename TT>
+void q_vjp_mode(const AdjArgs &a, int mode, unsigned g, cudaStream_t s)
+{
+    if (mode == 0) adj::k_q_vjp<float, float, TT><<<g, 128, 0, s>>>(a);
+    else if (mode == 1) adj::k_q_vjp<float, double, TT><<<g, 128, 0, s>>>(a);
+    else adj::k_q_vjp<double, double, TT><<<g, 128, 0, s>>>(a);
+}
+
+template <typename TT>
+void reverse_mode(const AdjArgs &a, int mode, int grid, cudaStream_t s)
+{
+    if (mode == 0) adj::k_reverse<float, float, TT><<<grid, 128, 0, s>>>(a);
+    else if (mode == 1) adj::k_reverse<float, double, TT><<<grid, 128, 0, s>>>(a);
+    else adj::k_reverse<double, double, TT><<<grid, 128, 0, s>>>(a);
+}
+
+template <typename TT>
+int reverse_blocks(int mode)
+{
+    int b = 0;
+    if (mode == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adj::k_reverse<float, float, TT>, 128, 0);
+    else if (mode == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adj::k_reverse<float, double, TT>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adj::k_reverse<double, double, TT>, 128, 0);
+    return b > 0 ? b : 1;
+}
+}  // namespace
+
+cudaError_t launch_q_vjp(const AdjArgs &a, int mode, bool tape_f64, cudaStream_t s)
 {
     const unsigned g = adj::grid_for(a.n, 128, 16);
-    if (mode == 0) adj::k_q_vjp<float, float><<<g, 128, 0, s>>>(a);
-    else if (mode == 1) adj::k_q_vjp<float, double><<<g, 128, 0, s>>>(a);
-    else adj::k_q_vjp<double, double><<<g, 128, 0, s>>>(a);
+    if (tape_f64) q_vjp_mode<double>(a, mode, g, s);
+    else q_vjp_mode<float>(a, mode, g, s);
     return cudaGetLastError();
 }
 
-int reverse_blocks_per_sm(int mode)
+int reverse_blocks_per_sm(int mode, bool tape_f64)
 {
-    int b = 0;
-    if (mode == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adj::k_reverse<float, float>, 128, 0);
-    else if (mode == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adj::k_reverse<float, double>, 128, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adj::k_reverse<double, double>, 128, 0);
-    return b > 0 ? b : 1;
+    return tape_f64 ? reverse_blocks<double>(mode) : reverse_blocks<float>(mode);
 }
 
-cudaError_t launch_reverse(const AdjArgs &a, int mode, int grid, cudaStream_t s)
+cudaError_t launch_reverse(const AdjArgs &a, int mode, bool tape_f64, int grid, cudaStream_t s)
 {
-    if (mode == 0) adj::k_reverse<float, float><<<grid, 128, 0, s>>>(a);
-    else if (mode == 1) adj::k_reverse<float, double><<<grid, 128, 0, s>>>(a);
-    else adj::k_reverse<double, double><<<grid, 128, 0, s>>>(a);
+    if (tape_f64) reverse_mode<double>(a, mode, grid, s);
+    else reverse_mode<float>(a, mode, grid, s);
     return cudaGetLastError();
 }
 
@@ -863,6 +931,15 @@ cudaError_t launch_curl_adjoint(const void *acc, bool acc64, const FieldView &g,
             adj::k_curl_adjoint<float, double><<<grid, 256, 0, s>>>((const float *)acc, g.nx, g.ny, g.nz, g.d[0],
                                                                     g.d[1], g.d[2], (double *)dB);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tape_export(const Tape &tp, bool f64, const uint8_t *st, long long halves, int cap, int32_t *ns,
+                               int32_t *code, double *hx, double *h, cudaStream_t s)
+{
+    const unsigned g = adj::grid_for(halves, 256, 8);
+    if (f64) adj::k_tape_export<double><<<g, 256, 0, s>>>(tp, st, halves, cap, ns, code, hx, h);
+    else adj::k_tape_export<float><<<g, 256, 0, s>>>(tp, st, halves, cap, ns, code, hx, h);
     return cudaGetLastError();
 }
 

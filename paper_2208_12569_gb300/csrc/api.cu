@@ -67,7 +67,7 @@ struct fqsl_field_s {
     int blocks_cache[3][3] = {};  // [precision][source] resident blocks per SM
     int blocks_cache_m2[2][2] = {};  // Method II: [fp64][way - 1]
     int blocks_cache_tape[3] = {};   // taped lattice tracer: [precision]
-    int blocks_cache_rev[3] = {};    // adjoint reverse sweep: [precision]
+    int blocks_cache_rev[3][2] = {};  // adjoint reverse sweep: [mode][tape is FP64]
     bool timing = false, timed = false, extra_timed = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // the last plane map traced with params->tape = 1 (for fqsl_backward): its
@@ -110,6 +110,7 @@ void fqsl_params_default(fqsl_params *p)
     p->graze = 1e-3;
     p->eps_way2 = 1e-3;
     p->sync_dirs = -1;
+    p->reverse_precision = -1;
 }
 
 const char *fqsl_version(void) { return "fqsl 0.1.0 (sm_103a)"; }
@@ -314,6 +315,13 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 64) return fail(FQSL_ERR_ARG, "%s: blocks_per_sm in [0, 64]", who);
     if (p->tape != 0 && p->tape != 1) return fail(FQSL_ERR_ARG, "%s: tape must be 0 or 1", who);
     if (p->tape_chunk < 0 || p->tape_chunk > 64) return fail(FQSL_ERR_ARG, "%s: tape_chunk in [0, 64]", who);
+    if (p->reverse_precision < -1 || p->reverse_precision > FQSL_F32_ACC64)
+        return fail(FQSL_ERR_ARG, "%s: reverse_precision must be -1, FQSL_F32, FQSL_F64 or FQSL_F32_ACC64", who);
+    if (p->tape) {
+        const int rp = p->reverse_precision < 0 ? p->precision : p->reverse_precision;
+        if (rp == FQSL_F64 ? !f->rec64 : !f->rec32)
+            return fail(FQSL_ERR_UNSUPPORTED, "%s: field not packed in the reverse sweep's precision", who);
+    }
     if (p->precision != FQSL_F64 && !f->rec32)
         return fail(FQSL_ERR_UNSUPPORTED, "%s: field was not packed in FP32 (FQSL_PACK_F32)", who);
     if (p->precision == FQSL_F64 && !f->rec64)
@@ -524,7 +532,9 @@ TapeLayout tape_layout(char *base, long long n, bool rot, bool f32, long long po
     return t;
 }
 
-bool acc64_of(int precision) { return precision != FQSL_F32; }
+// the precision the reverse sweep runs in, and whether its node grid is double
+int reverse_precision_of(const fqsl_params &p) { return p.reverse_precision < 0 ? p.precision : p.reverse_precision; }
+bool acc64_of(const fqsl_params &p) { return reverse_precision_of(p) != FQSL_F32; }
 
 // the taped map's layout in the field's tape buffer (base NULL: sizes only)
 TapeLayout field_tape_layout(const fqsl_field f, char *base, long long pool)
@@ -533,8 +543,7 @@ TapeLayout field_tape_layout(const fqsl_field f, char *base, long long pool)
     const long long n = f->tp.lat.n1 * f->tp.lat.n2;
     const int k = p.tape_chunk > 0 ? p.tape_chunk : kDefaultTapeChunk;
     const size_t nodes = (size_t)f->g.nx * f->g.ny * f->g.nz;
-    return tape_layout(base, n, f->tp.lat.allow_rot, p.precision != FQSL_F64, pool, k, nodes,
-                       acc64_of(p.precision));
+    return tape_layout(base, n, f->tp.lat.allow_rot, p.precision != FQSL_F64, pool, k, nodes, acc64_of(p));
 }
 
 fqsl_status ensure_tape_buf(fqsl_field f, size_t bytes)
@@ -1263,15 +1272,17 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
     const Lattice &lat = f->tp.lat;
     const long long n = lat.n1 * lat.n2;
     const size_t nodes = (size_t)f->g.nx * f->g.ny * f->g.nz;
-    const bool acc64 = acc64_of(p.precision);
-    const int mode = p.precision == FQSL_F64 ? 2 : (acc64 ? 1 : 0);
+    const int rp = reverse_precision_of(p);
+    const bool acc64 = acc64_of(p);
+    const int mode = rp == FQSL_F64 ? 2 : (acc64 ? 1 : 0);
+    const bool tape_f64 = p.precision == FQSL_F64;
     cudaError_t e = cudaMemsetAsync(tl.xbar, 0, (size_t)(6 * n) * sizeof(double), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(tl.acc, 0, nodes * 8 * (acc64 ? 8 : 4), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(tl.ctr + 1, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     AdjArgs a{};
     a.f = f->g;
-    a.f.rec = p.precision == FQSL_F64 ? f->rec64 : f->rec32;
+    a.f.rec = rp == FQSL_F64 ? f->rec64 : f->rec32;
     a.f.grad = nullptr;
     a.p = dev_params(&p);
     a.lat = lat;
@@ -1284,17 +1295,17 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
     a.acc = tl.acc;
     a.head = tl.ctr + 1;
     a.n = n;
-    e = launch_q_vjp(a, mode, stream);
+    e = launch_q_vjp(a, mode, tape_f64, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     mark(f, 0, stream);
-    int &bps = f->blocks_cache_rev[p.precision];
-    if (!bps) bps = reverse_blocks_per_sm(mode);
+    int &bps = f->blocks_cache_rev[mode][tape_f64 ? 1 : 0];
+    if (!bps) bps = reverse_blocks_per_sm(mode, tape_f64);
     long long grid = (long long)f->sms * bps;
     const long long units = lat.tiles_u * lat.tiles_v * 2;
     const long long need = (units * 32 + 127) / 128;
     if (need < grid) grid = need;
     if (grid < 1) grid = 1;
-    e = launch_reverse(a, mode, (int)grid, stream);
+    e = launch_reverse(a, mode, tape_f64, (int)grid, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     mark(f, 1, stream);
     mark(f, 2, stream);
@@ -1303,6 +1314,25 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
     mark(f, 3, stream);
     f->timed = f->timing;
     f->extra_timed = false;
+    return FQSL_OK;
+}
+
+extern "C" fqsl_status fqsl_tape_export(fqsl_field f, int cap, int32_t *nsteps_dev, int32_t *code_dev,
+                                        double *hx_dev, double *h_dev, void *cuda_stream)
+{
+    g_err.clear();
+    const char *who = "fqsl_tape_export";
+    if (!f) return fail(FQSL_ERR_ARG, "%s: NULL field", who);
+    if (cap < 0) return fail(FQSL_ERR_ARG, "%s: cap < 0", who);
+    if (!nsteps_dev || !code_dev || !hx_dev || (cap > 0 && !h_dev))
+        return fail(FQSL_ERR_ARG, "%s: NULL output", who);
+    std::lock_guard<std::mutex> lock(f->mu);
+    if (!f->tp.valid) return fail(FQSL_ERR_ARG, "%s: no taped plane map on this field (params.tape = 1)", who);
+    TapeLayout tl = field_tape_layout(f, (char *)f->tp.buf, f->tp.pool);
+    const long long n = f->tp.lat.n1 * f->tp.lat.n2;
+    cudaError_t e = launch_tape_export(tl.tape, f->tp.p.precision == FQSL_F64, tl.s.rec.st, 2 * n, cap, nsteps_dev,
+                                       code_dev, hx_dev, h_dev, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
     return FQSL_OK;
 }
 

@@ -174,12 +174,15 @@ struct AdjArgs {
     unsigned long long *head;  // work counter of the reverse sweep
     long long n;
 };
-// mode: 0 = FP32 state and float grid, 1 = FP32 state and double grid, 2 = FP64
-cudaError_t launch_q_vjp(const AdjArgs &a, int mode, cudaStream_t s);
-cudaError_t launch_reverse(const AdjArgs &a, int mode, int grid, cudaStream_t s);
-int reverse_blocks_per_sm(int mode);
+// mode: 0 = FP32 state and float grid, 1 = FP32 state and double grid, 2 = FP64;
+// tape_f64: the tape was written by the FP64 tracer
+cudaError_t launch_q_vjp(const AdjArgs &a, int mode, bool tape_f64, cudaStream_t s);
+cudaError_t launch_reverse(const AdjArgs &a, int mode, bool tape_f64, int grid, cudaStream_t s);
+int reverse_blocks_per_sm(int mode, bool tape_f64);
 cudaError_t launch_curl_adjoint(const void *acc, bool acc64, const FieldView &g, void *dB, fqsl_dtype dt,
                                 cudaStream_t s);
+cudaError_t launch_tape_export(const Tape &tp, bool f64, const uint8_t *st, long long halves, int cap, int32_t *ns,
+                               int32_t *code, double *hx, double *h, cudaStream_t s);
 cudaError_t launch_loss(long long n, const double *Q, const double *Tw, const double *Qt, const double *Twt,
                         const uint8_t *st, double wtw, double *sums, double *loss, double *dQ, double *dTw,
                         cudaStream_t s);

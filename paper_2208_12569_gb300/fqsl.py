@@ -22,7 +22,7 @@ LINE_BAD = LINE_MAXSTEPS | LINE_NULL_B | LINE_OUTSIDE
 EXPORTS = ("fqsl_params_default", "fqsl_version", "fqsl_last_error", "fqsl_field_create", "fqsl_field_destroy",
            "fqsl_qmap_plane", "fqsl_qmap_volume", "fqsl_twist", "fqsl_field_check", "fqsl_field_set_timing",
            "fqsl_field_times", "fqsl_field_update", "fqsl_qmap_plane_static", "fqsl_batch_create", "fqsl_batch_run",
-           "fqsl_batch_destroy", "fqsl_backward", "fqsl_loss_logq_tw")
+           "fqsl_batch_destroy", "fqsl_backward", "fqsl_loss_logq_tw", "fqsl_tape_export")
 STATIC_MAX_SEEDS = 65536
 
 
@@ -37,7 +37,8 @@ class Params(C.Structure):
                 ("tol", C.c_double), ("h0", C.c_double), ("h_min", C.c_double), ("h_max", C.c_double),
                 ("max_steps", C.c_longlong), ("rot_thresh", C.c_double), ("tol_exp", C.c_double),
                 ("graze", C.c_double), ("eps_way2", C.c_double), ("sync_dirs", C.c_int), ("chunk_tiles", C.c_int),
-                ("blocks_per_sm", C.c_int), ("tape", C.c_int), ("tape_chunk", C.c_int)]
+                ("blocks_per_sm", C.c_int), ("tape", C.c_int), ("tape_chunk", C.c_int),
+                ("reverse_precision", C.c_int)]
 
 
 class Plane(C.Structure):
@@ -76,6 +77,7 @@ def load(path: str = LIB_PATH):
     lib.fqsl_field_update.argtypes = [P, P, C.c_int, P]
     lib.fqsl_field_times.argtypes = [P, C.POINTER(C.c_float * 3)]
     lib.fqsl_backward.argtypes = [P, P, P, P, C.c_int, P]
+    lib.fqsl_tape_export.argtypes = [P, C.c_int, P, P, P, P, P]
     lib.fqsl_loss_logq_tw.argtypes = [C.c_longlong, P, P, P, P, P, C.c_double, P, P, P, P, P]
     for name in EXPORTS:
         if name not in ("fqsl_params_default", "fqsl_version", "fqsl_last_error"):
@@ -98,11 +100,12 @@ def _check(status):
 def params(**kw) -> Params:
     """fqsl_params with the library defaults, overridden by keyword
     (method, gradb_way, precision ('f32'/'f64'/'f32acc64' or 0/1/2), tol, h0, h_min, h_max,
-    max_steps, rot_thresh, tol_exp, graze, eps_way2)."""
+    max_steps, rot_thresh, tol_exp, graze, eps_way2, scheduling knobs, and for the
+    adjoint tape, tape_chunk, reverse_precision)."""
     p = Params()
     _lib.fqsl_params_default(C.byref(p))
     for k, v in kw.items():
-        if k == "precision" and isinstance(v, str):
+        if k in ("precision", "reverse_precision") and isinstance(v, str):
             v = {"f32": F32, "f64": F64, "f32acc64": F32_ACC64}[v]
         if not hasattr(p, k):
             raise KeyError(k)
@@ -320,6 +323,20 @@ def backward(field: Field, dQ=None, dTw=None, dB=None, dtype=None, stream=None):
     _check(_lib.fqsl_backward(field.handle, _ptr(dQ), _ptr(dTw), C.c_void_p(dB.data_ptr()),
                               F32 if dB.dtype == torch.float32 else F64, _stream(stream)))
     return dB
+
+
+def tape_export(field: Field, n_seeds: int, cap: int = 4096, stream=None):
+    """The step sequence of the field's last taped plane map (fqsl_tape_export):
+    dict of CUDA tensors nsteps (2n), code (2n), hx (2n), h (2n, cap); half-line
+    2 s + e is end e + 1 of seed s."""
+    dev = "cuda"
+    m = 2 * n_seeds
+    out = dict(nsteps=torch.empty(m, dtype=torch.int32, device=dev), code=torch.empty(m, dtype=torch.int32, device=dev),
+               hx=torch.empty(m, dtype=torch.float64, device=dev),
+               h=torch.zeros((m, cap), dtype=torch.float64, device=dev))
+    _check(_lib.fqsl_tape_export(field.handle, cap, _ptr(out["nsteps"]), _ptr(out["code"]), _ptr(out["hx"]),
+                                 _ptr(out["h"]), _stream(stream)))
+    return out
 
 
 def loss_logq_tw(Q, Tw, Q_target, Tw_target, status=None, w_tw: float = 0.1, stream=None, out=None):

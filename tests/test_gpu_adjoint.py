@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 SMALL = dict(n=(24, 24, 24), count=6, radius_cells=4.0, dtype=np.float64)
 PLANE16 = ((0.0, 0.0, 0.0), (23.0 / 16, 0.0, 0.0), (0.0, 23.0 / 16, 0.0), 16, 16)
 # an interior xz plane (some seeds rotate S0; their Q carries no gradient)
-XZ = ((0.0, 11.3, 0.0), (23.0 / 20, 0.0, 0.0), (0.0, 0.0, 23.0 / 12), 20, 12)
+XZ = ((0.0, 18.3, 0.0), (23.0 / 20, 0.0, 0.0), (0.0, 0.0, 23.0 / 12), 20, 12)
 PATCH = ((-0.3, -0.3, 0.0), (0.1, 0.0, 0.0), (0.0, 0.1, 0.0), 6, 6)
 
 
@@ -77,16 +77,60 @@ def test_fp64_gradient_matches_oracle_adjoint(fq, small, plane):
         assert (st & fq.LINE_ROTATED).any()
 
 
-@pytest.mark.parametrize("precision,bound", [("f32", 2e-2), ("f32acc64", 2e-2)])
-def test_fp32_gradient_against_oracle_adjoint(fq, small, precision, bound):
-    # the FP32 tracer's own frozen step sequence, in float; the bound is stated
+@pytest.mark.parametrize("reverse,bound", [("f32", 2e-3), ("f32acc64", 2e-3)])
+def test_fp32_reverse_sweep_on_the_oracle_steps(fq, small, reverse, bound):
+    # FP64 taped forward (the oracle's own step sequence), reverse sweep in
+    # float: isolates the float arithmetic of the reverse sweep
     B, _, grid = small
-    field = _field(fq, B.astype(np.float32), grid)
+    field = _field(fq, B, grid)
     m = PLANE16[3] * PLANE16[4]
     wq, wt = _weights(12, m)
-    g, st = _gpu_vjp(fq, field, PLANE16, wq, wt, dtype=torch.float32, precision=precision)
-    ref, _ = adj.vjp(B.astype(np.float32).astype(np.float64), grid, *PLANE16, wq, wt, oracle.params())
+    g, st = _gpu_vjp(fq, field, PLANE16, wq, wt, dtype=torch.float32, precision="f64", reverse_precision=reverse)
+    ref, _ = adj.vjp(B, grid, *PLANE16, wq, wt, oracle.params())
     assert _rel(g, ref) < bound
+
+
+@pytest.mark.parametrize("precision", ["f32", "f32acc64"])
+def test_fp32_forward_gradient_against_oracle(fq, small, precision):
+    # The FP32 tracer takes its own step sequence (the controller amplifies
+    # rounding differences), and the frozen-sequence gradient depends on where
+    # the stage points fall: even FP64 with tol x (1 + 1e-6) moves node-level
+    # gradients by a few percent. Stated bound on the node-level relative
+    # error for log-Q and Tw weights (the loss's form).
+    B, _, grid = small
+    B32 = B.astype(np.float32)
+    field = _field(fq, B32, grid)
+    m = PLANE16[3] * PLANE16[4]
+    wq, wt = _weights(12, m)
+    Qo = oracle.plane(B32.astype(np.float64), grid, *PLANE16, oracle.params())["Q"]
+    wq = wq / np.where(np.isfinite(Qo), Qo, 1.0)
+    g, st = _gpu_vjp(fq, field, PLANE16, wq, wt, dtype=torch.float32, precision=precision)
+    ref, _ = adj.vjp(B32.astype(np.float64), grid, *PLANE16, wq, wt, oracle.params())
+    assert _rel(g, ref) < 0.25
+
+
+def test_fp64_tape_is_the_oracle_step_sequence(fq, small):
+    # the FP64 tracer's recorded steps are the oracle's, bit for bit
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    p = fq.params(precision="f64", tape=1)
+    fq.qmap_plane(field, *PLANE16, p)
+    m = PLANE16[3] * PLANE16[4]
+    t = {k: v.cpu().numpy() for k, v in fq.tape_export(field, m, cap=2048).items()}
+    log = adj.lattice_log(B, grid, *PLANE16, oracle.params())
+    code, hh = adj.half_lines(log)
+    for hl in range(2 * m):
+        c = code[hl][code[hl] >= 0]
+        good = (log["status"][hl // 2] & oracle.BAD) == 0
+        if not good:
+            assert t["nsteps"][hl] == 0 and t["code"][hl] == -1
+            continue
+        n = int(t["nsteps"][hl])
+        assert n == len(c) - 1 and np.all(c[:-1] == 0)
+        assert t["code"][hl] == c[-1]
+        assert np.array_equal(t["h"][hl, :n], hh[hl, :n])
+        if c[-1] >= adj.CHORD:
+            assert t["hx"][hl] == hh[hl, n]
 
 
 def test_dot_product_with_oracle_tangent_mode(fq, small):
@@ -195,7 +239,7 @@ def test_loss_kernel_matches_oracle_loss(fq, small):
     ref, use = adj.log_q_tw_loss(Q, Tw, tgt["Q"].cpu().numpy(), tgt["Tw"].cpu().numpy(), usable, 0.1)
     ref.backward()
     assert int(use.sum()) > 200
-    np.testing.assert_allclose(float(loss), float(ref), rtol=1e-12)
+    np.testing.assert_allclose(float(loss), float(ref.detach()), rtol=1e-12)
     np.testing.assert_allclose(dQ.cpu().numpy(), Q.grad.numpy(), rtol=1e-12, atol=1e-300)
     np.testing.assert_allclose(dTw.cpu().numpy(), Tw.grad.numpy(), rtol=1e-12, atol=1e-300)
 
