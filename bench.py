@@ -388,6 +388,243 @@ def run_batch(args):
         b.close()
 
 
+ADJ_CUBE = (128, 128, 64)
+ADJ_SEEDS = 256
+ADJ_WORKLOAD = "adjoint_monopole24_twisttube_128x128x64_f32_z0plane_256x256_logQ_Tw_loss_methodI"
+ADJ_METRIC = "adjoint s/grad"
+ADJ_SAMPLE = 64  # oracle seeds per check (plus their 4-neighbour lines)
+# Algorithmic work of one accepted step in the reverse sweep, counted from
+# adjoint.cu: the 5 stages of the 4th-order solution are evaluated once (the
+# forward values the VJP needs: 5 right-hand sides of 145 flops and 8 x 32-byte
+# corner records each) and reversed once (5 stage VJPs: 8 corners x 6
+# components x 4 products for the value and its 3 derivatives = 192 FMAs, 60
+# flops of local derivative, 48 products for the scatter, 3 x 6 for the
+# position adjoint; 8 x 32-byte records and 8 x 24 bytes of scattered adjoints).
+# The recompute of each chunk from its checkpoint is extra (not counted).
+REV_FLOPS_PER_STEP = 5 * 145 + 5 * (2 * 192 + 60 + 48 + 36) + 250
+REV_GATHER_BYTES_PER_STEP = 10 * 8 * 32
+REV_SCATTER_BYTES_PER_STEP = 5 * 8 * 24
+
+
+def _adj_plane():
+    u = (float(ADJ_CUBE[0] - 1) / ADJ_SEEDS, 0.0, 0.0)
+    v = (0.0, float(ADJ_CUBE[1] - 1) / ADJ_SEEDS, 0.0)
+    return (0.0, 0.0, 0.0), u, v, ADJ_SEEDS, ADJ_SEEDS
+
+
+def run_adjoint(args):
+    """Differentiation workload: d(loss)/dB of the log-Q/Tw misfit on the z=0
+    map of a 128x128x64 monopole cube with a twist tube (256x256 seeds). A
+    step = repack B with its curl, the taped FP32 map, the loss and its
+    gradient, and the reverse sweep into dB (s per gradient)."""
+    import torch
+
+    import __graft_entry__
+    import oracle
+    import synth
+    from oracle import adjoint as oadj
+
+    __graft_entry__._builder().build()
+    import paper_2208_12569_gb300 as fq
+
+    dev = torch.device("cuda", 0)
+    B, Bt, grid = synth.adjoint_cubes(seed=SEED, n=ADJ_CUBE)
+    plane = _adj_plane()
+    n = ADJ_SEEDS * ADJ_SEEDS
+    Bd = torch.from_numpy(B).to(dev)
+    # one field per traced precision, as a user would create it (repacking a
+    # field repacks every precision it holds); a third with both for the
+    # FP64-forward / float-reverse check
+    field = fq.Field(Bd, grid.origin, grid.spacing, pack=("f32",))
+    field64 = fq.Field(Bd, grid.origin, grid.spacing, pack=("f64",))
+    fieldx = fq.Field(Bd, grid.origin, grid.spacing, pack=("f32", "f64"))
+    ftgt = fq.Field(torch.from_numpy(Bt).to(dev), grid.origin, grid.spacing, pack=("f32",))
+    tgt = fq.qmap_plane(ftgt, *plane, fq.params(precision="f32", tol=TOL))
+    out = fq.alloc_out(n, device=dev)
+    dB = torch.zeros_like(Bd)
+    dB64 = torch.zeros(Bd.shape, dtype=torch.float64, device=dev)
+    lbuf = dict(sums=torch.empty(2, dtype=torch.float64, device=dev),
+                loss=torch.empty((), dtype=torch.float64, device=dev),
+                dQ=torch.empty(n, dtype=torch.float64, device=dev), dTw=torch.empty(n, dtype=torch.float64, device=dev))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    p32 = fq.params(precision="f32", tol=TOL, tape=1)
+    p64 = fq.params(precision="f64", tol=TOL, tape=1)
+
+    def step(pp, Bsrc, g):
+        fld = field64 if pp.precision == fq.F64 else field
+        fld.update(Bsrc)
+        fq.qmap_plane(fld, *plane, pp, out=out)
+        fq.loss_logq_tw(out["Q"], out["Tw"], tgt["Q"], tgt["Tw"], out["status"], 0.1, out=lbuf)
+        g.zero_()
+        fq.backward(fld, lbuf["dQ"], lbuf["dTw"], g)
+
+    def timed(pp, g, k):
+        ms = []
+        for _ in range(k):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(pp, Bd, g)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    def kernel_times(pp, g, k):
+        field.set_timing(True)
+        fwd, rev, curlt = [], [], []
+        for _ in range(k):
+            flush.fill_(1.0)
+            field.update(Bd)
+            fq.qmap_plane(field, *plane, pp, out=out)
+            fwd.append(field.times()[0])
+            fq.loss_logq_tw(out["Q"], out["Tw"], tgt["Q"], tgt["Tw"], out["status"], 0.1, out=lbuf)
+            g.zero_()
+            fq.backward(field, lbuf["dQ"], lbuf["dTw"], g)
+            t = field.times()
+            rev.append(t[0])
+            curlt.append(t[2])
+        field.set_timing(False)
+        return float(np.mean(fwd)), float(np.mean(rev)), float(np.mean(curlt))
+
+    for _ in range(args.warmup):
+        step(p32, Bd, dB)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ms32 = timed(p32, dB, args.steps)
+    clk = clocks.stop()
+    loss32 = float(lbuf["loss"])
+    g32 = dB.cpu().numpy().astype(np.float64)
+    tape = fq.tape_export(field, n, cap=0)
+    acc_steps = float(tape["nsteps"].to(torch.float64).sum())
+    t_fwd, t_rev, t_curl = kernel_times(p32, dB, max(3, args.steps // 2))
+    # FP64 beside it
+    step(p64, Bd, dB64)
+    torch.cuda.synchronize()
+    ms64 = timed(p64, dB64, max(2, args.fp64_steps))
+    loss64 = float(lbuf["loss"])
+    g64 = dB64.cpu().numpy()
+
+    # end to end from pinned host memory: B in, loss and dB out
+    Bh = torch.from_numpy(B).pin_memory()
+    Bdev = torch.empty_like(Bd)
+    dBh = torch.empty(Bd.shape, dtype=torch.float32).pin_memory()
+    lh = torch.empty((), dtype=torch.float64).pin_memory()
+    e2e = []
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Bdev.copy_(Bh, non_blocking=True)
+        step(p32, Bdev, dB)
+        dBh.copy_(dB, non_blocking=True)
+        lh.copy_(lbuf["loss"], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e.append(e0.elapsed_time(e1))
+
+    # oracle checks on a seeded sample of seeds (weights only there): the
+    # FP64 gradient, the float reverse sweep on the FP64 steps, and the FP32
+    # gradient; timed as the CPU baseline
+    rng = np.random.default_rng(SEED)
+    sample = np.sort(rng.choice(n, ADJ_SAMPLE, replace=False))
+    wq, wt = rng.standard_normal(ADJ_SAMPLE), rng.standard_normal(ADJ_SAMPLE)
+    WQ = torch.zeros(n, dtype=torch.float64, device=dev)
+    WT = torch.zeros(n, dtype=torch.float64, device=dev)
+    WQ[torch.from_numpy(sample).to(dev)] = torch.from_numpy(wq).to(dev)
+    WT[torch.from_numpy(sample).to(dev)] = torch.from_numpy(wt).to(dev)
+    B64 = B.astype(np.float64)
+    t0 = time.perf_counter()
+    ref, info = oadj.vjp_sample(B64, grid, *plane, sample, wq, wt, oracle.params(tol=TOL))
+    ora_s = time.perf_counter() - t0
+
+    def gpu_vjp(pp):
+        fieldx.update(Bd)
+        fq.qmap_plane(fieldx, *plane, pp, out=out)
+        g = torch.zeros(Bd.shape, dtype=torch.float64, device=dev)
+        fq.backward(fieldx, WQ, WT, g)
+        return g.cpu().numpy()
+
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
+    errs = {"f64": rel(gpu_vjp(p64), ref),
+            "f64_forward_f32_reverse": rel(gpu_vjp(fq.params(precision="f64", tol=TOL, tape=1,
+                                                             reverse_precision="f32")), ref),
+            "f32": rel(gpu_vjp(p32), ref),
+            "f32_vs_f64_full_loss_gradient": rel(g32, g64),
+            "scale_invariance_f32": float(abs(np.sum(g32 * B)) / (np.linalg.norm(g32) * np.linalg.norm(B))),
+            "scale_invariance_f64": float(abs(np.sum(g64 * B)) / (np.linalg.norm(g64) * np.linalg.norm(B))),
+            "sample_seeds": ADJ_SAMPLE, "sample_lines": int(len(info["lines"]))}
+    peaks, peak_kind = _measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    achieved = acc_steps * REV_FLOPS_PER_STEP / (t_rev / 1000.0) / 1e12
+    s32 = float(np.mean(ms32)) / 1000.0
+    line = {"metric": ADJ_METRIC, "value": s32, "unit": "s/grad", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * s32, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": ADJ_WORKLOAD, "cube": list(ADJ_CUBE), "seeds": [ADJ_SEEDS, ADJ_SEEDS],
+                       "tol_perp": TOL, "tape_chunk": 16, "loss": "mean (log10 Q - log10 Qt)^2 + 0.1 (Tw - Twt)^2",
+                       "l2": "flushed between steps (256 MB write)", "inputs_resident": True},
+            "loss": {"f32": loss32, "f64": loss64},
+            "fp64": {"value": float(np.mean(ms64)) / 1000.0, "unit": "s/grad"},
+            "kernels_ms": {"forward_taped_trace_f32": t_fwd, "reverse_sweep_f32": t_rev, "curl_transpose": t_curl},
+            "work": {"accepted_steps": acc_steps, "per_half_line": acc_steps / (2 * n)},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved / alu_peak, "traffic": None, "kernel": "reverse sweep (k_reverse<float>)",
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, peak_kind),
+                         "gather_TBs": acc_steps * REV_GATHER_BYTES_PER_STEP / (t_rev / 1000.0) / 1e12,
+                         "scatter_GBs": acc_steps * REV_SCATTER_BYTES_PER_STEP / (t_rev / 1000.0) / 1e9},
+            "error_vs_oracle": errs,
+            "e2e": {"value": float(np.mean(e2e)) / 1000.0, "unit": "s/grad", "h2d_bytes_per_step": int(B.nbytes),
+                    "d2h_bytes_per_step": int(B.nbytes + 8)},
+            "gpu_launches": 11 * args.steps, "clocks": clk,
+            "cpu_baseline": {"value": ora_s * n / ADJ_SAMPLE, "unit": "s/grad", "cores": oracle.max_threads(),
+                             "kind": "oracle",
+                             "sample": "%d seeded-random seeds (%d lines with their neighbours), %.1f s, scaled "
+                                       "by %d" % (ADJ_SAMPLE, len(info["lines"]), ora_s, n // ADJ_SAMPLE)}}
+    print(json.dumps(line), flush=True)
+    for fl in (field, field64, fieldx, ftgt):
+        fl.close()
+
+
+def run_reference_adjoint(args):
+    """The FP64 CPU adjoint oracle on a bounded seeded sample of the
+    differentiation workload, scaled to seconds per full gradient."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    from oracle import adjoint as oadj
+
+    oracle.build()
+    B, _, grid = synth.adjoint_cubes(seed=SEED, n=ADJ_CUBE)
+    B64 = B.astype(np.float64)
+    plane = _adj_plane()
+    n = ADJ_SEEDS * ADJ_SEEDS
+    rng = np.random.default_rng(17)
+    per_step = 16
+    times = []
+    for it in range(args.warmup + args.steps):
+        sample = np.sort(rng.choice(n, per_step, replace=False))
+        t0 = time.perf_counter()
+        oadj.vjp_sample(B64, grid, *plane, sample, np.ones(per_step), np.ones(per_step), oracle.params(tol=TOL))
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = float(np.mean(times)) * n / per_step
+    line = {"impl": "reference", "metric": ADJ_METRIC, "value": value, "unit": "s/grad", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": ADJ_WORKLOAD, "sample_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": "s/grad", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": "%d seeded-random seeds per step, scaled by %d" % (per_step, n // per_step)},
+            "e2e": {"value": value, "unit": "s/grad", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -398,12 +635,18 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--only-f32", action="store_true",
                     help="time only the FP32 map (no FP64, e2e or CPU legs); used for ncu captures")
-    ap.add_argument("--workload", default="plane", choices=["plane", "volume", "batch"],
+    ap.add_argument("--workload", default="plane", choices=["plane", "volume", "batch", "adjoint"],
                     help="plane: the benchmark line; volume: the large-volume configuration; "
-                         "batch: 48 uneven cubes in one launch")
+                         "batch: 48 uneven cubes in one launch; adjoint: d(loss)/dB on the 128x128x64 cube")
     args = ap.parse_args()
     if args.impl == "reference":
-        run_reference(args)
+        if args.workload == "adjoint":
+            run_reference_adjoint(args)
+        else:
+            run_reference(args)
+        return
+    if args.workload == "adjoint":
+        run_adjoint(args)
         return
     if args.workload == "volume":
         run_volume(args)

@@ -111,7 +111,7 @@ typedef struct {
     int tape;             /* 1: fqsl_qmap_plane (Method I) also records the step tape that fqsl_backward
                              differentiates (0 = default, no tape). Results do not depend on it. */
     int tape_chunk;       /* steps per tape chunk, i.e. the checkpoint interval k of the reverse sweep
-                             (1..64; 0 = default 16) */
+                             (1..32; 0 = default 16) */
     int reverse_precision; /* precision of fqsl_backward's reverse sweep for this taped map: -1 (default)
                              = precision; FQSL_F32, FQSL_F32_ACC64 (float state, double node grid) or
                              FQSL_F64; the field must be packed in it */
@@ -307,9 +307,9 @@ FQSL_API fqsl_status fqsl_backward(fqsl_field field, const double *dQ_dev, const
 /* The step sequence of the field's last taped plane map (the paper has no
  * counterpart; for inspection and for replaying a map's exact steps
  * elsewhere). For half-line hl = 2 s + e (seed s, end e = 0 for end 1):
- * nsteps_dev[hl] accepted steps (-1 if more than cap; 0 with code -1 for a
- * line with MAXSTEPS, NULL_B or OUTSIDE), h_dev[hl * cap + i] their sizes in
- * cells in order, code_dev[hl] how the direction ended (16 + face: exit step
+ * nsteps_dev[hl] accepted steps (0 with code -1 for a line with MAXSTEPS,
+ * NULL_B or OUTSIDE), h_dev[hl * cap + i] their sizes in cells in order when
+ * nsteps_dev[hl] <= cap (cap = 0: counts only), code_dev[hl] how the direction ended (16 + face: exit step
  * onto that face; 40 + face: the same with the other coordinates clamped into
  * the box; 48 + face: chord onto that face after an exiting step of size
  * hx_dev[hl], which is 0 otherwise). Device arrays of 2 nu nv elements

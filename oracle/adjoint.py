@@ -38,14 +38,16 @@ _B4 = [25 / 216, 0.0, 1408 / 2565, 2197 / 4104, -1 / 5, 0.0]
 START, STEP, EXIT, EXIT_CLAMPED, CHORD = 99, 0, 16, 40, 48
 
 
-def lattice_log(B, grid, origin, u, v, nu, nv, p=None, cap=8192, J=None):
-    """Trace every line of the plane lattice once with the C oracle; return
-    its step records and per-line outcomes (numpy arrays)."""
+def lattice_log(B, grid, origin, u, v, nu, nv, p=None, cap=8192, J=None, which=None):
+    """Trace every line of the plane lattice (or only the lattice indices in
+    ``which``, in that order) once with the C oracle; return their step
+    records and outcomes (numpy arrays, one row per traced line)."""
     p = p or params()
     B = _f64(B)
     J = _f64(curl(B, grid) if J is None else J)
     n, o, d = _grid_args(grid)
-    m = nu * nv
+    wh = None if which is None else np.ascontiguousarray(which, dtype=np.int64)
+    m = nu * nv if wh is None else len(wh)
     out = dict(h=np.zeros((m, cap)), code=np.zeros((m, cap), np.int32), n=np.zeros(m, np.int32),
                s0=np.zeros(m), tol=np.zeros(m), bn0=np.zeros(m), ends=np.zeros((m, 2, 11)),
                faces=np.zeros((m, 2), np.int32), status=np.zeros(m, np.int32))
@@ -57,7 +59,7 @@ def lattice_log(B, grid, origin, u, v, nu, nv, p=None, cap=8192, J=None):
     rc = L.oracle_lattice_log(_p(B), _p(J), _p(n), _p(o), _p(d), _p(lo), _p(a1), _p(a2), _p(ln), C.byref(p),
                               C.c_int(cap), _p(out["h"]), _p(out["code"]), _p(out["n"]), _p(out["s0"]),
                               _p(out["tol"]), _p(out["bn0"]), _p(out["ends"]), _p(out["faces"]),
-                              _p(out["status"]))
+                              _p(out["status"]), _p(wh), C.c_longlong(0 if wh is None else len(wh)))
     if rc:
         raise ValueError("oracle_lattice_log: error %d" % rc)
     if np.any(out["n"] < 0):
@@ -227,36 +229,42 @@ def replay(fld, xi0, s0, log):
     return xi.reshape(m, 2, 3), tw.reshape(m, 2)
 
 
-def stencils(faces, status, nu, nv, du, dv):
+def stencils(faces, status, nu, nv, du, dv, targets=None, row=None):
     """Method I difference coefficients (reading R8) chosen from the traced
-    faces: a list of (seed, end, lattice axis, line, coefficient) with
-    J_e[r][c](seed) = sum coefficient * face coordinate r of that line's end e;
-    and the seeds left MIXED (no usable neighbour on some axis)."""
+    faces: a list of (target position, end, lattice axis, row, coefficient)
+    with J_e[r][c](target) = sum coefficient * face coordinate r of that row's
+    end e; and the targets left MIXED (no usable neighbour on some axis).
+    Rows are the traced lines (row[lattice index]; all, in order, by
+    default); targets the seeds whose Q is formed (default all)."""
     m = nu * nv
+    targets = np.arange(m) if targets is None else np.asarray(targets)
+    row = {k: k for k in range(m)} if row is None else row
     ok = (status & BAD) == 0
     entries = []
-    mixed = np.zeros(m, bool)
-    for s in range(m):
-        if not ok[s]:
+    mixed = np.zeros(len(targets), bool)
+    for t, s in enumerate(targets):
+        s = int(s)
+        rs = row[s]
+        if not ok[rs]:
             continue
         i, j = s % nu, s // nu
         for e in range(2):
-            fe = faces[s, e]
+            fe = faces[rs, e]
             for c, (di, dj, dl) in enumerate(((1, 0, du), (0, 1, dv))):
                 def usable(ii, jj):
                     if not (0 <= ii < nu and 0 <= jj < nv):
                         return None
-                    k = ii + nu * jj
-                    return k if ok[k] and faces[k, e] == fe else None
+                    k = row.get(ii + nu * jj)
+                    return k if k is not None and ok[k] and faces[k, e] == fe else None
                 kp, km = usable(i + di, j + dj), usable(i - di, j - dj)
                 if kp is not None and km is not None:
-                    entries += [(s, e, c, kp, 0.5 / dl), (s, e, c, km, -0.5 / dl)]
+                    entries += [(t, e, c, kp, 0.5 / dl), (t, e, c, km, -0.5 / dl)]
                 elif kp is not None:
-                    entries += [(s, e, c, kp, 1.0 / dl), (s, e, c, s, -1.0 / dl)]
+                    entries += [(t, e, c, kp, 1.0 / dl), (t, e, c, rs, -1.0 / dl)]
                 elif km is not None:
-                    entries += [(s, e, c, s, 1.0 / dl), (s, e, c, km, -1.0 / dl)]
+                    entries += [(t, e, c, rs, 1.0 / dl), (t, e, c, km, -1.0 / dl)]
                 else:
-                    mixed[s] = True
+                    mixed[t] = True
     return entries, mixed
 
 
@@ -272,52 +280,75 @@ def seeds_index(grid, origin, u, v, nu, nv):
     return (r0 - np.asarray(grid.origin, float)) / np.asarray(grid.spacing, float)
 
 
-def qmap_t(Bt, grid, origin, u, v, nu, nv, log):
-    """Q and Tw of the lattice (differentiable in the tensor Bt) from the
-    frozen step sequence in log. Returns (Q, Tw, usable mask, end positions)."""
+def neighbourhood(seeds, nu, nv):
+    """The seeds and their lattice neighbours (the lines Method I differences
+    use), sorted."""
+    out = set()
+    for s in np.asarray(seeds).ravel():
+        i, j = int(s) % nu, int(s) // nu
+        for di, dj in ((0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)):
+            if 0 <= i + di < nu and 0 <= j + dj < nv:
+                out.add(i + di + nu * (j + dj))
+    return np.array(sorted(out), dtype=np.int64)
+
+
+def qmap_t(Bt, grid, origin, u, v, nu, nv, log, lines=None, targets=None):
+    """Q and Tw (differentiable in the tensor Bt) from the frozen step
+    sequence in log. ``lines``: the lattice indices of log's rows (default:
+    every seed, in order); ``targets``: the seeds whose Q and Tw are formed
+    (default: every seed), each with its lattice neighbours among the lines.
+    Returns (Q, Tw, usable mask, end positions of the rows)."""
     n = grid.n
     Jt = curl_t(Bt, grid.spacing)
     fld = _Field(Bt, Jt, n, grid.spacing)
     m = nu * nv
-    xi0 = torch.from_numpy(seeds_index(grid, origin, u, v, nu, nv))
+    lines = np.arange(m) if lines is None else np.asarray(lines, dtype=np.int64)
+    targets = lines if targets is None else np.asarray(targets, dtype=np.int64)
+    row = {int(l): k for k, l in enumerate(lines)}
+    tr = np.array([row[int(t)] for t in targets], dtype=np.int64)
+    mr = len(lines)
+    xi_all = seeds_index(grid, origin, u, v, nu, nv)
+    xi0 = torch.from_numpy(xi_all[lines])
     s0 = torch.from_numpy(log["s0"])
     xi, tw = replay(fld, xi0, s0, log)
     faces, status = log["faces"], log["status"]
     good = (status & BAD) == 0
     o = torch.tensor(grid.origin, dtype=torch.float64)
-    phys = o + fld.d * xi  # (m, 2, 3)
-    rows = []
+    phys = o + fld.d * xi  # (rows, 2, 3)
+    cols = []
     for e in range(2):
         for r in range(2):
-            idx = torch.from_numpy(np.array([_FACE_AXES[max(faces[s, e], 0) // 2][r] for s in range(m)]))
-            rows.append(phys[:, e, :].gather(1, idx[:, None])[:, 0])
-    fc = torch.stack(rows, dim=1).reshape(m, 2, 2)  # line, end, face row
+            idx = torch.from_numpy(np.array([_FACE_AXES[max(faces[k, e], 0) // 2][r] for k in range(mr)]))
+            cols.append(phys[:, e, :].gather(1, idx[:, None])[:, 0])
+    fc = torch.stack(cols, dim=1).reshape(mr, 2, 2)  # row, end, face coordinate
     du, dv = float(np.linalg.norm(u)), float(np.linalg.norm(v))
-    entries, mixed = stencils(faces, status, nu, nv, du, dv)
-    Jm = torch.zeros((m, 2, 2, 2), dtype=torch.float64)  # seed, end, face row r, lattice axis c
+    entries, mixed = stencils(faces, status, nu, nv, du, dv, targets, row)
+    nt = len(targets)
+    Jm = torch.zeros((nt, 2, 2, 2), dtype=torch.float64)  # target, end, face row r, lattice axis c
     if entries:
         es = np.array(entries, dtype=float)
-        s_i, e_i, c_i, l_i = (torch.from_numpy(es[:, k].astype(np.int64)) for k in range(4))
+        t_i, e_i, c_i, l_i = (torch.from_numpy(es[:, k].astype(np.int64)) for k in range(4))
         coef = torch.from_numpy(es[:, 4])
         for r in range(2):
-            Jm = Jm.index_put((s_i, e_i, torch.full_like(s_i, r), c_i), coef * fc[l_i, e_i, r], accumulate=True)
+            Jm = Jm.index_put((t_i, e_i, torch.full_like(t_i, r), c_i), coef * fc[l_i, e_i, r], accumulate=True)
     J1, J2 = Jm[:, 0], Jm[:, 1]
     adj = torch.stack([torch.stack([J1[:, 1, 1], -J1[:, 0, 1]], -1),
                        torch.stack([-J1[:, 1, 0], J1[:, 0, 0]], -1)], 1)
     M = torch.einsum("srk,skc->src", J2, adj)
     norm2 = (M * M).sum((1, 2))
-    Bend, _ = fld.interp(xi.reshape(-1, 3))
-    Bend = Bend.reshape(m, 2, 3)
-    fax = torch.from_numpy(np.maximum(faces, 0) // 2)
+    trt = torch.from_numpy(tr)
+    Bend, _ = fld.interp(xi[trt].reshape(-1, 3))
+    Bend = Bend.reshape(nt, 2, 3)
+    fax = torch.from_numpy(np.maximum(faces[tr], 0) // 2)
     bn1 = Bend[:, 0].gather(1, fax[:, 0:1])[:, 0]
     bn2 = Bend[:, 1].gather(1, fax[:, 1:2])[:, 0]
     n0 = np.cross(np.asarray(u, float), np.asarray(v, float))
     n0 = torch.from_numpy(n0 / np.linalg.norm(n0))
-    B0, _ = fld.interp(xi0)
+    B0, _ = fld.interp(torch.from_numpy(xi_all[targets]))
     bn0 = (B0 * n0).sum(-1)
     Q = norm2 * torch.abs(bn1 * bn2) / (bn0 * bn0)
-    usable = torch.from_numpy(good & ~mixed & ((status & ROTATED) == 0))
-    return Q, tw.sum(1), usable, xi
+    usable = torch.from_numpy(good[tr] & ~mixed & ((status[tr] & ROTATED) == 0))
+    return Q, tw[trt].sum(1), usable, xi
 
 
 def log_q_tw_loss(Q, Tw, Qt, Twt, usable, wtw=0.1):
@@ -362,6 +393,27 @@ def vjp(B, grid, origin, u, v, nu, nv, wQ, wTw, p=None, log=None):
     s = (wq[usable] * Q[usable]).sum() + (wt[good] * Tw[good]).sum()
     s.backward()
     return Bt.grad.numpy(), log
+
+
+def vjp_sample(B, grid, origin, u, v, nu, nv, seeds, wQ, wTw, p=None):
+    """J^T w for weights on a sample of seeds only (wQ, wTw: one per sample
+    seed): traces just the sample's lines and their lattice neighbours, so it
+    scales to full-size lattices. Same masks as vjp()."""
+    p = p or params()
+    B = _f64(B)
+    seeds = np.asarray(seeds, dtype=np.int64)
+    lines = neighbourhood(seeds, nu, nv)
+    log = lattice_log(B, grid, origin, u, v, nu, nv, p, which=lines)
+    Bt = torch.tensor(B, dtype=torch.float64, requires_grad=True)
+    Q, Tw, usable, _ = qmap_t(Bt, grid, origin, u, v, nu, nv, log, lines=lines, targets=seeds)
+    row = {int(l): k for k, l in enumerate(lines)}
+    good = torch.from_numpy((log["status"][[row[int(s)] for s in seeds]] & BAD) == 0)
+    wq = torch.as_tensor(np.asarray(wQ, float))
+    wt = torch.as_tensor(np.asarray(wTw, float))
+    s = (wq[usable] * Q[usable]).sum() + (wt[good] * Tw[good]).sum()
+    s.backward()
+    return Bt.grad.numpy(), dict(Q=Q.detach().numpy(), Tw=Tw.detach().numpy(), usable=usable.numpy(),
+                                 good=good.numpy(), lines=lines)
 
 
 def jvp(B, grid, origin, u, v, nu, nv, dB, p=None, log=None):

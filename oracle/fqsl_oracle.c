@@ -896,14 +896,16 @@ int oracle_max_threads(void)
 #endif
 }
 
-/* Every line of a plane lattice traced once, with the record of its accepted
+/* Lines of a plane lattice traced once, with the record of their accepted
  * steps (OLog codes; at most cap entries per line, logn[s] = -1 on overflow),
- * its orientation sign s0, tolerance, Bn0, end states (s x 2 x 11), faces and
- * status. Used by the adjoint tests to replay the frozen step sequence. */
+ * orientation sign s0, tolerance, Bn0, end states (s x 2 x 11), faces and
+ * status: every seed (which = NULL; output s = lattice index), or the nwhich
+ * lattice indices which[] (output s = position in which). Used by the adjoint
+ * tests to replay the frozen step sequence. */
 int oracle_lattice_log(const double *B, const double *J, const long long n[3], const double o[3], const double d[3],
                        const double lo[3], const double a1[3], const double a2[3], const long long ln[2],
                        const OParams *p, int cap, double *logh, int *logc, int *logn, double *s0o, double *tolo,
-                       double *bn0o, double *ends, int *faces, int *st)
+                       double *bn0o, double *ends, int *faces, int *st, const long long *which, long long nwhich)
 {
     OField f;
     if (o_make_field(&f, B, J, NULL, n, o, d)) return 1;
@@ -918,10 +920,14 @@ int oracle_lattice_log(const double *B, const double *J, const long long n[3], c
     L.n1 = ln[0];
     L.n2 = ln[1];
     L.n3 = 1;
-    long long total = L.n1 * L.n2;
+    long long total = which ? nwhich : L.n1 * L.n2;
+    if (which)
+        for (long long s = 0; s < nwhich; s++)
+            if (which[s] < 0 || which[s] >= L.n1 * L.n2) return 3;
 #pragma omp parallel for schedule(dynamic, 4)
     for (long long s = 0; s < total; s++) {
-        long long i = s % L.n1, j = s / L.n1;
+        long long idx = which ? which[s] : s;
+        long long i = idx % L.n1, j = idx / L.n1;
         OSeed S;
         OLine c;
         OLog g = {logh + s * cap, logc + s * cap, cap, 0, 0};

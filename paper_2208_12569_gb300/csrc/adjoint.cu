@@ -32,6 +32,25 @@ namespace adj {
 
 using trace::Fehlberg;
 
+// Failed index checks (the access is skipped and the first failure kept for
+// the host): 1 chunk id, 2 steps in a chunk, 3 end code, 4 cell of a gather or
+// scatter, 5 footpoint-adjoint index.
+__device__ __forceinline__ void record_fail(unsigned long long *err, unsigned code, long long value)
+{
+    if (!err) return;
+    const unsigned long long w = ((unsigned long long)code << 56) | ((unsigned long long)value & ((1ull << 56) - 1));
+    atomicCAS(err, 0ull, w);
+    atomicAdd(err + 1, 1ull);
+}
+
+// the 8 corners of the cell at node base lie in the cube (else record it)
+__device__ __forceinline__ bool cell_ok(const FieldView &f, long long base)
+{
+    const bool ok = base >= 0 && base + (long long)f.nx * f.ny + f.nx + 1 < f.nodes;
+    if (!ok) record_fail(f.err, 4, base);
+    return ok;
+}
+
 // ---------------------------------------------------------------------------
 // trilinear interpolation with the derivative of the interpolant
 // ---------------------------------------------------------------------------
@@ -142,6 +161,7 @@ __device__ __forceinline__ void scatter_node(double *acc, long long node, double
 template <typename T, typename AccT>
 __device__ __forceinline__ void scatter(const FieldView &f, const Cell<T> &c, const T Vb[6], AccT *acc)
 {
+    if (Vb[0] == (T)0 && Vb[1] == (T)0 && Vb[2] == (T)0 && Vb[3] == (T)0 && Vb[4] == (T)0 && Vb[5] == (T)0) return;
     AccT vb[6];
 #pragma unroll
     for (int k = 0; k < 6; k++) vb[k] = (AccT)Vb[k];
@@ -177,10 +197,23 @@ __device__ __forceinline__ double inv_spacing<double>(const FieldView &f, int a)
     return 1.0 / f.d[a];
 }
 
-template <typename T, typename AccT, typename Bars>
-__device__ __forceinline__ void stage_vjp(const FieldView &f, T sgn, T px, T py, T pz, Bars bars, T pb[3], AccT *acc)
+template <typename T>
+struct V3 {
+    T x, y, z;
+};
+
+// Stage VJP. ax < 0: the adjoints of F and dtw are
+// (kb, twb); ax >= 0 (exit step): kb and twb are the adjoints of K = F/F_ax
+// and dtw/F_ax, converted with the stage's own F_ax. All-zero adjoints
+// return at once.
+template <typename T, typename AccT>
+__device__ __forceinline__ V3<T> stage_vjp(const FieldView &f, T sgn, T px, T py, T pz, int ax, T kb0, T kb1, T kb2,
+                                        T twb, AccT *acc)
 {
+    V3<T> r = {(T)0, (T)0, (T)0};
+    if (kb0 == (T)0 && kb1 == (T)0 && kb2 == (T)0 && twb == (T)0) return r;
     const Cell<T> c = cell_of(f, px, py, pz);
+    if (!cell_ok(f, c.base)) return r;
     T V[6], dV[3][6];
     interp_d(f, c, V, dV);
     const T rd[3] = {inv_spacing<T>(f, 0), inv_spacing<T>(f, 1), inv_spacing<T>(f, 2)};
@@ -189,13 +222,22 @@ __device__ __forceinline__ void stage_vjp(const FieldView &f, T sgn, T px, T py,
     const T BB = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
     const T nbt = sqrt(bb), m = sqrt(BB);
     const T u[3] = {bt[0] / nbt, bt[1] / nbt, bt[2] / nbt};
-    const T F[3] = {sgn * u[0], sgn * u[1], sgn * u[2]};
     const T c4 = (T)12.566370614359172 * m * nbt;  // 4 pi |B| |bt|
     const T JB = V[3] * V[0] + V[4] * V[1] + V[5] * V[2];
     const T dtw = JB / c4;
-    T Fb[3], dtwb;
-    bars(F, dtw, Fb, dtwb);
-    // F: d(bt/|bt|) = (I - u u^T)/|bt|
+    T Fb[3] = {kb0, kb1, kb2}, dtwb = twb;
+    if (ax >= 0) {
+        // K = F / F_ax and twK = dtw / F_ax
+        const T F[3] = {sgn * u[0], sgn * u[1], sgn * u[2]};
+        const T fa = F[ax];
+        const T g = (kb0 * F[0] + kb1 * F[1] + kb2 * F[2] + twb * dtw) / (fa * fa);
+        Fb[0] = kb0 / fa;
+        Fb[1] = kb1 / fa;
+        Fb[2] = kb2 / fa;
+        Fb[ax] -= g;
+        dtwb = twb / fa;
+    }
+    // F = sgn bt/|bt|: d(bt/|bt|) = (I - u u^T)/|bt|
     const T uf = u[0] * Fb[0] + u[1] * Fb[1] + u[2] * Fb[2];
     T Vb[6];
 #pragma unroll
@@ -204,6 +246,7 @@ __device__ __forceinline__ void stage_vjp(const FieldView &f, T sgn, T px, T py,
         Vb[a] = btb * rd[a] + dtwb * (V[3 + a] / c4 - dtw * V[a] / BB - dtw * u[a] * rd[a] / nbt);
         Vb[3 + a] = dtwb * V[a] / c4;
     }
+    T pb[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         T s = (T)0;
@@ -212,28 +255,43 @@ __device__ __forceinline__ void stage_vjp(const FieldView &f, T sgn, T px, T py,
         pb[a] = s;
     }
     scatter(f, c, Vb, acc);
+    r.x = pb[0];
+    r.y = pb[1];
+    r.z = pb[2];
+    return r;
 }
+
+template <typename T>
+struct Rhs {
+    T F[3], dl, dtw;
+};
 
 // right-hand side in the tracer's own form (the same function the forward ran)
-__device__ __forceinline__ void rhs_fwd(const FieldView &f, float sgn, float x, float y, float z, float o[5])
+__device__ __forceinline__ Rhs<float> rhs_fwd(const FieldView &f, float sgn, float x, float y, float z)
 {
-    o[0] = o[1] = o[2] = o[3] = o[4] = 0.f;
-    trace::rhs(f, f.rd, sgn, x, y, z, o);
+    float o[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (cell_ok(f, cell_of(f, x, y, z).base)) trace::rhs(f, f.rd, sgn, x, y, z, o);
+    return Rhs<float>{{o[0], o[1], o[2]}, o[3], o[4]};
 }
 
-__device__ __forceinline__ void rhs_fwd(const FieldView &f, double sgn, double x, double y, double z, double o[5])
+__device__ __forceinline__ Rhs<double> rhs_fwd(const FieldView &f, double sgn, double x, double y, double z)
 {
-    o[0] = o[1] = o[2] = o[3] = o[4] = 0.0;
-    trace::rhs(f, f.d, sgn, x, y, z, o);
+    double o[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (cell_ok(f, cell_of(f, x, y, z).base)) trace::rhs(f, f.d, sgn, x, y, z, o);
+    return Rhs<double>{{o[0], o[1], o[2]}, o[3], o[4]};
 }
 
-// one accepted step of the 4th-order solution, as the tracer forms it (stages
-// 0..4: the 4th-order weights of stages 1 and 5 are zero); also the stage
-// derivatives k and the Tw increment
+// One RKF45 step of the 4th-order solution from x, as the tracer forms it
+// (stages 0..4; the 4th-order weights of stages 1 and 5 are zero). ax < 0: an
+// accepted step of size h; ax >= 0: the exit step, whose independent variable
+// is the ax index coordinate (h = target - x_ax, RHS divided by its ax
+// component). Writes the end state and, per stage, the (divided) derivative
+// and Tw integrand k[s] = {F (3), dtw}.
 template <typename T>
-__device__ __forceinline__ void advance(const FieldView &f, T sgn, const T x[3], T h, T x4[3], T k[5][3], T *dtw4)
+__device__ __forceinline__ void advance(const FieldView &f, T sgn, const T x[3], T h, int ax, T x4[3], T k[5][4])
 {
-    T a4[3] = {0, 0, 0}, tw4 = 0;
+    constexpr bool kF64 = sizeof(T) == 8;
+    T a4[3] = {0, 0, 0};
 #pragma unroll
     for (int s = 0; s < 5; s++) {
         T px = 0, py = 0, pz = 0;
@@ -244,36 +302,50 @@ __device__ __forceinline__ void advance(const FieldView &f, T sgn, const T x[3],
             py += c * k[r][1];
             pz += c * k[r][2];
         }
-        T o[5];
-        rhs_fwd(f, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz, o);
-        k[s][0] = o[0];
-        k[s][1] = o[1];
-        k[s][2] = o[2];
+        const Rhs<T> o = rhs_fwd(f, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz);
+        T F[4] = {o.F[0], o.F[1], o.F[2], o.dtw};
+        if (ax >= 0) {
+            const T fa = o.F[ax];
+            if (kF64) {
+#pragma unroll
+                for (int a = 0; a < 4; a++) F[a] = F[a] / fa;
+            } else {
+                const T inv = (T)1 / fa;
+#pragma unroll
+                for (int a = 0; a < 4; a++) F[a] = F[a] * inv;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; a++) k[s][a] = F[a];
         const T b = Fehlberg<T>::b4(s);
-        a4[0] += b * o[0];
-        a4[1] += b * o[1];
-        a4[2] += b * o[2];
-        tw4 += b * o[4];
+        a4[0] += b * F[0];
+        a4[1] += b * F[1];
+        a4[2] += b * F[2];
     }
     x4[0] = x[0] + h * a4[0];
     x4[1] = x[1] + h * a4[1];
     x4[2] = x[2] + h * a4[2];
-    if (dtw4) *dtw4 = h * tw4;
 }
 
-// Reverse of one accepted step of size h from x: on entry xb is the adjoint of
-// the step's end state and wb that of its Tw increment; on exit xb is the
-// adjoint of x.
+// Reverse of that step (its stages are evaluated again here: cheaper than
+// keeping them per step): on entry xb is the adjoint of the end state and wb
+// that of the Tw increment; on exit xb is the adjoint of x through the stages
+// and, for the exit step (ax >= 0), *db the adjoint of its length h.
 template <typename T, typename AccT>
-__device__ __forceinline__ void step_reverse(const FieldView &f, T sgn, const T x[3], T h, T xb[3], T wb, AccT *acc)
+__device__ __forceinline__ void step_reverse(const FieldView &f, T sgn, const T x[3], T h, int ax, T xb[3], T wb,
+                                             T *db, AccT *acc)
 {
-    T k[5][3], x4[3];
-    advance(f, sgn, x, h, x4, k, (T *)nullptr);
+    T k[5][4], x4[3];
+    advance(f, sgn, x, h, ax, x4, k);
     T kb[5][3];
+    T d = 0;
 #pragma unroll
-    for (int s = 0; s < 5; s++)
+    for (int s = 0; s < 5; s++) {
+        const T b = Fehlberg<T>::b4(s);
 #pragma unroll
-        for (int a = 0; a < 3; a++) kb[s][a] = h * Fehlberg<T>::b4(s) * xb[a];
+        for (int a = 0; a < 3; a++) kb[s][a] = h * b * xb[a];
+        d += b * (k[s][0] * xb[0] + k[s][1] * xb[1] + k[s][2] * xb[2] + k[s][3] * wb);
+    }
     T xin[3] = {xb[0], xb[1], xb[2]};
 #pragma unroll
     for (int s = 4; s >= 0; s--) {
@@ -285,239 +357,344 @@ __device__ __forceinline__ void step_reverse(const FieldView &f, T sgn, const T 
             py += c * k[r][1];
             pz += c * k[r][2];
         }
-        const T twb = h * Fehlberg<T>::b4(s) * wb;
-        T pb[3];
-        stage_vjp<T, AccT>(
-            f, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz,
-            [&](const T *, T, T *Fb, T &dtwb) {
-                Fb[0] = kb[s][0];
-                Fb[1] = kb[s][1];
-                Fb[2] = kb[s][2];
-                dtwb = twb;
-            },
-            pb, acc);
-#pragma unroll
-        for (int a = 0; a < 3; a++) xin[a] += pb[a];
+        const V3<T> pb = stage_vjp<T, AccT>(f, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz, ax, kb[s][0],
+                                            kb[s][1], kb[s][2], h * Fehlberg<T>::b4(s) * wb, acc);
+        xin[0] += pb.x;
+        xin[1] += pb.y;
+        xin[2] += pb.z;
+        d += pb.x * px + pb.y * py + pb.z * pz;
 #pragma unroll
         for (int r = 0; r < s; r++) {
             const T c = h * Fehlberg<T>::a(s, r);
-#pragma unroll
-            for (int a = 0; a < 3; a++) kb[r][a] += c * pb[a];
+            kb[r][0] += c * pb.x;
+            kb[r][1] += c * pb.y;
+            kb[r][2] += c * pb.z;
         }
     }
 #pragma unroll
     for (int a = 0; a < 3; a++) xb[a] = xin[a];
+    if (db) *db = d;
 }
 
-// Reverse of the exit step from x onto face `face` (the face-normal index
-// coordinate is the independent variable, Sec. 2.1): the end point is
-// x + delta sum b4 K_s, K = F/F_ax, delta = target - x_ax, with its ax
-// coordinate set to the face and (clamped) the others clamped into the box.
-template <typename T, typename AccT>
-__device__ __forceinline__ void exit_reverse(const FieldView &f, T sgn, const T x[3], int face, bool clamped, T xb[3],
-                                             T wb, AccT *acc)
+// ---------------------------------------------------------------------------
+// The reverse sweep, parallel in time. The adjoint of one accepted step is
+// linear in the adjoints of its end state and of the Tw sum:
+//   xbar_i = J_i^T xbar_{i+1} + g_i wbar,
+// J_i = d x_{i+1} / d x_i, g_i = d (Tw increment) / d x_i. So, rather than one
+// thread walking a whole direction backwards (a chain of ~15 dependent field
+// gathers per step), three passes:
+//   A (per tape chunk)  recompute the chunk's states from its checkpoint and
+//                       each step's J_i, g_i by forward-mode tangents;
+//   B (per half-line)   the exit step's VJP (with its scatter), then the
+//                       recurrence above over the stored J_i, g_i (no gathers),
+//                       storing each step's xbar_{i+1};
+//   C (per tape chunk)  each step's stage VJPs and scatters given xbar_{i+1}.
+// A and C run one thread per chunk of at most k steps, so the longest chain of
+// dependent gathers is k steps instead of a whole line.
+// ---------------------------------------------------------------------------
+
+// V, dV/dxi at p and, from them, F, dtw and their position Jacobians:
+// Jm[i][j] = dF_i/dp_j, g[j] = d dtw/dp_j. Returns false (values zero) when the
+// cell check fails.
+template <typename T>
+__device__ __forceinline__ bool stage_jac(const FieldView &f, T sgn, T px, T py, T pz, T F[3], T &dtw, T Jm[3][3],
+                                          T g[3])
 {
-    constexpr bool kF64 = sizeof(T) == 8;
-    const int ax = face >> 1;
-    const int nax = ax == 0 ? f.nx : (ax == 1 ? f.ny : f.nz);
-    const T target = (face & 1) ? (T)(nax - 1) : (T)0;
-    const T delta = target - x[ax];
-    T K[5][3], twK[5];
-    T a4[3] = {0, 0, 0};
+    const Cell<T> c = cell_of(f, px, py, pz);
+    if (!cell_ok(f, c.base)) {
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            F[i] = g[i] = (T)0;
+            Jm[i][0] = Jm[i][1] = Jm[i][2] = (T)0;
+        }
+        dtw = (T)0;
+        return false;
+    }
+    T V[6], dV[3][6];
+    interp_d(f, c, V, dV);
+    const T rd[3] = {inv_spacing<T>(f, 0), inv_spacing<T>(f, 1), inv_spacing<T>(f, 2)};
+    const T bt[3] = {V[0] * rd[0], V[1] * rd[1], V[2] * rd[2]};
+    const T bb = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
+    const T BB = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+    const T nbt = sqrt(bb), m = sqrt(BB);
+    const T u[3] = {bt[0] / nbt, bt[1] / nbt, bt[2] / nbt};
+    const T c4 = (T)12.566370614359172 * m * nbt;  // 4 pi |B| |bt|
+    const T JB = V[3] * V[0] + V[4] * V[1] + V[5] * V[2];
+    dtw = JB / c4;
+    // d dtw / dB and d dtw / dJ
+    T dB[3], dJ[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        F[a] = sgn * u[a];
+        dB[a] = V[3 + a] / c4 - dtw * V[a] / BB - dtw * u[a] * rd[a] / nbt;
+        dJ[a] = V[a] / c4;
+    }
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        // F = sgn u(bt), u = bt/|bt|: dF_i/dp_j = sgn (rd_i dB_i/dp_j - u_i q_j)/|bt|
+        const T q = u[0] * rd[0] * dV[j][0] + u[1] * rd[1] * dV[j][1] + u[2] * rd[2] * dV[j][2];
+#pragma unroll
+        for (int i = 0; i < 3; i++) Jm[i][j] = sgn * (rd[i] * dV[j][i] - u[i] * q) / nbt;
+        g[j] = dB[0] * dV[j][0] + dB[1] * dV[j][1] + dB[2] * dV[j][2] + dJ[0] * dV[j][3] + dJ[1] * dV[j][4] +
+               dJ[2] * dV[j][5];
+    }
+    return true;
+}
+
+// One accepted step (as advance with ax < 0) with its tangent map: the end
+// state x4, Jt[a][b] = d x4_b / d x_a (J^T) and gw[a] = d (Tw increment)/d x_a.
+template <typename T>
+__device__ __forceinline__ void step_jac(const FieldView &f, T sgn, const T x[3], T h, T x4[3], T Jt[3][3], T gw[3])
+{
+    T k[5][3], D[5][3][3];  // stage derivatives and their tangents D_s = d k_s / d x
+    T a4[3] = {0, 0, 0}, Ds[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gs[3] = {0, 0, 0};
 #pragma unroll
     for (int s = 0; s < 5; s++) {
         T px = 0, py = 0, pz = 0;
+        T P[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};  // d p_s / d x
 #pragma unroll
         for (int r = 0; r < s; r++) {
             const T c = Fehlberg<T>::a(s, r);
-            px += c * K[r][0];
-            py += c * K[r][1];
-            pz += c * K[r][2];
-        }
-        T o[5];
-        rhs_fwd(f, sgn, x[0] + delta * px, x[1] + delta * py, x[2] + delta * pz, o);
-        const T fa = trace::sel3<T>(ax, o[0], o[1], o[2]);
-        if (kF64) {
+            px += c * k[r][0];
+            py += c * k[r][1];
+            pz += c * k[r][2];
 #pragma unroll
-            for (int a = 0; a < 3; a++) K[s][a] = o[a] / fa;
-            twK[s] = o[4] / fa;
-        } else {
-            const T inv = (T)1 / fa;
+            for (int i = 0; i < 3; i++)
 #pragma unroll
-            for (int a = 0; a < 3; a++) K[s][a] = o[a] * inv;
-            twK[s] = o[4] * inv;
+                for (int j = 0; j < 3; j++) P[i][j] += h * c * D[r][i][j];
         }
+        T F[3], dtw, Jm[3][3], g[3];
+        stage_jac(f, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz, F, dtw, Jm, g);
         const T b = Fehlberg<T>::b4(s);
-        a4[0] += b * K[s][0];
-        a4[1] += b * K[s][1];
-        a4[2] += b * K[s][2];
-    }
-    T eb[3] = {xb[0], xb[1], xb[2]};
-    eb[ax] = (T)0;
-    if (clamped) {
-        const int nn[3] = {f.nx, f.ny, f.nz};
 #pragma unroll
-        for (int b = 0; b < 3; b++) {
-            const T e = x[b] + delta * a4[b];
-            if (b != ax && (e < (T)0 || e > (T)(nn[b] - 1))) eb[b] = (T)0;
+        for (int i = 0; i < 3; i++) {
+            k[s][i] = F[i];
+            a4[i] += b * F[i];
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                D[s][i][j] = Jm[i][0] * P[0][j] + Jm[i][1] * P[1][j] + Jm[i][2] * P[2][j];
+                Ds[i][j] += b * D[s][i][j];
+            }
         }
+#pragma unroll
+        for (int j = 0; j < 3; j++) gs[j] += b * (g[0] * P[0][j] + g[1] * P[1][j] + g[2] * P[2][j]);
     }
-    T db = 0;
-    T Kb[5][3], twKb[5];
 #pragma unroll
-    for (int s = 0; s < 5; s++) {
-        const T b = Fehlberg<T>::b4(s);
-        db += b * (K[s][0] * eb[0] + K[s][1] * eb[1] + K[s][2] * eb[2] + twK[s] * wb);
+    for (int i = 0; i < 3; i++) {
+        x4[i] = x[i] + h * a4[i];
+        gw[i] = h * gs[i];
 #pragma unroll
-        for (int a = 0; a < 3; a++) Kb[s][a] = delta * b * eb[a];
-        twKb[s] = delta * b * wb;
+        for (int j = 0; j < 3; j++) Jt[j][i] = (i == j ? (T)1 : (T)0) + h * Ds[i][j];
     }
-    T xin[3] = {eb[0], eb[1], eb[2]};
-#pragma unroll
-    for (int s = 4; s >= 0; s--) {
-        T px = 0, py = 0, pz = 0;
-#pragma unroll
-        for (int r = 0; r < s; r++) {
-            const T c = Fehlberg<T>::a(s, r);
-            px += c * K[r][0];
-            py += c * K[r][1];
-            pz += c * K[r][2];
-        }
-        T pb[3];
-        stage_vjp<T, AccT>(
-            f, sgn, x[0] + delta * px, x[1] + delta * py, x[2] + delta * pz,
-            [&](const T *F, T dtw, T *Fb, T &dtwb) {
-                // K = F / F_ax and twK = dtw / F_ax
-                const T fa = F[ax];
-                const T g = (Kb[s][0] * F[0] + Kb[s][1] * F[1] + Kb[s][2] * F[2] + twKb[s] * dtw) / (fa * fa);
-                Fb[0] = Kb[s][0] / fa;
-                Fb[1] = Kb[s][1] / fa;
-                Fb[2] = Kb[s][2] / fa;
-                Fb[ax] -= g;
-                dtwb = twKb[s] / fa;
-            },
-            pb, acc);
-#pragma unroll
-        for (int a = 0; a < 3; a++) xin[a] += pb[a];
-        db += pb[0] * px + pb[1] * py + pb[2] * pz;
-#pragma unroll
-        for (int r = 0; r < s; r++) {
-            const T c = delta * Fehlberg<T>::a(s, r);
-#pragma unroll
-            for (int a = 0; a < 3; a++) Kb[r][a] += c * pb[a];
-        }
-    }
-    xin[ax] -= db;
-#pragma unroll
-    for (int a = 0; a < 3; a++) xb[a] = xin[a];
 }
 
-// Reverse of the chord end: after an exiting step of size h from x to x4, the
-// end is x + t0 (x4 - x) with t0 = (target - x_ax)/(x4_ax - x_ax), its ax
-// coordinate set to the face; Tw gains t0 times the step's increment.
-template <typename T, typename AccT>
-__device__ __forceinline__ void chord_reverse(const FieldView &f, T sgn, const T x[3], int face, T h, T xb[3], T wb,
-                                              AccT *acc)
+constexpr int kMaxChunk = 32;  // largest steps per tape chunk
+
+// Does half-line hl carry a nonzero adjoint (footpoint or Tw weight)?
+__device__ __forceinline__ bool half_live(const AdjArgs &A, long long hl, double &w)
 {
-    const int ax = face >> 1;
-    const int nax = ax == 0 ? f.nx : (ax == 1 ? f.ny : f.nz);
-    const T target = (face & 1) ? (T)(nax - 1) : (T)0;
-    T k[5][3], x4[3], dtw;
-    advance(f, sgn, x, h, x4, k, &dtw);
-    const T den = x4[ax] - x[ax];
-    const T t0 = (target - x[ax]) / den;
-    T cb[3] = {xb[0], xb[1], xb[2]};
-    cb[ax] = (T)0;
-    const T t0b = cb[0] * (x4[0] - x[0]) + cb[1] * (x4[1] - x[1]) + cb[2] * (x4[2] - x[2]) + wb * dtw;
-    T x4b[3] = {t0 * cb[0], t0 * cb[1], t0 * cb[2]};
-    x4b[ax] -= t0b * t0 / den;
-    T xin[3] = {((T)1 - t0) * cb[0], ((T)1 - t0) * cb[1], ((T)1 - t0) * cb[2]};
-    xin[ax] += t0b * (t0 - (T)1) / den;
-    step_reverse<T, AccT>(f, sgn, x, h, x4b, t0 * wb, acc);
-#pragma unroll
-    for (int a = 0; a < 3; a++) xb[a] = xin[a] + x4b[a];
+    w = A.dTw ? A.dTw[hl >> 1] : 0.0;
+    if (!(w == w) || fabs(w) == INFINITY) w = 0.0;
+    const double *xb = A.xbar + 3 * hl;
+    return w != 0.0 || xb[0] != 0.0 || xb[1] != 0.0 || xb[2] != 0.0;
 }
 
-constexpr int kMaxChunk = 64;  // largest steps per tape chunk
-
-// Reverse sweep of half-line hl = 2 line + e (TT: the tape's scalar type).
-template <typename T, typename AccT, typename TT>
-__device__ __forceinline__ void reverse_half_line(const AdjArgs &A, long long line, int e, T (*xs)[3])
+// The chunk's half-line, orientation and step count; false if nothing to do.
+__device__ __forceinline__ bool chunk_of(const AdjArgs &A, long long c, long long &hl, int &n, int &sgn, double &w)
 {
     const Tape &tp = A.tape;
-    const long long hl = 2 * line + e;
+    hl = tp.owner[c];
+    if (hl < 0 || hl >= 2 * A.n) {
+        record_fail(A.f.err, 1, c);
+        return false;
+    }
+    if (A.rec.st[hl >> 1] & kBad) return false;
+    if (!half_live(A, hl, w)) return false;
     const int4 hd = tp.head[hl];
-    if (hd.x < 0 || hd.z < 0) return;
-    T xb[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) xb[a] = (T)A.xbar[3 * hl + a];
-    double w = A.dTw ? A.dTw[line] : 0.0;
-    if (!(w == w) || fabs(w) == INFINITY) w = 0.0;
-    const T wb = (T)w;
-    if (xb[0] == (T)0 && xb[1] == (T)0 && xb[2] == (T)0 && wb == (T)0) return;
-    AccT *acc = (AccT *)A.acc;
-    const FieldView &f = A.f;
-    const T sgn = (T)hd.w;
-    const TT *H = (const TT *)tp.h;
+    if (hd.x < 0 || hd.z < 0) return false;
+    n = hd.x == (int)c ? hd.y : tp.k;
+    if (n < 0 || n > tp.k || n > kMaxChunk) {
+        record_fail(A.f.err, 2, n);
+        return false;
+    }
+    sgn = hd.w;
+    return true;
+}
+
+// pass A: states and step Jacobians of every chunk
+template <typename T, typename TT>
+__global__ void __launch_bounds__(128) k_adj_fwd(const AdjArgs A)
+{
+    const Tape &tp = A.tape;
+    const int K = tp.k;
+    T *WX = (T *)A.wx;
+    T *WJ = (T *)A.wj;
     const TT *X = (const TT *)tp.xi;
-    // last chunk: its states up to the exit step
-    int c = hd.x;
-    int n = hd.y;
-    xs[0][0] = (T)X[4 * (long long)c];
-    xs[0][1] = (T)X[4 * (long long)c + 1];
-    xs[0][2] = (T)X[4 * (long long)c + 2];
-    for (int i = 0; i < n; i++) {
-        T k[5][3];
-        advance(f, sgn, xs[i], (T)H[(long long)c * tp.k + i], xs[i + 1], k, (T *)nullptr);
-    }
-    const int code = hd.z;
-    if (code >= kTapeChord) {
-        const T hx = (T)((const TT *)tp.xe)[4 * hl + 3];
-        chord_reverse<T, AccT>(f, sgn, xs[n], code - kTapeChord, hx, xb, wb, acc);
-    } else if (code >= kTapeExitClamped) {
-        exit_reverse<T, AccT>(f, sgn, xs[n], code - kTapeExitClamped, true, xb, wb, acc);
-    } else {
-        exit_reverse<T, AccT>(f, sgn, xs[n], code - kTapeExit, false, xb, wb, acc);
-    }
-    for (;;) {
-        for (int i = n - 1; i >= 0; i--)
-            step_reverse<T, AccT>(f, sgn, xs[i], (T)H[(long long)c * tp.k + i], xb, wb, acc);
-        const int pc = tp.prev[c];
-        if (pc < 0 || pc >= c) break;  // chunks of a half-line are taken in increasing order
-        c = pc;
-        n = tp.k;
-        xs[0][0] = (T)X[4 * (long long)c];
-        xs[0][1] = (T)X[4 * (long long)c + 1];
-        xs[0][2] = (T)X[4 * (long long)c + 2];
-        for (int i = 0; i + 1 < n; i++) {
-            T k[5][3];
-            advance(f, sgn, xs[i], (T)H[(long long)c * tp.k + i], xs[i + 1], k, (T *)nullptr);
+    const TT *H = (const TT *)tp.h;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < A.chunks;
+         c += (long long)gridDim.x * blockDim.x) {
+        long long hl;
+        int n, sg;
+        double w;
+        if (!chunk_of(A, c, hl, n, sg, w)) continue;
+        T x[3] = {(T)X[4 * c], (T)X[4 * c + 1], (T)X[4 * c + 2]};
+        T *wx = WX + c * (K + 1) * 3;
+        T *wj = WJ + c * K * 12;
+        wx[0] = x[0];
+        wx[1] = x[1];
+        wx[2] = x[2];
+        for (int i = 0; i < n; i++) {
+            T x4[3], Jt[3][3], gw[3];
+            step_jac(A.f, (T)sg, x, (T)H[c * K + i], x4, Jt, gw);
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                wj[12 * i + 3 * a + 0] = Jt[a][0];
+                wj[12 * i + 3 * a + 1] = Jt[a][1];
+                wj[12 * i + 3 * a + 2] = Jt[a][2];
+                wj[12 * i + 9 + a] = gw[a];
+                x[a] = x4[a];
+                wx[3 * (i + 1) + a] = x4[a];
+            }
         }
     }
 }
 
+// pass B: per half-line, the exit step's VJP and the recurrence over its steps
 template <typename T, typename AccT, typename TT>
-__global__ void __launch_bounds__(128) k_reverse(const AdjArgs A)
+__global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
 {
-    constexpr unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const Lattice &G = A.lat;
-    const long long units = G.tiles_u * G.tiles_v * 2;  // (tile, end) pairs
-    T xs[kMaxChunk + 1][3];
-    for (;;) {
-        unsigned long long u = 0;
-        if (lane == 0) u = atomicAdd(A.head, 1ull);
-        u = __shfl_sync(FULL, u, 0);
-        if ((long long)u >= units) break;
-        const long long t = (long long)(u >> 1);
-        const int e = (int)(u & 1);
-        const long long i = (t % G.tiles_u) * kTileU + (lane % kTileU);
-        const long long j = (t / G.tiles_u) * kTileV + (lane / kTileU);
-        if (i < G.n1 && j < G.n2) {
-            const long long line = i + G.n1 * j;
-            if (!(A.rec.st[line] & kBad)) reverse_half_line<T, AccT, TT>(A, line, e, xs);
+    const Tape &tp = A.tape;
+    const FieldView &f = A.f;
+    const int K = tp.k;
+    const T *WX = (const T *)A.wx;
+    const T *WJ = (const T *)A.wj;
+    T *WB = (T *)A.wb;
+    AccT *acc = (AccT *)A.acc;
+    for (long long hl = blockIdx.x * (long long)blockDim.x + threadIdx.x; hl < 2 * A.n;
+         hl += (long long)gridDim.x * blockDim.x) {
+        if (A.rec.st[hl >> 1] & kBad) continue;
+        double w;
+        if (!half_live(A, hl, w)) continue;
+        const int4 hd = tp.head[hl];
+        if (hd.x < 0 || hd.z < 0) continue;
+        if (hd.x >= A.chunks) {
+            record_fail(f.err, 1, hd.x);
+            continue;
         }
-        __syncwarp();
+        const int code = hd.z;
+        const bool chord = code >= kTapeChord && code < kTapeChord + 6;
+        const bool clamped = code >= kTapeExitClamped && code < kTapeExitClamped + 6;
+        if (!(chord || clamped || (code >= kTapeExit && code < kTapeExit + 6))) {
+            record_fail(f.err, 3, code);
+            continue;
+        }
+        if (hd.y < 0 || hd.y > K) {
+            record_fail(f.err, 2, hd.y);
+            continue;
+        }
+        const T wb = (T)w;
+        const T sgn = (T)hd.w;
+        const int face = code - (chord ? kTapeChord : (clamped ? kTapeExitClamped : kTapeExit));
+        const int fax = face >> 1;
+        const T target = (face & 1) ? (T)((fax == 0 ? f.nx : (fax == 1 ? f.ny : f.nz)) - 1) : (T)0;
+        T xb[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) xb[a] = (T)A.xbar[3 * hl + a];
+        // the exiting step from the state after the last accepted step
+        const T *xn = WX + ((long long)hd.x * (K + 1) + hd.y) * 3;
+        const T x[3] = {xn[0], xn[1], xn[2]};
+        T h, d = 0, ws = wb;
+        int ax = -1;
+        T yb[3] = {xb[0], xb[1], xb[2]}, keep[3] = {0, 0, 0};
+        T x4[3], kt[5][4];
+        if (chord) {
+            // end = x + t0 (x4 - x), t0 = (target - x_ax)/(x4_ax - x_ax); Tw gains t0 of the step's increment
+            h = (T)((const TT *)tp.xe)[4 * hl + 3];
+            advance(f, sgn, x, h, -1, x4, kt);
+            T dtw = 0;
+#pragma unroll
+            for (int s = 0; s < 5; s++) dtw += Fehlberg<T>::b4(s) * kt[s][3];
+            dtw *= h;
+            const T den = x4[fax] - x[fax];
+            const T t0 = (target - x[fax]) / den;
+            T cb[3] = {xb[0], xb[1], xb[2]};
+            cb[fax] = (T)0;
+            const T t0b = cb[0] * (x4[0] - x[0]) + cb[1] * (x4[1] - x[1]) + cb[2] * (x4[2] - x[2]) + wb * dtw;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                yb[a] = t0 * cb[a];
+                keep[a] = ((T)1 - t0) * cb[a];
+            }
+            yb[fax] -= t0b * t0 / den;
+            keep[fax] += t0b * (t0 - (T)1) / den;
+            ws = t0 * wb;
+        } else {
+            // exit step onto the face: its ax coordinate is the face, the
+            // others are clamped into the box when the code says so
+            ax = fax;
+            h = target - x[fax];
+            yb[fax] = (T)0;
+            if (clamped) {
+                advance(f, sgn, x, h, ax, x4, kt);
+                const int nn[3] = {f.nx, f.ny, f.nz};
+#pragma unroll
+                for (int b = 0; b < 3; b++)
+                    if (b != fax && (x4[b] < (T)0 || x4[b] > (T)(nn[b] - 1))) yb[b] = (T)0;
+            }
+        }
+        step_reverse<T, AccT>(f, sgn, x, h, ax, yb, ws, ax >= 0 ? &d : (T *)nullptr, acc);
+        T y[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) y[a] = yb[a] + keep[a];
+        if (ax >= 0) y[fax] -= d;  // h = target - x_ax
+        // the accepted steps, last first: store each step's end-state adjoint,
+        // then xbar_i = J_i^T xbar_{i+1} + g_i wbar
+        int c = hd.x, n = hd.y;
+        for (;;) {
+            const T *wj = WJ + (long long)c * K * 12;
+            T *wbp = WB + (long long)c * K * 3;
+            for (int i = n - 1; i >= 0; i--) {
+                wbp[3 * i + 0] = y[0];
+                wbp[3 * i + 1] = y[1];
+                wbp[3 * i + 2] = y[2];
+                const T *J = wj + 12 * i;
+                const T z0 = J[0] * y[0] + J[1] * y[1] + J[2] * y[2] + J[9] * wb;
+                const T z1 = J[3] * y[0] + J[4] * y[1] + J[5] * y[2] + J[10] * wb;
+                const T z2 = J[6] * y[0] + J[7] * y[1] + J[8] * y[2] + J[11] * wb;
+                y[0] = z0;
+                y[1] = z1;
+                y[2] = z2;
+            }
+            const int pc = tp.prev[c];
+            if (pc < 0 || pc >= c) break;  // chunks of a half-line are taken in increasing order
+            c = pc;
+            n = K;
+        }
+    }
+}
+
+// pass C: the stage VJPs of every step, given its end-state adjoint
+template <typename T, typename AccT, typename TT>
+__global__ void __launch_bounds__(128) k_adj_rev(const AdjArgs A)
+{
+    const Tape &tp = A.tape;
+    const int K = tp.k;
+    const T *WX = (const T *)A.wx;
+    const T *WB = (const T *)A.wb;
+    const TT *H = (const TT *)tp.h;
+    AccT *acc = (AccT *)A.acc;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < A.chunks;
+         c += (long long)gridDim.x * blockDim.x) {
+        long long hl;
+        int n, sg;
+        double w;
+        if (!chunk_of(A, c, hl, n, sg, w)) continue;
+        const T *wx = WX + c * (K + 1) * 3;
+        const T *wbp = WB + c * K * 3;
+        for (int i = 0; i < n; i++) {
+            T yb[3] = {wbp[3 * i], wbp[3 * i + 1], wbp[3 * i + 2]};
+            step_reverse<T, AccT>(A.f, (T)sg, wx + 3 * i, (T)H[c * K + i], -1, yb, (T)w, (T *)nullptr, acc);
+        }
     }
 }
 
@@ -537,6 +714,8 @@ template <typename T, typename AccT>
 __device__ __forceinline__ double bn_vjp(const FieldView &f, const T p[3], int ax, double bnb, double g[3], AccT *acc)
 {
     const Cell<T> c = cell_of(f, p[0], p[1], p[2]);
+    g[0] = g[1] = g[2] = 0.0;
+    if (!cell_ok(f, c.base)) return 0.0;
     T V[6], dV[3][6];
     interp_d(f, c, V, dV);
     g[0] = (double)dV[0][ax];
@@ -684,7 +863,7 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
         }
         const Cell<T> c0 = cell_of(f, p0[0], p0[1], p0[2]);
         const T Vb[6] = {(T)(bn0b * G.n0[0]), (T)(bn0b * G.n0[1]), (T)(bn0b * G.n0[2]), 0, 0, 0};
-        scatter(f, c0, Vb, acc);
+        if (cell_ok(f, c0.base)) scatter(f, c0, Vb, acc);
     }
 }
 
@@ -801,8 +980,8 @@ __global__ void __launch_bounds__(256) k_loss_grad(long long n, const double *Q,
     }
 }
 
-// The step sequence of every half-line, in order: ns[hl] steps (-1: more
-// than cap; 0 with code -1: line not traced), h[hl * cap + i], end code and the
+// The step sequence of every half-line, in order: ns[hl] steps (0 with code
+// -1: line not traced), h[hl * cap + i] when ns[hl] <= cap, end code and the
 // chord's exiting step.
 template <typename T>
 __global__ void __launch_bounds__(256) k_tape_export(const Tape tp, const uint8_t *__restrict__ st, long long halves,
@@ -826,11 +1005,8 @@ __global__ void __launch_bounds__(256) k_tape_export(const Tape tp, const uint8_
         }
         code[hl] = hd.z;
         hx[hl] = (double)((const T *)tp.xe)[4 * hl + 3];
-        if (total > cap) {
-            ns[hl] = -1;
-            continue;
-        }
         ns[hl] = (int32_t)total;
+        if (total > cap) continue;
         long long pos = total;
         int c = hd.x, m = hd.y;
         for (;;) {
@@ -872,22 +1048,22 @@ void q_vjp_mode(const AdjArgs &a, int mode, unsigned g, cudaStream_t s)
     else adj::k_q_vjp<double, double, TT><<<g, 128, 0, s>>>(a);
 }
 
-template <typename TT>
-void reverse_mode(const AdjArgs &a, int mode, int grid, cudaStream_t s)
+template <typename T, typename AccT, typename TT>
+void reverse_passes(const AdjArgs &a, cudaStream_t s)
 {
-    if (mode == 0) adj::k_reverse<float, float, TT><<<grid, 128, 0, s>>>(a);
-    else if (mode == 1) adj::k_reverse<float, double, TT><<<grid, 128, 0, s>>>(a);
-    else adj::k_reverse<double, double, TT><<<grid, 128, 0, s>>>(a);
+    const unsigned gc = adj::grid_for(a.chunks, 128, 16);
+    const unsigned gl = adj::grid_for(2 * a.n, 128, 16);
+    adj::k_adj_fwd<T, TT><<<gc, 128, 0, s>>>(a);
+    adj::k_adj_lines<T, AccT, TT><<<gl, 128, 0, s>>>(a);
+    adj::k_adj_rev<T, AccT, TT><<<gc, 128, 0, s>>>(a);
 }
 
 template <typename TT>
-int reverse_blocks(int mode)
+void reverse_mode(const AdjArgs &a, int mode, cudaStream_t s)
 {
-    int b = 0;
-    if (mode == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adj::k_reverse<float, float, TT>, 128, 0);
-    else if (mode == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adj::k_reverse<float, double, TT>, 128, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adj::k_reverse<double, double, TT>, 128, 0);
-    return b > 0 ? b : 1;
+    if (mode == 0) reverse_passes<float, float, TT>(a, s);
+    else if (mode == 1) reverse_passes<float, double, TT>(a, s);
+    else reverse_passes<double, double, TT>(a, s);
 }
 }  // namespace
 
@@ -899,15 +1075,12 @@ cudaError_t launch_q_vjp(const AdjArgs &a, int mode, bool tape_f64, cudaStream_t
     return cudaGetLastError();
 }
 
-int reverse_blocks_per_sm(int mode, bool tape_f64)
+cudaError_t launch_reverse(const AdjArgs &a, int mode, bool tape_f64, cudaStream_t s)
 {
-    return tape_f64 ? reverse_blocks<double>(mode) : reverse_blocks<float>(mode);
-}
-
-cudaError_t launch_reverse(const AdjArgs &a, int mode, bool tape_f64, int grid, cudaStream_t s)
-{
-    if (tape_f64) reverse_mode<double>(a, mode, grid, s);
-    else reverse_mode<float>(a, mode, grid, s);
+    if (a.chunks > 0) {
+        if (tape_f64) reverse_mode<double>(a, mode, s);
+        else reverse_mode<float>(a, mode, s);
+    }
     return cudaGetLastError();
 }
 

@@ -67,7 +67,6 @@ struct fqsl_field_s {
     int blocks_cache[3][3] = {};  // [precision][source] resident blocks per SM
     int blocks_cache_m2[2][2] = {};  // Method II: [fp64][way - 1]
     int blocks_cache_tape[3] = {};   // taped lattice tracer: [precision]
-    int blocks_cache_rev[3][2] = {};  // adjoint reverse sweep: [mode][tape is FP64]
     bool timing = false, timed = false, extra_timed = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // the last plane map traced with params->tape = 1 (for fqsl_backward): its
@@ -80,6 +79,8 @@ struct fqsl_field_s {
         long long pool = 0;  // tape chunks of the next taped call
         void *buf = nullptr;
         size_t cap = 0;
+        void *work = nullptr;  // per-step arrays of the reverse sweep
+        size_t work_cap = 0;
     } tp;
     std::mutex mu;
 };
@@ -161,6 +162,8 @@ fqsl_status fqsl_field_create(const void *B_dev, fqsl_dtype b_dtype, long long n
     f->g.cmax[2] = (float)(nz - 2);
     f->g.sy32 = (unsigned)(nx * 32);
     f->g.sz32 = (unsigned)(nx * ny * 32 <= 0xffffffffLL ? nx * ny * 32 : 0);
+    f->g.nodes = nx * ny * nz;
+    f->g.err = nullptr;
     const size_t nodes = (size_t)nx * ny * nz;
     if (flags & FQSL_PACK_F32) {
         e = cudaMalloc(&f->rec32, nodes * 32);
@@ -273,17 +276,9 @@ fqsl_status fqsl_field_destroy(fqsl_field f)
     cudaFree(f->grad64);
     cudaFree(f->scratch);
     cudaFree(f->tp.buf);
+    cudaFree(f->tp.work);
     cudaFree(f->counters);
     delete f;
-    return FQSL_OK;
-}
-
-fqsl_status fqsl_field_check(fqsl_field f, void *cuda_stream)
-{
-    g_err.clear();
-    if (!f) return fail(FQSL_ERR_ARG, "fqsl_field_check: NULL handle");
-    cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
-    if (e != cudaSuccess) return cuda_fail(e, "fqsl_field_check");
     return FQSL_OK;
 }
 
@@ -314,7 +309,7 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
     if (p->chunk_tiles < 0 || p->chunk_tiles > 64) return fail(FQSL_ERR_ARG, "%s: chunk_tiles in [0, 64]", who);
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 64) return fail(FQSL_ERR_ARG, "%s: blocks_per_sm in [0, 64]", who);
     if (p->tape != 0 && p->tape != 1) return fail(FQSL_ERR_ARG, "%s: tape must be 0 or 1", who);
-    if (p->tape_chunk < 0 || p->tape_chunk > 64) return fail(FQSL_ERR_ARG, "%s: tape_chunk in [0, 64]", who);
+    if (p->tape_chunk < 0 || p->tape_chunk > 32) return fail(FQSL_ERR_ARG, "%s: tape_chunk in [0, 32]", who);
     if (p->reverse_precision < -1 || p->reverse_precision > FQSL_F32_ACC64)
         return fail(FQSL_ERR_ARG, "%s: reverse_precision must be -1, FQSL_F32, FQSL_F64 or FQSL_F32_ACC64", who);
     if (p->tape) {
@@ -500,7 +495,8 @@ void index_lattice(const fqsl_field f, Lattice &lat)
 // footpoint adjoints, the loss sums and the adjoint node grid.
 struct TapeLayout {
     Scratch s;
-    unsigned long long *ctr;  // [0] tape chunks handed out, [1] reverse-sweep work counter
+    unsigned long long *ctr;  // [0] tape chunks handed out, [1] reverse-sweep work counter,
+                              // [2], [3] failed index checks of the adjoint kernels
     Tape tape;
     double *xbar, *sums;
     void *acc;
@@ -525,6 +521,7 @@ TapeLayout tape_layout(char *base, long long n, bool rot, bool f32, long long po
     t.tape.h = c.take<char>((size_t)pool * k * ts);
     t.tape.head = c.take<int4>((size_t)(2 * n));
     t.tape.xe = c.take<char>((size_t)(2 * n) * 4 * ts);
+    t.tape.owner = c.take<int32_t>((size_t)pool);
     t.xbar = c.take<double>((size_t)(6 * n));
     t.sums = c.take<double>(2);
     t.acc = c.take<char>(nodes * 8 * (acc64 ? 8 : 4));
@@ -1254,9 +1251,9 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
     const fqsl_params p = f->tp.p;
     // the pool of the taped call must have held every chunk; if not, trace the
     // same map again with a larger pool (the map is deterministic)
+    unsigned long long used = 0;
     for (int attempt = 0;; attempt++) {
         TapeLayout tl = field_tape_layout(f, (char *)f->tp.buf, f->tp.pool);
-        unsigned long long used = 0;
         cudaError_t e = cudaMemcpyAsync(&used, tl.ctr, sizeof used, cudaMemcpyDeviceToHost, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) return cuda_fail(e, who);
@@ -1276,14 +1273,34 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
     const bool acc64 = acc64_of(p);
     const int mode = rp == FQSL_F64 ? 2 : (acc64 ? 1 : 0);
     const bool tape_f64 = p.precision == FQSL_F64;
+    // per-step work arrays of the reverse sweep for the chunks in use
+    const int K = tl.tape.k;
+    const size_t rs = rp == FQSL_F64 ? 8 : 4;
+    const size_t bx = align_up((size_t)used * (K + 1) * 3 * rs), bj = align_up((size_t)used * K * 12 * rs),
+                 bb = align_up((size_t)used * K * 3 * rs);
+    if (bx + bj + bb > f->tp.work_cap) {
+        cudaError_t e0 = cudaDeviceSynchronize();
+        if (e0 == cudaSuccess) {
+            cudaFree(f->tp.work);
+            f->tp.work = nullptr;
+            f->tp.work_cap = 0;
+            e0 = cudaMalloc(&f->tp.work, bx + bj + bb);
+        }
+        if (e0 != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_fail(e0, "fqsl_backward: work arrays");
+        }
+        f->tp.work_cap = bx + bj + bb;
+    }
     cudaError_t e = cudaMemsetAsync(tl.xbar, 0, (size_t)(6 * n) * sizeof(double), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(tl.acc, 0, nodes * 8 * (acc64 ? 8 : 4), stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tl.ctr + 1, 0, sizeof(unsigned long long), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tl.ctr + 1, 0, 3 * sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     AdjArgs a{};
     a.f = f->g;
     a.f.rec = rp == FQSL_F64 ? f->rec64 : f->rec32;
     a.f.grad = nullptr;
+    a.f.err = tl.ctr + 2;
     a.p = dev_params(&p);
     a.lat = lat;
     a.rec = tl.s.rec;
@@ -1295,17 +1312,14 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
     a.acc = tl.acc;
     a.head = tl.ctr + 1;
     a.n = n;
+    a.chunks = (long long)used;
+    a.wx = f->tp.work;
+    a.wj = (char *)f->tp.work + bx;
+    a.wb = (char *)f->tp.work + bx + bj;
     e = launch_q_vjp(a, mode, tape_f64, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     mark(f, 0, stream);
-    int &bps = f->blocks_cache_rev[mode][tape_f64 ? 1 : 0];
-    if (!bps) bps = reverse_blocks_per_sm(mode, tape_f64);
-    long long grid = (long long)f->sms * bps;
-    const long long units = lat.tiles_u * lat.tiles_v * 2;
-    const long long need = (units * 32 + 127) / 128;
-    if (need < grid) grid = need;
-    if (grid < 1) grid = 1;
-    e = launch_reverse(a, mode, tape_f64, (int)grid, stream);
+    e = launch_reverse(a, mode, tape_f64, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     mark(f, 1, stream);
     mark(f, 2, stream);
@@ -1352,3 +1366,26 @@ extern "C" fqsl_status fqsl_loss_logq_tw(long long n, const double *Q_dev, const
     if (e != cudaSuccess) return cuda_fail(e, who);
     return FQSL_OK;
 }
+
+extern "C" fqsl_status fqsl_field_check(fqsl_field f, void *cuda_stream)
+{
+    g_err.clear();
+    if (!f) return fail(FQSL_ERR_ARG, "fqsl_field_check: NULL handle");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fqsl_field_check");
+    std::lock_guard<std::mutex> lock(f->mu);
+    if (f->tp.valid && f->tp.buf) {
+        // index checks of the adjoint kernels (cleared here)
+        unsigned long long w[2] = {0, 0};
+        unsigned long long *ctr = field_tape_layout(f, (char *)f->tp.buf, f->tp.pool).ctr;
+        e = cudaMemcpy(w, ctr + 2, sizeof w, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && w[1]) e = cudaMemset(ctr + 2, 0, sizeof w);
+        if (e != cudaSuccess) return cuda_fail(e, "fqsl_field_check");
+        if (w[1])
+            return fail(FQSL_ERR_CUDA, "fqsl_field_check: %llu failed index checks in the adjoint kernels, first: "
+                                       "check %llu, value %lld", w[1], w[0] >> 56,
+                        (long long)(w[0] & ((1ull << 56) - 1)));
+    }
+    return FQSL_OK;
+}
+

@@ -36,6 +36,9 @@ struct FieldView {
     unsigned sy32, sz32;      // FP32 record byte strides along y and z
     const void *grad;         // grad(B/|B|) node records (Method II way 1) or NULL:
                               // FP32 48 B {g0..g8, 0, 0, 0}, FP64 80 B {g0..g8, 0}
+    long long nodes;          // nx * ny * nz
+    unsigned long long *err;  // adjoint kernels: [0] first failed index check
+                              // (code << 56 | value), [1] failed checks; NULL elsewhere
 };
 
 struct DevParams {
@@ -124,6 +127,7 @@ struct Tape {
     void *h;                    // [cap * k] T: accepted step sizes
     int4 *head;                 // [2 n] {last chunk, steps in it, end code, orientation sign}
     void *xe;                   // [2 n] T[4]: {footpoint x, y, z, exiting step of a chord end}
+    int32_t *owner;             // [cap] half-line of each chunk
 };
 
 struct TraceArgs {
@@ -173,12 +177,16 @@ struct AdjArgs {
     void *acc;                 // [nodes][8] {dB (3), dJ (3), 0, 0}, float or double
     unsigned long long *head;  // work counter of the reverse sweep
     long long n;
+    // per-step work arrays of the reverse sweep, for chunks 0..chunks-1 (T):
+    //   wx [chunk][k + 1][3] states, wj [chunk][k][12] step Jacobian J^T (9)
+    //   and Tw gradient (3), wb [chunk][k][3] adjoint of each step's end state
+    long long chunks;
+    void *wx, *wj, *wb;
 };
 // mode: 0 = FP32 state and float grid, 1 = FP32 state and double grid, 2 = FP64;
 // tape_f64: the tape was written by the FP64 tracer
 cudaError_t launch_q_vjp(const AdjArgs &a, int mode, bool tape_f64, cudaStream_t s);
-cudaError_t launch_reverse(const AdjArgs &a, int mode, bool tape_f64, int grid, cudaStream_t s);
-int reverse_blocks_per_sm(int mode, bool tape_f64);
+cudaError_t launch_reverse(const AdjArgs &a, int mode, bool tape_f64, cudaStream_t s);
 cudaError_t launch_curl_adjoint(const void *acc, bool acc64, const FieldView &g, void *dB, fqsl_dtype dt,
                                 cudaStream_t s);
 cudaError_t launch_tape_export(const Tape &tp, bool f64, const uint8_t *st, long long halves, int cap, int32_t *ns,

@@ -548,6 +548,7 @@ __device__ __forceinline__ bool tape_chunk(const Tape &tp, Lane<T> &L)
         return false;
     }
     tp.prev[c] = L.tcur;
+    tp.owner[c] = (int32_t)(2 * L.line + L.end);
     T *x = (T *)tp.xi + 4 * c;
     x[0] = L.x;
     x[1] = L.y;

@@ -333,7 +333,7 @@ def tape_export(field: Field, n_seeds: int, cap: int = 4096, stream=None):
     m = 2 * n_seeds
     out = dict(nsteps=torch.empty(m, dtype=torch.int32, device=dev), code=torch.empty(m, dtype=torch.int32, device=dev),
                hx=torch.empty(m, dtype=torch.float64, device=dev),
-               h=torch.zeros((m, cap), dtype=torch.float64, device=dev))
+               h=torch.zeros((m, max(cap, 1)), dtype=torch.float64, device=dev))
     _check(_lib.fqsl_tape_export(field.handle, cap, _ptr(out["nsteps"]), _ptr(out["code"]), _ptr(out["hx"]),
                                  _ptr(out["h"]), _stream(stream)))
     return out
