@@ -383,14 +383,15 @@ __device__ __forceinline__ void step_reverse(const FieldView &f, T sgn, const T 
 // J_i = d x_{i+1} / d x_i, g_i = d (Tw increment) / d x_i. So, rather than one
 // thread walking a whole direction backwards (a chain of ~15 dependent field
 // gathers per step), three passes:
-//   A (per tape chunk)  recompute the chunk's states from its checkpoint and
-//                       each step's J_i, g_i by forward-mode tangents;
+//   A1 (per tape chunk) recompute the chunk's states and stage derivatives
+//                       from its checkpoint;
+//   A2 (per step)       each step's J_i, g_i by forward-mode tangents;
 //   B (per half-line)   the exit step's VJP (with its scatter), then the
 //                       recurrence above over the stored J_i, g_i (no gathers),
 //                       storing each step's xbar_{i+1};
-//   C (per tape chunk)  each step's stage VJPs and scatters given xbar_{i+1}.
-// A and C run one thread per chunk of at most k steps, so the longest chain of
-// dependent gathers is k steps instead of a whole line.
+//   C (per step)        each step's stage VJPs and scatters given xbar_{i+1}.
+// Only A1 walks a chunk (at most k steps) sequentially, so the longest chain of
+// dependent gathers is one chunk's recompute instead of a whole line's reverse.
 // ---------------------------------------------------------------------------
 
 // V, dV/dxi at p and, from them, F, dtw and their position Jacobians:
@@ -441,50 +442,39 @@ __device__ __forceinline__ bool stage_jac(const FieldView &f, T sgn, T px, T py,
     return true;
 }
 
-// One accepted step (as advance with ax < 0) with its tangent map: the end
-// state x4, Jt[a][b] = d x4_b / d x_a (J^T) and gw[a] = d (Tw increment)/d x_a.
-template <typename T>
-__device__ __forceinline__ void step_jac(const FieldView &f, T sgn, const T x[3], T h, T x4[3], T Jt[3][3], T gw[3])
+// Reverse of an accepted step whose stage derivatives k are known (from
+// pass A1): xb in = adjoint of the end state, out = adjoint of x.
+template <typename T, typename AccT>
+__device__ __forceinline__ void step_reverse_k(const FieldView &f, T sgn, const T x[3], T h, const T k[5][3], T xb[3],
+                                               T wb, AccT *acc)
 {
-    T k[5][3], D[5][3][3];  // stage derivatives and their tangents D_s = d k_s / d x
-    T a4[3] = {0, 0, 0}, Ds[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gs[3] = {0, 0, 0};
+    T kb[5][3];
 #pragma unroll
-    for (int s = 0; s < 5; s++) {
+    for (int s = 0; s < 5; s++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) kb[s][a] = h * Fehlberg<T>::b4(s) * xb[a];
+#pragma unroll
+    for (int s = 4; s >= 0; s--) {
         T px = 0, py = 0, pz = 0;
-        T P[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};  // d p_s / d x
 #pragma unroll
         for (int r = 0; r < s; r++) {
             const T c = Fehlberg<T>::a(s, r);
             px += c * k[r][0];
             py += c * k[r][1];
             pz += c * k[r][2];
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) P[i][j] += h * c * D[r][i][j];
         }
-        T F[3], dtw, Jm[3][3], g[3];
-        stage_jac(f, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz, F, dtw, Jm, g);
-        const T b = Fehlberg<T>::b4(s);
+        const V3<T> pb = stage_vjp<T, AccT>(f, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz, -1, kb[s][0],
+                                            kb[s][1], kb[s][2], h * Fehlberg<T>::b4(s) * wb, acc);
+        xb[0] += pb.x;
+        xb[1] += pb.y;
+        xb[2] += pb.z;
 #pragma unroll
-        for (int i = 0; i < 3; i++) {
-            k[s][i] = F[i];
-            a4[i] += b * F[i];
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                D[s][i][j] = Jm[i][0] * P[0][j] + Jm[i][1] * P[1][j] + Jm[i][2] * P[2][j];
-                Ds[i][j] += b * D[s][i][j];
-            }
+        for (int r = 0; r < s; r++) {
+            const T c = h * Fehlberg<T>::a(s, r);
+            kb[r][0] += c * pb.x;
+            kb[r][1] += c * pb.y;
+            kb[r][2] += c * pb.z;
         }
-#pragma unroll
-        for (int j = 0; j < 3; j++) gs[j] += b * (g[0] * P[0][j] + g[1] * P[1][j] + g[2] * P[2][j]);
-    }
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        x4[i] = x[i] + h * a4[i];
-        gw[i] = h * gs[i];
-#pragma unroll
-        for (int j = 0; j < 3; j++) Jt[j][i] = (i == j ? (T)1 : (T)0) + h * Ds[i][j];
     }
 }
 
@@ -521,40 +511,148 @@ __device__ __forceinline__ bool chunk_of(const AdjArgs &A, long long c, long lon
     return true;
 }
 
-// pass A: states and step Jacobians of every chunk
+// pass A1: the states and stage derivatives of every chunk, from its
+// checkpoint (the only sequential recompute)
 template <typename T, typename TT>
-__global__ void __launch_bounds__(128) k_adj_fwd(const AdjArgs A)
+__global__ void __launch_bounds__(128) k_adj_states(const AdjArgs A)
 {
     const Tape &tp = A.tape;
     const int K = tp.k;
     T *WX = (T *)A.wx;
-    T *WJ = (T *)A.wj;
+    T *WK = (T *)A.wk;
     const TT *X = (const TT *)tp.xi;
     const TT *H = (const TT *)tp.h;
+    const int lane = threadIdx.x & 31;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < A.chunks;
          c += (long long)gridDim.x * blockDim.x) {
         long long hl;
-        int n, sg;
+        int n = 0, sg = 0;
         double w;
-        if (!chunk_of(A, c, hl, n, sg, w)) continue;
+        const bool live = chunk_of(A, c, hl, n, sg, w);
+        A.cinfo[c] = live ? make_int4(n, sg, (int)hl, 1) : make_int4(0, 0, -1, 0);
+        // this chunk's steps in the compacted list of passes A2 and C: one
+        // atomic per warp. The lanes still in the loop are a prefix of the
+        // warp (consecutive c); the *_sync intrinsics below converge them.
+        const long long left = A.chunks - (c - lane);
+        const unsigned mask = left >= 32 ? 0xffffffffu : ((1u << (unsigned)left) - 1u);
+        const int v = live ? n : 0;
+        int inc = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(mask, inc, d);
+            if (lane >= d) inc += t;
+        }
+        const int last = 31 - __clz(mask);
+        const int total = __shfl_sync(mask, inc, last);
+        unsigned long long base = 0;
+        if (lane == 0 && total > 0) base = atomicAdd(A.nsteps, (unsigned long long)total);
+        base = __shfl_sync(mask, base, 0) + (unsigned long long)(inc - v);
+        if (!live) continue;
+        for (int i = 0; i < n; i++) A.steps[base + i] = (int32_t)(c * K + i);
         T x[3] = {(T)X[4 * c], (T)X[4 * c + 1], (T)X[4 * c + 2]};
         T *wx = WX + c * (K + 1) * 3;
-        T *wj = WJ + c * K * 12;
+        T *wk = WK + c * K * 15;
         wx[0] = x[0];
         wx[1] = x[1];
         wx[2] = x[2];
         for (int i = 0; i < n; i++) {
-            T x4[3], Jt[3][3], gw[3];
-            step_jac(A.f, (T)sg, x, (T)H[c * K + i], x4, Jt, gw);
+            T x4[3], kt[5][4];
+            advance(A.f, (T)sg, x, (T)H[c * K + i], -1, x4, kt);
+#pragma unroll
+            for (int s = 0; s < 5; s++)
+#pragma unroll
+                for (int a = 0; a < 3; a++) wk[15 * i + 3 * s + a] = kt[s][a];
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                wj[12 * i + 3 * a + 0] = Jt[a][0];
-                wj[12 * i + 3 * a + 1] = Jt[a][1];
-                wj[12 * i + 3 * a + 2] = Jt[a][2];
-                wj[12 * i + 9 + a] = gw[a];
                 x[a] = x4[a];
                 wx[3 * (i + 1) + a] = x4[a];
             }
+        }
+    }
+}
+
+// entry t of the compacted step list: the step's flat index j = c k + i,
+// its chunk c and index i, the half-line's orientation and Tw weight
+__device__ __forceinline__ bool step_of(const AdjArgs &A, long long t, long long &j, long long &c, int &i, int &sg,
+                                        double &w)
+{
+    const int K = A.tape.k;
+    j = A.steps[t];
+    c = j / K;
+    i = (int)(j - c * K);
+    if (j < 0 || c >= A.chunks) {
+        record_fail(A.f.err, 1, j);
+        return false;
+    }
+    const int4 ci = A.cinfo[c];
+    if (!ci.w || i >= ci.x) return false;
+    sg = ci.y;
+    w = A.dTw ? A.dTw[ci.z >> 1] : 0.0;
+    if (!(w == w) || fabs(w) == INFINITY) w = 0.0;
+    return true;
+}
+
+// pass A2: each step's Jacobian J^T and Tw gradient (one thread per step)
+template <typename T, typename TT>
+__global__ void __launch_bounds__(128) k_adj_jac(const AdjArgs A)
+{
+    const int K = A.tape.k;
+    const T *WX = (const T *)A.wx;
+    const T *WK = (const T *)A.wk;
+    T *WJ = (T *)A.wj;
+    const TT *H = (const TT *)A.tape.h;
+    const long long steps = (long long)*A.nsteps;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < steps;
+         t += (long long)gridDim.x * blockDim.x) {
+        long long j, c;
+        int i, sg;
+        double w;
+        if (!step_of(A, t, j, c, i, sg, w)) continue;
+        const T *x = WX + (c * (K + 1) + i) * 3;
+        const T *wk = WK + j * 15;
+        const T h = (T)H[j];
+        const T sgn = (T)sg;
+        T k[5][3];
+#pragma unroll
+        for (int s = 0; s < 5; s++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) k[s][a] = wk[3 * s + a];
+        // tangents: P_s = d p_s / d x = I + h sum_r a_sr D_r, D_s = dF(p_s)/dp P_s
+        T D[5][3][3], Ds[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gs[3] = {0, 0, 0};
+#pragma unroll
+        for (int s = 0; s < 5; s++) {
+            T px = 0, py = 0, pz = 0;
+            T P[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+#pragma unroll
+            for (int r = 0; r < s; r++) {
+                const T cc = Fehlberg<T>::a(s, r);
+                px += cc * k[r][0];
+                py += cc * k[r][1];
+                pz += cc * k[r][2];
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+#pragma unroll
+                    for (int b = 0; b < 3; b++) P[a][b] += h * cc * D[r][a][b];
+            }
+            T F[3], dtw, Jm[3][3], g[3];
+            stage_jac(A.f, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz, F, dtw, Jm, g);
+            const T b4 = Fehlberg<T>::b4(s);
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int b = 0; b < 3; b++) {
+                    D[s][a][b] = Jm[a][0] * P[0][b] + Jm[a][1] * P[1][b] + Jm[a][2] * P[2][b];
+                    Ds[a][b] += b4 * D[s][a][b];
+                }
+#pragma unroll
+            for (int b = 0; b < 3; b++) gs[b] += b4 * (g[0] * P[0][b] + g[1] * P[1][b] + g[2] * P[2][b]);
+        }
+        T *wj = WJ + j * 12;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+#pragma unroll
+            for (int b = 0; b < 3; b++) wj[3 * a + b] = (a == b ? (T)1 : (T)0) + h * Ds[b][a];
+            wj[9 + a] = h * gs[a];
         }
     }
 }
@@ -605,8 +703,9 @@ __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
         const T x[3] = {xn[0], xn[1], xn[2]};
         T h, d = 0, ws = wb;
         int ax = -1;
-        T yb[3] = {xb[0], xb[1], xb[2]}, keep[3] = {0, 0, 0};
+        T yb[3] = {xb[0], xb[1], xb[2]}, keep[3] = {0, 0, 0}, y[3];
         T x4[3], kt[5][4];
+        bool zero = false;  // a zero-length exit step
         if (chord) {
             // end = x + t0 (x4 - x), t0 = (target - x_ax)/(x4_ax - x_ax); Tw gains t0 of the step's increment
             h = (T)((const TT *)tp.xe)[4 * hl + 3];
@@ -634,7 +733,20 @@ __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
             ax = fax;
             h = target - x[fax];
             yb[fax] = (T)0;
-            if (clamped) {
+            if (h == (T)0) {
+                // a zero-length exit step (a seed on the face): the end is x,
+                // all stages sit at x, nothing is scattered; only the length's
+                // dependence on x_ax remains: d = K(x) . yb + twK(x) wbar
+                if (hd.y == 0 && tp.prev[hd.x] < 0) continue;  // no earlier step: the seed's adjoint is not needed
+                const Rhs<T> o = rhs_fwd(f, sgn, x[0], x[1], x[2]);
+                const T fa = o.F[fax];
+                d = (o.F[0] * yb[0] + o.F[1] * yb[1] + o.F[2] * yb[2] + o.dtw * wb) / fa;
+                y[0] = yb[0];
+                y[1] = yb[1];
+                y[2] = yb[2];
+                y[fax] -= d;
+                zero = true;
+            } else if (clamped) {
                 advance(f, sgn, x, h, ax, x4, kt);
                 const int nn[3] = {f.nx, f.ny, f.nz};
 #pragma unroll
@@ -642,17 +754,19 @@ __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
                     if (b != fax && (x4[b] < (T)0 || x4[b] > (T)(nn[b] - 1))) yb[b] = (T)0;
             }
         }
-        step_reverse<T, AccT>(f, sgn, x, h, ax, yb, ws, ax >= 0 ? &d : (T *)nullptr, acc);
-        T y[3];
+        if (!zero) {
+            step_reverse<T, AccT>(f, sgn, x, h, ax, yb, ws, ax >= 0 ? &d : (T *)nullptr, acc);
 #pragma unroll
-        for (int a = 0; a < 3; a++) y[a] = yb[a] + keep[a];
-        if (ax >= 0) y[fax] -= d;  // h = target - x_ax
+            for (int a = 0; a < 3; a++) y[a] = yb[a] + keep[a];
+            if (ax >= 0) y[fax] -= d;  // h = target - x_ax
+        }
         // the accepted steps, last first: store each step's end-state adjoint,
         // then xbar_i = J_i^T xbar_{i+1} + g_i wbar
         int c = hd.x, n = hd.y;
         for (;;) {
             const T *wj = WJ + (long long)c * K * 12;
             T *wbp = WB + (long long)c * K * 3;
+#pragma unroll 4
             for (int i = n - 1; i >= 0; i--) {
                 wbp[3 * i + 0] = y[0];
                 wbp[3 * i + 1] = y[1];
@@ -673,28 +787,32 @@ __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
     }
 }
 
-// pass C: the stage VJPs of every step, given its end-state adjoint
+// pass C: the stage VJPs of every step, given its end-state adjoint (one
+// thread per step)
 template <typename T, typename AccT, typename TT>
 __global__ void __launch_bounds__(128) k_adj_rev(const AdjArgs A)
 {
-    const Tape &tp = A.tape;
-    const int K = tp.k;
+    const int K = A.tape.k;
     const T *WX = (const T *)A.wx;
     const T *WB = (const T *)A.wb;
-    const TT *H = (const TT *)tp.h;
+    const T *WK = (const T *)A.wk;
+    const TT *H = (const TT *)A.tape.h;
     AccT *acc = (AccT *)A.acc;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < A.chunks;
-         c += (long long)gridDim.x * blockDim.x) {
-        long long hl;
-        int n, sg;
+    const long long steps = (long long)*A.nsteps;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < steps;
+         t += (long long)gridDim.x * blockDim.x) {
+        long long j, c;
+        int i, sg;
         double w;
-        if (!chunk_of(A, c, hl, n, sg, w)) continue;
-        const T *wx = WX + c * (K + 1) * 3;
-        const T *wbp = WB + c * K * 3;
-        for (int i = 0; i < n; i++) {
-            T yb[3] = {wbp[3 * i], wbp[3 * i + 1], wbp[3 * i + 2]};
-            step_reverse<T, AccT>(A.f, (T)sg, wx + 3 * i, (T)H[c * K + i], -1, yb, (T)w, (T *)nullptr, acc);
-        }
+        if (!step_of(A, t, j, c, i, sg, w)) continue;
+        const T *wk = WK + j * 15;
+        T yb[3] = {WB[3 * j], WB[3 * j + 1], WB[3 * j + 2]};
+        T ks[5][3];
+#pragma unroll
+        for (int s = 0; s < 5; s++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) ks[s][a] = wk[3 * s + a];
+        step_reverse_k<T, AccT>(A.f, (T)sg, WX + (c * (K + 1) + i) * 3, (T)H[j], ks, yb, (T)w, acc);
     }
 }
 
@@ -871,13 +989,14 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
 // dB += dB_interp + curl^T dJ_interp (per node)
 // ---------------------------------------------------------------------------
 // coefficient of node jn in row i of the curl grid's derivative stencil along
-// an axis of n nodes and spacing h
-__device__ __forceinline__ double stencil(long long i, long long jn, long long n, double h)
+// an axis of n nodes, rh = 1/spacing
+template <typename A>
+__device__ __forceinline__ A stencil(int i, int jn, int n, A rh)
 {
-    if (n == 2) return jn == 1 ? 1.0 / h : -1.0 / h;
-    if (i == 0) return jn == 0 ? -1.5 / h : (jn == 1 ? 2.0 / h : (jn == 2 ? -0.5 / h : 0.0));
-    if (i == n - 1) return jn == n - 1 ? 1.5 / h : (jn == n - 2 ? -2.0 / h : (jn == n - 3 ? 0.5 / h : 0.0));
-    return jn == i + 1 ? 0.5 / h : (jn == i - 1 ? -0.5 / h : 0.0);
+    if (n == 2) return jn == 1 ? rh : -rh;
+    if (i == 0) return jn == 0 ? (A)-1.5 * rh : (jn == 1 ? (A)2 * rh : (jn == 2 ? (A)-0.5 * rh : (A)0));
+    if (i == n - 1) return jn == n - 1 ? (A)1.5 * rh : (jn == n - 2 ? (A)-2 * rh : (jn == n - 3 ? (A)0.5 * rh : (A)0));
+    return jn == i + 1 ? (A)0.5 * rh : (jn == i - 1 ? (A)-0.5 * rh : (A)0);
 }
 
 template <typename AccT, typename OutT>
@@ -886,34 +1005,54 @@ __global__ void __launch_bounds__(256) k_curl_adjoint(const AccT *__restrict__ a
 {
     const long long total = (long long)nx * ny * nz;
     const long long sy = nx, sz = (long long)nx * ny;
+    // half reciprocal spacings for the central rows, in the grid's precision
+    const AccT hx = (AccT)(0.5 / dx), hy = (AccT)(0.5 / dy), hz = (AccT)(0.5 / dz);
     for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < total;
          node += (long long)gridDim.x * blockDim.x) {
-        const long long idx[3] = {node % nx, (node / nx) % ny, node / sz};
+        const unsigned un = (unsigned)node, uxy = (unsigned)nx * (unsigned)ny;  // nodes < 2^31
+        const unsigned iz = un / uxy, rem = un - iz * uxy, iy = rem / (unsigned)nx, ix = rem - iy * (unsigned)nx;
         const long long n[3] = {nx, ny, nz}, stride[3] = {1, sy, sz};
-        const double h[3] = {dx, dy, dz};
+        const int idx[3] = {(int)ix, (int)iy, (int)iz};
+        const AccT hh[3] = {hx, hy, hz};
         // DT[axis][c] = (D_axis^T dJ_c)(node)
-        double DT[3][3];
+        AccT DT[3][3];
+#pragma unroll
         for (int a = 0; a < 3; a++) {
-            DT[a][0] = DT[a][1] = DT[a][2] = 0.0;
-            const long long j0 = idx[a];
-            const long long lo = j0 - 2 < 0 ? 0 : j0 - 2, hi = j0 + 2 > n[a] - 1 ? n[a] - 1 : j0 + 2;
-            for (long long i = lo; i <= hi; i++) {
-                const double cf = stencil(i, j0, n[a], h[a]);
-                if (cf == 0.0) continue;
-                const AccT *q = acc + 8 * (node + (i - j0) * stride[a]);
-                DT[a][0] += cf * (double)q[3];
-                DT[a][1] += cf * (double)q[4];
-                DT[a][2] += cf * (double)q[5];
+            const int j0 = idx[a];
+            if (j0 >= 3 && j0 + 3 < n[a]) {
+                // only the central rows j0 -+ 1 reach this node: coefficients -+1/(2h)
+                const AccT *qm = acc + 8 * (node - stride[a]);
+                const AccT *qp = acc + 8 * (node + stride[a]);
+                DT[a][0] = hh[a] * (qm[3] - qp[3]);
+                DT[a][1] = hh[a] * (qm[4] - qp[4]);
+                DT[a][2] = hh[a] * (qm[5] - qp[5]);
+            } else {
+                // rows near the faces (the one-sided stencils of the curl grid)
+                AccT t0 = 0, t1 = 0, t2 = 0;
+                const int na = (int)n[a];
+                const int lo = j0 - 2 < 0 ? 0 : j0 - 2, hi = j0 + 2 > na - 1 ? na - 1 : j0 + 2;
+                for (int i = lo; i <= hi; i++) {
+                    const AccT cf = stencil<AccT>(i, j0, na, (AccT)2 * hh[a]);
+                    if (cf == (AccT)0) continue;
+                    const AccT *q = acc + 8 * (node + (long long)(i - j0) * stride[a]);
+                    t0 += cf * q[3];
+                    t1 += cf * q[4];
+                    t2 += cf * q[5];
+                }
+                DT[a][0] = t0;
+                DT[a][1] = t1;
+                DT[a][2] = t2;
             }
         }
         // Jx = Dy Bz - Dz By, Jy = Dz Bx - Dx Bz, Jz = Dx By - Dy Bx
         const AccT *p = acc + 8 * node;
-        const double bx = (double)p[0] + DT[2][1] - DT[1][2];
-        const double by = (double)p[1] + DT[0][2] - DT[2][0];
-        const double bz = (double)p[2] + DT[1][0] - DT[0][1];
-        dB[3 * node + 0] = (OutT)((double)dB[3 * node + 0] + bx);
-        dB[3 * node + 1] = (OutT)((double)dB[3 * node + 1] + by);
-        dB[3 * node + 2] = (OutT)((double)dB[3 * node + 2] + bz);
+        const AccT bx = p[0] + DT[2][1] - DT[1][2];
+        const AccT by = p[1] + DT[0][2] - DT[2][0];
+        const AccT bz = p[2] + DT[1][0] - DT[0][1];
+        using W = decltype(AccT{} + OutT{});  // the wider of the two
+        dB[3 * node + 0] = (OutT)((W)dB[3 * node + 0] + (W)bx);
+        dB[3 * node + 1] = (OutT)((W)dB[3 * node + 1] + (W)by);
+        dB[3 * node + 2] = (OutT)((W)dB[3 * node + 2] + (W)bz);
     }
 }
 
@@ -1052,10 +1191,12 @@ template <typename T, typename AccT, typename TT>
 void reverse_passes(const AdjArgs &a, cudaStream_t s)
 {
     const unsigned gc = adj::grid_for(a.chunks, 128, 16);
+    const unsigned gs = adj::grid_for(a.chunks * a.tape.k, 128, 16);
     const unsigned gl = adj::grid_for(2 * a.n, 128, 16);
-    adj::k_adj_fwd<T, TT><<<gc, 128, 0, s>>>(a);
+    adj::k_adj_states<T, TT><<<gc, 128, 0, s>>>(a);
+    adj::k_adj_jac<T, TT><<<gs, 128, 0, s>>>(a);
     adj::k_adj_lines<T, AccT, TT><<<gl, 128, 0, s>>>(a);
-    adj::k_adj_rev<T, AccT, TT><<<gc, 128, 0, s>>>(a);
+    adj::k_adj_rev<T, AccT, TT><<<gs, 128, 0, s>>>(a);
 }
 
 template <typename TT>

@@ -495,7 +495,7 @@ void index_lattice(const fqsl_field f, Lattice &lat)
 // footpoint adjoints, the loss sums and the adjoint node grid.
 struct TapeLayout {
     Scratch s;
-    unsigned long long *ctr;  // [0] tape chunks handed out, [1] reverse-sweep work counter,
+    unsigned long long *ctr;  // [0] tape chunks handed out, [1] live steps of the reverse sweep,
                               // [2], [3] failed index checks of the adjoint kernels
     Tape tape;
     double *xbar, *sums;
@@ -1277,20 +1277,22 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
     const int K = tl.tape.k;
     const size_t rs = rp == FQSL_F64 ? 8 : 4;
     const size_t bx = align_up((size_t)used * (K + 1) * 3 * rs), bj = align_up((size_t)used * K * 12 * rs),
-                 bb = align_up((size_t)used * K * 3 * rs);
-    if (bx + bj + bb > f->tp.work_cap) {
+                 bk = align_up((size_t)used * K * 15 * rs), bb = align_up((size_t)used * K * 3 * rs),
+                 bi = align_up((size_t)used * sizeof(int4)), bs = align_up((size_t)used * K * sizeof(int32_t));
+    const size_t wbytes = bx + bj + bk + bb + bi + bs;
+    if (wbytes > f->tp.work_cap) {
         cudaError_t e0 = cudaDeviceSynchronize();
         if (e0 == cudaSuccess) {
             cudaFree(f->tp.work);
             f->tp.work = nullptr;
             f->tp.work_cap = 0;
-            e0 = cudaMalloc(&f->tp.work, bx + bj + bb);
+            e0 = cudaMalloc(&f->tp.work, wbytes);
         }
         if (e0 != cudaSuccess) {
             cudaGetLastError();
             return cuda_fail(e0, "fqsl_backward: work arrays");
         }
-        f->tp.work_cap = bx + bj + bb;
+        f->tp.work_cap = wbytes;
     }
     cudaError_t e = cudaMemsetAsync(tl.xbar, 0, (size_t)(6 * n) * sizeof(double), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(tl.acc, 0, nodes * 8 * (acc64 ? 8 : 4), stream);
@@ -1310,12 +1312,15 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
     a.dTw = dTw_dev;
     a.xbar = tl.xbar;
     a.acc = tl.acc;
-    a.head = tl.ctr + 1;
     a.n = n;
     a.chunks = (long long)used;
     a.wx = f->tp.work;
     a.wj = (char *)f->tp.work + bx;
-    a.wb = (char *)f->tp.work + bx + bj;
+    a.wk = (char *)f->tp.work + bx + bj;
+    a.wb = (char *)f->tp.work + bx + bj + bk;
+    a.cinfo = (int4 *)((char *)f->tp.work + bx + bj + bk + bb);
+    a.steps = (int32_t *)((char *)f->tp.work + bx + bj + bk + bb + bi);
+    a.nsteps = tl.ctr + 1;  // cleared with the check words below
     e = launch_q_vjp(a, mode, tape_f64, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     mark(f, 0, stream);

@@ -175,13 +175,16 @@ struct AdjArgs {
     const double *dQ, *dTw;    // per-seed weights (NULL = 0)
     double *xbar;              // [2 n][3] adjoint of each footpoint (index coordinates)
     void *acc;                 // [nodes][8] {dB (3), dJ (3), 0, 0}, float or double
-    unsigned long long *head;  // work counter of the reverse sweep
     long long n;
     // per-step work arrays of the reverse sweep, for chunks 0..chunks-1 (T):
     //   wx [chunk][k + 1][3] states, wj [chunk][k][12] step Jacobian J^T (9)
-    //   and Tw gradient (3), wb [chunk][k][3] adjoint of each step's end state
+    //   and Tw gradient (3), wk [chunk][k][15] stage derivatives, wb
+    //   [chunk][k][3] adjoint of each step's end state
     long long chunks;
-    void *wx, *wj, *wb;
+    void *wx, *wj, *wk, *wb;
+    int4 *cinfo;               // [chunks] {steps, orientation, half-line, live} (pass A1)
+    int32_t *steps;            // [chunks * k] live steps c k + i, compacted (pass A1)
+    unsigned long long *nsteps;  // number of entries in steps
 };
 // mode: 0 = FP32 state and float grid, 1 = FP32 state and double grid, 2 = FP64;
 // tape_f64: the tape was written by the FP64 tracer
