@@ -607,6 +607,14 @@ fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params
     cudaError_t e = cudaMemsetAsync(f->counters, 0, 4 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess && lat.allow_rot) e = cudaMemsetAsync(s.rot_slot, 0, (size_t)n * sizeof(int32_t), stream);
     if (e == cudaSuccess && tape) e = cudaMemsetAsync(tl.ctr, 0, 4 * sizeof(unsigned long long), stream);
+    if (e == cudaSuccess && tape) {
+        // the taped tracer traces the two directions of a line as separate
+        // items and combines status, trial count and (FP64) sums atomically
+        e = cudaMemsetAsync(s.rec.st, 0, (size_t)n, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s.rec.steps, 0, (size_t)n * sizeof(int32_t), stream);
+        if (e == cudaSuccess && s.rec.tw) e = cudaMemsetAsync(s.rec.tw, 0, (size_t)n * sizeof(double), stream);
+        if (e == cudaSuccess && s.rec.len) e = cudaMemsetAsync(s.rec.len, 0, (size_t)n * sizeof(double), stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, who);
 
     TraceArgs a{};
@@ -652,6 +660,7 @@ fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params
         int bps = tape_blocks_per_sm(f, p->precision);
         if (p->blocks_per_sm > 0 && p->blocks_per_sm < bps) bps = p->blocks_per_sm;
         long long grid = (long long)f->sms * bps;
+        a.nitems *= 2;  // one item per direction of a line
         const long long need = (a.nitems + kTraceBlock - 1) / kTraceBlock;
         if (need < grid) grid = need;
         if (grid < 1) grid = 1;

@@ -585,9 +585,39 @@ __device__ __forceinline__ void tape_end(const Tape &tp, Lane<T> &L, int code, T
     e[3] = hx;
 }
 
+// Split directions (the taped tracer): each direction of a line is its own
+// work item, so the line's status bits, trial count and (FP64) length/Tw sums
+// are combined with atomics on records cleared before the launch. Each
+// direction finishes with its share; the one that completes the trial count
+// marks the line MAXSTEPS if both together used more than max_steps. (A sum of
+// two values onto zero does not depend on their order.)
+__device__ __forceinline__ void or_status(uint8_t *st, long long line, unsigned bits)
+{
+    unsigned *w = (unsigned *)(st + (line & ~3LL));
+    atomicOr(w, bits << (8 * (unsigned)(line & 3)));
+}
+
+template <typename T>
+__device__ __forceinline__ void split_finish(const TraceArgs &A, const LineRecs &R, Lane<T> &L, bool bad)
+{
+    const int before = atomicAdd(R.steps + L.line, L.steps);
+    unsigned st = (unsigned)L.st;
+    if ((long long)before + L.steps > A.p.max_steps) {
+        st |= FQSL_LINE_MAXSTEPS;
+        bad = true;
+    }
+    or_status(R.st, L.line, st);
+    if constexpr (sizeof(T) == 8) {
+        if (bad) {
+            if (R.tw) R.tw[L.line] = NAN;
+            if (R.len) R.len[L.line] = NAN;
+        }
+    }
+}
+
 // Finish the line with a bad status (MAXSTEPS or NULL_B): the unfinished end
 // is the current position, an untraced end the seed, their faces -1.
-template <typename T>
+template <typename T, bool SPLIT = false>
 __device__ __forceinline__ void finish_bad(const TraceArgs &A, const LineRecs &R, Lane<T> &L, unsigned bit)
 {
     const FieldView &f = A.f;
@@ -595,22 +625,26 @@ __device__ __forceinline__ void finish_bad(const TraceArgs &A, const LineRecs &R
     if constexpr (sizeof(T) == 8) {
         write_end(A, R, L, L.end, to_phys(f.o[0], f.d[0], (double)L.x), to_phys(f.o[1], f.d[1], (double)L.y),
                   to_phys(f.o[2], f.d[2], (double)L.z), -1, 0.0);
-        if (L.end == 0)
+        if (L.end == 0 && !SPLIT)
             write_end(A, R, L, 1, to_phys(f.o[0], f.d[0], (double)L.sx), to_phys(f.o[1], f.d[1], (double)L.sy),
                       to_phys(f.o[2], f.d[2], (double)L.sz), -1, 0.0);
         if (R.tw) R.tw[L.line] = NAN;
         if (R.len) R.len[L.line] = NAN;
     } else {
         write_end32(R, L.line, L.end, (float)L.x, (float)L.y, (float)L.z, -1);
-        if (L.end == 0) write_end32(R, L.line, 1, (float)L.sx, (float)L.sy, (float)L.sz, -1);
+        if (L.end == 0 && !SPLIT) write_end32(R, L.line, 1, (float)L.sx, (float)L.sy, (float)L.sz, -1);
     }
-    R.st[L.line] = (uint8_t)L.st;
-    R.steps[L.line] = L.steps;
+    if constexpr (SPLIT) {
+        split_finish(A, R, L, true);
+    } else {
+        R.st[L.line] = (uint8_t)L.st;
+        R.steps[L.line] = L.steps;
+    }
 }
 
 // A direction reached a face at index position (x, y, z) with deviation
 // vectors (du, dv) (Method II only).
-template <typename T, bool ACC, int DEV = 0>
+template <typename T, bool ACC, int DEV = 0, bool SPLIT = false>
 __device__ __forceinline__ bool finish_dir(const TraceArgs &A, const LineRecs &R, Lane<T> &L, T x, T y, T z,
                                            int face, const T *du = nullptr, const T *dv = nullptr)
 {
@@ -657,6 +691,14 @@ __device__ __forceinline__ bool finish_dir(const TraceArgs &A, const LineRecs &R
             }
             R.kacc[2 * L.line + L.end] = k;
         }
+    }
+    if constexpr (SPLIT) {
+        if constexpr (sizeof(T) == 8) {
+            if (R.tw) atomicAdd(R.tw + L.line, acc_tw<T, ACC>(L));
+            if (R.len) atomicAdd(R.len + L.line, acc_len<T, ACC>(L));
+        }
+        split_finish(A, R, L, false);
+        return false;
     }
     if (L.end == 0) {
         if constexpr (sizeof(T) == 8) {
@@ -768,9 +810,10 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
     return true;
 }
 
-// Lattice seed: frame, tolerance and rotation decision (Sec. 4).
+// Lattice seed: frame, tolerance and rotation decision (Sec. 4). reg_rot:
+// queue a rotated seed for its extra lines (once per seed).
 template <typename T, bool ACC, int DEV = 0>
-__device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, long long item)
+__device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, long long item, bool reg_rot = true)
 {
     constexpr bool kF64 = sizeof(T) == 8;
     const Lattice &G = A.lat;
@@ -856,9 +899,11 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
                 if (G.allow_rot && ratio < (T)A.p.rot && !on_face) {
                     st0 = FQSL_LINE_ROTATED;
                     bn0 = (double)nB;
-                    const unsigned slot = atomicAdd(A.q.rot_count, 1u);
-                    A.q.rot_seed[slot] = (int32_t)idx;
-                    A.q.rot_slot[idx] = (int32_t)slot + 1;
+                    if (reg_rot) {
+                        const unsigned slot = atomicAdd(A.q.rot_count, 1u);
+                        A.q.rot_seed[slot] = (int32_t)idx;
+                        A.q.rot_slot[idx] = (int32_t)slot + 1;
+                    }
                 } else {
                     bn0 = (double)bn;
                     if (kF64) {
@@ -945,7 +990,9 @@ __device__ __forceinline__ bool init_list(const TraceArgs &A, Lane<T> &L, long l
 // vectors with grad(B/|B|) by way 1 or way 2 (lattice source only).
 // BATCH: the launch traces the entries of a batch (BatchArgs); each lane keeps
 // the entry of its line. A0 holds the launch-wide parameters and counter.
-// TAPE: also write the step tape A0.tape (lattice lines, Method I).
+// TAPE: also write the step tape A0.tape (lattice lines, Method I), and trace
+// the two directions of a line as separate work items (twice the lattice's
+// items; see split_finish) so that a long line's halves run side by side.
 template <typename T, int SRC, bool ACC, int DEV = 0, bool BATCH = false, bool TAPE = false>
 __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs &BA)
 {
@@ -1011,7 +1058,17 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                 const long long item = ck_cur + rank - ck_base;
                 eb = ck_ent;
                 const TraceArgs &E = ent();
-                if (SRC == kSrcLattice) active = init_lattice<T, ACC, DEV>(E, L, item);
+                if (SRC == kSrcLattice) {
+                    if constexpr (TAPE) {
+                        // items come in 32-lane groups: a tile's direction 0,
+                        // then the same tile's direction 1
+                        const long long g = item >> 5;
+                        active = init_lattice<T, ACC, DEV>(E, L, ((g >> 1) << 5) | (item & 31), (g & 1) == 0);
+                        if (active && (g & 1)) L.end = 1;
+                    } else {
+                        active = init_lattice<T, ACC, DEV>(E, L, item);
+                    }
+                }
                 else if (SRC == kSrcExtra) active = item < 4LL * (long long)*E.q.rot_count && init_extra<T, ACC>(E, L, item);
                 else active = init_list<T, ACC>(E, L, item);
             }
@@ -1043,7 +1100,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
         T hh;
         if (!henon) {
             if (L.steps >= max_steps) {
-                finish_bad(A, R, L, FQSL_LINE_MAXSTEPS);
+                finish_bad<T, TAPE>(A, R, L, FQSL_LINE_MAXSTEPS);
                 active = false;
                 continue;
             }
@@ -1141,7 +1198,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
         }
 
         if (fail == 1) {
-            finish_bad(A, R, L, FQSL_LINE_NULL_B);
+            finish_bad<T, TAPE>(A, R, L, FQSL_LINE_NULL_B);
             active = false;
             continue;
         }
@@ -1284,7 +1341,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                     ev[c] = L.v[c] + L.t0 * (L.ov[c] - L.v[c]);
                 }
             }
-            active = finish_dir<T, ACC, DEV>(A, R, L, ex, ey, ez, L.fc0, eu, ev);
+            active = finish_dir<T, ACC, DEV, TAPE>(A, R, L, ex, ey, ez, L.fc0, eu, ev);
             waiting = active && A0.p.sync_dirs;
             continue;
         }
@@ -1323,7 +1380,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                 ev[c] = L.v[c] + hh * ad[3 + c];
             }
         }
-        active = finish_dir<T, ACC, DEV>(A, R, L, tx, ty, tz, L.hface, eu, ev);
+        active = finish_dir<T, ACC, DEV, TAPE>(A, R, L, tx, ty, tz, L.hface, eu, ev);
         waiting = active && A0.p.sync_dirs;
     }
 }

@@ -298,3 +298,26 @@ def test_backward_argument_errors(fq, small):
     dB = fq.backward(field, None, None)
     field.check()
     assert float(dB.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("plane", [PLANE16, XZ], ids=["z0_plane", "interior_xz_plane"])
+def test_taped_map_equals_plain_map(fq, small, precision, plane):
+    # the taped tracer runs the two directions of a line as separate items;
+    # the map it returns is the plain map's
+    from parity import assert_bitwise, to_np
+
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    plain = to_np(fq.qmap_plane(field, *plane, fq.params(precision=precision)))
+    taped = to_np(fq.qmap_plane(field, *plane, fq.params(precision=precision, tape=1)))
+    field.check()
+    if precision == "f64":
+        assert_bitwise(taped, plain)
+    else:
+        for k in ("face1", "face2", "status", "steps"):
+            assert np.array_equal(taped[k], plain[k]), k
+        ok = np.isfinite(plain["Q"])
+        assert np.array_equal(ok, np.isfinite(taped["Q"]))
+        np.testing.assert_allclose(taped["Q"][ok], plain["Q"][ok], rtol=1e-5)
+        np.testing.assert_allclose(taped["Tw"], plain["Tw"], rtol=1e-5, atol=1e-7)
