@@ -49,8 +49,8 @@ NUM_SMS = 152
 # DRAM bytes (read + write) of one k_trace_f32 launch on this workload, from
 # the ncu capture summarised in profiles/trace_f32_c2_monopole_1024x1024.md,
 # valid while the tracer sources hash to TRACE_F32_SRC_HASH.
-TRACE_F32_DRAM_BYTES = 308.808448e6 + 59.993856e6
-TRACE_F32_SRC_HASH = "efc172667b648b79"
+TRACE_F32_DRAM_BYTES = 308.475648e6 + 59.954432e6
+TRACE_F32_SRC_HASH = "e2a9cc893567a927"
 
 
 def _trace_src_hash():
@@ -393,16 +393,17 @@ ADJ_SEEDS = 256
 ADJ_WORKLOAD = "adjoint_monopole24_twisttube_128x128x64_f32_z0plane_256x256_logQ_Tw_loss_methodI"
 ADJ_METRIC = "adjoint s/grad"
 ADJ_SAMPLE = 64  # oracle seeds per check (plus their 4-neighbour lines)
-# Algorithmic work of one accepted step in the reverse sweep, counted from
-# adjoint.cu: the 5 stages of the 4th-order solution are evaluated once (the
-# forward values the VJP needs: 5 right-hand sides of 145 flops and 8 x 32-byte
-# corner records each) and reversed once (5 stage VJPs: 8 corners x 6
-# components x 4 products for the value and its 3 derivatives = 192 FMAs, 60
-# flops of local derivative, 48 products for the scatter, 3 x 6 for the
-# position adjoint; 8 x 32-byte records and 8 x 24 bytes of scattered adjoints).
-# The recompute of each chunk from its checkpoint is extra (not counted).
-REV_FLOPS_PER_STEP = 5 * 145 + 5 * (2 * 192 + 60 + 48 + 36) + 250
-REV_GATHER_BYTES_PER_STEP = 10 * 8 * 32
+# Work of one accepted step in the reverse sweep, counted from adjoint.cu:
+#   A1 (recompute)  5 right-hand sides of 145 flops, 8 x 32-byte corner records each
+#   A2 (Jacobian)   5 stage Jacobians: trilinear value and 3 derivatives of 6
+#                   components (8 x 6 x 4 FMAs = 384 flops), 3x3 local Jacobian and
+#                   Tw gradient (~110), tangent products (~100)
+#   C (VJP)         5 stage VJPs: the same gather with derivatives (384), local
+#                   adjoint (~60), scatter of 8 x 6 products (96), position adjoint (36)
+# plus stage combinations (~300). Gathers: 15 x 8 records of 32 bytes; scatter:
+# 5 x 8 corners x 24 bytes of atomics.
+REV_FLOPS_PER_STEP = 5 * 145 + 5 * (384 + 110 + 100) + 5 * (384 + 60 + 96 + 36) + 300
+REV_GATHER_BYTES_PER_STEP = 15 * 8 * 32
 REV_SCATTER_BYTES_PER_STEP = 5 * 8 * 24
 
 
@@ -499,6 +500,7 @@ def run_adjoint(args):
     g32 = dB.cpu().numpy().astype(np.float64)
     tape = fq.tape_export(field, n, cap=0)
     acc_steps = float(tape["nsteps"].to(torch.float64).sum())
+    trials = float(out["steps"].to(torch.float64).sum())
     t_fwd, t_rev, t_curl = kernel_times(p32, dB, max(3, args.steps // 2))
     # FP64 beside it
     step(p64, Bd, dB64)
@@ -560,7 +562,8 @@ def run_adjoint(args):
     peaks, peak_kind = _measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    achieved = acc_steps * REV_FLOPS_PER_STEP / (t_rev / 1000.0) / 1e12
+    achieved = trials * FLOPS_PER_TRIAL / (t_fwd / 1000.0) / 1e12
+    rev_tflops = acc_steps * REV_FLOPS_PER_STEP / (t_rev / 1000.0) / 1e12
     s32 = float(np.mean(ms32)) / 1000.0
     line = {"metric": ADJ_METRIC, "value": s32, "unit": "s/grad", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * s32, "higher_is_better": False, "scaling": "weak",
@@ -571,16 +574,20 @@ def run_adjoint(args):
             "loss": {"f32": loss32, "f64": loss64},
             "fp64": {"value": float(np.mean(ms64)) / 1000.0, "unit": "s/grad"},
             "kernels_ms": {"forward_taped_trace_f32": t_fwd, "reverse_sweep_f32": t_rev, "curl_transpose": t_curl},
-            "work": {"accepted_steps": acc_steps, "per_half_line": acc_steps / (2 * n)},
+            "work": {"trial_steps": trials, "accepted_steps": acc_steps, "accepted_per_half_line": acc_steps / (2 * n)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": achieved / alu_peak, "traffic": None, "kernel": "reverse sweep (k_reverse<float>)",
+                         "frac": achieved / alu_peak, "traffic": None,
+                         "kernel": "taped lattice tracer k_trace_tape_f32 (trial steps x %d flops)" % FLOPS_PER_TRIAL,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, peak_kind),
-                         "gather_TBs": acc_steps * REV_GATHER_BYTES_PER_STEP / (t_rev / 1000.0) / 1e12,
-                         "scatter_GBs": acc_steps * REV_SCATTER_BYTES_PER_STEP / (t_rev / 1000.0) / 1e9},
+                         "note": "latency-bound: the longest direction of a line is a chain of dependent gathers"},
+            "reverse_sweep": {"ms": t_rev, "passes": "A1 states, A2 Jacobians, B per-line recurrence, C VJP + scatter",
+                              "achieved_TFLOPs": rev_tflops, "frac_of_alu_peak": rev_tflops / alu_peak,
+                              "gather_TBs": acc_steps * REV_GATHER_BYTES_PER_STEP / (t_rev / 1000.0) / 1e12,
+                              "scatter_GBs": acc_steps * REV_SCATTER_BYTES_PER_STEP / (t_rev / 1000.0) / 1e9},
             "error_vs_oracle": errs,
             "e2e": {"value": float(np.mean(e2e)) / 1000.0, "unit": "s/grad", "h2d_bytes_per_step": int(B.nbytes),
                     "d2h_bytes_per_step": int(B.nbytes + 8)},
-            "gpu_launches": 11 * args.steps, "clocks": clk,
+            "gpu_launches": 12 * args.steps, "clocks": clk,
             "cpu_baseline": {"value": ora_s * n / ADJ_SAMPLE, "unit": "s/grad", "cores": oracle.max_threads(),
                              "kind": "oracle",
                              "sample": "%d seeded-random seeds (%d lines with their neighbours), %.1f s, scaled "
