@@ -108,8 +108,8 @@ typedef struct {
                              (1..64; 0 = default 1; batches always take 1). Results do not depend on it. */
     int blocks_per_sm;    /* scheduling: resident 128-thread blocks per SM of the persistent tracer
                              (0 = as many as fit). Results do not depend on it. */
-    int tape;             /* 1: fqsl_qmap_plane (Method I) also records the step tape that fqsl_backward
-                             differentiates (0 = default, no tape). Results do not depend on it. */
+    int tape;             /* 1: fqsl_qmap_plane / fqsl_qmap_volume (Method I) also record the step tape
+                             that fqsl_backward differentiates (0 = default). Results do not depend on it. */
     int tape_chunk;       /* steps per tape chunk, i.e. the checkpoint interval k of the reverse sweep
                              (1..32; 0 = default 16) */
     int reverse_precision; /* precision of fqsl_backward's reverse sweep for this taped map: -1 (default)
@@ -271,8 +271,9 @@ FQSL_API fqsl_status fqsl_qmap_plane_static(fqsl_field field, const double origi
                                             const fqsl_params *params, const fqsl_out *out, void *cuda_stream);
 
 /* Reverse mode (the paper has no derivative; this is the discrete adjoint of
- * the computation it defines). For the plane map that fqsl_qmap_plane last
- * traced on this field with params->tape = 1 (Method I), accumulate
+ * the computation it defines). For the plane or volume map that
+ * fqsl_qmap_plane or fqsl_qmap_volume last traced on this field with
+ * params->tape = 1 (Method I), accumulate
  *   dB += d/dB ( sum_s dQ[s] Q[s] + dTw[s] Tw[s] )
  * where the derivative is that of the traced computation with each line's
  * accepted step sizes, exit faces and exit kinds (exit step onto a face, the
@@ -282,7 +283,7 @@ FQSL_API fqsl_status fqsl_qmap_plane_static(fqsl_field field, const double origi
  * Eq. interp), exit-step length, chord parameter, Bn at the seed and at both
  * ends (Eq. Bn1), the Method I difference stencils' values (Eqs. D+-2, D+-3)
  * and the curl grid (Eq. tw) vary with B.
- *   dQ_dev, dTw_dev  double[nu*nv] per-seed weights in the map's output order
+ *   dQ_dev, dTw_dev  double[seeds] per-seed weights in the map's output order
  *                    (either may be NULL = 0). Seeds whose Q is NaN (status
  *                    MAXSTEPS, NULL_B, OUTSIDE or MIXED) or whose S0 was
  *                    rotated (ROTATED: their Q comes from four extra lines
@@ -299,12 +300,12 @@ FQSL_API fqsl_status fqsl_qmap_plane_static(fqsl_field field, const double origi
  * not, it traces the map again with a larger pool), so it cannot be captured
  * in a CUDA graph. With timing enabled, fqsl_field_times reports ms[0] =
  * reverse sweep, ms[1] = 0, ms[2] = curl transpose. Errors: FQSL_ERR_ARG (no
- * taped map, NULL or misaligned pointers, db_dtype), FQSL_ERR_OOM,
- * FQSL_ERR_CUDA. */
+ * taped map, the field updated since, NULL or misaligned pointers, db_dtype),
+ * FQSL_ERR_OOM, FQSL_ERR_CUDA. */
 FQSL_API fqsl_status fqsl_backward(fqsl_field field, const double *dQ_dev, const double *dTw_dev, void *dB_dev,
                                    fqsl_dtype db_dtype, void *cuda_stream);
 
-/* The step sequence of the field's last taped plane map (the paper has no
+/* The step sequence of the field's last taped map (the paper has no
  * counterpart; for inspection and for replaying a map's exact steps
  * elsewhere). For half-line hl = 2 s + e (seed s, end e = 0 for end 1):
  * nsteps_dev[hl] accepted steps (0 with code -1 for a line with MAXSTEPS,
@@ -312,11 +313,18 @@ FQSL_API fqsl_status fqsl_backward(fqsl_field field, const double *dQ_dev, const
  * nsteps_dev[hl] <= cap (cap = 0: counts only), code_dev[hl] how the direction ended (16 + face: exit step
  * onto that face; 40 + face: the same with the other coordinates clamped into
  * the box; 48 + face: chord onto that face after an exiting step of size
- * hx_dev[hl], which is 0 otherwise). Device arrays of 2 nu nv elements
- * (h_dev: 2 nu nv cap). The pool must have sufficed (run fqsl_backward first
+ * hx_dev[hl], which is 0 otherwise). Device arrays of 2 x seeds elements
+ * (h_dev: 2 x seeds x cap). The pool must have sufficed (run fqsl_backward first
  * if unsure). Errors: FQSL_ERR_ARG, FQSL_ERR_CUDA. */
 FQSL_API fqsl_status fqsl_tape_export(fqsl_field field, int cap, int32_t *nsteps_dev, int32_t *code_dev,
                                       double *hx_dev, double *h_dev, void *cuda_stream);
+
+/* Number of the field's current taped map (1 for its first, incremented by
+ * every taped call; 0 if none), so that a caller holding several taped maps
+ * can check which one fqsl_backward would differentiate. fqsl_backward
+ * refuses (FQSL_ERR_ARG) if fqsl_field_update ran after the taped call.
+ * Errors: FQSL_ERR_ARG. */
+FQSL_API fqsl_status fqsl_tape_id(fqsl_field field, unsigned long long *id);
 
 /* The log-Q / Tw misfit of two maps and its gradient (a loss for
  * fqsl_backward; the paper has no counterpart):

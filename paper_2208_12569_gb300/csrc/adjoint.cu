@@ -861,13 +861,14 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
         if (st & (kBad | FQSL_LINE_ROTATED)) continue;
         const double qb = A.dQ ? A.dQ[idx] : 0.0;
         if (!(qb == qb) || qb == 0.0 || fabs(qb) == INFINITY) continue;
-        const long long i = idx % G.n1, j = idx / G.n1;
+        // lattice index (i, j) within its layer k (each layer is its own S0)
+        const long long i = idx % G.n1, j = (idx / G.n1) % G.n2, k = idx / (G.n1 * G.n2);
         const long long ni[4] = {i + 1, i - 1, i, i}, nj[4] = {j, j, j + 1, j - 1};
         long long nid[4];
         bool has[4];
         for (int q = 0; q < 4; q++) {
             has[q] = ni[q] >= 0 && ni[q] < G.n1 && nj[q] >= 0 && nj[q] < G.n2;
-            nid[q] = has[q] ? ni[q] + G.n1 * nj[q] : 0;
+            nid[q] = has[q] ? ni[q] + G.n1 * (nj[q] + G.n2 * k) : 0;
         }
         const double inv[2] = {1.0 / G.du, 1.0 / G.dv};
         const int fe2[2] = {R.f1[idx], R.f2[idx]};
@@ -976,7 +977,7 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
         } else {
             // the FP64 tracer's seed: (r0 - o)/d as written
             double r0[3];
-            trace::lattice_seed(G, i, j, 0, r0);
+            trace::lattice_seed(G, i, j, k, r0);
             for (int a = 0; a < 3; a++) p0[a] = (T)((r0[a] - f.o[a]) / f.d[a]);
         }
         const Cell<T> c0 = cell_of(f, p0[0], p0[1], p0[2]);

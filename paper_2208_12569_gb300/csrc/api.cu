@@ -81,7 +81,10 @@ struct fqsl_field_s {
         size_t cap = 0;
         void *work = nullptr;  // per-step arrays of the reverse sweep
         size_t work_cap = 0;
+        unsigned long long id = 0;   // taped maps so far on this field (the last one's number)
+        unsigned long long gen = 0;  // the field's record generation when it was taped
     } tp;
+    unsigned long long gen = 0;  // incremented by every fqsl_field_update
     std::mutex mu;
 };
 
@@ -229,6 +232,7 @@ fqsl_status fqsl_field_update(fqsl_field f, const void *B_dev, fqsl_dtype b_dtyp
     if (e == cudaSuccess && (f->grad32 || f->grad64))
         e = launch_gradb_pack(B_dev, b_dtype, f->g, f->grad32, f->grad64, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return cuda_fail(e, "fqsl_field_update: curl_pack launch");
+    f->gen++;
     return FQSL_OK;
 }
 
@@ -537,7 +541,7 @@ bool acc64_of(const fqsl_params &p) { return reverse_precision_of(p) != FQSL_F32
 TapeLayout field_tape_layout(const fqsl_field f, char *base, long long pool)
 {
     const fqsl_params &p = f->tp.p;
-    const long long n = f->tp.lat.n1 * f->tp.lat.n2;
+    const long long n = f->tp.lat.n1 * f->tp.lat.n2 * f->tp.lat.n3;
     const int k = p.tape_chunk > 0 ? p.tape_chunk : kDefaultTapeChunk;
     const size_t nodes = (size_t)f->g.nx * f->g.ny * f->g.nz;
     return tape_layout(base, n, f->tp.lat.allow_rot, p.precision != FQSL_F64, pool, k, nodes, acc64_of(p));
@@ -586,6 +590,8 @@ fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params
     TapeLayout tl{};
     if (tape) {
         f->tp.valid = false;
+        f->tp.id++;
+        f->tp.gen = f->gen;
         f->tp.lat = lat;
         f->tp.p = *p;
         f->tp.face_plane = face_plane;
@@ -782,8 +788,8 @@ fqsl_status fqsl_qmap_volume(fqsl_field f, const double origin[3], const double 
     lat.dv = step[1];
     lat.drot = fmin(step[0], step[1]);
     lat.normal_axis = 2;
-    if (p->tape) return fail(FQSL_ERR_UNSUPPORTED, "%s: the step tape is recorded for plane maps only", who);
-    return run_qmap(f, lat, p, out, (cudaStream_t)cuda_stream, false, who);
+    if (p->tape && p->method != 1) return fail(FQSL_ERR_UNSUPPORTED, "%s: the step tape needs Method I", who);
+    return run_qmap(f, lat, p, out, (cudaStream_t)cuda_stream, false, who, p->tape != 0);
 }
 
 fqsl_status fqsl_twist(fqsl_field f, const double *seeds_dev, long long n, const fqsl_params *p, const fqsl_out *out,
@@ -1256,7 +1262,9 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
         return fail(FQSL_ERR_ARG, "%s: dQ_dev and dTw_dev must be 8-byte aligned", who);
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     std::lock_guard<std::mutex> lock(f->mu);
-    if (!f->tp.valid) return fail(FQSL_ERR_ARG, "%s: no taped plane map on this field (params.tape = 1)", who);
+    if (!f->tp.valid) return fail(FQSL_ERR_ARG, "%s: no taped map on this field (params.tape = 1)", who);
+    if (f->tp.gen != f->gen)
+        return fail(FQSL_ERR_ARG, "%s: the field was updated after its taped map (trace it again)", who);
     const fqsl_params p = f->tp.p;
     // the pool of the taped call must have held every chunk; if not, trace the
     // same map again with a larger pool (the map is deterministic)
@@ -1276,7 +1284,7 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
     }
     TapeLayout tl = field_tape_layout(f, (char *)f->tp.buf, f->tp.pool);
     const Lattice &lat = f->tp.lat;
-    const long long n = lat.n1 * lat.n2;
+    const long long n = lat.n1 * lat.n2 * lat.n3;
     const size_t nodes = (size_t)f->g.nx * f->g.ny * f->g.nz;
     const int rp = reverse_precision_of(p);
     const bool acc64 = acc64_of(p);
@@ -1355,9 +1363,9 @@ extern "C" fqsl_status fqsl_tape_export(fqsl_field f, int cap, int32_t *nsteps_d
     if (!nsteps_dev || !code_dev || !hx_dev || (cap > 0 && !h_dev))
         return fail(FQSL_ERR_ARG, "%s: NULL output", who);
     std::lock_guard<std::mutex> lock(f->mu);
-    if (!f->tp.valid) return fail(FQSL_ERR_ARG, "%s: no taped plane map on this field (params.tape = 1)", who);
+    if (!f->tp.valid) return fail(FQSL_ERR_ARG, "%s: no taped map on this field (params.tape = 1)", who);
     TapeLayout tl = field_tape_layout(f, (char *)f->tp.buf, f->tp.pool);
-    const long long n = f->tp.lat.n1 * f->tp.lat.n2;
+    const long long n = f->tp.lat.n1 * f->tp.lat.n2 * f->tp.lat.n3;
     cudaError_t e = launch_tape_export(tl.tape, f->tp.p.precision == FQSL_F64, tl.s.rec.st, 2 * n, cap, nsteps_dev,
                                        code_dev, hx_dev, h_dev, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
@@ -1403,3 +1411,12 @@ extern "C" fqsl_status fqsl_field_check(fqsl_field f, void *cuda_stream)
     return FQSL_OK;
 }
 
+
+extern "C" fqsl_status fqsl_tape_id(fqsl_field f, unsigned long long *id)
+{
+    g_err.clear();
+    if (!f || !id) return fail(FQSL_ERR_ARG, "fqsl_tape_id: NULL argument");
+    std::lock_guard<std::mutex> lock(f->mu);
+    *id = f->tp.valid ? f->tp.id : 0;
+    return FQSL_OK;
+}

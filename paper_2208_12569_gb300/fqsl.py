@@ -22,7 +22,8 @@ LINE_BAD = LINE_MAXSTEPS | LINE_NULL_B | LINE_OUTSIDE
 EXPORTS = ("fqsl_params_default", "fqsl_version", "fqsl_last_error", "fqsl_field_create", "fqsl_field_destroy",
            "fqsl_qmap_plane", "fqsl_qmap_volume", "fqsl_twist", "fqsl_field_check", "fqsl_field_set_timing",
            "fqsl_field_times", "fqsl_field_update", "fqsl_qmap_plane_static", "fqsl_batch_create", "fqsl_batch_run",
-           "fqsl_batch_destroy", "fqsl_backward", "fqsl_loss_logq_tw", "fqsl_tape_export")
+           "fqsl_batch_destroy", "fqsl_backward", "fqsl_loss_logq_tw", "fqsl_tape_export",
+           "fqsl_tape_id")
 STATIC_MAX_SEEDS = 65536
 
 
@@ -78,6 +79,7 @@ def load(path: str = LIB_PATH):
     lib.fqsl_field_times.argtypes = [P, C.POINTER(C.c_float * 3)]
     lib.fqsl_backward.argtypes = [P, P, P, P, C.c_int, P]
     lib.fqsl_tape_export.argtypes = [P, C.c_int, P, P, P, P, P]
+    lib.fqsl_tape_id.argtypes = [P, C.POINTER(C.c_ulonglong)]
     lib.fqsl_loss_logq_tw.argtypes = [C.c_longlong, P, P, P, P, P, C.c_double, P, P, P, P, P]
     for name in EXPORTS:
         if name not in ("fqsl_params_default", "fqsl_version", "fqsl_last_error"):
@@ -325,6 +327,13 @@ def backward(field: Field, dQ=None, dTw=None, dB=None, dtype=None, stream=None):
     return dB
 
 
+def tape_id(field: Field) -> int:
+    """Number of the field's current taped map (0 if none)."""
+    v = C.c_ulonglong()
+    _check(_lib.fqsl_tape_id(field.handle, C.byref(v)))
+    return int(v.value)
+
+
 def tape_export(field: Field, n_seeds: int, cap: int = 4096, stream=None):
     """The step sequence of the field's last taped plane map (fqsl_tape_export):
     dict of CUDA tensors nsteps (2n), code (2n), hx (2n), h (2n, cap); half-line
@@ -373,10 +382,14 @@ class QTwPlane(torch.autograd.Function):
         field.update(B.detach())
         out = qmap_plane(field, origin, u, v, nu, nv, q)
         ctx.field = field
+        ctx.tape = tape_id(field)
         ctx.b_dtype = B.dtype
         return out["Q"], out["Tw"]
 
     @staticmethod
     def backward(ctx, gQ, gTw):
+        if tape_id(ctx.field) != ctx.tape:
+            raise RuntimeError("QTwPlane.backward: the field traced another taped map after this one; "
+                               "use one Field per differentiable map")
         dB = backward(ctx.field, gQ, gTw, dtype=ctx.b_dtype)
         return dB, None, None, None, None, None, None, None

@@ -288,7 +288,7 @@ def test_backward_argument_errors(fq, small):
         fq.qmap_plane(field, *PLANE16, fq.params(tape=1, method=2))
     assert ei.value.status == 5
     with pytest.raises(fq.FqslError) as ei:
-        fq.qmap_volume(field, (0.0, 0.0, 0.0), (2.0, 2.0, 2.0), 4, 4, 4, fq.params(tape=1))
+        fq.qmap_volume(field, (0.0, 0.0, 0.0), (2.0, 2.0, 2.0), 4, 4, 4, fq.params(tape=1, method=2))
     assert ei.value.status == 5
     with pytest.raises(fq.FqslError) as ei:
         fq.qmap_plane(field, *PLANE16, fq.params(tape=1, tape_chunk=33))
@@ -321,3 +321,45 @@ def test_taped_map_equals_plain_map(fq, small, precision, plane):
         assert np.array_equal(ok, np.isfinite(taped["Q"]))
         np.testing.assert_allclose(taped["Q"][ok], plain["Q"][ok], rtol=1e-5)
         np.testing.assert_allclose(taped["Tw"], plain["Tw"], rtol=1e-5, atol=1e-7)
+
+
+def test_volume_gradient_matches_oracle(fq, small):
+    # a volume map: each z-layer is its own S0, so its adjoint is the sum of
+    # the layers' plane adjoints
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    step = (23.0 / 6, 23.0 / 6, 4.0)
+    nx, ny, nz = 6, 6, 3
+    m = nx * ny * nz
+    wq, wt = _weights(21, m)
+    out = fq.qmap_volume(field, (0.0, 0.0, 0.0), step, nx, ny, nz, fq.params(precision="f64", tape=1))
+    st = out["status"].cpu().numpy()
+    dB = fq.backward(field, torch.from_numpy(wq).cuda(), torch.from_numpy(wt).cuda(), dtype=torch.float64)
+    field.check()
+    g = dB.cpu().numpy()
+    ref = np.zeros_like(B)
+    per = nx * ny
+    for k in range(nz):
+        plane = ((0.0, 0.0, (k + 0.5) * step[2]), (step[0], 0.0, 0.0), (0.0, step[1], 0.0), nx, ny)
+        r, log = adj.vjp(B, grid, *plane, wq[k * per:(k + 1) * per], wt[k * per:(k + 1) * per], oracle.params())
+        line_bits = oracle.BAD | oracle.ROTATED | oracle.CHORD | oracle.STALL
+        assert np.array_equal(log["status"] & line_bits, st[k * per:(k + 1) * per] & line_bits)
+        ref += r
+    assert np.linalg.norm(ref) > 0
+    assert _rel(g, ref) < 1e-10
+
+
+def test_backward_refuses_a_stale_tape(fq, small):
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    assert fq.tape_id(field) == 0
+    fq.qmap_plane(field, *PLANE16, fq.params(tape=1))
+    assert fq.tape_id(field) == 1
+    fq.qmap_plane(field, *PLANE16, fq.params())  # an untaped map leaves the tape
+    assert fq.tape_id(field) == 1
+    fq.qmap_plane(field, *PLANE16, fq.params(tape=1))
+    assert fq.tape_id(field) == 2
+    field.update(torch.from_numpy(B).cuda())
+    with pytest.raises(fq.FqslError) as ei:
+        fq.backward(field, None, None)
+    assert ei.value.status == 1 and "updated" in str(ei.value)
