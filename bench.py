@@ -413,11 +413,12 @@ def _adj_plane():
     return (0.0, 0.0, 0.0), u, v, ADJ_SEEDS, ADJ_SEEDS
 
 
-def run_adjoint(args):
+def run_adjoint(args, emit=True):
     """Differentiation workload: d(loss)/dB of the log-Q/Tw misfit on the z=0
     map of a 128x128x64 monopole cube with a twist tube (256x256 seeds). A
     step = repack B with its curl, the taped FP32 map, the loss and its
-    gradient, and the reverse sweep into dB (s per gradient)."""
+    gradient, and the reverse sweep into dB (s per gradient). Prints the JSON
+    line (emit) and returns it."""
     import torch
 
     import __graft_entry__
@@ -592,9 +593,11 @@ def run_adjoint(args):
                              "kind": "oracle",
                              "sample": "%d seeded-random seeds (%d lines with their neighbours), %.1f s, scaled "
                                        "by %d" % (ADJ_SAMPLE, len(info["lines"]), ora_s, n // ADJ_SAMPLE)}}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
     for fl in (field, field64, fieldx, ftgt):
         fl.close()
+    return line
 
 
 def run_reference_adjoint(args):
@@ -639,6 +642,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fqsl", choices=["fqsl", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="plane workload: skip the adjoint s/grad measurement embedded in its line")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--only-f32", action="store_true",
                     help="time only the FP32 map (no FP64, e2e or CPU legs); used for ncu captures")
@@ -826,6 +831,13 @@ def main():
             "e2e": {"value": e2e_value, "unit": "Q+Tw values/s", "ms_per_step": float(np.mean(e2e_ms)),
                     "h2d_bytes_per_step": int(B.nbytes), "d2h_bytes_per_step": int(2 * n * 8)},
             "gpu_launches": 3 * args.steps, "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_adjoint:
+        # the metric's second part: seconds per gradient of the differentiation workload
+        a = run_adjoint(argparse.Namespace(steps=args.steps, warmup=args.warmup, fp64_steps=args.fp64_steps),
+                        emit=False)
+        line["adjoint"] = {k: a[k] for k in ("metric", "value", "unit", "ms_per_step", "higher_is_better", "config",
+                                             "fp64", "kernels_ms", "error_vs_oracle", "e2e", "cpu_baseline",
+                                             "roofline", "reverse_sweep", "loss")}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, sample, ref = cpu_baseline(B, grid, u, v)
         line["cpu_baseline"] = cb

@@ -487,6 +487,11 @@ void cross(const double *a, const double *b, double *c)
 void index_lattice(const fqsl_field f, Lattice &lat)
 {
     for (int a = 0; a < 3; a++) {
+        lat.sdu[a] = f->g.d[a] / lat.du;
+        lat.sdv[a] = f->g.d[a] / lat.dv;
+        lat.sdr[a] = f->g.d[a] / lat.drot;
+    }
+    for (int a = 0; a < 3; a++) {
         lat.xo[a] = (lat.o[a] - f->g.o[a]) / f->g.d[a];
         lat.xa1[a] = lat.a1[a] / f->g.d[a];
         lat.xa2[a] = lat.a2[a] / f->g.d[a];

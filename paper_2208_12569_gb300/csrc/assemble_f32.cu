@@ -45,27 +45,29 @@ __device__ __forceinline__ void assemble_one_f32(const AssembleArgs &A, long lon
         const int f1 = R.f1[idx], f2 = R.f2[idx];
         double Q = NAN;
         if (A.want_q && !bad) {
-            const long long i = idx % G.n1, j = (idx / G.n1) % G.n2, k = idx / (G.n1 * G.n2);
+            // 32-bit index arithmetic (a lattice holds fewer than 2^31 seeds)
+            const unsigned u = (unsigned)idx, n1 = (unsigned)G.n1, n12 = (unsigned)(G.n1 * G.n2);
+            const unsigned k = u / n12, rem = u - k * n12, j = rem / n1, i = rem - j * n1;
             const int slot = A.rot_slot ? A.rot_slot[idx] : 0;
             const LineRecs *NR = slot > 0 ? &A.ext : &A.rec;
             long long nid[4];
             bool has[4];
-            double du = G.du, dv = G.dv;
+            // spacing over lattice step per axis (host-computed: no FP64 division here)
+            const double *sc[2] = {G.sdu, G.sdv};
             if (slot > 0) {
                 for (int q = 0; q < 4; q++) {
                     nid[q] = (long long)(slot - 1) * 4 + q;
                     has[q] = true;
                 }
-                du = dv = G.drot;
+                sc[0] = sc[1] = G.sdr;
             } else {
-                const long long ni[4] = {i + 1, i - 1, i, i}, nj[4] = {j, j, j + 1, j - 1};
+                const long long ii = i, jj = j, kk = k;
+                const long long ni[4] = {ii + 1, ii - 1, ii, ii}, nj[4] = {jj, jj, jj + 1, jj - 1};
                 for (int q = 0; q < 4; q++) {
                     has[q] = ni[q] >= 0 && ni[q] < G.n1 && nj[q] >= 0 && nj[q] < G.n2;
-                    nid[q] = ni[q] + G.n1 * (nj[q] + G.n2 * k);
+                    nid[q] = ni[q] + G.n1 * (nj[q] + G.n2 * kk);
                 }
             }
-            // reciprocal lattice steps: one division per axis instead of one per entry
-            const double inv[2] = {1.0 / du, 1.0 / dv};
             double Jm[2][2][2];
             bool mixed = false;
             for (int e = 0; e < 2 && !mixed; e++) {
@@ -75,7 +77,7 @@ __device__ __forceinline__ void assemble_one_f32(const AssembleArgs &A, long lon
                 const float *c0 = e == 0 ? x1 : x2;
                 for (int s = 0; s < 2 && !mixed; s++) {
                     const int P = 2 * s, M = 2 * s + 1;
-                    const double rdel = inv[s];
+                    const double *scs = sc[s];
                     const float *cp = nullptr, *cm = nullptr;
                     if (has[P] && !(NR->st[nid[P]] & kBad) && (e == 0 ? NR->f1 : NR->f2)[nid[P]] == fe)
                         cp = (e == 0 ? NR->xi1 : NR->xi2) + 3 * nid[P];
@@ -83,9 +85,9 @@ __device__ __forceinline__ void assemble_one_f32(const AssembleArgs &A, long lon
                         cm = (e == 0 ? NR->xi1 : NR->xi2) + 3 * nid[M];
                     for (int r = 0; r < 2; r++) {
                         const int a = ra[r];
-                        if (cp && cm) Jm[e][r][s] = (double)(cp[a] - cm[a]) * (0.5 * f.d[a] * rdel);
-                        else if (cp) Jm[e][r][s] = (double)(cp[a] - c0[a]) * (f.d[a] * rdel);
-                        else if (cm) Jm[e][r][s] = (double)(c0[a] - cm[a]) * (f.d[a] * rdel);
+                        if (cp && cm) Jm[e][r][s] = (double)(cp[a] - cm[a]) * (0.5 * scs[a]);
+                        else if (cp) Jm[e][r][s] = (double)(cp[a] - c0[a]) * scs[a];
+                        else if (cm) Jm[e][r][s] = (double)(c0[a] - cm[a]) * scs[a];
                         else mixed = true;
                     }
                 }

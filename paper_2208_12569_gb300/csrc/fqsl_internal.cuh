@@ -64,6 +64,9 @@ struct Lattice {
     long long n1, n2, n3;
     long long tiles_u, tiles_v;
     double du, dv, drot;
+    // spacing over lattice step, per axis: d_a/du, d_a/dv, d_a/drot (the FP32
+    // assembly scales index-space footpoint differences by these)
+    double sdu[3], sdv[3], sdr[3];
     int normal_axis;   // axis of n0 if it is a coordinate axis, else -1
     int allow_rot;     // Method I and some layer may be interior
 };

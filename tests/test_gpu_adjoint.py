@@ -363,3 +363,31 @@ def test_backward_refuses_a_stale_tape(fq, small):
     with pytest.raises(fq.FqslError) as ei:
         fq.backward(field, None, None)
     assert ei.value.status == 1 and "updated" in str(ei.value)
+
+
+def test_full_size_workload_sampled(fq):
+    # the differentiation workload at full size (128x128x64 cube, 256^2 seeds,
+    # checkpoints every 16 steps, the launch the benchmark times): weights on a
+    # seeded sample of 32 seeds, against the oracle traced for just those lines
+    # and their neighbours
+    B, _, grid = synth.adjoint_cubes(seed=2208, n=(128, 128, 64))
+    plane = ((0.0, 0.0, 0.0), (127.0 / 256, 0.0, 0.0), (0.0, 127.0 / 256, 0.0), 256, 256)
+    n = 256 * 256
+    rng = np.random.default_rng(2208)
+    sample = np.sort(rng.choice(n, 32, replace=False))
+    wq, wt = rng.standard_normal(32), rng.standard_normal(32)
+    WQ, WT = np.zeros(n), np.zeros(n)
+    WQ[sample], WT[sample] = wq, wt
+    ref, info = adj.vjp_sample(B.astype(np.float64), grid, *plane, sample, wq, wt, oracle.params())
+    assert np.linalg.norm(ref) > 0
+    field = _field(fq, B, grid)
+    g64, _ = _gpu_vjp(fq, field, plane, WQ, WT, precision="f64", tape_chunk=16)
+    assert _rel(g64, ref) < 1e-10
+    g32r, _ = _gpu_vjp(fq, field, plane, WQ, WT, dtype=torch.float32, precision="f64", reverse_precision="f32",
+                       tape_chunk=16)
+    assert _rel(g32r, ref) < 2e-3
+    g32, _ = _gpu_vjp(fq, field, plane, WQ, WT, dtype=torch.float32, precision="f32", tape_chunk=16)
+    assert _rel(g32, ref) < 0.25
+    Bd = B.astype(np.float64)
+    for g in (g64, g32):
+        assert abs(np.sum(g * Bd)) < 1e-4 * np.linalg.norm(g) * np.linalg.norm(Bd)
