@@ -131,13 +131,30 @@ def _dist():
     return ws, rank, local
 
 
-def c2_inputs(rank: int = 0):
+def c2_inputs(rank: int = 0, cube=CUBE):
+    """Rank r maps its own cube: the same shape, sources seeded with 2208 + r."""
     import synth
 
-    B, grid, _ = synth.c2_monopole(seed=SEED + rank, n=CUBE)
-    u = (float(CUBE[0] - 1) / NU, 0.0, 0.0)
-    v = (0.0, float(CUBE[1] - 1) / NV, 0.0)
+    B, grid, _ = synth.c2_monopole(seed=SEED + rank, n=cube)
+    u = (float(cube[0] - 1) / NU, 0.0, 0.0)
+    v = (0.0, float(cube[1] - 1) / NV, 0.0)
     return B, grid, u, v
+
+
+def job_rate(ms_local: float, units_per_rank: int, dist=None, device="cpu"):
+    """Whole-job throughput of a weak-scaling step: every rank processed
+    units_per_rank units; the job's step time is the slowest rank's. Returns
+    (max step ms over ranks, units of all ranks per second)."""
+    import torch
+
+    ws = 1
+    ms = float(ms_local)
+    if dist is not None:
+        ws = dist.get_world_size()
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units_per_rank * ws / (ms / 1000.0)
 
 
 def cpu_baseline(B, grid, u, v, target_s=12.0, seed=5):
@@ -763,12 +780,7 @@ def main():
     ms64, kern64 = timed(p64, args.fp64_steps)
     res64 = {k: t.cpu().numpy() for k, t in out.items() if t is not None}
 
-    ms_step = float(np.mean(ms32))
-    if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = n * ws / (ms_step / 1000.0)
+    ms_step, value = job_rate(float(np.mean(ms32)), n, dist, dev)
     value64 = n / (float(np.mean(ms64)) / 1000.0)
 
     # end to end through the C ABI from pinned host memory
