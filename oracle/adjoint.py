@@ -38,10 +38,12 @@ _B4 = [25 / 216, 0.0, 1408 / 2565, 2197 / 4104, -1 / 5, 0.0]
 START, STEP, EXIT, EXIT_CLAMPED, CHORD = 99, 0, 16, 40, 48
 
 
-def lattice_log(B, grid, origin, u, v, nu, nv, p=None, cap=8192, J=None, which=None):
+def lattice_log(B, grid, origin, u, v, nu, nv, p=None, cap=8192, J=None, which=None, extra=True):
     """Trace every line of the plane lattice (or only the lattice indices in
     ``which``, in that order) once with the C oracle; return their step
-    records and outcomes (numpy arrays, one row per traced line)."""
+    records and outcomes (numpy arrays, one row per traced line). With extra,
+    the four extra lines of each rotated-S0 seed are recorded too (x* arrays,
+    4 per row)."""
     p = p or params()
     B = _f64(B)
     J = _f64(curl(B, grid) if J is None else J)
@@ -51,6 +53,10 @@ def lattice_log(B, grid, origin, u, v, nu, nv, p=None, cap=8192, J=None, which=N
     out = dict(h=np.zeros((m, cap)), code=np.zeros((m, cap), np.int32), n=np.zeros(m, np.int32),
                s0=np.zeros(m), tol=np.zeros(m), bn0=np.zeros(m), ends=np.zeros((m, 2, 11)),
                faces=np.zeros((m, 2), np.int32), status=np.zeros(m, np.int32))
+    if extra:
+        out.update(xh=np.zeros((m, 4, cap)), xcode=np.zeros((m, 4, cap), np.int32), xn=np.zeros((m, 4), np.int32),
+                   xs0=np.zeros((m, 4)), xfaces=np.zeros((m, 4, 2), np.int32), xstatus=np.zeros((m, 4), np.int32))
+    X = (lambda k: _p(out[k]) if extra else None)  # noqa: E731
     lo = np.array(origin, float)
     a1, a2 = np.array(u, float), np.array(v, float)
     ln = np.array([nu, nv], np.int64)
@@ -59,10 +65,11 @@ def lattice_log(B, grid, origin, u, v, nu, nv, p=None, cap=8192, J=None, which=N
     rc = L.oracle_lattice_log(_p(B), _p(J), _p(n), _p(o), _p(d), _p(lo), _p(a1), _p(a2), _p(ln), C.byref(p),
                               C.c_int(cap), _p(out["h"]), _p(out["code"]), _p(out["n"]), _p(out["s0"]),
                               _p(out["tol"]), _p(out["bn0"]), _p(out["ends"]), _p(out["faces"]),
-                              _p(out["status"]), _p(wh), C.c_longlong(0 if wh is None else len(wh)))
+                              _p(out["status"]), _p(wh), C.c_longlong(0 if wh is None else len(wh)),
+                              X("xh"), X("xcode"), X("xn"), X("xs0"), X("xfaces"), X("xstatus"))
     if rc:
         raise ValueError("oracle_lattice_log: error %d" % rc)
-    if np.any(out["n"] < 0):
+    if np.any(out["n"] < 0) or (extra and np.any(out["xn"] < 0)):
         raise ValueError("step record overflow: raise cap")
     return out
 
@@ -229,34 +236,27 @@ def replay(fld, xi0, s0, log):
     return xi.reshape(m, 2, 3), tw.reshape(m, 2)
 
 
-def stencils(faces, status, nu, nv, du, dv, targets=None, row=None):
+def stencils(faces, status, centres, neighbours, steps):
     """Method I difference coefficients (reading R8) chosen from the traced
-    faces: a list of (target position, end, lattice axis, row, coefficient)
-    with J_e[r][c](target) = sum coefficient * face coordinate r of that row's
-    end e; and the targets left MIXED (no usable neighbour on some axis).
-    Rows are the traced lines (row[lattice index]; all, in order, by
-    default); targets the seeds whose Q is formed (default all)."""
-    m = nu * nv
-    targets = np.arange(m) if targets is None else np.asarray(targets)
-    row = {k: k for k in range(m)} if row is None else row
+    faces: for target t with centre row centres[t], neighbour rows
+    neighbours[t] = (+u, -u, +v, -v) (None off the lattice) and lattice steps
+    steps[t] = (du, dv), a list of (target, end, lattice axis, row,
+    coefficient) with J_e[r][c](target) = sum coefficient * face coordinate r
+    of that row's end e; and the targets left MIXED."""
     ok = (status & BAD) == 0
     entries = []
-    mixed = np.zeros(len(targets), bool)
-    for t, s in enumerate(targets):
-        s = int(s)
-        rs = row[s]
+    mixed = np.zeros(len(centres), bool)
+    for t, rs in enumerate(centres):
         if not ok[rs]:
             continue
-        i, j = s % nu, s // nu
         for e in range(2):
             fe = faces[rs, e]
-            for c, (di, dj, dl) in enumerate(((1, 0, du), (0, 1, dv))):
-                def usable(ii, jj):
-                    if not (0 <= ii < nu and 0 <= jj < nv):
-                        return None
-                    k = row.get(ii + nu * jj)
+            for c in range(2):
+                dl = steps[t][c]
+
+                def usable(k):
                     return k if k is not None and ok[k] and faces[k, e] == fe else None
-                kp, km = usable(i + di, j + dj), usable(i - di, j - dj)
+                kp, km = usable(neighbours[t][2 * c]), usable(neighbours[t][2 * c + 1])
                 if kp is not None and km is not None:
                     entries += [(t, e, c, kp, 0.5 / dl), (t, e, c, km, -0.5 / dl)]
                 elif kp is not None:
@@ -292,12 +292,23 @@ def neighbourhood(seeds, nu, nv):
     return np.array(sorted(out), dtype=np.int64)
 
 
+def perp_frame_t(bh, m):
+    """Rotated S0 frame (reading R9): u = unit(bhat x e_m), v = bhat x u, with
+    the axis m (smallest |bhat_m|) given (chosen without a derivative)."""
+    e = torch.nn.functional.one_hot(torch.as_tensor(m), 3).to(bh.dtype)
+    t = torch.cross(bh, e, dim=-1)
+    uu = t / torch.sqrt((t * t).sum(-1, keepdim=True))
+    return uu, torch.cross(bh, uu, dim=-1)
+
+
 def qmap_t(Bt, grid, origin, u, v, nu, nv, log, lines=None, targets=None):
     """Q and Tw (differentiable in the tensor Bt) from the frozen step
     sequence in log. ``lines``: the lattice indices of log's rows (default:
     every seed, in order); ``targets``: the seeds whose Q and Tw are formed
     (default: every seed), each with its lattice neighbours among the lines.
-    Returns (Q, Tw, usable mask, end positions of the rows)."""
+    A rotated-S0 target's Q uses its four extra lines (recorded in log), whose
+    seeds follow the frame of B at the seed. Returns (Q, Tw, usable mask, end
+    positions of the lattice rows)."""
     n = grid.n
     Jt = curl_t(Bt, grid.spacing)
     fld = _Field(Bt, Jt, n, grid.spacing)
@@ -307,22 +318,73 @@ def qmap_t(Bt, grid, origin, u, v, nu, nv, log, lines=None, targets=None):
     row = {int(l): k for k, l in enumerate(lines)}
     tr = np.array([row[int(t)] for t in targets], dtype=np.int64)
     mr = len(lines)
-    xi_all = seeds_index(grid, origin, u, v, nu, nv)
-    xi0 = torch.from_numpy(xi_all[lines])
-    s0 = torch.from_numpy(log["s0"])
-    xi, tw = replay(fld, xi0, s0, log)
     faces, status = log["faces"], log["status"]
     good = (status & BAD) == 0
-    o = torch.tensor(grid.origin, dtype=torch.float64)
-    phys = o + fld.d * xi  # (rows, 2, 3)
+    xi_all = seeds_index(grid, origin, u, v, nu, nv)
+    d = np.asarray(grid.spacing, float)
+    o_np = np.asarray(grid.origin, float)
+    n0 = np.cross(np.asarray(u, float), np.asarray(v, float))
+    n0 = n0 / np.linalg.norm(n0)
+    du, dv = float(np.linalg.norm(u)), float(np.linalg.norm(v))
+    drot = min(du, dv)
+    xi0 = torch.from_numpy(xi_all[lines])
+    s0 = torch.from_numpy(log["s0"])
+    B0t, _ = fld.interp(torch.from_numpy(xi_all[targets]))
+    nB0 = torch.sqrt((B0t * B0t).sum(-1))
+    # rotated targets: their extra lines become rows mr, mr + 1, ...
+    rot = [t for t in range(len(targets)) if good[tr[t]] and (status[tr[t]] & ROTATED) and "xn" in log]
+    xrows = {}
+    xi_x, s0_x, xh, xc, xn, xf, xs = [], [], [], [], [], [], []
+    for t in rot:
+        rs = tr[t]
+        bh = B0t[t] / nB0[t]
+        with torch.no_grad():
+            mm = int(torch.argmin(torch.abs(bh)))  # lowest index on ties
+        uu, vv = perp_frame_t(bh, mm)
+        r0 = torch.from_numpy(o_np + d * xi_all[targets[t]])
+        for q in range(4):
+            dirq = uu if q < 2 else vv
+            sg = -1.0 if q & 1 else 1.0
+            xi_x.append(((r0 + sg * drot * dirq) - torch.from_numpy(o_np)) / torch.from_numpy(d))
+            s0_x.append(log["xs0"][rs, q])
+            xh.append(log["xh"][rs, q])
+            xc.append(log["xcode"][rs, q])
+            xn.append(log["xn"][rs, q])
+            xf.append(log["xfaces"][rs, q])
+            xs.append(log["xstatus"][rs, q])
+            xrows[(t, q)] = mr + len(xi_x) - 1
+    if xi_x:
+        rlog = dict(h=np.concatenate([log["h"], np.stack(xh)]), code=np.concatenate([log["code"], np.stack(xc)]),
+                    n=np.concatenate([log["n"], np.array(xn, np.int32)]))
+        xi0 = torch.cat([xi0, torch.stack(xi_x)])
+        s0 = torch.cat([s0, torch.tensor(s0_x, dtype=torch.float64)])
+        faces = np.concatenate([faces, np.stack(xf)])
+        status = np.concatenate([status, np.array(xs, np.int32)])
+    else:
+        rlog = log
+    xi, tw = replay(fld, xi0, s0, rlog)
+    nrows = xi.shape[0]
+    phys = torch.from_numpy(o_np) + fld.d * xi  # (rows, 2, 3)
     cols = []
     for e in range(2):
         for r in range(2):
-            idx = torch.from_numpy(np.array([_FACE_AXES[max(faces[k, e], 0) // 2][r] for k in range(mr)]))
+            idx = torch.from_numpy(np.array([_FACE_AXES[max(faces[k, e], 0) // 2][r] for k in range(nrows)]))
             cols.append(phys[:, e, :].gather(1, idx[:, None])[:, 0])
-    fc = torch.stack(cols, dim=1).reshape(mr, 2, 2)  # row, end, face coordinate
-    du, dv = float(np.linalg.norm(u)), float(np.linalg.norm(v))
-    entries, mixed = stencils(faces, status, nu, nv, du, dv, targets, row)
+    fc = torch.stack(cols, dim=1).reshape(nrows, 2, 2)  # row, end, face coordinate
+    neigh, steps = [], []
+    for t, sd in enumerate(targets):
+        if (t, 0) in xrows:
+            neigh.append(tuple(xrows[(t, q)] for q in range(4)))
+            steps.append((drot, drot))
+        else:
+            i, j = int(sd) % nu, int(sd) // nu
+            nb = []
+            for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                ii, jj = i + di, j + dj
+                nb.append(row.get(ii + nu * jj) if 0 <= ii < nu and 0 <= jj < nv else None)
+            neigh.append(tuple(nb))
+            steps.append((du, dv))
+    entries, mixed = stencils(faces, status, tr, neigh, steps)
     nt = len(targets)
     Jm = torch.zeros((nt, 2, 2, 2), dtype=torch.float64)  # target, end, face row r, lattice axis c
     if entries:
@@ -342,13 +404,13 @@ def qmap_t(Bt, grid, origin, u, v, nu, nv, log, lines=None, targets=None):
     fax = torch.from_numpy(np.maximum(faces[tr], 0) // 2)
     bn1 = Bend[:, 0].gather(1, fax[:, 0:1])[:, 0]
     bn2 = Bend[:, 1].gather(1, fax[:, 1:2])[:, 0]
-    n0 = np.cross(np.asarray(u, float), np.asarray(v, float))
-    n0 = torch.from_numpy(n0 / np.linalg.norm(n0))
-    B0, _ = fld.interp(torch.from_numpy(xi_all[targets]))
-    bn0 = (B0 * n0).sum(-1)
+    rotm = torch.from_numpy((status[tr] & ROTATED) != 0)
+    bn0 = torch.where(rotm, nB0, (B0t * torch.from_numpy(n0)).sum(-1))
     Q = norm2 * torch.abs(bn1 * bn2) / (bn0 * bn0)
-    usable = torch.from_numpy(good[tr] & ~mixed & ((status[tr] & ROTATED) == 0))
-    return Q, tw[trt].sum(1), usable, xi
+    usable = torch.from_numpy(good[tr] & ~mixed)
+    if "xn" not in log:
+        usable = usable & ~rotm
+    return Q, tw[trt].sum(1), usable, xi[:mr]
 
 
 def log_q_tw_loss(Q, Tw, Qt, Twt, usable, wtw=0.1):

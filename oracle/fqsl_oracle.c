@@ -900,12 +900,16 @@ int oracle_max_threads(void)
  * steps (OLog codes; at most cap entries per line, logn[s] = -1 on overflow),
  * orientation sign s0, tolerance, Bn0, end states (s x 2 x 11), faces and
  * status: every seed (which = NULL; output s = lattice index), or the nwhich
- * lattice indices which[] (output s = position in which). Used by the adjoint
- * tests to replay the frozen step sequence. */
+ * lattice indices which[] (output s = position in which). For a seed whose S0
+ * is rotated, the four extra lines (+u, -u, +v, -v of the rotated frame) are
+ * traced as the Q map traces them and, if xlogh is not NULL, recorded in the
+ * x* arrays (4 per seed: records of cap entries, counts, s0, faces (2),
+ * status). Used by the adjoint tests to replay the frozen step sequence. */
 int oracle_lattice_log(const double *B, const double *J, const long long n[3], const double o[3], const double d[3],
                        const double lo[3], const double a1[3], const double a2[3], const long long ln[2],
                        const OParams *p, int cap, double *logh, int *logc, int *logn, double *s0o, double *tolo,
-                       double *bn0o, double *ends, int *faces, int *st, const long long *which, long long nwhich)
+                       double *bn0o, double *ends, int *faces, int *st, const long long *which, long long nwhich,
+                       double *xlogh, int *xlogc, int *xlogn, double *xs0, int *xfaces, int *xst)
 {
     OField f;
     if (o_make_field(&f, B, J, NULL, n, o, d)) return 1;
@@ -942,6 +946,33 @@ int oracle_lattice_log(const double *B, const double *J, const long long n[3], c
             if (S.rotated) c.status |= ST_ROTATED;
         }
         logn[s] = g.overflow ? -1 : g.n;
+        if (xlogh) {
+            for (int q = 0; q < 4; q++) {
+                xlogn[4 * s + q] = 0;
+                xs0[4 * s + q] = 1.0;
+                xfaces[8 * s + 2 * q] = xfaces[8 * s + 2 * q + 1] = -1;
+                xst[4 * s + q] = 0;
+            }
+            if (!S.bad && S.rotated) {
+                /* the extra lines as the Q map traces them (ordered like the centre) */
+                const double du = sqrt(o_dot(a1, a1)), dv = sqrt(o_dot(a2, a2)), drot = fmin(du, dv);
+                double nrot[3];
+                for (int a = 0; a < 3; a++) nrot[a] = (S.bn0s < 0.0 ? -1.0 : 1.0) * S.bh[a];
+                for (int q = 0; q < 4; q++) {
+                    const double *dir = (q < 2) ? S.u : S.v;
+                    double sg = (q & 1) ? -1.0 : 1.0, rr[3], sx = 1.0;
+                    for (int a = 0; a < 3; a++) rr[a] = S.r0[a] + sg * drot * dir[a];
+                    OLine xl;
+                    OLog gx = {xlogh + (4 * s + q) * (long long)cap, xlogc + (4 * s + q) * (long long)cap, cap, 0, 0};
+                    o_trace_line_log(&f, p, rr, nrot, p->tol, NULL, NULL, &xl, &gx, &sx);
+                    xlogn[4 * s + q] = gx.overflow ? -1 : gx.n;
+                    xs0[4 * s + q] = sx;
+                    xfaces[8 * s + 2 * q] = xl.face[0];
+                    xfaces[8 * s + 2 * q + 1] = xl.face[1];
+                    xst[4 * s + q] = xl.status;
+                }
+            }
+        }
         s0o[s] = s0;
         tolo[s] = S.tol;
         bn0o[s] = S.bn0;

@@ -163,3 +163,54 @@ def _mesh(grid):
     x, y, z = (grid.axis(a) for a in range(3))
     Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
     return X, Y, Z
+
+
+# an interior xz plane of the 24^3 case: 21 seeds rotate S0
+XZ = ((0.0, 18.3, 0.0), (23.0 / 20, 0.0, 0.0), (0.0, 0.0, 23.0 / 12), 20, 12)
+
+
+def test_replay_of_rotated_seeds_reproduces_oracle(small):
+    # a rotated seed's Q comes from its four extra lines, whose seeds the
+    # replay places with the frame of B at the seed
+    B, _, grid = small
+    p = oracle.params()
+    ref = oracle.plane(B, grid, *XZ, p)
+    log = adj.lattice_log(B, grid, *XZ, p)
+    Q, Tw, usable, _ = adj.qmap_t(torch.tensor(B), grid, *XZ, log)
+    us = usable.numpy()
+    rot = (ref["status"] & oracle.ROTATED) != 0
+    assert (us & rot).sum() >= 15
+    np.testing.assert_allclose(Q.numpy()[us], ref["Q"][us], rtol=1e-11)
+    assert np.array_equal(us, np.isfinite(ref["Q"]))
+
+
+def test_rotated_seed_gradient_at_its_cell(small):
+    # the frame's dependence on B enters through the 8 nodes of the seed's
+    # cell: central differences of free re-traces (tol 1e-9) on those 24
+    # entries (a frame held constant misses by about 9 %)
+    B, _, grid = small
+    pt = oracle.params(tol=1e-9, max_steps=1000000)
+    ref = oracle.plane(B, grid, *XZ, pt)
+    rot = np.nonzero(((ref["status"] & oracle.ROTATED) != 0) & np.isfinite(ref["Q"]))[0]
+    s = rot[len(rot) // 2]
+    m = XZ[3] * XZ[4]
+    w = np.zeros(m)
+    w[s] = 1.0 / ref["Q"][s]
+    c = np.floor(adj.seeds_index(grid, *XZ)[s]).astype(int)
+    nx, ny, _ = grid.n
+    ents = [(((c[2] + dz) * ny + (c[1] + dy)) * nx + (c[0] + dx)) * 3 + comp
+            for dz in (0, 1) for dy in (0, 1) for dx in (0, 1) for comp in range(3)]
+    eps = 1e-4 * float(np.sqrt(np.mean(B * B)))
+    fd = []
+    for k in ents:
+        Bp = B.copy().ravel()
+        Bm = B.copy().ravel()
+        Bp[k] += eps
+        Bm[k] -= eps
+        qp = oracle.plane(Bp.reshape(B.shape), grid, *XZ, pt)["Q"][s]
+        qm = oracle.plane(Bm.reshape(B.shape), grid, *XZ, pt)["Q"][s]
+        fd.append(w[s] * (qp - qm) / (2 * eps))
+    fd = np.array(fd)
+    g, _ = adj.vjp(B, grid, *XZ, w, 0 * w, pt)
+    assert np.linalg.norm(g.ravel()[ents] - fd) < 3e-2 * np.linalg.norm(fd)
+    assert abs(np.sum(g * B)) < 1e-12 * np.linalg.norm(g) * np.linalg.norm(B)
