@@ -442,8 +442,8 @@ def loss_grad(B, grid, origin, u, v, nu, nv, Qt, Twt, p=None, wtw=0.1, log=None)
 
 def vjp(B, grid, origin, u, v, nu, nv, wQ, wTw, p=None, log=None):
     """J^T w = d(sum of wQ Q over usable seeds + wTw Tw over good lines)/dB of
-    the frozen-sequence map (Q of MIXED or rotated seeds is not used; Tw of
-    every line without MAXSTEPS, NULL_B or OUTSIDE is)."""
+    the frozen-sequence map (Q of MIXED seeds is not used; Tw of every line
+    without MAXSTEPS, NULL_B or OUTSIDE is)."""
     p = p or params()
     B = _f64(B)
     log = lattice_log(B, grid, origin, u, v, nu, nv, p) if log is None else log

@@ -480,10 +480,26 @@ __device__ __forceinline__ void step_reverse_k(const FieldView &f, T sgn, const 
 
 constexpr int kMaxChunk = 32;  // largest steps per tape chunk
 
-// Does half-line hl carry a nonzero adjoint (footpoint or Tw weight)?
+// Half-lines of the taped map: 2 line + end for the lattice lines, then
+// 2 n + 2 (4 slot + q) + end for the extra lines of rotated seeds.
+__device__ __forceinline__ long long halves_of(const AdjArgs &A)
+{
+    if (!A.rot_count) return 2 * A.n;
+    const long long r = (long long)*A.rot_count;
+    return 2 * A.n + 8 * (r < A.n ? r : A.n);
+}
+
+// status of the line that half-line hl belongs to
+__device__ __forceinline__ unsigned half_status(const AdjArgs &A, long long hl)
+{
+    return hl < 2 * A.n ? A.rec.st[hl >> 1] : A.ext.st[(hl - 2 * A.n) >> 1];
+}
+
+// Does half-line hl carry a nonzero adjoint (footpoint or Tw weight)? Extra
+// lines carry no Tw weight.
 __device__ __forceinline__ bool half_live(const AdjArgs &A, long long hl, double &w)
 {
-    w = A.dTw ? A.dTw[hl >> 1] : 0.0;
+    w = (A.dTw && hl < 2 * A.n) ? A.dTw[hl >> 1] : 0.0;
     if (!(w == w) || fabs(w) == INFINITY) w = 0.0;
     const double *xb = A.xbar + 3 * hl;
     return w != 0.0 || xb[0] != 0.0 || xb[1] != 0.0 || xb[2] != 0.0;
@@ -494,11 +510,11 @@ __device__ __forceinline__ bool chunk_of(const AdjArgs &A, long long c, long lon
 {
     const Tape &tp = A.tape;
     hl = tp.owner[c];
-    if (hl < 0 || hl >= 2 * A.n) {
+    if (hl < 0 || hl >= halves_of(A)) {
         record_fail(A.f.err, 1, c);
         return false;
     }
-    if (A.rec.st[hl >> 1] & kBad) return false;
+    if (half_status(A, hl) & kBad) return false;
     if (!half_live(A, hl, w)) return false;
     const int4 hd = tp.head[hl];
     if (hd.x < 0 || hd.z < 0) return false;
@@ -587,7 +603,7 @@ __device__ __forceinline__ bool step_of(const AdjArgs &A, long long t, long long
     const int4 ci = A.cinfo[c];
     if (!ci.w || i >= ci.x) return false;
     sg = ci.y;
-    w = A.dTw ? A.dTw[ci.z >> 1] : 0.0;
+    w = (A.dTw && ci.z < 2 * A.n) ? A.dTw[ci.z >> 1] : 0.0;
     if (!(w == w) || fabs(w) == INFINITY) w = 0.0;
     return true;
 }
@@ -657,7 +673,8 @@ __global__ void __launch_bounds__(128) k_adj_jac(const AdjArgs A)
     }
 }
 
-// pass B: per half-line, the exit step's VJP and the recurrence over its steps
+// pass B: per half-line, the exit step's VJP and the recurrence over its
+// steps; an extra line's half-line also keeps the adjoint of its seed
 template <typename T, typename AccT, typename TT>
 __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
 {
@@ -668,9 +685,10 @@ __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
     const T *WJ = (const T *)A.wj;
     T *WB = (T *)A.wb;
     AccT *acc = (AccT *)A.acc;
-    for (long long hl = blockIdx.x * (long long)blockDim.x + threadIdx.x; hl < 2 * A.n;
+    const long long halves = halves_of(A);
+    for (long long hl = blockIdx.x * (long long)blockDim.x + threadIdx.x; hl < halves;
          hl += (long long)gridDim.x * blockDim.x) {
-        if (A.rec.st[hl >> 1] & kBad) continue;
+        if (half_status(A, hl) & kBad) continue;
         double w;
         if (!half_live(A, hl, w)) continue;
         const int4 hd = tp.head[hl];
@@ -737,7 +755,8 @@ __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
                 // a zero-length exit step (a seed on the face): the end is x,
                 // all stages sit at x, nothing is scattered; only the length's
                 // dependence on x_ax remains: d = K(x) . yb + twK(x) wbar
-                if (hd.y == 0 && tp.prev[hd.x] < 0) continue;  // no earlier step: the seed's adjoint is not needed
+                // no earlier step: a lattice seed's adjoint is not needed
+                if (hd.y == 0 && tp.prev[hd.x] < 0 && hl < 2 * A.n) continue;
                 const Rhs<T> o = rhs_fwd(f, sgn, x[0], x[1], x[2]);
                 const T fa = o.F[fax];
                 d = (o.F[0] * yb[0] + o.F[1] * yb[1] + o.F[2] * yb[2] + o.dtw * wb) / fa;
@@ -783,6 +802,12 @@ __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
             if (pc < 0 || pc >= c) break;  // chunks of a half-line are taken in increasing order
             c = pc;
             n = K;
+        }
+        if (hl >= 2 * A.n) {
+            double *xs = A.xseed + 3 * (hl - 2 * A.n);
+            xs[0] = (double)y[0];
+            xs[1] = (double)y[1];
+            xs[2] = (double)y[2];
         }
     }
 }
@@ -858,23 +883,36 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < A.n;
          idx += (long long)gridDim.x * blockDim.x) {
         const unsigned st = R.st[idx];
-        if (st & (kBad | FQSL_LINE_ROTATED)) continue;
+        if (st & kBad) continue;
         const double qb = A.dQ ? A.dQ[idx] : 0.0;
         if (!(qb == qb) || qb == 0.0 || fabs(qb) == INFINITY) continue;
+        // a rotated seed (Sec. 4) differences its four extra lines over drot
+        const bool rot = (st & FQSL_LINE_ROTATED) != 0;
+        const int slot = (rot && A.rot_slot) ? A.rot_slot[idx] : 0;
+        if (rot && (slot <= 0 || slot > A.n)) continue;
         // lattice index (i, j) within its layer k (each layer is its own S0)
         const long long i = idx % G.n1, j = (idx / G.n1) % G.n2, k = idx / (G.n1 * G.n2);
-        const long long ni[4] = {i + 1, i - 1, i, i}, nj[4] = {j, j, j + 1, j - 1};
-        long long nid[4];
+        long long nid[4];  // neighbour lines (in NR)
         bool has[4];
-        for (int q = 0; q < 4; q++) {
-            has[q] = ni[q] >= 0 && ni[q] < G.n1 && nj[q] >= 0 && nj[q] < G.n2;
-            nid[q] = has[q] ? ni[q] + G.n1 * (nj[q] + G.n2 * k) : 0;
+        if (rot) {
+            for (int q = 0; q < 4; q++) {
+                nid[q] = 4LL * (slot - 1) + q;
+                has[q] = true;
+            }
+        } else {
+            const long long ni[4] = {i + 1, i - 1, i, i}, nj[4] = {j, j, j + 1, j - 1};
+            for (int q = 0; q < 4; q++) {
+                has[q] = ni[q] >= 0 && ni[q] < G.n1 && nj[q] >= 0 && nj[q] < G.n2;
+                nid[q] = has[q] ? ni[q] + G.n1 * (nj[q] + G.n2 * k) : 0;
+            }
         }
-        const double inv[2] = {1.0 / G.du, 1.0 / G.dv};
+        const LineRecs &NR = rot ? A.ext : R;
+        const long long hbase = rot ? 2 * A.n : 0;  // half-line of NR's line 0
+        const double inv[2] = {rot ? 1.0 / G.drot : 1.0 / G.du, rot ? 1.0 / G.drot : 1.0 / G.dv};
         const int fe2[2] = {R.f1[idx], R.f2[idx]};
-        // J_e[r][s] = sum over two lines of cf * xi_{ra[r]}(line, e)
+        // J_e[r][s] = sum over two half-lines of cf * xi_{ra[r]}(half-line)
         double Jm[2][2][2];
-        long long ln[2][2][2];  // [e][s][plus/minus line]
+        long long ln[2][2][2];  // [e][s][plus/minus]: half-line
         double cf[2][2][2];     // the two coefficients (index units; times d below)
         bool mixed = false;
         for (int e = 0; e < 2 && !mixed; e++) {
@@ -882,21 +920,22 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
             face_axes(fe2[e], ra[0], ra[1]);
             for (int s = 0; s < 2 && !mixed; s++) {
                 const int P = 2 * s, M = 2 * s + 1;
-                const bool okp = has[P] && !(R.st[nid[P]] & kBad) && (e == 0 ? R.f1 : R.f2)[nid[P]] == fe2[e];
-                const bool okm = has[M] && !(R.st[nid[M]] & kBad) && (e == 0 ? R.f1 : R.f2)[nid[M]] == fe2[e];
+                const bool okp = has[P] && !(NR.st[nid[P]] & kBad) && (e == 0 ? NR.f1 : NR.f2)[nid[P]] == fe2[e];
+                const bool okm = has[M] && !(NR.st[nid[M]] & kBad) && (e == 0 ? NR.f1 : NR.f2)[nid[M]] == fe2[e];
+                const long long hp = hbase + 2 * nid[P] + e, hm = hbase + 2 * nid[M] + e, h0 = 2 * idx + e;
                 if (okp && okm) {
-                    ln[e][s][0] = nid[P];
-                    ln[e][s][1] = nid[M];
+                    ln[e][s][0] = hp;
+                    ln[e][s][1] = hm;
                     cf[e][s][0] = 0.5 * inv[s];
                     cf[e][s][1] = -0.5 * inv[s];
                 } else if (okp) {
-                    ln[e][s][0] = nid[P];
-                    ln[e][s][1] = idx;
+                    ln[e][s][0] = hp;
+                    ln[e][s][1] = h0;
                     cf[e][s][0] = inv[s];
                     cf[e][s][1] = -inv[s];
                 } else if (okm) {
-                    ln[e][s][0] = idx;
-                    ln[e][s][1] = nid[M];
+                    ln[e][s][0] = h0;
+                    ln[e][s][1] = hm;
                     cf[e][s][0] = inv[s];
                     cf[e][s][1] = -inv[s];
                 } else {
@@ -905,8 +944,8 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
                 }
                 for (int r = 0; r < 2; r++) {
                     const int a = ra[r];
-                    const double xp = (double)XE[4 * (2 * ln[e][s][0] + e) + a];
-                    const double xm = (double)XE[4 * (2 * ln[e][s][1] + e) + a];
+                    const double xp = (double)XE[4 * ln[e][s][0] + a];
+                    const double xm = (double)XE[4 * ln[e][s][1] + a];
                     Jm[e][r][s] = (cf[e][s][0] * xp + cf[e][s][1] * xm) * f.d[a];
                 }
             }
@@ -951,8 +990,8 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
                 for (int r = 0; r < 2; r++) {
                     const int a = ra[r];
                     const double v = Jb[e][r][s] * f.d[a];
-                    atomicAdd(A.xbar + 3 * (2 * ln[e][s][0] + e) + a, cf[e][s][0] * v);
-                    atomicAdd(A.xbar + 3 * (2 * ln[e][s][1] + e) + a, cf[e][s][1] * v);
+                    atomicAdd(A.xbar + 3 * ln[e][s][0] + a, cf[e][s][0] * v);
+                    atomicAdd(A.xbar + 3 * ln[e][s][1] + a, cf[e][s][1] * v);
                 }
         }
         // |Bn1 Bn2| / Bn0^2
@@ -966,7 +1005,7 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
             atomicAdd(A.xbar + 3 * (2 * idx + 0) + a, bn1b * g1[a]);
             atomicAdd(A.xbar + 3 * (2 * idx + 1) + a, bn2b * g2[a]);
         }
-        // Bn0 = B(seed) . n0
+        // Bn0 = B(seed) . n0, or |B(seed)| for a rotated seed
         T p0[3];
         if (A.prep.seed) {
             // the FP32 tracer's seed (its pre-pass)
@@ -981,8 +1020,99 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
             for (int a = 0; a < 3; a++) p0[a] = (T)((r0[a] - f.o[a]) / f.d[a]);
         }
         const Cell<T> c0 = cell_of(f, p0[0], p0[1], p0[2]);
-        const T Vb[6] = {(T)(bn0b * G.n0[0]), (T)(bn0b * G.n0[1]), (T)(bn0b * G.n0[2]), 0, 0, 0};
-        if (cell_ok(f, c0.base)) scatter(f, c0, Vb, acc);
+        if (!cell_ok(f, c0.base)) continue;
+        double nb[3] = {G.n0[0], G.n0[1], G.n0[2]};
+        if (rot) {
+            T V[6], dV[3][6];
+            interp_d(f, c0, V, dV);
+            const double B0[3] = {(double)V[0], (double)V[1], (double)V[2]};
+            const double nB = sqrt(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
+            if (!(nB > 0.0)) continue;
+            for (int a = 0; a < 3; a++) nb[a] = B0[a] / nB;
+        }
+        const T Vb[6] = {(T)(bn0b * nb[0]), (T)(bn0b * nb[1]), (T)(bn0b * nb[2]), 0, 0, 0};
+        scatter(f, c0, Vb, acc);
+    }
+}
+
+// The extra lines of a rotated seed start at r0 +- drot u and r0 +- drot v,
+// where (u, v) = perp_frame(B(r0)/|B(r0)|) (Sec. 4): the adjoints of their
+// seeds (pass B) are carried back through the frame to B at the seed's cell.
+// u = t/|t| with t = bhat x e_m (m: the smallest |bhat_m|, held fixed), v =
+// bhat x u. One thread per rotated seed.
+template <typename T, typename AccT>
+__global__ void __launch_bounds__(128) k_frame_vjp(const AdjArgs A)
+{
+    const Lattice &G = A.lat;
+    const FieldView &f = A.f;
+    AccT *acc = (AccT *)A.acc;
+    long long nrot = (long long)*A.rot_count;
+    if (nrot > A.n) nrot = A.n;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nrot;
+         s += (long long)gridDim.x * blockDim.x) {
+        // adjoints of the four extra seeds (physical coordinates): both
+        // half-lines of a line start at its seed
+        double rb[4][3];
+        bool any = false;
+        for (int q = 0; q < 4; q++) {
+            const double *x0 = A.xseed + 3 * (2 * (4 * s + q));
+            for (int a = 0; a < 3; a++) {
+                rb[q][a] = (x0[a] + x0[3 + a]) / f.d[a];
+                any = any || rb[q][a] != 0.0;
+            }
+        }
+        if (!any) continue;
+        const long long idx = A.rot_seed[s];
+        if (idx < 0 || idx >= A.n) {
+            record_fail(f.err, 4, idx);
+            continue;
+        }
+        const long long i = idx % G.n1, j = (idx / G.n1) % G.n2, k = idx / (G.n1 * G.n2);
+        double r0[3], xi[3];
+        trace::lattice_seed(G, i, j, k, r0);
+        for (int a = 0; a < 3; a++) xi[a] = (r0[a] - f.o[a]) / f.d[a];
+        const Cell<T> c = cell_of(f, (T)xi[0], (T)xi[1], (T)xi[2]);
+        if (!cell_ok(f, c.base)) continue;
+        T V[6], dV[3][6];
+        interp_d(f, c, V, dV);
+        const double B0[3] = {(double)V[0], (double)V[1], (double)V[2]};
+        const double nB = sqrt(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
+        if (!(nB > 0.0)) continue;
+        const double bh[3] = {B0[0] / nB, B0[1] / nB, B0[2] / nB};
+        int m = 0;
+        if (fabs(bh[1]) < fabs(bh[m])) m = 1;
+        if (fabs(bh[2]) < fabs(bh[m])) m = 2;
+        const int m1 = (m + 1) % 3, m2 = (m + 2) % 3;
+        // t = bhat x e_m: t_m = 0, t_m1 = bhat_m2, t_m2 = -bhat_m1
+        double t[3];
+        t[m] = 0.0;
+        t[m1] = bh[m2];
+        t[m2] = -bh[m1];
+        const double nt = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+        const double u[3] = {t[0] / nt, t[1] / nt, t[2] / nt};
+        // seeds r0 + sg drot dir: ubar, vbar
+        double ub[3], vb[3];
+        for (int a = 0; a < 3; a++) {
+            ub[a] = G.drot * (rb[0][a] - rb[1][a]);
+            vb[a] = G.drot * (rb[2][a] - rb[3][a]);
+        }
+        // v = bhat x u: bhat_bar = u x vbar, ubar += vbar x bhat
+        double bhb[3] = {u[1] * vb[2] - u[2] * vb[1], u[2] * vb[0] - u[0] * vb[2], u[0] * vb[1] - u[1] * vb[0]};
+        ub[0] += vb[1] * bh[2] - vb[2] * bh[1];
+        ub[1] += vb[2] * bh[0] - vb[0] * bh[2];
+        ub[2] += vb[0] * bh[1] - vb[1] * bh[0];
+        // u = t/|t|: tbar = (ubar - u (u . ubar))/|t|
+        const double uu = u[0] * ub[0] + u[1] * ub[1] + u[2] * ub[2];
+        double tb[3];
+        for (int a = 0; a < 3; a++) tb[a] = (ub[a] - u[a] * uu) / nt;
+        // t = bhat x e_m: bhat_bar += e_m x tbar
+        bhb[m1] += -tb[m2];
+        bhb[m2] += tb[m1];
+        // bhat = B0/|B0|
+        const double bb = bh[0] * bhb[0] + bh[1] * bhb[1] + bh[2] * bhb[2];
+        const T Vb[6] = {(T)((bhb[0] - bh[0] * bb) / nB), (T)((bhb[1] - bh[1] * bb) / nB),
+                         (T)((bhb[2] - bh[2] * bb) / nB), 0, 0, 0};
+        scatter(f, c, Vb, acc);
     }
 }
 
@@ -1064,7 +1194,7 @@ __device__ __forceinline__ bool usable(long long s, const double *Q, const doubl
                                        const double *Twt, const uint8_t *st)
 {
     const double q = Q[s], qt = Qt[s], t = Tw[s], tt = Twt[s];
-    if (st && (st[s] & (kBad | FQSL_LINE_MIXED | FQSL_LINE_ROTATED))) return false;
+    if (st && (st[s] & (kBad | FQSL_LINE_MIXED))) return false;
     return isfinite(q) && isfinite(qt) && isfinite(t) && isfinite(tt) && q > 0.0 && qt > 0.0;
 }
 
@@ -1198,6 +1328,7 @@ void reverse_passes(const AdjArgs &a, cudaStream_t s)
     adj::k_adj_jac<T, TT><<<gs, 128, 0, s>>>(a);
     adj::k_adj_lines<T, AccT, TT><<<gl, 128, 0, s>>>(a);
     adj::k_adj_rev<T, AccT, TT><<<gs, 128, 0, s>>>(a);
+    if (a.rot_count) adj::k_frame_vjp<T, AccT><<<adj::grid_for(a.n, 128, 4), 128, 0, s>>>(a);
 }
 
 template <typename TT>

@@ -66,7 +66,7 @@ struct fqsl_field_s {
     unsigned long long *counters = nullptr;  // [0] primary head, [1] extra head, [2] rotated count (low 32 bits)
     int blocks_cache[3][3] = {};  // [precision][source] resident blocks per SM
     int blocks_cache_m2[2][2] = {};  // Method II: [fp64][way - 1]
-    int blocks_cache_tape[3] = {};   // taped lattice tracer: [precision]
+    int blocks_cache_tape[3][2] = {};  // taped tracers: [precision][lattice, extra]
     bool timing = false, timed = false, extra_timed = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // the last plane map traced with params->tape = 1 (for fqsl_backward): its
@@ -499,15 +499,19 @@ void index_lattice(const fqsl_field f, Lattice &lat)
     }
 }
 
-// Layout of a taped plane map in the field's tape buffer: the line records
-// (as in layout()), counters, the step tape (pool chunks of k steps), the
-// footpoint adjoints, the loss sums and the adjoint node grid.
+// Layout of a taped map in the field's tape buffer: the line records (as in
+// layout()), counters, the step tape (pool chunks of k steps), the footpoint
+// and extra-seed adjoints, the loss sums and the adjoint node grid. With
+// rotation possible the half-lines of the 4 n extra lines follow the 2 n
+// lattice half-lines.
 struct TapeLayout {
     Scratch s;
     unsigned long long *ctr;  // [0] tape chunks handed out, [1] live steps of the reverse sweep,
-                              // [2], [3] failed index checks of the adjoint kernels
+                              // [2], [3] failed index checks of the adjoint kernels,
+                              // [4] rotated seeds (as unsigned), [5] work counter of the extra tracer
     Tape tape;
-    double *xbar, *sums;
+    double *xbar, *xseed, *sums;
+    long long halves;
     void *acc;
     size_t bytes;
 };
@@ -521,17 +525,19 @@ TapeLayout tape_layout(char *base, long long n, bool rot, bool f32, long long po
     t.s = layout(base, n, rot, true, f32);
     Carver c{base ? base + t.s.bytes : nullptr};
     const size_t ts = f32 ? 4 : 8;
-    t.ctr = c.take<unsigned long long>(4);
+    t.halves = 2 * n + (rot ? 8 * n : 0);
+    t.ctr = c.take<unsigned long long>(6);
     t.tape.k = k;
     t.tape.cap = pool;
     t.tape.next = t.ctr;
     t.tape.prev = c.take<int32_t>((size_t)pool);
     t.tape.xi = c.take<char>((size_t)pool * 4 * ts);
     t.tape.h = c.take<char>((size_t)pool * k * ts);
-    t.tape.head = c.take<int4>((size_t)(2 * n));
-    t.tape.xe = c.take<char>((size_t)(2 * n) * 4 * ts);
+    t.tape.head = c.take<int4>((size_t)t.halves);
+    t.tape.xe = c.take<char>((size_t)t.halves * 4 * ts);
     t.tape.owner = c.take<int32_t>((size_t)pool);
-    t.xbar = c.take<double>((size_t)(6 * n));
+    t.xbar = c.take<double>((size_t)(3 * t.halves));
+    t.xseed = rot ? c.take<double>((size_t)(24 * n)) : nullptr;
     t.sums = c.take<double>(2);
     t.acc = c.take<char>(nodes * 8 * (acc64 ? 8 : 4));
     t.bytes = t.s.bytes + c.off;
@@ -569,12 +575,19 @@ fqsl_status ensure_tape_buf(fqsl_field f, size_t bytes)
     return FQSL_OK;
 }
 
-int tape_blocks_per_sm(fqsl_field f, int precision)
+int tape_blocks_per_sm(fqsl_field f, int precision, int src)
 {
-    int &c = f->blocks_cache_tape[precision];
-    if (!c) c = precision == FQSL_F64 ? trace_tape_blocks_per_sm_f64()
-                                      : trace_tape_blocks_per_sm_f32(precision == FQSL_F32_ACC64);
+    int &c = f->blocks_cache_tape[precision][src == kSrcExtra ? 1 : 0];
+    if (!c) c = precision == FQSL_F64 ? trace_tape_blocks_per_sm_f64(src)
+                                      : trace_tape_blocks_per_sm_f32(src, precision == FQSL_F32_ACC64);
     return c;
+}
+
+cudaError_t launch_tape(const TraceArgs &a, const fqsl_params *p, int src, long long grid, cudaStream_t s)
+{
+    if (grid < 1) grid = 1;
+    return p->precision == FQSL_F64 ? launch_trace_tape_f64(a, src, (int)grid, s)
+                                    : launch_trace_tape_f32(a, src, (int)grid, s, p->precision == FQSL_F32_ACC64);
 }
 
 // Shared body of the plane and volume Q maps (the caller holds f->mu). With
@@ -617,7 +630,7 @@ fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params
 
     cudaError_t e = cudaMemsetAsync(f->counters, 0, 4 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess && lat.allow_rot) e = cudaMemsetAsync(s.rot_slot, 0, (size_t)n * sizeof(int32_t), stream);
-    if (e == cudaSuccess && tape) e = cudaMemsetAsync(tl.ctr, 0, 4 * sizeof(unsigned long long), stream);
+    if (e == cudaSuccess && tape) e = cudaMemsetAsync(tl.ctr, 0, 6 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess && tape) {
         // the taped tracer traces the two directions of a line as separate
         // items and combines status, trial count and (FP64) sums atomically
@@ -637,7 +650,9 @@ fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params
     a.rec = s.rec;
     a.ext = s.ext;
     a.q.head = f->counters;
-    a.q.rot_count = (unsigned int *)(f->counters + 2);
+    // a taped map keeps its rotated-seed count with the tape (f->counters is
+    // shared with the field's other calls)
+    a.q.rot_count = tape ? (unsigned int *)(tl.ctr + 4) : (unsigned int *)(f->counters + 2);
     a.q.rot_seed = s.rot_seed;
     a.q.rot_slot = s.rot_slot;
     a.prep = s.prep;
@@ -668,23 +683,32 @@ fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params
         return FQSL_OK;
     }
     if (tape) {
-        int bps = tape_blocks_per_sm(f, p->precision);
+        int bps = tape_blocks_per_sm(f, p->precision, kSrcLattice);
         if (p->blocks_per_sm > 0 && p->blocks_per_sm < bps) bps = p->blocks_per_sm;
         long long grid = (long long)f->sms * bps;
         a.nitems *= 2;  // one item per direction of a line
         const long long need = (a.nitems + kTraceBlock - 1) / kTraceBlock;
         if (need < grid) grid = need;
         if (grid < 1) grid = 1;
-        e = p->precision == FQSL_F64 ? launch_trace_tape_f64(a, (int)grid, stream)
-                                     : launch_trace_tape_f32(a, (int)grid, stream, p->precision == FQSL_F32_ACC64);
+        e = launch_tape(a, p, kSrcLattice, grid, stream);
     } else {
         e = launch_trace(f, p, a, kSrcLattice, a.nitems, stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, who);
     mark(f, 1, stream);
     if (lat.allow_rot) {
-        a.q.head = f->counters + 1;
-        e = launch_trace(f, p, a, kSrcExtra, 4 * n, stream);
+        if (tape) {
+            // the extra lines' half-lines follow the lattice's on the tape;
+            // their count is read on the device (persistent grid)
+            a.q.head = tl.ctr + 5;
+            a.tape.hl_base = 2 * n;
+            int bps = tape_blocks_per_sm(f, p->precision, kSrcExtra);
+            if (p->blocks_per_sm > 0 && p->blocks_per_sm < bps) bps = p->blocks_per_sm;
+            e = launch_tape(a, p, kSrcExtra, (long long)f->sms * bps, stream);
+        } else {
+            a.q.head = f->counters + 1;
+            e = launch_trace(f, p, a, kSrcExtra, 4 * n, stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, who);
     }
     mark(f, 2, stream);
@@ -1316,7 +1340,8 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
         }
         f->tp.work_cap = wbytes;
     }
-    cudaError_t e = cudaMemsetAsync(tl.xbar, 0, (size_t)(6 * n) * sizeof(double), stream);
+    cudaError_t e = cudaMemsetAsync(tl.xbar, 0, (size_t)(3 * tl.halves) * sizeof(double), stream);
+    if (e == cudaSuccess && tl.xseed) e = cudaMemsetAsync(tl.xseed, 0, (size_t)(24 * n) * sizeof(double), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(tl.acc, 0, nodes * 8 * (acc64 ? 8 : 4), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(tl.ctr + 1, 0, 3 * sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
@@ -1335,6 +1360,13 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
     a.xbar = tl.xbar;
     a.acc = tl.acc;
     a.n = n;
+    if (lat.allow_rot) {
+        a.ext = tl.s.ext;
+        a.rot_slot = tl.s.rot_slot;
+        a.rot_seed = tl.s.rot_seed;
+        a.rot_count = (const unsigned *)(tl.ctr + 4);
+        a.xseed = tl.xseed;
+    }
     a.chunks = (long long)used;
     a.wx = f->tp.work;
     a.wj = (char *)f->tp.work + bx;

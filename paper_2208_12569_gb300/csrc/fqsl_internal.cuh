@@ -128,9 +128,11 @@ struct Tape {
     int32_t *prev;              // [cap] previous chunk of the half-line, -1 for its first
     void *xi;                   // [cap] T[4]: state at the chunk's first step {x, y, z, 0}
     void *h;                    // [cap * k] T: accepted step sizes
-    int4 *head;                 // [2 n] {last chunk, steps in it, end code, orientation sign}
-    void *xe;                   // [2 n] T[4]: {footpoint x, y, z, exiting step of a chord end}
+    int4 *head;                 // [halves] {last chunk, steps in it, end code, orientation sign}
+    void *xe;                   // [halves] T[4]: {footpoint x, y, z, exiting step of a chord end}
     int32_t *owner;             // [cap] half-line of each chunk
+    long long hl_base;          // half-line of a launch's line 0: 0 for lattice lines,
+                                // 2 n for the extra lines of rotated seeds (item = 4 slot + q)
 };
 
 struct TraceArgs {
@@ -179,6 +181,11 @@ struct AdjArgs {
     double *xbar;              // [2 n][3] adjoint of each footpoint (index coordinates)
     void *acc;                 // [nodes][8] {dB (3), dJ (3), 0, 0}, float or double
     long long n;
+    LineRecs ext;              // extra lines of rotated seeds (4 per slot)
+    const int32_t *rot_slot;   // lattice index -> rotated slot + 1 (0: not rotated); NULL if none
+    const int32_t *rot_seed;   // rotated slot -> lattice index
+    const unsigned *rot_count; // rotated seeds of the taped map
+    double *xseed;             // [8 n][3] adjoint of each extra half-line's seed (index coordinates)
     // per-step work arrays of the reverse sweep, for chunks 0..chunks-1 (T):
     //   wx [chunk][k + 1][3] states, wj [chunk][k][12] step Jacobian J^T (9)
     //   and Tw gradient (3), wk [chunk][k][15] stage derivatives, wb
@@ -206,11 +213,11 @@ cudaError_t launch_curl_pack(const void *B, fqsl_dtype bt, const FieldView &g, v
                              cudaStream_t s);
 cudaError_t launch_trace_f32(const TraceArgs &a, int src, int grid, int block, cudaStream_t s, bool acc64);
 cudaError_t launch_trace_f64(const TraceArgs &a, int src, int grid, int block, cudaStream_t s);
-// lattice tracers that also write the step tape (a.tape)
-cudaError_t launch_trace_tape_f32(const TraceArgs &a, int grid, cudaStream_t s, bool acc64);
-cudaError_t launch_trace_tape_f64(const TraceArgs &a, int grid, cudaStream_t s);
-int trace_tape_blocks_per_sm_f32(bool acc64);
-int trace_tape_blocks_per_sm_f64();
+// tracers that also write the step tape (a.tape; lattice or extra lines)
+cudaError_t launch_trace_tape_f32(const TraceArgs &a, int src, int grid, cudaStream_t s, bool acc64);
+cudaError_t launch_trace_tape_f64(const TraceArgs &a, int src, int grid, cudaStream_t s);
+int trace_tape_blocks_per_sm_f32(int src, bool acc64);
+int trace_tape_blocks_per_sm_f64(int src);
 int trace_blocks_per_sm_f32(int src, bool acc64);
 int trace_blocks_per_sm_f64(int src);
 // Method II tracers (deviation vectors; way 1 = gradient grid, 2 = +-eps)

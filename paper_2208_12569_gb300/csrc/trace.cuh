@@ -548,7 +548,7 @@ __device__ __forceinline__ bool tape_chunk(const Tape &tp, Lane<T> &L)
         return false;
     }
     tp.prev[c] = L.tcur;
-    tp.owner[c] = (int32_t)(2 * L.line + L.end);
+    tp.owner[c] = (int32_t)(tp.hl_base + 2 * L.line + L.end);
     T *x = (T *)tp.xi + 4 * c;
     x[0] = L.x;
     x[1] = L.y;
@@ -575,7 +575,7 @@ template <typename T>
 __device__ __forceinline__ void tape_end(const Tape &tp, Lane<T> &L, int code, T x, T y, T z, T hx)
 {
     if (L.tcur == -1) tape_chunk(tp, L);  // no accepted step: the checkpoint is the seed
-    const long long hl = 2 * L.line + L.end;
+    const long long hl = tp.hl_base + 2 * L.line + L.end;
     const int sg = (L.end == 0) == (L.s0 > (T)0) ? -1 : 1;
     tp.head[hl] = make_int4(L.tcur, L.tn, L.tcur >= 0 ? code : -2, sg);
     T *e = (T *)tp.xe + 4 * hl;
@@ -990,12 +990,14 @@ __device__ __forceinline__ bool init_list(const TraceArgs &A, Lane<T> &L, long l
 // vectors with grad(B/|B|) by way 1 or way 2 (lattice source only).
 // BATCH: the launch traces the entries of a batch (BatchArgs); each lane keeps
 // the entry of its line. A0 holds the launch-wide parameters and counter.
-// TAPE: also write the step tape A0.tape (lattice lines, Method I), and trace
-// the two directions of a line as separate work items (twice the lattice's
-// items; see split_finish) so that a long line's halves run side by side.
+// TAPE: also write the step tape A0.tape (Method I). Lattice lines are then
+// traced with their two directions as separate work items (twice the
+// lattice's items; see split_finish) so that a long line's halves run side by
+// side; the extra lines of rotated seeds keep one item per line.
 template <typename T, int SRC, bool ACC, int DEV = 0, bool BATCH = false, bool TAPE = false>
 __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs &BA)
 {
+    constexpr bool SPLIT = TAPE && SRC == kSrcLattice;
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -1059,7 +1061,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                 eb = ck_ent;
                 const TraceArgs &E = ent();
                 if (SRC == kSrcLattice) {
-                    if constexpr (TAPE) {
+                    if constexpr (SPLIT) {
                         // items come in 32-lane groups: a tile's direction 0,
                         // then the same tile's direction 1
                         const long long g = item >> 5;
@@ -1100,7 +1102,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
         T hh;
         if (!henon) {
             if (L.steps >= max_steps) {
-                finish_bad<T, TAPE>(A, R, L, FQSL_LINE_MAXSTEPS);
+                finish_bad<T, SPLIT>(A, R, L, FQSL_LINE_MAXSTEPS);
                 active = false;
                 continue;
             }
@@ -1198,7 +1200,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
         }
 
         if (fail == 1) {
-            finish_bad<T, TAPE>(A, R, L, FQSL_LINE_NULL_B);
+            finish_bad<T, SPLIT>(A, R, L, FQSL_LINE_NULL_B);
             active = false;
             continue;
         }
@@ -1341,7 +1343,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                     ev[c] = L.v[c] + L.t0 * (L.ov[c] - L.v[c]);
                 }
             }
-            active = finish_dir<T, ACC, DEV, TAPE>(A, R, L, ex, ey, ez, L.fc0, eu, ev);
+            active = finish_dir<T, ACC, DEV, SPLIT>(A, R, L, ex, ey, ez, L.fc0, eu, ev);
             waiting = active && A0.p.sync_dirs;
             continue;
         }
@@ -1380,7 +1382,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                 ev[c] = L.v[c] + hh * ad[3 + c];
             }
         }
-        active = finish_dir<T, ACC, DEV, TAPE>(A, R, L, tx, ty, tz, L.hface, eu, ev);
+        active = finish_dir<T, ACC, DEV, SPLIT>(A, R, L, tx, ty, tz, L.hface, eu, ev);
         waiting = active && A0.p.sync_dirs;
     }
 }

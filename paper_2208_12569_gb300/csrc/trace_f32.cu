@@ -193,25 +193,35 @@ int batch_trace_blocks_per_sm_f32(bool acc64)
 // ---------------------------------------------------------------------------
 namespace fqsl {
 namespace {
-template <bool ACC>
+template <int SRC, bool ACC>
 __global__ void __launch_bounds__(kBlock, FQSL_TRACE_F32_MINB) k_trace_tape_f32(const TraceArgs A)
 {
-    trace::trace_body<float, kSrcLattice, ACC, 0, false, true>(A, BatchArgs{});
+    trace::trace_body<float, SRC, ACC, 0, false, true>(A, BatchArgs{});
 }
 }  // namespace
 
-cudaError_t launch_trace_tape_f32(const TraceArgs &a, int grid, cudaStream_t s, bool acc64)
+cudaError_t launch_trace_tape_f32(const TraceArgs &a, int src, int grid, cudaStream_t s, bool acc64)
 {
-    if (acc64) k_trace_tape_f32<true><<<grid, kBlock, 0, s>>>(a);
-    else k_trace_tape_f32<false><<<grid, kBlock, 0, s>>>(a);
+    if (src == kSrcExtra) {
+        if (acc64) k_trace_tape_f32<kSrcExtra, true><<<grid, kBlock, 0, s>>>(a);
+        else k_trace_tape_f32<kSrcExtra, false><<<grid, kBlock, 0, s>>>(a);
+    } else {
+        if (acc64) k_trace_tape_f32<kSrcLattice, true><<<grid, kBlock, 0, s>>>(a);
+        else k_trace_tape_f32<kSrcLattice, false><<<grid, kBlock, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
-int trace_tape_blocks_per_sm_f32(bool acc64)
+int trace_tape_blocks_per_sm_f32(int src, bool acc64)
 {
     int b = 0;
-    if (acc64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_f32<true>, kBlock, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_f32<false>, kBlock, 0);
+    if (src == kSrcExtra) {
+        if (acc64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_f32<kSrcExtra, true>, kBlock, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_f32<kSrcExtra, false>, kBlock, 0);
+    } else {
+        if (acc64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_f32<kSrcLattice, true>, kBlock, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_f32<kSrcLattice, false>, kBlock, 0);
+    }
     return b > 0 ? b : 1;
 }
 }  // namespace fqsl

@@ -85,23 +85,26 @@ int batch_trace_blocks_per_sm_f64()
 
 namespace fqsl {
 namespace {
-// adjoint forward pass: the lattice tracer that also writes the step tape
+// adjoint forward pass: the tracers that also write the step tape
+template <int SRC>
 __global__ void __launch_bounds__(kBlock) k_trace_tape_f64(const TraceArgs A)
 {
-    trace::trace_body<double, kSrcLattice, true, 0, false, true>(A, BatchArgs{});
+    trace::trace_body<double, SRC, true, 0, false, true>(A, BatchArgs{});
 }
 }  // namespace
 
-cudaError_t launch_trace_tape_f64(const TraceArgs &a, int grid, cudaStream_t s)
+cudaError_t launch_trace_tape_f64(const TraceArgs &a, int src, int grid, cudaStream_t s)
 {
-    k_trace_tape_f64<<<grid, kBlock, 0, s>>>(a);
+    if (src == kSrcExtra) k_trace_tape_f64<kSrcExtra><<<grid, kBlock, 0, s>>>(a);
+    else k_trace_tape_f64<kSrcLattice><<<grid, kBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-int trace_tape_blocks_per_sm_f64()
+int trace_tape_blocks_per_sm_f64(int src)
 {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_f64, kBlock, 0);
+    if (src == kSrcExtra) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_f64<kSrcExtra>, kBlock, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_f64<kSrcLattice>, kBlock, 0);
     return b > 0 ? b : 1;
 }
 }  // namespace fqsl

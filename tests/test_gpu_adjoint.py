@@ -20,7 +20,8 @@ pytestmark = pytest.mark.gpu
 
 SMALL = dict(n=(24, 24, 24), count=6, radius_cells=4.0, dtype=np.float64)
 PLANE16 = ((0.0, 0.0, 0.0), (23.0 / 16, 0.0, 0.0), (0.0, 23.0 / 16, 0.0), 16, 16)
-# an interior xz plane (some seeds rotate S0; their Q carries no gradient)
+# an interior xz plane: 21 seeds rotate S0 (their Q comes from four extra
+# lines seeded along the frame of B at the seed, differentiated through it)
 XZ = ((0.0, 18.3, 0.0), (23.0 / 20, 0.0, 0.0), (0.0, 0.0, 23.0 / 12), 20, 12)
 PATCH = ((-0.3, -0.3, 0.0), (0.1, 0.0, 0.0), (0.0, 0.1, 0.0), 6, 6)
 
@@ -75,6 +76,61 @@ def test_fp64_gradient_matches_oracle_adjoint(fq, small, plane):
     assert np.abs(g - ref).max() < 1e-10 * np.abs(ref).max()
     if plane is XZ:
         assert (st & fq.LINE_ROTATED).any()
+
+
+def _rotated_weights(fq, field, B, grid):
+    # log-Q weights on the usable rotated seeds of XZ only
+    ref = oracle.plane(B, grid, *XZ, oracle.params())
+    rot = ((ref["status"] & oracle.ROTATED) != 0) & np.isfinite(ref["Q"])
+    assert rot.sum() >= 15
+    wq = np.where(rot, 1.0 / np.where(rot, ref["Q"], 1.0), 0.0)
+    return wq, 0.0 * wq
+
+
+def test_rotated_seeds_gradient_matches_oracle(fq, small):
+    # only rotated seeds weighted: the extra lines' reverse sweep, their seed
+    # adjoints and the frame VJP carry the whole gradient
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    wq, wt = _rotated_weights(fq, field, B, grid)
+    g, st = _gpu_vjp(fq, field, XZ, wq, wt, precision="f64")
+    ref, _ = adj.vjp(B, grid, *XZ, wq, wt, oracle.params())
+    assert np.linalg.norm(ref) > 0
+    assert _rel(g, ref) < 1e-10
+    # FP32 reverse sweep on the same (oracle) steps
+    g32, _ = _gpu_vjp(fq, field, XZ, wq, wt, dtype=torch.float32, precision="f64", reverse_precision="f32")
+    assert _rel(g32, ref) < 2e-3
+
+
+def test_rotated_frame_is_differentiated(fq, small, monkeypatch):
+    # Planted in the oracle: with the frame of the extra seeds held constant
+    # (no derivative through B at the seed) the oracle's gradient moves away
+    # from the CUDA one by far more than rounding.
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    wq, wt = _rotated_weights(fq, field, B, grid)
+    g, _ = _gpu_vjp(fq, field, XZ, wq, wt, precision="f64")
+    real = adj.perp_frame_t
+    monkeypatch.setattr(adj, "perp_frame_t", lambda bh, m: tuple(x.detach() for x in real(bh.detach(), m)))
+    planted, _ = adj.vjp(B, grid, *XZ, wq, wt, oracle.params())
+    assert _rel(g, planted) > 1e-3
+
+
+def test_rotated_seeds_survive_an_untaped_map(fq, small):
+    # the rotated-seed count of a taped map is kept with its tape: an untaped
+    # map on the same field in between leaves the gradient unchanged
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    m = XZ[3] * XZ[4]
+    wq, wt = _weights(13, m)
+    g0, _ = _gpu_vjp(fq, field, XZ, wq, wt, precision="f64")
+    fq.qmap_plane(field, *XZ, fq.params(precision="f64", tape=1))
+    fq.qmap_plane(field, *PLANE16, fq.params(precision="f64"))
+    fq.qmap_plane(field, (0.0, 4.3, 0.0), (23.0 / 8, 0.0, 0.0), (0.0, 0.0, 23.0 / 8), 8, 8, fq.params())
+    g1 = fq.backward(field, torch.from_numpy(wq).cuda(), torch.from_numpy(wt).cuda(), dtype=torch.float64)
+    field.check()
+    # (node sums are accumulated with atomics: equal up to their order)
+    assert _rel(g1.cpu().numpy(), g0) < 1e-13
 
 
 @pytest.mark.parametrize("reverse,bound", [("f32", 2e-3), ("f32acc64", 2e-3)])
@@ -235,7 +291,7 @@ def test_loss_kernel_matches_oracle_loss(fq, small):
     Q = torch.tensor(out["Q"].cpu().numpy(), requires_grad=True)
     Tw = torch.tensor(out["Tw"].cpu().numpy(), requires_grad=True)
     st = out["status"].cpu().numpy()
-    usable = torch.from_numpy((st & (oracle.BAD | oracle.MIXED | oracle.ROTATED)) == 0)
+    usable = torch.from_numpy((st & (oracle.BAD | oracle.MIXED)) == 0)
     ref, use = adj.log_q_tw_loss(Q, Tw, tgt["Q"].cpu().numpy(), tgt["Tw"].cpu().numpy(), usable, 0.1)
     ref.backward()
     assert int(use.sum()) > 200
@@ -244,19 +300,20 @@ def test_loss_kernel_matches_oracle_loss(fq, small):
     np.testing.assert_allclose(dTw.cpu().numpy(), Tw.grad.numpy(), rtol=1e-12, atol=1e-300)
 
 
-def test_loss_gradient_end_to_end_matches_oracle(fq, small):
+@pytest.mark.parametrize("plane", [PLANE16, XZ], ids=["z0_plane", "interior_xz_plane"])
+def test_loss_gradient_end_to_end_matches_oracle(fq, small, plane):
     # loss -> dQ, dTw (loss kernel) -> dB (fqsl_backward), FP64, against the
     # oracle's autograd of the same loss over the frozen step sequence
     B, Bt, grid = small
     field = _field(fq, B, grid)
-    tgt = oracle.plane(Bt, grid, *PLANE16, oracle.params())
+    tgt = oracle.plane(Bt, grid, *plane, oracle.params())
     p = fq.params(precision="f64", tape=1)
-    out = fq.qmap_plane(field, *PLANE16, p)
+    out = fq.qmap_plane(field, *plane, p)
     qt = torch.from_numpy(tgt["Q"]).cuda()
     twt = torch.from_numpy(tgt["Tw"]).cuda()
     loss, dQ, dTw = fq.loss_logq_tw(out["Q"], out["Tw"], qt, twt, out["status"], 0.1)
     dB = fq.backward(field, dQ, dTw, dtype=torch.float64).cpu().numpy()
-    ref_loss, ref_g, _ = adj.loss_grad(B, grid, *PLANE16, tgt["Q"], tgt["Tw"], oracle.params())
+    ref_loss, ref_g, _ = adj.loss_grad(B, grid, *plane, tgt["Q"], tgt["Tw"], oracle.params())
     np.testing.assert_allclose(float(loss), ref_loss, rtol=1e-11)
     assert _rel(dB, ref_g) < 1e-10
 
