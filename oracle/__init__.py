@@ -59,7 +59,8 @@ def lib():
             L = C.CDLL(build())
             P = C.c_void_p
             for name in ("oracle_curl", "oracle_gradb", "oracle_interp", "oracle_qmap", "oracle_twist",
-                         "oracle_trace", "oracle_max_threads"):
+                         "oracle_trace", "oracle_max_threads", "oracle_curl_rect", "oracle_qmap_rect",
+                         "oracle_twist_rect", "oracle_interp_rect", "oracle_cell_rect"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -73,7 +74,19 @@ def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
 
 
+def is_rect(grid) -> bool:
+    """A stretched grid (node coordinate arrays, reading R16) rather than a
+    uniform one."""
+    return hasattr(grid, "coords")
+
+
+def _coords(grid):
+    return np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.float64) for c in grid.coords]))
+
+
 def _grid_args(grid):
+    if is_rect(grid):
+        raise ValueError("this oracle function takes a uniform grid")
     n = np.array(grid.n, dtype=np.int64)
     o = np.array(grid.origin, dtype=np.float64)
     d = np.array(grid.spacing, dtype=np.float64)
@@ -87,8 +100,14 @@ def max_threads() -> int:
 def curl(B, grid):
     """curl B at the nodes (same layout as B, float64)."""
     B = _f64(B)
-    n, o, d = _grid_args(grid)
     J = np.empty_like(B)
+    if is_rect(grid):
+        n = np.array(grid.n, dtype=np.int64)
+        rc = lib().oracle_curl_rect(_p(B), _p(n), _p(_coords(grid)), _p(J))
+        if rc:
+            raise ValueError("oracle_curl_rect: bad grid")
+        return J
+    n, o, d = _grid_args(grid)
     rc = lib().oracle_curl(_p(B), _p(n), _p(d), _p(J))
     if rc:
         raise ValueError("oracle_curl: bad grid")
@@ -118,6 +137,31 @@ def interp(arr, n, xi):
     return out
 
 
+def interp_rect(arr, grid, r):
+    """Trilinear interpolation (Eqs. interp, w0, w1) of node array ``arr``
+    (nz,ny,nx,nc) on the stretched grid at physical points ``r`` (m, 3)."""
+    arr = _f64(arr)
+    nc = arr.shape[-1]
+    r = _f64(np.atleast_2d(r))
+    out = np.empty((r.shape[0], nc))
+    n = np.array(grid.n, dtype=np.int64)
+    rc = lib().oracle_interp_rect(_p(arr), C.c_int(nc), _p(n), _p(_coords(grid)), _p(r), C.c_longlong(r.shape[0]),
+                                  _p(out))
+    if rc:
+        raise ValueError("oracle_interp_rect: bad grid")
+    return out
+
+
+def cell_rect(X, x):
+    """Cell index of each coordinate x on an axis with node coordinates X."""
+    X = _f64(np.asarray(X))
+    x = _f64(np.atleast_1d(x))
+    out = np.empty(len(x), np.int64)
+    if lib().oracle_cell_rect(_p(X), C.c_longlong(len(X)), _p(x), C.c_longlong(len(x)), _p(out)):
+        raise ValueError("oracle_cell_rect: bad axis")
+    return out
+
+
 def _prep_field(B, grid, J, G, p):
     B = _f64(B)
     if J is None:
@@ -138,7 +182,6 @@ def qmap(B, grid, origin, a1, a2, a3=(0.0, 0.0, 0.0), counts=(1, 1, 1), p: Param
     to compute (default: all, in that order)."""
     p = p or params()
     B, J, G = _prep_field(B, grid, J, G, p)
-    n, o, d = _grid_args(grid)
     lo = np.array(origin, dtype=np.float64)
     A1, A2, A3 = (np.array(v, dtype=np.float64) for v in (a1, a2, a3))
     ln = np.array(counts, dtype=np.int64)
@@ -150,10 +193,19 @@ def qmap(B, grid, origin, a1, a2, a3=(0.0, 0.0, 0.0), counts=(1, 1, 1), p: Param
     out = dict(Q=np.empty(m), Tw=np.empty(m), length=np.empty(m), r1=np.empty((m, 3)),
                r2=np.empty((m, 3)), face1=np.empty(m, np.int32), face2=np.empty(m, np.int32),
                status=np.empty(m, np.int32), steps=np.empty(m, np.int64))
-    rc = lib().oracle_qmap(_p(B), _p(J), _p(G), _p(n), _p(o), _p(d), _p(lo), _p(A1), _p(A2), _p(A3),
-                           _p(ln), C.byref(p), _p(sample), C.c_longlong(m if sample is not None else 0),
-                           _p(out["Q"]), _p(out["Tw"]), _p(out["length"]), _p(out["r1"]), _p(out["r2"]),
-                           _p(out["face1"]), _p(out["face2"]), _p(out["status"]), _p(out["steps"]))
+    outs = (_p(out["Q"]), _p(out["Tw"]), _p(out["length"]), _p(out["r1"]), _p(out["r2"]), _p(out["face1"]),
+            _p(out["face2"]), _p(out["status"]), _p(out["steps"]))
+    if is_rect(grid):
+        if p.method != 1:
+            raise ValueError("stretched grids: Method I only")
+        n = np.array(grid.n, dtype=np.int64)
+        rc = lib().oracle_qmap_rect(_p(B), _p(J), _p(n), _p(_coords(grid)), _p(lo), _p(A1), _p(A2), _p(A3),
+                                    _p(ln), C.byref(p), _p(sample), C.c_longlong(m if sample is not None else 0),
+                                    *outs)
+    else:
+        n, o, d = _grid_args(grid)
+        rc = lib().oracle_qmap(_p(B), _p(J), _p(G), _p(n), _p(o), _p(d), _p(lo), _p(A1), _p(A2), _p(A3),
+                               _p(ln), C.byref(p), _p(sample), C.c_longlong(m if sample is not None else 0), *outs)
     if rc:
         raise ValueError("oracle_qmap: argument error %d" % rc)
     return out
@@ -169,15 +221,20 @@ def twist(B, grid, seeds, p: Params | None = None, J=None):
     p = p or params()
     B = _f64(B)
     J = _f64(curl(B, grid) if J is None else J)
-    n, o, d = _grid_args(grid)
     seeds = _f64(np.atleast_2d(seeds))
     m = seeds.shape[0]
     out = dict(Tw=np.empty(m), length=np.empty(m), r1=np.empty((m, 3)), r2=np.empty((m, 3)),
                face1=np.empty(m, np.int32), face2=np.empty(m, np.int32), status=np.empty(m, np.int32),
                steps=np.empty(m, np.int64))
-    rc = lib().oracle_twist(_p(B), _p(J), _p(n), _p(o), _p(d), _p(seeds), C.c_longlong(m), C.byref(p),
-                            _p(out["Tw"]), _p(out["length"]), _p(out["r1"]), _p(out["r2"]),
-                            _p(out["face1"]), _p(out["face2"]), _p(out["status"]), _p(out["steps"]))
+    outs = (_p(out["Tw"]), _p(out["length"]), _p(out["r1"]), _p(out["r2"]), _p(out["face1"]), _p(out["face2"]),
+            _p(out["status"]), _p(out["steps"]))
+    if is_rect(grid):
+        n = np.array(grid.n, dtype=np.int64)
+        rc = lib().oracle_twist_rect(_p(B), _p(J), _p(n), _p(_coords(grid)), _p(seeds), C.c_longlong(m),
+                                     C.byref(p), *outs)
+    else:
+        n, o, d = _grid_args(grid)
+        rc = lib().oracle_twist(_p(B), _p(J), _p(n), _p(o), _p(d), _p(seeds), C.c_longlong(m), C.byref(p), *outs)
     if rc:
         raise ValueError("oracle_twist: argument error %d" % rc)
     return out

@@ -89,6 +89,23 @@
  *       evaluation), STALL 4, MIXED 8, OUTSIDE 16 (seed outside the box),
  *       ROTATED 32, CHORD 64. Q and Tw are NaN when MAXSTEPS, NULL_B or OUTSIDE
  *       is set; Q is NaN when MIXED is set.
+ *   R16 Stretched (rectilinear) grids, Sec. 2.2 and 2.3: the nodes are
+ *       x_i, y_j, z_k from three increasing coordinate arrays. The cell of a
+ *       point is the largest i in [0, n-2] with x_i <= x (a binary search;
+ *       points below x_0 and NaN map to cell 0), and the weights are Eqs. w0,
+ *       w1 as written, omega_0 = (x_{i+1} - x)/(x_{i+1} - x_i). The state is the
+ *       physical position. Each trial step takes the widths D_a of the cell
+ *       holding its start point and integrates dr/dtau = B/|bt| with bt_a =
+ *       B_a/D_a: the step is step x scaling and the tolerance tol x scaling of
+ *       the paper's stretched-grid rule, with scaling = |B|/|bt| evaluated
+ *       along the step instead of once per cell. The error is |(r5 - r4)_a/D_a|
+ *       (cells of the start cell), so on a uniform grid this is R1-R2 in exact
+ *       arithmetic. The exit step uses x_a itself as the independent variable;
+ *       its grazing test is on (dr_a/dtau)/D_a. Curl B uses the 2nd-order
+ *       three-point differences of a non-uniform axis (the derivative of the
+ *       quadratic through the three nodes; one-sided on the faces), which are
+ *       the R4 stencils on a uniform axis. Method II is not defined on a
+ *       stretched grid here.
  *   R13 Derivatives (the paper has none; the adjoint tests): d(Q, Tw)/dB is
  *       that of the traced computation with each line's accepted step sizes,
  *       exit faces and exit kinds (exit step, clamped exit step, chord after
@@ -136,6 +153,7 @@ typedef struct {
     long long n[3];
     double o[3], d[3];
     const double *B, *J, *G;
+    const double *X[3]; /* stretched grid (R16): node coordinates per axis; NULL = uniform */
 } OField;
 
 typedef struct {
@@ -181,6 +199,54 @@ static double o_dnode(const double *f, int nc, int c, long long node, long long 
     if (i == n - 1) return (3.0 * F_(n - 1) - 4.0 * F_(n - 2) + F_(n - 3)) / (2.0 * h);
     return (F_(i + 1) - F_(i - 1)) / (2.0 * h);
 #undef F_
+}
+
+/* d f/d x_a at node index i along an axis with node coordinates X (R16):
+ * the derivative of the quadratic through three neighbouring nodes,
+ * one-sided at the ends, first order when n = 2. */
+static double o_dnode_rect(const double *f, int nc, int c, long long node, long long stride, long long i,
+                           long long n, const double *X)
+{
+#define F_(k) f[(node + ((long long)(k) - i) * stride) * nc + c]
+    if (n == 2) return (F_(1) - F_(0)) / (X[1] - X[0]);
+    if (i == 0) {
+        double h1 = X[1] - X[0], h2 = X[2] - X[1];
+        return -(2.0 * h1 + h2) / (h1 * (h1 + h2)) * F_(0) + (h1 + h2) / (h1 * h2) * F_(1) -
+               h1 / (h2 * (h1 + h2)) * F_(2);
+    }
+    if (i == n - 1) {
+        double h1 = X[n - 2] - X[n - 3], h2 = X[n - 1] - X[n - 2];
+        return h2 / (h1 * (h1 + h2)) * F_(n - 3) - (h1 + h2) / (h1 * h2) * F_(n - 2) +
+               (h1 + 2.0 * h2) / (h2 * (h1 + h2)) * F_(n - 1);
+    }
+    double h1 = X[i] - X[i - 1], h2 = X[i + 1] - X[i];
+    return -h2 / (h1 * (h1 + h2)) * F_(i - 1) + (h2 - h1) / (h1 * h2) * F_(i) + h1 / (h2 * (h1 + h2)) * F_(i + 1);
+#undef F_
+}
+
+/* J = curl B at every node of a stretched grid; X = x (n0), y (n1), z (n2)
+ * coordinates back to back. */
+int oracle_curl_rect(const double *B, const long long n[3], const double *X, double *J)
+{
+    if (n[0] < 2 || n[1] < 2 || n[2] < 2) return 1;
+    const double *xs = X, *ys = X + n[0], *zs = X + n[0] + n[1];
+    long long sx = 1, sy = n[0], sz = n[0] * n[1];
+#pragma omp parallel for schedule(static)
+    for (long long k = 0; k < n[2]; k++)
+        for (long long j = 0; j < n[1]; j++)
+            for (long long i = 0; i < n[0]; i++) {
+                long long node = (k * n[1] + j) * n[0] + i;
+                double dyBz = o_dnode_rect(B, 3, 2, node, sy, j, n[1], ys);
+                double dzBy = o_dnode_rect(B, 3, 1, node, sz, k, n[2], zs);
+                double dzBx = o_dnode_rect(B, 3, 0, node, sz, k, n[2], zs);
+                double dxBz = o_dnode_rect(B, 3, 2, node, sx, i, n[0], xs);
+                double dxBy = o_dnode_rect(B, 3, 1, node, sx, i, n[0], xs);
+                double dyBx = o_dnode_rect(B, 3, 0, node, sy, j, n[1], ys);
+                J[node * 3 + 0] = dyBz - dzBy;
+                J[node * 3 + 1] = dzBx - dxBz;
+                J[node * 3 + 2] = dxBy - dyBx;
+            }
+    return 0;
 }
 
 /* J = curl B at every node (the curl grid used by Eq. tw). */
@@ -236,11 +302,32 @@ int oracle_gradb(const double *B, const long long n[3], const double d[3], doubl
 /* ------------------------------------------------------------------ */
 /* trilinear interpolation (Sec. 2.2, Eqs. interp, w0, w1; R3)         */
 
+/* stretched grid (R16): the cell of coordinate x on an axis with n nodes X */
+static long long o_cell_rect(const double *X, long long n, double x)
+{
+    if (!(x >= X[0])) return 0; /* also NaN */
+    long long lo = 0, hi = n - 2;  /* invariant: X[lo] <= x */
+    while (lo < hi) {
+        long long mid = (lo + hi + 1) / 2;
+        if (X[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 static void o_interp(const OField *f, const double *arr, int nc, const double xi[3], double *out)
 {
     long long i[3];
     double w[3][2];
     for (int a = 0; a < 3; a++) {
+        if (f->X[a]) {
+            /* stretched grid: binary search, Eq. w0 in physical coordinates */
+            const double *X = f->X[a];
+            i[a] = o_cell_rect(X, f->n[a], xi[a]);
+            w[a][0] = (X[i[a] + 1] - xi[a]) / (X[i[a] + 1] - X[i[a]]);
+            w[a][1] = 1.0 - w[a][0];
+            continue;
+        }
         double c = floor(xi[a]);            /* uniform grid: floor of x/spacing */
         if (!(c >= 0.0)) c = 0.0;           /* also maps NaN to cell 0 */
         if (c > (double)(f->n[a] - 2)) c = (double)(f->n[a] - 2);
@@ -281,21 +368,28 @@ static int o_unit_b(const OField *f, const double xi[3], double bh[3])
     return 0;
 }
 
-/* dy/dtau for the state y (ns = 5 or 11 comps); sigma = +1 forward, -1 backward.
+/* dy/dtau for the state y (ns = 5 or 11 comps); sigma = +1 forward, -1 backward;
+ * D = the cell widths that normalise bt (the spacing on a uniform grid).
  * Returns 1 on a null / non-finite field. */
-static int o_rhs(const OField *f, const OParams *p, double sigma, int ns, const double *y, double *dy)
+static int o_rhs(const OField *f, const OParams *p, const double *D, double sigma, int ns, const double *y,
+                 double *dy)
 {
     double B[3], bt[3];
     o_interp(f, f->B, 3, y, B);
     double bb = 0.0, BB = 0.0;
     for (int a = 0; a < 3; a++) {
-        bt[a] = B[a] / f->d[a];
+        bt[a] = B[a] / D[a];
         bb += bt[a] * bt[a];
         BB += B[a] * B[a];
     }
     if (!(bb > 0.0) || !isfinite(bb)) return 1;
     double nbt = sqrt(bb), nB = sqrt(BB);
-    for (int a = 0; a < 3; a++) dy[a] = sigma * bt[a] / nbt;
+    if (f->X[0]) {
+        /* stretched grid (R16): physical velocity B/|bt| */
+        for (int a = 0; a < 3; a++) dy[a] = sigma * B[a] / nbt;
+    } else {
+        for (int a = 0; a < 3; a++) dy[a] = sigma * bt[a] / nbt;
+    }
     double dl = nB / nbt; /* ds/dtau: physical arc length per cell of tau */
     dy[3] = dl;
     if (f->J) {
@@ -351,12 +445,13 @@ static const double FB4[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.
 static const double FB5[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0,
                               2.0 / 55.0};
 
-/* One RKF45 step of size h from y. With haxis >= 0 the independent variable is
- * xi[haxis] (Henon step, R5): the RHS is divided by its haxis component, which
- * must be >= graze in the outward direction hsign at every stage.
+/* One RKF45 step of size h from y (D: see o_rhs). With haxis >= 0 the
+ * independent variable is y[haxis] (Henon step, R5): the RHS is divided by its
+ * haxis component, which must be >= graze in the outward direction hsign at
+ * every stage.
  * Returns 0 ok, 1 null field, 2 grazing. y5 may be NULL. */
-static int o_rkf45(const OField *f, const OParams *p, double sigma, int ns, int haxis, double hsign,
-                   const double *y, double h, double *y4, double *y5)
+static int o_rkf45(const OField *f, const OParams *p, const double *D, double sigma, int ns, int haxis,
+                   double hsign, const double *y, double h, double *y4, double *y5)
 {
     double k[6][NSTATE], ys[NSTATE];
     for (int s = 0; s < 6; s++) {
@@ -365,10 +460,11 @@ static int o_rkf45(const OField *f, const OParams *p, double sigma, int ns, int 
             for (int r = 0; r < s; r++) acc += FA[s][r] * k[r][c];
             ys[c] = y[c] + h * acc;
         }
-        if (o_rhs(f, p, sigma, ns, ys, k[s])) return 1;
+        if (o_rhs(f, p, D, sigma, ns, ys, k[s])) return 1;
         if (haxis >= 0) {
             double fa = k[s][haxis];
-            if (!(fa * hsign >= p->graze)) return 2;
+            double fn = f->X[0] ? fa / D[haxis] : fa; /* in cells per unit tau (R16) */
+            if (!(fn * hsign >= p->graze)) return 2;
             for (int c = 0; c < ns; c++) k[s][c] = k[s][c] / fa;
         }
     }
@@ -384,14 +480,35 @@ static int o_rkf45(const OField *f, const OParams *p, double sigma, int ns, int 
     return 0;
 }
 
+/* the box in state coordinates: [0, n-1] cells, or [x_0, x_{n-1}] (R16) */
+static double o_lo(const OField *f, int a) { return f->X[a] ? f->X[a][0] : 0.0; }
+static double o_hi(const OField *f, int a) { return f->X[a] ? f->X[a][f->n[a] - 1] : (double)(f->n[a] - 1); }
+
 static int o_inside(const OField *f, const double *xi)
 {
     for (int a = 0; a < 3; a++)
-        if (!(xi[a] >= 0.0 && xi[a] <= (double)(f->n[a] - 1))) return 0;
+        if (!(xi[a] >= o_lo(f, a) && xi[a] <= o_hi(f, a))) return 0;
     return 1;
 }
 
-static double o_face_value(const OField *f, int face) { return (face & 1) ? (double)(f->n[face >> 1] - 1) : 0.0; }
+static double o_face_value(const OField *f, int face) { return (face & 1) ? o_hi(f, face >> 1) : o_lo(f, face >> 1); }
+
+/* widths of the cell holding y (the spacing on a uniform grid) */
+static void o_widths(const OField *f, const double *y, double D[3])
+{
+    for (int a = 0; a < 3; a++) {
+        if (f->X[a]) {
+            long long c = o_cell_rect(f->X[a], f->n[a], y[a]);
+            D[a] = f->X[a][c + 1] - f->X[a][c];
+        } else {
+            D[a] = f->d[a];
+        }
+    }
+}
+
+/* state <-> physical coordinates */
+static double o_phys(const OField *f, const double *y, int a) { return f->X[a] ? y[a] : f->o[a] + f->d[a] * y[a]; }
+static double o_state(const OField *f, const double *r, int a) { return f->X[a] ? r[a] : (r[a] - f->o[a]) / f->d[a]; }
 
 /* face first crossed by the chord from y (inside) to yn (outside); t = chord parameter */
 static int o_chord_face(const OField *f, const double *y, const double *yn, double *tout)
@@ -399,10 +516,10 @@ static int o_chord_face(const OField *f, const double *y, const double *yn, doub
     int best = -1;
     double tb = INFINITY;
     for (int a = 0; a < 3; a++) {
-        double hi = (double)(f->n[a] - 1), t;
+        double lo = o_lo(f, a), hi = o_hi(f, a), t;
         int fc;
-        if (yn[a] < 0.0) {
-            t = (0.0 - y[a]) / (yn[a] - y[a]);
+        if (yn[a] < lo) {
+            t = (lo - y[a]) / (yn[a] - y[a]);
             fc = 2 * a;
         } else if (yn[a] > hi) {
             t = (hi - y[a]) / (yn[a] - y[a]);
@@ -425,7 +542,7 @@ static int o_trace_dir(const OField *f, const OParams *p, double tol, double sig
                        double *yend, int *face, long long *steps, int *status, OLog *log)
 {
     o_log(log, sigma, 99);
-    double y[NSTATE], y4[NSTATE], y5[NSTATE], yt[NSTATE];
+    double y[NSTATE], y4[NSTATE], y5[NSTATE], yt[NSTATE], D[3];
     memcpy(y, yseed, sizeof(double) * ns);
     double h = p->h0;
     *face = -1;
@@ -436,13 +553,18 @@ static int o_trace_dir(const OField *f, const OParams *p, double tol, double sig
             return 1;
         }
         (*steps)++;
-        if (o_rkf45(f, p, sigma, ns, -1, 0.0, y, h, y4, y5)) {
+        o_widths(f, y, D);
+        if (o_rkf45(f, p, D, sigma, ns, -1, 0.0, y, h, y4, y5)) {
             *status |= ST_NULL;
             memcpy(yend, y, sizeof(double) * ns);
             return 1;
         }
         double e2 = 0.0;
-        for (int a = 0; a < 3; a++) e2 += (y5[a] - y4[a]) * (y5[a] - y4[a]);
+        if (f->X[0]) {
+            for (int a = 0; a < 3; a++) e2 += ((y5[a] - y4[a]) / D[a]) * ((y5[a] - y4[a]) / D[a]);
+        } else {
+            for (int a = 0; a < 3; a++) e2 += (y5[a] - y4[a]) * (y5[a] - y4[a]);
+        }
         double err = sqrt(e2);
         if (err > tol) {
             if (h > p->hmin) {
@@ -469,7 +591,7 @@ static int o_trace_dir(const OField *f, const OParams *p, double tol, double sig
             int a = fc >> 1;
             double target = o_face_value(f, fc), hsign = (fc & 1) ? 1.0 : -1.0;
             (*steps)++;
-            int r = o_rkf45(f, p, sigma, ns, a, hsign, y, target - y[a], yt, NULL);
+            int r = o_rkf45(f, p, D, sigma, ns, a, hsign, y, target - y[a], yt, NULL);
             if (r == 1) {
                 *status |= ST_NULL;
                 memcpy(yend, y, sizeof(double) * ns);
@@ -483,8 +605,8 @@ static int o_trace_dir(const OField *f, const OParams *p, double tol, double sig
             int nf = -1;
             for (int b = 0; b < 3 && nf < 0; b++) {
                 if (b == a) continue;
-                if (yt[b] < 0.0) nf = 2 * b;
-                else if (yt[b] > (double)(f->n[b] - 1)) nf = 2 * b + 1;
+                if (yt[b] < o_lo(f, b)) nf = 2 * b;
+                else if (yt[b] > o_hi(f, b)) nf = 2 * b + 1;
             }
             if (nf < 0) {
                 o_log(log, 0.0, 16 + fc);
@@ -494,8 +616,8 @@ static int o_trace_dir(const OField *f, const OParams *p, double tol, double sig
             }
             if (tries >= 2) {
                 for (int b = 0; b < 3; b++) {
-                    if (yt[b] < 0.0) yt[b] = 0.0;
-                    if (yt[b] > (double)(f->n[b] - 1)) yt[b] = (double)(f->n[b] - 1);
+                    if (yt[b] < o_lo(f, b)) yt[b] = o_lo(f, b);
+                    if (yt[b] > o_hi(f, b)) yt[b] = o_hi(f, b);
                 }
                 o_log(log, 0.0, 40 + fc);
                 memcpy(yend, yt, sizeof(double) * ns);
@@ -530,7 +652,7 @@ static void o_trace_line_log(const OField *f, const OParams *p, const double r0[
     double y0[NSTATE];
     memset(L, 0, sizeof *L);
     L->face[0] = L->face[1] = -1;
-    for (int a = 0; a < 3; a++) y0[a] = (r0[a] - f->o[a]) / f->d[a];
+    for (int a = 0; a < 3; a++) y0[a] = o_state(f, r0, a);
     y0[3] = 0.0;
     y0[4] = 0.0;
     if (ns == NSTATE)
@@ -543,8 +665,9 @@ static void o_trace_line_log(const OField *f, const OParams *p, const double r0[
         L->status |= ST_OUTSIDE;
         return;
     }
-    double dy[NSTATE];
-    if (o_rhs(f, p, 1.0, ns, y0, dy)) {
+    double dy[NSTATE], D0[3];
+    o_widths(f, y0, D0);
+    if (o_rhs(f, p, D0, 1.0, ns, y0, dy)) {
         L->status |= ST_NULL;
         return;
     }
@@ -596,7 +719,7 @@ static void o_face_coords(const OField *f, const double *xi, int face, double fc
 {
     int a = face >> 1, k = 0;
     for (int b = 0; b < 3; b++)
-        if (b != a) fc[k++] = f->o[b] + f->d[b] * xi[b];
+        if (b != a) fc[k++] = o_phys(f, xi, b);
 }
 
 static int o_line_ok(const OLine *L) { return L && !(L->status & ST_BAD); }
@@ -681,8 +804,8 @@ static int o_on_face(const OField *f, const double n0[3], const double r[3])
         else axis = a;
     }
     if (zeros != 2) return 0;
-    double xi = (r[axis] - f->o[axis]) / f->d[axis];
-    return xi == 0.0 || xi == (double)(f->n[axis] - 1);
+    double xi = o_state(f, r, axis);
+    return xi == o_lo(f, axis) || xi == o_hi(f, axis);
 }
 
 typedef struct {
@@ -702,7 +825,7 @@ static void o_seed_setup(const OField *f, const OParams *p, const OLattice *L, l
     double m = sqrt(o_dot(nn, nn));
     for (int a = 0; a < 3; a++) S->n0[a] = nn[a] / m;
     double xi[3], B[3];
-    for (int a = 0; a < 3; a++) xi[a] = (S->r0[a] - f->o[a]) / f->d[a];
+    for (int a = 0; a < 3; a++) xi[a] = o_state(f, S->r0, a);
     if (!o_inside(f, xi)) {
         S->bad = ST_OUTSIDE;
         return;
@@ -741,8 +864,8 @@ static void o_write(const OField *f, const OLine *c, long long s, double Q, doub
     if (Two) Two[s] = bad ? NAN : c->end[0][4] + c->end[1][4];
     if (leno) leno[s] = bad ? NAN : c->end[0][3] + c->end[1][3];
     for (int a = 0; a < 3; a++) {
-        if (r1) r1[3 * s + a] = f->o[a] + f->d[a] * c->end[0][a];
-        if (r2) r2[3 * s + a] = f->o[a] + f->d[a] * c->end[1][a];
+        if (r1) r1[3 * s + a] = o_phys(f, c->end[0], a);
+        if (r2) r2[3 * s + a] = o_phys(f, c->end[1], a);
     }
     if (f1) f1[s] = c->face[0];
     if (f2) f2[s] = c->face[1];
@@ -762,12 +885,38 @@ static int o_make_field(OField *f, const double *B, const double *J, const doubl
     f->B = B;
     f->J = J;
     f->G = G;
+    f->X[0] = f->X[1] = f->X[2] = NULL;
+    return 0;
+}
+
+/* stretched grid (R16): X = x, y, z node coordinates back to back, each
+ * strictly increasing */
+static int o_make_field_rect(OField *f, const double *B, const double *J, const long long n[3], const double *X)
+{
+    long long off = 0;
+    for (int a = 0; a < 3; a++) {
+        if (n[a] < 2) return 1;
+        f->n[a] = n[a];
+        f->X[a] = X + off;
+        for (long long i = 0; i + 1 < n[a]; i++)
+            if (!(f->X[a][i + 1] > f->X[a][i])) return 1;
+        f->o[a] = f->X[a][0];
+        f->d[a] = NAN; /* not used on a stretched grid */
+        off += n[a];
+    }
+    f->B = B;
+    f->J = J;
+    f->G = NULL;
     return 0;
 }
 
 /* Q, Tw, length, footpoints, faces, status and step counts on a seed lattice.
  * ln = {n1, n2, n3}; a3 = 0 and n3 = 1 for a plane. sample = linear lattice
  * indices (i + n1 (j + n2 k)) to compute, or NULL for the whole lattice. */
+static int o_qmap(const OField *fp, const double lo[3], const double a1[3], const double a2[3], const double a3[3],
+                  const long long ln[3], const OParams *p, const long long *sample, long long nsample, double *Qo,
+                  double *Two, double *leno, double *r1, double *r2, int *f1, int *f2, int *st, long long *steps);
+
 int oracle_qmap(const double *B, const double *J, const double *G, const long long n[3], const double o[3],
                 const double d[3], const double lo[3], const double a1[3], const double a2[3], const double a3[3],
                 const long long ln[3], const OParams *p, const long long *sample, long long nsample, double *Qo,
@@ -776,6 +925,26 @@ int oracle_qmap(const double *B, const double *J, const double *G, const long lo
     OField f;
     if (o_make_field(&f, B, J, G, n, o, d)) return 1;
     if (p->method == 2 && p->way == 1 && !G) return 2;
+    return o_qmap(&f, lo, a1, a2, a3, ln, p, sample, nsample, Qo, Two, leno, r1, r2, f1, f2, st, steps);
+}
+
+/* The same on a stretched grid (R16; Method I only). */
+int oracle_qmap_rect(const double *B, const double *J, const long long n[3], const double *X, const double lo[3],
+                     const double a1[3], const double a2[3], const double a3[3], const long long ln[3],
+                     const OParams *p, const long long *sample, long long nsample, double *Qo, double *Two,
+                     double *leno, double *r1, double *r2, int *f1, int *f2, int *st, long long *steps)
+{
+    OField f;
+    if (o_make_field_rect(&f, B, J, n, X)) return 1;
+    if (p->method != 1) return 2;
+    return o_qmap(&f, lo, a1, a2, a3, ln, p, sample, nsample, Qo, Two, leno, r1, r2, f1, f2, st, steps);
+}
+
+static int o_qmap(const OField *fp, const double lo[3], const double a1[3], const double a2[3], const double a3[3],
+                  const long long ln[3], const OParams *p, const long long *sample, long long nsample, double *Qo,
+                  double *Two, double *leno, double *r1, double *r2, int *f1, int *f2, int *st, long long *steps)
+{
+    const OField f = *fp;
     OLattice L;
     for (int a = 0; a < 3; a++) {
         L.o[a] = lo[a];
@@ -803,7 +972,7 @@ int oracle_qmap(const double *B, const double *J, const double *G, const long lo
             c.face[0] = c.face[1] = -1;
             c.status = S.bad;
             for (int e = 0; e < 2; e++)
-                for (int a = 0; a < 3; a++) c.end[e][a] = (S.r0[a] - f.o[a]) / f.d[a];
+                for (int a = 0; a < 3; a++) c.end[e][a] = o_state(&f, S.r0, a);
             o_write(&f, &c, s, NAN, Qo, Two, leno, r1, r2, f1, f2, st, steps);
             continue;
         }
@@ -847,18 +1016,55 @@ int oracle_qmap(const double *B, const double *J, const double *G, const long lo
 }
 
 /* Tw, length and footpoints for an explicit list of physical seeds (no Q). */
-int oracle_twist(const double *B, const double *J, const long long n[3], const double o[3], const double d[3],
-                 const double *seeds, long long ns, const OParams *p, double *Two, double *leno, double *r1,
-                 double *r2, int *f1, int *f2, int *st, long long *steps)
+static int o_twist(const OField *fp, const double *seeds, long long ns, const OParams *p, double *Two, double *leno,
+                   double *r1, double *r2, int *f1, int *f2, int *st, long long *steps)
 {
-    OField f;
-    if (o_make_field(&f, B, J, NULL, n, o, d)) return 1;
+    const OField f = *fp;
 #pragma omp parallel for schedule(dynamic, 4)
     for (long long s = 0; s < ns; s++) {
         OLine c;
         o_trace_line(&f, p, seeds + 3 * s, NULL, p->tol, NULL, NULL, &c);
         o_write(&f, &c, s, NAN, NULL, Two, leno, r1, r2, f1, f2, st, steps);
     }
+    return 0;
+}
+
+int oracle_twist(const double *B, const double *J, const long long n[3], const double o[3], const double d[3],
+                 const double *seeds, long long ns, const OParams *p, double *Two, double *leno, double *r1,
+                 double *r2, int *f1, int *f2, int *st, long long *steps)
+{
+    OField f;
+    if (o_make_field(&f, B, J, NULL, n, o, d)) return 1;
+    return o_twist(&f, seeds, ns, p, Two, leno, r1, r2, f1, f2, st, steps);
+}
+
+/* Tw, length and footpoints on a stretched grid (R16). */
+int oracle_twist_rect(const double *B, const double *J, const long long n[3], const double *X, const double *seeds,
+                      long long ns, const OParams *p, double *Two, double *leno, double *r1, double *r2, int *f1,
+                      int *f2, int *st, long long *steps)
+{
+    OField f;
+    if (o_make_field_rect(&f, B, J, n, X)) return 1;
+    return o_twist(&f, seeds, ns, p, Two, leno, r1, r2, f1, f2, st, steps);
+}
+
+/* Trilinear interpolation (Eqs. interp, w0, w1) on a stretched grid at
+ * physical points r (np x 3). */
+int oracle_interp_rect(const double *arr, int nc, const long long n[3], const double *X, const double *r,
+                       long long np, double *out)
+{
+    OField f;
+    memset(&f, 0, sizeof f);
+    if (o_make_field_rect(&f, arr, NULL, n, X)) return 1;
+    for (long long k = 0; k < np; k++) o_interp(&f, arr, nc, r + 3 * k, out + (long long)nc * k);
+    return 0;
+}
+
+/* Cell index of each coordinate on one stretched axis (for tests). */
+int oracle_cell_rect(const double *X, long long n, const double *x, long long m, long long *out)
+{
+    if (n < 2) return 1;
+    for (long long k = 0; k < m; k++) out[k] = o_cell_rect(X, n, x[k]);
     return 0;
 }
 

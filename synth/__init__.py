@@ -2,12 +2,16 @@
 oracle tests, the CUDA parity tests and the benchmark.
 
 This package only *generates inputs*: it samples analytic or point-source
-magnetic fields on uniform grids. It holds none of the method's arithmetic
+magnetic fields on uniform or stretched (rectilinear) grids. It holds none of the method's arithmetic
 (no curl, no interpolation, no tracing, no Q), so both the CPU oracle and the
 CUDA library can be fed from it without sharing any computation.
 """
 from .fields import (  # noqa: F401
     Grid,
+    RectGrid,
+    stretched_axis,
+    stretched_grid,
+    c2_stretched,
     analytic_cube,
     monopole_cube,
     random_charges,

@@ -2,7 +2,8 @@
 
 Layout of every cube returned here: a C-contiguous array of shape
 (nz, ny, nx, 3) (x fastest, the three Cartesian components innermost),
-sampled at the nodes x_i = origin_x + i * spacing_x (and likewise for y, z).
+sampled at the nodes x_i = origin_x + i * spacing_x (and likewise for y, z),
+or at the node coordinates of a stretched RectGrid.
 
 Workloads (stand-ins for the paper's active-region extrapolation and TD99
 runs, whose data are not available):
@@ -42,6 +43,58 @@ class Grid:
 
     def axis(self, a):
         return self.origin[a] + self.spacing[a] * np.arange(self.n[a], dtype=np.float64)
+
+
+@dataclass(frozen=True)
+class RectGrid:
+    """Stretched (rectilinear) grid: strictly increasing node coordinates per
+    axis, ``coords`` = (x, y, z) as tuples of floats."""
+
+    coords: tuple
+
+    @property
+    def n(self):
+        return tuple(len(c) for c in self.coords)
+
+    @property
+    def shape(self):
+        nx, ny, nz = self.n
+        return (nz, ny, nx, 3)
+
+    @property
+    def origin(self):
+        return tuple(float(c[0]) for c in self.coords)
+
+    @property
+    def hi(self):
+        return tuple(float(c[-1]) for c in self.coords)
+
+    def axis(self, a):
+        return np.asarray(self.coords[a], dtype=np.float64)
+
+
+def stretched_axis(n: int, lo: float, hi: float, ratio: float, kind: str = "bottom"):
+    """n node coordinates from lo to hi whose cell widths grow geometrically by
+    ``ratio`` per cell: from the low end ('bottom') or from the middle towards
+    both ends ('edges'). ratio = 1 gives the uniform axis."""
+    m = n - 1
+    if kind == "bottom":
+        e = np.arange(m, dtype=np.float64)
+    elif kind == "edges":
+        e = np.abs(np.arange(m, dtype=np.float64) - 0.5 * (m - 1))
+    else:
+        raise ValueError(kind)
+    w = ratio ** e
+    x = np.concatenate([[0.0], np.cumsum(w)])
+    x = lo + (hi - lo) * x / x[-1]
+    x[0], x[-1] = lo, hi
+    return tuple(float(v) for v in x)
+
+
+def stretched_grid(n, lo, hi, ratios=(1.01, 1.01, 1.02), kinds=("edges", "edges", "bottom")):
+    """RectGrid over the box [lo, hi] with the axes of stretched_axis."""
+    return RectGrid(tuple(stretched_axis(int(n[a]), float(lo[a]), float(hi[a]), ratios[a], kinds[a])
+                          for a in range(3)))
 
 
 def _grid_from_box(n, lo, hi):
@@ -164,6 +217,19 @@ def monopole_cube(grid: Grid, charges, dtype=np.float32, device=None):
             acc[..., 2] += s * dz
         out[k] = acc.astype(dtype)
     return out
+
+
+def c2_stretched(seed: int = 2208, n=(256, 256, 128), count: int = 24, dtype=np.float32,
+                 ratios=(1.01, 1.01, 1.02)):
+    """The 24-monopole field of c2_monopole (same sources) sampled on a
+    stretched grid over the same box: horizontal cells growing by ratios[0],
+    ratios[1] per cell from the middle to the edges, vertical cells by
+    ratios[2] per cell upward. Returns (B, RectGrid, charges)."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = n
+    ch = random_charges(rng, count, ((0.0, nx - 1.0), (0.0, ny - 1.0)))
+    grid = stretched_grid(n, (0.0, 0.0, 0.0), (nx - 1.0, ny - 1.0, nz - 1.0), ratios)
+    return monopole_cube(grid, ch, dtype=dtype), grid, ch
 
 
 def c2_monopole(seed: int = 2208, n=(256, 256, 128), count: int = 24, dtype=np.float32,
