@@ -18,9 +18,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 # Translation units whose FP64 arithmetic must round like a plain evaluation
-# of the method (no fused multiply-add contraction): the FP64 tracer, the curl
-# grid and the Q assembly. The FP32 tracer keeps contraction.
-NO_FMAD = {"trace_f64.cu", "field.cu", "assemble.cu"}
+# of the method (no fused multiply-add contraction): the FP64 tracers, the curl
+# grid and the Q assembly. The FP32 tracers keep contraction.
+NO_FMAD = {"trace_f64.cu", "trace_rect_f64.cu", "field.cu", "assemble.cu"}
 
 
 def nvcc() -> str:

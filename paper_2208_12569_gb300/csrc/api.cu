@@ -63,6 +63,7 @@ struct fqsl_field_s {
     void *grad32 = nullptr, *grad64 = nullptr;  // Method II way 1 gradient grid
     void *scratch = nullptr;
     size_t scratch_cap = 0;
+    void *rect_buf = nullptr;  // stretched grid: coordinate, width and bucket tables (FieldView::x64 ...)
     unsigned long long *counters = nullptr;  // [0] primary head, [1] extra head, [2] rotated count (low 32 bits)
     int blocks_cache[3][3] = {};  // [precision][source] resident blocks per SM
     int blocks_cache_m2[2][2] = {};  // Method II: [fp64][way - 1]
@@ -92,6 +93,94 @@ namespace {
 void mark(fqsl_field f, int i, cudaStream_t s)
 {
     if (f->timing) cudaEventRecord(f->ev[i], s);
+}
+
+// argument checks shared by the two field constructors
+fqsl_status check_create(const void *B_dev, fqsl_dtype b_dtype, long long nx, long long ny, long long nz,
+                         unsigned flags, fqsl_field *out, const char *who)
+{
+    if (!out) return fail(FQSL_ERR_ARG, "%s: out is NULL", who);
+    if (!B_dev) return fail(FQSL_ERR_ARG, "%s: B_dev is NULL", who);
+    if (b_dtype != FQSL_F32 && b_dtype != FQSL_F64)
+        return fail(FQSL_ERR_ARG, "%s: b_dtype must be FQSL_F32 or FQSL_F64", who);
+    if (nx < 2 || ny < 2 || nz < 2) return fail(FQSL_ERR_ARG, "%s: need nx, ny, nz >= 2", who);
+    if (nx >= (1 << 23) || ny >= (1 << 23) || nz >= (1 << 23) || nx * ny * nz >= (1LL << 31))
+        return fail(FQSL_ERR_ARG, "%s: grid too large (each axis < 2^23 nodes, < 2^31 nodes)", who);
+    if (!(flags & (FQSL_PACK_F32 | FQSL_PACK_F64)) || (flags & ~(FQSL_PACK_F32 | FQSL_PACK_F64 | FQSL_PACK_GRADB)))
+        return fail(FQSL_ERR_ARG, "%s: flags must hold FQSL_PACK_F32 and/or FQSL_PACK_F64 "
+                                  "(and optionally FQSL_PACK_GRADB)", who);
+    if (((uintptr_t)B_dev) % 16) return fail(FQSL_ERR_ARG, "%s: B_dev must be 16-byte aligned", who);
+    return FQSL_OK;
+}
+
+// B_dev must be device (or managed) memory; checked after the host-side
+// argument checks
+fqsl_status check_device_ptr(const void *B_dev, const char *who)
+{
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, B_dev);
+    if (e != cudaSuccess || (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return fail(FQSL_ERR_ARG, "%s: B_dev is not device memory", who);
+    }
+    return FQSL_OK;
+}
+
+void set_dims(fqsl_field f, long long nx, long long ny, long long nz)
+{
+    cudaGetDevice(&f->device);
+    cudaDeviceGetAttribute(&f->sms, cudaDevAttrMultiProcessorCount, f->device);
+    f->g.nx = (int)nx;
+    f->g.ny = (int)ny;
+    f->g.nz = (int)nz;
+    f->g.cmax[0] = (float)(nx - 2);
+    f->g.cmax[1] = (float)(ny - 2);
+    f->g.cmax[2] = (float)(nz - 2);
+    f->g.sy32 = (unsigned)(nx * 32);
+    f->g.sz32 = (unsigned)(nx * ny * 32 <= 0xffffffffLL ? nx * ny * 32 : 0);
+    f->g.nodes = nx * ny * nz;
+    f->g.err = nullptr;
+}
+
+// release everything a handle under construction may hold
+void free_field(fqsl_field f)
+{
+    cudaFree(f->rec32);
+    cudaFree(f->rec64);
+    cudaFree(f->grad32);
+    cudaFree(f->grad64);
+    cudaFree(f->counters);
+    cudaFree(f->rect_buf);
+    delete f;
+}
+
+// records, counters and the first packing of a handle whose geometry is set
+fqsl_status finish_create(fqsl_field f, const void *B_dev, fqsl_dtype b_dtype, unsigned flags, void *cuda_stream,
+                          fqsl_field *out, const char *who)
+{
+    const size_t nodes = (size_t)f->g.nodes;
+    cudaError_t e = cudaSuccess;
+    if (flags & FQSL_PACK_F32) e = cudaMalloc(&f->rec32, nodes * 32);
+    if (e == cudaSuccess && (flags & FQSL_PACK_F64)) e = cudaMalloc(&f->rec64, nodes * 64);
+    if (e == cudaSuccess && (flags & FQSL_PACK_GRADB)) {
+        if (f->rec32) e = cudaMalloc(&f->grad32, nodes * 48);
+        if (e == cudaSuccess && f->rec64) e = cudaMalloc(&f->grad64, nodes * 80);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&f->counters, 4 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_field(f);
+        return cuda_fail(e, who);
+    }
+    e = launch_curl_pack(B_dev, b_dtype, f->g, f->rec32, f->rec64, (cudaStream_t)cuda_stream);
+    if (e == cudaSuccess && (f->grad32 || f->grad64))
+        e = launch_gradb_pack(B_dev, b_dtype, f->g, f->grad32, f->grad64, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) {
+        free_field(f);
+        return cuda_fail(e, who);
+    }
+    *out = f;
+    return FQSL_OK;
 }
 }  // namespace
 
@@ -126,97 +215,137 @@ fqsl_status fqsl_field_create(const void *B_dev, fqsl_dtype b_dtype, long long n
                               fqsl_field *out)
 {
     g_err.clear();
-    if (!out) return fail(FQSL_ERR_ARG, "fqsl_field_create: out is NULL");
-    *out = nullptr;
-    if (!B_dev) return fail(FQSL_ERR_ARG, "fqsl_field_create: B_dev is NULL");
-    if (b_dtype != FQSL_F32 && b_dtype != FQSL_F64)
-        return fail(FQSL_ERR_ARG, "fqsl_field_create: b_dtype must be FQSL_F32 or FQSL_F64");
-    if (nx < 2 || ny < 2 || nz < 2) return fail(FQSL_ERR_ARG, "fqsl_field_create: need nx, ny, nz >= 2");
-    if (nx >= (1 << 23) || ny >= (1 << 23) || nz >= (1 << 23) || nx * ny * nz >= (1LL << 31))
-        return fail(FQSL_ERR_ARG, "fqsl_field_create: grid too large (each axis < 2^23 nodes, < 2^31 nodes)");
-    if (!finite3(origin) || !finite3(spacing))
-        return fail(FQSL_ERR_ARG, "fqsl_field_create: origin/spacing must be finite");
+    const char *who = "fqsl_field_create";
+    if (out) *out = nullptr;
+    fqsl_status st = check_create(B_dev, b_dtype, nx, ny, nz, flags, out, who);
+    if (st != FQSL_OK) return st;
+    if (!finite3(origin) || !finite3(spacing)) return fail(FQSL_ERR_ARG, "%s: origin/spacing must be finite", who);
     if (!(spacing[0] > 0 && spacing[1] > 0 && spacing[2] > 0))
-        return fail(FQSL_ERR_ARG, "fqsl_field_create: spacing must be > 0");
-    if (!(flags & (FQSL_PACK_F32 | FQSL_PACK_F64)) || (flags & ~(FQSL_PACK_F32 | FQSL_PACK_F64 | FQSL_PACK_GRADB)))
-        return fail(FQSL_ERR_ARG, "fqsl_field_create: flags must hold FQSL_PACK_F32 and/or FQSL_PACK_F64 "
-                                  "(and optionally FQSL_PACK_GRADB)");
-    if (((uintptr_t)B_dev) % 16) return fail(FQSL_ERR_ARG, "fqsl_field_create: B_dev must be 16-byte aligned");
-    cudaPointerAttributes attr;
-    cudaError_t e = cudaPointerGetAttributes(&attr, B_dev);
-    if (e != cudaSuccess || (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
-        cudaGetLastError();
-        return fail(FQSL_ERR_ARG, "fqsl_field_create: B_dev is not device memory");
-    }
+        return fail(FQSL_ERR_ARG, "%s: spacing must be > 0", who);
+    st = check_device_ptr(B_dev, who);
+    if (st != FQSL_OK) return st;
     fqsl_field f = new (std::nothrow) fqsl_field_s();
-    if (!f) return fail(FQSL_ERR_OOM, "fqsl_field_create: host allocation failed");
-    cudaGetDevice(&f->device);
-    cudaDeviceGetAttribute(&f->sms, cudaDevAttrMultiProcessorCount, f->device);
-    f->g.nx = (int)nx;
-    f->g.ny = (int)ny;
-    f->g.nz = (int)nz;
+    if (!f) return fail(FQSL_ERR_OOM, "%s: host allocation failed", who);
+    set_dims(f, nx, ny, nz);
     for (int a = 0; a < 3; a++) {
         f->g.o[a] = origin[a];
         f->g.d[a] = spacing[a];
+        f->g.rd[a] = (float)(1.0 / spacing[a]);
     }
-    for (int a = 0; a < 3; a++) f->g.rd[a] = (float)(1.0 / spacing[a]);
-    f->g.cmax[0] = (float)(nx - 2);
-    f->g.cmax[1] = (float)(ny - 2);
-    f->g.cmax[2] = (float)(nz - 2);
-    f->g.sy32 = (unsigned)(nx * 32);
-    f->g.sz32 = (unsigned)(nx * ny * 32 <= 0xffffffffLL ? nx * ny * 32 : 0);
-    f->g.nodes = nx * ny * nz;
-    f->g.err = nullptr;
-    const size_t nodes = (size_t)nx * ny * nz;
-    if (flags & FQSL_PACK_F32) {
-        e = cudaMalloc(&f->rec32, nodes * 32);
-        if (e != cudaSuccess) {
-            delete f;
-            return cuda_fail(e, "fqsl_field_create: FP32 records");
+    return finish_create(f, B_dev, b_dtype, flags, cuda_stream, out, who);
+}
+
+fqsl_status fqsl_field_create_rect(const void *B_dev, fqsl_dtype b_dtype, long long nx, long long ny, long long nz,
+                                   const double *x, const double *y, const double *z, unsigned flags,
+                                   void *cuda_stream, fqsl_field *out)
+{
+    g_err.clear();
+    const char *who = "fqsl_field_create_rect";
+    if (out) *out = nullptr;
+    fqsl_status st = check_create(B_dev, b_dtype, nx, ny, nz, flags, out, who);
+    if (st != FQSL_OK) return st;
+    if (flags & FQSL_PACK_GRADB) return fail(FQSL_ERR_ARG, "%s: no gradient grid on a stretched grid", who);
+    const double *X[3] = {x, y, z};
+    const long long N[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; a++) {
+        if (!X[a]) return fail(FQSL_ERR_ARG, "%s: coordinate array %d is NULL", who, a);
+        for (long long i = 0; i < N[a]; i++)
+            if (!isfinite(X[a][i])) return fail(FQSL_ERR_ARG, "%s: coordinate %d of axis %d is not finite", who, (int)i, a);
+        for (long long i = 0; i + 1 < N[a]; i++)
+            if (!(X[a][i + 1] > X[a][i]))
+                return fail(FQSL_ERR_ARG, "%s: axis %d coordinates are not strictly increasing at %lld", who, a, i);
+        if (flags & FQSL_PACK_F32)
+            for (long long i = 0; i + 1 < N[a]; i++)
+                if (!((float)(X[a][i + 1] - X[a][0]) > (float)(X[a][i] - X[a][0])))
+                    return fail(FQSL_ERR_ARG, "%s: axis %d cells %lld, %lld collapse in float (FP32 records)", who,
+                                a, i, i + 1);
+    }
+    st = check_device_ptr(B_dev, who);
+    if (st != FQSL_OK) return st;
+    // host tables: x64 | x32 | rw32 | buckets, one device buffer
+    std::vector<double> x64;
+    std::vector<float> x32, rw32;
+    std::vector<int> bkt;
+    long long nb[3];
+    for (int a = 0; a < 3; a++) {
+        const double *A = X[a];
+        const long long n = N[a];
+        const double L = A[n - 1] - A[0];
+        double wmin = INFINITY;
+        for (long long i = 0; i + 1 < n; i++) wmin = fmin(wmin, A[i + 1] - A[i]);
+        // buckets no wider than the narrowest cell, within [n - 1, 16 (n - 1)]
+        long long b = (long long)ceil(L / wmin);
+        if (b < n - 1) b = n - 1;
+        if (b > 16 * (n - 1)) b = 16 * (n - 1);
+        nb[a] = b;
+        for (long long i = 0; i < n; i++) {
+            x64.push_back(A[i]);
+            x32.push_back((float)(A[i] - A[0]));
+        }
+        for (long long i = 0; i + 1 < n; i++) {
+            const double w = (double)(float)(A[i + 1] - A[0]) - (double)(float)(A[i] - A[0]);
+            rw32.push_back((float)(1.0 / w));
+        }
+        for (long long k = 0; k < b; k++) {
+            // the cell of the bucket's lower end (largest i in [0, n-2] with A[i] <= t)
+            const double t = A[0] + (double)k * (L / (double)b);
+            long long lo = 0, hi = n - 2;
+            while (lo < hi) {
+                const long long mid = (lo + hi + 1) / 2;
+                if (A[mid] <= t) lo = mid;
+                else hi = mid - 1;
+            }
+            bkt.push_back((int)lo);
         }
     }
-    if (flags & FQSL_PACK_F64) {
-        e = cudaMalloc(&f->rec64, nodes * 64);
-        if (e != cudaSuccess) {
-            cudaFree(f->rec32);
-            delete f;
-            return cuda_fail(e, "fqsl_field_create: FP64 records");
-        }
-    }
-    if (flags & FQSL_PACK_GRADB) {
-        if (f->rec32) e = cudaMalloc(&f->grad32, nodes * 48);
-        if (e == cudaSuccess && f->rec64) e = cudaMalloc(&f->grad64, nodes * 80);
-        if (e != cudaSuccess) {
-            cudaFree(f->rec32);
-            cudaFree(f->rec64);
-            cudaFree(f->grad32);
-            delete f;
-            return cuda_fail(e, "fqsl_field_create: gradient records");
-        }
-    }
-    e = cudaMalloc(&f->counters, 4 * sizeof(unsigned long long));
+    fqsl_field f = new (std::nothrow) fqsl_field_s();
+    if (!f) return fail(FQSL_ERR_OOM, "%s: host allocation failed", who);
+    set_dims(f, nx, ny, nz);
+    const size_t b64 = align_up(x64.size() * sizeof(double)), b32 = align_up(x32.size() * sizeof(float)),
+                 brw = align_up(rw32.size() * sizeof(float)), bbk = align_up(bkt.size() * sizeof(int));
+    cudaError_t e = cudaMalloc(&f->rect_buf, b64 + b32 + brw + bbk);
     if (e != cudaSuccess) {
-        cudaFree(f->rec32);
-        cudaFree(f->rec64);
-        cudaFree(f->grad32);
-        cudaFree(f->grad64);
         delete f;
-        return cuda_fail(e, "fqsl_field_create: counters");
+        cudaGetLastError();
+        return cuda_fail(e, "fqsl_field_create_rect: coordinate tables");
     }
-    e = launch_curl_pack(B_dev, b_dtype, f->g, f->rec32, f->rec64, (cudaStream_t)cuda_stream);
-    if (e == cudaSuccess && (f->grad32 || f->grad64))
-        e = launch_gradb_pack(B_dev, b_dtype, f->g, f->grad32, f->grad64, (cudaStream_t)cuda_stream);
+    char *base = (char *)f->rect_buf;
+    e = cudaMemcpy(base, x64.data(), x64.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + b64, x32.data(), x32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base + b64 + b32, rw32.data(), rw32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base + b64 + b32 + brw, bkt.data(), bkt.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(f->rec32);
-        cudaFree(f->rec64);
-        cudaFree(f->grad32);
-        cudaFree(f->grad64);
-        cudaFree(f->counters);
+        cudaFree(f->rect_buf);
         delete f;
-        return cuda_fail(e, "fqsl_field_create: curl_pack launch");
+        return cuda_fail(e, "fqsl_field_create_rect: coordinate tables");
     }
-    *out = f;
-    return FQSL_OK;
+    FieldView &g = f->g;
+    g.rect = 1;
+    long long o64 = 0, orw = 0, obk = 0;
+    for (int a = 0; a < 3; a++) {
+        const long long n = N[a];
+        g.x64[a] = (const double *)base + o64;
+        g.x32[a] = (const float *)(base + b64) + o64;
+        g.rw32[a] = (const float *)(base + b64 + b32) + orw;
+        g.bkt[a] = (const int *)(base + b64 + b32 + brw) + obk;
+        g.nbkt[a] = (int)nb[a];
+        const double L = X[a][n - 1] - X[a][0];
+        g.bsc64[a] = (double)nb[a] / L;
+        g.bsc32[a] = (float)g.bsc64[a];
+        g.lo64[a] = X[a][0];
+        g.hi64[a] = X[a][n - 1];
+        g.hi32[a] = x32[o64 + n - 1];
+        // FP32 state = physical position relative to the first node
+        g.o[a] = X[a][0];
+        g.d[a] = 1.0;
+        g.rd[a] = 1.f;
+        o64 += n;
+        orw += n - 1;
+        obk += nb[a];
+    }
+    return finish_create(f, B_dev, b_dtype, flags, cuda_stream, out, who);
 }
 
 fqsl_status fqsl_field_update(fqsl_field f, const void *B_dev, fqsl_dtype b_dtype, void *cuda_stream)
@@ -282,6 +411,7 @@ fqsl_status fqsl_field_destroy(fqsl_field f)
     cudaFree(f->tp.buf);
     cudaFree(f->tp.work);
     cudaFree(f->counters);
+    cudaFree(f->rect_buf);
     delete f;
     return FQSL_OK;
 }
@@ -327,6 +457,9 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
         return fail(FQSL_ERR_UNSUPPORTED, "%s: field was not packed in FP64 (FQSL_PACK_F64)", who);
     if (p->method == 2 && p->gradb_way == 1 && !(p->precision == FQSL_F64 ? f->grad64 : f->grad32))
         return fail(FQSL_ERR_UNSUPPORTED, "%s: Method II way 1 needs a field packed with FQSL_PACK_GRADB", who);
+    if (f->g.rect && p->method != 1)
+        return fail(FQSL_ERR_UNSUPPORTED, "%s: Method II is not available on a stretched grid", who);
+    if (f->g.rect && p->tape) return fail(FQSL_ERR_UNSUPPORTED, "%s: no step tape on a stretched grid", who);
     return FQSL_OK;
 }
 
@@ -441,9 +574,14 @@ fqsl_status ensure_scratch(fqsl_field f, size_t bytes)
 int blocks_per_sm(fqsl_field f, int precision, int src)
 {
     int &c = f->blocks_cache[precision][src];
-    if (!c)
-        c = precision == FQSL_F64 ? trace_blocks_per_sm_f64(src)
-                                  : trace_blocks_per_sm_f32(src, precision == FQSL_F32_ACC64);
+    if (!c) {
+        if (f->g.rect)
+            c = precision == FQSL_F64 ? trace_rect_blocks_per_sm_f64(src)
+                                      : trace_rect_blocks_per_sm_f32(src, precision == FQSL_F32_ACC64);
+        else
+            c = precision == FQSL_F64 ? trace_blocks_per_sm_f64(src)
+                                      : trace_blocks_per_sm_f32(src, precision == FQSL_F32_ACC64);
+    }
     return c;
 }
 
@@ -1133,6 +1271,10 @@ extern "C" fqsl_status fqsl_batch_create(const fqsl_field *fields, const fqsl_pl
         if (st != FQSL_OK) {
             delete b;
             return st;
+        }
+        if (fields[k]->g.rect) {
+            delete b;
+            return fail(FQSL_ERR_UNSUPPORTED, "%s: batches take uniform grids only", who);
         }
         st = plane_lattice(fields[k], planes[k], p, lats[k], who);
         if (st != FQSL_OK) {

@@ -7,7 +7,9 @@
 // coordinates) by central differences when both neighbours end on the
 // centre's face, one-sided when one does, NaN and FQSL_LINE_MIXED otherwise.
 // Neighbouring footpoints are differenced in index space first (exact for
-// nearby values in float) and scaled by the spacing in FP64.
+// nearby values in float) and scaled by the spacing in FP64. On a stretched
+// grid the FP32 state is the physical position relative to the first node
+// (the field view's origin, with unit spacing), so the same forms apply.
 #include <math.h>
 
 #include "trace.cuh"
@@ -26,7 +28,8 @@ __device__ __forceinline__ void face_axes(int face, int &r0, int &r1)
 __device__ __forceinline__ double bn_at(const FieldView &f, const float *xi, int face)
 {
     float B[3], J[3];
-    trace::gather(f, xi[0], xi[1], xi[2], B, J);
+    if (f.rect) trace::gather_rect(f, xi[0], xi[1], xi[2], B, J);
+    else trace::gather(f, xi[0], xi[1], xi[2], B, J);
     const int a = face >> 1;
     return (double)(a == 0 ? B[0] : (a == 1 ? B[1] : B[2]));
 }

@@ -7,7 +7,9 @@
 // axis, and packed next to B so that one trilinear gather (Sec. 2.2, Eq.
 // interp) fetches both. FP64 records (and FP32 records of an FP64 cube) use
 // FP64 stencils written as plain expressions; FP32 records of an FP32 cube use
-// float stencils. One thread per node, grid-stride; streaming and HBM-bound.
+// float stencils. On a stretched grid the three-point stencils of a
+// non-uniform axis are used, in FP64. One thread per node, grid-stride;
+// streaming and HBM-bound.
 #include "fqsl_internal.cuh"
 
 namespace fqsl {
@@ -43,6 +45,64 @@ __global__ void __launch_bounds__(256) k_curl_pack(const TI *__restrict__ B, int
         const double dxBz = node_diff(B, 2, node, 1, i, nx, dx);
         const double dxBy = node_diff(B, 1, node, 1, i, nx, dx);
         const double dyBx = node_diff(B, 0, node, sy, j, ny, dy);
+        const double Jx = dyBz - dzBy, Jy = dzBx - dxBz, Jz = dxBy - dyBx;
+        const double Bx = (double)B[node * 3 + 0], By = (double)B[node * 3 + 1], Bz = (double)B[node * 3 + 2];
+        if (rec32) {
+            rec32[2 * node + 0] = make_float4((float)Bx, (float)By, (float)Bz, (float)Jx);
+            rec32[2 * node + 1] = make_float4((float)Jy, (float)Jz, 0.f, 0.f);
+        }
+        if (rec64) {
+            rec64[4 * node + 0] = make_double2(Bx, By);
+            rec64[4 * node + 1] = make_double2(Bz, Jx);
+            rec64[4 * node + 2] = make_double2(Jy, Jz);
+            rec64[4 * node + 3] = make_double2(0.0, 0.0);
+        }
+    }
+}
+
+// Stretched grid (Sec. 2.2): d f/d x_a at node index i along an axis with node
+// coordinates X, as the derivative of the quadratic through three
+// neighbouring nodes (one-sided at the ends, first order on a 2-node axis);
+// on a uniform axis these are the stencils above. Written as plain
+// expressions in a fixed order.
+template <typename TI>
+__device__ __forceinline__ double node_diff_rect(const TI *__restrict__ B, int c, long long node, long long stride,
+                                                 long long i, long long n, const double *__restrict__ X)
+{
+    auto F = [&](long long kk) -> double { return (double)B[(node + (kk - i) * stride) * 3 + c]; };
+    if (n == 2) return (F(1) - F(0)) / (X[1] - X[0]);
+    if (i == 0) {
+        const double h1 = X[1] - X[0], h2 = X[2] - X[1];
+        return -(2.0 * h1 + h2) / (h1 * (h1 + h2)) * F(0) + (h1 + h2) / (h1 * h2) * F(1) -
+               h1 / (h2 * (h1 + h2)) * F(2);
+    }
+    if (i == n - 1) {
+        const double h1 = X[n - 2] - X[n - 3], h2 = X[n - 1] - X[n - 2];
+        return h2 / (h1 * (h1 + h2)) * F(n - 3) - (h1 + h2) / (h1 * h2) * F(n - 2) +
+               (h1 + 2.0 * h2) / (h2 * (h1 + h2)) * F(n - 1);
+    }
+    const double h1 = X[i] - X[i - 1], h2 = X[i + 1] - X[i];
+    return -h2 / (h1 * (h1 + h2)) * F(i - 1) + (h2 - h1) / (h1 * h2) * F(i) + h1 / (h2 * (h1 + h2)) * F(i + 1);
+}
+
+template <typename TI>
+__global__ void __launch_bounds__(256) k_curl_pack_rect(const TI *__restrict__ B, const FieldView g,
+                                                        float4 *__restrict__ rec32, double2 *__restrict__ rec64)
+{
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const long long total = (long long)nx * ny * nz;
+    const long long sy = nx, sz = (long long)nx * ny;
+    for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < total;
+         node += (long long)gridDim.x * blockDim.x) {
+        const long long i = node % nx;
+        const long long j = (node / nx) % ny;
+        const long long k = node / sz;
+        const double dyBz = node_diff_rect(B, 2, node, sy, j, ny, g.x64[1]);
+        const double dzBy = node_diff_rect(B, 1, node, sz, k, nz, g.x64[2]);
+        const double dzBx = node_diff_rect(B, 0, node, sz, k, nz, g.x64[2]);
+        const double dxBz = node_diff_rect(B, 2, node, 1, i, nx, g.x64[0]);
+        const double dxBy = node_diff_rect(B, 1, node, 1, i, nx, g.x64[0]);
+        const double dyBx = node_diff_rect(B, 0, node, sy, j, ny, g.x64[1]);
         const double Jx = dyBz - dzBy, Jy = dzBx - dxBz, Jz = dxBy - dyBx;
         const double Bx = (double)B[node * 3 + 0], By = (double)B[node * 3 + 1], Bz = (double)B[node * 3 + 2];
         if (rec32) {
@@ -169,6 +229,16 @@ cudaError_t launch_curl_pack(const void *B, fqsl_dtype bt, const FieldView &g, v
     const long long cap = (long long)sms * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    if (g.rect) {
+        // stretched grid: FP64 stencils for every record precision
+        if (bt == FQSL_F32)
+            k_curl_pack_rect<float><<<(unsigned)blocks, 256, 0, s>>>((const float *)B, g, (float4 *)rec32,
+                                                                    (double2 *)rec64);
+        else
+            k_curl_pack_rect<double><<<(unsigned)blocks, 256, 0, s>>>((const double *)B, g, (float4 *)rec32,
+                                                                     (double2 *)rec64);
+        return cudaGetLastError();
+    }
     if (bt == FQSL_F32 && rec32) {
         // FP32 records from an FP32 cube: float stencils (the FP64 records, if
         // also wanted, come from the FP64 stencils below)

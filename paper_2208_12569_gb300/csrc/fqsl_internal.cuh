@@ -39,6 +39,20 @@ struct FieldView {
     long long nodes;          // nx * ny * nz
     unsigned long long *err;  // adjoint kernels: [0] first failed index check
                               // (code << 56 | value), [1] failed checks; NULL elsewhere
+    // Stretched (rectilinear) grid, rect = 1: node coordinates per axis. o is
+    // then the first node and d = 1, so FP32 state coordinates (r - o)/d are
+    // physical coordinates relative to the first node; the FP64 state is the
+    // physical position itself.
+    int rect;
+    const double *x64[3];  // node coordinates
+    const float *x32[3];   // node coordinates minus the first, as float
+    const float *rw32[3];  // 1/(x_{i+1} - x_i) per cell, float
+    const int *bkt[3];     // cell search: bucket b covers [x_0 + b/bsc, x_0 + (b+1)/bsc), bkt[b] <= its cells
+    int nbkt[3];
+    double bsc64[3];       // buckets per unit length
+    float bsc32[3];
+    double lo64[3], hi64[3];  // first and last node coordinate
+    float hi32[3];            // x32[n-1]
 };
 
 struct DevParams {
@@ -220,6 +234,12 @@ int trace_tape_blocks_per_sm_f32(int src, bool acc64);
 int trace_tape_blocks_per_sm_f64(int src);
 int trace_blocks_per_sm_f32(int src, bool acc64);
 int trace_blocks_per_sm_f64(int src);
+// the same on a stretched grid (FieldView::rect)
+cudaError_t launch_trace_rect_f32(const TraceArgs &a, int src, int grid, cudaStream_t s, bool acc64);
+cudaError_t launch_trace_rect_f64(const TraceArgs &a, int src, int grid, cudaStream_t s);
+int trace_rect_blocks_per_sm_f32(int src, bool acc64);
+int trace_rect_blocks_per_sm_f64(int src);
+cudaError_t launch_seed_prep_rect_f32(const TraceArgs &a, long long n, unsigned grid, cudaStream_t s);
 // Method II tracers (deviation vectors; way 1 = gradient grid, 2 = +-eps)
 cudaError_t launch_trace_dev_f32(const TraceArgs &a, int way, int grid, int block, cudaStream_t s);
 cudaError_t launch_trace_dev_f64(const TraceArgs &a, int way, int grid, int block, cudaStream_t s);

@@ -150,15 +150,11 @@ __device__ __forceinline__ int small_int(float c) { return __float_as_int(c + 83
 // 32-bit cell arithmetic and byte strides (field_create keeps every axis below
 // 2^23 nodes and the cube below 2^31 nodes; sz32 = 0 marks a z stride that
 // does not fit 32 bits).
-__device__ __forceinline__ void gather(const FieldView &f, float x, float y, float z, float B[3], float J[3])
+// The 8 corners of cell node (its lowest corner) with per-axis weights w (the
+// upper node's) and u = 1 - w.
+__device__ __forceinline__ void gather_cell32(const FieldView &f, unsigned node, float wx, float wy, float wz,
+                                              float ux, float uy, float uz, float B[3], float J[3])
 {
-    const float cx = fminf(fmaxf(floorf(x), 0.f), f.cmax[0]);
-    const float cy = fminf(fmaxf(floorf(y), 0.f), f.cmax[1]);
-    const float cz = fminf(fmaxf(floorf(z), 0.f), f.cmax[2]);
-    const float wx = x - cx, wy = y - cy, wz = z - cz;
-    const float ux = 1.f - wx, uy = 1.f - wy, uz = 1.f - wz;
-    const unsigned node = ((unsigned)small_int(cz) * (unsigned)f.ny + (unsigned)small_int(cy)) * (unsigned)f.nx +
-                          (unsigned)small_int(cx);
     const char *p00 = (const char *)f.rec + (size_t)node * 32u;
     const size_t szb = f.sz32 ? (size_t)f.sz32 : (size_t)f.nx * (size_t)f.ny * 32u;
     const char *pc[4] = {p00, p00 + f.sy32, p00 + szb, p00 + szb + f.sy32};
@@ -183,6 +179,18 @@ __device__ __forceinline__ void gather(const FieldView &f, float x, float y, flo
             J[2] += w * r5;
         }
     }
+}
+
+__device__ __forceinline__ void gather(const FieldView &f, float x, float y, float z, float B[3], float J[3])
+{
+    const float cx = fminf(fmaxf(floorf(x), 0.f), f.cmax[0]);
+    const float cy = fminf(fmaxf(floorf(y), 0.f), f.cmax[1]);
+    const float cz = fminf(fmaxf(floorf(z), 0.f), f.cmax[2]);
+    const float wx = x - cx, wy = y - cy, wz = z - cz;
+    const float ux = 1.f - wx, uy = 1.f - wy, uz = 1.f - wz;
+    const unsigned node = ((unsigned)small_int(cz) * (unsigned)f.ny + (unsigned)small_int(cy)) * (unsigned)f.nx +
+                          (unsigned)small_int(cx);
+    gather_cell32(f, node, wx, wy, wz, ux, uy, uz, B, J);
 }
 
 // FP64: Eq. interp term by term, omega_0 = (i+1) - xi and omega_1 = 1 - omega_0
@@ -222,6 +230,148 @@ __device__ __forceinline__ void gather(const FieldView &f, double x, double y, d
                 J[1] += wt * jy;
                 J[2] += wt * jz;
             }
+}
+
+// ---------------------------------------------------------------------------
+// Stretched (rectilinear) grids (Sec. 2.2): the cell of a coordinate is the
+// largest i in [0, n-2] with x_i <= x (below x_0, and NaN: cell 0). The paper
+// finds it by binary search; here a bucket table gives a nearby cell and a
+// step or two along the axis finish it (each loop moves one way and stops at
+// the axis ends), which gives the same cell for every x.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int axis_n(const FieldView &f, int a) { return a == 0 ? f.nx : (a == 1 ? f.ny : f.nz); }
+
+__device__ __forceinline__ int rect_cell(const FieldView &f, int a, double x)
+{
+    if (!(x >= f.lo64[a])) return 0;
+    const double *X = f.x64[a];
+    const int n = axis_n(f, a);
+    const double bf = (x - f.lo64[a]) * f.bsc64[a];
+    int i = __ldg(f.bkt[a] + (bf < (double)(f.nbkt[a] - 1) ? (int)bf : f.nbkt[a] - 1));
+    while (i < n - 2 && __ldg(X + i + 1) <= x) i++;
+    while (i > 0 && __ldg(X + i) > x) i--;
+    return i;
+}
+
+__device__ __forceinline__ int rect_cell(const FieldView &f, int a, float x)
+{
+    if (!(x >= 0.f)) return 0;
+    const float *X = f.x32[a];
+    const int n = axis_n(f, a);
+    const float bf = x * f.bsc32[a];
+    int i = __ldg(f.bkt[a] + (bf < (float)(f.nbkt[a] - 1) ? (int)bf : f.nbkt[a] - 1));
+    while (i < n - 2 && __ldg(X + i + 1) <= x) i++;
+    while (i > 0 && __ldg(X + i) > x) i--;
+    return i;
+}
+
+// FP32 on a stretched grid: state coordinates relative to the first node,
+// omega_0 = (x_{i+1} - x) / (x_{i+1} - x_i) with the reciprocal width (Eq. w0)
+__device__ __forceinline__ void gather_rect(const FieldView &f, float x, float y, float z, float B[3], float J[3])
+{
+    const int cx = rect_cell(f, 0, x), cy = rect_cell(f, 1, y), cz = rect_cell(f, 2, z);
+    const float ux = (__ldg(f.x32[0] + cx + 1) - x) * __ldg(f.rw32[0] + cx);
+    const float uy = (__ldg(f.x32[1] + cy + 1) - y) * __ldg(f.rw32[1] + cy);
+    const float uz = (__ldg(f.x32[2] + cz + 1) - z) * __ldg(f.rw32[2] + cz);
+    const unsigned node = ((unsigned)cz * (unsigned)f.ny + (unsigned)cy) * (unsigned)f.nx + (unsigned)cx;
+    gather_cell32(f, node, 1.f - ux, 1.f - uy, 1.f - uz, ux, uy, uz, B, J);
+}
+
+// FP64 on a stretched grid: Eqs. interp, w0, w1 as written in physical
+// coordinates, the sum nested as in the uniform FP64 gather
+__device__ __forceinline__ void gather_rect(const FieldView &f, double x, double y, double z, double B[3],
+                                            double J[3])
+{
+    const double xi[3] = {x, y, z};
+    long long c[3];
+    double w[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        c[a] = rect_cell(f, a, xi[a]);
+        const double x1 = __ldg(f.x64[a] + c[a] + 1), x0 = __ldg(f.x64[a] + c[a]);
+        w[a][0] = (x1 - xi[a]) / (x1 - x0);
+        w[a][1] = 1.0 - w[a][0];
+    }
+    const long long sy = f.nx, sz = (long long)f.nx * f.ny;
+    const long long base = c[2] * sz + c[1] * sy + c[0];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        B[k] = 0.0;
+        J[k] = 0.0;
+    }
+#pragma unroll
+    for (int m = 0; m < 2; m++)
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+#pragma unroll
+            for (int p = 0; p < 2; p++) {
+                const double wt = w[0][m] * w[1][q] * w[2][p];
+                double bx, by, bz, jx, jy, jz;
+                load_node(f, base + p * sz + q * sy + m, bx, by, bz, jx, jy, jz);
+                B[0] += wt * bx;
+                B[1] += wt * by;
+                B[2] += wt * bz;
+                J[0] += wt * jx;
+                J[1] += wt * jy;
+                J[2] += wt * jz;
+            }
+}
+
+template <bool RECT, typename T>
+__device__ __forceinline__ void gatherg(const FieldView &f, T x, T y, T z, T B[3], T J[3])
+{
+    if constexpr (RECT) gather_rect(f, x, y, z, B, J);
+    else gather(f, x, y, z, B, J);
+}
+
+// Box bounds in state coordinates: [0, n-1] cells; on a stretched grid the
+// first and last node (FP64: physical; FP32: relative to the first node).
+template <typename T, bool RECT>
+__device__ __forceinline__ T lo_of(const FieldView &f, int a)
+{
+    if constexpr (RECT && sizeof(T) == 8) return (T)f.lo64[a];
+    else return (T)0;
+}
+
+template <typename T, bool RECT>
+__device__ __forceinline__ T hi_of(const FieldView &f, int a)
+{
+    if constexpr (RECT) {
+        if constexpr (sizeof(T) == 8) return (T)f.hi64[a];
+        else return (T)f.hi32[a];
+    } else {
+        return (T)(axis_n(f, a) - 1);
+    }
+}
+
+// The step's scale per axis, fixed at the start of a trial: FP64 the width
+// of the cell holding the start point (the spacing on a uniform grid), FP32
+// its reciprocal (Sec. 2.3: step and tol scaled per cell).
+template <typename T, bool RECT>
+__device__ __forceinline__ void step_dd(const FieldView &f, T x, T y, T z, T dd[3])
+{
+    if constexpr (!RECT) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) dd[a] = sizeof(T) == 8 ? (T)f.d[a] : (T)f.rd[a];
+    } else {
+        const T p[3] = {x, y, z};
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const int c = rect_cell(f, a, p[a]);
+            if constexpr (sizeof(T) == 8) dd[a] = (T)(__ldg(f.x64[a] + c + 1) - __ldg(f.x64[a] + c));
+            else dd[a] = (T)__ldg(f.rw32[a] + c);
+        }
+    }
+}
+
+// state <-> physical coordinates (double): (r - o)/d and o + d x on a uniform
+// grid (and for FP32 on a stretched one, where o is the first node and d = 1);
+// the FP64 state on a stretched grid is the physical position.
+template <typename T, bool RECT>
+__device__ __forceinline__ double state_of(const FieldView &f, double r, int a)
+{
+    if constexpr (RECT && sizeof(T) == 8) return r;
+    else return (r - f.o[a]) / f.d[a];
 }
 
 // Right-hand side in index space: out = {F (3), dl/dtau, dTw/dtau}.
@@ -266,6 +416,55 @@ __device__ __forceinline__ bool rhs(const FieldView &f, const double d[3], doubl
     out[3] = dl;
     out[4] = (J[0] * B[0] + J[1] * B[1] + J[2] * B[2]) / (12.566370614359172 * BB) * dl;
     return true;
+}
+
+// Stretched grid: bt_a = B_a / D_a with the step's cell widths D, and the
+// physical velocity F = sigma B / |bt| (FP32: rw = 1/D).
+__device__ __forceinline__ bool rhs_rect(const FieldView &f, const float rw[3], float sgn, float x, float y, float z,
+                                         float out[5])
+{
+    float B[3], J[3];
+    gather_rect(f, x, y, z, B, J);
+    const float b0 = B[0] * rw[0], b1 = B[1] * rw[1], b2 = B[2] * rw[2];
+    const float bb = b0 * b0 + b1 * b1 + b2 * b2;
+    const float BB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    if (!(bb > 0.f) || !(bb < INFINITY)) return false;
+    const float inv = rsqrtf(bb);
+    const float s = sgn * inv;
+    out[0] = B[0] * s;
+    out[1] = B[1] * s;
+    out[2] = B[2] * s;
+    const float dl = sqrtf(BB) * inv;
+    out[3] = dl;
+    const float JB = J[0] * B[0] + J[1] * B[1] + J[2] * B[2];
+    out[4] = __fdividef(JB * dl, 12.566370614359172f * BB);
+    return true;
+}
+
+__device__ __forceinline__ bool rhs_rect(const FieldView &f, const double D[3], double sgn, double x, double y,
+                                         double z, double out[5])
+{
+    double B[3], J[3];
+    gather_rect(f, x, y, z, B, J);
+    const double bt[3] = {B[0] / D[0], B[1] / D[1], B[2] / D[2]};
+    const double bb = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
+    const double BB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    if (!(bb > 0.0) || !(bb < INFINITY)) return false;
+    const double nbt = sqrt(bb), nB = sqrt(BB);
+    out[0] = sgn * B[0] / nbt;
+    out[1] = sgn * B[1] / nbt;
+    out[2] = sgn * B[2] / nbt;
+    const double dl = nB / nbt;
+    out[3] = dl;
+    out[4] = (J[0] * B[0] + J[1] * B[1] + J[2] * B[2]) / (12.566370614359172 * BB) * dl;
+    return true;
+}
+
+template <bool RECT, typename T>
+__device__ __forceinline__ bool rhsg(const FieldView &f, const T dd[3], T sgn, T x, T y, T z, T out[5])
+{
+    if constexpr (RECT) return rhs_rect(f, dd, sgn, x, y, z, out);
+    else return rhs(f, dd, sgn, x, y, z, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -390,6 +589,40 @@ __device__ __forceinline__ double obliq_pow(double x, double e) { return e == 1.
 // value matches a plain multiply-then-add
 __device__ __forceinline__ double to_phys(double o, double d, double xi) { return __dadd_rn(o, __dmul_rn(d, xi)); }
 
+// physical coordinate of a state coordinate (the FP64 state on a stretched
+// grid is physical already)
+template <typename T, bool RECT>
+__device__ __forceinline__ double phys_of(const FieldView &f, double x, int a)
+{
+    if constexpr (RECT && sizeof(T) == 8) return x;
+    else return to_phys(f.o[a], f.d[a], x);
+}
+
+// the box bounds in double state coordinates (for seeds; the FP32 tracer's
+// float bounds are these rounded, so a seed inside stays inside)
+template <typename T, bool RECT>
+__device__ __forceinline__ double dlo(const FieldView &f, int a)
+{
+    return (RECT && sizeof(T) == 8) ? f.lo64[a] : 0.0;
+}
+
+template <typename T, bool RECT>
+__device__ __forceinline__ double dhi(const FieldView &f, int a)
+{
+    if constexpr (RECT) return sizeof(T) == 8 ? f.hi64[a] : f.hi64[a] - f.lo64[a];
+    else return (double)(axis_n(f, a) - 1);
+}
+
+// a state position (double) inside the closed box
+template <typename T, bool RECT>
+__device__ __forceinline__ bool in_box(const FieldView &f, const double xi[3])
+{
+    bool in = true;
+#pragma unroll
+    for (int a = 0; a < 3; a++) in = in && xi[a] >= dlo<T, RECT>(f, a) && xi[a] <= dhi<T, RECT>(f, a);
+    return in;
+}
+
 template <typename T>
 __device__ __forceinline__ T sel3(int a, T v0, T v1, T v2)
 {
@@ -427,12 +660,12 @@ __device__ __forceinline__ void perp_frame(const double bh[3], double u[3], doub
     v[2] = bh[0] * u[1] - bh[1] * u[0];
 }
 
-// B at an index position in double (for seeds, frames and end normals)
-template <typename T>
+// B at a state position in double (for seeds, frames and end normals)
+template <typename T, bool RECT = false>
 __device__ __forceinline__ void b_at(const FieldView &f, double x, double y, double z, double B[3])
 {
     T Bt[3], Jt[3];
-    gather(f, (T)x, (T)y, (T)z, Bt, Jt);
+    gatherg<RECT>(f, (T)x, (T)y, (T)z, Bt, Jt);
     B[0] = (double)Bt[0];
     B[1] = (double)Bt[1];
     B[2] = (double)Bt[2];
@@ -617,17 +850,17 @@ __device__ __forceinline__ void split_finish(const TraceArgs &A, const LineRecs 
 
 // Finish the line with a bad status (MAXSTEPS or NULL_B): the unfinished end
 // is the current position, an untraced end the seed, their faces -1.
-template <typename T, bool SPLIT = false>
+template <typename T, bool SPLIT = false, bool RECT = false>
 __device__ __forceinline__ void finish_bad(const TraceArgs &A, const LineRecs &R, Lane<T> &L, unsigned bit)
 {
     const FieldView &f = A.f;
     L.st |= bit;
     if constexpr (sizeof(T) == 8) {
-        write_end(A, R, L, L.end, to_phys(f.o[0], f.d[0], (double)L.x), to_phys(f.o[1], f.d[1], (double)L.y),
-                  to_phys(f.o[2], f.d[2], (double)L.z), -1, 0.0);
+        write_end(A, R, L, L.end, phys_of<T, RECT>(f, (double)L.x, 0), phys_of<T, RECT>(f, (double)L.y, 1),
+                  phys_of<T, RECT>(f, (double)L.z, 2), -1, 0.0);
         if (L.end == 0 && !SPLIT)
-            write_end(A, R, L, 1, to_phys(f.o[0], f.d[0], (double)L.sx), to_phys(f.o[1], f.d[1], (double)L.sy),
-                      to_phys(f.o[2], f.d[2], (double)L.sz), -1, 0.0);
+            write_end(A, R, L, 1, phys_of<T, RECT>(f, (double)L.sx, 0), phys_of<T, RECT>(f, (double)L.sy, 1),
+                      phys_of<T, RECT>(f, (double)L.sz, 2), -1, 0.0);
         if (R.tw) R.tw[L.line] = NAN;
         if (R.len) R.len[L.line] = NAN;
     } else {
@@ -644,7 +877,7 @@ __device__ __forceinline__ void finish_bad(const TraceArgs &A, const LineRecs &R
 
 // A direction reached a face at index position (x, y, z) with deviation
 // vectors (du, dv) (Method II only).
-template <typename T, bool ACC, int DEV = 0, bool SPLIT = false>
+template <typename T, bool ACC, int DEV = 0, bool SPLIT = false, bool RECT = false>
 __device__ __forceinline__ bool finish_dir(const TraceArgs &A, const LineRecs &R, Lane<T> &L, T x, T y, T z,
                                            int face, const T *du = nullptr, const T *dv = nullptr)
 {
@@ -668,10 +901,10 @@ __device__ __forceinline__ bool finish_dir(const TraceArgs &A, const LineRecs &R
     }
     if constexpr (sizeof(T) == 8) {
         double B[3];
-        b_at<T>(f, (double)x, (double)y, (double)z, B);
+        b_at<T, RECT>(f, (double)x, (double)y, (double)z, B);
         const int ax = face >> 1;
-        write_end(A, R, L, L.end, to_phys(f.o[0], f.d[0], (double)x), to_phys(f.o[1], f.d[1], (double)y),
-                  to_phys(f.o[2], f.d[2], (double)z), face, sel3<double>(ax, B[0], B[1], B[2]));
+        write_end(A, R, L, L.end, phys_of<T, RECT>(f, (double)x, 0), phys_of<T, RECT>(f, (double)y, 1),
+                  phys_of<T, RECT>(f, (double)z, 2), face, sel3<double>(ax, B[0], B[1], B[2]));
         if (R.be64) {
             double *be = R.be64 + 6 * L.line + 3 * L.end;
             be[0] = B[0];
@@ -732,17 +965,21 @@ __device__ __forceinline__ bool finish_dir(const TraceArgs &A, const LineRecs &R
     return false;
 }
 
-template <typename T>
+template <typename T, bool RECT = false>
 __device__ __forceinline__ bool inside(const FieldView &f, T x, T y, T z)
 {
-    return x >= (T)0 && x <= (T)(f.nx - 1) && y >= (T)0 && y <= (T)(f.ny - 1) && z >= (T)0 &&
-           z <= (T)(f.nz - 1);
+    if constexpr (RECT)
+        return x >= lo_of<T, RECT>(f, 0) && x <= hi_of<T, RECT>(f, 0) && y >= lo_of<T, RECT>(f, 1) &&
+               y <= hi_of<T, RECT>(f, 1) && z >= lo_of<T, RECT>(f, 2) && z <= hi_of<T, RECT>(f, 2);
+    else
+        return x >= (T)0 && x <= (T)(f.nx - 1) && y >= (T)0 && y <= (T)(f.ny - 1) && z >= (T)0 &&
+               z <= (T)(f.nz - 1);
 }
 
 // Start a line at index position xi (FP64: (r0 - o)/d as written) with
 // orientation vector n (NULL: end 1 is the backward end). Returns false if the
 // line ends at once (outside / null).
-template <typename T, bool ACC>
+template <typename T, bool ACC, bool RECT = false>
 __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R, Lane<T> &L, const double xi[3],
                                            const double *n, double tol, int st0)
 {
@@ -768,21 +1005,21 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
         L.tol = tol * tol;
         L.tolf2 = (float)L.tol;
     }
-    const bool in = xi[0] >= 0.0 && xi[0] <= (double)(f.nx - 1) && xi[1] >= 0.0 && xi[1] <= (double)(f.ny - 1) &&
-                    xi[2] >= 0.0 && xi[2] <= (double)(f.nz - 1);
+    const bool in = in_box<T, RECT>(f, xi);
     unsigned bad = 0;
     T B0[3] = {0, 0, 0};
     if (!in) {
         bad = FQSL_LINE_OUTSIDE;
     } else {
-        T J0[3];
-        gather(f, L.sx, L.sy, L.sz, B0, J0);
+        T J0[3], dd[3];
+        gatherg<RECT>(f, L.sx, L.sy, L.sz, B0, J0);
+        step_dd<T, RECT>(f, L.sx, L.sy, L.sz, dd);
         T bb;
         if (kF64) {
-            const T b0 = B0[0] / (T)f.d[0], b1 = B0[1] / (T)f.d[1], b2 = B0[2] / (T)f.d[2];
+            const T b0 = B0[0] / dd[0], b1 = B0[1] / dd[1], b2 = B0[2] / dd[2];
             bb = b0 * b0 + b1 * b1 + b2 * b2;
         } else {
-            const T b0 = B0[0] * (T)f.rd[0], b1 = B0[1] * (T)f.rd[1], b2 = B0[2] * (T)f.rd[2];
+            const T b0 = B0[0] * dd[0], b1 = B0[1] * dd[1], b2 = B0[2] * dd[2];
             bb = b0 * b0 + b1 * b1 + b2 * b2;
         }
         if (!(bb > (T)0) || !(bb < (T)INFINITY)) bad = FQSL_LINE_NULL_B;
@@ -791,8 +1028,8 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
         L.st |= bad;
         // footpoints of a line that never started: its seed
         if constexpr (sizeof(T) == 8) {
-            const double qx = to_phys(f.o[0], f.d[0], xi[0]), qy = to_phys(f.o[1], f.d[1], xi[1]),
-                         qz = to_phys(f.o[2], f.d[2], xi[2]);
+            const double qx = phys_of<T, RECT>(f, xi[0], 0), qy = phys_of<T, RECT>(f, xi[1], 1),
+                         qz = phys_of<T, RECT>(f, xi[2], 2);
             write_end(A, R, L, 0, qx, qy, qz, -1, 0.0);
             write_end(A, R, L, 1, qx, qy, qz, -1, 0.0);
             if (R.tw) R.tw[L.line] = NAN;
@@ -812,9 +1049,10 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
 
 // Lattice seed: frame, tolerance and rotation decision (Sec. 4). reg_rot:
 // queue a rotated seed for its extra lines (once per seed).
-template <typename T, bool ACC, int DEV = 0>
+template <typename T, bool ACC, int DEV = 0, bool RECT = false>
 __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, long long item, bool reg_rot = true)
 {
+    static_assert(!(RECT && DEV != 0), "Method II is not defined on stretched grids");
     constexpr bool kF64 = sizeof(T) == 8;
     const Lattice &G = A.lat;
     const long long per_tile = kTileU * kTileV;
@@ -864,11 +1102,12 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
     }
     double xi[3];
     if (kF64) {
-        // physical seed, then (r0 - o)/d, as written
+        // physical seed, then (r0 - o)/d, as written (the physical seed itself
+        // on a stretched grid)
         double r0[3];
         lattice_seed(G, i, j, k, r0);
 #pragma unroll
-        for (int a = 0; a < 3; a++) xi[a] = (r0[a] - f.o[a]) / f.d[a];
+        for (int a = 0; a < 3; a++) xi[a] = state_of<T, RECT>(f, r0[a], a);
     } else {
         const double fi = (double)i + 0.5, fj = (double)j + 0.5, fk = (double)k + 0.5;
 #pragma unroll
@@ -878,11 +1117,10 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
     double tol = A.p.tol;
     int st0 = 0;
     double bn0 = 0.0;
-    const bool in = xi[0] >= 0.0 && xi[0] <= (double)(f.nx - 1) && xi[1] >= 0.0 && xi[1] <= (double)(f.ny - 1) &&
-                    xi[2] >= 0.0 && xi[2] <= (double)(f.nz - 1);
+    const bool in = in_box<T, RECT>(f, xi);
     if (in) {
         T B0[3], J0[3];
-        gather(f, (T)xi[0], (T)xi[1], (T)xi[2], B0, J0);
+        gatherg<RECT>(f, (T)xi[0], (T)xi[1], (T)xi[2], B0, J0);
         const T nB = sqrt(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
         if (nB > (T)0 && nB < (T)INFINITY) {
             const T bn = B0[0] * (T)G.n0[0] + B0[1] * (T)G.n0[1] + B0[2] * (T)G.n0[2];
@@ -893,8 +1131,7 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
                 bool on_face = false;
                 if (G.normal_axis >= 0) {
                     const double xa = xi[G.normal_axis];
-                    const int na = G.normal_axis == 0 ? f.nx : (G.normal_axis == 1 ? f.ny : f.nz);
-                    on_face = (xa == 0.0) || (xa == (double)(na - 1));
+                    on_face = (xa == dlo<T, RECT>(f, G.normal_axis)) || (xa == dhi<T, RECT>(f, G.normal_axis));
                 }
                 if (G.allow_rot && ratio < (T)A.p.rot && !on_face) {
                     st0 = FQSL_LINE_ROTATED;
@@ -918,7 +1155,7 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
         }
     }
     R.bn0[idx] = bn0;
-    const bool started = start_line<T, ACC>(A, R, L, xi, G.n0, tol, st0);
+    const bool started = start_line<T, ACC, RECT>(A, R, L, xi, G.n0, tol, st0);
     if constexpr (DEV != 0) {
         if (started) {
             // S0 perpendicular to B: U0, V0 = the frame of B/|B| at the seed (Sec. 4)
@@ -938,7 +1175,7 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
 }
 
 // Rotated extra line q (0: +u, 1: -u, 2: +v, 3: -v) of rotated slot s (Sec. 4).
-template <typename T, bool ACC>
+template <typename T, bool ACC, bool RECT = false>
 __device__ __forceinline__ bool init_extra(const TraceArgs &A, Lane<T> &L, long long item)
 {
     const Lattice &G = A.lat;
@@ -951,8 +1188,8 @@ __device__ __forceinline__ bool init_extra(const TraceArgs &A, Lane<T> &L, long 
     const FieldView &f = A.f;
     double xi[3], B0[3];
 #pragma unroll
-    for (int a = 0; a < 3; a++) xi[a] = (r0[a] - f.o[a]) / f.d[a];
-    b_at<T>(f, xi[0], xi[1], xi[2], B0);
+    for (int a = 0; a < 3; a++) xi[a] = state_of<T, RECT>(f, r0[a], a);
+    b_at<T, RECT>(f, xi[0], xi[1], xi[2], B0);
     const double nB = sqrt(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
     double bh[3] = {B0[0] / nB, B0[1] / nB, B0[2] / nB}, u[3], v[3];
     perp_frame(bh, u, v);
@@ -965,20 +1202,20 @@ __device__ __forceinline__ bool init_extra(const TraceArgs &A, Lane<T> &L, long 
     for (int a = 0; a < 3; a++) rr[a] = r0[a] + sg * G.drot * dir[a];
     double xr[3];
 #pragma unroll
-    for (int a = 0; a < 3; a++) xr[a] = (rr[a] - f.o[a]) / f.d[a];
+    for (int a = 0; a < 3; a++) xr[a] = state_of<T, RECT>(f, rr[a], a);
     L.line = item;
-    return start_line<T, ACC>(A, A.ext, L, xr, nrot, A.p.tol, 0);
+    return start_line<T, ACC, RECT>(A, A.ext, L, xr, nrot, A.p.tol, 0);
 }
 
-template <typename T, bool ACC>
+template <typename T, bool ACC, bool RECT = false>
 __device__ __forceinline__ bool init_list(const TraceArgs &A, Lane<T> &L, long long item)
 {
     L.line = item;
     const FieldView &f = A.f;
     double xi[3];
 #pragma unroll
-    for (int a = 0; a < 3; a++) xi[a] = (A.seeds[3 * item + a] - f.o[a]) / f.d[a];
-    return start_line<T, ACC>(A, A.rec, L, xi, nullptr, A.p.tol, 0);
+    for (int a = 0; a < 3; a++) xi[a] = state_of<T, RECT>(f, A.seeds[3 * item + a], a);
+    return start_line<T, ACC, RECT>(A, A.rec, L, xi, nullptr, A.p.tol, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -994,9 +1231,14 @@ __device__ __forceinline__ bool init_list(const TraceArgs &A, Lane<T> &L, long l
 // traced with their two directions as separate work items (twice the
 // lattice's items; see split_finish) so that a long line's halves run side by
 // side; the extra lines of rotated seeds keep one item per line.
-template <typename T, int SRC, bool ACC, int DEV = 0, bool BATCH = false, bool TAPE = false>
+// RECT: the field is on a stretched grid (FieldView::rect; Method I and
+// twist lists): positions are physical (FP32: relative to the first node),
+// cells are searched, and each trial scales its step and error by the widths
+// of the cell it starts in (Sec. 2.3).
+template <typename T, int SRC, bool ACC, int DEV = 0, bool BATCH = false, bool TAPE = false, bool RECT = false>
 __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs &BA)
 {
+    static_assert(!(RECT && (DEV != 0 || TAPE)), "stretched grids: Method I and twist lists, no tape");
     constexpr bool SPLIT = TAPE && SRC == kSrcLattice;
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -1068,11 +1310,12 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                         active = init_lattice<T, ACC, DEV>(E, L, ((g >> 1) << 5) | (item & 31), (g & 1) == 0);
                         if (active && (g & 1)) L.end = 1;
                     } else {
-                        active = init_lattice<T, ACC, DEV>(E, L, item);
+                        active = init_lattice<T, ACC, DEV, RECT>(E, L, item);
                     }
                 }
-                else if (SRC == kSrcExtra) active = item < 4LL * (long long)*E.q.rot_count && init_extra<T, ACC>(E, L, item);
-                else active = init_list<T, ACC>(E, L, item);
+                else if (SRC == kSrcExtra)
+                    active = item < 4LL * (long long)*E.q.rot_count && init_extra<T, ACC, RECT>(E, L, item);
+                else active = init_list<T, ACC, RECT>(E, L, item);
             }
             ck_cur += min((long long)__popc(idle), avail);
             idle = __ballot_sync(FULL, !active);
@@ -1087,22 +1330,22 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
         const TraceArgs &A = ent();
         const FieldView &f = A.f;
         const LineRecs &R = (SRC == kSrcExtra) ? A.ext : A.rec;
-        // FP32 multiplies by 1/d, FP64 divides by d (see rhs)
-        const T dd[3] = {kF64 ? (T)f.d[0] : (T)f.rd[0], kF64 ? (T)f.d[1] : (T)f.rd[1],
-                         kF64 ? (T)f.d[2] : (T)f.rd[2]};
+        // FP32 multiplies by 1/d, FP64 divides by d (see rhs); on a stretched
+        // grid d is the width of the start point's cell
+        T dd[3];
+        step_dd<T, RECT>(f, L.x, L.y, L.z, dd);
 
         // ---- one trial: normal RKF45 step or exit (Henon) step ----
         const bool henon = L.mode != 0;
         const int hax = L.hface >> 1;
         const int hmaxside = L.hface & 1;
         const T hsign = hmaxside ? (T)1 : (T)-1;
-        const int nax = hax == 0 ? f.nx : (hax == 1 ? f.ny : f.nz);
-        const T target = hmaxside ? (T)(nax - 1) : (T)0;
+        const T target = hmaxside ? hi_of<T, RECT>(f, hax) : lo_of<T, RECT>(f, hax);
         const T sgn = (L.end == 0) ? -L.s0 : L.s0;
         T hh;
         if (!henon) {
             if (L.steps >= max_steps) {
-                finish_bad<T, SPLIT>(A, R, L, FQSL_LINE_MAXSTEPS);
+                finish_bad<T, SPLIT, RECT>(A, R, L, FQSL_LINE_MAXSTEPS);
                 active = false;
                 continue;
             }
@@ -1133,7 +1376,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
             py = L.y + hh * py;
             pz = L.z + hh * pz;
             T o[NS];
-            bool ok = rhs(f, dd, sgn, px, py, pz, o);
+            bool ok = rhsg<RECT>(f, dd, sgn, px, py, pz, o);
             if constexpr (DEV != 0) {
                 // stage deviation vectors and Eq. rb2: dU/dtau = sigma (ds/dtau) (U . grad)(B/|B|)
                 T us[6];
@@ -1162,7 +1405,10 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
             if (!ok && !fail) fail = 1;
             if (henon) {
                 const T fa = sel3<T>(hax, o[0], o[1], o[2]);
-                const bool bad = !(fa * hsign >= graze);
+                // grazing test in cells per unit tau (physical velocity over the cell width)
+                T fn = fa;
+                if constexpr (RECT) fn = kF64 ? fa / sel3<T>(hax, dd[0], dd[1], dd[2]) : fa * sel3<T>(hax, dd[0], dd[1], dd[2]);
+                const bool bad = !(fn * hsign >= graze);
                 if (bad && !fail) fail = 2;
                 if (kF64) {
                     const T den = bad ? (T)1 : fa;
@@ -1200,7 +1446,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
         }
 
         if (fail == 1) {
-            finish_bad<T, SPLIT>(A, R, L, FQSL_LINE_NULL_B);
+            finish_bad<T, SPLIT, RECT>(A, R, L, FQSL_LINE_NULL_B);
             active = false;
             continue;
         }
@@ -1214,19 +1460,36 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
             float rf = 0.f;
             bool over, pos;
             if (kF64) {
-                const double d0 = (double)((L.x + hh * a5[0]) - nx), d1 = (double)((L.y + hh * a5[1]) - ny),
-                             d2 = (double)((L.z + hh * a5[2]) - nz);
+                double d0 = (double)((L.x + hh * a5[0]) - nx), d1 = (double)((L.y + hh * a5[1]) - ny),
+                       d2 = (double)((L.z + hh * a5[2]) - nz);
+                if constexpr (RECT) {
+                    // in cells of the start cell
+                    d0 = d0 / (double)dd[0];
+                    d1 = d1 / (double)dd[1];
+                    d2 = d2 / (double)dd[2];
+                }
                 err = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
                 over = err > L.tol;
                 pos = err > 0.0;
             } else if (ACC) {
-                const double ex = (double)a5[0], ey = (double)a5[1], ez = (double)a5[2];
+                double ex = (double)a5[0], ey = (double)a5[1], ez = (double)a5[2];
+                if constexpr (RECT) {
+                    ex *= (double)dd[0];
+                    ey *= (double)dd[1];
+                    ez *= (double)dd[2];
+                }
                 err = (double)(hh * hh) * (ex * ex + ey * ey + ez * ez);  // err^2
                 over = err > L.tol;
                 pos = err > 0.0;
                 rf = __fdividef(L.tolf2, (float)err);
             } else {
-                const float e2 = (float)(hh * hh) * (float)(a5[0] * a5[0] + a5[1] * a5[1] + a5[2] * a5[2]);
+                T e5[3] = {a5[0], a5[1], a5[2]};
+                if constexpr (RECT) {
+                    e5[0] *= dd[0];
+                    e5[1] *= dd[1];
+                    e5[2] *= dd[2];
+                }
+                const float e2 = (float)(hh * hh) * (float)(e5[0] * e5[0] + e5[1] * e5[1] + e5[2] * e5[2]);
                 over = e2 > L.tolf2;
                 pos = e2 > 0.f;
                 rf = __fdividef(L.tolf2, e2);
@@ -1248,7 +1511,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                 hn = (T)4 * L.h;
             }
             hn = hn < hmin ? hmin : (hn > hmax ? hmax : hn);
-            if (inside<T>(f, nx, ny, nz)) {
+            if (inside<T, RECT>(f, nx, ny, nz)) {
                 if constexpr (TAPE) tape_step(A.tape, L, hh);
                 L.x = nx;
                 L.y = ny;
@@ -1268,14 +1531,13 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
             int best = -1;
             T tb = (T)INFINITY;
             const T cur[3] = {L.x, L.y, L.z}, nxt[3] = {nx, ny, nz};
-            const int nn[3] = {f.nx, f.ny, f.nz};
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                const T hi = (T)(nn[a] - 1);
+                const T lo = lo_of<T, RECT>(f, a), hi = hi_of<T, RECT>(f, a);
                 T t;
                 int fc;
-                if (nxt[a] < (T)0) {
-                    t = ((T)0 - cur[a]) / (nxt[a] - cur[a]);
+                if (nxt[a] < lo) {
+                    t = (lo - cur[a]) / (nxt[a] - cur[a]);
                     fc = 2 * a;
                 } else if (nxt[a] > hi) {
                     t = (hi - cur[a]) / (nxt[a] - cur[a]);
@@ -1322,8 +1584,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
             // chord fallback onto the first crossed face
             T ex = L.x + L.t0 * (L.ox - L.x), ey = L.y + L.t0 * (L.oy - L.y), ez = L.z + L.t0 * (L.oz - L.z);
             const int a0 = L.fc0 >> 1;
-            const int n0 = a0 == 0 ? f.nx : (a0 == 1 ? f.ny : f.nz);
-            const T v0 = (L.fc0 & 1) ? (T)(n0 - 1) : (T)0;
+            const T v0 = (L.fc0 & 1) ? hi_of<T, RECT>(f, a0) : lo_of<T, RECT>(f, a0);
             if (a0 == 0) ex = v0;
             else if (a0 == 1) ey = v0;
             else ez = v0;
@@ -1343,7 +1604,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                     ev[c] = L.v[c] + L.t0 * (L.ov[c] - L.v[c]);
                 }
             }
-            active = finish_dir<T, ACC, DEV, SPLIT>(A, R, L, ex, ey, ez, L.fc0, eu, ev);
+            active = finish_dir<T, ACC, DEV, SPLIT, RECT>(A, R, L, ex, ey, ez, L.fc0, eu, ev);
             waiting = active && A0.p.sync_dirs;
             continue;
         }
@@ -1354,12 +1615,11 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
         int nf = -1;
         {
             const T tt[3] = {tx, ty, tz};
-            const int nn[3] = {f.nx, f.ny, f.nz};
 #pragma unroll
             for (int b = 0; b < 3; b++) {
                 if (b == hax || nf >= 0) continue;
-                if (tt[b] < (T)0) nf = 2 * b;
-                else if (tt[b] > (T)(nn[b] - 1)) nf = 2 * b + 1;
+                if (tt[b] < lo_of<T, RECT>(f, b)) nf = 2 * b;
+                else if (tt[b] > hi_of<T, RECT>(f, b)) nf = 2 * b + 1;
             }
         }
         if (nf >= 0 && L.tries < 2) {
@@ -1368,9 +1628,9 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
             continue;
         }
         if (nf >= 0) {
-            tx = fmin(fmax(tx, (T)0), (T)(f.nx - 1));
-            ty = fmin(fmax(ty, (T)0), (T)(f.ny - 1));
-            tz = fmin(fmax(tz, (T)0), (T)(f.nz - 1));
+            tx = fmin(fmax(tx, lo_of<T, RECT>(f, 0)), hi_of<T, RECT>(f, 0));
+            ty = fmin(fmax(ty, lo_of<T, RECT>(f, 1)), hi_of<T, RECT>(f, 1));
+            tz = fmin(fmax(tz, lo_of<T, RECT>(f, 2)), hi_of<T, RECT>(f, 2));
         }
         acc_add<T, ACC>(L, hh * l4, hh * tw4);
         if constexpr (TAPE) tape_end(A.tape, L, (nf >= 0 ? kTapeExitClamped : kTapeExit) + L.hface, tx, ty, tz, (T)0);
@@ -1382,7 +1642,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                 ev[c] = L.v[c] + hh * ad[3 + c];
             }
         }
-        active = finish_dir<T, ACC, DEV, SPLIT>(A, R, L, tx, ty, tz, L.hface, eu, ev);
+        active = finish_dir<T, ACC, DEV, SPLIT, RECT>(A, R, L, tx, ty, tz, L.hface, eu, ev);
         waiting = active && A0.p.sync_dirs;
     }
 }
@@ -1391,6 +1651,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
 // index-space seed, Bn0, the S0 rotation decision and the per-line tolerance
 // (Sec. 4, Eq. tol), or the final record of a seed outside the box or on a
 // null field.
+template <bool RECT = false>
 __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
 {
     const Lattice &G = A.lat;
@@ -1405,14 +1666,14 @@ __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
     uint8_t fl = 0;
     unsigned bad = 0;
     double bn0 = 0.0, tol = A.p.tol;
-    const bool in = xi[0] >= 0.0 && xi[0] <= (double)(f.nx - 1) && xi[1] >= 0.0 && xi[1] <= (double)(f.ny - 1) &&
-                    xi[2] >= 0.0 && xi[2] <= (double)(f.nz - 1);
+    const bool in = in_box<float, RECT>(f, xi);
     if (!in) {
         bad = FQSL_LINE_OUTSIDE;
     } else {
-        float B0[3], J0[3];
-        gather(f, x, y, z, B0, J0);
-        const float b0 = B0[0] * f.rd[0], b1 = B0[1] * f.rd[1], b2 = B0[2] * f.rd[2];
+        float B0[3], J0[3], rd[3];
+        gatherg<RECT>(f, x, y, z, B0, J0);
+        step_dd<float, RECT>(f, x, y, z, rd);
+        const float b0 = B0[0] * rd[0], b1 = B0[1] * rd[1], b2 = B0[2] * rd[2];
         const float bb = b0 * b0 + b1 * b1 + b2 * b2;
         const float nB = sqrtf(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
         if (!(bb > 0.f) || !(bb < INFINITY) || !(nB > 0.f)) {
@@ -1427,8 +1688,7 @@ __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
                 bool on_face = false;
                 if (G.normal_axis >= 0) {
                     const double xa = xi[G.normal_axis];
-                    const int na = G.normal_axis == 0 ? f.nx : (G.normal_axis == 1 ? f.ny : f.nz);
-                    on_face = (xa == 0.0) || (xa == (double)(na - 1));
+                    on_face = (xa == dlo<float, RECT>(f, G.normal_axis)) || (xa == dhi<float, RECT>(f, G.normal_axis));
                 }
                 if (G.allow_rot && ratio < (float)A.p.rot && !on_face) {
                     fl |= kSeedRotated;

@@ -47,6 +47,7 @@ int blocks(int src)
 cudaError_t launch_trace_f32(const TraceArgs &a, int src, int grid, int block, cudaStream_t s, bool acc64)
 {
     if (block != kBlock) return cudaErrorInvalidValue;
+    if (a.f.rect) return launch_trace_rect_f32(a, src, grid, s, acc64);
     if (acc64) launch<true>(a, src, grid, block, s);
     else launch<false>(a, src, grid, block, s);
     return cudaGetLastError();
@@ -74,6 +75,7 @@ cudaError_t launch_seed_prep_f32(const TraceArgs &a, long long n, cudaStream_t s
     long long blocks = (n + 255) / 256;
     if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
     if (blocks < 1) blocks = 1;
+    if (a.f.rect) return launch_seed_prep_rect_f32(a, n, (unsigned)blocks, s);
     k_seed_prep_f32<<<(unsigned)blocks, 256, 0, s>>>(a, n);
     return cudaGetLastError();
 }

@@ -23,7 +23,7 @@ EXPORTS = ("fqsl_params_default", "fqsl_version", "fqsl_last_error", "fqsl_field
            "fqsl_qmap_plane", "fqsl_qmap_volume", "fqsl_twist", "fqsl_field_check", "fqsl_field_set_timing",
            "fqsl_field_times", "fqsl_field_update", "fqsl_qmap_plane_static", "fqsl_batch_create", "fqsl_batch_run",
            "fqsl_batch_destroy", "fqsl_backward", "fqsl_loss_logq_tw", "fqsl_tape_export",
-           "fqsl_tape_id")
+           "fqsl_tape_id", "fqsl_field_create_rect")
 STATIC_MAX_SEEDS = 65536
 
 
@@ -63,6 +63,8 @@ def load(path: str = LIB_PATH):
     lib.fqsl_last_error.restype = C.c_char_p
     lib.fqsl_field_create.argtypes = [P, C.c_int, C.c_longlong, C.c_longlong, C.c_longlong, P, P, C.c_uint, P,
                                       C.POINTER(P)]
+    lib.fqsl_field_create_rect.argtypes = [P, C.c_int, C.c_longlong, C.c_longlong, C.c_longlong, P, P, P, C.c_uint,
+                                           P, C.POINTER(P)]
     lib.fqsl_field_destroy.argtypes = [P]
     lib.fqsl_qmap_plane.argtypes = [P, P, P, P, C.c_longlong, C.c_longlong, C.POINTER(Params), C.POINTER(Out), P]
     lib.fqsl_qmap_plane_static.argtypes = [P, P, P, P, C.c_longlong, C.c_longlong, C.POINTER(Params),
@@ -128,24 +130,40 @@ def _stream(stream):
 class Field:
     """A field handle: B (torch CUDA tensor (nz, ny, nx, 3), float32 or float64)
     packed with its curl into node records (pack: 'f32', 'f64' or both, plus
-    'gradb' for the grad(B/|B|) grid of Method II way 1)."""
+    'gradb' for the grad(B/|B|) grid of Method II way 1). The grid is uniform
+    (origin, spacing) or stretched (coords = the x, y, z node coordinates,
+    fqsl_field_create_rect)."""
 
-    def __init__(self, B: torch.Tensor, origin, spacing, pack=("f32", "f64"), stream=None):
+    def __init__(self, B: torch.Tensor, origin=None, spacing=None, pack=("f32", "f64"), stream=None, coords=None):
         if not (isinstance(B, torch.Tensor) and B.is_cuda and B.dim() == 4 and B.shape[-1] == 3):
             raise ValueError("B must be a CUDA tensor of shape (nz, ny, nx, 3)")
         if B.dtype not in (torch.float32, torch.float64):
             raise ValueError("B must be float32 or float64")
+        if (coords is None) == (origin is None or spacing is None):
+            raise ValueError("give either origin and spacing (uniform grid) or coords (stretched grid)")
         B = B.contiguous()
         nz, ny, nx, _ = B.shape
         flags = ((PACK_F32 if "f32" in pack else 0) | (PACK_F64 if "f64" in pack else 0) |
                  (PACK_GRADB if "gradb" in pack else 0))
         h = C.c_void_p()
-        _check(_lib.fqsl_field_create(C.c_void_p(B.data_ptr()), F32 if B.dtype == torch.float32 else F64, nx, ny,
-                                      nz, _vec3(origin), _vec3(spacing), flags, _stream(stream), C.byref(h)))
+        bt = F32 if B.dtype == torch.float32 else F64
+        if coords is None:
+            _check(_lib.fqsl_field_create(C.c_void_p(B.data_ptr()), bt, nx, ny, nz, _vec3(origin), _vec3(spacing),
+                                          flags, _stream(stream), C.byref(h)))
+            self.origin = tuple(float(v) for v in origin)
+            self.spacing = tuple(float(v) for v in spacing)
+            self.coords = None
+        else:
+            xs = [(C.c_double * len(c))(*[float(v) for v in c]) for c in coords]
+            if tuple(len(c) for c in coords) != (nx, ny, nz):
+                raise ValueError("coords must hold nx, ny, nz node coordinates")
+            _check(_lib.fqsl_field_create_rect(C.c_void_p(B.data_ptr()), bt, nx, ny, nz, xs[0], xs[1], xs[2], flags,
+                                               _stream(stream), C.byref(h)))
+            self.coords = tuple(tuple(float(v) for v in c) for c in coords)
+            self.origin = tuple(c[0] for c in self.coords)
+            self.spacing = None
         self._h = h
         self.n = (nx, ny, nz)
-        self.origin = tuple(float(v) for v in origin)
-        self.spacing = tuple(float(v) for v in spacing)
         self._keep = B  # the packing kernel reads B asynchronously
 
     @property

@@ -68,3 +68,29 @@ def test_host_argument_errors(lib):
                                  C.byref(h)) == 1
     lib.fqsl_qmap_plane.restype = C.c_int
     assert lib.fqsl_qmap_plane(None, o, o, o, C.c_longlong(1), C.c_longlong(1), None, None, None) == 1
+
+
+def test_stretched_grid_argument_errors(lib):
+    # fqsl_field_create_rect checks its coordinate arrays on the host before
+    # touching the device
+    lib.fqsl_field_create_rect.restype = C.c_int
+    lib.fqsl_last_error.restype = C.c_char_p
+    h = C.c_void_p()
+    fake = C.c_void_p(4096)
+    n = C.c_longlong(4)
+    good = (C.c_double * 4)(0.0, 0.5, 1.5, 3.0)
+    flat = (C.c_double * 4)(0.0, 0.5, 0.5, 3.0)
+    nan = (C.c_double * 4)(0.0, float("nan"), 1.5, 3.0)
+    tiny = (C.c_double * 4)(0.0, 1e6, 1e6 + 1e-4, 2e6)  # float keeps about 7 digits of x - x_0
+
+    def create(x, y, z, flags=1):
+        return lib.fqsl_field_create_rect(fake, 0, n, n, n, x, y, z, flags, None, C.byref(h))
+
+    assert create(good, None, good) == 1 and b"NULL" in lib.fqsl_last_error()
+    assert create(good, flat, good) == 1 and b"increasing" in lib.fqsl_last_error()
+    assert create(nan, good, good) == 1 and b"finite" in lib.fqsl_last_error()
+    assert create(good, good, good, 1 | 4) == 1 and b"gradient" in lib.fqsl_last_error()
+    # cells that float cannot tell apart are refused for FP32 records only
+    assert create(good, good, tiny, 1) == 1 and b"float" in lib.fqsl_last_error()
+    assert create(good, good, good, 0) == 1
+    assert lib.fqsl_field_create_rect(None, 0, n, n, n, good, good, good, 1, None, C.byref(h)) == 1

@@ -1,0 +1,221 @@
+"""Stretched (rectilinear) grids on the CUDA path against the FP64 oracle on the
+same seeded inputs, through the C ABI (fqsl_field_create_rect; Sec. 2.2 cell
+search and Eqs. interp, w0, w1; Sec. 2.3 per-cell step and tolerance scaling;
+reading R16 of the oracle).
+
+FP64 tracer: every output identical to the oracle's to the last bit (so the
+parity bars hold too; both are asserted). FP32 tracer: its error against the
+oracle is bounded as on uniform grids."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import assert_bitwise, assert_fp64_parity, q_rel, to_np, tw_rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+E2 = math.e ** 2 + math.e ** -2
+
+
+@pytest.fixture(scope="module")
+def fq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2208_12569_gb300 as m
+
+    return m
+
+
+def _field(fq, B, grid, **kw):
+    return fq.Field(torch.from_numpy(np.ascontiguousarray(B)).cuda(), coords=grid.coords, **kw)
+
+
+def _plane(fq, field, *args, **kw):
+    out = fq.qmap_plane(field, *args, fq.params(**kw))
+    field.check()
+    return to_np(out)
+
+
+@pytest.fixture(scope="module")
+def mono():
+    # 64 x 56 x 32 nodes over [0, 63] x [0, 55] x [0, 31]: horizontal cells
+    # growing 3 % per cell from the middle, vertical 4 % per cell upward
+    grid = synth.stretched_grid((64, 56, 32), (0.0, 0.0, 0.0), (63.0, 55.0, 31.0), ratios=(1.03, 1.03, 1.04))
+    ch = synth.random_charges(np.random.default_rng(2208), 10, ((0.0, 63.0), (0.0, 55.0)), depth=(4.0, 12.0))
+    B = synth.monopole_cube(grid, ch, dtype=np.float32)
+    return B, grid
+
+
+def _cells_exact(g, r, grid, margin=1e-9):
+    # footpoint cells (cell search of the oracle) agree except within margin
+    # (relative to the cell width) of a node
+    ok = (r["status"] & 19) == 0
+    for k in ("r1", "r2"):
+        for a in range(3):
+            X = grid.axis(a)
+            cr = oracle.cell_rect(X, r[k][ok, a])
+            cg = oracle.cell_rect(X, g[k][ok, a])
+            w = X[cr + 1] - X[cr]
+            near = np.minimum(np.abs(r[k][ok, a] - X[cr]), np.abs(X[cr + 1] - r[k][ok, a])) < margin * w
+            assert np.all((cr == cg) | near)
+
+
+def test_plane_fp64_bitwise_ragged(fq, oracle_lib, mono):
+    """z = 0 plane, several 8x4 tiles and ragged tails (101 x 75 seeds)."""
+    B, grid = mono
+    field = _field(fq, B, grid)
+    nu, nv = 101, 75
+    args = ((0.0, 0.0, 0.0), (63.0 / nu, 0, 0), (0, 55.0 / nv, 0), nu, nv)
+    g = _plane(fq, field, *args, precision="f64")
+    r = oracle.plane(B.astype(np.float64), grid, *args, oracle.params())
+    assert np.isfinite(r["Q"]).sum() > 6000
+    assert_fp64_parity(g, r)
+    _cells_exact(g, r, grid)
+    assert_bitwise(g, r)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f32acc64"])
+def test_plane_fp32_error_stated(fq, oracle_lib, mono, precision):
+    B, grid = mono
+    field = _field(fq, B, grid)
+    nu, nv = 101, 75
+    args = ((0.0, 0.0, 0.0), (63.0 / nu, 0, 0), (0, 55.0 / nv, 0), nu, nv)
+    g = _plane(fq, field, *args, precision=precision)
+    r = oracle.plane(B.astype(np.float64), grid, *args, oracle.params())
+    assert np.array_equal(g["status"] & oracle.BAD, r["status"] & oracle.BAD)
+    assert np.mean(g["face2"] == r["face2"]) > 0.99
+    rel = q_rel(g, r)
+    assert np.mean(np.isfinite(g["Q"]) & np.isfinite(r["Q"])) > 0.95
+    assert np.median(rel[np.isfinite(rel)]) < 1e-3
+    t = tw_rel(g, r)
+    assert np.median(t[np.isfinite(t)]) < 1e-4
+
+
+def test_interior_plane_rotation_fp64_bitwise(fq, oracle_lib, mono):
+    """A vertical interior plane: near-tangent seeds rotate S0 and trace four
+    extra lines (Sec. 4) on the stretched grid."""
+    B, grid = mono
+    field = _field(fq, B, grid)
+    nu, nv = 70, 36
+    args = ((0.0, 10.3, 0.0), (63.0 / nu, 0, 0), (0, 0, 31.0 / nv), nu, nv)
+    g = _plane(fq, field, *args, precision="f64")
+    r = oracle.plane(B.astype(np.float64), grid, *args, oracle.params())
+    assert (r["status"] & oracle.ROTATED).sum() > 30
+    assert_fp64_parity(g, r)
+    assert_bitwise(g, r)
+
+
+def test_volume_fp64_bitwise(fq, oracle_lib, mono):
+    B, grid = mono
+    field = _field(fq, B, grid)
+    step = (63.0 / 20, 55.0 / 18, 31.0 / 6)
+    g = to_np(fq.qmap_volume(field, (0.0, 0.0, 0.0), step, 20, 18, 6, fq.params(precision="f64")))
+    field.check()
+    r = oracle.qmap(B.astype(np.float64), grid, (0.0, 0.0, 0.0), (step[0], 0, 0), (0, step[1], 0), (0, 0, step[2]),
+                    (20, 18, 6), oracle.params())
+    assert_bitwise(g, r)
+
+
+def test_twist_list_fp64_bitwise(fq, oracle_lib, mono):
+    B, grid = mono
+    field = _field(fq, B, grid)
+    rng = np.random.default_rng(3)
+    seeds = np.concatenate([rng.uniform([0, 0, 0], [63, 55, 31], size=(500, 3)),
+                            [[70.0, 1.0, 1.0], [-0.5, 3.0, 3.0], [0.0, 0.0, 0.0], [63.0, 55.0, 31.0]]])
+    g = to_np(fq.twist(field, torch.from_numpy(seeds).cuda(), fq.params(precision="f64")))
+    field.check()
+    r = oracle.twist(B.astype(np.float64), grid, seeds, oracle.params())
+    assert_bitwise(g, r)
+    assert np.all(g["status"][-4:-2] == 16)
+
+
+def test_closed_forms_on_gpu(fq, oracle_lib):
+    # linear fields are exact under trilinear interpolation on any grid
+    grid = synth.stretched_grid((40, 36, 30), (-1.0, -1.0, 0.0), (1.0, 1.0, 1.0), ratios=(1.04, 1.05, 1.06))
+    d = 0.6 / 24
+    xs = -0.3 + (np.arange(24) + 0.5) * d
+    X, Y = (v.ravel() for v in np.meshgrid(xs, xs, indexing="xy"))
+    field = _field(fq, synth.analytic_cube("hyperbolic", grid), grid)
+    args = ((-0.3, -0.3, 0.0), (d, 0, 0), (0, d, 0), 24, 24)
+    for prec, tol, qtol in (("f64", 1e-10, 1e-8), ("f32", 10 ** -3.2, 2e-3)):
+        g = _plane(fq, field, *args, precision=prec, tol=tol)
+        assert np.all((g["status"] & oracle.BAD) == 0) and np.all(g["face2"] == 5)
+        np.testing.assert_allclose(g["Q"], E2, rtol=qtol)
+    g = _plane(fq, field, *args, precision="f64", tol=1e-10)
+    np.testing.assert_allclose(g["r2"][:, 0], X * math.e, rtol=0, atol=1e-8)
+    np.testing.assert_allclose(g["r2"][:, 1], Y / math.e, rtol=0, atol=1e-8)
+    q = 2.0 * math.pi
+    field = _field(fq, synth.analytic_cube("rotation", grid, q=q), grid)
+    g = _plane(fq, field, *args, precision="f64", tol=1e-10)
+    r2 = X * X + Y * Y
+    np.testing.assert_allclose(g["Tw"], q / (2 * math.pi * np.sqrt(1 + q * q * r2)), rtol=1e-7)
+
+
+def test_uniform_coordinates_match_the_uniform_field(fq, oracle_lib, mono):
+    # a stretched handle with uniform coordinates agrees with the uniform
+    # handle of the same cube to the integration error (different rounding of
+    # the same method); the FP64 stretched map is still the oracle's bit for bit
+    B, _ = mono
+    ug = synth.Grid((64, 56, 32), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    rg = synth.RectGrid(tuple(tuple(float(v) for v in ug.axis(a)) for a in range(3)))
+    args = ((0.0, 0.0, 0.0), (63.0 / 48, 0, 0), (0, 55.0 / 40, 0), 48, 40)
+    fu = fq.Field(torch.from_numpy(B).cuda(), ug.origin, ug.spacing)
+    fr = _field(fq, B, rg)
+    a = _plane(fq, fu, *args, precision="f64", tol=1e-10)
+    b = _plane(fq, fr, *args, precision="f64", tol=1e-10)
+    assert np.array_equal(a["face2"], b["face2"])
+    ok = np.isfinite(a["Q"]) & np.isfinite(b["Q"])
+    assert np.median(np.abs(b["Q"][ok] / a["Q"][ok] - 1)) < 1e-7
+    assert_bitwise(b, oracle.plane(B.astype(np.float64), rg, *args, oracle.params(tol=1e-10)))
+
+
+def test_static_entry_point(fq, oracle_lib, mono):
+    # the allocation-free entry point serves stretched handles too
+    B, grid = mono
+    field = _field(fq, B, grid)
+    args = ((0.0, 0.0, 0.0), (63.0 / 40, 0, 0), (0, 55.0 / 30, 0), 40, 30)
+    out = fq.alloc_out(40 * 30)
+    fq.qmap_plane_static(field, *args, fq.params(precision="f64"), out=out)
+    field.check()
+    assert_bitwise(to_np(out), oracle.plane(B.astype(np.float64), grid, *args, oracle.params()))
+
+
+def test_unsupported_modes(fq, mono):
+    B, grid = mono
+    field = _field(fq, B, grid)
+    args = ((0.0, 0.0, 0.0), (1.0, 0, 0), (0, 1.0, 0), 4, 4)
+    for kw in (dict(method=2), dict(tape=1)):
+        with pytest.raises(fq.FqslError) as ei:
+            fq.qmap_plane(field, *args, fq.params(**kw))
+        assert ei.value.status == 5
+    with pytest.raises(fq.FqslError) as ei:
+        _field(fq, B, grid, pack=("f32", "gradb"))
+    assert ei.value.status == 1
+    with pytest.raises(fq.FqslError) as ei:
+        fq.Batch([field], [dict(origin=args[0], u=args[1], v=args[2], nu=4, nv=4)], fq.params())
+    assert ei.value.status == 5
+
+
+def test_full_size_stretched_workload_sampled(fq, oracle_lib):
+    """The stretched benchmark workload at full size (the 256x256x128 monopole
+    field on a stretched grid, 1024x1024 seeds on z=0) in the benchmark's
+    launch configuration; the oracle recomputes a seeded sample of seeds."""
+    B, grid, _ = synth.c2_stretched()
+    field = _field(fq, B, grid)
+    n = 1024
+    args = ((0.0, 0.0, 0.0), (255.0 / n, 0, 0), (0, 255.0 / n, 0), n, n)
+    g64 = _plane(fq, field, *args, precision="f64")
+    g32 = _plane(fq, field, *args, precision="f32")
+    sample = np.sort(np.random.default_rng(12).choice(n * n, 2000, replace=False))
+    r = oracle.plane(B.astype(np.float64), grid, *args, oracle.params(), sample=sample)
+    gs = {k: v[sample] for k, v in g64.items()}
+    assert_fp64_parity(gs, r)
+    assert_bitwise(gs, r)
+    g32s = {k: v[sample] for k, v in g32.items()}
+    assert np.mean(g32s["face2"] == r["face2"]) > 0.98
+    rel = q_rel(g32s, r)
+    assert np.median(rel[np.isfinite(rel)]) < 1e-3
