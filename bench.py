@@ -303,6 +303,97 @@ def run_volume(args):
     print(json.dumps(line), flush=True)
 
 
+RECT_WORKLOAD = "monopole24_stretched256x256x128_f32_z0plane_1024x1024_methodI_rkf45"
+
+
+def run_stretched(args, emit=True):
+    """The C2 map on a stretched grid (Sec. 2.2-2.3): the same 24 monopoles
+    sampled on 256x256x128 nodes over the same box, horizontal cells growing
+    1 % per cell from the middle to the edges and vertical cells 2 % per cell
+    upward; 1024x1024 seeds on z=0. FP32 and FP64, next to the uniform C2 map
+    (the paper reports 45-80 % of the uniform speed for its binary search);
+    error against the oracle on a seeded sample."""
+    import torch
+
+    import __graft_entry__
+    import oracle
+    import synth
+
+    __graft_entry__._builder().build()
+    import paper_2208_12569_gb300 as fq
+
+    dev = torch.device("cuda", 0)
+    B, grid, _ = synth.c2_stretched(seed=SEED, n=CUBE)
+    Bd = torch.from_numpy(B).to(dev)
+    u = ((CUBE[0] - 1.0) / NU, 0.0, 0.0)
+    v = (0.0, (CUBE[1] - 1.0) / NV, 0.0)
+    n = NU * NV
+    out = fq.alloc_out(n, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(field, p, k):
+        for _ in range(args.warmup):
+            fq.qmap_plane(field, (0.0, 0.0, 0.0), u, v, NU, NV, p, out=out)
+        torch.cuda.synchronize()
+        field.check()
+        ms, kern = [], []
+        for _ in range(k):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fq.qmap_plane(field, (0.0, 0.0, 0.0), u, v, NU, NV, p, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            kern.append(field.times())
+        return float(np.mean(ms)), float(np.mean([k[0] for k in kern])), \
+            {k: t.cpu().numpy() for k, t in out.items() if t is not None}
+
+    res = {}
+    fr = fq.Field(Bd, coords=grid.coords, pack=("f32", "f64"))
+    fr.set_timing(True)
+    for prec, k in (("f32", args.steps), ("f32acc64", args.steps), ("f64", max(1, args.fp64_steps))):
+        ms, tr, o = timed(fr, fq.params(precision=prec, tol=TOL), k)
+        res[prec] = {"value": n / (ms / 1000.0), "unit": "Q+Tw values/s", "ms_per_step": ms, "trace_ms": tr,
+                     "mean_trials_per_line": float(o["steps"].astype(np.int64).sum()) / n, "out": o}
+    fr.close()
+    # the uniform C2 map in the same run, for the ratio
+    Bu, ugrid, uu, vu = c2_inputs(0)
+    Bud = torch.from_numpy(Bu).to(dev)
+    fu = fq.Field(Bud, ugrid.origin, ugrid.spacing, pack=("f32",))
+    fu.set_timing(True)
+    ms_u, tr_u, _ = timed(fu, fq.params(precision="f32", tol=TOL), args.steps)
+    fu.close()
+    line = {"metric": METRIC, "workload": "stretched", "unit": "Q+Tw values/s", "value": res["f32"]["value"],
+            "ms_per_step": res["f32"]["ms_per_step"], "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": RECT_WORKLOAD, "cube": list(CUBE), "seeds": [NU, NV], "tol_perp": TOL,
+                       "stretch": "x, y cells x1.01 per cell from the middle; z cells x1.02 per cell upward",
+                       "cell_width_range": [float(min(np.diff(grid.axis(a)).min() for a in range(3))),
+                                            float(max(np.diff(grid.axis(a)).max() for a in range(3)))],
+                       "l2": "flushed between steps (256 MB write)", "inputs_resident": True},
+            "f32_acc64": {k: res["f32acc64"][k] for k in ("value", "ms_per_step", "trace_ms")},
+            "fp64": {k: res["f64"][k] for k in ("value", "ms_per_step", "trace_ms")},
+            "kernels_ms": {"trace_f32": res["f32"]["trace_ms"]},
+            "work": {"mean_trials_per_line": res["f32"]["mean_trials_per_line"]},
+            "uniform_c2_f32": {"value": n / (ms_u / 1000.0), "ms_per_step": ms_u, "trace_ms": tr_u,
+                               "stretched_over_uniform": ms_u / res["f32"]["ms_per_step"]},
+            "gpu_launches": 3 * args.steps}
+    if emit and not args.no_cpu_baseline:
+        sample = np.sort(np.random.default_rng(23).choice(n, 2000, replace=False))
+        t0 = time.perf_counter()
+        ref = oracle.plane(B.astype(np.float64), grid, (0.0, 0.0, 0.0), u, v, NU, NV, oracle.params(tol=TOL),
+                           sample=sample)
+        dt = time.perf_counter() - t0
+        line["error_vs_oracle"] = {p: err_stats(res[p]["out"], ref, sample) for p in ("f32", "f32acc64", "f64")}
+        line["cpu_baseline"] = {"value": len(sample) / dt, "unit": "Q+Tw values/s", "cores": oracle.max_threads(),
+                                "kind": "oracle", "sample": "%d seeded-random seeds of the map" % len(sample)}
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
 def run_batch(args):
     """Batched uneven workload: 48 monopole cubes with sizes drawn from
     {64^3, 128^2x64, 256^2x128, 384^2x192}, 8-64 sources each, each with the
@@ -664,9 +755,12 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--only-f32", action="store_true",
                     help="time only the FP32 map (no FP64, e2e or CPU legs); used for ncu captures")
-    ap.add_argument("--workload", default="plane", choices=["plane", "volume", "batch", "adjoint"],
+    ap.add_argument("--no-stretched", action="store_true",
+                    help="plane workload: skip the stretched-grid map embedded in its line")
+    ap.add_argument("--workload", default="plane", choices=["plane", "volume", "batch", "adjoint", "stretched"],
                     help="plane: the benchmark line; volume: the large-volume configuration; "
-                         "batch: 48 uneven cubes in one launch; adjoint: d(loss)/dB on the 128x128x64 cube")
+                         "batch: 48 uneven cubes in one launch; adjoint: d(loss)/dB on the 128x128x64 cube; "
+                         "stretched: the plane map on a stretched grid")
     args = ap.parse_args()
     if args.impl == "reference":
         if args.workload == "adjoint":
@@ -682,6 +776,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.workload == "stretched":
+        run_stretched(args)
         return
 
     import torch
@@ -850,6 +947,12 @@ def main():
         line["adjoint"] = {k: a[k] for k in ("metric", "value", "unit", "ms_per_step", "higher_is_better", "config",
                                              "fp64", "kernels_ms", "error_vs_oracle", "e2e", "cpu_baseline",
                                              "roofline", "reverse_sweep", "loss")}
+    if rank == 0 and ws == 1 and not args.no_stretched:
+        # the same map on a stretched grid (its oracle check runs in the tests and in --workload stretched)
+        st = run_stretched(argparse.Namespace(steps=args.steps, warmup=args.warmup, fp64_steps=args.fp64_steps,
+                                              no_cpu_baseline=True), emit=False)
+        line["stretched"] = {k: st[k] for k in ("value", "unit", "ms_per_step", "config", "f32_acc64", "fp64",
+                                                "kernels_ms", "work", "uniform_c2_f32")}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, sample, ref = cpu_baseline(B, grid, u, v)
         line["cpu_baseline"] = cb

@@ -262,29 +262,35 @@ fqsl_status fqsl_field_create_rect(const void *B_dev, fqsl_dtype b_dtype, long l
     }
     st = check_device_ptr(B_dev, who);
     if (st != FQSL_OK) return st;
-    // host tables: x64 | x32 | rw32 | buckets, one device buffer
+    // host tables, one device buffer: x64 | cell64 | cell32 | bkt | bk32
     std::vector<double> x64;
-    std::vector<float> x32, rw32;
+    std::vector<double2> cell64;
+    std::vector<float4> cell32;
     std::vector<int> bkt;
+    std::vector<float4> bk32;
     long long nb[3];
+    float hi32[3];
     for (int a = 0; a < 3; a++) {
         const double *A = X[a];
         const long long n = N[a];
         const double L = A[n - 1] - A[0];
         double wmin = INFINITY;
         for (long long i = 0; i + 1 < n; i++) wmin = fmin(wmin, A[i + 1] - A[i]);
-        // buckets no wider than the narrowest cell, within [n - 1, 16 (n - 1)]
+        // buckets no wider than the narrowest cell, within [n - 1, 16 (n - 1)] and below 2^22
         long long b = (long long)ceil(L / wmin);
         if (b < n - 1) b = n - 1;
         if (b > 16 * (n - 1)) b = 16 * (n - 1);
+        if (b > (1LL << 22)) b = 1LL << 22;
         nb[a] = b;
+        std::vector<float> r(n);
         for (long long i = 0; i < n; i++) {
             x64.push_back(A[i]);
-            x32.push_back((float)(A[i] - A[0]));
+            r[i] = (float)(A[i] - A[0]);
         }
+        hi32[a] = r[n - 1];
         for (long long i = 0; i + 1 < n; i++) {
-            const double w = (double)(float)(A[i + 1] - A[0]) - (double)(float)(A[i] - A[0]);
-            rw32.push_back((float)(1.0 / w));
+            cell64.push_back(make_double2(A[i], A[i + 1]));
+            cell32.push_back(make_float4(r[i], r[i + 1], (float)(1.0 / ((double)r[i + 1] - (double)r[i])), 0.f));
         }
         for (long long k = 0; k < b; k++) {
             // the cell of the bucket's lower end (largest i in [0, n-2] with A[i] <= t)
@@ -296,26 +302,34 @@ fqsl_status fqsl_field_create_rect(const void *B_dev, fqsl_dtype b_dtype, long l
                 else hi = mid - 1;
             }
             bkt.push_back((int)lo);
+            const int c = (int)lo;
+            float cbits;
+            memcpy(&cbits, &c, sizeof cbits);
+            const float4 c0 = cell32[cell32.size() - (size_t)(n - 1) + (size_t)c];
+            const bool last = lo == n - 2;
+            const float4 c1 = last ? make_float4(0.f, INFINITY, 0.f, 0.f) : cell32[cell32.size() - (size_t)(n - 1) + (size_t)c + 1];
+            bk32.push_back(make_float4(cbits, c0.x, c0.y, c0.z));
+            bk32.push_back(make_float4(last ? INFINITY : c0.y, c1.y, c1.z, 0.f));
         }
     }
     fqsl_field f = new (std::nothrow) fqsl_field_s();
     if (!f) return fail(FQSL_ERR_OOM, "%s: host allocation failed", who);
     set_dims(f, nx, ny, nz);
-    const size_t b64 = align_up(x64.size() * sizeof(double)), b32 = align_up(x32.size() * sizeof(float)),
-                 brw = align_up(rw32.size() * sizeof(float)), bbk = align_up(bkt.size() * sizeof(int));
-    cudaError_t e = cudaMalloc(&f->rect_buf, b64 + b32 + brw + bbk);
+    const size_t s0 = align_up(x64.size() * sizeof(double)), s1 = align_up(cell64.size() * sizeof(double2)),
+                 s2 = align_up(cell32.size() * sizeof(float4)), s3 = align_up(bkt.size() * sizeof(int)),
+                 s4 = align_up(bk32.size() * sizeof(float4));
+    cudaError_t e = cudaMalloc(&f->rect_buf, s0 + s1 + s2 + s3 + s4);
     if (e != cudaSuccess) {
         delete f;
         cudaGetLastError();
         return cuda_fail(e, "fqsl_field_create_rect: coordinate tables");
     }
     char *base = (char *)f->rect_buf;
-    e = cudaMemcpy(base, x64.data(), x64.size() * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(base + b64, x32.data(), x32.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(base + b64 + b32, rw32.data(), rw32.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(base + b64 + b32 + brw, bkt.data(), bkt.size() * sizeof(int), cudaMemcpyHostToDevice);
+    const void *src[5] = {x64.data(), cell64.data(), cell32.data(), bkt.data(), bk32.data()};
+    const size_t len[5] = {x64.size() * sizeof(double), cell64.size() * sizeof(double2),
+                           cell32.size() * sizeof(float4), bkt.size() * sizeof(int), bk32.size() * sizeof(float4)};
+    const size_t off[5] = {0, s0, s0 + s1, s0 + s1 + s2, s0 + s1 + s2 + s3};
+    for (int k = 0; k < 5 && e == cudaSuccess; k++) e = cudaMemcpy(base + off[k], src[k], len[k], cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(f->rect_buf);
         delete f;
@@ -323,27 +337,28 @@ fqsl_status fqsl_field_create_rect(const void *B_dev, fqsl_dtype b_dtype, long l
     }
     FieldView &g = f->g;
     g.rect = 1;
-    long long o64 = 0, orw = 0, obk = 0;
+    long long on = 0, oc = 0, ob = 0;
     for (int a = 0; a < 3; a++) {
         const long long n = N[a];
-        g.x64[a] = (const double *)base + o64;
-        g.x32[a] = (const float *)(base + b64) + o64;
-        g.rw32[a] = (const float *)(base + b64 + b32) + orw;
-        g.bkt[a] = (const int *)(base + b64 + b32 + brw) + obk;
+        g.x64[a] = (const double *)(base + off[0]) + on;
+        g.cell64[a] = (const double2 *)(base + off[1]) + oc;
+        g.cell32[a] = (const float4 *)(base + off[2]) + oc;
+        g.bkt[a] = (const int *)(base + off[3]) + ob;
+        g.bk32[a] = (const float4 *)(base + off[4]) + 2 * ob;
         g.nbkt[a] = (int)nb[a];
         const double L = X[a][n - 1] - X[a][0];
         g.bsc64[a] = (double)nb[a] / L;
         g.bsc32[a] = (float)g.bsc64[a];
         g.lo64[a] = X[a][0];
         g.hi64[a] = X[a][n - 1];
-        g.hi32[a] = x32[o64 + n - 1];
+        g.hi32[a] = hi32[a];
         // FP32 state = physical position relative to the first node
         g.o[a] = X[a][0];
         g.d[a] = 1.0;
         g.rd[a] = 1.f;
-        o64 += n;
-        orw += n - 1;
-        obk += nb[a];
+        on += n;
+        oc += n - 1;
+        ob += nb[a];
     }
     return finish_create(f, B_dev, b_dtype, flags, cuda_stream, out, who);
 }

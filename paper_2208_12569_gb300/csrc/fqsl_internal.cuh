@@ -43,16 +43,22 @@ struct FieldView {
     // then the first node and d = 1, so FP32 state coordinates (r - o)/d are
     // physical coordinates relative to the first node; the FP64 state is the
     // physical position itself.
+    // Cell search: bucket b covers [x_0 + b/bsc, x_0 + (b+1)/bsc) and is no
+    // wider than the narrowest cell (unless that would exceed 16 buckets per
+    // cell), so it holds at most one node.
     int rect;
-    const double *x64[3];  // node coordinates
-    const float *x32[3];   // node coordinates minus the first, as float
-    const float *rw32[3];  // 1/(x_{i+1} - x_i) per cell, float
-    const int *bkt[3];     // cell search: bucket b covers [x_0 + b/bsc, x_0 + (b+1)/bsc), bkt[b] <= its cells
+    const double *x64[3];    // node coordinates
+    const double2 *cell64[3];  // per cell {x_i, x_{i+1}}
+    const int *bkt[3];       // per bucket: the cell of its lower end
+    const float4 *cell32[3];   // per cell, relative to x_0 in float: {x_i, x_{i+1}, 1/(x_{i+1} - x_i), 0}
+    // per bucket (float), 32 B: {bits of c (the cell of its lower end), x_c, x_{c+1}, 1/w_c},
+    // {x_{c+1} or inf when c = n-2, x_{c+2}, 1/w_{c+1}, 0}
+    const float4 *bk32[3];
     int nbkt[3];
-    double bsc64[3];       // buckets per unit length
+    double bsc64[3];         // buckets per unit length
     float bsc32[3];
     double lo64[3], hi64[3];  // first and last node coordinate
-    float hi32[3];            // x32[n-1]
+    float hi32[3];            // x_{n-1} - x_0 in float
 };
 
 struct DevParams {

@@ -235,61 +235,103 @@ __device__ __forceinline__ void gather(const FieldView &f, double x, double y, d
 // ---------------------------------------------------------------------------
 // Stretched (rectilinear) grids (Sec. 2.2): the cell of a coordinate is the
 // largest i in [0, n-2] with x_i <= x (below x_0, and NaN: cell 0). The paper
-// finds it by binary search; here a bucket table gives a nearby cell and a
-// step or two along the axis finish it (each loop moves one way and stops at
-// the axis ends), which gives the same cell for every x.
+// finds it by binary search. Here the coordinate's bucket names a cell and the
+// next node, one comparison picks the cell, and its record (both nodes) checks
+// it; a bucket index that rounding moved to a neighbour fails the check and is
+// walked to the right cell (each walk moves one way and stops at the axis
+// ends), so every x gets the binary search's cell.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int axis_n(const FieldView &f, int a) { return a == 0 ? f.nx : (a == 1 ? f.ny : f.nz); }
 
-__device__ __forceinline__ int rect_cell(const FieldView &f, int a, double x)
+// FP32: cell of x (relative to x_0) with its record {x_c, x_{c+1}, 1/width}.
+// One 32-byte load of the bucket holds both cells a point of the bucket can
+// fall in.
+__device__ __forceinline__ int rect_cell(const FieldView &f, int a, float x, float4 &cr)
 {
-    if (!(x >= f.lo64[a])) return 0;
-    const double *X = f.x64[a];
     const int n = axis_n(f, a);
-    const double bf = (x - f.lo64[a]) * f.bsc64[a];
-    int i = __ldg(f.bkt[a] + (bf < (double)(f.nbkt[a] - 1) ? (int)bf : f.nbkt[a] - 1));
-    while (i < n - 2 && __ldg(X + i + 1) <= x) i++;
-    while (i > 0 && __ldg(X + i) > x) i--;
-    return i;
+    const float bf = fminf(fmaxf(x, 0.f) * f.bsc32[a], (float)(f.nbkt[a] - 1));  // NaN -> bucket 0
+    float c0, x0, x1, r0, thr, x2, r1, pad;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(c0), "=f"(x0), "=f"(x1), "=f"(r0), "=f"(thr), "=f"(x2), "=f"(r1), "=f"(pad)
+        : "l"(f.bk32[a] + 2 * small_int(floorf(bf))));
+    int c = __float_as_int(c0);
+    if (x >= thr) {
+        c++;
+        cr = make_float4(x1, x2, r1, 0.f);
+    } else {
+        cr = make_float4(x0, x1, r0, 0.f);
+    }
+    if ((c > 0 && !(x >= cr.x)) || (c < n - 2 && x >= cr.y)) {
+        // the bucket index was rounded into a neighbour (or x is NaN)
+        if (!(x >= 0.f)) c = 0;
+        while (c < n - 2 && x >= __ldg(f.cell32[a] + c).y) c++;
+        while (c > 0 && x < __ldg(f.cell32[a] + c).x) c--;
+        cr = __ldg(f.cell32[a] + c);
+    }
+    return c;
 }
 
-__device__ __forceinline__ int rect_cell(const FieldView &f, int a, float x)
+// FP64: cell of x (physical) with its nodes {x_c, x_{c+1}}
+__device__ __forceinline__ int rect_cell(const FieldView &f, int a, double x, double2 &cr)
 {
-    if (!(x >= 0.f)) return 0;
-    const float *X = f.x32[a];
     const int n = axis_n(f, a);
-    const float bf = x * f.bsc32[a];
-    int i = __ldg(f.bkt[a] + (bf < (float)(f.nbkt[a] - 1) ? (int)bf : f.nbkt[a] - 1));
-    while (i < n - 2 && __ldg(X + i + 1) <= x) i++;
-    while (i > 0 && __ldg(X + i) > x) i--;
-    return i;
+    int c = 0;
+    if (x >= f.lo64[a]) {
+        const double bf = (x - f.lo64[a]) * f.bsc64[a];
+        c = __ldg(f.bkt[a] + (bf < (double)(f.nbkt[a] - 1) ? (int)bf : f.nbkt[a] - 1));
+    }
+    cr = __ldg(f.cell64[a] + c);
+    while (c < n - 2 && x >= cr.y) cr = __ldg(f.cell64[a] + (++c));
+    while (c > 0 && x < cr.x) cr = __ldg(f.cell64[a] + (--c));
+    return c;
+}
+
+// The cells of a point on the three axes with their records.
+template <typename T>
+struct RectCells;
+template <>
+struct RectCells<float> {
+    int c[3];
+    float4 r[3];
+};
+template <>
+struct RectCells<double> {
+    int c[3];
+    double2 r[3];
+};
+
+template <typename T>
+__device__ __forceinline__ void rect_cells(const FieldView &f, T x, T y, T z, RectCells<T> &rc)
+{
+    rc.c[0] = rect_cell(f, 0, x, rc.r[0]);
+    rc.c[1] = rect_cell(f, 1, y, rc.r[1]);
+    rc.c[2] = rect_cell(f, 2, z, rc.r[2]);
 }
 
 // FP32 on a stretched grid: state coordinates relative to the first node,
 // omega_0 = (x_{i+1} - x) / (x_{i+1} - x_i) with the reciprocal width (Eq. w0)
-__device__ __forceinline__ void gather_rect(const FieldView &f, float x, float y, float z, float B[3], float J[3])
+__device__ __forceinline__ void gather_rect_at(const FieldView &f, float x, float y, float z, const RectCells<float> &rc,
+                                               float B[3], float J[3])
 {
-    const int cx = rect_cell(f, 0, x), cy = rect_cell(f, 1, y), cz = rect_cell(f, 2, z);
-    const float ux = (__ldg(f.x32[0] + cx + 1) - x) * __ldg(f.rw32[0] + cx);
-    const float uy = (__ldg(f.x32[1] + cy + 1) - y) * __ldg(f.rw32[1] + cy);
-    const float uz = (__ldg(f.x32[2] + cz + 1) - z) * __ldg(f.rw32[2] + cz);
-    const unsigned node = ((unsigned)cz * (unsigned)f.ny + (unsigned)cy) * (unsigned)f.nx + (unsigned)cx;
+    const float ux = (rc.r[0].y - x) * rc.r[0].z, uy = (rc.r[1].y - y) * rc.r[1].z, uz = (rc.r[2].y - z) * rc.r[2].z;
+    const unsigned node =
+        ((unsigned)rc.c[2] * (unsigned)f.ny + (unsigned)rc.c[1]) * (unsigned)f.nx + (unsigned)rc.c[0];
     gather_cell32(f, node, 1.f - ux, 1.f - uy, 1.f - uz, ux, uy, uz, B, J);
 }
 
 // FP64 on a stretched grid: Eqs. interp, w0, w1 as written in physical
 // coordinates, the sum nested as in the uniform FP64 gather
-__device__ __forceinline__ void gather_rect(const FieldView &f, double x, double y, double z, double B[3],
-                                            double J[3])
+__device__ __forceinline__ void gather_rect_at(const FieldView &f, double x, double y, double z,
+                                               const RectCells<double> &rc, double B[3], double J[3])
 {
     const double xi[3] = {x, y, z};
     long long c[3];
     double w[3][2];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        c[a] = rect_cell(f, a, xi[a]);
-        const double x1 = __ldg(f.x64[a] + c[a] + 1), x0 = __ldg(f.x64[a] + c[a]);
-        w[a][0] = (x1 - xi[a]) / (x1 - x0);
+        const double2 cr = rc.r[a];
+        c[a] = rc.c[a];
+        w[a][0] = (cr.y - xi[a]) / (cr.y - cr.x);
         w[a][1] = 1.0 - w[a][0];
     }
     const long long sy = f.nx, sz = (long long)f.nx * f.ny;
@@ -315,6 +357,14 @@ __device__ __forceinline__ void gather_rect(const FieldView &f, double x, double
                 J[1] += wt * jy;
                 J[2] += wt * jz;
             }
+}
+
+template <typename T>
+__device__ __forceinline__ void gather_rect(const FieldView &f, T x, T y, T z, T B[3], T J[3])
+{
+    RectCells<T> rc;
+    rect_cells(f, x, y, z, rc);
+    gather_rect_at(f, x, y, z, rc, B, J);
 }
 
 template <bool RECT, typename T>
@@ -344,6 +394,18 @@ __device__ __forceinline__ T hi_of(const FieldView &f, int a)
     }
 }
 
+// FP64: the cells' widths; FP32: their reciprocals
+__device__ __forceinline__ void dd_of(const RectCells<double> &rc, double dd[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; a++) dd[a] = rc.r[a].y - rc.r[a].x;
+}
+__device__ __forceinline__ void dd_of(const RectCells<float> &rc, float dd[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; a++) dd[a] = rc.r[a].z;
+}
+
 // The step's scale per axis, fixed at the start of a trial: FP64 the width
 // of the cell holding the start point (the spacing on a uniform grid), FP32
 // its reciprocal (Sec. 2.3: step and tol scaled per cell).
@@ -354,13 +416,9 @@ __device__ __forceinline__ void step_dd(const FieldView &f, T x, T y, T z, T dd[
 #pragma unroll
         for (int a = 0; a < 3; a++) dd[a] = sizeof(T) == 8 ? (T)f.d[a] : (T)f.rd[a];
     } else {
-        const T p[3] = {x, y, z};
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const int c = rect_cell(f, a, p[a]);
-            if constexpr (sizeof(T) == 8) dd[a] = (T)(__ldg(f.x64[a] + c + 1) - __ldg(f.x64[a] + c));
-            else dd[a] = (T)__ldg(f.rw32[a] + c);
-        }
+        RectCells<T> rc;
+        rect_cells(f, x, y, z, rc);
+        dd_of(rc, dd);
     }
 }
 
@@ -421,10 +479,11 @@ __device__ __forceinline__ bool rhs(const FieldView &f, const double d[3], doubl
 // Stretched grid: bt_a = B_a / D_a with the step's cell widths D, and the
 // physical velocity F = sigma B / |bt| (FP32: rw = 1/D).
 __device__ __forceinline__ bool rhs_rect(const FieldView &f, const float rw[3], float sgn, float x, float y, float z,
-                                         float out[5])
+                                         float out[5], const RectCells<float> *pre = nullptr)
 {
     float B[3], J[3];
-    gather_rect(f, x, y, z, B, J);
+    if (pre) gather_rect_at(f, x, y, z, *pre, B, J);
+    else gather_rect(f, x, y, z, B, J);
     const float b0 = B[0] * rw[0], b1 = B[1] * rw[1], b2 = B[2] * rw[2];
     const float bb = b0 * b0 + b1 * b1 + b2 * b2;
     const float BB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
@@ -442,10 +501,11 @@ __device__ __forceinline__ bool rhs_rect(const FieldView &f, const float rw[3], 
 }
 
 __device__ __forceinline__ bool rhs_rect(const FieldView &f, const double D[3], double sgn, double x, double y,
-                                         double z, double out[5])
+                                         double z, double out[5], const RectCells<double> *pre = nullptr)
 {
     double B[3], J[3];
-    gather_rect(f, x, y, z, B, J);
+    if (pre) gather_rect_at(f, x, y, z, *pre, B, J);
+    else gather_rect(f, x, y, z, B, J);
     const double bt[3] = {B[0] / D[0], B[1] / D[1], B[2] / D[2]};
     const double bb = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
     const double BB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
@@ -460,10 +520,12 @@ __device__ __forceinline__ bool rhs_rect(const FieldView &f, const double D[3], 
     return true;
 }
 
+// pre (stretched grid): the point's cells, already searched
 template <bool RECT, typename T>
-__device__ __forceinline__ bool rhsg(const FieldView &f, const T dd[3], T sgn, T x, T y, T z, T out[5])
+__device__ __forceinline__ bool rhsg(const FieldView &f, const T dd[3], T sgn, T x, T y, T z, T out[5],
+                                     const RectCells<T> *pre = nullptr)
 {
-    if constexpr (RECT) return rhs_rect(f, dd, sgn, x, y, z, out);
+    if constexpr (RECT) return rhs_rect(f, dd, sgn, x, y, z, out, pre);
     else return rhs(f, dd, sgn, x, y, z, out);
 }
 
@@ -1333,7 +1395,13 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
         // FP32 multiplies by 1/d, FP64 divides by d (see rhs); on a stretched
         // grid d is the width of the start point's cell
         T dd[3];
-        step_dd<T, RECT>(f, L.x, L.y, L.z, dd);
+        RectCells<T> rc0;  // stretched grid: the start point's cells (the first stage is there too)
+        if constexpr (RECT) {
+            rect_cells(f, L.x, L.y, L.z, rc0);
+            dd_of(rc0, dd);
+        } else {
+            step_dd<T, RECT>(f, L.x, L.y, L.z, dd);
+        }
 
         // ---- one trial: normal RKF45 step or exit (Henon) step ----
         const bool henon = L.mode != 0;
@@ -1376,7 +1444,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
             py = L.y + hh * py;
             pz = L.z + hh * pz;
             T o[NS];
-            bool ok = rhsg<RECT>(f, dd, sgn, px, py, pz, o);
+            bool ok = rhsg<RECT>(f, dd, sgn, px, py, pz, o, (RECT && s == 0) ? &rc0 : nullptr);
             if constexpr (DEV != 0) {
                 // stage deviation vectors and Eq. rb2: dU/dtau = sigma (ds/dtau) (U . grad)(B/|B|)
                 T us[6];
