@@ -262,8 +262,8 @@ fqsl_status fqsl_field_create_rect(const void *B_dev, fqsl_dtype b_dtype, long l
     }
     st = check_device_ptr(B_dev, who);
     if (st != FQSL_OK) return st;
-    // host tables, one device buffer: x64 | cell64 | cell32 | bkt | bk32
-    std::vector<double> x64;
+    // host tables, one device buffer: x64 | cell64 | cell32 | bkt | bk32 | dco
+    std::vector<double> x64, dco;
     std::vector<double2> cell64;
     std::vector<float4> cell32;
     std::vector<int> bkt;
@@ -286,6 +286,30 @@ fqsl_status fqsl_field_create_rect(const void *B_dev, fqsl_dtype b_dtype, long l
         for (long long i = 0; i < n; i++) {
             x64.push_back(A[i]);
             r[i] = (float)(A[i] - A[0]);
+            // curl stencil coefficients of node i: the derivative of the
+            // quadratic through three neighbouring nodes (see field.cu)
+            double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+            if (n > 2) {
+                if (i == 0) {
+                    const double h1 = A[1] - A[0], h2 = A[2] - A[1];
+                    c0 = -(2.0 * h1 + h2) / (h1 * (h1 + h2));
+                    c1 = (h1 + h2) / (h1 * h2);
+                    c2 = h1 / (h2 * (h1 + h2));
+                } else if (i == n - 1) {
+                    const double h1 = A[n - 2] - A[n - 3], h2 = A[n - 1] - A[n - 2];
+                    c0 = h2 / (h1 * (h1 + h2));
+                    c1 = (h1 + h2) / (h1 * h2);
+                    c2 = (h1 + 2.0 * h2) / (h2 * (h1 + h2));
+                } else {
+                    const double h1 = A[i] - A[i - 1], h2 = A[i + 1] - A[i];
+                    c0 = -h2 / (h1 * (h1 + h2));
+                    c1 = (h2 - h1) / (h1 * h2);
+                    c2 = h1 / (h2 * (h1 + h2));
+                }
+            }
+            dco.push_back(c0);
+            dco.push_back(c1);
+            dco.push_back(c2);
         }
         hi32[a] = r[n - 1];
         for (long long i = 0; i + 1 < n; i++) {
@@ -317,19 +341,20 @@ fqsl_status fqsl_field_create_rect(const void *B_dev, fqsl_dtype b_dtype, long l
     set_dims(f, nx, ny, nz);
     const size_t s0 = align_up(x64.size() * sizeof(double)), s1 = align_up(cell64.size() * sizeof(double2)),
                  s2 = align_up(cell32.size() * sizeof(float4)), s3 = align_up(bkt.size() * sizeof(int)),
-                 s4 = align_up(bk32.size() * sizeof(float4));
-    cudaError_t e = cudaMalloc(&f->rect_buf, s0 + s1 + s2 + s3 + s4);
+                 s4 = align_up(bk32.size() * sizeof(float4)), s5 = align_up(dco.size() * sizeof(double));
+    cudaError_t e = cudaMalloc(&f->rect_buf, s0 + s1 + s2 + s3 + s4 + s5);
     if (e != cudaSuccess) {
         delete f;
         cudaGetLastError();
         return cuda_fail(e, "fqsl_field_create_rect: coordinate tables");
     }
     char *base = (char *)f->rect_buf;
-    const void *src[5] = {x64.data(), cell64.data(), cell32.data(), bkt.data(), bk32.data()};
-    const size_t len[5] = {x64.size() * sizeof(double), cell64.size() * sizeof(double2),
-                           cell32.size() * sizeof(float4), bkt.size() * sizeof(int), bk32.size() * sizeof(float4)};
-    const size_t off[5] = {0, s0, s0 + s1, s0 + s1 + s2, s0 + s1 + s2 + s3};
-    for (int k = 0; k < 5 && e == cudaSuccess; k++) e = cudaMemcpy(base + off[k], src[k], len[k], cudaMemcpyHostToDevice);
+    const void *src[6] = {x64.data(), cell64.data(), cell32.data(), bkt.data(), bk32.data(), dco.data()};
+    const size_t len[6] = {x64.size() * sizeof(double), cell64.size() * sizeof(double2),
+                           cell32.size() * sizeof(float4), bkt.size() * sizeof(int), bk32.size() * sizeof(float4),
+                           dco.size() * sizeof(double)};
+    const size_t off[6] = {0, s0, s0 + s1, s0 + s1 + s2, s0 + s1 + s2 + s3, s0 + s1 + s2 + s3 + s4};
+    for (int k = 0; k < 6 && e == cudaSuccess; k++) e = cudaMemcpy(base + off[k], src[k], len[k], cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(f->rect_buf);
         delete f;
@@ -341,6 +366,7 @@ fqsl_status fqsl_field_create_rect(const void *B_dev, fqsl_dtype b_dtype, long l
     for (int a = 0; a < 3; a++) {
         const long long n = N[a];
         g.x64[a] = (const double *)(base + off[0]) + on;
+        g.dco[a] = (const double *)(base + off[5]) + 3 * on;
         g.cell64[a] = (const double2 *)(base + off[1]) + oc;
         g.cell32[a] = (const float4 *)(base + off[2]) + oc;
         g.bkt[a] = (const int *)(base + off[3]) + ob;

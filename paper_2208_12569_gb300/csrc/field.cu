@@ -60,29 +60,25 @@ __global__ void __launch_bounds__(256) k_curl_pack(const TI *__restrict__ B, int
     }
 }
 
-// Stretched grid (Sec. 2.2): d f/d x_a at node index i along an axis with node
-// coordinates X, as the derivative of the quadratic through three
-// neighbouring nodes (one-sided at the ends, first order on a 2-node axis);
-// on a uniform axis these are the stencils above. Written as plain
-// expressions in a fixed order.
+// Stretched grid (Sec. 2.2): d f/d x_a at node index i along an axis, as the
+// derivative of the quadratic through three neighbouring nodes (one-sided at
+// the ends, first order on a 2-node axis); on a uniform axis these are the
+// stencils above. co = the node's three coefficients, formed on the host
+// from the node coordinates X (fqsl_field_create_rect); with them each
+// derivative is a plain sum of products in a fixed order:
+//   inside: c0 f_{i-1} + c1 f_i + c2 f_{i+1}; first node: c0 f_0 + c1 f_1 -
+//   c2 f_2; last node: c0 f_{n-3} - c1 f_{n-2} + c2 f_{n-1}.
 template <typename TI>
 __device__ __forceinline__ double node_diff_rect(const TI *__restrict__ B, int c, long long node, long long stride,
-                                                 long long i, long long n, const double *__restrict__ X)
+                                                 long long i, long long n, const double *__restrict__ X,
+                                                 const double *__restrict__ co)
 {
     auto F = [&](long long kk) -> double { return (double)B[(node + (kk - i) * stride) * 3 + c]; };
     if (n == 2) return (F(1) - F(0)) / (X[1] - X[0]);
-    if (i == 0) {
-        const double h1 = X[1] - X[0], h2 = X[2] - X[1];
-        return -(2.0 * h1 + h2) / (h1 * (h1 + h2)) * F(0) + (h1 + h2) / (h1 * h2) * F(1) -
-               h1 / (h2 * (h1 + h2)) * F(2);
-    }
-    if (i == n - 1) {
-        const double h1 = X[n - 2] - X[n - 3], h2 = X[n - 1] - X[n - 2];
-        return h2 / (h1 * (h1 + h2)) * F(n - 3) - (h1 + h2) / (h1 * h2) * F(n - 2) +
-               (h1 + 2.0 * h2) / (h2 * (h1 + h2)) * F(n - 1);
-    }
-    const double h1 = X[i] - X[i - 1], h2 = X[i + 1] - X[i];
-    return -h2 / (h1 * (h1 + h2)) * F(i - 1) + (h2 - h1) / (h1 * h2) * F(i) + h1 / (h2 * (h1 + h2)) * F(i + 1);
+    const double c0 = co[3 * i], c1 = co[3 * i + 1], c2 = co[3 * i + 2];
+    if (i == 0) return c0 * F(0) + c1 * F(1) - c2 * F(2);
+    if (i == n - 1) return c0 * F(n - 3) - c1 * F(n - 2) + c2 * F(n - 1);
+    return c0 * F(i - 1) + c1 * F(i) + c2 * F(i + 1);
 }
 
 template <typename TI>
@@ -97,12 +93,12 @@ __global__ void __launch_bounds__(256) k_curl_pack_rect(const TI *__restrict__ B
         const long long i = node % nx;
         const long long j = (node / nx) % ny;
         const long long k = node / sz;
-        const double dyBz = node_diff_rect(B, 2, node, sy, j, ny, g.x64[1]);
-        const double dzBy = node_diff_rect(B, 1, node, sz, k, nz, g.x64[2]);
-        const double dzBx = node_diff_rect(B, 0, node, sz, k, nz, g.x64[2]);
-        const double dxBz = node_diff_rect(B, 2, node, 1, i, nx, g.x64[0]);
-        const double dxBy = node_diff_rect(B, 1, node, 1, i, nx, g.x64[0]);
-        const double dyBx = node_diff_rect(B, 0, node, sy, j, ny, g.x64[1]);
+        const double dyBz = node_diff_rect(B, 2, node, sy, j, ny, g.x64[1], g.dco[1]);
+        const double dzBy = node_diff_rect(B, 1, node, sz, k, nz, g.x64[2], g.dco[2]);
+        const double dzBx = node_diff_rect(B, 0, node, sz, k, nz, g.x64[2], g.dco[2]);
+        const double dxBz = node_diff_rect(B, 2, node, 1, i, nx, g.x64[0], g.dco[0]);
+        const double dxBy = node_diff_rect(B, 1, node, 1, i, nx, g.x64[0], g.dco[0]);
+        const double dyBx = node_diff_rect(B, 0, node, sy, j, ny, g.x64[1], g.dco[1]);
         const double Jx = dyBz - dzBy, Jy = dzBx - dxBz, Jz = dxBy - dyBx;
         const double Bx = (double)B[node * 3 + 0], By = (double)B[node * 3 + 1], Bz = (double)B[node * 3 + 2];
         if (rec32) {

@@ -48,6 +48,7 @@ struct FieldView {
     // cell), so it holds at most one node.
     int rect;
     const double *x64[3];    // node coordinates
+    const double *dco[3];    // per node, the three coefficients of its d/dx_a stencil (curl B)
     const double2 *cell64[3];  // per cell {x_i, x_{i+1}}
     const int *bkt[3];       // per bucket: the cell of its lower end
     const float4 *cell32[3];   // per cell, relative to x_0 in float: {x_i, x_{i+1}, 1/(x_{i+1} - x_i), 0}

@@ -243,6 +243,16 @@ __device__ __forceinline__ void gather(const FieldView &f, double x, double y, d
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int axis_n(const FieldView &f, int a) { return a == 0 ? f.nx : (a == 1 ? f.ny : f.nz); }
 
+// The walk of a bucket index that rounding moved into a neighbouring bucket
+// (rare; kept out of line to keep the tracer's code small).
+static __device__ __noinline__ int rect_walk32(const float4 *__restrict__ cells, int n, float x, int c)
+{
+    if (!(x >= 0.f)) return 0;
+    while (c < n - 2 && x >= __ldg(cells + c).y) c++;
+    while (c > 0 && x < __ldg(cells + c).x) c--;
+    return c;
+}
+
 // FP32: cell of x (relative to x_0) with its record {x_c, x_{c+1}, 1/width}.
 // One 32-byte load of the bucket holds both cells a point of the bucket can
 // fall in.
@@ -263,9 +273,7 @@ __device__ __forceinline__ int rect_cell(const FieldView &f, int a, float x, flo
     }
     if ((c > 0 && !(x >= cr.x)) || (c < n - 2 && x >= cr.y)) {
         // the bucket index was rounded into a neighbour (or x is NaN)
-        if (!(x >= 0.f)) c = 0;
-        while (c < n - 2 && x >= __ldg(f.cell32[a] + c).y) c++;
-        while (c > 0 && x < __ldg(f.cell32[a] + c).x) c--;
+        c = rect_walk32(f.cell32[a], n, x, c);
         cr = __ldg(f.cell32[a] + c);
     }
     return c;
