@@ -44,12 +44,14 @@ class Params(C.Structure):
     _fields_ = [("method", C.c_int), ("way", C.c_int), ("tol", C.c_double), ("h0", C.c_double),
                 ("hmin", C.c_double), ("hmax", C.c_double), ("max_steps", C.c_longlong),
                 ("rot_thresh", C.c_double), ("tol_exp", C.c_double), ("graze", C.c_double),
-                ("eps2", C.c_double)]
+                ("eps2", C.c_double), ("qperp", C.c_int)]
 
 
 def params(method=1, way=1, tol=10 ** -3.2, h0=0.5, hmin=1e-6, hmax=4.0, max_steps=100000,
-           rot_thresh=0.05, tol_exp=1.5, graze=1e-3, eps2=1e-3) -> Params:
-    return Params(method, way, tol, h0, hmin, hmax, max_steps, rot_thresh, tol_exp, graze, eps2)
+           rot_thresh=0.05, tol_exp=1.5, graze=1e-3, eps2=1e-3, qperp=0) -> Params:
+    """Oracle parameters (readings R2, R5, R9, R10, R17 of fqsl_oracle.c);
+    qperp = 1 gives Q_perp (Method II)."""
+    return Params(method, way, tol, h0, hmin, hmax, max_steps, rot_thresh, tol_exp, graze, eps2, qperp)
 
 
 def lib():

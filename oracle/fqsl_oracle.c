@@ -85,6 +85,12 @@
  *   R10 Method II: S0 is always perpendicular to B (Sec. 4), U0, V0 = the u, v
  *       of R9, tol = tol as given; dU/ds = (U . grad)(B/B), integrated in physical
  *       coordinates alongside R1; Q by Eq. q_scott with absolute values.
+ *   R17 Q_perp (Sec. 2.1, after Titov 2007): S1 and S2 turned perpendicular to
+ *       the line at its ends, so in Eq. q_scott n = B/|B| at each end: U~ = U -
+ *       (U . B)/(B . B) B and B_n,e = |B_e|; with S0 perpendicular to B as in
+ *       R10, Q_perp = |U~1^2 V~2^2 + U~2^2 V~1^2 - 2 (U~1.V~1)(U~2.V~2)|
+ *       |B1| |B2| / |B0|^2. Method II only (the paper notes Method I's
+ *       difficulty with it).
  *   R11 Line status bits: MAXSTEPS 1, NULL_B 2 (|bt| = 0 or not finite at an
  *       evaluation), STALL 4, MIXED 8, OUTSIDE 16 (seed outside the box),
  *       ROTATED 32, CHORD 64. Q and Tw are NaN when MAXSTEPS, NULL_B or OUTSIDE
@@ -147,6 +153,7 @@ typedef struct {
     double tol_exp;      /* 1.5 */
     double graze;        /* 1e-3 */
     double eps2;         /* 1e-3 cells */
+    int qperp;           /* Method II: 1 = Q_perp (R17) */
 } OParams;
 
 typedef struct {
@@ -763,13 +770,23 @@ static double o_q_method1(const OField *f, const OLine *c, const OLine *nb[4], d
     return norm2 * fabs(bn1 * bn2) / (bn0 * bn0);
 }
 
-/* Method II (R10, Eq. q_scott) from the deviation vectors at both ends */
-static double o_q_method2(const OLine *c, double bn0)
+/* Method II (R10, Eq. q_scott) from the deviation vectors at both ends;
+ * perp: Q_perp (R17), the end planes perpendicular to B */
+static double o_q_method2(const OLine *c, double bn0, int perp)
 {
     double Ut[2][3], Vt[2][3], bn[2];
     for (int e = 0; e < 2; e++) {
         int a = c->face[e] >> 1;
         const double *U = c->end[e] + 5, *V = c->end[e] + 8, *B = c->Bend[e];
+        if (perp) {
+            double BB = o_dot(B, B), ub = o_dot(U, B) / BB, vb = o_dot(V, B) / BB;
+            bn[e] = sqrt(BB);
+            for (int b = 0; b < 3; b++) {
+                Ut[e][b] = U[b] - ub * B[b];
+                Vt[e][b] = V[b] - vb * B[b];
+            }
+            continue;
+        }
         bn[e] = B[a];
         for (int b = 0; b < 3; b++) {
             Ut[e][b] = U[b] - U[a] / B[a] * B[b];
@@ -979,7 +996,7 @@ static int o_qmap(const OField *fp, const double lo[3], const double a1[3], cons
         double Q;
         if (p->method == 2) {
             o_trace_line(&f, p, S.r0, S.n0, S.tol, S.u, S.v, &c);
-            Q = o_q_method2(&c, S.bn0);
+            Q = o_q_method2(&c, S.bn0, p->qperp);
         } else {
             o_trace_line(&f, p, S.r0, S.n0, S.tol, NULL, NULL, &c);
             OLine nbl[4];
