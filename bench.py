@@ -852,8 +852,8 @@ def main():
     # Method II (deviation vectors) on the same map, both ways of grad(B/|B|)
     fieldg = fq.Field(Bd, grid.origin, grid.spacing, pack=("f32", "gradb"))
     m2 = {}
-    for way in (1, 2):
-        pm2 = fq.params(precision="f32", tol=TOL, method=2, gradb_way=way)
+    for way, qperp in ((1, 0), (2, 0), (1, 1)):
+        pm2 = fq.params(precision="f32", tol=TOL, method=2, gradb_way=way, qperp=qperp)
         fq.qmap_plane(fieldg, (0.0, 0.0, 0.0), u, v, NU, NV, pm2, out=out)
         torch.cuda.synchronize()
         tms = []
@@ -865,8 +865,8 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
             tms.append(e0.elapsed_time(e1))
-        m2["way%d" % way] = {"value": n / (float(np.mean(tms)) / 1000.0), "unit": "Q+Tw values/s",
-                             "ms_per_step": float(np.mean(tms))}
+        m2["way%d" % way + ("_qperp" if qperp else "")] = {"value": n / (float(np.mean(tms)) / 1000.0),
+                                                          "unit": "Q+Tw values/s", "ms_per_step": float(np.mean(tms))}
     fieldg.close()
     step(pacc)
     torch.cuda.synchronize()
@@ -922,7 +922,8 @@ def main():
                           "ms_per_step": float(np.mean(msacc)),
                           "trace_ms": float(np.mean([k[0] for k in kernacc])),
                           "note": "error norm and length/Tw sums accumulated in FP64 every step"},
-            "method2_f32": dict(m2, note="deviation vectors (Method II), tol = tol_perp, same map"),
+            "method2_f32": dict(m2, note="deviation vectors (Method II), tol = tol_perp, same map; "
+                                         "_qperp: Q_perp, end planes perpendicular to B"),
             "fp64": {"value": value64, "unit": "Q+Tw values/s", "ms_per_step": float(np.mean(ms64)),
                      "trace_ms": float(np.mean([k[0] for k in kern64])),
                      "speedup_fp32_over_fp64": value / ws / value64},

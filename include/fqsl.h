@@ -115,6 +115,10 @@ typedef struct {
     int reverse_precision; /* precision of fqsl_backward's reverse sweep for this taped map: -1 (default)
                              = precision; FQSL_F32, FQSL_F32_ACC64 (float state, double node grid) or
                              FQSL_F64; the field must be packed in it */
+    int qperp;            /* Method II: 1 = Q_perp, with S1 and S2 turned perpendicular to the line at its
+                             ends (Sec. 2.1, after Titov 2007): in Eq. q_scott n = B/|B| at each end, so
+                             U~ = U - (U.B)/(B.B) B and B_n,e = |B_e|; 0 (default) = Q on the exit faces.
+                             Method I returns FQSL_ERR_UNSUPPORTED for 1 */
 } fqsl_params;
 
 /* Output buffers of one call (caller-owned device memory, n = number of

@@ -498,6 +498,8 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
         return fail(FQSL_ERR_UNSUPPORTED, "%s: field was not packed in FP64 (FQSL_PACK_F64)", who);
     if (p->method == 2 && p->gradb_way == 1 && !(p->precision == FQSL_F64 ? f->grad64 : f->grad32))
         return fail(FQSL_ERR_UNSUPPORTED, "%s: Method II way 1 needs a field packed with FQSL_PACK_GRADB", who);
+    if (p->qperp != 0 && p->qperp != 1) return fail(FQSL_ERR_ARG, "%s: qperp must be 0 or 1", who);
+    if (p->qperp && p->method != 2) return fail(FQSL_ERR_UNSUPPORTED, "%s: Q_perp needs Method II", who);
     if (f->g.rect && p->method != 1)
         return fail(FQSL_ERR_UNSUPPORTED, "%s: Method II is not available on a stretched grid", who);
     if (f->g.rect && p->tape) return fail(FQSL_ERR_UNSUPPORTED, "%s: no step tape on a stretched grid", who);
@@ -854,6 +856,7 @@ fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params
         g.out = *out;
         g.n = n;
         g.want_q = 1;
+        g.qperp = p->qperp;
         e = f32 ? launch_assemble_m2_f32(g, stream) : launch_assemble_m2_f64(g, stream);
         if (e != cudaSuccess) return cuda_fail(e, who);
         mark(f, 3, stream);

@@ -126,6 +126,7 @@ __device__ __forceinline__ double dot3(const double *a, const double *b) { retur
 // deviation vectors are projected onto the exit face along B, U~ = U -
 // (U.n)/(B.n) B, and Q = |U~1^2 V~2^2 + U~2^2 V~1^2 - 2 (U~1.V~1)(U~2.V~2)|
 // |Bn1 Bn2| / Bn0^2 with Bn0 = |B| at the seed (S0 perpendicular to B).
+// Q_perp (qperp): the end planes perpendicular to B, n = B/|B| at each end.
 __global__ void __launch_bounds__(256) k_assemble_m2(const AssembleArgs A)
 {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < A.n;
@@ -139,6 +140,16 @@ __global__ void __launch_bounds__(256) k_assemble_m2(const AssembleArgs A)
             for (int e = 0; e < 2; e++) {
                 const int a = (e == 0 ? R.f1 : R.f2)[idx] >> 1;
                 const double *U = R.dev64 + 12 * idx + 6 * e, *V = U + 3, *B = R.be64 + 6 * idx + 3 * e;
+                if (A.qperp) {
+                    // Q_perp: the end plane perpendicular to B, n = B/|B|
+                    const double BB = dot3(B, B), ub = dot3(U, B) / BB, vb = dot3(V, B) / BB;
+                    bn[e] = sqrt(BB);
+                    for (int b = 0; b < 3; b++) {
+                        Ut[e][b] = U[b] - ub * B[b];
+                        Vt[e][b] = V[b] - vb * B[b];
+                    }
+                    continue;
+                }
                 bn[e] = B[a];
                 for (int b = 0; b < 3; b++) {
                     Ut[e][b] = U[b] - U[a] / B[a] * B[b];

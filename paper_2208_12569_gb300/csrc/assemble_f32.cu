@@ -163,8 +163,18 @@ __global__ void __launch_bounds__(256) k_assemble_m2_f32(const AssembleArgs A)
                 const double B[3] = {Bf[0], Bf[1], Bf[2]};
                 const float *dv = R.dev32 + 12 * idx + 6 * e;
                 const double U[3] = {dv[0], dv[1], dv[2]}, V[3] = {dv[3], dv[4], dv[5]};
-                bn[e] = B[a];
-                const double ru = U[a] / B[a], rv = V[a] / B[a];
+                double ru, rv;
+                if (A.qperp) {
+                    // Q_perp: the end plane perpendicular to B
+                    const double BB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+                    bn[e] = sqrt(BB);
+                    ru = (U[0] * B[0] + U[1] * B[1] + U[2] * B[2]) / BB;
+                    rv = (V[0] * B[0] + V[1] * B[1] + V[2] * B[2]) / BB;
+                } else {
+                    bn[e] = B[a];
+                    ru = U[a] / B[a];
+                    rv = V[a] / B[a];
+                }
                 for (int b = 0; b < 3; b++) {
                     Ut[e][b] = U[b] - ru * B[b];
                     Vt[e][b] = V[b] - rv * B[b];

@@ -186,6 +186,7 @@ struct AssembleArgs {
     fqsl_out out;
     long long n;
     int want_q;
+    int qperp;  // Method II: Q_perp (end planes perpendicular to B)
 };
 
 constexpr unsigned kBad = FQSL_LINE_MAXSTEPS | FQSL_LINE_NULL_B | FQSL_LINE_OUTSIDE;

@@ -295,3 +295,58 @@ def test_method2_way1_needs_gradient_grid(fq):
     with pytest.raises(fq.FqslError) as ei:
         fq.qmap_plane(field, (-1, -1, 0), (0.1, 0, 0), (0, 0.1, 0), 4, 4, fq.params(method=2, gradb_way=1))
     assert ei.value.status == 5
+
+
+# ---------------------------------------------------------------------------
+# Q_perp: Method II with S1, S2 perpendicular to the line at its ends (Sec. 2.1
+# after Titov 2007)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("way", [1, 2])
+def test_qperp_monopole_fp64_bitwise_and_fp32(fq, oracle_lib, mono, way):
+    B, grid = mono
+    field = _field_m2(fq, B, grid)
+    nu, nv = 61, 43
+    args = ((0.0, 0.0, 0.0), (63.0 / nu, 0, 0), (0, 55.0 / nv, 0), nu, nv)
+    g = _gpu_plane(fq, field, *args, precision="f64", method=2, gradb_way=way, qperp=1)
+    r = oracle.plane(B.astype(np.float64), grid, *args, oracle.params(method=2, way=way, qperp=1))
+    assert_fp64_parity(g, r)
+    assert_bitwise(g, r)
+    # Q_perp and the face Q are different numbers on this map
+    rf = oracle.plane(B.astype(np.float64), grid, *args, oracle.params(method=2, way=way))
+    ok = np.isfinite(r["Q"])
+    assert np.median(np.abs(r["Q"][ok] / rf["Q"][ok] - 1)) > 1e-3
+    g32 = _gpu_plane(fq, field, *args, precision="f32", method=2, gradb_way=way, qperp=1)
+    rel = q_rel(g32, r)
+    assert np.median(rel[np.isfinite(rel)]) < 1e-3
+
+
+def test_qperp_interior_volume_fp64_bitwise(fq, oracle_lib, mono):
+    B, grid = mono
+    field = _field_m2(fq, B, grid)
+    step = (63.0 / 12, 55.0 / 10, 31.0 / 4)
+    g = to_np(fq.qmap_volume(field, (0.0, 0.0, 0.0), step, 12, 10, 4,
+                             fq.params(precision="f64", method=2, qperp=1)))
+    field.check()
+    r = oracle.qmap(B.astype(np.float64), grid, (0.0, 0.0, 0.0), (step[0], 0, 0), (0, step[1], 0), (0, 0, step[2]),
+                    (12, 10, 4), oracle.params(method=2, qperp=1))
+    assert_bitwise(g, r)
+
+
+def test_qperp_closed_form_on_gpu(fq, oracle_lib):
+    # the rigid rotation maps perpendicular cross-sections isometrically:
+    # Q_perp = 2. (FP32 way 2 differences B/|B| in float over 0.002 cells, and
+    # the rounding of B/|B| it amplifies leaves about 1 % on these lines.)
+    B = synth.analytic_cube("rotation")
+    field = _field_m2(fq, B, G1)
+    d = 0.5 / 16
+    for prec, tol, bound in (("f64", 1e-10, 1e-6), ("f32", 1e-6, 2e-2)):
+        g = _gpu_plane(fq, field, (-0.25, -0.25, 0.0), (d, 0, 0), (0, d, 0), 16, 16, precision=prec, method=2,
+                       gradb_way=2, tol=tol, qperp=1)
+        assert np.max(np.abs(g["Q"] / 2 - 1)) < bound
+
+
+def test_qperp_needs_method2(fq):
+    field = _field(fq, synth.analytic_cube("uniform"), G1)
+    with pytest.raises(fq.FqslError) as ei:
+        fq.qmap_plane(field, (-1, -1, 0), (0.1, 0, 0), (0, 0.1, 0), 4, 4, fq.params(qperp=1))
+    assert ei.value.status == 5
