@@ -44,14 +44,18 @@ class Params(C.Structure):
     _fields_ = [("method", C.c_int), ("way", C.c_int), ("tol", C.c_double), ("h0", C.c_double),
                 ("hmin", C.c_double), ("hmax", C.c_double), ("max_steps", C.c_longlong),
                 ("rot_thresh", C.c_double), ("tol_exp", C.c_double), ("graze", C.c_double),
-                ("eps2", C.c_double), ("qperp", C.c_int)]
+                ("eps2", C.c_double), ("qperp", C.c_int), ("scheme", C.c_int), ("step", C.c_double),
+                ("step_min", C.c_double)]
 
 
 def params(method=1, way=1, tol=10 ** -3.2, h0=0.5, hmin=1e-6, hmax=4.0, max_steps=100000,
-           rot_thresh=0.05, tol_exp=1.5, graze=1e-3, eps2=1e-3, qperp=0) -> Params:
-    """Oracle parameters (readings R2, R5, R9, R10, R17 of fqsl_oracle.c);
-    qperp = 1 gives Q_perp (Method II)."""
-    return Params(method, way, tol, h0, hmin, hmax, max_steps, rot_thresh, tol_exp, graze, eps2, qperp)
+           rot_thresh=0.05, tol_exp=1.5, graze=1e-3, eps2=1e-3, qperp=0, scheme=0, step=3.0,
+           step_min=0.15) -> Params:
+    """Oracle parameters (readings R2, R5, R9, R10, R17, R18 of fqsl_oracle.c);
+    qperp = 1 gives Q_perp (Method II); scheme = 1 the fixed-step 3/8-rule RK4
+    with step_perp = step and Eq. step's floor step_min."""
+    return Params(method, way, tol, h0, hmin, hmax, max_steps, rot_thresh, tol_exp, graze, eps2, qperp, scheme,
+                  step, step_min)
 
 
 def lib():

@@ -112,6 +112,16 @@
  *       quadratic through the three nodes; one-sided on the faces), which are
  *       the R4 stencils on a uniform axis. Method II is not defined on a
  *       stretched grid here.
+ *   R18 Fixed-step scheme (Sec. 2.3, Kutta's 3/8-rule RK4; Sec. 4 Eq. step):
+ *       with scheme = 1 every trial is one 3/8-rule step of the line's fixed size
+ *       (cells, index space as in R1; length and Tw ride along) and is always
+ *       accepted. A Method I lattice seed steps max(step_perp |Bn0/B|,
+ *       step_min) (Eq. step); rotated seeds and their extra lines, Method II
+ *       lines and seed lists step step_perp (the perpendicular case). The exit
+ *       is R5 with 3/8-rule stages; a grazing exit halves the step, which then
+ *       stays halved, down to h_min before the chord fallback. The paper gives
+ *       no step_min; the library's default is step_perp x rot_thresh (the
+ *       obliquity floor of R9).
  *   R13 Derivatives (the paper has none; the adjoint tests): d(Q, Tw)/dB is
  *       that of the traced computation with each line's accepted step sizes,
  *       exit faces and exit kinds (exit step, clamped exit step, chord after
@@ -154,6 +164,9 @@ typedef struct {
     double graze;        /* 1e-3 */
     double eps2;         /* 1e-3 cells */
     int qperp;           /* Method II: 1 = Q_perp (R17) */
+    int scheme;          /* 0 = RKF45 (R2), 1 = fixed-step 3/8-rule RK4 (R18) */
+    double step;         /* R18: step_perp (cells) */
+    double step_min;     /* R18: lower bound of Eq. step (cells) */
 } OParams;
 
 typedef struct {
@@ -451,6 +464,9 @@ static const double FA[6][5] = {
 static const double FB4[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0};
 static const double FB5[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0,
                               2.0 / 55.0};
+/* Kutta's 3/8 rule (R18) */
+static const double K38A[4][3] = {{0, 0, 0}, {1.0 / 3.0, 0, 0}, {-1.0 / 3.0, 1.0, 0}, {1.0, -1.0, 1.0}};
+static const double K38B[4] = {1.0 / 8.0, 3.0 / 8.0, 3.0 / 8.0, 1.0 / 8.0};
 
 /* One RKF45 step of size h from y (D: see o_rhs). With haxis >= 0 the
  * independent variable is y[haxis] (Henon step, R5): the RHS is divided by its
@@ -461,10 +477,12 @@ static int o_rkf45(const OField *f, const OParams *p, const double *D, double si
                    double hsign, const double *y, double h, double *y4, double *y5)
 {
     double k[6][NSTATE], ys[NSTATE];
-    for (int s = 0; s < 6; s++) {
+    const int rk38 = p->scheme == 1;  /* R18: the 3/8 rule, 4 stages, no error estimate */
+    const int nst = rk38 ? 4 : 6;
+    for (int s = 0; s < nst; s++) {
         for (int c = 0; c < ns; c++) {
             double acc = 0.0;
-            for (int r = 0; r < s; r++) acc += FA[s][r] * k[r][c];
+            for (int r = 0; r < s; r++) acc += (rk38 ? K38A[s][r] : FA[s][r]) * k[r][c];
             ys[c] = y[c] + h * acc;
         }
         if (o_rhs(f, p, D, sigma, ns, ys, k[s])) return 1;
@@ -477,6 +495,12 @@ static int o_rkf45(const OField *f, const OParams *p, const double *D, double si
     }
     for (int c = 0; c < ns; c++) {
         double a4 = 0.0, a5 = 0.0;
+        if (rk38) {
+            for (int s = 0; s < 4; s++) a4 += K38B[s] * k[s][c];
+            y4[c] = y[c] + h * a4;
+            if (y5) y5[c] = y4[c];
+            continue;
+        }
         for (int s = 0; s < 6; s++) {
             a4 += FB4[s] * k[s][c];
             a5 += FB5[s] * k[s][c];
@@ -544,6 +568,7 @@ static int o_chord_face(const OField *f, const double *y, const double *yn, doub
 }
 
 /* Trace one direction from the seed state; writes the end state and face.
+ * tol: the line's tolerance, or with the fixed-step scheme its step (R18).
  * Returns nonzero when the line must stop with a bad status. */
 static int o_trace_dir(const OField *f, const OParams *p, double tol, double sigma, int ns, const double *yseed,
                        double *yend, int *face, long long *steps, int *status, OLog *log)
@@ -551,7 +576,7 @@ static int o_trace_dir(const OField *f, const OParams *p, double tol, double sig
     o_log(log, sigma, 99);
     double y[NSTATE], y4[NSTATE], y5[NSTATE], yt[NSTATE], D[3];
     memcpy(y, yseed, sizeof(double) * ns);
-    double h = p->h0;
+    double h = p->scheme == 1 ? tol : p->h0;
     *face = -1;
     for (;;) {
         if (*steps >= p->max_steps) {
@@ -566,24 +591,27 @@ static int o_trace_dir(const OField *f, const OParams *p, double tol, double sig
             memcpy(yend, y, sizeof(double) * ns);
             return 1;
         }
-        double e2 = 0.0;
-        if (f->X[0]) {
-            for (int a = 0; a < 3; a++) e2 += ((y5[a] - y4[a]) / D[a]) * ((y5[a] - y4[a]) / D[a]);
-        } else {
-            for (int a = 0; a < 3; a++) e2 += (y5[a] - y4[a]) * (y5[a] - y4[a]);
-        }
-        double err = sqrt(e2);
-        if (err > tol) {
-            if (h > p->hmin) {
-                h = h * fmax(0.1, 0.9 * sqrt(sqrt(tol / err)));
-                if (h < p->hmin) h = p->hmin;
-                continue;
+        double hn = h; /* the fixed step (R18) */
+        if (p->scheme != 1) {
+            double e2 = 0.0;
+            if (f->X[0]) {
+                for (int a = 0; a < 3; a++) e2 += ((y5[a] - y4[a]) / D[a]) * ((y5[a] - y4[a]) / D[a]);
+            } else {
+                for (int a = 0; a < 3; a++) e2 += (y5[a] - y4[a]) * (y5[a] - y4[a]);
             }
-            *status |= ST_STALL;
+            double err = sqrt(e2);
+            if (err > tol) {
+                if (h > p->hmin) {
+                    h = h * fmax(0.1, 0.9 * sqrt(sqrt(tol / err)));
+                    if (h < p->hmin) h = p->hmin;
+                    continue;
+                }
+                *status |= ST_STALL;
+            }
+            hn = (err > 0.0) ? h * fmin(4.0, 0.9 * sqrt(sqrt(tol / err))) : 4.0 * h;
+            if (hn < p->hmin) hn = p->hmin;
+            if (hn > p->hmax) hn = p->hmax;
         }
-        double hn = (err > 0.0) ? h * fmin(4.0, 0.9 * sqrt(sqrt(tol / err))) : 4.0 * h;
-        if (hn < p->hmin) hn = p->hmin;
-        if (hn > p->hmax) hn = p->hmax;
         if (o_inside(f, y4)) {
             o_log(log, h, 0);
             memcpy(y, y4, sizeof(double) * ns);
@@ -827,9 +855,12 @@ static int o_on_face(const OField *f, const double n0[3], const double r[3])
 
 typedef struct {
     double r0[3], n0[3], bh[3], u[3], v[3];
-    double bn0, bn0s, tol; /* Bn0 used by Q, signed B0.n0 */
+    double bn0, bn0s, tol; /* Bn0 used by Q, signed B0.n0; tol: the line's tolerance or step (R18) */
     int rotated, bad;
 } OSeed;
+
+/* the tolerance (RKF45) or step (3/8 rule) of a line in the perpendicular case */
+static double o_ctl_perp(const OParams *p) { return p->scheme == 1 ? p->step : p->tol; }
 
 /* S0 frame and tolerance of one lattice seed (R9, R10) */
 static void o_seed_setup(const OField *f, const OParams *p, const OLattice *L, long long i, long long j,
@@ -858,18 +889,22 @@ static void o_seed_setup(const OField *f, const OParams *p, const OLattice *L, l
     o_perp_frame(S->bh, S->u, S->v);
     if (p->method == 2) {
         S->bn0 = nB;
-        S->tol = p->tol;
+        S->tol = o_ctl_perp(p);
         return;
     }
     double ratio = fabs(o_dot(B, S->n0)) / nB;
     if (ratio < p->rot_thresh && !o_on_face(f, S->n0, S->r0)) {
         S->rotated = 1;
         S->bn0 = nB;
-        S->tol = p->tol;
+        S->tol = o_ctl_perp(p);
     } else {
         S->bn0 = o_dot(B, S->n0);
-        double x = fmax(ratio, p->rot_thresh);
-        S->tol = p->tol * (p->tol_exp == 1.5 ? x * sqrt(x) : pow(x, p->tol_exp));
+        if (p->scheme == 1) {
+            S->tol = fmax(p->step * ratio, p->step_min); /* Eq. step (R18) */
+        } else {
+            double x = fmax(ratio, p->rot_thresh);
+            S->tol = p->tol * (p->tol_exp == 1.5 ? x * sqrt(x) : pow(x, p->tol_exp));
+        }
     }
 }
 
@@ -1010,7 +1045,7 @@ static int o_qmap(const OField *fp, const double lo[3], const double a1[3], cons
                     const double *dir = (q < 2) ? S.u : S.v;
                     double sg = (q & 1) ? -1.0 : 1.0, rr[3];
                     for (int a = 0; a < 3; a++) rr[a] = S.r0[a] + sg * drot * dir[a];
-                    o_trace_line(&f, p, rr, nrot, p->tol, NULL, NULL, &nbl[q]);
+                    o_trace_line(&f, p, rr, nrot, o_ctl_perp(p), NULL, NULL, &nbl[q]);
                     nb[q] = &nbl[q];
                 }
                 Q = o_q_method1(&f, &c, nb, drot, drot, S.bn0, &c.status);
@@ -1040,7 +1075,7 @@ static int o_twist(const OField *fp, const double *seeds, long long ns, const OP
 #pragma omp parallel for schedule(dynamic, 4)
     for (long long s = 0; s < ns; s++) {
         OLine c;
-        o_trace_line(&f, p, seeds + 3 * s, NULL, p->tol, NULL, NULL, &c);
+        o_trace_line(&f, p, seeds + 3 * s, NULL, o_ctl_perp(p), NULL, NULL, &c);
         o_write(&f, &c, s, NAN, NULL, Two, leno, r1, r2, f1, f2, st, steps);
     }
     return 0;
@@ -1136,7 +1171,7 @@ int oracle_lattice_log(const double *B, const double *J, const long long n[3], c
 {
     OField f;
     if (o_make_field(&f, B, J, NULL, n, o, d)) return 1;
-    if (p->method != 1) return 2;
+    if (p->method != 1 || p->scheme != 0) return 2; /* the adjoint differentiates RKF45 (R13) */
     OLattice L;
     for (int a = 0; a < 3; a++) {
         L.o[a] = lo[a];
@@ -1187,7 +1222,7 @@ int oracle_lattice_log(const double *B, const double *J, const long long n[3], c
                     for (int a = 0; a < 3; a++) rr[a] = S.r0[a] + sg * drot * dir[a];
                     OLine xl;
                     OLog gx = {xlogh + (4 * s + q) * (long long)cap, xlogc + (4 * s + q) * (long long)cap, cap, 0, 0};
-                    o_trace_line_log(&f, p, rr, nrot, p->tol, NULL, NULL, &xl, &gx, &sx);
+                    o_trace_line_log(&f, p, rr, nrot, o_ctl_perp(p), NULL, NULL, &xl, &gx, &sx);
                     xlogn[4 * s + q] = gx.overflow ? -1 : gx.n;
                     xs0[4 * s + q] = sx;
                     xfaces[8 * s + 2 * q] = xl.face[0];
