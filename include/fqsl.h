@@ -119,6 +119,15 @@ typedef struct {
                              ends (Sec. 2.1, after Titov 2007): in Eq. q_scott n = B/|B| at each end, so
                              U~ = U - (U.B)/(B.B) B and B_n,e = |B_e|; 0 (default) = Q on the exit faces.
                              Method I returns FQSL_ERR_UNSUPPORTED for 1 */
+    int scheme;           /* 0 = RKF45 (default); 1 = fixed-step 3/8-rule RK4 (Sec. 2.3): every trial is one
+                             Kutta 3/8 step of the line's fixed size, always accepted (tol, h0, h_max unused).
+                             A Method I lattice seed steps max(step |Bn0/B|, step_min) (Sec. 4 Eq. step);
+                             rotated seeds, their extra lines, Method II lines and seed lists step `step`.
+                             A grazing exit halves the step for the rest of the direction (down to h_min).
+                             Uniform grids only; no step tape, no batches (FQSL_ERR_UNSUPPORTED) */
+    double step;          /* scheme 1: step_perp in cells, default 3.0 (Method I in the paper's Table 1) */
+    double step_min;      /* scheme 1: lower bound of Eq. step in cells, default 0.15 = 3.0 x rot_thresh (the
+                             paper gives no value) */
 } fqsl_params;
 
 /* Output buffers of one call (caller-owned device memory, n = number of

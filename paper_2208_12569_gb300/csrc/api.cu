@@ -65,8 +65,8 @@ struct fqsl_field_s {
     size_t scratch_cap = 0;
     void *rect_buf = nullptr;  // stretched grid: coordinate, width and bucket tables (FieldView::x64 ...)
     unsigned long long *counters = nullptr;  // [0] primary head, [1] extra head, [2] rotated count (low 32 bits)
-    int blocks_cache[3][3] = {};  // [precision][source] resident blocks per SM
-    int blocks_cache_m2[2][2] = {};  // Method II: [fp64][way - 1]
+    int blocks_cache[2][3][3] = {};  // [scheme][precision][source] resident blocks per SM
+    int blocks_cache_m2[2][2][2] = {};  // Method II: [scheme][fp64][way - 1]
     int blocks_cache_tape[3][2] = {};  // taped tracers: [precision][lattice, extra]
     bool timing = false, timed = false, extra_timed = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -204,6 +204,9 @@ void fqsl_params_default(fqsl_params *p)
     p->eps_way2 = 1e-3;
     p->sync_dirs = -1;
     p->reverse_precision = -1;
+    p->scheme = 0;
+    p->step = 3.0;
+    p->step_min = 0.15;
 }
 
 const char *fqsl_version(void) { return "fqsl 0.1.0 (sm_103a)"; }
@@ -499,6 +502,14 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
     if (p->method == 2 && p->gradb_way == 1 && !(p->precision == FQSL_F64 ? f->grad64 : f->grad32))
         return fail(FQSL_ERR_UNSUPPORTED, "%s: Method II way 1 needs a field packed with FQSL_PACK_GRADB", who);
     if (p->qperp != 0 && p->qperp != 1) return fail(FQSL_ERR_ARG, "%s: qperp must be 0 or 1", who);
+    if (p->scheme != 0 && p->scheme != 1) return fail(FQSL_ERR_ARG, "%s: scheme must be 0 or 1", who);
+    if (p->scheme == 1) {
+        if (!(p->step > 0) || !isfinite(p->step)) return fail(FQSL_ERR_ARG, "%s: step must be > 0", who);
+        if (!(p->step_min >= 0) || !(p->step_min <= p->step))
+            return fail(FQSL_ERR_ARG, "%s: need 0 <= step_min <= step", who);
+        if (f->g.rect) return fail(FQSL_ERR_UNSUPPORTED, "%s: the fixed-step scheme runs on uniform grids", who);
+        if (p->tape) return fail(FQSL_ERR_UNSUPPORTED, "%s: the step tape records RKF45 maps", who);
+    }
     if (p->qperp && p->method != 2) return fail(FQSL_ERR_UNSUPPORTED, "%s: Q_perp needs Method II", who);
     if (f->g.rect && p->method != 1)
         return fail(FQSL_ERR_UNSUPPORTED, "%s: Method II is not available on a stretched grid", who);
@@ -527,6 +538,9 @@ DevParams dev_params(const fqsl_params *p)
     d.refill = p->refill_lanes > 0 ? p->refill_lanes : kDefaultRefill;
     d.sync_dirs = p->sync_dirs >= 0 ? p->sync_dirs : kDefaultSyncDirs;
     d.chunk = (p->chunk_tiles > 0 ? p->chunk_tiles : 1) * kTileU * kTileV;
+    d.scheme = p->scheme;
+    d.step = p->step;
+    d.step_min = p->step_min;
     return d;
 }
 
@@ -614,11 +628,14 @@ fqsl_status ensure_scratch(fqsl_field f, size_t bytes)
     return FQSL_OK;
 }
 
-int blocks_per_sm(fqsl_field f, int precision, int src)
+int blocks_per_sm(fqsl_field f, int precision, int src, int p_scheme)
 {
-    int &c = f->blocks_cache[precision][src];
+    int &c = f->blocks_cache[p_scheme][precision][src];
     if (!c) {
-        if (f->g.rect)
+        if (p_scheme == 1)
+            c = precision == FQSL_F64 ? trace_rk38_blocks_per_sm_f64(src)
+                                      : trace_rk38_blocks_per_sm_f32(src, precision == FQSL_F32_ACC64);
+        else if (f->g.rect)
             c = precision == FQSL_F64 ? trace_rect_blocks_per_sm_f64(src)
                                       : trace_rect_blocks_per_sm_f32(src, precision == FQSL_F32_ACC64);
         else
@@ -632,7 +649,7 @@ cudaError_t launch_trace(fqsl_field f, const fqsl_params *p, const TraceArgs &a,
                          cudaStream_t s)
 {
     const long long warps_needed = (items + 31) / 32;
-    int bps = blocks_per_sm(f, p->precision, src);
+    int bps = blocks_per_sm(f, p->precision, src, p->scheme);
     if (p->blocks_per_sm > 0 && p->blocks_per_sm < bps) bps = p->blocks_per_sm;
     long long grid = (long long)f->sms * bps;
     const long long need = (warps_needed * 32 + kTraceBlock - 1) / kTraceBlock;
@@ -645,10 +662,15 @@ cudaError_t launch_trace(fqsl_field f, const fqsl_params *p, const TraceArgs &a,
 
 cudaError_t launch_trace_m2(fqsl_field f, const fqsl_params *p, const TraceArgs &a, cudaStream_t s)
 {
-    int &c = f->blocks_cache_m2[p->precision == FQSL_F64 ? 1 : 0][p->gradb_way - 1];
-    if (!c)
-        c = p->precision == FQSL_F64 ? trace_dev_blocks_per_sm_f64(p->gradb_way)
-                                     : trace_dev_blocks_per_sm_f32(p->gradb_way);
+    int &c = f->blocks_cache_m2[p->scheme][p->precision == FQSL_F64 ? 1 : 0][p->gradb_way - 1];
+    if (!c) {
+        if (p->scheme == 1)
+            c = p->precision == FQSL_F64 ? trace_dev_rk38_blocks_per_sm_f64(p->gradb_way)
+                                         : trace_dev_rk38_blocks_per_sm_f32(p->gradb_way);
+        else
+            c = p->precision == FQSL_F64 ? trace_dev_blocks_per_sm_f64(p->gradb_way)
+                                         : trace_dev_blocks_per_sm_f32(p->gradb_way);
+    }
     long long grid = (long long)f->sms * (p->blocks_per_sm > 0 && p->blocks_per_sm < c ? p->blocks_per_sm : c);
     const long long need = (a.nitems + kTraceBlock - 1) / kTraceBlock;
     if (need < grid) grid = need;
@@ -1297,6 +1319,7 @@ extern "C" fqsl_status fqsl_batch_create(const fqsl_field *fields, const fqsl_pl
     if (!fields || !planes || !outs || n < 1) return fail(FQSL_ERR_ARG, "%s: need n >= 1 fields, planes, outs", who);
     if (!p) return fail(FQSL_ERR_ARG, "%s: NULL params", who);
     if (p->method != 1) return fail(FQSL_ERR_UNSUPPORTED, "%s: batches run Method I", who);
+    if (p->scheme != 0) return fail(FQSL_ERR_UNSUPPORTED, "%s: batches run RKF45", who);
     const bool f32 = p->precision != FQSL_F64;
     std::vector<Lattice> lats(n);
     std::vector<size_t> off(n);

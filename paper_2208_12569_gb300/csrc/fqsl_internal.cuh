@@ -69,6 +69,8 @@ struct DevParams {
     int refill;     // minimum idle lanes before a warp takes new seeds
     int sync_dirs;  // lanes wait for each other before their second direction
     int chunk;      // work items per grab of the counter (a multiple of 32)
+    int scheme;     // 0 = RKF45, 1 = fixed-step 3/8 rule
+    double step, step_min;  // fixed-step scheme: step_perp and Eq. step's floor (cells)
 };
 
 // Cell-centred lattice seed(i,j,k) = o + (i+1/2) a1 + (j+1/2) a2 + (k+1/2) a3.
@@ -248,6 +250,15 @@ cudaError_t launch_trace_rect_f64(const TraceArgs &a, int src, int grid, cudaStr
 int trace_rect_blocks_per_sm_f32(int src, bool acc64);
 int trace_rect_blocks_per_sm_f64(int src);
 cudaError_t launch_seed_prep_rect_f32(const TraceArgs &a, long long n, unsigned grid, cudaStream_t s);
+// the fixed-step 3/8-rule instantiations (uniform grids; Method I sources and Method II ways)
+cudaError_t launch_trace_rk38_f32(const TraceArgs &a, int src, int grid, cudaStream_t s, bool acc64);
+cudaError_t launch_trace_rk38_f64(const TraceArgs &a, int src, int grid, cudaStream_t s);
+cudaError_t launch_trace_dev_rk38_f32(const TraceArgs &a, int way, int grid, cudaStream_t s);
+cudaError_t launch_trace_dev_rk38_f64(const TraceArgs &a, int way, int grid, cudaStream_t s);
+int trace_rk38_blocks_per_sm_f32(int src, bool acc64);
+int trace_rk38_blocks_per_sm_f64(int src);
+int trace_dev_rk38_blocks_per_sm_f32(int way);
+int trace_dev_rk38_blocks_per_sm_f64(int way);
 // Method II tracers (deviation vectors; way 1 = gradient grid, 2 = +-eps)
 cudaError_t launch_trace_dev_f32(const TraceArgs &a, int way, int grid, int block, cudaStream_t s);
 cudaError_t launch_trace_dev_f64(const TraceArgs &a, int way, int grid, int block, cudaStream_t s);

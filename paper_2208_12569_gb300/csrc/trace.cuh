@@ -81,6 +81,30 @@ struct Fehlberg {
     }
 };
 
+// Kutta's 3/8 rule (fixed-step scheme, Sec. 2.3).
+template <typename T>
+struct Kutta38 {
+    static __device__ __forceinline__ T a(int s, int r)
+    {
+        const double A[4][3] = {{0, 0, 0}, {1.0 / 3.0, 0, 0}, {-1.0 / 3.0, 1.0, 0}, {1.0, -1.0, 1.0}};
+        return (T)A[s][r];
+    }
+    static __device__ __forceinline__ T b(int s)
+    {
+        const double B[4] = {1.0 / 8.0, 3.0 / 8.0, 3.0 / 8.0, 1.0 / 8.0};
+        return (T)B[s];
+    }
+};
+
+// The stages of a trial: SCH 0 = RKF45 (6 stages, 4th-order solution and the
+// 5th-order error estimate), 1 = the 3/8 rule (4 stages, no estimate).
+template <typename T, int SCH>
+struct Tab {
+    static constexpr int N = SCH ? 4 : 6;
+    static __device__ __forceinline__ T a(int s, int r) { return SCH ? Kutta38<T>::a(s, r) : Fehlberg<T>::a(s, r); }
+    static __device__ __forceinline__ T b(int s) { return SCH ? Kutta38<T>::b(s) : Fehlberg<T>::b4(s); }
+};
+
 // ---------------------------------------------------------------------------
 // trilinear gather of B and curl B at index position (x, y, z)
 // ---------------------------------------------------------------------------
@@ -652,6 +676,10 @@ __device__ __forceinline__ bool grad_bhat(const FieldView &f, T eps, T x, T y, T
 __device__ __forceinline__ float root4(float v) { return sqrtf(sqrtf(v)); }
 __device__ __forceinline__ double root4(double v) { return sqrt(sqrt(v)); }
 
+// the tolerance (RKF45) or step (fixed-step scheme) of a line in the
+// perpendicular case: rotated seeds, their extra lines, Method II, seed lists
+__device__ __forceinline__ double ctl_perp(const DevParams &p) { return p.scheme == 1 ? p.step : p.tol; }
+
 // x^e for the obliquity factor of Eq. tol (x sqrt(x) for the usual e = 1.5)
 __device__ __forceinline__ double obliq_pow(double x, double e) { return e == 1.5 ? x * sqrt(x) : pow(x, e); }
 
@@ -1019,7 +1047,7 @@ __device__ __forceinline__ bool finish_dir(const TraceArgs &A, const LineRecs &R
                 L.v[c] = L.v0[c];
             }
         }
-        L.h = (T)A.p.h0;
+        L.h = A.p.scheme == 1 ? (T)L.tol : (T)A.p.h0;  // fixed step: the line's step (in tol)
         L.mode = 0;
         L.tcur = -1;
         L.tn = 0;
@@ -1047,8 +1075,9 @@ __device__ __forceinline__ bool inside(const FieldView &f, T x, T y, T z)
 }
 
 // Start a line at index position xi (FP64: (r0 - o)/d as written) with
-// orientation vector n (NULL: end 1 is the backward end). Returns false if the
-// line ends at once (outside / null).
+// orientation vector n (NULL: end 1 is the backward end) and tolerance tol
+// (with the fixed-step scheme: its step). Returns false if the line ends at
+// once (outside / null).
 template <typename T, bool ACC, bool RECT = false>
 __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R, Lane<T> &L, const double xi[3],
                                            const double *n, double tol, int st0)
@@ -1069,7 +1098,11 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
     L.tn = 0;
     acc_reset<T, ACC>(L);
     L.h = (T)A.p.h0;
-    if (kF64) {
+    if (A.p.scheme == 1) {
+        // fixed-step scheme: tol carries the line's step
+        L.tol = tol;
+        L.h = (T)tol;
+    } else if (kF64) {
         L.tol = tol;
     } else {
         L.tol = tol * tol;
@@ -1158,7 +1191,7 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
         L.tcur = -1;
         L.tn = 0;
         acc_reset<T, ACC>(L);
-        L.h = (T)A.p.h0;
+        L.h = A.p.scheme == 1 ? (T)sd.w : (T)A.p.h0;  // fixed step: the pre-pass's step
         if constexpr (DEV != 0) {
             const float4 fu = A.prep.fu[idx], fv = A.prep.fv[idx];
             L.u[0] = L.u0[0] = fu.x;
@@ -1183,8 +1216,8 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
 #pragma unroll
         for (int a = 0; a < 3; a++) xi[a] = fma(fk, G.xa3[a], fma(fj, G.xa2[a], fma(fi, G.xa1[a], G.xo[a])));
     }
-    // B at the seed, S0 obliquity and tolerance
-    double tol = A.p.tol;
+    // B at the seed, S0 obliquity and tolerance (fixed-step scheme: step)
+    double tol = ctl_perp(A.p);
     int st0 = 0;
     double bn0 = 0.0;
     const bool in = in_box<T, RECT>(f, xi);
@@ -1213,7 +1246,9 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
                     }
                 } else {
                     bn0 = (double)bn;
-                    if (kF64) {
+                    if (A.p.scheme == 1) {
+                        tol = fmax(A.p.step * (double)ratio, A.p.step_min);  // Eq. step
+                    } else if (kF64) {
                         tol = A.p.tol * obliq_pow(fmax((double)ratio, A.p.rot), A.p.texp);
                     } else {
                         const float x = fmaxf((float)ratio, (float)A.p.rot);
@@ -1274,7 +1309,7 @@ __device__ __forceinline__ bool init_extra(const TraceArgs &A, Lane<T> &L, long 
 #pragma unroll
     for (int a = 0; a < 3; a++) xr[a] = state_of<T, RECT>(f, rr[a], a);
     L.line = item;
-    return start_line<T, ACC, RECT>(A, A.ext, L, xr, nrot, A.p.tol, 0);
+    return start_line<T, ACC, RECT>(A, A.ext, L, xr, nrot, ctl_perp(A.p), 0);
 }
 
 template <typename T, bool ACC, bool RECT = false>
@@ -1285,7 +1320,7 @@ __device__ __forceinline__ bool init_list(const TraceArgs &A, Lane<T> &L, long l
     double xi[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) xi[a] = state_of<T, RECT>(f, A.seeds[3 * item + a], a);
-    return start_line<T, ACC, RECT>(A, A.rec, L, xi, nullptr, A.p.tol, 0);
+    return start_line<T, ACC, RECT>(A, A.rec, L, xi, nullptr, ctl_perp(A.p), 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1305,10 +1340,14 @@ __device__ __forceinline__ bool init_list(const TraceArgs &A, Lane<T> &L, long l
 // twist lists): positions are physical (FP32: relative to the first node),
 // cells are searched, and each trial scales its step and error by the widths
 // of the cell it starts in (Sec. 2.3).
-template <typename T, int SRC, bool ACC, int DEV = 0, bool BATCH = false, bool TAPE = false, bool RECT = false>
+// SCH: 0 = RKF45, 1 = the fixed-step 3/8 rule (every trial accepted; the
+// line's step is held in L.h, halved only by a grazing exit).
+template <typename T, int SRC, bool ACC, int DEV = 0, bool BATCH = false, bool TAPE = false, bool RECT = false,
+          int SCH = 0>
 __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs &BA)
 {
     static_assert(!(RECT && (DEV != 0 || TAPE)), "stretched grids: Method I and twist lists, no tape");
+    static_assert(!(SCH && (RECT || TAPE || BATCH)), "fixed-step scheme: uniform grids, no tape, no batches");
     constexpr bool SPLIT = TAPE && SRC == kSrcLattice;
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -1438,12 +1477,13 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
         T ad[6] = {0, 0, 0, 0, 0, 0};           // Method II: 4th-order sums of U, V
         T l4 = 0, tw4 = 0;
         int fail = 0;  // first failing stage: 1 null field, 2 grazing exit step
+        constexpr int NST = Tab<T, SCH>::N;
 #pragma unroll
-        for (int s = 0; s < 6; s++) {
+        for (int s = 0; s < NST; s++) {
             T px = 0, py = 0, pz = 0;
 #pragma unroll
             for (int r = 0; r < s; r++) {
-                const T c = Fehlberg<T>::a(s, r);
+                const T c = Tab<T, SCH>::a(s, r);
                 px += c * k0[r];
                 py += c * k1[r];
                 pz += c * k2[r];
@@ -1460,7 +1500,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                 for (int c = 0; c < 6; c++) {
                     T acc = 0;
 #pragma unroll
-                    for (int r = 0; r < s; r++) acc += Fehlberg<T>::a(s, r) * kd[r][c];
+                    for (int r = 0; r < s; r++) acc += Tab<T, SCH>::a(s, r) * kd[r][c];
                     us[c] = (c < 3 ? L.u[c] : L.v[c - 3]) + hh * acc;
                 }
                 T G[3][3];
@@ -1496,7 +1536,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                     for (int c = 0; c < NS; c++) o[c] *= inv;
                 }
             }
-            if (s < 5) {
+            if (s < NST - 1) {
                 k0[s] = o[0];
                 k1[s] = o[1];
                 k2[s] = o[2];
@@ -1507,16 +1547,18 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
             }
             if constexpr (DEV != 0) {
 #pragma unroll
-                for (int c = 0; c < 6; c++) ad[c] += Fehlberg<T>::b4(s) * o[5 + c];
+                for (int c = 0; c < 6; c++) ad[c] += Tab<T, SCH>::b(s) * o[5 + c];
             }
-            const T b = Fehlberg<T>::b4(s);
-            const T e = kF64 ? Fehlberg<T>::b5(s) : Fehlberg<T>::e(s);
+            const T b = Tab<T, SCH>::b(s);
             a4[0] += b * o[0];
             a4[1] += b * o[1];
             a4[2] += b * o[2];
-            a5[0] += e * o[0];
-            a5[1] += e * o[1];
-            a5[2] += e * o[2];
+            if constexpr (SCH == 0) {
+                const T e = kF64 ? Fehlberg<T>::b5(s) : Fehlberg<T>::e(s);
+                a5[0] += e * o[0];
+                a5[1] += e * o[1];
+                a5[2] += e * o[2];
+            }
             l4 += b * o[3];
             tw4 += b * o[4];
         }
@@ -1532,61 +1574,63 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
             // written; FP32: err^2 = h^2 |sum (b5 - b4) k|^2 accumulated in FP64
             // and compared with tol^2, the step factor (tol/err)^(1/4) =
             // (tol^2/err^2)^(1/8) in float)
-            double err = 0.0;
-            float rf = 0.f;
-            bool over, pos;
-            if (kF64) {
-                double d0 = (double)((L.x + hh * a5[0]) - nx), d1 = (double)((L.y + hh * a5[1]) - ny),
-                       d2 = (double)((L.z + hh * a5[2]) - nz);
-                if constexpr (RECT) {
-                    // in cells of the start cell
-                    d0 = d0 / (double)dd[0];
-                    d1 = d1 / (double)dd[1];
-                    d2 = d2 / (double)dd[2];
+            T hn = L.h;  // fixed-step scheme: every trial is accepted, the step is kept
+            if constexpr (SCH == 0) {
+                double err = 0.0;
+                float rf = 0.f;
+                bool over, pos;
+                if (kF64) {
+                    double d0 = (double)((L.x + hh * a5[0]) - nx), d1 = (double)((L.y + hh * a5[1]) - ny),
+                           d2 = (double)((L.z + hh * a5[2]) - nz);
+                    if constexpr (RECT) {
+                        // in cells of the start cell
+                        d0 = d0 / (double)dd[0];
+                        d1 = d1 / (double)dd[1];
+                        d2 = d2 / (double)dd[2];
+                    }
+                    err = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                    over = err > L.tol;
+                    pos = err > 0.0;
+                } else if (ACC) {
+                    double ex = (double)a5[0], ey = (double)a5[1], ez = (double)a5[2];
+                    if constexpr (RECT) {
+                        ex *= (double)dd[0];
+                        ey *= (double)dd[1];
+                        ez *= (double)dd[2];
+                    }
+                    err = (double)(hh * hh) * (ex * ex + ey * ey + ez * ez);  // err^2
+                    over = err > L.tol;
+                    pos = err > 0.0;
+                    rf = __fdividef(L.tolf2, (float)err);
+                } else {
+                    T e5[3] = {a5[0], a5[1], a5[2]};
+                    if constexpr (RECT) {
+                        e5[0] *= dd[0];
+                        e5[1] *= dd[1];
+                        e5[2] *= dd[2];
+                    }
+                    const float e2 = (float)(hh * hh) * (float)(e5[0] * e5[0] + e5[1] * e5[1] + e5[2] * e5[2]);
+                    over = e2 > L.tolf2;
+                    pos = e2 > 0.f;
+                    rf = __fdividef(L.tolf2, e2);
                 }
-                err = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-                over = err > L.tol;
-                pos = err > 0.0;
-            } else if (ACC) {
-                double ex = (double)a5[0], ey = (double)a5[1], ez = (double)a5[2];
-                if constexpr (RECT) {
-                    ex *= (double)dd[0];
-                    ey *= (double)dd[1];
-                    ez *= (double)dd[2];
+                if (over) {
+                    if (L.h > hmin) {
+                        const T q = kF64 ? (T)root4(L.tol / err) : (T)sqrtf(root4(rf));
+                        T hn = L.h * fmax((T)0.1, (T)0.9 * q);
+                        L.h = hn < hmin ? hmin : hn;
+                        continue;
+                    }
+                    L.st |= FQSL_LINE_STALL;
                 }
-                err = (double)(hh * hh) * (ex * ex + ey * ey + ez * ez);  // err^2
-                over = err > L.tol;
-                pos = err > 0.0;
-                rf = __fdividef(L.tolf2, (float)err);
-            } else {
-                T e5[3] = {a5[0], a5[1], a5[2]};
-                if constexpr (RECT) {
-                    e5[0] *= dd[0];
-                    e5[1] *= dd[1];
-                    e5[2] *= dd[2];
-                }
-                const float e2 = (float)(hh * hh) * (float)(e5[0] * e5[0] + e5[1] * e5[1] + e5[2] * e5[2]);
-                over = e2 > L.tolf2;
-                pos = e2 > 0.f;
-                rf = __fdividef(L.tolf2, e2);
-            }
-            if (over) {
-                if (L.h > hmin) {
+                if (pos) {
                     const T q = kF64 ? (T)root4(L.tol / err) : (T)sqrtf(root4(rf));
-                    T hn = L.h * fmax((T)0.1, (T)0.9 * q);
-                    L.h = hn < hmin ? hmin : hn;
-                    continue;
+                    hn = L.h * fmin((T)4, (T)0.9 * q);
+                } else {
+                    hn = (T)4 * L.h;
                 }
-                L.st |= FQSL_LINE_STALL;
+                hn = hn < hmin ? hmin : (hn > hmax ? hmax : hn);
             }
-            T hn;
-            if (pos) {
-                const T q = kF64 ? (T)root4(L.tol / err) : (T)sqrtf(root4(rf));
-                hn = L.h * fmin((T)4, (T)0.9 * q);
-            } else {
-                hn = (T)4 * L.h;
-            }
-            hn = hn < hmin ? hmin : (hn > hmax ? hmax : hn);
             if (inside<T, RECT>(f, nx, ny, nz)) {
                 if constexpr (TAPE) tape_step(A.tape, L, hh);
                 L.x = nx;
@@ -1741,7 +1785,7 @@ __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
     const float x = (float)xi[0], y = (float)xi[1], z = (float)xi[2];
     uint8_t fl = 0;
     unsigned bad = 0;
-    double bn0 = 0.0, tol = A.p.tol;
+    double bn0 = 0.0, tol = ctl_perp(A.p);
     const bool in = in_box<float, RECT>(f, xi);
     if (!in) {
         bad = FQSL_LINE_OUTSIDE;
@@ -1772,6 +1816,9 @@ __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
                     const unsigned slot = atomicAdd(A.q.rot_count, 1u);
                     A.q.rot_seed[slot] = (int32_t)idx;
                     A.q.rot_slot[idx] = (int32_t)slot + 1;
+                } else if (A.p.scheme == 1) {
+                    bn0 = (double)bn;
+                    tol = fmax(A.p.step * (double)ratio, A.p.step_min);  // Eq. step
                 } else {
                     bn0 = (double)bn;
                     const float xr = fmaxf(ratio, (float)A.p.rot);
@@ -1806,7 +1853,8 @@ __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
         R.st[idx] = (uint8_t)bad;
         R.steps[idx] = 0;
     }
-    A.prep.seed[idx] = make_float4(x, y, z, (float)(tol * tol));
+    // w: tol^2, or with the fixed-step scheme the line's step
+    A.prep.seed[idx] = make_float4(x, y, z, A.p.scheme == 1 ? (float)tol : (float)(tol * tol));
     A.prep.flags[idx] = fl;
 }
 

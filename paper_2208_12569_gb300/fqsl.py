@@ -39,7 +39,8 @@ class Params(C.Structure):
                 ("max_steps", C.c_longlong), ("rot_thresh", C.c_double), ("tol_exp", C.c_double),
                 ("graze", C.c_double), ("eps_way2", C.c_double), ("sync_dirs", C.c_int), ("chunk_tiles", C.c_int),
                 ("blocks_per_sm", C.c_int), ("tape", C.c_int), ("tape_chunk", C.c_int),
-                ("reverse_precision", C.c_int), ("qperp", C.c_int)]
+                ("reverse_precision", C.c_int), ("qperp", C.c_int), ("scheme", C.c_int), ("step", C.c_double),
+                ("step_min", C.c_double)]
 
 
 class Plane(C.Structure):
@@ -104,8 +105,9 @@ def _check(status):
 def params(**kw) -> Params:
     """fqsl_params with the library defaults, overridden by keyword
     (method, gradb_way, precision ('f32'/'f64'/'f32acc64' or 0/1/2), tol, h0, h_min, h_max,
-    max_steps, rot_thresh, tol_exp, graze, eps_way2, qperp (Method II Q_perp), scheduling
-    knobs, and for the adjoint tape, tape_chunk, reverse_precision)."""
+    max_steps, rot_thresh, tol_exp, graze, eps_way2, qperp (Method II Q_perp), scheme (0 RKF45, 1
+    fixed-step 3/8-rule RK4) with step and step_min, scheduling knobs, and for the adjoint tape,
+    tape_chunk, reverse_precision)."""
     p = Params()
     _lib.fqsl_params_default(C.byref(p))
     for k, v in kw.items():

@@ -46,6 +46,7 @@ def test_params_defaults():
     assert p.sync_dirs == -1 and p.chunk_tiles == 0 and p.blocks_per_sm == 0 and p.refill_lanes == 0
     assert p.eps_way2 == 1e-3 and p.graze == 1e-3
     assert p.tape == 0 and p.tape_chunk == 0 and p.reverse_precision == -1 and p.qperp == 0
+    assert p.scheme == 0 and p.step == 3.0 and p.step_min == 0.15
 
 
 def test_host_argument_errors(lib):

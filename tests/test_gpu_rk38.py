@@ -1,0 +1,131 @@
+"""The fixed-step scheme (Sec. 2.3: Kutta's 3/8-rule RK4; Sec. 4 Eq. step for
+the per-line step; reading R18 of the oracle) on the CUDA path against the FP64
+oracle, through the C ABI: FP64 bit-identical, FP32 error bounded."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import assert_bitwise, assert_fp64_parity, q_rel, to_np, tw_rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+G1 = synth.C1_GRID
+E2 = math.e ** 2 + math.e ** -2
+
+
+@pytest.fixture(scope="module")
+def fq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2208_12569_gb300 as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def mono():
+    grid = synth.Grid((64, 56, 32), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    ch = synth.random_charges(np.random.default_rng(2208), 10, ((0.0, 63.0), (0.0, 55.0)), depth=(4.0, 12.0))
+    return synth.monopole_cube(grid, ch, dtype=np.float32), grid
+
+
+def _field(fq, B, grid, pack=("f32", "f64")):
+    return fq.Field(torch.from_numpy(np.ascontiguousarray(B)).cuda(), grid.origin, grid.spacing, pack=pack)
+
+
+def _plane(fq, field, *args, **kw):
+    out = fq.qmap_plane(field, *args, fq.params(scheme=1, **kw))
+    field.check()
+    return to_np(out)
+
+
+def _ora(**kw):
+    return oracle.params(scheme=1, **kw)
+
+
+@pytest.mark.parametrize("step", [3.0, 0.7])
+def test_plane_fp64_bitwise_and_fp32(fq, oracle_lib, mono, step):
+    B, grid = mono
+    field = _field(fq, B, grid)
+    nu, nv = 101, 75
+    args = ((0.0, 0.0, 0.0), (63.0 / nu, 0, 0), (0, 55.0 / nv, 0), nu, nv)
+    g = _plane(fq, field, *args, precision="f64", step=step)
+    r = oracle.plane(B.astype(np.float64), grid, *args, _ora(step=step))
+    assert_fp64_parity(g, r)
+    assert_bitwise(g, r)
+    for prec in ("f32", "f32acc64"):
+        g32 = _plane(fq, field, *args, precision=prec, step=step)
+        assert np.mean(g32["face2"] == r["face2"]) > 0.99
+        rel = q_rel(g32, r)
+        assert np.median(rel[np.isfinite(rel)]) < 1e-3
+        t = tw_rel(g32, r)
+        assert np.median(t[np.isfinite(t)]) < 1e-4
+
+
+def test_interior_plane_rotation_fp64_bitwise(fq, oracle_lib, mono):
+    B, grid = mono
+    field = _field(fq, B, grid)
+    args = ((0.0, 10.3, 0.0), (63.0 / 70, 0, 0), (0, 0, 31.0 / 36), 70, 36)
+    g = _plane(fq, field, *args, precision="f64")
+    r = oracle.plane(B.astype(np.float64), grid, *args, _ora())
+    assert (r["status"] & oracle.ROTATED).sum() > 30
+    assert_bitwise(g, r)
+
+
+def test_volume_and_twist_fp64_bitwise(fq, oracle_lib, mono):
+    B, grid = mono
+    field = _field(fq, B, grid)
+    step = (63.0 / 20, 55.0 / 18, 31.0 / 6)
+    g = to_np(fq.qmap_volume(field, (0.0, 0.0, 0.0), step, 20, 18, 6, fq.params(precision="f64", scheme=1)))
+    r = oracle.qmap(B.astype(np.float64), grid, (0.0, 0.0, 0.0), (step[0], 0, 0), (0, step[1], 0), (0, 0, step[2]),
+                    (20, 18, 6), _ora())
+    assert_bitwise(g, r)
+    seeds = np.random.default_rng(3).uniform([0, 0, 0], [63, 55, 31], size=(300, 3))
+    g = to_np(fq.twist(field, torch.from_numpy(seeds).cuda(), fq.params(precision="f64", scheme=1, step=1.3)))
+    field.check()
+    assert_bitwise(g, oracle.twist(B.astype(np.float64), grid, seeds, _ora(step=1.3)))
+
+
+@pytest.mark.parametrize("way", [1, 2])
+def test_method2_fp64_bitwise(fq, oracle_lib, mono, way):
+    # Method II with step = 4.0 (the paper's Table 1 setting for way 1)
+    B, grid = mono
+    field = fq.Field(torch.from_numpy(B).cuda(), grid.origin, grid.spacing, pack=("f32", "f64", "gradb"))
+    args = ((0.0, 0.0, 0.0), (63.0 / 61, 0, 0), (0, 55.0 / 43, 0), 61, 43)
+    g = _plane(fq, field, *args, precision="f64", method=2, gradb_way=way, step=4.0)
+    r = oracle.plane(B.astype(np.float64), grid, *args, _ora(method=2, way=way, step=4.0))
+    assert_bitwise(g, r)
+
+
+def test_closed_form_on_gpu(fq, oracle_lib):
+    B = synth.analytic_cube("hyperbolic")
+    field = _field(fq, B, G1)
+    d = 0.6 / 24
+    args = ((-0.3, -0.3, 0.0), (d, 0, 0), (0, d, 0), 24, 24)
+    for prec, bound in (("f64", 1e-6), ("f32", 2e-3)):
+        g = _plane(fq, field, *args, precision=prec, step=0.2, step_min=0.01)
+        assert np.all(g["face2"] == 5)
+        np.testing.assert_allclose(g["Q"], E2, rtol=bound)
+
+
+def test_argument_errors(fq, mono):
+    B, grid = mono
+    field = _field(fq, B, grid)
+    args = ((0.0, 0.0, 0.0), (1.0, 0, 0), (0, 1.0, 0), 4, 4)
+    for kw, status in ((dict(scheme=2), 1), (dict(scheme=1, step=0.0), 1), (dict(scheme=1, step_min=5.0), 1),
+                       (dict(scheme=1, tape=1), 5)):
+        with pytest.raises(fq.FqslError) as ei:
+            fq.qmap_plane(field, *args, fq.params(**kw))
+        assert ei.value.status == status, kw
+    rg = synth.stretched_grid((8, 8, 8), (0, 0, 0), (7, 7, 7), ratios=(1.1, 1.1, 1.1))
+    fr = fq.Field(torch.from_numpy(synth.analytic_cube("uniform", rg)).cuda(), coords=rg.coords)
+    with pytest.raises(fq.FqslError) as ei:
+        fq.qmap_plane(fr, *args, fq.params(scheme=1))
+    assert ei.value.status == 5
+    with pytest.raises(fq.FqslError) as ei:
+        fq.Batch([field], [dict(origin=args[0], u=args[1], v=args[2], nu=4, nv=4)], fq.params(scheme=1))
+    assert ei.value.status == 5
