@@ -868,6 +868,25 @@ def main():
         m2["way%d" % way + ("_qperp" if qperp else "")] = {"value": n / (float(np.mean(tms)) / 1000.0),
                                                           "unit": "Q+Tw values/s", "ms_per_step": float(np.mean(tms))}
     fieldg.close()
+    # the paper's fixed-step scheme on the same map: 3/8-rule RK4, step_perp = 3 cells (Table 1), Eq. step
+    rk = {}
+    for prec in ("f32", "f64"):
+        prk = fq.params(precision=prec, tol=TOL, scheme=1, step=3.0)
+        fld = field64 if prec == "f64" else field32
+        fq.qmap_plane(fld, (0.0, 0.0, 0.0), u, v, NU, NV, prk, out=out)
+        torch.cuda.synchronize()
+        tms = []
+        for _ in range(max(3, (args.steps if prec == "f32" else args.fp64_steps))):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fq.qmap_plane(fld, (0.0, 0.0, 0.0), u, v, NU, NV, prk, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tms.append(e0.elapsed_time(e1))
+        rk[prec] = {"value": n / (float(np.mean(tms)) / 1000.0), "unit": "Q+Tw values/s",
+                    "ms_per_step": float(np.mean(tms)),
+                    "mean_trials_per_line": float(out["steps"].double().mean())}
     step(pacc)
     torch.cuda.synchronize()
     msacc, kernacc = timed(pacc, args.steps)
@@ -924,6 +943,8 @@ def main():
                           "note": "error norm and length/Tw sums accumulated in FP64 every step"},
             "method2_f32": dict(m2, note="deviation vectors (Method II), tol = tol_perp, same map; "
                                          "_qperp: Q_perp, end planes perpendicular to B"),
+            "fixed_step_rk38": dict(rk, note="Method I, 3/8-rule RK4, step_perp = 3 cells scaled per line by "
+                                             "Eq. step (step_min 0.15), same map"),
             "fp64": {"value": value64, "unit": "Q+Tw values/s", "ms_per_step": float(np.mean(ms64)),
                      "trace_ms": float(np.mean([k[0] for k in kern64])),
                      "speedup_fp32_over_fp64": value / ws / value64},
