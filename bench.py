@@ -49,8 +49,8 @@ NUM_SMS = 152
 # DRAM bytes (read + write) of one k_trace_f32 launch on this workload, from
 # the ncu capture summarised in profiles/trace_f32_c2_monopole_1024x1024.md,
 # valid while the tracer sources hash to TRACE_F32_SRC_HASH.
-TRACE_F32_DRAM_BYTES = 308.475648e6 + 59.954432e6
-TRACE_F32_SRC_HASH = "e2a9cc893567a927"
+TRACE_F32_DRAM_BYTES = 308.642304e6 + 59.467776e6
+TRACE_F32_SRC_HASH = "8e3679a2f437b3eb"
 
 
 def _trace_src_hash():
