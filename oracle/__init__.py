@@ -66,7 +66,7 @@ def lib():
             P = C.c_void_p
             for name in ("oracle_curl", "oracle_gradb", "oracle_interp", "oracle_qmap", "oracle_twist",
                          "oracle_trace", "oracle_max_threads", "oracle_curl_rect", "oracle_qmap_rect",
-                         "oracle_twist_rect", "oracle_interp_rect", "oracle_cell_rect"):
+                         "oracle_twist_rect", "oracle_interp_rect", "oracle_cell_rect", "oracle_gradb_rect"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -123,8 +123,13 @@ def curl(B, grid):
 def gradb(B, grid):
     """d(B_b/|B|)/dx_a at the nodes, shape (nz, ny, nx, 9), index a*3+b."""
     B = _f64(B)
-    n, o, d = _grid_args(grid)
     G = np.empty(B.shape[:3] + (9,), dtype=np.float64)
+    if is_rect(grid):
+        n = np.array(grid.n, dtype=np.int64)
+        if lib().oracle_gradb_rect(_p(B), _p(n), _p(_coords(grid)), _p(G)):
+            raise ValueError("oracle_gradb_rect: bad grid")
+        return G
+    n, o, d = _grid_args(grid)
     rc = lib().oracle_gradb(_p(B), _p(n), _p(d), _p(G))
     if rc:
         raise ValueError("oracle_gradb: bad grid")
@@ -202,10 +207,8 @@ def qmap(B, grid, origin, a1, a2, a3=(0.0, 0.0, 0.0), counts=(1, 1, 1), p: Param
     outs = (_p(out["Q"]), _p(out["Tw"]), _p(out["length"]), _p(out["r1"]), _p(out["r2"]), _p(out["face1"]),
             _p(out["face2"]), _p(out["status"]), _p(out["steps"]))
     if is_rect(grid):
-        if p.method != 1:
-            raise ValueError("stretched grids: Method I only")
         n = np.array(grid.n, dtype=np.int64)
-        rc = lib().oracle_qmap_rect(_p(B), _p(J), _p(n), _p(_coords(grid)), _p(lo), _p(A1), _p(A2), _p(A3),
+        rc = lib().oracle_qmap_rect(_p(B), _p(J), _p(G), _p(n), _p(_coords(grid)), _p(lo), _p(A1), _p(A2), _p(A3),
                                     _p(ln), C.byref(p), _p(sample), C.c_longlong(m if sample is not None else 0),
                                     *outs)
     else:

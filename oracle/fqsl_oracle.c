@@ -110,8 +110,9 @@
  *       its grazing test is on (dr_a/dtau)/D_a. Curl B uses the 2nd-order
  *       three-point differences of a non-uniform axis (the derivative of the
  *       quadratic through the three nodes; one-sided on the faces), which are
- *       the R4 stencils on a uniform axis. Method II is not defined on a
- *       stretched grid here.
+ *       the R4 stencils on a uniform axis. Method II: the grad(B/B) grid of
+ *       way 1 takes the same three-point differences; way 2 offsets +-eps2
+ *       cells of the step's start cell (eps2 D_a) and divides by 2 eps2 D_a.
  *   R18 Fixed-step scheme (Sec. 2.3, Kutta's 3/8-rule RK4; Sec. 4 Eq. step):
  *       with scheme = 1 every trial is one 3/8-rule step of the line's fixed size
  *       (cells, index space as in R1; length and Tw ride along) and is always
@@ -266,6 +267,34 @@ int oracle_curl_rect(const double *B, const long long n[3], const double *X, dou
                 J[node * 3 + 1] = dzBx - dxBz;
                 J[node * 3 + 2] = dxBy - dyBx;
             }
+    return 0;
+}
+
+/* G[a*3+b] = d(B_b/|B|)/dx_a at every node of a stretched grid (R16, the
+ * stencils of oracle_curl_rect); X as there. */
+int oracle_gradb_rect(const double *B, const long long n[3], const double *X, double *G)
+{
+    if (n[0] < 2 || n[1] < 2 || n[2] < 2) return 1;
+    long long nn = n[0] * n[1] * n[2];
+    double *bh = (double *)malloc((size_t)nn * 3 * sizeof(double));
+    if (!bh) return 2;
+    for (long long q = 0; q < nn; q++) {
+        double m = sqrt(B[3 * q] * B[3 * q] + B[3 * q + 1] * B[3 * q + 1] + B[3 * q + 2] * B[3 * q + 2]);
+        for (int c = 0; c < 3; c++) bh[3 * q + c] = m > 0 ? B[3 * q + c] / m : 0.0;
+    }
+    const double *Xa[3] = {X, X + n[0], X + n[0] + n[1]};
+    long long stride[3] = {1, n[0], n[0] * n[1]};
+#pragma omp parallel for schedule(static)
+    for (long long k = 0; k < n[2]; k++)
+        for (long long j = 0; j < n[1]; j++)
+            for (long long i = 0; i < n[0]; i++) {
+                long long node = (k * n[1] + j) * n[0] + i;
+                long long idx[3] = {i, j, k};
+                for (int a = 0; a < 3; a++)
+                    for (int b = 0; b < 3; b++)
+                        G[node * 9 + a * 3 + b] = o_dnode_rect(bh, 3, b, node, stride[a], idx[a], n[a], Xa[a]);
+            }
+    free(bh);
     return 0;
 }
 
@@ -430,11 +459,14 @@ static int o_rhs(const OField *f, const OParams *p, const double *D, double sigm
         } else {
             for (int a = 0; a < 3; a++) {
                 double xp[3] = {y[0], y[1], y[2]}, xm[3] = {y[0], y[1], y[2]};
-                xp[a] += p->eps2;
-                xm[a] -= p->eps2;
+                /* +-eps2 cells: of the grid (uniform; index state) or of the
+                   step's start cell (stretched; physical state, R16) */
+                double off = f->X[0] ? p->eps2 * D[a] : p->eps2, span = 2.0 * p->eps2 * D[a];
+                xp[a] += off;
+                xm[a] -= off;
                 double bp[3], bm[3];
                 if (o_unit_b(f, xp, bp) || o_unit_b(f, xm, bm)) return 1;
-                for (int b = 0; b < 3; b++) Gm[a][b] = (bp[b] - bm[b]) / (2.0 * p->eps2 * f->d[a]);
+                for (int b = 0; b < 3; b++) Gm[a][b] = (bp[b] - bm[b]) / span;
             }
         }
         /* Eq. rb2: dU/ds = (U . grad)(B/B); ds = sigma * dl * dtau */
@@ -943,7 +975,8 @@ static int o_make_field(OField *f, const double *B, const double *J, const doubl
 
 /* stretched grid (R16): X = x, y, z node coordinates back to back, each
  * strictly increasing */
-static int o_make_field_rect(OField *f, const double *B, const double *J, const long long n[3], const double *X)
+static int o_make_field_rect(OField *f, const double *B, const double *J, const double *G, const long long n[3],
+                             const double *X)
 {
     long long off = 0;
     for (int a = 0; a < 3; a++) {
@@ -958,7 +991,7 @@ static int o_make_field_rect(OField *f, const double *B, const double *J, const 
     }
     f->B = B;
     f->J = J;
-    f->G = NULL;
+    f->G = G;
     return 0;
 }
 
@@ -980,15 +1013,16 @@ int oracle_qmap(const double *B, const double *J, const double *G, const long lo
     return o_qmap(&f, lo, a1, a2, a3, ln, p, sample, nsample, Qo, Two, leno, r1, r2, f1, f2, st, steps);
 }
 
-/* The same on a stretched grid (R16; Method I only). */
-int oracle_qmap_rect(const double *B, const double *J, const long long n[3], const double *X, const double lo[3],
-                     const double a1[3], const double a2[3], const double a3[3], const long long ln[3],
-                     const OParams *p, const long long *sample, long long nsample, double *Qo, double *Two,
-                     double *leno, double *r1, double *r2, int *f1, int *f2, int *st, long long *steps)
+/* The same on a stretched grid (R16). */
+int oracle_qmap_rect(const double *B, const double *J, const double *G, const long long n[3], const double *X,
+                     const double lo[3], const double a1[3], const double a2[3], const double a3[3],
+                     const long long ln[3], const OParams *p, const long long *sample, long long nsample, double *Qo,
+                     double *Two, double *leno, double *r1, double *r2, int *f1, int *f2, int *st, long long *steps)
 {
     OField f;
-    if (o_make_field_rect(&f, B, J, n, X)) return 1;
-    if (p->method != 1) return 2;
+    if (o_make_field_rect(&f, B, J, G, n, X)) return 1;
+    if (p->method == 2 && p->way == 1 && !G) return 2;
+    if (p->scheme != 0) return 2; /* the fixed-step scheme runs on uniform grids */
     return o_qmap(&f, lo, a1, a2, a3, ln, p, sample, nsample, Qo, Two, leno, r1, r2, f1, f2, st, steps);
 }
 
@@ -1096,7 +1130,7 @@ int oracle_twist_rect(const double *B, const double *J, const long long n[3], co
                       int *f2, int *st, long long *steps)
 {
     OField f;
-    if (o_make_field_rect(&f, B, J, n, X)) return 1;
+    if (o_make_field_rect(&f, B, J, NULL, n, X)) return 1;
     return o_twist(&f, seeds, ns, p, Two, leno, r1, r2, f1, f2, st, steps);
 }
 
@@ -1107,7 +1141,7 @@ int oracle_interp_rect(const double *arr, int nc, const long long n[3], const do
 {
     OField f;
     memset(&f, 0, sizeof f);
-    if (o_make_field_rect(&f, arr, NULL, n, X)) return 1;
+    if (o_make_field_rect(&f, arr, NULL, NULL, n, X)) return 1;
     for (long long k = 0; k < np; k++) o_interp(&f, arr, nc, r + 3 * k, out + (long long)nc * k);
     return 0;
 }

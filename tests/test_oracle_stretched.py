@@ -207,3 +207,51 @@ def test_line_invariants_on_a_stretched_grid():
     again = oracle.twist(B, g, out["r2"][sel], p)
     np.testing.assert_allclose(again["Tw"], out["Tw"][sel], rtol=1e-6, atol=1e-9)
     np.testing.assert_allclose(again["length"], out["length"][sel], rtol=1e-6)
+
+
+def test_gradb_grid_matches_numpy_gradient():
+    # Method II way 1: d(B_b/|B|)/dx_a at the nodes with the same three-point
+    # stencils as the curl
+    g = _grid((15, 12, 10))
+    rng = np.random.default_rng(6)
+    B = rng.standard_normal(g.shape) + np.array([0.0, 0.0, 3.0])
+    G = oracle.gradb(B, g)
+    bh = B / np.linalg.norm(B, axis=-1, keepdims=True)
+    x, y, z = (g.axis(a) for a in range(3))
+    for b in range(3):
+        dz, dy, dx = np.gradient(bh[..., b], z, y, x, edge_order=2)
+        for a, d in enumerate((dx, dy, dz)):
+            np.testing.assert_allclose(G[..., 3 * a + b], d, rtol=0, atol=1e-9 * np.abs(d).max())
+
+
+def test_method2_closed_forms_on_a_stretched_grid():
+    # deviation vectors (way 2) carry no finite-difference error of the
+    # lattice: B = (x, -y, 1) gives Q = e^2 + e^-2 on top exits, and the rigid
+    # rotation Q_perp = 2
+    g = _grid()
+    d, o, u, v = _seeds(12, -0.3, 0.3)
+    B = synth.analytic_cube("hyperbolic", g)
+    out = oracle.plane(B, g, o, u, v, 12, 12, oracle.params(method=2, way=2, tol=1e-10))
+    assert np.all(out["face2"] == 5)
+    np.testing.assert_allclose(out["Q"], E2, rtol=1e-6)
+    B = synth.analytic_cube("rotation", g, q=2.0 * math.pi)
+    out = oracle.plane(B, g, o, u, v, 12, 12, oracle.params(method=2, way=2, tol=1e-10, qperp=1))
+    np.testing.assert_allclose(out["Q"], 2.0, rtol=1e-6)
+
+
+def test_method2_uniform_coordinates_reduce_to_the_uniform_method():
+    ug = synth.Grid((21, 19, 13), (-3.0, -2.0, 0.0), (0.5, 0.5, 0.25))
+    rg = synth.RectGrid(tuple(tuple(float(v) for v in ug.axis(a)) for a in range(3)))
+    B = _monopole(ug)
+    plane = ((-3.0, -2.0, 0.0), (10.0 / 16, 0.0, 0.0), (0.0, 9.0 / 16, 0.0), 16, 16)
+    # way 1 converges with the tolerance (median 1.6e-9 at 1e-10); way 2's
+    # +-0.001-cell differences have kinks where a stage point comes within
+    # 0.001 cells of a cell face, so two step sequences that differ by rounding
+    # keep differences near 1e-5 at any tolerance
+    for way, bound in ((1, 1e-7), (2, 1e-4)):
+        p = oracle.params(method=2, way=way, tol=1e-10)
+        a = oracle.plane(B, ug, *plane, p)
+        b = oracle.plane(B, rg, *plane, p)
+        ok = np.isfinite(a["Q"])
+        assert ok.sum() > 200 and np.array_equal(a["face2"], b["face2"])
+        assert np.median(np.abs(b["Q"][ok] / a["Q"][ok] - 1)) < bound
