@@ -179,20 +179,22 @@ FQSL_API fqsl_status fqsl_field_create(const void *B_dev, fqsl_dtype b_dtype, lo
  * [x_i, y_j, z_k] from three increasing coordinate arrays; Sec. 2.3: step and
  * tolerance scaled per cell). x, y, z: HOST arrays of nx, ny, nz strictly
  * increasing finite coordinates (copied; the caller keeps ownership). B_dev,
- * b_dtype, nx, ny, nz, flags and cuda_stream as in fqsl_field_create, except
- * that FQSL_PACK_GRADB is refused. Interpolation finds a point's cell (the
- * largest i with x_i <= x, clamped to [0, n-2]; the paper uses a binary
- * search, the library a bucket table that gives the same cell) and weights it
- * by Eqs. w0, w1. Curl B takes the 2nd-order three-point differences of a
- * non-uniform axis (one-sided on the faces). Each trial step is scaled by the
- * widths of the cell it starts in: d r/d tau = B/|bt| with bt_a = B_a/w_a, and
- * the error is measured in those cells, so step, h_min, h_max and tol stay in
- * cells. Handles made here serve fqsl_qmap_plane, fqsl_qmap_volume,
- * fqsl_qmap_plane_static and fqsl_twist with Method I; Method II, the step tape
- * and batches return FQSL_ERR_UNSUPPORTED. Errors: FQSL_ERR_ARG (null pointers,
- * sizes, flags, coordinates not strictly increasing or not finite, coordinates
- * that collapse in float when FQSL_PACK_F32 is asked for), FQSL_ERR_OOM,
- * FQSL_ERR_CUDA. */
+ * b_dtype, nx, ny, nz, flags and cuda_stream as in fqsl_field_create
+ * (FQSL_PACK_GRADB builds the gradient grid with the stencils below).
+ * Interpolation finds a point's cell (the largest i with x_i <= x, clamped to
+ * [0, n-2]; the paper uses a binary search, the library a bucket table that
+ * gives the same cell) and weights it by Eqs. w0, w1. Curl B and grad(B/|B|)
+ * take the 2nd-order three-point differences of a non-uniform axis
+ * (one-sided on the faces). Each trial step is scaled by the widths w of the
+ * cell it starts in: d r/d tau = B/|bt| with bt_a = B_a/w_a, and the error is
+ * measured in those cells, so step, h_min, h_max and tol stay in cells.
+ * Handles made here serve fqsl_qmap_plane, fqsl_qmap_volume,
+ * fqsl_qmap_plane_static and fqsl_twist with Method I and Method II (way 2
+ * offsets +-eps_way2 cells of the trial's start cell); the step tape, the
+ * fixed-step scheme and batches return FQSL_ERR_UNSUPPORTED. Errors:
+ * FQSL_ERR_ARG (null pointers, sizes, flags, coordinates not strictly
+ * increasing or not finite, coordinates that collapse in float when
+ * FQSL_PACK_F32 is asked for), FQSL_ERR_OOM, FQSL_ERR_CUDA. */
 FQSL_API fqsl_status fqsl_field_create_rect(const void *B_dev, fqsl_dtype b_dtype, long long nx, long long ny,
                                             long long nz, const double *x, const double *y, const double *z,
                                             unsigned flags, void *cuda_stream, fqsl_field *out);

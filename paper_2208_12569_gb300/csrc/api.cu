@@ -247,7 +247,6 @@ fqsl_status fqsl_field_create_rect(const void *B_dev, fqsl_dtype b_dtype, long l
     if (out) *out = nullptr;
     fqsl_status st = check_create(B_dev, b_dtype, nx, ny, nz, flags, out, who);
     if (st != FQSL_OK) return st;
-    if (flags & FQSL_PACK_GRADB) return fail(FQSL_ERR_ARG, "%s: no gradient grid on a stretched grid", who);
     const double *X[3] = {x, y, z};
     const long long N[3] = {nx, ny, nz};
     for (int a = 0; a < 3; a++) {
@@ -511,8 +510,6 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
         if (p->tape) return fail(FQSL_ERR_UNSUPPORTED, "%s: the step tape records RKF45 maps", who);
     }
     if (p->qperp && p->method != 2) return fail(FQSL_ERR_UNSUPPORTED, "%s: Q_perp needs Method II", who);
-    if (f->g.rect && p->method != 1)
-        return fail(FQSL_ERR_UNSUPPORTED, "%s: Method II is not available on a stretched grid", who);
     if (f->g.rect && p->tape) return fail(FQSL_ERR_UNSUPPORTED, "%s: no step tape on a stretched grid", who);
     return FQSL_OK;
 }
@@ -667,6 +664,9 @@ cudaError_t launch_trace_m2(fqsl_field f, const fqsl_params *p, const TraceArgs 
         if (p->scheme == 1)
             c = p->precision == FQSL_F64 ? trace_dev_rk38_blocks_per_sm_f64(p->gradb_way)
                                          : trace_dev_rk38_blocks_per_sm_f32(p->gradb_way);
+        else if (f->g.rect)
+            c = p->precision == FQSL_F64 ? trace_dev_rect_blocks_per_sm_f64(p->gradb_way)
+                                         : trace_dev_rect_blocks_per_sm_f32(p->gradb_way);
         else
             c = p->precision == FQSL_F64 ? trace_dev_blocks_per_sm_f64(p->gradb_way)
                                          : trace_dev_blocks_per_sm_f32(p->gradb_way);

@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(256) k_assemble_m2_f32(const AssembleArgs A)
                 const int a = (e == 0 ? f1 : f2) >> 1;
                 const float *xe = e == 0 ? x1 : x2;
                 float Bf[3], Jf[3];
-                trace::gather(f, xe[0], xe[1], xe[2], Bf, Jf);
+                if (f.rect) trace::gather_rect(f, xe[0], xe[1], xe[2], Bf, Jf);
+                else trace::gather(f, xe[0], xe[1], xe[2], Bf, Jf);
                 const double B[3] = {Bf[0], Bf[1], Bf[2]};
                 const float *dv = R.dev32 + 12 * idx + 6 * e;
                 const double U[3] = {dv[0], dv[1], dv[2]}, V[3] = {dv[3], dv[4], dv[5]};

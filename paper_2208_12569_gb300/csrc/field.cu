@@ -168,6 +168,42 @@ __device__ __forceinline__ double bhat_diff(const TI *__restrict__ B, int c, lon
     return (F(i + 1) - F(i - 1)) / (2.0 * h);
 }
 
+// Stretched grid: the same with the three-point stencils of node_diff_rect
+template <typename TI>
+__device__ __forceinline__ double bhat_diff_rect(const TI *__restrict__ B, int c, long long node, long long stride,
+                                                 long long i, long long n, const double *__restrict__ X,
+                                                 const double *__restrict__ co)
+{
+    auto F = [&](long long kk) -> double { return bhat(B, node + (kk - i) * stride, c); };
+    if (n == 2) return (F(1) - F(0)) / (X[1] - X[0]);
+    const double c0 = co[3 * i], c1 = co[3 * i + 1], c2 = co[3 * i + 2];
+    if (i == 0) return c0 * F(0) + c1 * F(1) - c2 * F(2);
+    if (i == n - 1) return c0 * F(n - 3) - c1 * F(n - 2) + c2 * F(n - 1);
+    return c0 * F(i - 1) + c1 * F(i) + c2 * F(i + 1);
+}
+
+template <typename TI>
+__global__ void __launch_bounds__(256) k_gradb_pack_rect(const TI *__restrict__ B, const FieldView g,
+                                                         float *__restrict__ g32, double *__restrict__ g64)
+{
+    const long long nx = g.nx, ny = g.ny, nz = g.nz;
+    const long long total = nx * ny * nz;
+    const long long stride[3] = {1, nx, nx * ny};
+    const long long n[3] = {nx, ny, nz};
+    for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < total;
+         node += (long long)gridDim.x * blockDim.x) {
+        const long long idx[3] = {node % nx, (node / nx) % ny, node / stride[2]};
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) {
+                const double v = bhat_diff_rect(B, b, node, stride[a], idx[a], n[a], g.x64[a], g.dco[a]);
+                if (g64) g64[node * 10 + a * 3 + b] = v;
+                if (g32) g32[node * 12 + a * 3 + b] = (float)v;
+            }
+        if (g64) g64[node * 10 + 9] = 0.0;
+        if (g32) g32[node * 12 + 9] = g32[node * 12 + 10] = g32[node * 12 + 11] = 0.f;
+    }
+}
+
 // grad(B/|B|) at the nodes for Method II way 1 (Sec. 4, Eq. grad_B): G[a*3+b]
 // = d(B_b/|B|)/dx_a with the stencils of the curl grid.
 template <typename TI>
@@ -205,6 +241,15 @@ cudaError_t launch_gradb_pack(const void *B, fqsl_dtype bt, const FieldView &g, 
     long long blocks = (total + 255) / 256;
     if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
     if (blocks < 1) blocks = 1;
+    if (g.rect) {
+        if (bt == FQSL_F32)
+            k_gradb_pack_rect<float><<<(unsigned)blocks, 256, 0, s>>>((const float *)B, g, (float *)grad32,
+                                                                     (double *)grad64);
+        else
+            k_gradb_pack_rect<double><<<(unsigned)blocks, 256, 0, s>>>((const double *)B, g, (float *)grad32,
+                                                                      (double *)grad64);
+        return cudaGetLastError();
+    }
     if (bt == FQSL_F32)
         k_gradb_pack<float><<<(unsigned)blocks, 256, 0, s>>>((const float *)B, g.nx, g.ny, g.nz, g.d[0], g.d[1],
                                                             g.d[2], (float *)grad32, (double *)grad64);

@@ -250,6 +250,10 @@ cudaError_t launch_trace_rect_f64(const TraceArgs &a, int src, int grid, cudaStr
 int trace_rect_blocks_per_sm_f32(int src, bool acc64);
 int trace_rect_blocks_per_sm_f64(int src);
 cudaError_t launch_seed_prep_rect_f32(const TraceArgs &a, long long n, unsigned grid, cudaStream_t s);
+cudaError_t launch_trace_dev_rect_f32(const TraceArgs &a, int way, int grid, cudaStream_t s);
+cudaError_t launch_trace_dev_rect_f64(const TraceArgs &a, int way, int grid, cudaStream_t s);
+int trace_dev_rect_blocks_per_sm_f32(int way);
+int trace_dev_rect_blocks_per_sm_f64(int way);
 // the fixed-step 3/8-rule instantiations (uniform grids; Method I sources and Method II ways)
 cudaError_t launch_trace_rk38_f32(const TraceArgs &a, int src, int grid, cudaStream_t s, bool acc64);
 cudaError_t launch_trace_rk38_f64(const TraceArgs &a, int src, int grid, cudaStream_t s);

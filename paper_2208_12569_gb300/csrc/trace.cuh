@@ -566,14 +566,9 @@ __device__ __forceinline__ bool rhsg(const FieldView &f, const T dd[3], T sgn, T
 // of Eq. grad_B trilinearly, way 2 differences B/|B| at xi +- eps e_a.
 // G[a][b] = d(B_b/|B|)/dx_a in physical units. Returns false on a null field.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void gather_grad(const FieldView &f, float x, float y, float z, float G[3][3])
+__device__ __forceinline__ void gather_grad_cell(const FieldView &f, long long base, float wx, float wy, float wz,
+                                                 float ux, float uy, float uz, float G[3][3])
 {
-    const float cx = fminf(fmaxf(floorf(x), 0.f), f.cmax[0]);
-    const float cy = fminf(fmaxf(floorf(y), 0.f), f.cmax[1]);
-    const float cz = fminf(fmaxf(floorf(z), 0.f), f.cmax[2]);
-    const float wx = x - cx, wy = y - cy, wz = z - cz;
-    const float ux = 1.f - wx, uy = 1.f - wy, uz = 1.f - wz;
-    const long long base = ((long long)small_int(cz) * f.ny + small_int(cy)) * f.nx + small_int(cx);
     const long long sy = f.nx, sz = (long long)f.nx * f.ny;
     const float4 *g = (const float4 *)f.grad;
     const float wyz[4] = {uy * uz, wy * uz, uy * wz, wy * wz};
@@ -597,18 +592,31 @@ __device__ __forceinline__ void gather_grad(const FieldView &f, float x, float y
         for (int b = 0; b < 3; b++) G[a][b] = acc[a * 3 + b];
 }
 
-// FP64: Eq. interp term by term on the 9 gradient components
-__device__ __forceinline__ void gather_grad(const FieldView &f, double x, double y, double z, double G[3][3])
+__device__ __forceinline__ void gather_grad(const FieldView &f, float x, float y, float z, float G[3][3])
 {
-    const double c[3] = {clampcell<double>(floor(x), f.nx), clampcell<double>(floor(y), f.ny),
-                         clampcell<double>(floor(z), f.nz)};
-    const double xi[3] = {x, y, z};
-    double w[3][2];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        w[a][0] = (c[a] + 1.0) - xi[a];
-        w[a][1] = 1.0 - w[a][0];
-    }
+    const float cx = fminf(fmaxf(floorf(x), 0.f), f.cmax[0]);
+    const float cy = fminf(fmaxf(floorf(y), 0.f), f.cmax[1]);
+    const float cz = fminf(fmaxf(floorf(z), 0.f), f.cmax[2]);
+    const float wx = x - cx, wy = y - cy, wz = z - cz;
+    const long long base = ((long long)small_int(cz) * f.ny + small_int(cy)) * f.nx + small_int(cx);
+    gather_grad_cell(f, base, wx, wy, wz, 1.f - wx, 1.f - wy, 1.f - wz, G);
+}
+
+// FP32 on a stretched grid: the cell search and Eq. w0 weights of gather_rect
+__device__ __forceinline__ void gather_grad_rect(const FieldView &f, float x, float y, float z, float G[3][3])
+{
+    RectCells<float> rc;
+    rect_cells(f, x, y, z, rc);
+    const float ux = (rc.r[0].y - x) * rc.r[0].z, uy = (rc.r[1].y - y) * rc.r[1].z, uz = (rc.r[2].y - z) * rc.r[2].z;
+    const long long base = ((long long)rc.c[2] * f.ny + rc.c[1]) * f.nx + rc.c[0];
+    gather_grad_cell(f, base, 1.f - ux, 1.f - uy, 1.f - uz, ux, uy, uz, G);
+}
+
+// FP64: Eq. interp term by term on the 9 gradient components, given the cell
+// and the per-axis weights
+__device__ __forceinline__ void gather_grad_cell(const FieldView &f, const long long c[3], const double w[3][2],
+                                                 double G[3][3])
+{
     const long long sy = f.nx, sz = (long long)f.nx * f.ny;
     const long long base = (long long)c[2] * sz + (long long)c[1] * sy + (long long)c[0];
     const double2 *g = (const double2 *)f.grad;
@@ -635,11 +643,45 @@ __device__ __forceinline__ void gather_grad(const FieldView &f, double x, double
         for (int b = 0; b < 3; b++) G[a][b] = acc[a * 3 + b];
 }
 
-template <typename T>
+__device__ __forceinline__ void gather_grad(const FieldView &f, double x, double y, double z, double G[3][3])
+{
+    const double cf[3] = {clampcell<double>(floor(x), f.nx), clampcell<double>(floor(y), f.ny),
+                          clampcell<double>(floor(z), f.nz)};
+    const double xi[3] = {x, y, z};
+    long long c[3];
+    double w[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        c[a] = (long long)cf[a];
+        w[a][0] = (cf[a] + 1.0) - xi[a];
+        w[a][1] = 1.0 - w[a][0];
+    }
+    gather_grad_cell(f, c, w, G);
+}
+
+// FP64 on a stretched grid: the weights of gather_rect_at
+__device__ __forceinline__ void gather_grad_rect(const FieldView &f, double x, double y, double z, double G[3][3])
+{
+    RectCells<double> rc;
+    rect_cells(f, x, y, z, rc);
+    const double xi[3] = {x, y, z};
+    long long c[3];
+    double w[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double2 cr = rc.r[a];
+        c[a] = rc.c[a];
+        w[a][0] = (cr.y - xi[a]) / (cr.y - cr.x);
+        w[a][1] = 1.0 - w[a][0];
+    }
+    gather_grad_cell(f, c, w, G);
+}
+
+template <typename T, bool RECT = false>
 __device__ __forceinline__ bool unit_b(const FieldView &f, T x, T y, T z, T bh[3])
 {
     T B[3], J[3];
-    gather(f, x, y, z, B, J);
+    gatherg<RECT>(f, x, y, z, B, J);
     const T m = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
     if (!(m > (T)0) || !(m < (T)INFINITY)) return false;
     bh[0] = B[0] / m;
@@ -648,11 +690,14 @@ __device__ __forceinline__ bool unit_b(const FieldView &f, T x, T y, T z, T bh[3
     return true;
 }
 
-template <typename T, int WAY>
-__device__ __forceinline__ bool grad_bhat(const FieldView &f, T eps, T x, T y, T z, T G[3][3])
+// dd: the trial's per-axis scale (step_dd): on a stretched grid way 2 offsets
+// +-eps cells of the start cell, eps D_a (FP64 dd = D, FP32 dd = 1/D).
+template <typename T, int WAY, bool RECT = false>
+__device__ __forceinline__ bool grad_bhat(const FieldView &f, T eps, T x, T y, T z, const T dd[3], T G[3][3])
 {
     if constexpr (WAY == 1) {
-        gather_grad(f, x, y, z, G);
+        if constexpr (RECT) gather_grad_rect(f, x, y, z, G);
+        else gather_grad(f, x, y, z, G);
         return true;
     } else {
         const T p[3] = {x, y, z};
@@ -660,13 +705,21 @@ __device__ __forceinline__ bool grad_bhat(const FieldView &f, T eps, T x, T y, T
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             T xp[3] = {p[0], p[1], p[2]}, xm[3] = {p[0], p[1], p[2]};
-            xp[a] += eps;
-            xm[a] -= eps;
+            T off = eps, span;
+            if constexpr (RECT) {
+                const T D = sizeof(T) == 8 ? dd[a] : (T)1 / dd[a];
+                off = eps * D;
+                span = (T)2 * eps * D;
+            } else {
+                span = (T)2 * eps * (T)f.d[a];
+            }
+            xp[a] += off;
+            xm[a] -= off;
             T bp[3], bm[3];
-            ok &= unit_b(f, xp[0], xp[1], xp[2], bp);
-            ok &= unit_b(f, xm[0], xm[1], xm[2], bm);
+            ok &= unit_b<T, RECT>(f, xp[0], xp[1], xp[2], bp);
+            ok &= unit_b<T, RECT>(f, xm[0], xm[1], xm[2], bm);
 #pragma unroll
-            for (int b = 0; b < 3; b++) G[a][b] = (bp[b] - bm[b]) / ((T)2 * eps * (T)f.d[a]);
+            for (int b = 0; b < 3; b++) G[a][b] = (bp[b] - bm[b]) / span;
         }
         return ok;
     }
@@ -1155,7 +1208,6 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
 template <typename T, bool ACC, int DEV = 0, bool RECT = false>
 __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, long long item, bool reg_rot = true)
 {
-    static_assert(!(RECT && DEV != 0), "Method II is not defined on stretched grids");
     constexpr bool kF64 = sizeof(T) == 8;
     const Lattice &G = A.lat;
     const long long per_tile = kTileU * kTileV;
@@ -1265,7 +1317,7 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
         if (started) {
             // S0 perpendicular to B: U0, V0 = the frame of B/|B| at the seed (Sec. 4)
             double B0[3], u[3], v[3];
-            b_at<T>(f, xi[0], xi[1], xi[2], B0);
+            b_at<T, RECT>(f, xi[0], xi[1], xi[2], B0);
             const double nB = sqrt(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
             const double bh[3] = {B0[0] / nB, B0[1] / nB, B0[2] / nB};
             perp_frame(bh, u, v);
@@ -1346,7 +1398,7 @@ template <typename T, int SRC, bool ACC, int DEV = 0, bool BATCH = false, bool T
           int SCH = 0>
 __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs &BA)
 {
-    static_assert(!(RECT && (DEV != 0 || TAPE)), "stretched grids: Method I and twist lists, no tape");
+    static_assert(!(RECT && TAPE), "stretched grids: no tape");
     static_assert(!(SCH && (RECT || TAPE || BATCH)), "fixed-step scheme: uniform grids, no tape, no batches");
     constexpr bool SPLIT = TAPE && SRC == kSrcLattice;
     constexpr unsigned FULL = 0xffffffffu;
@@ -1504,7 +1556,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                     us[c] = (c < 3 ? L.u[c] : L.v[c - 3]) + hh * acc;
                 }
                 T G[3][3];
-                ok = grad_bhat<T, DEV>(f, (T)A0.p.eps2, px, py, pz, G) && ok;
+                ok = grad_bhat<T, DEV, RECT>(f, (T)A0.p.eps2, px, py, pz, dd, G) && ok;
                 const T sdl = sgn * o[3];
 #pragma unroll
                 for (int b = 0; b < 3; b++) {
@@ -1834,7 +1886,7 @@ __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
         float4 fu = make_float4(0.f, 0.f, 0.f, 0.f), fv = fu;
         if (!bad) {
             float B0[3], J0[3];
-            gather(f, x, y, z, B0, J0);
+            gatherg<RECT>(f, x, y, z, B0, J0);
             const double b0 = B0[0], b1 = B0[1], b2 = B0[2];
             const double nB = sqrt(b0 * b0 + b1 * b1 + b2 * b2);
             const double bh[3] = {b0 / nB, b1 / nB, b2 / nB};

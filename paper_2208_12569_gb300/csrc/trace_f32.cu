@@ -96,6 +96,7 @@ cudaError_t launch_trace_dev_f32(const TraceArgs &a, int way, int grid, int bloc
 {
     if (block != kBlock) return cudaErrorInvalidValue;
     if (a.p.scheme == 1) return launch_trace_dev_rk38_f32(a, way, grid, s);
+    if (a.f.rect) return launch_trace_dev_rect_f32(a, way, grid, s);
     if (way == 1) k_trace_dev_f32<1><<<grid, block, 0, s>>>(a);
     else k_trace_dev_f32<2><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();

@@ -48,6 +48,7 @@ cudaError_t launch_trace_dev_f64(const TraceArgs &a, int way, int grid, int bloc
 {
     if (block != kBlock) return cudaErrorInvalidValue;
     if (a.p.scheme == 1) return launch_trace_dev_rk38_f64(a, way, grid, s);
+    if (a.f.rect) return launch_trace_dev_rect_f64(a, way, grid, s);
     if (way == 1) k_trace_dev_f64<1><<<grid, block, 0, s>>>(a);
     else k_trace_dev_f64<2><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();

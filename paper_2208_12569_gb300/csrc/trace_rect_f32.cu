@@ -1,8 +1,8 @@
 // FP32 tracer instantiations for fields on stretched (rectilinear) grids
 // (Sec. 2.2 and 2.3): the same persistent kernel as trace_f32.cu with the
 // cell search, physical positions relative to the first node and per-cell
-// step and error scaling of trace_body's RECT form, plus the FP32 seed
-// pre-pass on such a grid.
+// step and error scaling of trace_body's RECT form (Method I, seed lists and
+// Method II's deviation vectors), plus the FP32 seed pre-pass on such a grid.
 #include "trace.cuh"
 
 #ifndef FQSL_TRACE_F32_MINB
@@ -17,6 +17,13 @@ template <int SRC, bool ACC>
 __global__ void __launch_bounds__(kBlock, FQSL_TRACE_F32_MINB) k_trace_rect_f32(const TraceArgs A)
 {
     trace::trace_body<float, SRC, ACC, 0, false, false, true>(A, BatchArgs{});
+}
+
+// Method II (deviation vectors) on a stretched grid
+template <int WAY>
+__global__ void __launch_bounds__(kBlock) k_trace_dev_rect_f32(const TraceArgs A)
+{
+    trace::trace_body<float, kSrcLattice, false, WAY, false, false, true>(A, BatchArgs{});
 }
 
 template <bool ACC>
@@ -56,6 +63,21 @@ cudaError_t launch_trace_rect_f32(const TraceArgs &a, int src, int grid, cudaStr
 }
 
 int trace_rect_blocks_per_sm_f32(int src, bool acc64) { return acc64 ? blocks<true>(src) : blocks<false>(src); }
+
+cudaError_t launch_trace_dev_rect_f32(const TraceArgs &a, int way, int grid, cudaStream_t s)
+{
+    if (way == 1) k_trace_dev_rect_f32<1><<<grid, kBlock, 0, s>>>(a);
+    else k_trace_dev_rect_f32<2><<<grid, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int trace_dev_rect_blocks_per_sm_f32(int way)
+{
+    int b = 0;
+    if (way == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_dev_rect_f32<1>, kBlock, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_dev_rect_f32<2>, kBlock, 0);
+    return b > 0 ? b : 1;
+}
 
 cudaError_t launch_seed_prep_rect_f32(const TraceArgs &a, long long n, unsigned grid, cudaStream_t s)
 {

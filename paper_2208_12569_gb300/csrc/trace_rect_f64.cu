@@ -14,7 +14,28 @@ __global__ void __launch_bounds__(kBlock) k_trace_rect_f64(const TraceArgs A)
 {
     trace::trace_body<double, SRC, true, 0, false, false, true>(A, BatchArgs{});
 }
+// Method II (deviation vectors) on a stretched grid
+template <int WAY>
+__global__ void __launch_bounds__(kBlock) k_trace_dev_rect_f64(const TraceArgs A)
+{
+    trace::trace_body<double, kSrcLattice, true, WAY, false, false, true>(A, BatchArgs{});
+}
 }  // namespace
+
+cudaError_t launch_trace_dev_rect_f64(const TraceArgs &a, int way, int grid, cudaStream_t s)
+{
+    if (way == 1) k_trace_dev_rect_f64<1><<<grid, kBlock, 0, s>>>(a);
+    else k_trace_dev_rect_f64<2><<<grid, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int trace_dev_rect_blocks_per_sm_f64(int way)
+{
+    int b = 0;
+    if (way == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_dev_rect_f64<1>, kBlock, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_dev_rect_f64<2>, kBlock, 0);
+    return b > 0 ? b : 1;
+}
 
 cudaError_t launch_trace_rect_f64(const TraceArgs &a, int src, int grid, cudaStream_t s)
 {

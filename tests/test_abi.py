@@ -91,7 +91,6 @@ def test_stretched_grid_argument_errors(lib):
     assert create(good, None, good) == 1 and b"NULL" in lib.fqsl_last_error()
     assert create(good, flat, good) == 1 and b"increasing" in lib.fqsl_last_error()
     assert create(nan, good, good) == 1 and b"finite" in lib.fqsl_last_error()
-    assert create(good, good, good, 1 | 4) == 1 and b"gradient" in lib.fqsl_last_error()
     # cells that float cannot tell apart are refused for FP32 records only
     assert create(good, good, tiny, 1) == 1 and b"float" in lib.fqsl_last_error()
     assert create(good, good, good, 0) == 1

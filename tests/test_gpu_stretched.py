@@ -5,7 +5,8 @@ reading R16 of the oracle).
 
 FP64 tracer: every output identical to the oracle's to the last bit (so the
 parity bars hold too; both are asserted). FP32 tracer: its error against the
-oracle is bounded as on uniform grids."""
+oracle is bounded as on uniform grids. Method I, seed lists and Method II
+(both ways of grad(B/|B|), Q and Q_perp)."""
 import math
 
 import numpy as np
@@ -184,17 +185,45 @@ def test_static_entry_point(fq, oracle_lib, mono):
     assert_bitwise(to_np(out), oracle.plane(B.astype(np.float64), grid, *args, oracle.params()))
 
 
+@pytest.mark.parametrize("way", [1, 2])
+@pytest.mark.parametrize("qperp", [0, 1])
+def test_method2_fp64_bitwise_and_fp32(fq, oracle_lib, mono, way, qperp):
+    """Method II (deviation vectors) on the stretched grid: the gradient grid
+    of way 1 with non-uniform stencils, way 2's offsets in cells of the step's
+    start cell; Q and Q_perp."""
+    B, grid = mono
+    field = _field(fq, B, grid, pack=("f32", "f64", "gradb"))
+    args = ((0.0, 0.0, 0.0), (63.0 / 61, 0, 0), (0, 55.0 / 43, 0), 61, 43)
+    g = _plane(fq, field, *args, precision="f64", method=2, gradb_way=way, qperp=qperp)
+    r = oracle.plane(B.astype(np.float64), grid, *args, oracle.params(method=2, way=way, qperp=qperp))
+    assert np.isfinite(r["Q"]).sum() > 2000
+    assert_fp64_parity(g, r)
+    assert_bitwise(g, r)
+    g32 = _plane(fq, field, *args, precision="f32", method=2, gradb_way=way, qperp=qperp)
+    assert np.mean(g32["face2"] == r["face2"]) > 0.99
+    rel = q_rel(g32, r)
+    assert np.median(rel[np.isfinite(rel)]) < 1e-3
+
+
+def test_method2_volume_fp64_bitwise(fq, oracle_lib, mono):
+    B, grid = mono
+    field = _field(fq, B, grid, pack=("f64", "gradb"))
+    step = (63.0 / 12, 55.0 / 10, 31.0 / 4)
+    g = to_np(fq.qmap_volume(field, (0.0, 0.0, 0.0), step, 12, 10, 4, fq.params(precision="f64", method=2)))
+    field.check()
+    r = oracle.qmap(B.astype(np.float64), grid, (0.0, 0.0, 0.0), (step[0], 0, 0), (0, step[1], 0), (0, 0, step[2]),
+                    (12, 10, 4), oracle.params(method=2))
+    assert_bitwise(g, r)
+
+
 def test_unsupported_modes(fq, mono):
     B, grid = mono
     field = _field(fq, B, grid)
     args = ((0.0, 0.0, 0.0), (1.0, 0, 0), (0, 1.0, 0), 4, 4)
-    for kw in (dict(method=2), dict(tape=1)):
+    for kw in (dict(tape=1), dict(scheme=1), dict(method=2, gradb_way=1)):
         with pytest.raises(fq.FqslError) as ei:
             fq.qmap_plane(field, *args, fq.params(**kw))
-        assert ei.value.status == 5
-    with pytest.raises(fq.FqslError) as ei:
-        _field(fq, B, grid, pack=("f32", "gradb"))
-    assert ei.value.status == 1
+        assert ei.value.status == 5, kw
     with pytest.raises(fq.FqslError) as ei:
         fq.Batch([field], [dict(origin=args[0], u=args[1], v=args[2], nu=4, nv=4)], fq.params())
     assert ei.value.status == 5
