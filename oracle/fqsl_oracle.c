@@ -122,7 +122,8 @@
  *       is R5 with 3/8-rule stages; a grazing exit halves the step, which then
  *       stays halved, down to h_min before the chord fallback. The paper gives
  *       no step_min; the library's default is step_perp x rot_thresh (the
- *       obliquity floor of R9).
+ *       obliquity floor of R9). On a stretched grid (R16) the step is in cells
+ *       of each trial's start cell.
  *   R13 Derivatives (the paper has none; the adjoint tests): d(Q, Tw)/dB is
  *       that of the traced computation with each line's accepted step sizes,
  *       exit faces and exit kinds (exit step, clamped exit step, chord after
@@ -1022,7 +1023,6 @@ int oracle_qmap_rect(const double *B, const double *J, const double *G, const lo
     OField f;
     if (o_make_field_rect(&f, B, J, G, n, X)) return 1;
     if (p->method == 2 && p->way == 1 && !G) return 2;
-    if (p->scheme != 0) return 2; /* the fixed-step scheme runs on uniform grids */
     return o_qmap(&f, lo, a1, a2, a3, ln, p, sample, nsample, Qo, Two, leno, r1, r2, f1, f2, st, steps);
 }
 

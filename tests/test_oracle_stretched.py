@@ -255,3 +255,31 @@ def test_method2_uniform_coordinates_reduce_to_the_uniform_method():
         ok = np.isfinite(a["Q"])
         assert ok.sum() > 200 and np.array_equal(a["face2"], b["face2"])
         assert np.median(np.abs(b["Q"][ok] / a["Q"][ok] - 1)) < bound
+
+
+def test_fixed_step_scheme_on_a_stretched_grid():
+    # B = (0, 0, 1) on a z axis with cells growing by 1.3 and the 3/8 rule:
+    # every trial moves h times the width of the cell it starts in
+    zs = np.asarray(synth.stretched_axis(12, 0.0, 1.0, 1.3, "bottom"))
+    g = synth.RectGrid((synth.stretched_axis(5, -1.0, 1.0, 1.0), synth.stretched_axis(5, -1.0, 1.0, 1.0),
+                        tuple(zs)))
+    B = synth.analytic_cube("uniform", g)
+    out = oracle.twist(B, g, [[0.1, -0.2, 0.0]], oracle.params(scheme=1, step=0.7))
+    z, trials = 0.0, 0
+    while True:
+        c = min(np.searchsorted(zs, z, side="right") - 1, len(zs) - 2)
+        zn = z + 0.7 * (zs[c + 1] - zs[c])
+        trials += 1
+        if zn > 1.0:
+            trials += 1
+            break
+        z = zn
+    assert int(out["steps"][0]) == trials + 2
+    np.testing.assert_allclose(out["r2"][0], [0.1, -0.2, 1.0], rtol=0, atol=1e-15)
+    # and the hyperbolic closed form at a small step
+    g = _grid()
+    d, o, u, v = _seeds(10, -0.3, 0.3)
+    out = oracle.plane(synth.analytic_cube("hyperbolic", g), g, o, u, v, 10, 10,
+                       oracle.params(scheme=1, step=0.1, step_min=0.01))
+    assert np.all(out["face2"] == 5)
+    np.testing.assert_allclose(out["Q"], E2, rtol=2e-5)
