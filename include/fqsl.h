@@ -124,7 +124,8 @@ typedef struct {
                              A Method I lattice seed steps max(step |Bn0/B|, step_min) (Sec. 4 Eq. step);
                              rotated seeds, their extra lines, Method II lines and seed lists step `step`.
                              A grazing exit halves the step for the rest of the direction (down to h_min).
-                             Uniform grids only; no step tape, no batches (FQSL_ERR_UNSUPPORTED) */
+                             On a stretched grid the step is in cells of each trial's start cell.
+                             No step tape, no batches (FQSL_ERR_UNSUPPORTED) */
     double step;          /* scheme 1: step_perp in cells, default 3.0 (Method I in the paper's Table 1) */
     double step_min;      /* scheme 1: lower bound of Eq. step in cells, default 0.15 = 3.0 x rot_thresh (the
                              paper gives no value) */
@@ -190,8 +191,8 @@ FQSL_API fqsl_status fqsl_field_create(const void *B_dev, fqsl_dtype b_dtype, lo
  * measured in those cells, so step, h_min, h_max and tol stay in cells.
  * Handles made here serve fqsl_qmap_plane, fqsl_qmap_volume,
  * fqsl_qmap_plane_static and fqsl_twist with Method I and Method II (way 2
- * offsets +-eps_way2 cells of the trial's start cell); the step tape, the
- * fixed-step scheme and batches return FQSL_ERR_UNSUPPORTED. Errors:
+ * offsets +-eps_way2 cells of the trial's start cell) and both schemes; the
+ * step tape and batches return FQSL_ERR_UNSUPPORTED. Errors:
  * FQSL_ERR_ARG (null pointers, sizes, flags, coordinates not strictly
  * increasing or not finite, coordinates that collapse in float when
  * FQSL_PACK_F32 is asked for), FQSL_ERR_OOM, FQSL_ERR_CUDA. */

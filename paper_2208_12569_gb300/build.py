@@ -20,7 +20,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
 # Translation units whose FP64 arithmetic must round like a plain evaluation
 # of the method (no fused multiply-add contraction): the FP64 tracers, the curl
 # grid and the Q assembly. The FP32 tracers keep contraction.
-NO_FMAD = {"trace_f64.cu", "trace_rect_f64.cu", "trace_rk38_f64.cu", "field.cu", "assemble.cu"}
+NO_FMAD = {"trace_f64.cu", "trace_rect_f64.cu", "trace_rk38_f64.cu", "trace_rect_rk38_f64.cu", "field.cu", "assemble.cu"}
 
 
 def nvcc() -> str:

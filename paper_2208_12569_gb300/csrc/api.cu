@@ -506,7 +506,6 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
         if (!(p->step > 0) || !isfinite(p->step)) return fail(FQSL_ERR_ARG, "%s: step must be > 0", who);
         if (!(p->step_min >= 0) || !(p->step_min <= p->step))
             return fail(FQSL_ERR_ARG, "%s: need 0 <= step_min <= step", who);
-        if (f->g.rect) return fail(FQSL_ERR_UNSUPPORTED, "%s: the fixed-step scheme runs on uniform grids", who);
         if (p->tape) return fail(FQSL_ERR_UNSUPPORTED, "%s: the step tape records RKF45 maps", who);
     }
     if (p->qperp && p->method != 2) return fail(FQSL_ERR_UNSUPPORTED, "%s: Q_perp needs Method II", who);
@@ -629,7 +628,10 @@ int blocks_per_sm(fqsl_field f, int precision, int src, int p_scheme)
 {
     int &c = f->blocks_cache[p_scheme][precision][src];
     if (!c) {
-        if (p_scheme == 1)
+        if (p_scheme == 1 && f->g.rect)
+            c = precision == FQSL_F64 ? trace_rect_rk38_blocks_per_sm_f64(src)
+                                      : trace_rect_rk38_blocks_per_sm_f32(src, precision == FQSL_F32_ACC64);
+        else if (p_scheme == 1)
             c = precision == FQSL_F64 ? trace_rk38_blocks_per_sm_f64(src)
                                       : trace_rk38_blocks_per_sm_f32(src, precision == FQSL_F32_ACC64);
         else if (f->g.rect)
@@ -661,7 +663,10 @@ cudaError_t launch_trace_m2(fqsl_field f, const fqsl_params *p, const TraceArgs 
 {
     int &c = f->blocks_cache_m2[p->scheme][p->precision == FQSL_F64 ? 1 : 0][p->gradb_way - 1];
     if (!c) {
-        if (p->scheme == 1)
+        if (p->scheme == 1 && f->g.rect)
+            c = p->precision == FQSL_F64 ? trace_dev_rect_rk38_blocks_per_sm_f64(p->gradb_way)
+                                         : trace_dev_rect_rk38_blocks_per_sm_f32(p->gradb_way);
+        else if (p->scheme == 1)
             c = p->precision == FQSL_F64 ? trace_dev_rk38_blocks_per_sm_f64(p->gradb_way)
                                          : trace_dev_rk38_blocks_per_sm_f32(p->gradb_way);
         else if (f->g.rect)

@@ -263,6 +263,15 @@ int trace_rk38_blocks_per_sm_f32(int src, bool acc64);
 int trace_rk38_blocks_per_sm_f64(int src);
 int trace_dev_rk38_blocks_per_sm_f32(int way);
 int trace_dev_rk38_blocks_per_sm_f64(int way);
+// the fixed-step scheme on a stretched grid
+cudaError_t launch_trace_rect_rk38_f32(const TraceArgs &a, int src, int grid, cudaStream_t s, bool acc64);
+cudaError_t launch_trace_rect_rk38_f64(const TraceArgs &a, int src, int grid, cudaStream_t s);
+cudaError_t launch_trace_dev_rect_rk38_f32(const TraceArgs &a, int way, int grid, cudaStream_t s);
+cudaError_t launch_trace_dev_rect_rk38_f64(const TraceArgs &a, int way, int grid, cudaStream_t s);
+int trace_rect_rk38_blocks_per_sm_f32(int src, bool acc64);
+int trace_rect_rk38_blocks_per_sm_f64(int src);
+int trace_dev_rect_rk38_blocks_per_sm_f32(int way);
+int trace_dev_rect_rk38_blocks_per_sm_f64(int way);
 // Method II tracers (deviation vectors; way 1 = gradient grid, 2 = +-eps)
 cudaError_t launch_trace_dev_f32(const TraceArgs &a, int way, int grid, int block, cudaStream_t s);
 cudaError_t launch_trace_dev_f64(const TraceArgs &a, int way, int grid, int block, cudaStream_t s);

@@ -47,7 +47,8 @@ int blocks(int src)
 cudaError_t launch_trace_f32(const TraceArgs &a, int src, int grid, int block, cudaStream_t s, bool acc64)
 {
     if (block != kBlock) return cudaErrorInvalidValue;
-    if (a.p.scheme == 1) return launch_trace_rk38_f32(a, src, grid, s, acc64);
+    if (a.p.scheme == 1)
+        return a.f.rect ? launch_trace_rect_rk38_f32(a, src, grid, s, acc64) : launch_trace_rk38_f32(a, src, grid, s, acc64);
     if (a.f.rect) return launch_trace_rect_f32(a, src, grid, s, acc64);
     if (acc64) launch<true>(a, src, grid, block, s);
     else launch<false>(a, src, grid, block, s);
@@ -95,7 +96,8 @@ __global__ void __launch_bounds__(kBlock) k_trace_dev_f32(const TraceArgs A)
 cudaError_t launch_trace_dev_f32(const TraceArgs &a, int way, int grid, int block, cudaStream_t s)
 {
     if (block != kBlock) return cudaErrorInvalidValue;
-    if (a.p.scheme == 1) return launch_trace_dev_rk38_f32(a, way, grid, s);
+    if (a.p.scheme == 1)
+        return a.f.rect ? launch_trace_dev_rect_rk38_f32(a, way, grid, s) : launch_trace_dev_rk38_f32(a, way, grid, s);
     if (a.f.rect) return launch_trace_dev_rect_f32(a, way, grid, s);
     if (way == 1) k_trace_dev_f32<1><<<grid, block, 0, s>>>(a);
     else k_trace_dev_f32<2><<<grid, block, 0, s>>>(a);

@@ -16,7 +16,8 @@ __global__ void __launch_bounds__(kBlock) k_trace_f64(const TraceArgs A)
 cudaError_t launch_trace_f64(const TraceArgs &a, int src, int grid, int block, cudaStream_t s)
 {
     if (block != kBlock) return cudaErrorInvalidValue;
-    if (a.p.scheme == 1) return launch_trace_rk38_f64(a, src, grid, s);
+    if (a.p.scheme == 1)
+        return a.f.rect ? launch_trace_rect_rk38_f64(a, src, grid, s) : launch_trace_rk38_f64(a, src, grid, s);
     if (a.f.rect) return launch_trace_rect_f64(a, src, grid, s);
     if (src == kSrcLattice) k_trace_f64<kSrcLattice><<<grid, block, 0, s>>>(a);
     else if (src == kSrcExtra) k_trace_f64<kSrcExtra><<<grid, block, 0, s>>>(a);
@@ -47,7 +48,8 @@ __global__ void __launch_bounds__(kBlock) k_trace_dev_f64(const TraceArgs A)
 cudaError_t launch_trace_dev_f64(const TraceArgs &a, int way, int grid, int block, cudaStream_t s)
 {
     if (block != kBlock) return cudaErrorInvalidValue;
-    if (a.p.scheme == 1) return launch_trace_dev_rk38_f64(a, way, grid, s);
+    if (a.p.scheme == 1)
+        return a.f.rect ? launch_trace_dev_rect_rk38_f64(a, way, grid, s) : launch_trace_dev_rk38_f64(a, way, grid, s);
     if (a.f.rect) return launch_trace_dev_rect_f64(a, way, grid, s);
     if (way == 1) k_trace_dev_f64<1><<<grid, block, 0, s>>>(a);
     else k_trace_dev_f64<2><<<grid, block, 0, s>>>(a);

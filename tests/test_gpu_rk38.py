@@ -121,11 +121,6 @@ def test_argument_errors(fq, mono):
         with pytest.raises(fq.FqslError) as ei:
             fq.qmap_plane(field, *args, fq.params(**kw))
         assert ei.value.status == status, kw
-    rg = synth.stretched_grid((8, 8, 8), (0, 0, 0), (7, 7, 7), ratios=(1.1, 1.1, 1.1))
-    fr = fq.Field(torch.from_numpy(synth.analytic_cube("uniform", rg)).cuda(), coords=rg.coords)
-    with pytest.raises(fq.FqslError) as ei:
-        fq.qmap_plane(fr, *args, fq.params(scheme=1))
-    assert ei.value.status == 5
     with pytest.raises(fq.FqslError) as ei:
         fq.Batch([field], [dict(origin=args[0], u=args[1], v=args[2], nu=4, nv=4)], fq.params(scheme=1))
     assert ei.value.status == 5

@@ -216,11 +216,33 @@ def test_method2_volume_fp64_bitwise(fq, oracle_lib, mono):
     assert_bitwise(g, r)
 
 
+@pytest.mark.parametrize("method,way", [(1, 1), (2, 1), (2, 2)])
+def test_fixed_step_scheme_fp64_bitwise(fq, oracle_lib, mono, method, way):
+    # the 3/8 rule with Eq. step on the stretched grid (steps in cells of each
+    # trial's start cell)
+    B, grid = mono
+    field = _field(fq, B, grid, pack=("f32", "f64", "gradb"))
+    args = ((0.0, 0.0, 0.0), (63.0 / 61, 0, 0), (0, 55.0 / 43, 0), 61, 43)
+    kw = dict(method=method, gradb_way=way, scheme=1, step=3.0 if method == 1 else 4.0)
+    g = _plane(fq, field, *args, precision="f64", **kw)
+    r = oracle.plane(B.astype(np.float64), grid, *args,
+                     oracle.params(method=method, way=way, scheme=1, step=kw["step"]))
+    assert_bitwise(g, r)
+    g32 = _plane(fq, field, *args, precision="f32", **kw)
+    rel = q_rel(g32, r)
+    assert np.median(rel[np.isfinite(rel)]) < 1e-3
+    if method == 1:
+        seeds = np.random.default_rng(5).uniform([0, 0, 0], [63, 55, 31], size=(200, 3))
+        g = to_np(fq.twist(field, torch.from_numpy(seeds).cuda(), fq.params(precision="f64", scheme=1, step=1.1)))
+        field.check()
+        assert_bitwise(g, oracle.twist(B.astype(np.float64), grid, seeds, oracle.params(scheme=1, step=1.1)))
+
+
 def test_unsupported_modes(fq, mono):
     B, grid = mono
     field = _field(fq, B, grid)
     args = ((0.0, 0.0, 0.0), (1.0, 0, 0), (0, 1.0, 0), 4, 4)
-    for kw in (dict(tape=1), dict(scheme=1), dict(method=2, gradb_way=1)):
+    for kw in (dict(tape=1), dict(method=2, gradb_way=1)):
         with pytest.raises(fq.FqslError) as ei:
             fq.qmap_plane(field, *args, fq.params(**kw))
         assert ei.value.status == 5, kw
