@@ -94,7 +94,8 @@
  *   R11 Line status bits: MAXSTEPS 1, NULL_B 2 (|bt| = 0 or not finite at an
  *       evaluation), STALL 4, MIXED 8, OUTSIDE 16 (seed outside the box),
  *       ROTATED 32, CHORD 64. Q and Tw are NaN when MAXSTEPS, NULL_B or OUTSIDE
- *       is set; Q is NaN when MIXED is set.
+ *       is set; Q is NaN when MIXED is set. MIXED describes the stencil of a
+ *       good line's Q, so a line with MAXSTEPS, NULL_B or OUTSIDE never has it.
  *   R16 Stretched (rectilinear) grids, Sec. 2.2 and 2.3: the nodes are
  *       x_i, y_j, z_k from three increasing coordinate arrays. The cell of a
  *       point is the largest i in [0, n-2] with x_i <= x (a binary search;
@@ -1082,7 +1083,7 @@ static int o_qmap(const OField *fp, const double lo[3], const double a1[3], cons
                     o_trace_line(&f, p, rr, nrot, o_ctl_perp(p), NULL, NULL, &nbl[q]);
                     nb[q] = &nbl[q];
                 }
-                Q = o_q_method1(&f, &c, nb, drot, drot, S.bn0, &c.status);
+                Q = o_line_ok(&c) ? o_q_method1(&f, &c, nb, drot, drot, S.bn0, &c.status) : NAN;
             } else {
                 long long ni[4] = {i + 1, i - 1, i, i}, nj[4] = {j, j, j + 1, j - 1};
                 for (int q = 0; q < 4; q++) {
@@ -1093,7 +1094,7 @@ static int o_qmap(const OField *fp, const double lo[3], const double a1[3], cons
                     o_trace_line(&f, p, SN.r0, SN.n0, SN.tol, NULL, NULL, &nbl[q]);
                     nb[q] = &nbl[q];
                 }
-                Q = o_q_method1(&f, &c, nb, du, dv, S.bn0, &c.status);
+                Q = o_line_ok(&c) ? o_q_method1(&f, &c, nb, du, dv, S.bn0, &c.status) : NAN;
             }
         }
         o_write(&f, &c, s, Q, Qo, Two, leno, r1, r2, f1, f2, st, steps);

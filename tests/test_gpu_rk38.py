@@ -124,3 +124,30 @@ def test_argument_errors(fq, mono):
     with pytest.raises(fq.FqslError) as ei:
         fq.Batch([field], [dict(origin=args[0], u=args[1], v=args[2], nu=4, nv=4)], fq.params(scheme=1))
     assert ei.value.status == 5
+
+
+def test_edge_cases_bitwise(fq, oracle_lib):
+    # closed loops hit max_steps, a zero field is NULL_B, a plane partly
+    # outside the box gives OUTSIDE and MIXED, the tilted field rotates S0
+    cases = [
+        ("loops", ((-0.5, -0.5, 0.5), (0.25, 0, 0), (0, 0.25, 0), 4, 4), dict(max_steps=3000, step=0.5)),
+        ("zero", ((-0.5, -0.5, 0.0), (0.25, 0, 0), (0, 0.25, 0), 4, 4), {}),
+        ("uniform", ((0.6, -0.2, 0.0), (0.2, 0, 0), (0, 0.2, 0), 4, 2), {}),
+        ("tilted", ((-0.8, -0.8, 0.5), (0.1, 0, 0), (0, 0.1, 0), 16, 16), dict(step=0.3)),
+    ]
+    for kind, plane, kw in cases:
+        B = synth.analytic_cube(kind)
+        field = _field(fq, B, G1)
+        gg = _plane(fq, field, *plane, precision="f64", **kw)
+        r = oracle.plane(B, G1, *plane, _ora(**kw))
+        assert_bitwise(gg, r)
+        if kind == "loops":
+            assert np.all(gg["status"] & oracle.MAXSTEPS)
+        if kind == "zero":
+            assert np.all(gg["status"] == oracle.NULL_B)
+        if kind == "uniform":
+            assert (gg["status"] & oracle.OUTSIDE).any() and (gg["status"] & oracle.MIXED).any()
+        if kind == "tilted":
+            assert np.all(gg["status"] & oracle.ROTATED)
+            np.testing.assert_allclose(gg["Q"], 2.0, rtol=1e-6)
+        field.close()

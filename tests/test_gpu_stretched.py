@@ -270,3 +270,32 @@ def test_full_size_stretched_workload_sampled(fq, oracle_lib):
     assert np.mean(g32s["face2"] == r["face2"]) > 0.98
     rel = q_rel(g32s, r)
     assert np.median(rel[np.isfinite(rel)]) < 1e-3
+
+
+def test_edge_cases_bitwise(fq, oracle_lib):
+    # closed loops hit max_steps, a zero field is NULL_B, a plane partly outside
+    # the box gives OUTSIDE and MIXED seeds, the tilted field rotates S0 (Q = 2):
+    # every record as the oracle's, on a stretched grid
+    g = synth.stretched_grid((24, 20, 16), (-1.0, -1.0, 0.0), (1.0, 1.0, 1.0), ratios=(1.05, 1.04, 1.08))
+    cases = [
+        ("loops", ((-0.5, -0.5, 0.5), (0.25, 0, 0), (0, 0.25, 0), 4, 4), dict(max_steps=3000, tol=1e-6)),
+        ("zero", ((-0.5, -0.5, 0.0), (0.25, 0, 0), (0, 0.25, 0), 4, 4), {}),
+        ("uniform", ((0.6, -0.2, 0.0), (0.2, 0, 0), (0, 0.2, 0), 4, 2), {}),
+        ("tilted", ((-0.8, -0.8, 0.5), (0.1, 0, 0), (0, 0.1, 0), 16, 16), dict(tol=1e-10)),
+    ]
+    for kind, plane, kw in cases:
+        B = synth.analytic_cube(kind, g)
+        field = _field(fq, B, g)
+        gg = _plane(fq, field, *plane, precision="f64", **kw)
+        r = oracle.plane(B, g, *plane, oracle.params(**kw))
+        assert_bitwise(gg, r)
+        if kind == "loops":
+            assert np.all(gg["status"] & oracle.MAXSTEPS)
+        if kind == "zero":
+            assert np.all(gg["status"] == oracle.NULL_B)
+        if kind == "uniform":
+            assert (gg["status"] & oracle.OUTSIDE).any() and (gg["status"] & oracle.MIXED).any()
+        if kind == "tilted":
+            assert np.all(gg["status"] & oracle.ROTATED)
+            np.testing.assert_allclose(gg["Q"], 2.0, rtol=1e-8)
+        field.close()
