@@ -280,7 +280,7 @@ def test_edge_cases_bitwise(fq, oracle_lib):
     cases = [
         ("loops", ((-0.5, -0.5, 0.5), (0.25, 0, 0), (0, 0.25, 0), 4, 4), dict(max_steps=3000, tol=1e-6)),
         ("zero", ((-0.5, -0.5, 0.0), (0.25, 0, 0), (0, 0.25, 0), 4, 4), {}),
-        ("uniform", ((0.6, -0.2, 0.0), (0.2, 0, 0), (0, 0.2, 0), 4, 2), {}),
+        ("uniform", ((0.8, -0.2, 0.0), (0.2, 0, 0), (0, 0.2, 0), 4, 2), {}),
         ("tilted", ((-0.8, -0.8, 0.5), (0.1, 0, 0), (0, 0.1, 0), 16, 16), dict(tol=1e-10)),
     ]
     for kind, plane, kw in cases:
