@@ -299,3 +299,26 @@ def test_edge_cases_bitwise(fq, oracle_lib):
             assert np.all(gg["status"] & oracle.ROTATED)
             np.testing.assert_allclose(gg["Q"], 2.0, rtol=1e-8)
         field.close()
+
+
+def test_strongly_stretched_axes_bitwise(fq, oracle_lib):
+    # cell widths spanning a factor of about 800 along z and 60 along x: the
+    # buckets (at most 16 per cell) then hold several nodes, so the cell search
+    # often walks from the bucket's cell; the FP64 map stays the oracle's
+    g = synth.RectGrid((synth.stretched_axis(40, 0.0, 39.0, 1.23, "edges"),
+                        synth.stretched_axis(24, 0.0, 23.0, 1.0, "bottom"),
+                        synth.stretched_axis(32, 0.0, 31.0, 1.25, "bottom")))
+    w = [np.diff(g.axis(a)) for a in range(3)]
+    assert w[0].max() / w[0].min() > 50 and w[2].max() / w[2].min() > 500
+    ch = synth.random_charges(np.random.default_rng(8), 8, ((0.0, 39.0), (0.0, 23.0)), depth=(3.0, 8.0))
+    B = synth.monopole_cube(g, ch, dtype=np.float32)
+    field = _field(fq, B, g)
+    args = ((0.0, 0.0, 0.0), (39.0 / 50, 0, 0), (0, 23.0 / 30, 0), 50, 30)
+    gg = _plane(fq, field, *args, precision="f64")
+    r = oracle.plane(B.astype(np.float64), g, *args, oracle.params())
+    assert np.isfinite(r["Q"]).sum() > 1000
+    assert_bitwise(gg, r)
+    g32 = _plane(fq, field, *args, precision="f32")
+    assert np.array_equal(g32["status"] & oracle.BAD, r["status"] & oracle.BAD)
+    rel = q_rel(g32, r)
+    assert np.median(rel[np.isfinite(rel)]) < 1e-3
