@@ -33,6 +33,9 @@ from . import BAD, ROTATED, _f64, _grid_args, _p, curl, lib, params, plane
 _A = [[], [1 / 4], [3 / 32, 9 / 32], [1932 / 2197, -7200 / 2197, 7296 / 2197],
       [439 / 216, -8.0, 3680 / 513, -845 / 4104], [-8 / 27, 2.0, -3544 / 2565, 1859 / 4104, -11 / 40]]
 _B4 = [25 / 216, 0.0, 1408 / 2565, 2197 / 4104, -1 / 5, 0.0]
+# Kutta's 3/8 rule (the fixed-step scheme, reading R18)
+_A38 = [[], [1 / 3], [-1 / 3, 1.0], [1.0, -1.0, 1.0]]
+_B38 = [1 / 8, 3 / 8, 3 / 8, 1 / 8]
 
 # step-record codes of oracle_lattice_log
 START, STEP, EXIT, EXIT_CLAMPED, CHORD = 99, 0, 16, 40, 48
@@ -71,6 +74,7 @@ def lattice_log(B, grid, origin, u, v, nu, nv, p=None, cap=8192, J=None, which=N
         raise ValueError("oracle_lattice_log: error %d" % rc)
     if np.any(out["n"] < 0) or (extra and np.any(out["xn"] < 0)):
         raise ValueError("step record overflow: raise cap")
+    out["scheme"] = int(p.scheme)
     return out
 
 
@@ -141,21 +145,23 @@ class _Field:
         return F, dtw
 
 
-def _rk4(fld, x, h, sig, ax=None):
-    """One Fehlberg step of the 4th-order solution from x. With ax (face axis
-    per lane) the independent variable is that index coordinate (exit step):
-    the RHS is divided by its ax component."""
+def _rk4(fld, x, h, sig, ax=None, scheme=0):
+    """One Fehlberg step of the 4th-order solution from x (scheme 1: one
+    3/8-rule step). With ax (face axis per lane) the independent variable is
+    that index coordinate (exit step): the RHS is divided by its ax
+    component."""
+    A, Bw = (_A38, _B38) if scheme == 1 else (_A, _B4)
     ks, ts = [], []
-    for s in range(6):
-        acc = sum(_A[s][r] * ks[r] for r in range(s)) if s else torch.zeros_like(x)
+    for s in range(len(Bw)):
+        acc = sum(A[s][r] * ks[r] for r in range(s)) if s else torch.zeros_like(x)
         F, dtw = fld.rhs(x + h[:, None] * acc, sig)
         if ax is not None:
             fa = F.gather(1, ax[:, None])[:, 0]
             F, dtw = F / fa[:, None], dtw / fa
         ks.append(F)
         ts.append(dtw)
-    x4 = x + h[:, None] * sum(_B4[s] * ks[s] for s in range(6))
-    dtw4 = h * sum(_B4[s] * ts[s] for s in range(6))
+    x4 = x + h[:, None] * sum(Bw[s] * ks[s] for s in range(len(Bw)))
+    dtw4 = h * sum(Bw[s] * ts[s] for s in range(len(Bw)))
     return x4, dtw4
 
 
@@ -187,6 +193,7 @@ def replay(fld, xi0, s0, log):
     end positions (m, 2, 3) in index coordinates and Tw of each direction
     (m, 2). End 1 (half-line 2i) is traced along -s0 B."""
     m = xi0.shape[0]
+    scheme = log.get("scheme", 0)
     code, hh = half_lines(log)
     H, T = code.shape
     sig = torch.stack([-s0, s0], dim=1).reshape(H)
@@ -200,7 +207,7 @@ def replay(fld, xi0, s0, log):
         i_n = np.nonzero(ct == STEP)[0]
         if len(i_n):
             idx = torch.from_numpy(i_n)
-            x4, d4 = _rk4(fld, xi[idx], torch.from_numpy(hh[i_n, t]), sig[idx])
+            x4, d4 = _rk4(fld, xi[idx], torch.from_numpy(hh[i_n, t]), sig[idx], scheme=scheme)
             xi = xi.index_put((idx,), x4)
             tw = tw.index_put((idx,), tw[idx] + d4)
         # exit steps (independent variable = face-normal coordinate, Sec. 2.1)
@@ -212,7 +219,7 @@ def replay(fld, xi0, s0, log):
             target = torch.where(face % 2 == 1, hi[ax], torch.zeros(len(i_e), dtype=torch.float64))
             x = xi[idx]
             delta = target - x.gather(1, ax[:, None])[:, 0]
-            xe, de = _rk4(fld, x, delta, sig[idx], ax)
+            xe, de = _rk4(fld, x, delta, sig[idx], ax, scheme=scheme)
             onehot = torch.nn.functional.one_hot(ax, 3).to(torch.bool)
             xe = torch.where(onehot, target[:, None], xe)
             xe = torch.minimum(torch.maximum(xe, torch.zeros_like(xe)), hi)  # the clamp of code 40+
@@ -226,7 +233,7 @@ def replay(fld, xi0, s0, log):
             ax = face // 2
             target = torch.where(face % 2 == 1, hi[ax], torch.zeros(len(i_c), dtype=torch.float64))
             x = xi[idx]
-            x4, d4 = _rk4(fld, x, torch.from_numpy(hh[i_c, t]), sig[idx])
+            x4, d4 = _rk4(fld, x, torch.from_numpy(hh[i_c, t]), sig[idx], scheme=scheme)
             xa, x4a = x.gather(1, ax[:, None])[:, 0], x4.gather(1, ax[:, None])[:, 0]
             t0 = (target - xa) / (x4a - xa)
             onehot = torch.nn.functional.one_hot(ax, 3).to(torch.bool)
@@ -355,7 +362,7 @@ def qmap_t(Bt, grid, origin, u, v, nu, nv, log, lines=None, targets=None):
             xrows[(t, q)] = mr + len(xi_x) - 1
     if xi_x:
         rlog = dict(h=np.concatenate([log["h"], np.stack(xh)]), code=np.concatenate([log["code"], np.stack(xc)]),
-                    n=np.concatenate([log["n"], np.array(xn, np.int32)]))
+                    n=np.concatenate([log["n"], np.array(xn, np.int32)]), scheme=log.get("scheme", 0))
         xi0 = torch.cat([xi0, torch.stack(xi_x)])
         s0 = torch.cat([s0, torch.tensor(s0_x, dtype=torch.float64)])
         faces = np.concatenate([faces, np.stack(xf)])

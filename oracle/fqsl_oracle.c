@@ -133,7 +133,8 @@
  *       step's length to the face, the chord parameter, Bn at the seed and at
  *       both ends, the finite-difference stencils' values -- varies with B.
  *       oracle_lattice_log exports the frozen sequence; oracle/adjoint.py
- *       replays and differentiates it.
+ *       replays and differentiates it. With the fixed-step scheme (R18) the
+ *       frozen sequence is the line's fixed steps (halved where an exit grazed).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -1206,7 +1207,7 @@ int oracle_lattice_log(const double *B, const double *J, const long long n[3], c
 {
     OField f;
     if (o_make_field(&f, B, J, NULL, n, o, d)) return 1;
-    if (p->method != 1 || p->scheme != 0) return 2; /* the adjoint differentiates RKF45 (R13) */
+    if (p->method != 1) return 2;
     OLattice L;
     for (int a = 0; a < 3; a++) {
         L.o[a] = lo[a];
