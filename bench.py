@@ -617,6 +617,15 @@ def run_adjoint(args, emit=True):
     ms64 = timed(p64, dB64, max(2, args.fp64_steps))
     loss64 = float(lbuf["loss"])
     g64 = dB64.cpu().numpy()
+    # the fixed-step scheme (3/8 rule, Eq. step with step_perp = 3 cells): the
+    # same differentiation step, FP32
+    pfx = fq.params(precision="f32", tape=1, scheme=1)
+    for _ in range(args.warmup):
+        step(pfx, Bd, dB)
+    torch.cuda.synchronize()
+    msfx = timed(pfx, dB, args.steps)
+    tfx_fwd, tfx_rev, _ = kernel_times(pfx, dB, max(3, args.steps // 2))
+    accfx = float(fq.tape_export(field, n, cap=0)["nsteps"].to(torch.float64).sum())
 
     # end to end from pinned host memory: B in, loss and dB out
     Bh = torch.from_numpy(B).pin_memory()
@@ -660,6 +669,11 @@ def run_adjoint(args, emit=True):
         return g.cpu().numpy()
 
     rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
+    t0 = time.perf_counter()
+    ref_fx, _ = oadj.vjp_sample(B64, grid, *plane, sample, wq, wt, oracle.params(scheme=1))
+    ora_fx_s = time.perf_counter() - t0
+    errs_fx = {"f64": rel(gpu_vjp(fq.params(precision="f64", tape=1, scheme=1)), ref_fx),
+               "f32": rel(gpu_vjp(fq.params(precision="f32", tape=1, scheme=1)), ref_fx)}
     errs = {"f64": rel(gpu_vjp(p64), ref),
             "f64_forward_f32_reverse": rel(gpu_vjp(fq.params(precision="f64", tol=TOL, tape=1,
                                                              reverse_precision="f32")), ref),
@@ -694,6 +708,12 @@ def run_adjoint(args, emit=True):
                               "gather_TBs": acc_steps * REV_GATHER_BYTES_PER_STEP / (t_rev / 1000.0) / 1e12,
                               "scatter_GBs": acc_steps * REV_SCATTER_BYTES_PER_STEP / (t_rev / 1000.0) / 1e9},
             "error_vs_oracle": errs,
+            "fixed_step": {"value": float(np.mean(msfx)) / 1000.0, "unit": "s/grad", "dtype": "f32",
+                           "note": "the same differentiation step with the 3/8-rule scheme (step_perp = 3 "
+                                   "cells scaled per line by |Bn0/B|, step_min 0.15)",
+                           "kernels_ms": {"forward_taped_trace_rk38_f32": tfx_fwd, "reverse_sweep_f32": tfx_rev},
+                           "accepted_per_half_line": accfx / (2 * n), "error_vs_oracle": errs_fx,
+                           "oracle_sample_s": ora_fx_s},
             "e2e": {"value": float(np.mean(e2e)) / 1000.0, "unit": "s/grad", "h2d_bytes_per_step": int(B.nbytes),
                     "d2h_bytes_per_step": int(B.nbytes + 8)},
             "gpu_launches": 12 * args.steps, "clocks": clk,

@@ -125,7 +125,9 @@ typedef struct {
                              rotated seeds, their extra lines, Method II lines and seed lists step `step`.
                              A grazing exit halves the step for the rest of the direction (down to h_min).
                              On a stretched grid the step is in cells of each trial's start cell.
-                             No step tape, no batches (FQSL_ERR_UNSUPPORTED) */
+                             No batches (FQSL_ERR_UNSUPPORTED). With tape = 1 (uniform grids) the tape
+                             holds every step taken, grazing halvings included, and fqsl_backward
+                             reverses the 3/8 rule's four stages */
     double step;          /* scheme 1: step_perp in cells, default 3.0 (Method I in the paper's Table 1) */
     double step_min;      /* scheme 1: lower bound of Eq. step in cells, default 0.15 = 3.0 x rot_thresh (the
                              paper gives no value) */
@@ -323,10 +325,11 @@ FQSL_API fqsl_status fqsl_qmap_plane_static(fqsl_field field, const double origi
  * and the curl grid (Eq. tw) vary with B.
  *   dQ_dev, dTw_dev  double[seeds] per-seed weights in the map's output order
  *                    (either may be NULL = 0). Seeds whose Q is NaN (status
- *                    MAXSTEPS, NULL_B, OUTSIDE or MIXED) or whose S0 was
- *                    rotated (ROTATED: their Q comes from four extra lines
- *                    that are not taped) contribute nothing through Q; NaN
- *                    or infinite weights count as 0.
+ *                    MAXSTEPS, NULL_B, OUTSIDE or MIXED) contribute nothing
+ *                    through Q. A seed whose S0 was rotated (ROTATED, plane
+ *                    maps) takes Q from its four taped extra lines; its
+ *                    derivative also carries the rotated frame's dependence
+ *                    on B at the seed. NaN or infinite weights count as 0.
  *   dB_dev           B-shaped array (layout of fqsl_field_create) of db_dtype
  *                    (FQSL_F32 or FQSL_F64), accumulated into, not cleared.
  * The state is recomputed from checkpoints every params->tape_chunk accepted

@@ -67,7 +67,7 @@ struct fqsl_field_s {
     unsigned long long *counters = nullptr;  // [0] primary head, [1] extra head, [2] rotated count (low 32 bits)
     int blocks_cache[2][3][3] = {};  // [scheme][precision][source] resident blocks per SM
     int blocks_cache_m2[2][2][2] = {};  // Method II: [scheme][fp64][way - 1]
-    int blocks_cache_tape[3][2] = {};  // taped tracers: [precision][lattice, extra]
+    int blocks_cache_tape[2][3][2] = {};  // taped tracers: [scheme][precision][lattice, extra]
     bool timing = false, timed = false, extra_timed = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // the last plane map traced with params->tape = 1 (for fqsl_backward): its
@@ -506,7 +506,6 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
         if (!(p->step > 0) || !isfinite(p->step)) return fail(FQSL_ERR_ARG, "%s: step must be > 0", who);
         if (!(p->step_min >= 0) || !(p->step_min <= p->step))
             return fail(FQSL_ERR_ARG, "%s: need 0 <= step_min <= step", who);
-        if (p->tape) return fail(FQSL_ERR_UNSUPPORTED, "%s: the step tape records RKF45 maps", who);
     }
     if (p->qperp && p->method != 2) return fail(FQSL_ERR_UNSUPPORTED, "%s: Q_perp needs Method II", who);
     if (f->g.rect && p->tape) return fail(FQSL_ERR_UNSUPPORTED, "%s: no step tape on a stretched grid", who);
@@ -783,19 +782,26 @@ fqsl_status ensure_tape_buf(fqsl_field f, size_t bytes)
     return FQSL_OK;
 }
 
-int tape_blocks_per_sm(fqsl_field f, int precision, int src)
+int tape_blocks_per_sm(fqsl_field f, int precision, int src, int p_scheme)
 {
-    int &c = f->blocks_cache_tape[precision][src == kSrcExtra ? 1 : 0];
-    if (!c) c = precision == FQSL_F64 ? trace_tape_blocks_per_sm_f64(src)
-                                      : trace_tape_blocks_per_sm_f32(src, precision == FQSL_F32_ACC64);
+    int &c = f->blocks_cache_tape[p_scheme][precision][src == kSrcExtra ? 1 : 0];
+    const bool acc64 = precision == FQSL_F32_ACC64;
+    if (!c && p_scheme == 1)
+        c = precision == FQSL_F64 ? trace_tape_rk38_blocks_per_sm_f64(src) : trace_tape_rk38_blocks_per_sm_f32(src, acc64);
+    else if (!c)
+        c = precision == FQSL_F64 ? trace_tape_blocks_per_sm_f64(src) : trace_tape_blocks_per_sm_f32(src, acc64);
     return c;
 }
 
 cudaError_t launch_tape(const TraceArgs &a, const fqsl_params *p, int src, long long grid, cudaStream_t s)
 {
     if (grid < 1) grid = 1;
+    const bool acc64 = p->precision == FQSL_F32_ACC64;
+    if (p->scheme == 1)
+        return p->precision == FQSL_F64 ? launch_trace_tape_rk38_f64(a, src, (int)grid, s)
+                                        : launch_trace_tape_rk38_f32(a, src, (int)grid, s, acc64);
     return p->precision == FQSL_F64 ? launch_trace_tape_f64(a, src, (int)grid, s)
-                                    : launch_trace_tape_f32(a, src, (int)grid, s, p->precision == FQSL_F32_ACC64);
+                                    : launch_trace_tape_f32(a, src, (int)grid, s, acc64);
 }
 
 // Shared body of the plane and volume Q maps (the caller holds f->mu). With
@@ -892,7 +898,7 @@ fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params
         return FQSL_OK;
     }
     if (tape) {
-        int bps = tape_blocks_per_sm(f, p->precision, kSrcLattice);
+        int bps = tape_blocks_per_sm(f, p->precision, kSrcLattice, p->scheme);
         if (p->blocks_per_sm > 0 && p->blocks_per_sm < bps) bps = p->blocks_per_sm;
         long long grid = (long long)f->sms * bps;
         a.nitems *= 2;  // one item per direction of a line
@@ -911,7 +917,7 @@ fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params
             // their count is read on the device (persistent grid)
             a.q.head = tl.ctr + 5;
             a.tape.hl_base = 2 * n;
-            int bps = tape_blocks_per_sm(f, p->precision, kSrcExtra);
+            int bps = tape_blocks_per_sm(f, p->precision, kSrcExtra, p->scheme);
             if (p->blocks_per_sm > 0 && p->blocks_per_sm < bps) bps = p->blocks_per_sm;
             e = launch_tape(a, p, kSrcExtra, (long long)f->sms * bps, stream);
         } else {

@@ -448,3 +448,113 @@ def test_full_size_workload_sampled(fq):
     Bd = B.astype(np.float64)
     for g in (g64, g32):
         assert abs(np.sum(g * Bd)) < 1e-4 * np.linalg.norm(g) * np.linalg.norm(Bd)
+
+
+# ---------------------------------------------------------------------------
+# the fixed-step scheme (Sec. 2.3: Kutta's 3/8 rule with the per-line step of
+# Sec. 4 Eq. step): the tape holds the fixed steps (grazing halvings
+# included), the reverse sweep runs the four-stage step
+# ---------------------------------------------------------------------------
+FIXED = dict(scheme=1, step=0.3, step_min=0.05, max_steps=10 ** 6)
+
+
+@pytest.mark.parametrize("plane", [PLANE16, XZ], ids=["z0_plane", "interior_xz_plane"])
+def test_fixed_step_fp64_gradient_matches_oracle(fq, small, plane):
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    m = plane[3] * plane[4]
+    wq, wt = _weights(21, m)
+    g, st = _gpu_vjp(fq, field, plane, wq, wt, precision="f64", **FIXED)
+    ref, log = adj.vjp(B, grid, *plane, wq, wt, oracle.params(**FIXED))
+    assert log["scheme"] == 1
+    assert np.array_equal(st & oracle.BAD, log["status"] & oracle.BAD)
+    assert np.linalg.norm(ref) > 0
+    assert _rel(g, ref) < 1e-10
+    assert np.abs(g - ref).max() < 1e-10 * np.abs(ref).max()
+    if plane is XZ:
+        assert (st & fq.LINE_ROTATED).any()
+    # the RKF45 gradient of the same map is a different vector
+    g45, _ = _gpu_vjp(fq, field, plane, wq, wt, precision="f64")
+    assert _rel(g45, ref) > 1e-6
+
+
+def test_fixed_step_tape_is_the_oracle_step_sequence(fq, small):
+    # every recorded step is the line's Eq. step value (or a grazing halving
+    # of it), bit for bit the oracle's
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    fq.qmap_plane(field, *PLANE16, fq.params(precision="f64", tape=1, **FIXED))
+    m = PLANE16[3] * PLANE16[4]
+    t = {k: v.cpu().numpy() for k, v in fq.tape_export(field, m, cap=4096).items()}
+    log = adj.lattice_log(B, grid, *PLANE16, oracle.params(**FIXED))
+    code, hh = adj.half_lines(log)
+    distinct = set()
+    for hl in range(2 * m):
+        c = code[hl][code[hl] >= 0]
+        if (log["status"][hl // 2] & oracle.BAD) != 0:
+            assert t["nsteps"][hl] == 0 and t["code"][hl] == -1
+            continue
+        n = int(t["nsteps"][hl])
+        assert n == len(c) - 1 and t["code"][hl] == c[-1]
+        assert np.array_equal(t["h"][hl, :n], hh[hl, :n])
+        distinct.update(np.unique(t["h"][hl, :n]).tolist())
+    assert len(distinct) > 50  # Eq. step gives each line its own step
+
+
+@pytest.mark.parametrize("reverse", ["f32", "f32acc64"])
+def test_fixed_step_fp32_reverse_sweep_on_the_oracle_steps(fq, small, reverse):
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    m = PLANE16[3] * PLANE16[4]
+    wq, wt = _weights(22, m)
+    g, _ = _gpu_vjp(fq, field, PLANE16, wq, wt, dtype=torch.float32, precision="f64", reverse_precision=reverse,
+                    **FIXED)
+    ref, _ = adj.vjp(B, grid, *PLANE16, wq, wt, oracle.params(**FIXED))
+    assert _rel(g, ref) < 2e-3
+
+
+@pytest.mark.parametrize("precision", ["f32", "f32acc64"])
+def test_fixed_step_fp32_forward_gradient_against_oracle(fq, small, precision):
+    # With no step controller the FP32 tracer takes the oracle's steps up to the
+    # float rounding of each line's step, so its gradient stays far closer to
+    # the oracle's than the RKF45 one does
+    B, _, grid = small
+    B32 = B.astype(np.float32)
+    field = _field(fq, B32, grid)
+    m = PLANE16[3] * PLANE16[4]
+    wq, wt = _weights(23, m)
+    Bd = B32.astype(np.float64)
+    Qo = oracle.plane(Bd, grid, *PLANE16, oracle.params(**FIXED))["Q"]
+    wq = wq / np.where(np.isfinite(Qo), Qo, 1.0)
+    g, _ = _gpu_vjp(fq, field, PLANE16, wq, wt, dtype=torch.float32, precision=precision, **FIXED)
+    ref, _ = adj.vjp(Bd, grid, *PLANE16, wq, wt, oracle.params(**FIXED))
+    # (measured: 2.9e-5 on the 24^3 cube, both node-grid precisions)
+    assert _rel(g, ref) < 5e-4
+    assert abs(np.sum(g * Bd)) < 1e-4 * np.linalg.norm(g) * np.linalg.norm(Bd)
+
+
+@pytest.mark.parametrize("precision,rtol", [("f64", 1e-5), ("f32", 2e-3)])
+def test_fixed_step_hyperbolic_closed_form(fq, precision, rtol):
+    # B = (x, -y, 1), the closed form of the hyperbolic test above, through the
+    # 3/8 rule at 0.2 cells (its footpoints are exact to 1e-7 there)
+    grid = synth.C1_GRID
+    B = synth.analytic_cube("hyperbolic", grid)
+    field = _field(fq, B if precision == "f64" else B.astype(np.float32), grid)
+    X, Y, Z = _mesh(grid)
+    dB = np.stack([X, -Y, 0 * X], -1)
+    w = np.random.default_rng(3).uniform(0.5, 1.5, 36)
+    g, st = _gpu_vjp(fq, field, PATCH, w, 0 * w, precision=precision, scheme=1, step=0.2, step_min=0.01)
+    assert not (st & (oracle.BAD | oracle.MIXED)).any()
+    closed = 2.0 * (math.exp(2.0) - math.exp(-2.0))
+    np.testing.assert_allclose(np.sum(g * dB), np.sum(w) * closed, rtol=rtol)
+
+
+def test_fixed_step_checkpoint_interval_and_orthogonality(fq, small):
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    m = PLANE16[3] * PLANE16[4]
+    wq, wt = _weights(24, m)
+    gs = [_gpu_vjp(fq, field, PLANE16, wq, wt, precision="f64", tape_chunk=k, **FIXED)[0] for k in (1, 7, 32)]
+    for g in gs[1:]:
+        assert _rel(g, gs[0]) < 1e-12
+    assert abs(np.sum(gs[0] * B)) < 1e-11 * np.linalg.norm(gs[0]) * np.linalg.norm(B)

@@ -116,8 +116,7 @@ def test_argument_errors(fq, mono):
     B, grid = mono
     field = _field(fq, B, grid)
     args = ((0.0, 0.0, 0.0), (1.0, 0, 0), (0, 1.0, 0), 4, 4)
-    for kw, status in ((dict(scheme=2), 1), (dict(scheme=1, step=0.0), 1), (dict(scheme=1, step_min=5.0), 1),
-                       (dict(scheme=1, tape=1), 5)):
+    for kw, status in ((dict(scheme=2), 1), (dict(scheme=1, step=0.0), 1), (dict(scheme=1, step_min=5.0), 1)):
         with pytest.raises(fq.FqslError) as ei:
             fq.qmap_plane(field, *args, fq.params(**kw))
         assert ei.value.status == status, kw
