@@ -38,12 +38,15 @@ SEED = 2208
 WORKLOAD = "monopole24_256x256x128_f32_z0plane_1024x1024_methodI_rkf45"
 METRIC = "Q+Tw values/sec on 1 GB300 (FP32 vs FP64) at stated rel-err vs oracle"
 # Algorithmic work of one RKF45 trial step of the FP32 tracer, counted from the
-# kernel source (trace.cuh): 6 right-hand-side evaluations of 145 flops each
-# (trilinear weights 18, 8-corner x 6-component accumulation 96, normalisation
-# and twist integrand 31) plus 222 flops of stage combination; and 6 x 8
-# corner records of 32 bytes requested from L1.
-FLOPS_PER_TRIAL = 6 * 145 + 222
-GATHER_BYTES_PER_TRIAL = 6 * 8 * 32
+# kernel source (trace.cuh): 6 right-hand-side evaluations, 4 of them with the
+# twist integrand at 145 flops each (trilinear weights 18, 8-corner x
+# 6-component accumulation 96, normalisation and twist integrand 31) and the 2
+# whose 4th-order weight is zero (stages 1 and 5) with B alone at 89 flops
+# (accumulation 48, normalisation 23), plus 222 flops of stage combination; and
+# 4 x 8 corner records of 32 bytes plus 2 x 8 B halves of 16 bytes requested
+# from L1.
+FLOPS_PER_TRIAL = 4 * 145 + 2 * 89 + 222
+GATHER_BYTES_PER_TRIAL = 4 * 8 * 32 + 2 * 8 * 16
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 # DRAM bytes (read + write) of one k_trace_f32 launch on this workload, from
@@ -1040,7 +1043,7 @@ def main():
                         emit=False)
         line["adjoint"] = {k: a[k] for k in ("metric", "value", "unit", "ms_per_step", "higher_is_better", "config",
                                              "fp64", "kernels_ms", "error_vs_oracle", "e2e", "cpu_baseline",
-                                             "roofline", "reverse_sweep", "loss")}
+                                             "roofline", "reverse_sweep", "loss", "fixed_step")}
     if rank == 0 and ws == 1 and not args.no_stretched:
         # the same map on a stretched grid (its oracle check runs in the tests and in --workload stretched)
         st = run_stretched(argparse.Namespace(steps=args.steps, warmup=args.warmup, fp64_steps=args.fp64_steps,

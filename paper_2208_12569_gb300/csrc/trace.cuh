@@ -165,6 +165,16 @@ __device__ __forceinline__ void load_rec32(const char *p, float &b0, float &b1, 
 }
 #pragma nv_diag_default 550
 
+// The B half of a record (its first 16 bytes) in one 128-bit load, for
+// evaluations whose curl B is not used.
+#pragma nv_diag_suppress 550
+__device__ __forceinline__ void load_rec32_b(const char *p, float &b0, float &b1, float &b2)
+{
+    float j0;
+    asm("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(b0), "=f"(b1), "=f"(b2), "=f"(j0) : "l"(p));
+}
+#pragma nv_diag_default 550
+
 // Exact integer value of a float that holds an integer in [0, 2^23): adding
 // 2^23 puts it in the low mantissa bits. (A float -> 64-bit integer conversion
 // runs on GB300's narrow FP64 pipe; this is one FADD and one integer op.)
@@ -175,9 +185,9 @@ __device__ __forceinline__ int small_int(float c) { return __float_as_int(c + 83
 // 2^23 nodes and the cube below 2^31 nodes; sz32 = 0 marks a z stride that
 // does not fit 32 bits).
 // The 8 corners of cell node (its lowest corner) with per-axis weights w (the
-// upper node's) and u = 1 - w.
+// upper node's) and u = 1 - w. wj = false: B only (J = 0), half the bytes.
 __device__ __forceinline__ void gather_cell32(const FieldView &f, unsigned node, float wx, float wy, float wz,
-                                              float ux, float uy, float uz, float B[3], float J[3])
+                                              float ux, float uy, float uz, float B[3], float J[3], bool wj = true)
 {
     const char *p00 = (const char *)f.rec + (size_t)node * 32u;
     const size_t szb = f.sz32 ? (size_t)f.sz32 : (size_t)f.nx * (size_t)f.ny * 32u;
@@ -192,20 +202,24 @@ __device__ __forceinline__ void gather_cell32(const FieldView &f, unsigned node,
     for (int qp = 0; qp < 4; qp++) {
 #pragma unroll
         for (int m = 0; m < 2; m++) {
-            float r0, r1, r2, r3, r4, r5;
-            load_rec32(pc[qp] + 32 * m, r0, r1, r2, r3, r4, r5);
+            float r0, r1, r2, r3 = 0.f, r4 = 0.f, r5 = 0.f;
+            if (wj) load_rec32(pc[qp] + 32 * m, r0, r1, r2, r3, r4, r5);
+            else load_rec32_b(pc[qp] + 32 * m, r0, r1, r2);
             const float w = (m ? wx : ux) * wyz[qp];
             B[0] += w * r0;
             B[1] += w * r1;
             B[2] += w * r2;
-            J[0] += w * r3;
-            J[1] += w * r4;
-            J[2] += w * r5;
+            if (wj) {
+                J[0] += w * r3;
+                J[1] += w * r4;
+                J[2] += w * r5;
+            }
         }
     }
 }
 
-__device__ __forceinline__ void gather(const FieldView &f, float x, float y, float z, float B[3], float J[3])
+__device__ __forceinline__ void gather(const FieldView &f, float x, float y, float z, float B[3], float J[3],
+                                       bool wj = true)
 {
     const float cx = fminf(fmaxf(floorf(x), 0.f), f.cmax[0]);
     const float cy = fminf(fmaxf(floorf(y), 0.f), f.cmax[1]);
@@ -214,13 +228,15 @@ __device__ __forceinline__ void gather(const FieldView &f, float x, float y, flo
     const float ux = 1.f - wx, uy = 1.f - wy, uz = 1.f - wz;
     const unsigned node = ((unsigned)small_int(cz) * (unsigned)f.ny + (unsigned)small_int(cy)) * (unsigned)f.nx +
                           (unsigned)small_int(cx);
-    gather_cell32(f, node, wx, wy, wz, ux, uy, uz, B, J);
+    gather_cell32(f, node, wx, wy, wz, ux, uy, uz, B, J, wj);
 }
 
 // FP64: Eq. interp term by term, omega_0 = (i+1) - xi and omega_1 = 1 - omega_0
 // (Eqs. w0, w1 in cells), summed over m (x), n (y), p (z) in that nesting.
 // Built without contraction, this is the plain evaluation of the definition.
-__device__ __forceinline__ void gather(const FieldView &f, double x, double y, double z, double B[3], double J[3])
+// (wj: accepted for the common interface; the FP64 gather always forms J)
+__device__ __forceinline__ void gather(const FieldView &f, double x, double y, double z, double B[3], double J[3],
+                                       bool wj = true)
 {
     const double c[3] = {clampcell<double>(floor(x), f.nx), clampcell<double>(floor(y), f.ny),
                          clampcell<double>(floor(z), f.nz)};
@@ -343,18 +359,18 @@ __device__ __forceinline__ void rect_cells(const FieldView &f, T x, T y, T z, Re
 // FP32 on a stretched grid: state coordinates relative to the first node,
 // omega_0 = (x_{i+1} - x) / (x_{i+1} - x_i) with the reciprocal width (Eq. w0)
 __device__ __forceinline__ void gather_rect_at(const FieldView &f, float x, float y, float z, const RectCells<float> &rc,
-                                               float B[3], float J[3])
+                                               float B[3], float J[3], bool wj = true)
 {
     const float ux = (rc.r[0].y - x) * rc.r[0].z, uy = (rc.r[1].y - y) * rc.r[1].z, uz = (rc.r[2].y - z) * rc.r[2].z;
     const unsigned node =
         ((unsigned)rc.c[2] * (unsigned)f.ny + (unsigned)rc.c[1]) * (unsigned)f.nx + (unsigned)rc.c[0];
-    gather_cell32(f, node, 1.f - ux, 1.f - uy, 1.f - uz, ux, uy, uz, B, J);
+    gather_cell32(f, node, 1.f - ux, 1.f - uy, 1.f - uz, ux, uy, uz, B, J, wj);
 }
 
 // FP64 on a stretched grid: Eqs. interp, w0, w1 as written in physical
 // coordinates, the sum nested as in the uniform FP64 gather
 __device__ __forceinline__ void gather_rect_at(const FieldView &f, double x, double y, double z,
-                                               const RectCells<double> &rc, double B[3], double J[3])
+                                               const RectCells<double> &rc, double B[3], double J[3], bool wj = true)
 {
     const double xi[3] = {x, y, z};
     long long c[3];
@@ -392,18 +408,19 @@ __device__ __forceinline__ void gather_rect_at(const FieldView &f, double x, dou
 }
 
 template <typename T>
-__device__ __forceinline__ void gather_rect(const FieldView &f, T x, T y, T z, T B[3], T J[3])
+__device__ __forceinline__ void gather_rect(const FieldView &f, T x, T y, T z, T B[3], T J[3], bool wj = true)
 {
     RectCells<T> rc;
     rect_cells(f, x, y, z, rc);
-    gather_rect_at(f, x, y, z, rc, B, J);
+    gather_rect_at(f, x, y, z, rc, B, J, wj);
 }
 
+// wj = false: B only where the precision allows (FP32 loads half of each record)
 template <bool RECT, typename T>
-__device__ __forceinline__ void gatherg(const FieldView &f, T x, T y, T z, T B[3], T J[3])
+__device__ __forceinline__ void gatherg(const FieldView &f, T x, T y, T z, T B[3], T J[3], bool wj = true)
 {
-    if constexpr (RECT) gather_rect(f, x, y, z, B, J);
-    else gather(f, x, y, z, B, J);
+    if constexpr (RECT) gather_rect(f, x, y, z, B, J, wj);
+    else gather(f, x, y, z, B, J, wj);
 }
 
 // Box bounds in state coordinates: [0, n-1] cells; on a stretched grid the
@@ -465,12 +482,13 @@ __device__ __forceinline__ double state_of(const FieldView &f, double r, int a)
 }
 
 // Right-hand side in index space: out = {F (3), dl/dtau, dTw/dtau}.
-// Returns false on a null / non-finite field.
+// Returns false on a null / non-finite field. wj = false (a stage whose Tw
+// weight is zero): dTw/dtau = 0 without loading curl B.
 __device__ __forceinline__ bool rhs(const FieldView &f, const float invd[3], float sgn, float x, float y, float z,
-                                    float out[5])
+                                    float out[5], bool wj = true)
 {
     float B[3], J[3];
-    gather(f, x, y, z, B, J);
+    gather(f, x, y, z, B, J, wj);
     const float b0 = B[0] * invd[0], b1 = B[1] * invd[1], b2 = B[2] * invd[2];
     const float bb = b0 * b0 + b1 * b1 + b2 * b2;
     const float BB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
@@ -483,14 +501,15 @@ __device__ __forceinline__ bool rhs(const FieldView &f, const float invd[3], flo
     const float dl = sqrtf(BB) * inv;
     out[3] = dl;
     const float JB = J[0] * B[0] + J[1] * B[1] + J[2] * B[2];
-    out[4] = __fdividef(JB * dl, 12.566370614359172f * BB);
+    out[4] = wj ? __fdividef(JB * dl, 12.566370614359172f * BB) : 0.f;
     return true;
 }
 
 // FP64: bt_a = B_a / d_a, F = sigma bt / |bt|, dl/dtau = |B| / |bt|,
 // dTw/dtau = (J.B) / (4 pi B^2) dl/dtau, each as written.
+// (wj: accepted for the common interface; FP64 always forms dTw/dtau)
 __device__ __forceinline__ bool rhs(const FieldView &f, const double d[3], double sgn, double x, double y,
-                                    double z, double out[5])
+                                    double z, double out[5], bool wj = true)
 {
     double B[3], J[3];
     gather(f, x, y, z, B, J);
@@ -511,11 +530,11 @@ __device__ __forceinline__ bool rhs(const FieldView &f, const double d[3], doubl
 // Stretched grid: bt_a = B_a / D_a with the step's cell widths D, and the
 // physical velocity F = sigma B / |bt| (FP32: rw = 1/D).
 __device__ __forceinline__ bool rhs_rect(const FieldView &f, const float rw[3], float sgn, float x, float y, float z,
-                                         float out[5], const RectCells<float> *pre = nullptr)
+                                         float out[5], const RectCells<float> *pre = nullptr, bool wj = true)
 {
     float B[3], J[3];
-    if (pre) gather_rect_at(f, x, y, z, *pre, B, J);
-    else gather_rect(f, x, y, z, B, J);
+    if (pre) gather_rect_at(f, x, y, z, *pre, B, J, wj);
+    else gather_rect(f, x, y, z, B, J, wj);
     const float b0 = B[0] * rw[0], b1 = B[1] * rw[1], b2 = B[2] * rw[2];
     const float bb = b0 * b0 + b1 * b1 + b2 * b2;
     const float BB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
@@ -528,12 +547,13 @@ __device__ __forceinline__ bool rhs_rect(const FieldView &f, const float rw[3], 
     const float dl = sqrtf(BB) * inv;
     out[3] = dl;
     const float JB = J[0] * B[0] + J[1] * B[1] + J[2] * B[2];
-    out[4] = __fdividef(JB * dl, 12.566370614359172f * BB);
+    out[4] = wj ? __fdividef(JB * dl, 12.566370614359172f * BB) : 0.f;
     return true;
 }
 
 __device__ __forceinline__ bool rhs_rect(const FieldView &f, const double D[3], double sgn, double x, double y,
-                                         double z, double out[5], const RectCells<double> *pre = nullptr)
+                                         double z, double out[5], const RectCells<double> *pre = nullptr,
+                                         bool wj = true)
 {
     double B[3], J[3];
     if (pre) gather_rect_at(f, x, y, z, *pre, B, J);
@@ -555,10 +575,10 @@ __device__ __forceinline__ bool rhs_rect(const FieldView &f, const double D[3], 
 // pre (stretched grid): the point's cells, already searched
 template <bool RECT, typename T>
 __device__ __forceinline__ bool rhsg(const FieldView &f, const T dd[3], T sgn, T x, T y, T z, T out[5],
-                                     const RectCells<T> *pre = nullptr)
+                                     const RectCells<T> *pre = nullptr, bool wj = true)
 {
-    if constexpr (RECT) return rhs_rect(f, dd, sgn, x, y, z, out, pre);
-    else return rhs(f, dd, sgn, x, y, z, out);
+    if constexpr (RECT) return rhs_rect(f, dd, sgn, x, y, z, out, pre, wj);
+    else return rhs(f, dd, sgn, x, y, z, out, wj);
 }
 
 // ---------------------------------------------------------------------------
@@ -681,7 +701,7 @@ template <typename T, bool RECT = false>
 __device__ __forceinline__ bool unit_b(const FieldView &f, T x, T y, T z, T bh[3])
 {
     T B[3], J[3];
-    gatherg<RECT>(f, x, y, z, B, J);
+    gatherg<RECT>(f, x, y, z, B, J, false);
     const T m = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
     if (!(m > (T)0) || !(m < (T)INFINITY)) return false;
     bh[0] = B[0] / m;
@@ -816,7 +836,7 @@ template <typename T, bool RECT = false>
 __device__ __forceinline__ void b_at(const FieldView &f, double x, double y, double z, double B[3])
 {
     T Bt[3], Jt[3];
-    gatherg<RECT>(f, (T)x, (T)y, (T)z, Bt, Jt);
+    gatherg<RECT>(f, (T)x, (T)y, (T)z, Bt, Jt, false);
     B[0] = (double)Bt[0];
     B[1] = (double)Bt[1];
     B[2] = (double)Bt[2];
@@ -1168,7 +1188,7 @@ __device__ __forceinline__ bool start_line(const TraceArgs &A, const LineRecs &R
         bad = FQSL_LINE_OUTSIDE;
     } else {
         T J0[3], dd[3];
-        gatherg<RECT>(f, L.sx, L.sy, L.sz, B0, J0);
+        gatherg<RECT>(f, L.sx, L.sy, L.sz, B0, J0, false);
         step_dd<T, RECT>(f, L.sx, L.sy, L.sz, dd);
         T bb;
         if (kF64) {
@@ -1275,7 +1295,7 @@ __device__ __forceinline__ bool init_lattice(const TraceArgs &A, Lane<T> &L, lon
     const bool in = in_box<T, RECT>(f, xi);
     if (in) {
         T B0[3], J0[3];
-        gatherg<RECT>(f, (T)xi[0], (T)xi[1], (T)xi[2], B0, J0);
+        gatherg<RECT>(f, (T)xi[0], (T)xi[1], (T)xi[2], B0, J0, false);
         const T nB = sqrt(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
         if (nB > (T)0 && nB < (T)INFINITY) {
             const T bn = B0[0] * (T)G.n0[0] + B0[1] * (T)G.n0[1] + B0[2] * (T)G.n0[2];
@@ -1544,7 +1564,10 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
             py = L.y + hh * py;
             pz = L.z + hh * pz;
             T o[NS];
-            bool ok = rhsg<RECT>(f, dd, sgn, px, py, pz, o, (RECT && s == 0) ? &rc0 : nullptr);
+            // FP32: RKF45's stages 1 and 5 have zero 4th-order weight, so their
+            // Tw integrand is not formed (nor their curl B loaded)
+            const bool wj = kF64 || SCH != 0 || (s != 1 && s != 5);
+            bool ok = rhsg<RECT>(f, dd, sgn, px, py, pz, o, (RECT && s == 0) ? &rc0 : nullptr, wj);
             if constexpr (DEV != 0) {
                 // stage deviation vectors and Eq. rb2: dU/dtau = sigma (ds/dtau) (U . grad)(B/|B|)
                 T us[6];
@@ -1843,7 +1866,7 @@ __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
         bad = FQSL_LINE_OUTSIDE;
     } else {
         float B0[3], J0[3], rd[3];
-        gatherg<RECT>(f, x, y, z, B0, J0);
+        gatherg<RECT>(f, x, y, z, B0, J0, false);
         step_dd<float, RECT>(f, x, y, z, rd);
         const float b0 = B0[0] * rd[0], b1 = B0[1] * rd[1], b2 = B0[2] * rd[2];
         const float bb = b0 * b0 + b1 * b1 + b2 * b2;
@@ -1886,7 +1909,7 @@ __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
         float4 fu = make_float4(0.f, 0.f, 0.f, 0.f), fv = fu;
         if (!bad) {
             float B0[3], J0[3];
-            gatherg<RECT>(f, x, y, z, B0, J0);
+            gatherg<RECT>(f, x, y, z, B0, J0, false);
             const double b0 = B0[0], b1 = B0[1], b2 = B0[2];
             const double nB = sqrt(b0 * b0 + b1 * b1 + b2 * b2);
             const double bh[3] = {b0 / nB, b1 / nB, b2 / nB};
