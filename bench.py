@@ -874,7 +874,7 @@ def main():
         return
     # Method II (deviation vectors) on the same map, both ways of grad(B/|B|)
     fieldg = fq.Field(Bd, grid.origin, grid.spacing, pack=("f32", "gradb"))
-    m2 = {}
+    m2, leg_res = {}, {}
     for way, qperp in ((1, 0), (2, 0), (1, 1)):
         pm2 = fq.params(precision="f32", tol=TOL, method=2, gradb_way=way, qperp=qperp)
         fq.qmap_plane(fieldg, (0.0, 0.0, 0.0), u, v, NU, NV, pm2, out=out)
@@ -888,8 +888,11 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
             tms.append(e0.elapsed_time(e1))
-        m2["way%d" % way + ("_qperp" if qperp else "")] = {"value": n / (float(np.mean(tms)) / 1000.0),
-                                                          "unit": "Q+Tw values/s", "ms_per_step": float(np.mean(tms))}
+        key = "way%d" % way + ("_qperp" if qperp else "")
+        m2[key] = {"value": n / (float(np.mean(tms)) / 1000.0), "unit": "Q+Tw values/s",
+                   "ms_per_step": float(np.mean(tms))}
+        leg_res[("method2_f32", key)] = ({k: t.cpu().numpy() for k, t in out.items() if t is not None},
+                                        dict(method=2, way=way, qperp=qperp))
     fieldg.close()
     # the paper's fixed-step scheme on the same map: 3/8-rule RK4, step_perp = 3 cells (Table 1), Eq. step
     rk = {}
@@ -910,6 +913,8 @@ def main():
         rk[prec] = {"value": n / (float(np.mean(tms)) / 1000.0), "unit": "Q+Tw values/s",
                     "ms_per_step": float(np.mean(tms)),
                     "mean_trials_per_line": float(out["steps"].double().mean())}
+        leg_res[("fixed_step_rk38", prec)] = ({k: t.cpu().numpy() for k, t in out.items() if t is not None},
+                                             dict(scheme=1, step=3.0))
     step(pacc)
     torch.cuda.synchronize()
     msacc, kernacc = timed(pacc, args.steps)
@@ -1055,6 +1060,20 @@ def main():
         line["cpu_baseline"] = cb
         line["error_vs_oracle"] = {"f32": err_stats(res32, ref, sample), "f32_acc64": err_stats(resacc, ref, sample),
                                    "f64": err_stats(res64, ref, sample)}
+        # the Method II and fixed-step legs against the oracle on a seeded
+        # 4000-seed sample of the same lattice
+        import oracle
+
+        B64 = B.astype(np.float64)
+        Jo, Go = oracle.curl(B64, grid), oracle.gradb(B64, grid)
+        es = np.sort(np.random.default_rng(SEED + 7).choice(n, 4000, replace=False))
+        for (leg, key), (res, kw) in leg_res.items():
+            ref_l = oracle.plane(B64, grid, (0.0, 0.0, 0.0), u, v, NU, NV, oracle.params(tol=TOL, **kw), sample=es,
+                                 J=Jo, G=Go if kw.get("way") == 1 else None)
+            e = err_stats(res, ref_l, es)
+            e["bitwise"] = bool(all(np.array_equal(res[k][es], ref_l[k], equal_nan=True)
+                                    for k in ("Q", "Tw", "face1", "face2", "status")))
+            line[leg][key]["error_vs_oracle"] = e
     if rank == 0:
         print(json.dumps(line), flush=True)
     field32.close()

@@ -735,6 +735,13 @@ __device__ __forceinline__ bool grad_bhat(const FieldView &f, T eps, T x, T y, T
             }
             xp[a] += off;
             xm[a] -= off;
+            if constexpr (sizeof(T) == 4) {
+                // FP32: divide by the offset the rounded positions realise (their
+                // difference is exact); at x ~ 255 cells a float moves in steps
+                // of 1.5e-5 cells, 1.5 % of a 0.001-cell offset
+                const T h = xp[a] - xm[a];
+                span = RECT ? h : h * (T)f.d[a];
+            }
             T bp[3], bm[3];
             ok &= unit_b<T, RECT>(f, xp[0], xp[1], xp[2], bp);
             ok &= unit_b<T, RECT>(f, xm[0], xm[1], xm[2], bm);

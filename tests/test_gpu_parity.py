@@ -290,6 +290,30 @@ def test_method2_volume_fp64_bitwise(fq, oracle_lib, mono):
     assert_bitwise(g, r)
 
 
+@pytest.mark.parametrize("way,qperp", [(1, 0), (2, 0), (1, 1)], ids=["way1", "way2", "way1_qperp"])
+def test_method2_c2_full_size_sampled(fq, oracle_lib, way, qperp):
+    """Method II (and Q_perp) on the benchmark's full-size map (256x256x128
+    FP32 monopole cube, 1024x1024 seeds on z=0) in the launch the benchmark
+    times: FP64 bit-identical to the oracle on a seeded sample of seeds, each
+    recomputed on its own, and the FP32 error stated."""
+    B, grid, _ = synth.c2_monopole()
+    field = _field_m2(fq, B, grid)
+    n = 1024
+    args = ((0.0, 0.0, 0.0), (255.0 / n, 0, 0), (0, 255.0 / n, 0), n, n)
+    kw = dict(method=2, gradb_way=way, qperp=qperp)
+    g64 = _gpu_plane(fq, field, *args, precision="f64", **kw)
+    g32 = _gpu_plane(fq, field, *args, precision="f32", **kw)
+    sample = np.sort(np.random.default_rng(13 + way + 2 * qperp).choice(n * n, 1500, replace=False))
+    r = oracle.plane(B.astype(np.float64), grid, *args, oracle.params(method=2, way=way, qperp=qperp), sample=sample)
+    gs = {k: v[sample] for k, v in g64.items()}
+    assert_fp64_parity(gs, r)
+    assert_bitwise(gs, r)
+    g32s = {k: v[sample] for k, v in g32.items()}
+    assert np.mean(g32s["face2"] == r["face2"]) > 0.98
+    rel = q_rel(g32s, r)
+    assert np.median(rel[np.isfinite(rel)]) < 1e-3
+
+
 def test_method2_way1_needs_gradient_grid(fq):
     field = _field(fq, synth.analytic_cube("uniform"), G1)
     with pytest.raises(fq.FqslError) as ei:
