@@ -126,24 +126,26 @@ __device__ __forceinline__ float node_diff32(const float *__restrict__ B, int c,
     return (F(i + 1) - F(i - 1)) * rh2;
 }
 
+// Blocks take rows (j, k) of the cube, threads run along x: one division per
+// row instead of per node.
 __global__ void __launch_bounds__(256) k_curl_pack32(const float *__restrict__ B, int nx, int ny, int nz, float rx,
                                                      float ry, float rz, float4 *__restrict__ rec32)
 {
-    const long long total = (long long)nx * ny * nz;
+    const long long rows = (long long)ny * nz;
     const long long sy = nx, sz = (long long)nx * ny;
-    for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < total;
-         node += (long long)gridDim.x * blockDim.x) {
-        const long long i = node % nx;
-        const long long j = (node / nx) % ny;
-        const long long k = node / sz;
-        const float dyBz = node_diff32(B, 2, node, sy, j, ny, ry, 0.5f * ry);
-        const float dzBy = node_diff32(B, 1, node, sz, k, nz, rz, 0.5f * rz);
-        const float dzBx = node_diff32(B, 0, node, sz, k, nz, rz, 0.5f * rz);
-        const float dxBz = node_diff32(B, 2, node, 1, i, nx, rx, 0.5f * rx);
-        const float dxBy = node_diff32(B, 1, node, 1, i, nx, rx, 0.5f * rx);
-        const float dyBx = node_diff32(B, 0, node, sy, j, ny, ry, 0.5f * ry);
-        rec32[2 * node + 0] = make_float4(B[node * 3 + 0], B[node * 3 + 1], B[node * 3 + 2], dyBz - dzBy);
-        rec32[2 * node + 1] = make_float4(dzBx - dxBz, dxBy - dyBx, 0.f, 0.f);
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const long long j = row % ny, k = row / ny;
+        for (long long i = threadIdx.x; i < nx; i += blockDim.x) {
+            const long long node = row * nx + i;
+            const float dyBz = node_diff32(B, 2, node, sy, j, ny, ry, 0.5f * ry);
+            const float dzBy = node_diff32(B, 1, node, sz, k, nz, rz, 0.5f * rz);
+            const float dzBx = node_diff32(B, 0, node, sz, k, nz, rz, 0.5f * rz);
+            const float dxBz = node_diff32(B, 2, node, 1, i, nx, rx, 0.5f * rx);
+            const float dxBy = node_diff32(B, 1, node, 1, i, nx, rx, 0.5f * rx);
+            const float dyBx = node_diff32(B, 0, node, sy, j, ny, ry, 0.5f * ry);
+            rec32[2 * node + 0] = make_float4(B[node * 3 + 0], B[node * 3 + 1], B[node * 3 + 2], dyBz - dzBy);
+            rec32[2 * node + 1] = make_float4(dzBx - dxBz, dxBy - dyBx, 0.f, 0.f);
+        }
     }
 }
 
@@ -283,9 +285,13 @@ cudaError_t launch_curl_pack(const void *B, fqsl_dtype bt, const FieldView &g, v
     if (bt == FQSL_F32 && rec32) {
         // FP32 records from an FP32 cube: float stencils (the FP64 records, if
         // also wanted, come from the FP64 stencils below)
-        k_curl_pack32<<<(unsigned)blocks, 256, 0, s>>>((const float *)B, g.nx, g.ny, g.nz, (float)(1.0 / g.d[0]),
-                                                       (float)(1.0 / g.d[1]), (float)(1.0 / g.d[2]),
-                                                       (float4 *)rec32);
+        // a row per block: threads = nx rounded up to whole warps (at most 256)
+        const long long rows = (long long)g.ny * g.nz;
+        const int tpb = g.nx >= 256 ? 256 : ((g.nx + 31) / 32) * 32;
+        const long long rcap = (long long)sms * (2048 / tpb);
+        const unsigned rb = (unsigned)(rows < rcap ? rows : rcap);
+        k_curl_pack32<<<rb, tpb, 0, s>>>((const float *)B, g.nx, g.ny, g.nz, (float)(1.0 / g.d[0]),
+                                         (float)(1.0 / g.d[1]), (float)(1.0 / g.d[2]), (float4 *)rec32);
         if (rec64)
             k_curl_pack<float><<<(unsigned)blocks, 256, 0, s>>>((const float *)B, g.nx, g.ny, g.nz, g.d[0], g.d[1],
                                                                g.d[2], nullptr, (double2 *)rec64);
