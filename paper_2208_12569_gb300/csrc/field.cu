@@ -116,36 +116,35 @@ __global__ void __launch_bounds__(256) k_curl_pack_rect(const TI *__restrict__ B
 
 // FP32 records only: the same stencils in float with reciprocal spacings (the
 // FP64 kernel above is the one whose rounding matches a plain evaluation).
-__device__ __forceinline__ float node_diff32(const float *__restrict__ B, int c, long long node, long long stride,
-                                             long long i, long long n, float rh, float rh2)
+__device__ __forceinline__ float node_diff32(const float *__restrict__ B, int c, unsigned node, unsigned stride,
+                                             unsigned i, unsigned n, float rh, float rh2)
 {
-    auto F = [&](long long kk) -> float { return B[(node + (kk - i) * stride) * 3 + c]; };
+    auto F = [&](unsigned kk) -> float { return B[(size_t)(node + kk * stride - i * stride) * 3 + c]; };
     if (n == 2) return (F(1) - F(0)) * rh;
     if (i == 0) return (-3.f * F(0) + 4.f * F(1) - F(2)) * rh2;
     if (i == n - 1) return (3.f * F(n - 1) - 4.f * F(n - 2) + F(n - 3)) * rh2;
     return (F(i + 1) - F(i - 1)) * rh2;
 }
 
-// Blocks take rows (j, k) of the cube, threads run along x: one division per
-// row instead of per node.
+// 32-bit index arithmetic (a cube with FP32 records holds fewer than 2^31 nodes)
 __global__ void __launch_bounds__(256) k_curl_pack32(const float *__restrict__ B, int nx, int ny, int nz, float rx,
                                                      float ry, float rz, float4 *__restrict__ rec32)
 {
-    const long long rows = (long long)ny * nz;
-    const long long sy = nx, sz = (long long)nx * ny;
-    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-        const long long j = row % ny, k = row / ny;
-        for (long long i = threadIdx.x; i < nx; i += blockDim.x) {
-            const long long node = row * nx + i;
-            const float dyBz = node_diff32(B, 2, node, sy, j, ny, ry, 0.5f * ry);
-            const float dzBy = node_diff32(B, 1, node, sz, k, nz, rz, 0.5f * rz);
-            const float dzBx = node_diff32(B, 0, node, sz, k, nz, rz, 0.5f * rz);
-            const float dxBz = node_diff32(B, 2, node, 1, i, nx, rx, 0.5f * rx);
-            const float dxBy = node_diff32(B, 1, node, 1, i, nx, rx, 0.5f * rx);
-            const float dyBx = node_diff32(B, 0, node, sy, j, ny, ry, 0.5f * ry);
-            rec32[2 * node + 0] = make_float4(B[node * 3 + 0], B[node * 3 + 1], B[node * 3 + 2], dyBz - dzBy);
-            rec32[2 * node + 1] = make_float4(dzBx - dxBz, dxBy - dyBx, 0.f, 0.f);
-        }
+    const unsigned total = (unsigned)nx * (unsigned)ny * (unsigned)nz;
+    const unsigned sy = (unsigned)nx, sz = (unsigned)nx * (unsigned)ny;
+    for (unsigned node = blockIdx.x * blockDim.x + threadIdx.x; node < total; node += gridDim.x * blockDim.x) {
+        const unsigned t = node / sy;
+        const unsigned i = node - t * sy;
+        const unsigned k = t / (unsigned)ny;
+        const unsigned j = t - k * (unsigned)ny;
+        const float dyBz = node_diff32(B, 2, node, sy, j, ny, ry, 0.5f * ry);
+        const float dzBy = node_diff32(B, 1, node, sz, k, nz, rz, 0.5f * rz);
+        const float dzBx = node_diff32(B, 0, node, sz, k, nz, rz, 0.5f * rz);
+        const float dxBz = node_diff32(B, 2, node, 1, i, nx, rx, 0.5f * rx);
+        const float dxBy = node_diff32(B, 1, node, 1, i, nx, rx, 0.5f * rx);
+        const float dyBx = node_diff32(B, 0, node, sy, j, ny, ry, 0.5f * ry);
+        rec32[2 * (size_t)node + 0] = make_float4(B[(size_t)node * 3 + 0], B[(size_t)node * 3 + 1], B[(size_t)node * 3 + 2], dyBz - dzBy);
+        rec32[2 * (size_t)node + 1] = make_float4(dzBx - dxBz, dxBy - dyBx, 0.f, 0.f);
     }
 }
 
@@ -285,13 +284,9 @@ cudaError_t launch_curl_pack(const void *B, fqsl_dtype bt, const FieldView &g, v
     if (bt == FQSL_F32 && rec32) {
         // FP32 records from an FP32 cube: float stencils (the FP64 records, if
         // also wanted, come from the FP64 stencils below)
-        // a row per block: threads = nx rounded up to whole warps (at most 256)
-        const long long rows = (long long)g.ny * g.nz;
-        const int tpb = g.nx >= 256 ? 256 : ((g.nx + 31) / 32) * 32;
-        const long long rcap = (long long)sms * (2048 / tpb);
-        const unsigned rb = (unsigned)(rows < rcap ? rows : rcap);
-        k_curl_pack32<<<rb, tpb, 0, s>>>((const float *)B, g.nx, g.ny, g.nz, (float)(1.0 / g.d[0]),
-                                         (float)(1.0 / g.d[1]), (float)(1.0 / g.d[2]), (float4 *)rec32);
+        k_curl_pack32<<<(unsigned)blocks, 256, 0, s>>>((const float *)B, g.nx, g.ny, g.nz, (float)(1.0 / g.d[0]),
+                                                       (float)(1.0 / g.d[1]), (float)(1.0 / g.d[2]),
+                                                       (float4 *)rec32);
         if (rec64)
             k_curl_pack<float><<<(unsigned)blocks, 256, 0, s>>>((const float *)B, g.nx, g.ny, g.nz, g.d[0], g.d[1],
                                                                g.d[2], nullptr, (double2 *)rec64);

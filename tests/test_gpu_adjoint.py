@@ -581,3 +581,54 @@ def test_fixed_step_full_size_workload_sampled(fq):
     g32, _ = _gpu_vjp(fq, field, plane, WQ, WT, dtype=torch.float32, precision="f32", scheme=1)
     # (measured 1.0e-4 on the benchmark's 64-seed sample)
     assert _rel(g32, ref) < 2e-3
+
+
+@pytest.mark.parametrize("scheme", [0, 1], ids=["rkf45", "fixed_step"])
+def test_gradient_matches_central_differences_of_gpu_maps(fq, small, scheme):
+    # The FP64 GPU gradient of the loss against central differences of the
+    # GPU's own FP64 maps, each a free re-trace (steps chosen afresh), over the
+    # unperturbed map's usable seeds. Tight tolerance / small step, where the
+    # frozen step sequence moves the map by much less than the differences
+    # resolve (the bounds of the oracle's own finite-difference pins).
+    B, Bt, grid = small
+    plane = ((0.0, 0.0, 0.0), (23.0 / 8, 0.0, 0.0), (0.0, 23.0 / 8, 0.0), 8, 8)
+    kw = dict(precision="f64", tol=1e-8, max_steps=10 ** 6)
+    if scheme:
+        kw.update(scheme=1, step=0.3, step_min=0.05)
+    ft = _field(fq, Bt, grid)
+    tgt = {k: v.cpu().numpy() for k, v in fq.qmap_plane(ft, *plane, fq.params(**kw)).items() if v is not None}
+    field = _field(fq, B, grid)
+    out = fq.qmap_plane(field, *plane, fq.params(tape=1, **kw))
+    Q, Tw, st = (out[k].cpu().numpy() for k in ("Q", "Tw", "status"))
+    use = (np.isfinite(Q) & np.isfinite(tgt["Q"]) & (Q > 0) & (tgt["Q"] > 0) & np.isfinite(Tw)
+           & np.isfinite(tgt["Tw"]) & ((st & (oracle.BAD | oracle.MIXED)) == 0))
+    nuse = int(use.sum())
+    assert nuse > 40
+    r = np.log10(np.where(use, Q, 1.0)) - np.log10(np.where(use, tgt["Q"], 1.0))
+    dQ = np.where(use, 2.0 * r / (np.where(use, Q, 1.0) * math.log(10.0) * nuse), 0.0)
+    dTw = np.where(use, 0.2 * (Tw - tgt["Tw"]) / nuse, 0.0)
+    g = fq.backward(field, torch.from_numpy(dQ).cuda(), torch.from_numpy(dTw).cuda(), dtype=torch.float64)
+    field.check()
+    g = g.cpu().numpy().ravel()
+
+    def loss(Bx):
+        field.update(torch.from_numpy(Bx).cuda())
+        o = fq.qmap_plane(field, *plane, fq.params(**kw))
+        q, tw = o["Q"].cpu().numpy()[use], o["Tw"].cpu().numpy()[use]
+        lq = np.log10(q) - np.log10(tgt["Q"][use])
+        return float(np.sum(lq * lq + 0.1 * (tw - tgt["Tw"][use]) ** 2) / nuse)
+
+    flat = np.abs(g)
+    cand = np.nonzero(flat > 1e-2 * flat.max())[0]
+    pick = np.random.default_rng(31).choice(cand, min(48, len(cand)), replace=False)
+    eps = 1e-3 * float(np.sqrt(np.mean(B * B)))
+    err = []
+    for k in pick:
+        Bp = B.copy().ravel()
+        Bm = B.copy().ravel()
+        Bp[k] += eps
+        Bm[k] -= eps
+        err.append((loss(Bp.reshape(B.shape)) - loss(Bm.reshape(B.shape))) / (2 * eps) - g[k])
+    err = np.abs(np.array(err))
+    assert err.max() < 1e-2 * flat.max()
+    assert np.median(err / flat[pick]) < 1e-2
