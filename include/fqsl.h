@@ -125,7 +125,7 @@ typedef struct {
                              rotated seeds, their extra lines, Method II lines and seed lists step `step`.
                              A grazing exit halves the step for the rest of the direction (down to h_min).
                              On a stretched grid the step is in cells of each trial's start cell.
-                             No batches (FQSL_ERR_UNSUPPORTED). With tape = 1 (uniform grids) the tape
+                             Batches take it (all entries step with it). With tape = 1 (uniform grids) the tape
                              holds every step taken, grazing halvings included, and fqsl_backward
                              reverses the 3/8 rule's four stages */
     double step;          /* scheme 1: step_perp in cells, default 3.0 (Method I in the paper's Table 1) */

@@ -1330,7 +1330,6 @@ extern "C" fqsl_status fqsl_batch_create(const fqsl_field *fields, const fqsl_pl
     if (!fields || !planes || !outs || n < 1) return fail(FQSL_ERR_ARG, "%s: need n >= 1 fields, planes, outs", who);
     if (!p) return fail(FQSL_ERR_ARG, "%s: NULL params", who);
     if (p->method != 1) return fail(FQSL_ERR_UNSUPPORTED, "%s: batches run Method I", who);
-    if (p->scheme != 0) return fail(FQSL_ERR_UNSUPPORTED, "%s: batches run RKF45", who);
     const bool f32 = p->precision != FQSL_F64;
     std::vector<Lattice> lats(n);
     std::vector<size_t> off(n);
@@ -1438,8 +1437,8 @@ extern "C" fqsl_status fqsl_batch_create(const fqsl_field *fields, const fqsl_pl
         batch_free(b);
         return cuda_fail(e, who);
     }
-    const int bps = p->precision == FQSL_F64 ? batch_trace_blocks_per_sm_f64()
-                                             : batch_trace_blocks_per_sm_f32(p->precision == FQSL_F32_ACC64);
+    const int bps = p->precision == FQSL_F64 ? batch_trace_blocks_per_sm_f64(p->scheme)
+                                             : batch_trace_blocks_per_sm_f32(p->precision == FQSL_F32_ACC64, p->scheme);
     b->grid = b->sms * (p->blocks_per_sm > 0 && p->blocks_per_sm < bps ? p->blocks_per_sm : bps);
     *out = b;
     return FQSL_OK;

@@ -300,8 +300,14 @@ cudaError_t launch_batch_extra_prefix(const unsigned *rot_counts, int nent, long
 cudaError_t launch_batch_trace_f32(const TraceArgs &a0, const BatchArgs &b, int src, bool acc64, int grid,
                                    cudaStream_t s);
 cudaError_t launch_batch_trace_f64(const TraceArgs &a0, const BatchArgs &b, int src, int grid, cudaStream_t s);
-int batch_trace_blocks_per_sm_f32(bool acc64);
-int batch_trace_blocks_per_sm_f64();
+int batch_trace_blocks_per_sm_f32(bool acc64, int scheme);
+int batch_trace_blocks_per_sm_f64(int scheme);
+// the same with the fixed-step scheme (trace_rk38_f32.cu, trace_rk38_f64.cu)
+cudaError_t launch_batch_trace_rk38_f32(const TraceArgs &a0, const BatchArgs &b, int src, bool acc64, int grid,
+                                        cudaStream_t s);
+cudaError_t launch_batch_trace_rk38_f64(const TraceArgs &a0, const BatchArgs &b, int src, int grid, cudaStream_t s);
+int batch_trace_rk38_blocks_per_sm_f32(bool acc64);
+int batch_trace_rk38_blocks_per_sm_f64();
 cudaError_t launch_batch_assemble_f32(const AssembleArgs *desc, const long long *nbase, int nent, long long total,
                                       cudaStream_t s);
 cudaError_t launch_batch_assemble_f64(const AssembleArgs *desc, const long long *nbase, int nent, long long total,

@@ -1426,7 +1426,6 @@ template <typename T, int SRC, bool ACC, int DEV = 0, bool BATCH = false, bool T
 __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs &BA)
 {
     static_assert(!(RECT && TAPE), "stretched grids: no tape");
-    static_assert(!(SCH && BATCH), "fixed-step scheme: no batches");
     constexpr bool SPLIT = TAPE && SRC == kSrcLattice;
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;

@@ -176,6 +176,7 @@ cudaError_t launch_batch_extra_prefix(const unsigned *rot_counts, int nent, long
 cudaError_t launch_batch_trace_f32(const TraceArgs &a0, const BatchArgs &b, int src, bool acc64, int grid,
                                    cudaStream_t s)
 {
+    if (a0.p.scheme == 1) return launch_batch_trace_rk38_f32(a0, b, src, acc64, grid, s);
     if (src == kSrcLattice) {
         if (acc64) k_batch_trace_f32<kSrcLattice, true><<<grid, kBlock, 0, s>>>(a0, b);
         else k_batch_trace_f32<kSrcLattice, false><<<grid, kBlock, 0, s>>>(a0, b);
@@ -186,8 +187,9 @@ cudaError_t launch_batch_trace_f32(const TraceArgs &a0, const BatchArgs &b, int 
     return cudaGetLastError();
 }
 
-int batch_trace_blocks_per_sm_f32(bool acc64)
+int batch_trace_blocks_per_sm_f32(bool acc64, int scheme)
 {
+    if (scheme == 1) return batch_trace_rk38_blocks_per_sm_f32(acc64);
     int b = 0;
     if (acc64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_trace_f32<kSrcLattice, true>, kBlock, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_trace_f32<kSrcLattice, false>, kBlock, 0);

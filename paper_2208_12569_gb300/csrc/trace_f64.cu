@@ -76,13 +76,15 @@ __global__ void __launch_bounds__(kBlock) k_batch_trace_f64(const TraceArgs A0, 
 
 cudaError_t launch_batch_trace_f64(const TraceArgs &a0, const BatchArgs &b, int src, int grid, cudaStream_t s)
 {
+    if (a0.p.scheme == 1) return launch_batch_trace_rk38_f64(a0, b, src, grid, s);
     if (src == kSrcLattice) k_batch_trace_f64<kSrcLattice><<<grid, kBlock, 0, s>>>(a0, b);
     else k_batch_trace_f64<kSrcExtra><<<grid, kBlock, 0, s>>>(a0, b);
     return cudaGetLastError();
 }
 
-int batch_trace_blocks_per_sm_f64()
+int batch_trace_blocks_per_sm_f64(int scheme)
 {
+    if (scheme == 1) return batch_trace_rk38_blocks_per_sm_f64();
     int b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_trace_f64<kSrcLattice>, kBlock, 0);
     return b > 0 ? b : 1;

@@ -26,6 +26,14 @@ __global__ void __launch_bounds__(kBlock) k_trace_dev_rk38_f32(const TraceArgs A
     trace::trace_body<float, kSrcLattice, false, WAY, false, false, false, 1>(A, BatchArgs{});
 }
 
+// batches: many (field, plane) entries in one launch
+template <int SRC, bool ACC>
+__global__ void __launch_bounds__(kBlock, FQSL_TRACE_F32_MINB) k_batch_trace_rk38_f32(const TraceArgs A0,
+                                                                                      const BatchArgs B)
+{
+    trace::trace_body<float, SRC, ACC, 0, true, false, false, 1>(A0, B);
+}
+
 // the adjoint's forward pass: lattice or extra lines writing the step tape
 template <int SRC, bool ACC>
 __global__ void __launch_bounds__(kBlock, FQSL_TRACE_F32_MINB) k_trace_tape_rk38_f32(const TraceArgs A)
@@ -63,6 +71,27 @@ cudaError_t launch_trace_rk38_f32(const TraceArgs &a, int src, int grid, cudaStr
 }
 
 int trace_rk38_blocks_per_sm_f32(int src, bool acc64) { return acc64 ? blocks<true>(src) : blocks<false>(src); }
+
+cudaError_t launch_batch_trace_rk38_f32(const TraceArgs &a0, const BatchArgs &b, int src, bool acc64, int grid,
+                                        cudaStream_t s)
+{
+    if (src == kSrcLattice) {
+        if (acc64) k_batch_trace_rk38_f32<kSrcLattice, true><<<grid, kBlock, 0, s>>>(a0, b);
+        else k_batch_trace_rk38_f32<kSrcLattice, false><<<grid, kBlock, 0, s>>>(a0, b);
+    } else {
+        if (acc64) k_batch_trace_rk38_f32<kSrcExtra, true><<<grid, kBlock, 0, s>>>(a0, b);
+        else k_batch_trace_rk38_f32<kSrcExtra, false><<<grid, kBlock, 0, s>>>(a0, b);
+    }
+    return cudaGetLastError();
+}
+
+int batch_trace_rk38_blocks_per_sm_f32(bool acc64)
+{
+    int b = 0;
+    if (acc64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_trace_rk38_f32<kSrcLattice, true>, kBlock, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_trace_rk38_f32<kSrcLattice, false>, kBlock, 0);
+    return b > 0 ? b : 1;
+}
 
 cudaError_t launch_trace_tape_rk38_f32(const TraceArgs &a, int src, int grid, cudaStream_t s, bool acc64)
 {

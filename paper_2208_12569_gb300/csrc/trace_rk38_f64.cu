@@ -20,6 +20,13 @@ __global__ void __launch_bounds__(kBlock) k_trace_dev_rk38_f64(const TraceArgs A
     trace::trace_body<double, kSrcLattice, true, WAY, false, false, false, 1>(A, BatchArgs{});
 }
 
+// batches: many (field, plane) entries in one launch
+template <int SRC>
+__global__ void __launch_bounds__(kBlock) k_batch_trace_rk38_f64(const TraceArgs A0, const BatchArgs B)
+{
+    trace::trace_body<double, SRC, true, 0, true, false, false, 1>(A0, B);
+}
+
 // the adjoint's forward pass: lattice or extra lines writing the step tape
 template <int SRC>
 __global__ void __launch_bounds__(kBlock) k_trace_tape_rk38_f64(const TraceArgs A)
@@ -27,6 +34,20 @@ __global__ void __launch_bounds__(kBlock) k_trace_tape_rk38_f64(const TraceArgs 
     trace::trace_body<double, SRC, true, 0, false, true, false, 1>(A, BatchArgs{});
 }
 }  // namespace
+
+cudaError_t launch_batch_trace_rk38_f64(const TraceArgs &a0, const BatchArgs &b, int src, int grid, cudaStream_t s)
+{
+    if (src == kSrcLattice) k_batch_trace_rk38_f64<kSrcLattice><<<grid, kBlock, 0, s>>>(a0, b);
+    else k_batch_trace_rk38_f64<kSrcExtra><<<grid, kBlock, 0, s>>>(a0, b);
+    return cudaGetLastError();
+}
+
+int batch_trace_rk38_blocks_per_sm_f64()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_trace_rk38_f64<kSrcLattice>, kBlock, 0);
+    return b > 0 ? b : 1;
+}
 
 cudaError_t launch_trace_tape_rk38_f64(const TraceArgs &a, int src, int grid, cudaStream_t s)
 {

@@ -1,7 +1,7 @@
 """Batches (one set of launches over many cubes and planes of uneven sizes):
 every entry equals the single-plane entry point's result bit for bit, in both
-precisions, including interior planes that rotate S0; a captured CUDA graph
-replays to the same results."""
+precisions and with both integration schemes, including interior planes that
+rotate S0; a captured CUDA graph replays to the same results."""
 import numpy as np
 import pytest
 
@@ -36,10 +36,12 @@ def setup():
     return fq, fields, planes
 
 
+@pytest.mark.parametrize("scheme", [0, 1], ids=["rkf45", "fixed_step"])
 @pytest.mark.parametrize("precision", ["f64", "f32"])
-def test_batch_equals_single_entries(setup, precision):
+def test_batch_equals_single_entries(setup, precision, scheme):
+    # (scheme 1: the fixed-step 3/8 rule with Eq. step's per-line step, Sec. 2.3)
     fq, fields, planes = setup
-    p = fq.params(precision=precision)
+    p = fq.params(precision=precision, scheme=scheme)
     batch = fq.Batch(fields, planes, p)
     outs = [to_np(o) for o in batch.run()]
     torch.cuda.synchronize()

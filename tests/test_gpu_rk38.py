@@ -142,9 +142,6 @@ def test_argument_errors(fq, mono):
         with pytest.raises(fq.FqslError) as ei:
             fq.qmap_plane(field, *args, fq.params(**kw))
         assert ei.value.status == status, kw
-    with pytest.raises(fq.FqslError) as ei:
-        fq.Batch([field], [dict(origin=args[0], u=args[1], v=args[2], nu=4, nv=4)], fq.params(scheme=1))
-    assert ei.value.status == 5
 
 
 def test_edge_cases_bitwise(fq, oracle_lib):
