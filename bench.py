@@ -53,7 +53,7 @@ NUM_SMS = 152
 # the ncu capture summarised in profiles/trace_f32_c2_monopole_1024x1024.md,
 # valid while the tracer sources hash to TRACE_F32_SRC_HASH.
 TRACE_F32_DRAM_BYTES = 308.370176e6 + 59.896576e6
-TRACE_F32_SRC_HASH = "fccb136bd7e2ec42"
+TRACE_F32_SRC_HASH = "0b43cd71e2326598"
 
 
 def _trace_src_hash():

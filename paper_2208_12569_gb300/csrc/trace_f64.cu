@@ -7,7 +7,7 @@ namespace {
 constexpr int kBlock = 128;
 
 template <int SRC>
-__global__ void __launch_bounds__(kBlock) k_trace_f64(const TraceArgs A)
+__global__ void __launch_bounds__(kBlock, FQSL_TRACE_F64_MINB) k_trace_f64(const TraceArgs A)
 {
     trace::trace_body<double, SRC, true>(A, BatchArgs{});
 }
@@ -68,7 +68,7 @@ int trace_dev_blocks_per_sm_f64(int way)
 namespace fqsl {
 namespace {
 template <int SRC>
-__global__ void __launch_bounds__(kBlock) k_batch_trace_f64(const TraceArgs A0, const BatchArgs B)
+__global__ void __launch_bounds__(kBlock, FQSL_TRACE_F64_MINB) k_batch_trace_f64(const TraceArgs A0, const BatchArgs B)
 {
     trace::trace_body<double, SRC, true, 0, true>(A0, B);
 }
@@ -95,7 +95,7 @@ namespace fqsl {
 namespace {
 // adjoint forward pass: the tracers that also write the step tape
 template <int SRC>
-__global__ void __launch_bounds__(kBlock) k_trace_tape_f64(const TraceArgs A)
+__global__ void __launch_bounds__(kBlock, FQSL_TRACE_F64_MINB) k_trace_tape_f64(const TraceArgs A)
 {
     trace::trace_body<double, SRC, true, 0, false, true>(A, BatchArgs{});
 }

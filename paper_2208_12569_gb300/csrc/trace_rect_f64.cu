@@ -10,7 +10,7 @@ namespace {
 constexpr int kBlock = 128;
 
 template <int SRC>
-__global__ void __launch_bounds__(kBlock) k_trace_rect_f64(const TraceArgs A)
+__global__ void __launch_bounds__(kBlock, FQSL_TRACE_F64_MINB) k_trace_rect_f64(const TraceArgs A)
 {
     trace::trace_body<double, SRC, true, 0, false, false, true>(A, BatchArgs{});
 }
