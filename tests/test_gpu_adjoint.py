@@ -380,16 +380,18 @@ def test_taped_map_equals_plain_map(fq, small, precision, plane):
         np.testing.assert_allclose(taped["Tw"], plain["Tw"], rtol=1e-5, atol=1e-7)
 
 
-def test_volume_gradient_matches_oracle(fq, small):
+@pytest.mark.parametrize("scheme", [0, 1], ids=["rkf45", "fixed_step"])
+def test_volume_gradient_matches_oracle(fq, small, scheme):
     # a volume map: each z-layer is its own S0, so its adjoint is the sum of
-    # the layers' plane adjoints
+    # the layers' plane adjoints (scheme 1: the 3/8 rule with Eq. step)
     B, _, grid = small
     field = _field(fq, B, grid)
     step = (23.0 / 6, 23.0 / 6, 4.0)
     nx, ny, nz = 6, 6, 3
     m = nx * ny * nz
     wq, wt = _weights(21, m)
-    out = fq.qmap_volume(field, (0.0, 0.0, 0.0), step, nx, ny, nz, fq.params(precision="f64", tape=1))
+    kw = dict(scheme=1, step=0.3, step_min=0.05, max_steps=10 ** 6) if scheme else {}
+    out = fq.qmap_volume(field, (0.0, 0.0, 0.0), step, nx, ny, nz, fq.params(precision="f64", tape=1, **kw))
     st = out["status"].cpu().numpy()
     dB = fq.backward(field, torch.from_numpy(wq).cuda(), torch.from_numpy(wt).cuda(), dtype=torch.float64)
     field.check()
@@ -398,7 +400,8 @@ def test_volume_gradient_matches_oracle(fq, small):
     per = nx * ny
     for k in range(nz):
         plane = ((0.0, 0.0, (k + 0.5) * step[2]), (step[0], 0.0, 0.0), (0.0, step[1], 0.0), nx, ny)
-        r, log = adj.vjp(B, grid, *plane, wq[k * per:(k + 1) * per], wt[k * per:(k + 1) * per], oracle.params())
+        r, log = adj.vjp(B, grid, *plane, wq[k * per:(k + 1) * per], wt[k * per:(k + 1) * per],
+                         oracle.params(**kw))
         line_bits = oracle.BAD | oracle.ROTATED | oracle.CHORD | oracle.STALL
         assert np.array_equal(log["status"] & line_bits, st[k * per:(k + 1) * per] & line_bits)
         ref += r
