@@ -66,7 +66,8 @@ def lib():
             P = C.c_void_p
             for name in ("oracle_curl", "oracle_gradb", "oracle_interp", "oracle_qmap", "oracle_twist",
                          "oracle_trace", "oracle_max_threads", "oracle_curl_rect", "oracle_qmap_rect",
-                         "oracle_twist_rect", "oracle_interp_rect", "oracle_cell_rect", "oracle_gradb_rect"):
+                         "oracle_twist_rect", "oracle_interp_rect", "oracle_cell_rect", "oracle_gradb_rect",
+                         "oracle_lattice_log_rect"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib

@@ -27,7 +27,7 @@ import math
 import numpy as np
 import torch
 
-from . import BAD, ROTATED, _f64, _grid_args, _p, curl, lib, params, plane
+from . import BAD, ROTATED, _coords, _f64, _grid_args, _p, curl, is_rect, lib, params, plane
 
 # Fehlberg 4(5) stage matrix and 4th-order weights (the propagated solution)
 _A = [[], [1 / 4], [3 / 32, 9 / 32], [1932 / 2197, -7200 / 2197, 7296 / 2197],
@@ -50,7 +50,6 @@ def lattice_log(B, grid, origin, u, v, nu, nv, p=None, cap=8192, J=None, which=N
     p = p or params()
     B = _f64(B)
     J = _f64(curl(B, grid) if J is None else J)
-    n, o, d = _grid_args(grid)
     wh = None if which is None else np.ascontiguousarray(which, dtype=np.int64)
     m = nu * nv if wh is None else len(wh)
     out = dict(h=np.zeros((m, cap)), code=np.zeros((m, cap), np.int32), n=np.zeros(m, np.int32),
@@ -64,12 +63,18 @@ def lattice_log(B, grid, origin, u, v, nu, nv, p=None, cap=8192, J=None, which=N
     a1, a2 = np.array(u, float), np.array(v, float)
     ln = np.array([nu, nv], np.int64)
     L = lib()
-    L.oracle_lattice_log.restype = C.c_int
-    rc = L.oracle_lattice_log(_p(B), _p(J), _p(n), _p(o), _p(d), _p(lo), _p(a1), _p(a2), _p(ln), C.byref(p),
-                              C.c_int(cap), _p(out["h"]), _p(out["code"]), _p(out["n"]), _p(out["s0"]),
-                              _p(out["tol"]), _p(out["bn0"]), _p(out["ends"]), _p(out["faces"]),
-                              _p(out["status"]), _p(wh), C.c_longlong(0 if wh is None else len(wh)),
-                              X("xh"), X("xcode"), X("xn"), X("xs0"), X("xfaces"), X("xstatus"))
+    tail = (_p(lo), _p(a1), _p(a2), _p(ln), C.byref(p), C.c_int(cap), _p(out["h"]), _p(out["code"]), _p(out["n"]),
+            _p(out["s0"]), _p(out["tol"]), _p(out["bn0"]), _p(out["ends"]), _p(out["faces"]), _p(out["status"]),
+            _p(wh), C.c_longlong(0 if wh is None else len(wh)),
+            X("xh"), X("xcode"), X("xn"), X("xs0"), X("xfaces"), X("xstatus"))
+    if is_rect(grid):
+        # stretched grid (reading R16): the recorded ends are physical positions
+        n = np.array(grid.n, dtype=np.int64)
+        rc = L.oracle_lattice_log_rect(_p(B), _p(J), _p(n), _p(_coords(grid)), *tail)
+    else:
+        n, o, d = _grid_args(grid)
+        L.oracle_lattice_log.restype = C.c_int
+        rc = L.oracle_lattice_log(_p(B), _p(J), _p(n), _p(o), _p(d), *tail)
     if rc:
         raise ValueError("oracle_lattice_log: error %d" % rc)
     if np.any(out["n"] < 0) or (extra and np.any(out["xn"] < 0)):
@@ -102,6 +107,44 @@ def curl_t(B, spacing):
     return torch.stack([Jx, Jy, Jz], dim=-1)
 
 
+def _deriv_rect(f, dim, X):
+    """d f/d x along tensor dim with node coordinates X (reading R16): the
+    derivative of the quadratic through three neighbouring nodes, one-sided at
+    the ends, first order on an axis of 2 nodes."""
+    X = np.asarray(X, dtype=np.float64)
+    n = f.shape[dim]
+    s = lambda a, b: f.narrow(dim, a, b - a)  # noqa: E731
+
+    def col(v):
+        shape = [1] * f.dim()
+        shape[dim] = -1
+        return torch.as_tensor(np.atleast_1d(v), dtype=torch.float64).reshape(shape)
+    if n == 2:
+        g = (s(1, 2) - s(0, 1)) / float(X[1] - X[0])
+        return torch.cat([g, g], dim=dim)
+    h1, h2 = X[1] - X[0], X[2] - X[1]
+    first = (-(2.0 * h1 + h2) / (h1 * (h1 + h2)) * s(0, 1) + (h1 + h2) / (h1 * h2) * s(1, 2)
+             - h1 / (h2 * (h1 + h2)) * s(2, 3))
+    a, b = X[1:-1] - X[:-2], X[2:] - X[1:-1]
+    mid = (col(-b / (a * (a + b))) * s(0, n - 2) + col((b - a) / (a * b)) * s(1, n - 1)
+           + col(a / (b * (a + b))) * s(2, n))
+    h1, h2 = X[n - 2] - X[n - 3], X[n - 1] - X[n - 2]
+    last = (h2 / (h1 * (h1 + h2)) * s(n - 3, n - 2) - (h1 + h2) / (h1 * h2) * s(n - 2, n - 1)
+            + (h1 + 2.0 * h2) / (h2 * (h1 + h2)) * s(n - 1, n))
+    return torch.cat([first, mid, last], dim=dim)
+
+
+def curl_t_rect(B, coords):
+    """curl B at the nodes of a stretched grid (B of shape (nz, ny, nx, 3)), with
+    the three-point stencils of a non-uniform axis, in torch."""
+    xs, ys, zs = coords
+    Bx, By, Bz = B[..., 0], B[..., 1], B[..., 2]
+    Jx = _deriv_rect(Bz, 1, ys) - _deriv_rect(By, 0, zs)
+    Jy = _deriv_rect(Bx, 0, zs) - _deriv_rect(Bz, 2, xs)
+    Jz = _deriv_rect(By, 2, xs) - _deriv_rect(Bx, 1, ys)
+    return torch.stack([Jx, Jy, Jz], dim=-1)
+
+
 class _Field:
     """B and curl B node values flattened to (nodes, 6), and trilinear
     interpolation at index positions (Sec. 2.2): the cell is the floor of the
@@ -115,6 +158,11 @@ class _Field:
         self.cmax = torch.tensor([n[0] - 2, n[1] - 2, n[2] - 2], dtype=torch.float64)
         nx, ny, _ = n
         self.off = [(m, q, p, (p * ny + q) * nx + m) for m in (0, 1) for q in (0, 1) for p in (0, 1)]
+        self.lo = torch.zeros(3, dtype=torch.float64)
+        self.hi = torch.tensor([n[0] - 1.0, n[1] - 1.0, n[2] - 1.0], dtype=torch.float64)
+
+    def widths(self, xi):
+        return None  # index space: the spacing is part of rhs
 
     def interp(self, xi):
         nx, ny, _ = self.n
@@ -132,7 +180,7 @@ class _Field:
         out = (wts[:, :, None] * vals).sum(1)
         return out[:, :3], out[:, 3:]
 
-    def rhs(self, xi, sigma):
+    def rhs(self, xi, sigma, D=None):
         """Index-space line equation: F = sigma bt/|bt| (bt_a = B_a/d_a), and
         the Tw integrand (J.B)/(4 pi B^2) dl/dtau with dl/dtau = |B|/|bt|."""
         Bi, Ji = self.interp(xi)
@@ -145,16 +193,72 @@ class _Field:
         return F, dtw
 
 
+class _RectField:
+    """The same on a stretched grid (reading R16): physical positions; the cell
+    of a coordinate is the largest i in [0, n-2] with x_i <= x (below x_0, and
+    NaN, cell 0), chosen without a derivative; Eq. w0 weights in physical
+    coordinates; the line equation dr/dtau = sigma B/|bt| with bt_a = B_a/D_a,
+    D the widths of the cell the step starts in."""
+
+    def __init__(self, Bt, Jt, coords):
+        self.X = [np.asarray(c, dtype=np.float64) for c in coords]
+        self.Xt = [torch.from_numpy(x) for x in self.X]
+        self.n = tuple(len(x) for x in self.X)
+        self.BJ = torch.cat([Bt, Jt], dim=-1).reshape(-1, 6)
+        nx, ny, _ = self.n
+        self.off = [(m, q, p, (p * ny + q) * nx + m) for m in (0, 1) for q in (0, 1) for p in (0, 1)]
+        self.lo = torch.tensor([x[0] for x in self.X], dtype=torch.float64)
+        self.hi = torch.tensor([x[-1] for x in self.X], dtype=torch.float64)
+
+    def cells(self, x):
+        with torch.no_grad():
+            out = []
+            for a in range(3):
+                xa = x[:, a].detach().numpy()
+                c = np.searchsorted(self.X[a], xa, side="right") - 1
+                c = np.where(np.isnan(xa) | ~(xa >= self.X[a][0]), 0, c)
+                out.append(np.clip(c, 0, self.n[a] - 2))
+            return torch.from_numpy(np.stack(out, axis=1).astype(np.int64))
+
+    def widths(self, x):
+        c = self.cells(x)
+        return torch.stack([self.Xt[a][c[:, a] + 1] - self.Xt[a][c[:, a]] for a in range(3)], dim=1)
+
+    def interp(self, x):
+        nx, ny, _ = self.n
+        c = self.cells(x)
+        w0 = torch.stack([(self.Xt[a][c[:, a] + 1] - x[:, a]) / (self.Xt[a][c[:, a] + 1] - self.Xt[a][c[:, a]])
+                          for a in range(3)], dim=1)
+        w1 = 1.0 - w0
+        base = (c[:, 2] * ny + c[:, 1]) * nx + c[:, 0]
+        nodes = torch.stack([base + o for (_, _, _, o) in self.off], dim=1)
+        wts = torch.stack([(w1[:, 0] if m else w0[:, 0]) * (w1[:, 1] if q else w0[:, 1]) *
+                           (w1[:, 2] if p else w0[:, 2]) for (m, q, p, _) in self.off], dim=1)
+        out = (wts[:, :, None] * self.BJ[nodes]).sum(1)
+        return out[:, :3], out[:, 3:]
+
+    def rhs(self, x, sigma, D):
+        Bi, Ji = self.interp(x)
+        bt = Bi / D
+        nbt = torch.sqrt((bt * bt).sum(-1))
+        BB = (Bi * Bi).sum(-1)
+        F = sigma[:, None] * Bi / nbt[:, None]
+        dl = torch.sqrt(BB) / nbt
+        dtw = (Ji * Bi).sum(-1) / (4.0 * math.pi * BB) * dl
+        return F, dtw
+
+
 def _rk4(fld, x, h, sig, ax=None, scheme=0):
     """One Fehlberg step of the 4th-order solution from x (scheme 1: one
     3/8-rule step). With ax (face axis per lane) the independent variable is
     that index coordinate (exit step): the RHS is divided by its ax
     component."""
     A, Bw = (_A38, _B38) if scheme == 1 else (_A, _B4)
+    D = fld.widths(x)  # stretched grid: the widths of the step's start cell
     ks, ts = [], []
     for s in range(len(Bw)):
         acc = sum(A[s][r] * ks[r] for r in range(s)) if s else torch.zeros_like(x)
-        F, dtw = fld.rhs(x + h[:, None] * acc, sig)
+        F, dtw = fld.rhs(x + h[:, None] * acc, sig, D)
         if ax is not None:
             fa = F.gather(1, ax[:, None])[:, 0]
             F, dtw = F / fa[:, None], dtw / fa
@@ -197,8 +301,7 @@ def replay(fld, xi0, s0, log):
     code, hh = half_lines(log)
     H, T = code.shape
     sig = torch.stack([-s0, s0], dim=1).reshape(H)
-    n = fld.n
-    hi = torch.tensor([n[0] - 1.0, n[1] - 1.0, n[2] - 1.0], dtype=torch.float64)
+    lo, hi = fld.lo, fld.hi
     xi = xi0.repeat_interleave(2, dim=0)
     tw = torch.zeros(H, dtype=torch.float64)
     for t in range(T):
@@ -216,13 +319,13 @@ def replay(fld, xi0, s0, log):
             idx = torch.from_numpy(i_e)
             face = torch.from_numpy(np.where(ct[i_e] >= EXIT_CLAMPED, ct[i_e] - EXIT_CLAMPED, ct[i_e] - EXIT))
             ax = face // 2
-            target = torch.where(face % 2 == 1, hi[ax], torch.zeros(len(i_e), dtype=torch.float64))
+            target = torch.where(face % 2 == 1, hi[ax], lo[ax])
             x = xi[idx]
             delta = target - x.gather(1, ax[:, None])[:, 0]
             xe, de = _rk4(fld, x, delta, sig[idx], ax, scheme=scheme)
             onehot = torch.nn.functional.one_hot(ax, 3).to(torch.bool)
             xe = torch.where(onehot, target[:, None], xe)
-            xe = torch.minimum(torch.maximum(xe, torch.zeros_like(xe)), hi)  # the clamp of code 40+
+            xe = torch.minimum(torch.maximum(xe, lo), hi)  # the clamp of code 40+
             xi = xi.index_put((idx,), xe)
             tw = tw.index_put((idx,), tw[idx] + de)
         # chord fallback after an exiting step of size h
@@ -231,7 +334,7 @@ def replay(fld, xi0, s0, log):
             idx = torch.from_numpy(i_c)
             face = torch.from_numpy(ct[i_c] - CHORD)
             ax = face // 2
-            target = torch.where(face % 2 == 1, hi[ax], torch.zeros(len(i_c), dtype=torch.float64))
+            target = torch.where(face % 2 == 1, hi[ax], lo[ax])
             x = xi[idx]
             x4, d4 = _rk4(fld, x, torch.from_numpy(hh[i_c, t]), sig[idx], scheme=scheme)
             xa, x4a = x.gather(1, ax[:, None])[:, 0], x4.gather(1, ax[:, None])[:, 0]
@@ -279,11 +382,14 @@ _FACE_AXES = {0: (1, 2), 1: (0, 2), 2: (0, 1)}
 
 
 def seeds_index(grid, origin, u, v, nu, nv):
-    """Index-space lattice seeds o + (i+1/2) u + (j+1/2) v, i fastest."""
+    """Lattice seeds o + (i+1/2) u + (j+1/2) v, i fastest, in state
+    coordinates: index space on a uniform grid, physical on a stretched one."""
     ii = np.arange(nu * nv) % nu
     jj = np.arange(nu * nv) // nu
     r0 = (np.asarray(origin, float)[None] + (ii + 0.5)[:, None] * np.asarray(u, float)[None]) + \
         (jj + 0.5)[:, None] * np.asarray(v, float)[None]
+    if is_rect(grid):
+        return r0
     return (r0 - np.asarray(grid.origin, float)) / np.asarray(grid.spacing, float)
 
 
@@ -317,8 +423,13 @@ def qmap_t(Bt, grid, origin, u, v, nu, nv, log, lines=None, targets=None):
     seeds follow the frame of B at the seed. Returns (Q, Tw, usable mask, end
     positions of the lattice rows)."""
     n = grid.n
-    Jt = curl_t(Bt, grid.spacing)
-    fld = _Field(Bt, Jt, n, grid.spacing)
+    rect = is_rect(grid)
+    if rect:
+        Jt = curl_t_rect(Bt, grid.coords)
+        fld = _RectField(Bt, Jt, grid.coords)
+    else:
+        Jt = curl_t(Bt, grid.spacing)
+        fld = _Field(Bt, Jt, n, grid.spacing)
     m = nu * nv
     lines = np.arange(m) if lines is None else np.asarray(lines, dtype=np.int64)
     targets = lines if targets is None else np.asarray(targets, dtype=np.int64)
@@ -328,8 +439,9 @@ def qmap_t(Bt, grid, origin, u, v, nu, nv, log, lines=None, targets=None):
     faces, status = log["faces"], log["status"]
     good = (status & BAD) == 0
     xi_all = seeds_index(grid, origin, u, v, nu, nv)
-    d = np.asarray(grid.spacing, float)
-    o_np = np.asarray(grid.origin, float)
+    # state -> physical: o + d xi (uniform), the identity (stretched)
+    d = np.ones(3) if rect else np.asarray(grid.spacing, float)
+    o_np = np.zeros(3) if rect else np.asarray(grid.origin, float)
     n0 = np.cross(np.asarray(u, float), np.asarray(v, float))
     n0 = n0 / np.linalg.norm(n0)
     du, dv = float(np.linalg.norm(u)), float(np.linalg.norm(v))
@@ -371,7 +483,7 @@ def qmap_t(Bt, grid, origin, u, v, nu, nv, log, lines=None, targets=None):
         rlog = log
     xi, tw = replay(fld, xi0, s0, rlog)
     nrows = xi.shape[0]
-    phys = torch.from_numpy(o_np) + fld.d * xi  # (rows, 2, 3)
+    phys = torch.from_numpy(o_np) + torch.from_numpy(d) * xi  # (rows, 2, 3)
     cols = []
     for e in range(2):
         for r in range(2):

@@ -1199,14 +1199,13 @@ int oracle_max_threads(void)
  * traced as the Q map traces them and, if xlogh is not NULL, recorded in the
  * x* arrays (4 per seed: records of cap entries, counts, s0, faces (2),
  * status). Used by the adjoint tests to replay the frozen step sequence. */
-int oracle_lattice_log(const double *B, const double *J, const long long n[3], const double o[3], const double d[3],
-                       const double lo[3], const double a1[3], const double a2[3], const long long ln[2],
-                       const OParams *p, int cap, double *logh, int *logc, int *logn, double *s0o, double *tolo,
-                       double *bn0o, double *ends, int *faces, int *st, const long long *which, long long nwhich,
-                       double *xlogh, int *xlogc, int *xlogn, double *xs0, int *xfaces, int *xst)
+static int o_lattice_log(const OField *pf, const double lo[3], const double a1[3], const double a2[3],
+                         const long long ln[2], const OParams *p, int cap, double *logh, int *logc, int *logn,
+                         double *s0o, double *tolo, double *bn0o, double *ends, int *faces, int *st,
+                         const long long *which, long long nwhich, double *xlogh, int *xlogc, int *xlogn, double *xs0,
+                         int *xfaces, int *xst)
 {
-    OField f;
-    if (o_make_field(&f, B, J, NULL, n, o, d)) return 1;
+    OField f = *pf;
     if (p->method != 1) return 2;
     OLattice L;
     for (int a = 0; a < 3; a++) {
@@ -1276,4 +1275,31 @@ int oracle_lattice_log(const double *B, const double *J, const long long n[3], c
         st[s] = c.status;
     }
     return 0;
+}
+
+/* The step record of every lattice line (R13), uniform grid. */
+int oracle_lattice_log(const double *B, const double *J, const long long n[3], const double o[3], const double d[3],
+                       const double lo[3], const double a1[3], const double a2[3], const long long ln[2],
+                       const OParams *p, int cap, double *logh, int *logc, int *logn, double *s0o, double *tolo,
+                       double *bn0o, double *ends, int *faces, int *st, const long long *which, long long nwhich,
+                       double *xlogh, int *xlogc, int *xlogn, double *xs0, int *xfaces, int *xst)
+{
+    OField f;
+    if (o_make_field(&f, B, J, NULL, n, o, d)) return 1;
+    return o_lattice_log(&f, lo, a1, a2, ln, p, cap, logh, logc, logn, s0o, tolo, bn0o, ends, faces, st, which,
+                         nwhich, xlogh, xlogc, xlogn, xs0, xfaces, xst);
+}
+
+/* The same on a stretched grid (R16; X = the nx + ny + nz node coordinates):
+ * the recorded ends are physical positions. */
+int oracle_lattice_log_rect(const double *B, const double *J, const long long n[3], const double *X,
+                            const double lo[3], const double a1[3], const double a2[3], const long long ln[2],
+                            const OParams *p, int cap, double *logh, int *logc, int *logn, double *s0o, double *tolo,
+                            double *bn0o, double *ends, int *faces, int *st, const long long *which, long long nwhich,
+                            double *xlogh, int *xlogc, int *xlogn, double *xs0, int *xfaces, int *xst)
+{
+    OField f;
+    if (o_make_field_rect(&f, B, J, NULL, n, X)) return 1;
+    return o_lattice_log(&f, lo, a1, a2, ln, p, cap, logh, logc, logn, s0o, tolo, bn0o, ends, faces, st, which,
+                         nwhich, xlogh, xlogc, xlogn, xs0, xfaces, xst);
 }
