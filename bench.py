@@ -50,8 +50,8 @@ GATHER_BYTES_PER_TRIAL = 4 * 8 * 32 + 2 * 8 * 16
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 # DRAM bytes (read + write) of one k_trace_f32 launch on this workload, from
-# the ncu capture summarised in profiles/trace_f32_c2_monopole_1024x1024.md,
-# valid while the tracer sources hash to TRACE_F32_SRC_HASH.
+# an ncu capture of that kernel on this map, valid while the tracer sources
+# hash to TRACE_F32_SRC_HASH.
 TRACE_F32_DRAM_BYTES = 308.370176e6 + 59.896576e6
 TRACE_F32_SRC_HASH = "0b43cd71e2326598"
 
@@ -1034,7 +1034,7 @@ def main():
                                     "frac": gather_tbs / l1_peak,
                                     "note": "bytes requested by the trilinear gathers over the nominal L1 byte "
                                             "rate; the binding unit is the L1 data pipe's wavefronts "
-                                            "(ncu: 73% of peak, profiles/trace_f32_c2_monopole_1024x1024.md)"}},
+                                            "(ncu: 73% of peak on this map)"}},
             "e2e": {"value": e2e_value, "unit": "Q+Tw values/s", "ms_per_step": e2e_pipe_ms,
                     "h2d_bytes_per_step": int(B.nbytes), "d2h_bytes_per_step": int(2 * n * 8),
                     "note": "per step: H2D of B from pinned memory, repack (curl), map, D2H of Q and Tw; "

@@ -298,13 +298,20 @@ FQSL_API fqsl_status fqsl_batch_destroy(fqsl_batch batch);
  * call allocates nothing. Limits and rules:
  *   - nu*nv <= FQSL_STATIC_MAX_SEEDS, else FQSL_ERR_ARG with a message;
  *   - the first call on a device (with that device current) looks up the
- *     array's device address once; make that first call before any stream
- *     capture;
+ *     array's device address once. Under CUDA's lazy module loading (the
+ *     default) that lookup is also what loads the part of the library holding
+ *     the array, so the array's device memory is reserved then: the first call
+ *     can fail with FQSL_ERR_OOM (or FQSL_ERR_CUDA) if the device is full.
+ *     Make that first call at start-up, before the caller's arena takes the
+ *     device memory and before any stream capture;
  *   - all calls share the one array: the call clears what must start at zero,
  *     and calls whose work overlaps on the GPU (other streams, other host
  *     threads) race on it, so serialise them;
- *   - the field handle (created beforehand by fqsl_field_create) is only read;
- *   - Method I only (params->method = 2 gives FQSL_ERR_UNSUPPORTED).
+ *   - the field handle (created beforehand by fqsl_field_create or
+ *     fqsl_field_create_rect) is only read, apart from the timing events of
+ *     fqsl_field_set_timing, which this call records like fqsl_qmap_plane;
+ *   - Method I only (params->method = 2 gives FQSL_ERR_UNSUPPORTED), with
+ *     either scheme, on uniform and stretched grids.
  */
 FQSL_API fqsl_status fqsl_qmap_plane_static(fqsl_field field, const double origin[3], const double u[3],
                                             const double v[3], long long nu, long long nv,

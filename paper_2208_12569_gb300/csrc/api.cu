@@ -40,6 +40,12 @@ bool finite3(const double *v) { return v && isfinite(v[0]) && isfinite(v[1]) && 
 
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// 1 <= a, 1 <= b and a * b <= lim, decided without forming a product that can
+// overflow
+bool count_ok(long long a, long long b, long long lim) { return a >= 1 && b >= 1 && a <= lim && b <= lim / a; }
+
+constexpr long long kMaxCount = (1LL << 31) - 1;  // largest number of seeds (or nodes) of one call
+
 // sequential carve of one scratch allocation
 struct Carver {
     char *base;
@@ -104,7 +110,7 @@ fqsl_status check_create(const void *B_dev, fqsl_dtype b_dtype, long long nx, lo
     if (b_dtype != FQSL_F32 && b_dtype != FQSL_F64)
         return fail(FQSL_ERR_ARG, "%s: b_dtype must be FQSL_F32 or FQSL_F64", who);
     if (nx < 2 || ny < 2 || nz < 2) return fail(FQSL_ERR_ARG, "%s: need nx, ny, nz >= 2", who);
-    if (nx >= (1 << 23) || ny >= (1 << 23) || nz >= (1 << 23) || nx * ny * nz >= (1LL << 31))
+    if (nx >= (1 << 23) || ny >= (1 << 23) || nz >= (1 << 23) || !count_ok(nx * ny, nz, kMaxCount))
         return fail(FQSL_ERR_ARG, "%s: grid too large (each axis < 2^23 nodes, < 2^31 nodes)", who);
     if (!(flags & (FQSL_PACK_F32 | FQSL_PACK_F64)) || (flags & ~(FQSL_PACK_F32 | FQSL_PACK_F64 | FQSL_PACK_GRADB)))
         return fail(FQSL_ERR_ARG, "%s: flags must hold FQSL_PACK_F32 and/or FQSL_PACK_F64 "
@@ -967,7 +973,7 @@ fqsl_status fqsl_qmap_plane(fqsl_field f, const double origin[3], const double u
     if (st != FQSL_OK) return st;
     if (!out) return fail(FQSL_ERR_ARG, "%s: out is NULL", who);
     if (!finite3(origin) || !finite3(u) || !finite3(v)) return fail(FQSL_ERR_ARG, "%s: non-finite plane", who);
-    if (nu < 1 || nv < 1 || nu * nv > (1LL << 31) - 1) return fail(FQSL_ERR_ARG, "%s: need 1 <= nu*nv < 2^31", who);
+    if (!count_ok(nu, nv, kMaxCount)) return fail(FQSL_ERR_ARG, "%s: need nu, nv >= 1 and nu*nv < 2^31", who);
     double n0[3];
     cross(u, v, n0);
     const double nn = sqrt(n0[0] * n0[0] + n0[1] * n0[1] + n0[2] * n0[2]);
@@ -1017,8 +1023,8 @@ fqsl_status fqsl_qmap_volume(fqsl_field f, const double origin[3], const double 
     if (!out) return fail(FQSL_ERR_ARG, "%s: out is NULL", who);
     if (!finite3(origin) || !finite3(step)) return fail(FQSL_ERR_ARG, "%s: non-finite lattice", who);
     if (!(step[0] > 0 && step[1] > 0 && step[2] > 0)) return fail(FQSL_ERR_ARG, "%s: steps must be > 0", who);
-    if (nx < 1 || ny < 1 || nz < 1 || nx * ny * nz > (1LL << 31) - 1)
-        return fail(FQSL_ERR_ARG, "%s: need 1 <= nx*ny*nz < 2^31", who);
+    if (!count_ok(nx, ny, kMaxCount) || !count_ok(nx * ny, nz, kMaxCount))
+        return fail(FQSL_ERR_ARG, "%s: need nx, ny, nz >= 1 and nx*ny*nz < 2^31", who);
     Lattice lat{};
     for (int a = 0; a < 3; a++) {
         lat.o[a] = origin[a];
@@ -1141,8 +1147,8 @@ extern "C" fqsl_status fqsl_qmap_plane_static(fqsl_field f, const double origin[
     if (!out) return fail(FQSL_ERR_ARG, "%s: out is NULL", who);
     if (!finite3(origin) || !finite3(u) || !finite3(v)) return fail(FQSL_ERR_ARG, "%s: non-finite plane", who);
     if (nu < 1 || nv < 1) return fail(FQSL_ERR_ARG, "%s: need nu, nv >= 1", who);
-    if (nu * nv > FQSL_STATIC_MAX_SEEDS)
-        return fail(FQSL_ERR_ARG, "%s: nu*nv = %lld exceeds FQSL_STATIC_MAX_SEEDS = %d", who, nu * nv,
+    if (!count_ok(nu, nv, FQSL_STATIC_MAX_SEEDS))
+        return fail(FQSL_ERR_ARG, "%s: nu*nv (nu = %lld, nv = %lld) exceeds FQSL_STATIC_MAX_SEEDS = %d", who, nu, nv,
                     FQSL_STATIC_MAX_SEEDS);
     double n0[3];
     cross(u, v, n0);
@@ -1220,13 +1226,16 @@ extern "C" fqsl_status fqsl_qmap_plane_static(fqsl_field f, const double origin[
         e = launch_seed_prep_f32(a, n, stream);
         if (e != cudaSuccess) return cuda_fail(e, who);
     }
+    mark(f, 0, stream);
     e = launch_trace(f, p, a, kSrcLattice, a.nitems, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
+    mark(f, 1, stream);
     if (lat.allow_rot) {
         a.q.head = counters + 1;
         e = launch_trace(f, p, a, kSrcExtra, 4 * n, stream);
         if (e != cudaSuccess) return cuda_fail(e, who);
     }
+    mark(f, 2, stream);
     AssembleArgs g{};
     g.f = a.f;
     g.lat = lat;
@@ -1238,6 +1247,9 @@ extern "C" fqsl_status fqsl_qmap_plane_static(fqsl_field f, const double origin[
     g.want_q = 1;
     e = f32 ? launch_assemble_f32(g, stream) : launch_assemble(g, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
+    mark(f, 3, stream);
+    f->timed = f->timing;
+    f->extra_timed = lat.allow_rot != 0;
     return FQSL_OK;
 }
 
@@ -1270,7 +1282,7 @@ fqsl_status plane_lattice(const fqsl_field f, const fqsl_plane &pl, const fqsl_p
     const double *origin = pl.origin, *u = pl.u, *v = pl.v;
     const long long nu = pl.nu, nv = pl.nv;
     if (!finite3(origin) || !finite3(u) || !finite3(v)) return fail(FQSL_ERR_ARG, "%s: non-finite plane", who);
-    if (nu < 1 || nv < 1 || nu * nv > (1LL << 31) - 1) return fail(FQSL_ERR_ARG, "%s: need 1 <= nu*nv < 2^31", who);
+    if (!count_ok(nu, nv, kMaxCount)) return fail(FQSL_ERR_ARG, "%s: need nu, nv >= 1 and nu*nv < 2^31", who);
     double n0[3];
     cross(u, v, n0);
     const double nn = sqrt(n0[0] * n0[0] + n0[1] * n0[1] + n0[2] * n0[2]);

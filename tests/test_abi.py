@@ -68,6 +68,10 @@ def test_host_argument_errors(lib):
                                  C.byref(h)) == 1
     assert lib.fqsl_field_create(fake, 7, C.c_longlong(4), C.c_longlong(4), C.c_longlong(4), o, d, 1, None,
                                  C.byref(h)) == 1
+    # node counts whose product overflows 64 bits (each axis below 2^23) are refused on the host
+    big = C.c_longlong(1 << 22)
+    assert lib.fqsl_field_create(fake, 0, big, big, big, o, d, 1, None, C.byref(h)) == 1
+    assert b"too large" in lib.fqsl_last_error()
     lib.fqsl_qmap_plane.restype = C.c_int
     assert lib.fqsl_qmap_plane(None, o, o, o, C.c_longlong(1), C.c_longlong(1), None, None, None) == 1
 

@@ -203,6 +203,19 @@ def test_argument_errors(fq):
     with pytest.raises(fq.FqslError) as ei:
         fq.qmap_plane(f32only, (0, 0, 0), (0.1, 0, 0), (0, 0.1, 0), 2, 2, fq.params(precision="f64"))
     assert ei.value.status == 5
+    # seed counts whose product overflows 64 bits (2^32 x 2^32 wraps to 0) are
+    # refused before any launch
+    small = fq.alloc_out(1)
+    with pytest.raises(fq.FqslError) as ei:
+        fq.qmap_plane(field, (0, 0, 0), (0.1, 0, 0), (0, 0.1, 0), 1 << 32, 1 << 32, out=small)
+    assert ei.value.status == 1 and "2^31" in str(ei.value)
+    with pytest.raises(fq.FqslError) as ei:
+        fq.qmap_volume(field, (0, 0, 0), (0.1, 0.1, 0.1), 1 << 22, 1 << 21, 1 << 21, out=small)
+    assert ei.value.status == 1 and "2^31" in str(ei.value)
+    with pytest.raises(fq.FqslError) as ei:
+        fq.Batch([field], [dict(origin=(0, 0, 0), u=(0.1, 0, 0), v=(0, 0.1, 0), nu=1 << 32, nv=1 << 32)],
+                 outs=[small])
+    assert ei.value.status == 1
 
 
 def test_c2_full_size_sampled_parity(fq, oracle_lib):
