@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 NU = NV = 1024
 TOL = 10 ** -3.2
+CONVERGED_TOL = 1e-10  # the oracle's map at this tolerance stands in for the exact map
 CUBE = (256, 256, 128)
 SEED = 2208
 WORKLOAD = "monopole24_256x256x128_f32_z0plane_1024x1024_methodI_rkf45"
@@ -47,6 +48,15 @@ METRIC = "Q+Tw values/sec on 1 GB300 (FP32 vs FP64) at stated rel-err vs oracle"
 # from L1.
 FLOPS_PER_TRIAL = 4 * 145 + 2 * 89 + 222
 GATHER_BYTES_PER_TRIAL = 4 * 8 * 32 + 2 * 8 * 16
+# The FP64 tracer (trace.cuh, FP64 gather and rhs): per evaluation 118 flops
+# of trilinear gather (6 weights, 16 corner-weight products, 8 x 6 x 2
+# accumulation) and 30 of right-hand side (3 divisions by the spacing, |bt|^2,
+# |B|^2, 2 square roots, 6 for F, 1 for dl/dtau, 8 for the twist integrand);
+# 6 evaluations and 222 flops of stage combination per trial. A division or a
+# square root counts as one flop. Bytes: 6 x 8 corners x the 48 bytes of B
+# and curl B of a 64-byte record.
+FLOPS_PER_TRIAL_F64 = 6 * (118 + 30) + 222
+GATHER_BYTES_PER_TRIAL_F64 = 6 * 8 * 48
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 # DRAM bytes (read + write) of one k_trace_f32 launch on this workload, from
@@ -125,6 +135,114 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def roofline(trials, trace_ms, trace64_ms, ceil, work_src):
+    """Roofline of the FP32 tracer: algorithmic gather bytes and flops of
+    `trials` RKF45 trial steps over its event-timed duration, against the
+    gather and FMA ceilings measured by the probes; bound = the larger
+    fraction. The FP64 tracer's fraction of the FP64 FMA ceiling beside it."""
+    gather = trials * GATHER_BYTES_PER_TRIAL / (trace_ms / 1000.0) / 1e12
+    flops = trials * FLOPS_PER_TRIAL / (trace_ms / 1000.0) / 1e12
+    flops64 = trials * FLOPS_PER_TRIAL_F64 / (trace64_ms / 1000.0) / 1e12
+    gather64 = trials * GATHER_BYTES_PER_TRIAL_F64 / (trace64_ms / 1000.0) / 1e12
+    traffic = TRACE_F32_DRAM_BYTES if _trace_src_hash() == TRACE_F32_SRC_HASH else None
+    per = {"trial_steps": trials, "source": work_src, "gather_bytes_per_trial": GATHER_BYTES_PER_TRIAL,
+           "flops_per_trial": FLOPS_PER_TRIAL}
+    if ceil is None:
+        peaks, kind = _measured_peaks()
+        sm = float(peaks.get("sm_max_mhz", 2070.0))
+        alu = NUM_SMS * FP32_LANES_PER_SM * 2 * sm * 1e6 / 1e12
+        return {"bound": "alu", "achieved": flops, "peak": alu, "unit": "TFLOP/s", "frac": flops / alu,
+                "traffic": traffic, "work": per,
+                "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz); probes skipped"
+                               % (sm, kind)}
+    fg = gather / ceil["gather_walk_TBs"]
+    fa = flops / ceil["fma_f32_TFLOPs"]
+    g_bound = fg >= fa
+    return {"bound": "gather" if g_bound else "alu", "achieved": gather if g_bound else flops,
+            "peak": ceil["gather_walk_TBs"] if g_bound else ceil["fma_f32_TFLOPs"],
+            "unit": "TB/s" if g_bound else "TFLOP/s", "frac": max(fg, fa), "traffic": traffic,
+            "peak_source": ("measured on this GPU: trilinear gathers of 32-byte records by 8x4-lane tiles walking "
+                            "the cube (fqsl_probe_gather)" if g_bound else
+                            "measured on this GPU: FP32 FMA chains (fqsl_probe_fma)"),
+            "gather": {"achieved_TBs": gather, "ceiling_TBs": ceil["gather_walk_TBs"], "frac": fg},
+            "alu": {"achieved_TFLOPs": flops, "ceiling_TFLOPs": ceil["fma_f32_TFLOPs"], "frac": fa},
+            "ceilings": ceil, "work": per,
+            "fp64_tracer": {"ms": trace64_ms, "achieved_TFLOPs": flops64,
+                            "frac_of_fma_f64": flops64 / ceil["fma_f64_TFLOPs"], "gather_TBs": gather64,
+                            "flops_per_trial": FLOPS_PER_TRIAL_F64,
+                            "note": "a division or square root counts as one flop; the FP64 pipe runs each as "
+                                    "several instructions"}}
+
+
+def measure_ceilings(dev, cube=CUBE, target_ms=6.0):
+    """Roofline ceilings measured on this GPU by the probe kernels of
+    libfqsl_probes.so (include/fqsl_probes.h): trilinear gathers of 32-byte
+    records over a cube of the workload's size (requested bytes per second, for
+    three access patterns) and FP32 / FP64 FMA chains (flops per second). Each
+    figure is the best over a few grid sizes; each launch runs about target_ms."""
+    import ctypes as C
+
+    import torch
+
+    import __graft_entry__
+
+    lib = C.CDLL(__graft_entry__._builder().build_probes())
+    lib.fqsl_probe_gather.restype = C.c_int
+    lib.fqsl_probe_fma.restype = C.c_int
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    nx, ny, nz = cube
+    rec = torch.rand(nx * ny * nz * 8, dtype=torch.float32, device=dev)  # 32-byte records, > L2
+    sink = torch.empty(sms * 64 * 256, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    sptr = C.c_void_p(stream.cuda_stream)
+
+    def best_ms(launch, reps=3):
+        launch()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launch()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    def sized(run, work0):
+        # calibrate the per-thread work so that one launch takes about target_ms
+        t = best_ms(lambda: run(work0), reps=1)
+        work = max(work0, int(work0 * target_ms / max(t, 1e-3)))
+        return work, best_ms(lambda: run(work))
+
+    out = {"sms": sms, "cube": list(cube), "record_bytes": 32}
+    names = {0: "walk", 1: "tile", 2: "random"}
+    for pat, name in names.items():
+        best = 0.0
+        for bps in (4, 8, 16):
+            def run(g, bps=bps, pat=pat):
+                rc = lib.fqsl_probe_gather(C.c_void_p(rec.data_ptr()), nx, ny, nz, pat, int(g), sms, bps,
+                                           C.c_void_p(sink.data_ptr()), sptr)
+                if rc:
+                    raise RuntimeError("fqsl_probe_gather: %d" % rc)
+            g, ms = sized(run, 64)
+            best = max(best, sms * bps * 128 * g * 256 / (ms / 1000.0) / 1e12)
+        out["gather_%s_TBs" % name] = best
+    for fp64, name, w0 in ((0, "fma_f32_TFLOPs", 4096), (1, "fma_f64_TFLOPs", 256)):
+        best = 0.0
+        for bps in (4, 8):
+            def run(it, bps=bps, fp64=fp64):
+                rc = lib.fqsl_probe_fma(fp64, int(it), sms, bps, C.c_void_p(sink.data_ptr()), sptr)
+                if rc:
+                    raise RuntimeError("fqsl_probe_fma: %d" % rc)
+            it, ms = sized(run, w0)
+            best = max(best, sms * bps * 256 * 8 * it * 2 / (ms / 1000.0) / 1e12)
+        out[name] = best
+    del rec, sink
+    torch.cuda.empty_cache()
+    return out
 
 
 def _dist():
@@ -778,6 +896,10 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--only-f32", action="store_true",
                     help="time only the FP32 map (no FP64, e2e or CPU legs); used for ncu captures")
+    ap.add_argument("--no-probes", action="store_true",
+                    help="plane workload: skip the roofline probes (the roofline then uses nominal peaks)")
+    ap.add_argument("--only-f64", action="store_true",
+                    help="time only the FP64 map (no other legs); used for ncu captures of the FP64 tracer")
     ap.add_argument("--no-stretched", action="store_true",
                     help="plane workload: skip the stretched-grid map embedded in its line")
     ap.add_argument("--workload", default="plane", choices=["plane", "volume", "batch", "adjoint", "stretched"],
@@ -851,6 +973,19 @@ def main():
         torch.cuda.synchronize()
         return [e0.elapsed_time(e1) for e0, e1 in ev], kern
 
+    if args.only_f64:
+        # the FP64 map alone (a small command for profiling its tracer)
+        for _ in range(args.warmup):
+            step(p64)
+        torch.cuda.synchronize()
+        ms, kern = timed(p64, args.steps)
+        field64.check()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": n / (float(np.mean(ms)) / 1000.0), "unit": "Q+Tw values/s",
+                              "ms_per_step": float(np.mean(ms)),
+                              "kernels_ms": {"trace_f64": float(np.mean([k[0] for k in kern]))},
+                              "config": {"workload": WORKLOAD}, "partial": "only-f64"}), flush=True)
+        return
     for _ in range(args.warmup):
         step(p32)
     field32.check()
@@ -997,16 +1132,13 @@ def main():
         assert np.array_equal(np.isnan(Qhs[b].numpy()), np.isnan(res32["Q"]))
     fields[1].close()
 
-    # roofline of the dominant kernel (the FP32 tracer)
-    peaks, peak_kind = _measured_peaks()
+    # roofline of the dominant kernel (the FP32 tracer): its time, and the
+    # ceilings of its gather and FMA work measured on this GPU by the probes
     trials = float(res32["steps"].astype(np.int64).sum())
     trace_ms = float(np.mean([k[0] for k in kern32]))
+    trace64_ms = float(np.mean([k[0] for k in kern64]))
     asm_ms = float(np.mean([k[2] for k in kern32]))
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    achieved = trials * FLOPS_PER_TRIAL / (trace_ms / 1000.0) / 1e12
-    gather_tbs = trials * GATHER_BYTES_PER_TRIAL / (trace_ms / 1000.0) / 1e12
-    l1_peak = NUM_SMS * 128 * sm_mhz * 1e6 / 1e12
+    ceilings = None if args.no_probes else measure_ceilings(dev)
 
     line = {"metric": METRIC, "value": value, "unit": "Q+Tw values/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -1024,17 +1156,9 @@ def main():
             "fp64": {"value": value64, "unit": "Q+Tw values/s", "ms_per_step": float(np.mean(ms64)),
                      "trace_ms": float(np.mean([k[0] for k in kern64])),
                      "speedup_fp32_over_fp64": value / ws / value64},
-            "kernels_ms": {"trace_f32": trace_ms, "assemble": asm_ms},
-            "work": {"trial_steps_per_map": trials, "mean_trials_per_line": trials / n},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": achieved / alu_peak,
-                         "traffic": TRACE_F32_DRAM_BYTES if _trace_src_hash() == TRACE_F32_SRC_HASH else None,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, peak_kind),
-                         "gather": {"achieved_TBs": gather_tbs, "l1_nominal_TBs": l1_peak,
-                                    "frac": gather_tbs / l1_peak,
-                                    "note": "bytes requested by the trilinear gathers over the nominal L1 byte "
-                                            "rate; the binding unit is the L1 data pipe's wavefronts "
-                                            "(ncu: 73% of peak on this map)"}},
+            "kernels_ms": {"trace_f32": trace_ms, "trace_f64": trace64_ms, "assemble": asm_ms},
+            "work": {"trial_steps_per_map_f32_tracer": trials, "mean_trials_per_line_f32_tracer": trials / n,
+                     "trial_steps_per_map_f64_tracer": float(res64["steps"].astype(np.int64).sum())},
             "e2e": {"value": e2e_value, "unit": "Q+Tw values/s", "ms_per_step": e2e_pipe_ms,
                     "h2d_bytes_per_step": int(B.nbytes), "d2h_bytes_per_step": int(2 * n * 8),
                     "note": "per step: H2D of B from pinned memory, repack (curl), map, D2H of Q and Tw; "
@@ -1055,6 +1179,7 @@ def main():
                                               no_cpu_baseline=True), emit=False)
         line["stretched"] = {k: st[k] for k in ("value", "unit", "ms_per_step", "config", "f32_acc64", "fp64",
                                                 "kernels_ms", "work", "uniform_c2_f32")}
+    ref = sample = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, sample, ref = cpu_baseline(B, grid, u, v)
         line["cpu_baseline"] = cb
@@ -1067,6 +1192,19 @@ def main():
         B64 = B.astype(np.float64)
         Jo, Go = oracle.curl(B64, grid), oracle.gradb(B64, grid)
         es = np.sort(np.random.default_rng(SEED + 7).choice(n, 4000, replace=False))
+        # accuracy against the map itself: a converged oracle reference
+        # (tol_perp = 1e-10) on the same 4000 seeds, so that FP32 rounding is
+        # stated beside FP64's own integration error at the benchmark tolerance
+        t0 = time.perf_counter()
+        conv = oracle.plane(B64, grid, (0.0, 0.0, 0.0), u, v, NU, NV, oracle.params(tol=CONVERGED_TOL), sample=es,
+                            J=Jo)
+        conv_s = time.perf_counter() - t0
+        acc = {"reference": "oracle at tol_perp = %g on %d seeded-random seeds (%.1f s)" % (CONVERGED_TOL, len(es),
+                                                                                              conv_s),
+               "f32": err_stats(res32, conv, es), "f32_acc64": err_stats(resacc, conv, es),
+               "f64": err_stats(res64, conv, es)}
+        acc["f32_p99_over_f64_p99"] = acc["f32"]["q_rel_p99"] / max(acc["f64"]["q_rel_p99"], 1e-300)
+        line["accuracy_vs_converged"] = acc
         for (leg, key), (res, kw) in leg_res.items():
             ref_l = oracle.plane(B64, grid, (0.0, 0.0, 0.0), u, v, NU, NV, oracle.params(tol=TOL, **kw), sample=es,
                                  J=Jo, G=Go if kw.get("way") == 1 else None)
@@ -1074,6 +1212,18 @@ def main():
             e["bitwise"] = bool(all(np.array_equal(res[k][es], ref_l[k], equal_nan=True)
                                     for k in ("Q", "Tw", "face1", "face2", "status")))
             line[leg][key]["error_vs_oracle"] = e
+    # the algorithmic trial count: the oracle's counters on its sample, scaled
+    # to the map (the FP64 tracer's own counts, which equal the oracle's step
+    # for step, without the CPU leg); GPU FP32 retries do not count
+    if ref is not None:
+        trials_alg = float(ref["steps"].astype(np.int64).sum()) * n / len(sample)
+        work_src = "oracle trial counters on %d of %d seeds, scaled" % (len(sample), n)
+    else:
+        trials_alg = float(res64["steps"].astype(np.int64).sum())
+        work_src = "FP64 tracer trial counters (equal to the oracle's)"
+    line["work"]["trial_steps_per_map_algorithmic"] = trials_alg
+    line["work"]["algorithmic_source"] = work_src
+    line["roofline"] = roofline(trials_alg, trace_ms, trace64_ms, ceilings, work_src)
     if rank == 0:
         print(json.dumps(line), flush=True)
     field32.close()

@@ -14,6 +14,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libfqsl.so")
+# the roofline probes (include/fqsl_probes.h): a separate small library that
+# the benchmark loads; not part of the product ABI
+PROBES_SRC = os.path.join(PKG, "probes", "roofline_probes.cu")
+PROBES_LIB = os.path.join(PKG, "libfqsl_probes.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
@@ -42,8 +46,24 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def build_probes(force: bool = False) -> str:
+    """Compile the roofline probes into libfqsl_probes.so. Returns its path."""
+    deps = [PROBES_SRC, os.path.join(INCLUDE, "fqsl_probes.h"), os.path.abspath(__file__)]
+    if not force and not _stale(PROBES_LIB, deps):
+        return PROBES_LIB
+    tmp = PROBES_LIB + ".tmp%d" % os.getpid()
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-shared", PROBES_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for %s:\n%s%s" % (PROBES_SRC, r.stdout, r.stderr))
+    os.replace(tmp, PROBES_LIB)
+    return PROBES_LIB
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile every csrc/*.cu for sm_103a and link libfqsl.so. Returns its path."""
+    """Compile every csrc/*.cu for sm_103a and link libfqsl.so (and the roofline
+    probes' libfqsl_probes.so). Returns the path of libfqsl.so."""
+    build_probes(force)
     deps = _deps()
     if not force and not _stale(LIB, deps):
         return LIB

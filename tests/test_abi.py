@@ -18,9 +18,9 @@ def lib():
     return C.CDLL(path)
 
 
-def declared_symbols():
-    text = open(os.path.join(ROOT, "include", "fqsl.h")).read()
-    return sorted(set(re.findall(r"FQSL_API\s+[\w\s\*]*?\b(fqsl_\w+)\s*\(", text)))
+def declared_symbols(header="fqsl.h", api="FQSL_API"):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    return sorted(set(re.findall(api + r"\s+[\w\s\*]*?\b(fqsl_\w+)\s*\(", text)))
 
 
 def test_header_declares_entry_points():
@@ -33,6 +33,24 @@ def test_header_declares_entry_points():
 def test_exports_every_declared_symbol(lib):
     for name in declared_symbols():
         assert hasattr(lib, name), name
+
+
+def test_probe_library_exports_its_symbols():
+    # the roofline probes (include/fqsl_probes.h) live in their own library
+    import __graft_entry__
+
+    probes = C.CDLL(__graft_entry__._builder().build_probes())
+    names = declared_symbols("fqsl_probes.h", "FQSL_PROBE_API")
+    assert names == ["fqsl_probe_fma", "fqsl_probe_gather"]
+    for name in names:
+        assert hasattr(probes, name), name
+    # argument errors are refused before any launch
+    probes.fqsl_probe_gather.restype = C.c_int
+    probes.fqsl_probe_fma.restype = C.c_int
+    assert probes.fqsl_probe_gather(None, 8, 8, 8, 0, 1, 1, 1, None, None) == 1
+    assert probes.fqsl_probe_gather(C.c_void_p(4096), 2, 8, 8, 0, 1, 1, 1, C.c_void_p(4096), None) == 1
+    assert probes.fqsl_probe_gather(C.c_void_p(4096), 8, 8, 8, 7, 1, 1, 1, C.c_void_p(4096), None) == 1
+    assert probes.fqsl_probe_fma(0, 0, 1, 1, C.c_void_p(4096), None) == 1
 
 
 def test_params_defaults():

@@ -237,6 +237,34 @@ def test_c2_full_size_sampled_parity(fq, oracle_lib):
     assert np.mean(g32s["face2"] == r["face2"]) > 0.98
     rel = q_rel(g32s, r)
     assert np.median(rel[np.isfinite(rel)]) < 1e-3
+    # the FP32 map's tail against the FP64 map at the same tolerance (3.2 % at
+    # the 99th percentile over the whole map)
+    assert np.percentile(rel[np.isfinite(rel)], 99) < 0.06
+
+
+def test_c2_fp32_accuracy_against_the_converged_map(fq, oracle_lib):
+    """FP32 against the map itself: on the full-size benchmark map, both the
+    FP32 and the FP64 map at the benchmark tolerance (10^-3.2) are compared
+    with the oracle's map at tol_perp = 1e-10 on a seeded sample. FP64 at that
+    tolerance carries the method's own integration error (a different step
+    sequence than the converged one); FP32's error against the converged map
+    must stay within twice FP64's, at the median and the 99th percentile, so
+    that float rounding does not set the map's accuracy."""
+    B, grid, _ = synth.c2_monopole()
+    field = _field(fq, B, grid)
+    n = 1024
+    args = ((0.0, 0.0, 0.0), (255.0 / n, 0, 0), (0, 255.0 / n, 0), n, n)
+    g64 = _gpu_plane(fq, field, *args, precision="f64")
+    g32 = _gpu_plane(fq, field, *args, precision="f32")
+    sample = np.sort(np.random.default_rng(29).choice(n * n, 2000, replace=False))
+    conv = oracle.plane(B.astype(np.float64), grid, *args, oracle.params(tol=1e-10), sample=sample)
+    r32 = q_rel({k: v[sample] for k, v in g32.items()}, conv)
+    r64 = q_rel({k: v[sample] for k, v in g64.items()}, conv)
+    r32, r64 = r32[np.isfinite(r32)], r64[np.isfinite(r64)]
+    assert len(r32) > 1900
+    assert np.median(r64) > 1e-4  # the benchmark tolerance's own error is visible
+    assert np.median(r32) <= 2.0 * np.median(r64)
+    assert np.percentile(r32, 99) <= 2.0 * np.percentile(r64, 99)
 
 
 # ---------------------------------------------------------------------------
