@@ -347,11 +347,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_volume(args):
+VOL_CUBE = (1024, 1024, 512)
+VOL_SEEDS = (512, 512, 256)
+VOL_PLANE = (4096, 4096)
+VOL_WORKLOAD = "monopole64_1024x1024x512_f32_volume512x512x256_plane4096x4096_methodI"
+
+
+def run_volume(args, emit=True, sample_frac=0.0025, fp64_layers=32, conv_seeds=1000):
     """Large volume: 1024x1024x512 FP32 monopole cube (64 sources); Q and Tw on
     the 512x512x256 cell-centred seed volume spanning the cube (every z-layer
-    its own S0) and on a 4096x4096 z=0 map; FP32 and FP64 tracing of the same
-    cube; error against the oracle on a seeded 1% sample of the volume."""
+    its own S0) and on a 4096x4096 z=0 map. FP32 over the whole volume; FP64
+    on its lowest fp64_layers layers (a slab of the same volume, to bound the
+    run: the whole FP64 volume takes about 50 s) and on the whole 4096^2 map.
+    Errors against the oracle on a seeded sample of sample_frac of the volume
+    (FP64 on the sample's seeds in the slab), and FP32 and FP64 against the
+    converged oracle map (tol_perp = 1e-10) on conv_seeds of the slab's seeds."""
     import torch
 
     import __graft_entry__
@@ -362,66 +372,107 @@ def run_volume(args):
     import paper_2208_12569_gb300 as fq
 
     dev = torch.device("cuda", 0)
-    n = (1024, 1024, 512)
+    n = VOL_CUBE
     t0 = time.perf_counter()
     Bd, grid, _ = synth.large_monopole(n=n, device=dev)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
-    vol = (512, 512, 256)
+    vol = VOL_SEEDS
     step = tuple((n[a] - 1.0) / vol[a] for a in range(3))
-    plane = (4096, 4096)
+    plane = VOL_PLANE
     u = ((n[0] - 1.0) / plane[0], 0.0, 0.0)
     v = (0.0, (n[1] - 1.0) / plane[1], 0.0)
-    res = {}
-    outs = {}
+    nvol = vol[0] * vol[1] * vol[2]
+    slab = (vol[0], vol[1], fp64_layers)
+    nslab = slab[0] * slab[1] * slab[2]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def timed(fn, k):
+        ms, kern = [], []
+        for _ in range(k):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.mean(ms))
+
+    res, outs = {}, {}
     for prec in ("f32", "f64"):
         field = fq.Field(Bd, grid.origin, grid.spacing, pack=(prec,))
         field.set_timing(True)
         p = fq.params(precision=prec, tol=TOL)
-        nv = vol[0] * vol[1] * vol[2]
-        out = fq.alloc_out(nv, device=dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        fq.qmap_volume(field, (0.0, 0.0, 0.0), step, *vol, p, out=out)
-        e1.record()
+        lat = vol if prec == "f32" else slab
+        nl = lat[0] * lat[1] * lat[2]
+        out = fq.alloc_out(nl, device=dev)
+        run_v = lambda: fq.qmap_volume(field, (0.0, 0.0, 0.0), step, *lat, p, out=out)  # noqa: E731
+        run_v()  # warm-up
         torch.cuda.synchronize()
+        ms_v = timed(run_v, 1)
         field.check()
-        ms_v = e0.elapsed_time(e1)
         kern = field.times()
         outs[prec] = {k: t.cpu().numpy() for k, t in out.items() if t is not None}
         steps_total = float(outs[prec]["steps"].astype(np.int64).sum())
         del out
         outp = fq.alloc_out(plane[0] * plane[1], device=dev)
-        e0.record()
-        fq.qmap_plane(field, (0.0, 0.0, 0.0), u, v, *plane, p, out=outp)
-        e1.record()
+        run_p = lambda: fq.qmap_plane(field, (0.0, 0.0, 0.0), u, v, *plane, p, out=outp)  # noqa: E731
+        run_p()
         torch.cuda.synchronize()
-        ms_p = e0.elapsed_time(e1)
+        ms_p = timed(run_p, 3 if prec == "f32" else 1)
         del outp
         field.close()
-        res[prec] = {"volume": {"value": nv / (ms_v / 1000.0), "ms": ms_v, "kernels_ms": kern,
-                                "mean_trials_per_line": steps_total / nv},
-                     "plane_4096": {"value": plane[0] * plane[1] / (ms_p / 1000.0), "ms": ms_p}}
+        res[prec] = {"volume": {"value": nl / (ms_v / 1000.0), "unit": "Q+Tw values/s", "ms": ms_v,
+                                "seeds": list(lat), "kernels_ms": kern, "mean_trials_per_line": steps_total / nl},
+                     "plane_4096": {"value": plane[0] * plane[1] / (ms_p / 1000.0), "unit": "Q+Tw values/s",
+                                    "ms": ms_p}}
         torch.cuda.empty_cache()
-    # oracle on a 1% seeded sample of the volume
-    nvol = vol[0] * vol[1] * vol[2]
-    sample = np.sort(np.random.default_rng(19).choice(nvol, nvol // 100, replace=False))
-    B64 = Bd.cpu().numpy().astype(np.float64)
-    del Bd
-    torch.cuda.empty_cache()
-    t0 = time.perf_counter()
-    ref = oracle.qmap(B64, grid, (0.0, 0.0, 0.0), (step[0], 0, 0), (0, step[1], 0), (0, 0, step[2]), vol,
-                      oracle.params(tol=TOL), sample=sample)
-    ora_s = time.perf_counter() - t0
+    del flush
     line = {"metric": METRIC, "workload": "large_volume", "unit": "Q+Tw values/s",
-            "config": {"workload": "monopole64_1024x1024x512_f32_volume512x512x256_plane4096x4096_methodI",
-                       "tol_perp": TOL},
+            "config": {"workload": VOL_WORKLOAD, "cube": list(n), "seeds": list(vol), "plane": list(plane),
+                       "tol_perp": TOL, "fp64_volume_layers": fp64_layers,
+                       "l2": "flushed between steps (inputs far larger than L2)"},
             "value": res["f32"]["volume"]["value"], "f32": res["f32"], "f64": res["f64"],
-            "error_vs_oracle": {"f32": err_stats(outs["f32"], ref, sample), "f64": err_stats(outs["f64"], ref, sample)},
-            "cpu_baseline": {"value": len(sample) / ora_s, "unit": "Q+Tw values/s", "cores": oracle.max_threads(),
-                             "kind": "oracle", "sample": "%d seeded-random seeds of the volume (1%%)" % len(sample)},
-            "generation_s": gen_s}
-    print(json.dumps(line), flush=True)
+            "speedup_fp32_over_fp64_volume": res["f32"]["volume"]["value"] / res["f64"]["volume"]["value"],
+            "generation_s": gen_s, "gpu_launches": 10}
+    if not getattr(args, "no_cpu_baseline", False):
+        # the oracle on a seeded sample of the volume (the FP32 volume) and of
+        # its slab (the FP64 volume, bitwise)
+        m = max(1000, int(nvol * sample_frac))
+        sample = np.sort(np.random.default_rng(19).choice(nvol, m, replace=False))
+        B64 = Bd.cpu().numpy().astype(np.float64)
+        del Bd
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        J = oracle.curl(B64, grid)
+        curl_s = time.perf_counter() - t0
+        org, a1, a2, a3 = (0.0, 0.0, 0.0), (step[0], 0, 0), (0, step[1], 0), (0, 0, step[2])
+        t0 = time.perf_counter()
+        ref = oracle.qmap(B64, grid, org, a1, a2, a3, vol, oracle.params(tol=TOL), sample=sample, J=J)
+        ora_s = time.perf_counter() - t0
+        in_slab = sample < nslab
+        e64 = err_stats(outs["f64"], {k: v[in_slab] for k, v in ref.items()}, sample[in_slab])
+        e64["bitwise"] = bool(all(np.array_equal(outs["f64"][k][sample[in_slab]], ref[k][in_slab], equal_nan=True)
+                                  for k in ("Q", "Tw", "face1", "face2", "status")))
+        line["error_vs_oracle"] = {"f32": err_stats(outs["f32"], ref, sample), "f64_slab": e64,
+                                   "sample": "%d seeded-random seeds of the volume (%.2f%%); FP64 on the %d of them "
+                                             "in its slab" % (m, 100.0 * m / nvol, int(in_slab.sum()))}
+        cs = np.sort(np.random.default_rng(37).choice(nslab, conv_seeds, replace=False))
+        t1 = time.perf_counter()
+        conv = oracle.qmap(B64, grid, org, a1, a2, a3, vol, oracle.params(tol=CONVERGED_TOL), sample=cs, J=J)
+        conv_s = time.perf_counter() - t1
+        acc = {"reference": "oracle at tol_perp = %g on %d seeded-random seeds of the slab (%.1f s)"
+                            % (CONVERGED_TOL, conv_seeds, conv_s),
+               "f32": err_stats(outs["f32"], conv, cs), "f64": err_stats(outs["f64"], conv, cs)}
+        acc["f32_p99_over_f64_p99"] = acc["f32"]["q_rel_p99"] / max(acc["f64"]["q_rel_p99"], 1e-300)
+        line["accuracy_vs_converged"] = acc
+        line["cpu_baseline"] = {"value": m / ora_s, "unit": "Q+Tw values/s", "cores": oracle.max_threads(),
+                                "kind": "oracle", "sample": "%d seeded-random seeds of the volume (%.1f s; curl "
+                                                            "%.1f s)" % (m, ora_s, curl_s)}
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 RECT_WORKLOAD = "monopole24_stretched256x256x128_f32_z0plane_1024x1024_methodI_rkf45"
@@ -515,7 +566,7 @@ def run_stretched(args, emit=True):
     return line
 
 
-def run_batch(args):
+def run_batch(args, emit=True):
     """Batched uneven workload: 48 monopole cubes with sizes drawn from
     {64^3, 128^2x64, 256^2x128, 384^2x192}, 8-64 sources each, each with the
     z=0 plane or the mid-y vertical slice of 512x256 seeds (6.29 M lines).
@@ -585,20 +636,37 @@ def run_batch(args):
     ms_tuned = timed(tgraph.replay, args.steps)
     torch.cuda.synchronize()
     res = [{k: t.cpu().numpy() for k, t in o.items() if t is not None} for o in outs]
-    # oracle on a sample of seeds of the four smallest cubes
-    order = sorted(range(len(specs)), key=lambda k: np.prod(specs[k]["grid"].n))[:4]
+    # the same batch traced in FP64 (one launch set)
+    fields64 = [fq.Field(B, sp["grid"].origin, sp["grid"].spacing, pack=("f64",)) for B, sp in zip(cubes, specs)]
+    outs64 = [fq.alloc_out(pl["nu"] * pl["nv"], device=dev) for pl in planes]
+    batch64 = fq.Batch(fields64, planes, fq.params(precision="f64", tol=TOL), outs=outs64)
+    batch64.run()
+    torch.cuda.synchronize()
+    ms64 = timed(batch64.run, 1)
+    res64 = [{k: t.cpu().numpy() for k, t in o.items() if t is not None} for o in outs64]
+    batch64.close()
+    for fl in fields64:
+        fl.close()
+    del outs64
+    # oracle on a sample of seeds of the four smallest cubes and the largest
+    by_size = sorted(range(len(specs)), key=lambda k: np.prod(specs[k]["grid"].n))
+    order = by_size[:4] + by_size[-1:]
     errs = []
     ora_n, ora_s = 0, 0.0
     for k in order:
         sp, pl = specs[k], planes[k]
-        sample = np.sort(np.random.default_rng(k).choice(pl["nu"] * pl["nv"], 500, replace=False))
+        sample = np.sort(np.random.default_rng(k).choice(pl["nu"] * pl["nv"], 300, replace=False))
         B64 = cubes[k].cpu().numpy().astype(np.float64)
         t1 = time.perf_counter()
         ref = oracle.plane(B64, sp["grid"], pl["origin"], pl["u"], pl["v"], pl["nu"], pl["nv"],
                            oracle.params(tol=TOL), sample=sample)
         ora_s += time.perf_counter() - t1
         ora_n += len(sample)
-        errs.append(err_stats(res[k], ref, sample))
+        e = {"entry": int(k), "cube": list(sp["grid"].n), "f32": err_stats(res[k], ref, sample),
+             "f64": err_stats(res64[k], ref, sample)}
+        e["f64"]["bitwise"] = bool(all(np.array_equal(res64[k][c][sample], ref[c], equal_nan=True)
+                                       for c in ("Q", "Tw", "face1", "face2", "status")))
+        errs.append(e)
     line = {"metric": METRIC, "workload": "batch", "unit": "Q+Tw values/s",
             "config": {"workload": "batch48_monopole_mixed_sizes_512x256_seeds_methodI", "entries": len(specs),
                        "lines": total, "tol_perp": TOL, "l2": "flushed between steps"},
@@ -608,13 +676,18 @@ def run_batch(args):
             "batch_graph": {"ms": ms_graph, "value": total / (ms_graph / 1000.0)},
             "batch_graph_autotuned": {"ms": ms_tuned, "value": total / (ms_tuned / 1000.0),
                                       "best": {k: getattr(best, k) for k in space}, "table": table},
+            "fp64_batch_run": {"ms": ms64, "value": total / (ms64 / 1000.0)},
             "error_vs_oracle_sample": errs,
             "cpu_baseline": {"value": ora_n / ora_s, "unit": "Q+Tw values/s", "cores": oracle.max_threads(),
-                             "kind": "oracle", "sample": "500 seeds of each of the 4 smallest cubes"},
-            "generation_s": gen_s}
-    print(json.dumps(line), flush=True)
+                             "kind": "oracle", "sample": "300 seeds of each of the 4 smallest cubes and the largest"},
+            "generation_s": gen_s, "gpu_launches": 4 * args.steps}
+    if emit:
+        print(json.dumps(line), flush=True)
     for b in (batch, tuned):
         b.close()
+    for fl in fields:
+        fl.close()
+    return line
 
 
 ADJ_CUBE = (128, 128, 64)
@@ -900,6 +973,10 @@ def main():
                     help="plane workload: skip the roofline probes (the roofline then uses nominal peaks)")
     ap.add_argument("--only-f64", action="store_true",
                     help="time only the FP64 map (no other legs); used for ncu captures of the FP64 tracer")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="plane workload: skip the 48-cube batch embedded in its line")
+    ap.add_argument("--no-volume", action="store_true",
+                    help="plane workload: skip the large volume embedded in its line")
     ap.add_argument("--no-stretched", action="store_true",
                     help="plane workload: skip the stretched-grid map embedded in its line")
     ap.add_argument("--workload", default="plane", choices=["plane", "volume", "batch", "adjoint", "stretched"],
@@ -1173,6 +1250,18 @@ def main():
         line["adjoint"] = {k: a[k] for k in ("metric", "value", "unit", "ms_per_step", "higher_is_better", "config",
                                              "fp64", "kernels_ms", "error_vs_oracle", "e2e", "cpu_baseline",
                                              "roofline", "reverse_sweep", "loss", "fixed_step")}
+    if rank == 0 and ws == 1 and not args.no_batch:
+        # the batched uneven workload (48 cubes, one graph-captured autotuned launch)
+        bt = run_batch(argparse.Namespace(steps=args.steps, warmup=args.warmup), emit=False)
+        line["batch"] = {k: bt[k] for k in ("value", "unit", "config", "per_cube_launches", "batch_run",
+                                            "batch_graph", "batch_graph_autotuned", "fp64_batch_run",
+                                            "error_vs_oracle_sample", "cpu_baseline")}
+        line["batch"]["batch_graph_autotuned"] = {k: v for k, v in bt["batch_graph_autotuned"].items() if k != "table"}
+        line["batch"]["speedup_over_per_cube_launches"] = bt["value"] / bt["per_cube_launches"]["value"]
+    if rank == 0 and ws == 1 and not args.no_volume:
+        # the large volume (1024^2 x 512 cube, 512^2 x 256 seeds, 4096^2 map)
+        vl = run_volume(argparse.Namespace(no_cpu_baseline=args.no_cpu_baseline), emit=False)
+        line["volume"] = {k: vl[k] for k in vl if k not in ("metric", "workload")}
     if rank == 0 and ws == 1 and not args.no_stretched:
         # the same map on a stretched grid (its oracle check runs in the tests and in --workload stretched)
         st = run_stretched(argparse.Namespace(steps=args.steps, warmup=args.warmup, fp64_steps=args.fp64_steps,

@@ -51,6 +51,11 @@ extern "C" {
 
 typedef struct fqsl_field_s *fqsl_field;
 
+/* A taped map: the step sequence, checkpoints and line records of one plane or
+ * volume map traced with params->tape = 1, which fqsl_backward differentiates.
+ * Library-owned; made by the taped call, released by fqsl_tape_destroy. */
+typedef struct fqsl_tape_s *fqsl_tape;
+
 typedef enum {
     FQSL_OK = 0,
     FQSL_ERR_ARG = 1,         /* invalid argument; nothing was launched */
@@ -109,7 +114,8 @@ typedef struct {
     int blocks_per_sm;    /* scheduling: resident 128-thread blocks per SM of the persistent tracer
                              (0 = as many as fit). Results do not depend on it. */
     int tape;             /* 1: fqsl_qmap_plane / fqsl_qmap_volume (Method I) also record the step tape
-                             that fqsl_backward differentiates (0 = default). Results do not depend on it. */
+                             that fqsl_backward differentiates, into the call's tape_or_null (0 = default).
+                             Results do not depend on it. */
     int tape_chunk;       /* steps per tape chunk, i.e. the checkpoint interval k of the reverse sweep
                              (1..32; 0 = default 16) */
     int reverse_precision; /* precision of fqsl_backward's reverse sweep for this taped map: -1 (default)
@@ -222,18 +228,30 @@ FQSL_API fqsl_status fqsl_field_destroy(fqsl_field field);
  * carries the deviation vectors U, V of the frame perpendicular to B at its
  * seed (Sec. 2.1, Eq. rb2) and Q follows Eq. q_scott; gradb_way 1 needs a
  * field packed with FQSL_PACK_GRADB. The field must have been packed in
- * params->precision. Errors: FQSL_ERR_ARG, FQSL_ERR_UNSUPPORTED (precision or
- * gradient grid not packed), FQSL_ERR_OOM, FQSL_ERR_CUDA. */
+ * params->precision.
+ * tape_or_null: used only with params->tape = 1 (Method I), and then required.
+ * If *tape_or_null is NULL the call makes a new tape and stores it there;
+ * otherwise it records this map into the given tape, replacing what that tape
+ * held (its buffers are reused and grown as needed). A tape records one map of
+ * one field; several tapes may hold maps of the same field at once (for example
+ * Q on two planes in one loss), each differentiated by its own fqsl_backward.
+ * Calls that use the same tape must not overlap. If a call that made a new
+ * tape fails, the tape is released and *tape_or_null is NULL again.
+ * Errors: FQSL_ERR_ARG (including params->tape = 1 with tape_or_null NULL),
+ * FQSL_ERR_UNSUPPORTED (precision or gradient grid not packed; the tape with
+ * Method II or on a stretched grid), FQSL_ERR_OOM, FQSL_ERR_CUDA. */
 FQSL_API fqsl_status fqsl_qmap_plane(fqsl_field field, const double origin[3], const double u[3],
                             const double v[3], long long nu, long long nv,
-                            const fqsl_params *params, const fqsl_out *out, void *cuda_stream);
+                            const fqsl_params *params, const fqsl_out *out, fqsl_tape *tape_or_null,
+                            void *cuda_stream);
 
 /* The same on the 3D lattice seed(i,j,k) = origin + ((i+1/2) sx, (j+1/2) sy,
  * (k+1/2) sz), output index i + nx*(j + ny*k); every z-layer is its own
- * horizontal S0 (Q extended to 3D by being constant along a line, Eq. qline). */
+ * horizontal S0 (Q extended to 3D by being constant along a line, Eq. qline).
+ * tape_or_null as in fqsl_qmap_plane. */
 FQSL_API fqsl_status fqsl_qmap_volume(fqsl_field field, const double origin[3], const double step[3],
                              long long nx, long long ny, long long nz, const fqsl_params *params,
-                             const fqsl_out *out, void *cuda_stream);
+                             const fqsl_out *out, fqsl_tape *tape_or_null, void *cuda_stream);
 
 /* Tw, length, footpoints, faces, status and steps (no Q; out->Q ignored) for
  * an explicit list of physical seeds seeds_dev[3*n] (double), traced with
@@ -318,9 +336,9 @@ FQSL_API fqsl_status fqsl_qmap_plane_static(fqsl_field field, const double origi
                                             const fqsl_params *params, const fqsl_out *out, void *cuda_stream);
 
 /* Reverse mode (the paper has no derivative; this is the discrete adjoint of
- * the computation it defines). For the plane or volume map that
- * fqsl_qmap_plane or fqsl_qmap_volume last traced on this field with
- * params->tape = 1 (Method I), accumulate
+ * the computation it defines). For the plane or volume map recorded in tape
+ * (by fqsl_qmap_plane or fqsl_qmap_volume on this field with params->tape = 1,
+ * Method I), accumulate
  *   dB += d/dB ( sum_s dQ[s] Q[s] + dTw[s] Tw[s] )
  * where the derivative is that of the traced computation with each line's
  * accepted step sizes, exit faces and exit kinds (exit step onto a face, the
@@ -342,18 +360,21 @@ FQSL_API fqsl_status fqsl_qmap_plane_static(fqsl_field field, const double origi
  * The state is recomputed from checkpoints every params->tape_chunk accepted
  * steps, in the taped call's params->reverse_precision (default: its
  * precision); the node adjoints accumulate in float (FQSL_F32) or double
- * (FQSL_F32_ACC64, FQSL_F64). The field must not
- * be updated between the taped call and this one. The call synchronises
- * cuda_stream once (to confirm that the tape's chunk pool sufficed; if it did
- * not, it traces the map again with a larger pool), so it cannot be captured
- * in a CUDA graph. With timing enabled, fqsl_field_times reports ms[0] =
- * reverse sweep, ms[1] = 0, ms[2] = curl transpose. Errors: FQSL_ERR_ARG (no
- * taped map, the field updated since, NULL or misaligned pointers, db_dtype),
- * FQSL_ERR_OOM, FQSL_ERR_CUDA. */
-FQSL_API fqsl_status fqsl_backward(fqsl_field field, const double *dQ_dev, const double *dTw_dev, void *dB_dev,
-                                   fqsl_dtype db_dtype, void *cuda_stream);
+  * (FQSL_F32_ACC64, FQSL_F64). The field must not be updated between the
+ * taped call and this one; other maps of the field (taped into other tapes or
+ * not) may run in between. The call synchronises cuda_stream once (to confirm
+ * that the tape's chunk pool sufficed; if it did not, it traces the map again
+ * into the same tape with a larger pool), so it cannot be captured in a CUDA
+ * graph. The tape keeps its map: fqsl_backward may run on it again with other
+ * weights. With timing enabled, fqsl_field_times reports ms[0] = reverse
+ * sweep, ms[1] = 0, ms[2] = curl transpose. Errors: FQSL_ERR_ARG (NULL field
+ * or tape, a tape of another field or without a complete map, the field
+ * updated since, NULL or misaligned pointers, db_dtype), FQSL_ERR_OOM,
+ * FQSL_ERR_CUDA. */
+FQSL_API fqsl_status fqsl_backward(fqsl_field field, fqsl_tape tape, const double *dQ_dev, const double *dTw_dev,
+                                   void *dB_dev, fqsl_dtype db_dtype, void *cuda_stream);
 
-/* The step sequence of the field's last taped map (the paper has no
+/* The step sequence of the map held by a tape (the paper has no
  * counterpart; for inspection and for replaying a map's exact steps
  * elsewhere). For half-line hl = 2 s + e (seed s, end e = 0 for end 1):
  * nsteps_dev[hl] accepted steps (0 with code -1 for a line with MAXSTEPS,
@@ -364,15 +385,13 @@ FQSL_API fqsl_status fqsl_backward(fqsl_field field, const double *dQ_dev, const
  * hx_dev[hl], which is 0 otherwise). Device arrays of 2 x seeds elements
  * (h_dev: 2 x seeds x cap). The pool must have sufficed (run fqsl_backward first
  * if unsure). Errors: FQSL_ERR_ARG, FQSL_ERR_CUDA. */
-FQSL_API fqsl_status fqsl_tape_export(fqsl_field field, int cap, int32_t *nsteps_dev, int32_t *code_dev,
+FQSL_API fqsl_status fqsl_tape_export(fqsl_tape tape, int cap, int32_t *nsteps_dev, int32_t *code_dev,
                                       double *hx_dev, double *h_dev, void *cuda_stream);
 
-/* Number of the field's current taped map (1 for its first, incremented by
- * every taped call; 0 if none), so that a caller holding several taped maps
- * can check which one fqsl_backward would differentiate. fqsl_backward
- * refuses (FQSL_ERR_ARG) if fqsl_field_update ran after the taped call.
- * Errors: FQSL_ERR_ARG. */
-FQSL_API fqsl_status fqsl_tape_id(fqsl_field field, unsigned long long *id);
+/* Release a tape and its device memory (synchronises the device). A tape may
+ * outlive its field, but is then only good for fqsl_tape_export and this
+ * call. Errors: FQSL_ERR_ARG (NULL). */
+FQSL_API fqsl_status fqsl_tape_destroy(fqsl_tape tape);
 
 /* The log-Q / Tw misfit of two maps and its gradient (a loss for
  * fqsl_backward; the paper has no counterpart):

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -70,32 +71,41 @@ struct fqsl_field_s {
     void *scratch = nullptr;
     size_t scratch_cap = 0;
     void *rect_buf = nullptr;  // stretched grid: coordinate, width and bucket tables (FieldView::x64 ...)
-    unsigned long long *counters = nullptr;  // [0] primary head, [1] extra head, [2] rotated count (low 32 bits)
+    unsigned long long *counters = nullptr;  // [0] primary head, [1] extra head, [2] rotated count (low 32 bits),
+                                             // [4] first failed index check of the adjoint kernels, [5] their count
     int blocks_cache[2][3][3] = {};  // [scheme][precision][source] resident blocks per SM
     int blocks_cache_m2[2][2][2] = {};  // Method II: [scheme][fp64][way - 1]
     int blocks_cache_tape[2][3][2] = {};  // taped tracers: [scheme][precision][lattice, extra]
     bool timing = false, timed = false, extra_timed = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    // the last plane map traced with params->tape = 1 (for fqsl_backward): its
-    // records, step tape and adjoint buffers live in tape_buf
-    struct {
-        bool valid = false;
-        Lattice lat{};
-        fqsl_params p{};
-        bool face_plane = false;
-        long long pool = 0;  // tape chunks of the next taped call
-        void *buf = nullptr;
-        size_t cap = 0;
-        void *work = nullptr;  // per-step arrays of the reverse sweep
-        size_t work_cap = 0;
-        unsigned long long id = 0;   // taped maps so far on this field (the last one's number)
-        unsigned long long gen = 0;  // the field's record generation when it was taped
-    } tp;
-    unsigned long long gen = 0;  // incremented by every fqsl_field_update
+    unsigned long long serial = 0;  // unique per handle made in this process (tapes name their field by it)
+    unsigned long long gen = 0;     // incremented by every fqsl_field_update
     std::mutex mu;
 };
 
+// A taped plane or volume map (for fqsl_backward): its line records, step
+// tape and adjoint buffers live in buf, the reverse sweep's per-step arrays in
+// work. The tape names the field it was recorded on by handle and serial, and
+// the field's record generation at that time.
+struct fqsl_tape_s {
+    bool valid = false;
+    fqsl_field field = nullptr;
+    unsigned long long field_serial = 0;
+    unsigned long long gen = 0;
+    Lattice lat{};
+    fqsl_params p{};
+    bool face_plane = false;
+    size_t nodes = 0;      // the field's node count (size of the adjoint node grid)
+    long long pool = 0;    // tape chunks of the next taped call
+    void *buf = nullptr;
+    size_t cap = 0;
+    void *work = nullptr;  // per-step arrays of the reverse sweep
+    size_t work_cap = 0;
+};
+
 namespace {
+std::atomic<unsigned long long> g_field_serial{0};
+
 void mark(fqsl_field f, int i, cudaStream_t s)
 {
     if (f->timing) cudaEventRecord(f->ev[i], s);
@@ -134,6 +144,7 @@ fqsl_status check_device_ptr(const void *B_dev, const char *who)
 
 void set_dims(fqsl_field f, long long nx, long long ny, long long nz)
 {
+    f->serial = ++g_field_serial;
     cudaGetDevice(&f->device);
     cudaDeviceGetAttribute(&f->sms, cudaDevAttrMultiProcessorCount, f->device);
     f->g.nx = (int)nx;
@@ -172,13 +183,14 @@ fqsl_status finish_create(fqsl_field f, const void *B_dev, fqsl_dtype b_dtype, u
         if (f->rec32) e = cudaMalloc(&f->grad32, nodes * 48);
         if (e == cudaSuccess && f->rec64) e = cudaMalloc(&f->grad64, nodes * 80);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&f->counters, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&f->counters, 8 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_field(f);
         return cuda_fail(e, who);
     }
-    e = launch_curl_pack(B_dev, b_dtype, f->g, f->rec32, f->rec64, (cudaStream_t)cuda_stream);
+    e = cudaMemsetAsync(f->counters, 0, 8 * sizeof(unsigned long long), (cudaStream_t)cuda_stream);
+    if (e == cudaSuccess) e = launch_curl_pack(B_dev, b_dtype, f->g, f->rec32, f->rec64, (cudaStream_t)cuda_stream);
     if (e == cudaSuccess && (f->grad32 || f->grad64))
         e = launch_gradb_pack(B_dev, b_dtype, f->g, f->grad32, f->grad64, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) {
@@ -457,8 +469,6 @@ fqsl_status fqsl_field_destroy(fqsl_field f)
     cudaFree(f->grad32);
     cudaFree(f->grad64);
     cudaFree(f->scratch);
-    cudaFree(f->tp.buf);
-    cudaFree(f->tp.work);
     cudaFree(f->counters);
     cudaFree(f->rect_buf);
     delete f;
@@ -763,30 +773,29 @@ TapeLayout tape_layout(char *base, long long n, bool rot, bool f32, long long po
 int reverse_precision_of(const fqsl_params &p) { return p.reverse_precision < 0 ? p.precision : p.reverse_precision; }
 bool acc64_of(const fqsl_params &p) { return reverse_precision_of(p) != FQSL_F32; }
 
-// the taped map's layout in the field's tape buffer (base NULL: sizes only)
-TapeLayout field_tape_layout(const fqsl_field f, char *base, long long pool)
+// the taped map's layout in its tape's buffer (base NULL: sizes only)
+TapeLayout tape_layout_of(const fqsl_tape t, char *base, long long pool)
 {
-    const fqsl_params &p = f->tp.p;
-    const long long n = f->tp.lat.n1 * f->tp.lat.n2 * f->tp.lat.n3;
+    const fqsl_params &p = t->p;
+    const long long n = t->lat.n1 * t->lat.n2 * t->lat.n3;
     const int k = p.tape_chunk > 0 ? p.tape_chunk : kDefaultTapeChunk;
-    const size_t nodes = (size_t)f->g.nx * f->g.ny * f->g.nz;
-    return tape_layout(base, n, f->tp.lat.allow_rot, p.precision != FQSL_F64, pool, k, nodes, acc64_of(p));
+    return tape_layout(base, n, t->lat.allow_rot, p.precision != FQSL_F64, pool, k, t->nodes, acc64_of(p));
 }
 
-fqsl_status ensure_tape_buf(fqsl_field f, size_t bytes)
+fqsl_status ensure_tape_buf(fqsl_tape t, size_t bytes)
 {
-    if (bytes <= f->tp.cap) return FQSL_OK;
+    if (bytes <= t->cap) return FQSL_OK;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "tape buffer: synchronize");
-    cudaFree(f->tp.buf);
-    f->tp.buf = nullptr;
-    f->tp.cap = 0;
-    e = cudaMalloc(&f->tp.buf, bytes);
+    cudaFree(t->buf);
+    t->buf = nullptr;
+    t->cap = 0;
+    e = cudaMalloc(&t->buf, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_fail(e, "tape buffer allocation");
     }
-    f->tp.cap = bytes;
+    t->cap = bytes;
     return FQSL_OK;
 }
 
@@ -812,11 +821,11 @@ cudaError_t launch_tape(const TraceArgs &a, const fqsl_params *p, int src, long 
                                     : launch_trace_tape_f32(a, src, (int)grid, s, acc64);
 }
 
-// Shared body of the plane and volume Q maps (the caller holds f->mu). With
-// tape set (plane lattices, Method I) the records live in the field's tape
-// buffer and the lattice tracer also writes the step tape.
+// Shared body of the plane and volume Q maps (the caller holds f->mu). With a
+// tape (Method I) the records live in the tape's buffer and the lattice
+// tracer also writes the step tape into it.
 fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params *p, const fqsl_out *out,
-                            cudaStream_t stream, bool face_plane, bool tape, const char *who)
+                            cudaStream_t stream, bool face_plane, fqsl_tape tape, const char *who)
 {
     Lattice lat = lat0;
     index_lattice(f, lat);
@@ -829,19 +838,21 @@ fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params
     Scratch s;
     TapeLayout tl{};
     if (tape) {
-        f->tp.valid = false;
-        f->tp.id++;
-        f->tp.gen = f->gen;
-        f->tp.lat = lat;
-        f->tp.p = *p;
-        f->tp.face_plane = face_plane;
+        tape->valid = false;
+        tape->field = f;
+        tape->field_serial = f->serial;
+        tape->gen = f->gen;
+        tape->lat = lat;
+        tape->p = *p;
+        tape->face_plane = face_plane;
+        tape->nodes = (size_t)f->g.nx * f->g.ny * f->g.nz;
         const int k = p->tape_chunk > 0 ? p->tape_chunk : kDefaultTapeChunk;
         // first guess: 128 accepted steps per direction on average
         const long long guess = 2 * n * (128 / k + 1) + 1024;
-        if (f->tp.pool < guess) f->tp.pool = guess;
-        fqsl_status st = ensure_tape_buf(f, field_tape_layout(f, nullptr, f->tp.pool).bytes);
+        if (tape->pool < guess) tape->pool = guess;
+        fqsl_status st = ensure_tape_buf(tape, tape_layout_of(tape, nullptr, tape->pool).bytes);
         if (st != FQSL_OK) return st;
-        tl = field_tape_layout(f, (char *)f->tp.buf, f->tp.pool);
+        tl = tape_layout_of(tape, (char *)tape->buf, tape->pool);
         s = tl.s;
     } else {
         Scratch sz = layout(nullptr, n, lat.allow_rot, true, f32, m2);
@@ -949,15 +960,53 @@ fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params
     mark(f, 3, stream);
     f->timed = f->timing;
     f->extra_timed = lat.allow_rot != 0;
-    if (tape) f->tp.valid = true;
+    if (tape) tape->valid = true;
     return FQSL_OK;
 }
 
-fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, const fqsl_out *out,
-                     cudaStream_t stream, bool face_plane, const char *who, bool tape = false)
+// The tape of a call that asks for one (params->tape = 1): the caller's
+// *tape_or_null, or a new tape stored there. *created tells a failing call to
+// release a tape it made.
+fqsl_status take_tape(const fqsl_params *p, fqsl_tape *tape_or_null, fqsl_tape *t, bool *created, const char *who)
 {
-    std::lock_guard<std::mutex> lock(f->mu);
-    return run_qmap_locked(f, lat0, p, out, stream, face_plane, tape, who);
+    *t = nullptr;
+    *created = false;
+    if (!p->tape) return FQSL_OK;
+    if (p->method != 1) return fail(FQSL_ERR_UNSUPPORTED, "%s: the step tape needs Method I", who);
+    if (!tape_or_null) return fail(FQSL_ERR_ARG, "%s: params.tape = 1 needs a tape (tape_or_null)", who);
+    if (!*tape_or_null) {
+        *tape_or_null = new (std::nothrow) fqsl_tape_s();
+        if (!*tape_or_null) return fail(FQSL_ERR_OOM, "%s: host allocation of the tape", who);
+        *created = true;
+    }
+    *t = *tape_or_null;
+    return FQSL_OK;
+}
+
+void release_tape(fqsl_tape t)
+{
+    if (!t) return;
+    cudaFree(t->buf);
+    cudaFree(t->work);
+    delete t;
+}
+
+fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, const fqsl_out *out,
+                     cudaStream_t stream, bool face_plane, const char *who, fqsl_tape *tape_or_null)
+{
+    fqsl_tape t = nullptr;
+    bool created = false;
+    fqsl_status st = take_tape(p, tape_or_null, &t, &created, who);
+    if (st != FQSL_OK) return st;
+    {
+        std::lock_guard<std::mutex> lock(f->mu);
+        st = run_qmap_locked(f, lat0, p, out, stream, face_plane, t, who);
+    }
+    if (st != FQSL_OK && created) {
+        release_tape(t);
+        *tape_or_null = nullptr;
+    }
+    return st;
 }
 
 }  // namespace
@@ -965,7 +1014,8 @@ fqsl_status run_qmap(fqsl_field f, const Lattice &lat0, const fqsl_params *p, co
 extern "C" {
 
 fqsl_status fqsl_qmap_plane(fqsl_field f, const double origin[3], const double u[3], const double v[3],
-                            long long nu, long long nv, const fqsl_params *p, const fqsl_out *out, void *cuda_stream)
+                            long long nu, long long nv, const fqsl_params *p, const fqsl_out *out,
+                            fqsl_tape *tape_or_null, void *cuda_stream)
 {
     g_err.clear();
     const char *who = "fqsl_qmap_plane";
@@ -1009,12 +1059,12 @@ fqsl_status fqsl_qmap_plane(fqsl_field f, const double origin[3], const double u
         const double xi = (origin[a] - f->g.o[a]) / f->g.d[a];
         face_plane = (xi == 0.0) || (xi == (double)(na - 1));
     }
-    if (p->tape && p->method != 1) return fail(FQSL_ERR_UNSUPPORTED, "%s: the step tape needs Method I", who);
-    return run_qmap(f, lat, p, out, (cudaStream_t)cuda_stream, face_plane, who, p->tape != 0);
+    return run_qmap(f, lat, p, out, (cudaStream_t)cuda_stream, face_plane, who, tape_or_null);
 }
 
 fqsl_status fqsl_qmap_volume(fqsl_field f, const double origin[3], const double step[3], long long nx, long long ny,
-                             long long nz, const fqsl_params *p, const fqsl_out *out, void *cuda_stream)
+                             long long nz, const fqsl_params *p, const fqsl_out *out, fqsl_tape *tape_or_null,
+                             void *cuda_stream)
 {
     g_err.clear();
     const char *who = "fqsl_qmap_volume";
@@ -1040,8 +1090,7 @@ fqsl_status fqsl_qmap_volume(fqsl_field f, const double origin[3], const double 
     lat.dv = step[1];
     lat.drot = fmin(step[0], step[1]);
     lat.normal_axis = 2;
-    if (p->tape && p->method != 1) return fail(FQSL_ERR_UNSUPPORTED, "%s: the step tape needs Method I", who);
-    return run_qmap(f, lat, p, out, (cudaStream_t)cuda_stream, false, who, p->tape != 0);
+    return run_qmap(f, lat, p, out, (cudaStream_t)cuda_stream, false, who, tape_or_null);
 }
 
 fqsl_status fqsl_twist(fqsl_field f, const double *seeds_dev, long long n, const fqsl_params *p, const fqsl_out *out,
@@ -1508,14 +1557,15 @@ extern "C" fqsl_status fqsl_batch_destroy(fqsl_batch b)
 }
 
 // ---------------------------------------------------------------------------
-// fqsl_backward: reverse mode of the field's last taped plane map
+// fqsl_backward: reverse mode of a taped plane or volume map
 // ---------------------------------------------------------------------------
-extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const double *dTw_dev, void *dB_dev,
-                                     fqsl_dtype db_dtype, void *cuda_stream)
+extern "C" fqsl_status fqsl_backward(fqsl_field f, fqsl_tape tp, const double *dQ_dev, const double *dTw_dev,
+                                     void *dB_dev, fqsl_dtype db_dtype, void *cuda_stream)
 {
     g_err.clear();
     const char *who = "fqsl_backward";
     if (!f) return fail(FQSL_ERR_ARG, "%s: NULL field", who);
+    if (!tp) return fail(FQSL_ERR_ARG, "%s: NULL tape", who);
     if (!dB_dev) return fail(FQSL_ERR_ARG, "%s: dB_dev is NULL", who);
     if (db_dtype != FQSL_F32 && db_dtype != FQSL_F64)
         return fail(FQSL_ERR_ARG, "%s: db_dtype must be FQSL_F32 or FQSL_F64", who);
@@ -1524,28 +1574,30 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
         return fail(FQSL_ERR_ARG, "%s: dQ_dev and dTw_dev must be 8-byte aligned", who);
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     std::lock_guard<std::mutex> lock(f->mu);
-    if (!f->tp.valid) return fail(FQSL_ERR_ARG, "%s: no taped map on this field (params.tape = 1)", who);
-    if (f->tp.gen != f->gen)
-        return fail(FQSL_ERR_ARG, "%s: the field was updated after its taped map (trace it again)", who);
-    const fqsl_params p = f->tp.p;
+    if (!tp->valid) return fail(FQSL_ERR_ARG, "%s: the tape holds no complete taped map", who);
+    if (tp->field != f || tp->field_serial != f->serial)
+        return fail(FQSL_ERR_ARG, "%s: the tape was recorded on another field", who);
+    if (tp->gen != f->gen)
+        return fail(FQSL_ERR_ARG, "%s: the field was updated after the taped map (trace it again)", who);
+    const fqsl_params p = tp->p;
     // the pool of the taped call must have held every chunk; if not, trace the
     // same map again with a larger pool (the map is deterministic)
     unsigned long long used = 0;
     for (int attempt = 0;; attempt++) {
-        TapeLayout tl = field_tape_layout(f, (char *)f->tp.buf, f->tp.pool);
+        TapeLayout tl = tape_layout_of(tp, (char *)tp->buf, tp->pool);
         cudaError_t e = cudaMemcpyAsync(&used, tl.ctr, sizeof used, cudaMemcpyDeviceToHost, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) return cuda_fail(e, who);
-        if (used <= (unsigned long long)f->tp.pool) break;
+        if (used <= (unsigned long long)tp->pool) break;
         if (attempt >= 2) return fail(FQSL_ERR_CUDA, "%s: step tape pool still exhausted after re-tracing", who);
-        f->tp.pool = (long long)(used + used / 4 + 1024);
-        const Lattice lat = f->tp.lat;
+        tp->pool = (long long)(used + used / 4 + 1024);
+        const Lattice lat = tp->lat;
         const fqsl_out none{};
-        fqsl_status st = run_qmap_locked(f, lat, &p, &none, stream, f->tp.face_plane, true, who);
+        fqsl_status st = run_qmap_locked(f, lat, &p, &none, stream, tp->face_plane, tp, who);
         if (st != FQSL_OK) return st;
     }
-    TapeLayout tl = field_tape_layout(f, (char *)f->tp.buf, f->tp.pool);
-    const Lattice &lat = f->tp.lat;
+    TapeLayout tl = tape_layout_of(tp, (char *)tp->buf, tp->pool);
+    const Lattice &lat = tp->lat;
     const long long n = lat.n1 * lat.n2 * lat.n3;
     const size_t nodes = (size_t)f->g.nx * f->g.ny * f->g.nz;
     const int rp = reverse_precision_of(p);
@@ -1559,30 +1611,30 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
                  bk = align_up((size_t)used * K * 15 * rs), bb = align_up((size_t)used * K * 3 * rs),
                  bi = align_up((size_t)used * sizeof(int4)), bs = align_up((size_t)used * K * sizeof(int32_t));
     const size_t wbytes = bx + bj + bk + bb + bi + bs;
-    if (wbytes > f->tp.work_cap) {
+    if (wbytes > tp->work_cap) {
         cudaError_t e0 = cudaDeviceSynchronize();
         if (e0 == cudaSuccess) {
-            cudaFree(f->tp.work);
-            f->tp.work = nullptr;
-            f->tp.work_cap = 0;
-            e0 = cudaMalloc(&f->tp.work, wbytes);
+            cudaFree(tp->work);
+            tp->work = nullptr;
+            tp->work_cap = 0;
+            e0 = cudaMalloc(&tp->work, wbytes);
         }
         if (e0 != cudaSuccess) {
             cudaGetLastError();
             return cuda_fail(e0, "fqsl_backward: work arrays");
         }
-        f->tp.work_cap = wbytes;
+        tp->work_cap = wbytes;
     }
     cudaError_t e = cudaMemsetAsync(tl.xbar, 0, (size_t)(3 * tl.halves) * sizeof(double), stream);
     if (e == cudaSuccess && tl.xseed) e = cudaMemsetAsync(tl.xseed, 0, (size_t)(24 * n) * sizeof(double), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(tl.acc, 0, nodes * 8 * (acc64 ? 8 : 4), stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tl.ctr + 1, 0, 3 * sizeof(unsigned long long), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tl.ctr + 1, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     AdjArgs a{};
     a.f = f->g;
     a.f.rec = rp == FQSL_F64 ? f->rec64 : f->rec32;
     a.f.grad = nullptr;
-    a.f.err = tl.ctr + 2;
+    a.f.err = f->counters + 4;  // the field's record of failed index checks (fqsl_field_check)
     a.p = dev_params(&p);
     a.lat = lat;
     a.rec = tl.s.rec;
@@ -1601,13 +1653,13 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
         a.xseed = tl.xseed;
     }
     a.chunks = (long long)used;
-    a.wx = f->tp.work;
-    a.wj = (char *)f->tp.work + bx;
-    a.wk = (char *)f->tp.work + bx + bj;
-    a.wb = (char *)f->tp.work + bx + bj + bk;
-    a.cinfo = (int4 *)((char *)f->tp.work + bx + bj + bk + bb);
-    a.steps = (int32_t *)((char *)f->tp.work + bx + bj + bk + bb + bi);
-    a.nsteps = tl.ctr + 1;  // cleared with the check words below
+    a.wx = tp->work;
+    a.wj = (char *)tp->work + bx;
+    a.wk = (char *)tp->work + bx + bj;
+    a.wb = (char *)tp->work + bx + bj + bk;
+    a.cinfo = (int4 *)((char *)tp->work + bx + bj + bk + bb);
+    a.steps = (int32_t *)((char *)tp->work + bx + bj + bk + bb + bi);
+    a.nsteps = tl.ctr + 1;  // cleared above
     e = launch_q_vjp(a, mode, tape_f64, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
     mark(f, 0, stream);
@@ -1623,22 +1675,30 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, const double *dQ_dev, const d
     return FQSL_OK;
 }
 
-extern "C" fqsl_status fqsl_tape_export(fqsl_field f, int cap, int32_t *nsteps_dev, int32_t *code_dev,
+extern "C" fqsl_status fqsl_tape_export(fqsl_tape tp, int cap, int32_t *nsteps_dev, int32_t *code_dev,
                                         double *hx_dev, double *h_dev, void *cuda_stream)
 {
     g_err.clear();
     const char *who = "fqsl_tape_export";
-    if (!f) return fail(FQSL_ERR_ARG, "%s: NULL field", who);
+    if (!tp) return fail(FQSL_ERR_ARG, "%s: NULL tape", who);
     if (cap < 0) return fail(FQSL_ERR_ARG, "%s: cap < 0", who);
     if (!nsteps_dev || !code_dev || !hx_dev || (cap > 0 && !h_dev))
         return fail(FQSL_ERR_ARG, "%s: NULL output", who);
-    std::lock_guard<std::mutex> lock(f->mu);
-    if (!f->tp.valid) return fail(FQSL_ERR_ARG, "%s: no taped map on this field (params.tape = 1)", who);
-    TapeLayout tl = field_tape_layout(f, (char *)f->tp.buf, f->tp.pool);
-    const long long n = f->tp.lat.n1 * f->tp.lat.n2 * f->tp.lat.n3;
-    cudaError_t e = launch_tape_export(tl.tape, f->tp.p.precision == FQSL_F64, tl.s.rec.st, 2 * n, cap, nsteps_dev,
+    if (!tp->valid) return fail(FQSL_ERR_ARG, "%s: the tape holds no complete taped map", who);
+    TapeLayout tl = tape_layout_of(tp, (char *)tp->buf, tp->pool);
+    const long long n = tp->lat.n1 * tp->lat.n2 * tp->lat.n3;
+    cudaError_t e = launch_tape_export(tl.tape, tp->p.precision == FQSL_F64, tl.s.rec.st, 2 * n, cap, nsteps_dev,
                                        code_dev, hx_dev, h_dev, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
+    return FQSL_OK;
+}
+
+extern "C" fqsl_status fqsl_tape_destroy(fqsl_tape tp)
+{
+    g_err.clear();
+    if (!tp) return fail(FQSL_ERR_ARG, "fqsl_tape_destroy: NULL tape");
+    cudaDeviceSynchronize();
+    release_tape(tp);
     return FQSL_OK;
 }
 
@@ -1666,27 +1726,13 @@ extern "C" fqsl_status fqsl_field_check(fqsl_field f, void *cuda_stream)
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return cuda_fail(e, "fqsl_field_check");
     std::lock_guard<std::mutex> lock(f->mu);
-    if (f->tp.valid && f->tp.buf) {
-        // index checks of the adjoint kernels (cleared here)
-        unsigned long long w[2] = {0, 0};
-        unsigned long long *ctr = field_tape_layout(f, (char *)f->tp.buf, f->tp.pool).ctr;
-        e = cudaMemcpy(w, ctr + 2, sizeof w, cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess && w[1]) e = cudaMemset(ctr + 2, 0, sizeof w);
-        if (e != cudaSuccess) return cuda_fail(e, "fqsl_field_check");
-        if (w[1])
-            return fail(FQSL_ERR_CUDA, "fqsl_field_check: %llu failed index checks in the adjoint kernels, first: "
-                                       "check %llu, value %lld", w[1], w[0] >> 56,
-                        (long long)(w[0] & ((1ull << 56) - 1)));
-    }
-    return FQSL_OK;
-}
-
-
-extern "C" fqsl_status fqsl_tape_id(fqsl_field f, unsigned long long *id)
-{
-    g_err.clear();
-    if (!f || !id) return fail(FQSL_ERR_ARG, "fqsl_tape_id: NULL argument");
-    std::lock_guard<std::mutex> lock(f->mu);
-    *id = f->tp.valid ? f->tp.id : 0;
+    // index checks of the adjoint kernels (cleared here)
+    unsigned long long w[2] = {0, 0};
+    e = cudaMemcpy(w, f->counters + 4, sizeof w, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && w[1]) e = cudaMemset(f->counters + 4, 0, sizeof w);
+    if (e != cudaSuccess) return cuda_fail(e, "fqsl_field_check");
+    if (w[1])
+        return fail(FQSL_ERR_CUDA, "fqsl_field_check: %llu failed index checks in the adjoint kernels, first: "
+                                   "check %llu, value %lld", w[1], w[0] >> 56, (long long)(w[0] & ((1ull << 56) - 1)));
     return FQSL_OK;
 }

@@ -23,7 +23,7 @@ EXPORTS = ("fqsl_params_default", "fqsl_version", "fqsl_last_error", "fqsl_field
            "fqsl_qmap_plane", "fqsl_qmap_volume", "fqsl_twist", "fqsl_field_check", "fqsl_field_set_timing",
            "fqsl_field_times", "fqsl_field_update", "fqsl_qmap_plane_static", "fqsl_batch_create", "fqsl_batch_run",
            "fqsl_batch_destroy", "fqsl_backward", "fqsl_loss_logq_tw", "fqsl_tape_export",
-           "fqsl_tape_id", "fqsl_field_create_rect")
+           "fqsl_tape_destroy", "fqsl_field_create_rect")
 STATIC_MAX_SEEDS = 65536
 
 
@@ -67,11 +67,12 @@ def load(path: str = LIB_PATH):
     lib.fqsl_field_create_rect.argtypes = [P, C.c_int, C.c_longlong, C.c_longlong, C.c_longlong, P, P, P, C.c_uint,
                                            P, C.POINTER(P)]
     lib.fqsl_field_destroy.argtypes = [P]
-    lib.fqsl_qmap_plane.argtypes = [P, P, P, P, C.c_longlong, C.c_longlong, C.POINTER(Params), C.POINTER(Out), P]
+    lib.fqsl_qmap_plane.argtypes = [P, P, P, P, C.c_longlong, C.c_longlong, C.POINTER(Params), C.POINTER(Out),
+                                    C.POINTER(P), P]
     lib.fqsl_qmap_plane_static.argtypes = [P, P, P, P, C.c_longlong, C.c_longlong, C.POINTER(Params),
                                            C.POINTER(Out), P]
     lib.fqsl_qmap_volume.argtypes = [P, P, P, C.c_longlong, C.c_longlong, C.c_longlong, C.POINTER(Params),
-                                     C.POINTER(Out), P]
+                                     C.POINTER(Out), C.POINTER(P), P]
     lib.fqsl_twist.argtypes = [P, P, C.c_longlong, C.POINTER(Params), C.POINTER(Out), P]
     lib.fqsl_field_check.argtypes = [P, P]
     lib.fqsl_field_set_timing.argtypes = [P, C.c_int]
@@ -80,9 +81,9 @@ def load(path: str = LIB_PATH):
     lib.fqsl_batch_destroy.argtypes = [P]
     lib.fqsl_field_update.argtypes = [P, P, C.c_int, P]
     lib.fqsl_field_times.argtypes = [P, C.POINTER(C.c_float * 3)]
-    lib.fqsl_backward.argtypes = [P, P, P, P, C.c_int, P]
+    lib.fqsl_backward.argtypes = [P, P, P, P, P, C.c_int, P]
     lib.fqsl_tape_export.argtypes = [P, C.c_int, P, P, P, P, P]
-    lib.fqsl_tape_id.argtypes = [P, C.POINTER(C.c_ulonglong)]
+    lib.fqsl_tape_destroy.argtypes = [P]
     lib.fqsl_loss_logq_tw.argtypes = [C.c_longlong, P, P, P, P, P, C.c_double, P, P, P, P, P]
     for name in EXPORTS:
         if name not in ("fqsl_params_default", "fqsl_version", "fqsl_last_error"):
@@ -183,6 +184,7 @@ class Field:
         _check(_lib.fqsl_field_update(self._h, C.c_void_p(B.data_ptr()), F32 if B.dtype == torch.float32 else F64,
                                       _stream(stream)))
         self._keep = B
+        self._packed_from = None  # QTwPlane sets it after its own update
 
     def set_timing(self, enable: bool = True):
         """Record CUDA events around this field's kernels on each call's stream."""
@@ -195,6 +197,10 @@ class Field:
         return tuple(float(v) for v in ms)
 
     def close(self):
+        t = getattr(self, "_default_tape", None)
+        if t is not None:
+            t.close()
+            self._default_tape = None
         if getattr(self, "_h", None):
             _lib.fqsl_field_destroy(self._h)
             self._h = None
@@ -225,13 +231,59 @@ def _out_struct(out):
     return o
 
 
-def qmap_plane(field: Field, origin, u, v, nu: int, nv: int, p: Params | None = None, out=None, stream=None):
+class Tape:
+    """A taped map (fqsl_tape): made by the first qmap_plane / qmap_volume call
+    with params(tape=1) that is given it, re-recorded by later ones, read by
+    backward() and tape_export(); its device memory is released by close()."""
+
+    def __init__(self):
+        self._h = C.c_void_p()
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("the tape holds no map yet")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.fqsl_tape_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _tape_arg(field, p, tape):
+    """The tape of a taped call: the one given, else the field's own default
+    tape (made once, re-recorded by every taped call given no tape, so that a
+    loop reuses its device memory). The field remembers the last tape used for
+    backward() and tape_export() called without one."""
+    if not p.tape:
+        return None, None
+    t = tape
+    if t is None:
+        t = getattr(field, "_default_tape", None)
+        if t is None:
+            t = field._default_tape = Tape()
+    field.last_tape = t
+    return t, C.byref(t._h)
+
+
+def qmap_plane(field: Field, origin, u, v, nu: int, nv: int, p: Params | None = None, out=None, stream=None,
+               tape: Tape | None = None):
     """Q, Tw, length, footpoints, faces, status, steps on the plane lattice
-    origin + (i+1/2) u + (j+1/2) v (index i + nu j)."""
+    origin + (i+1/2) u + (j+1/2) v (index i + nu j). With params(tape=1) the
+    map is also recorded into ``tape`` (if None, the field's default tape),
+    which becomes ``field.last_tape``."""
     p = p or params()
     out = out or alloc_out(nu * nv)
+    _, tp = _tape_arg(field, p, tape)
     _check(_lib.fqsl_qmap_plane(field.handle, _vec3(origin), _vec3(u), _vec3(v), nu, nv, C.byref(p),
-                                C.byref(_out_struct(out)), _stream(stream)))
+                                C.byref(_out_struct(out)), tp, _stream(stream)))
     return out
 
 
@@ -249,12 +301,13 @@ def qmap_plane_static(field: Field, origin, u, v, nu: int, nv: int, p: Params | 
 
 
 def qmap_volume(field: Field, origin, step, nx: int, ny: int, nz: int, p: Params | None = None, out=None,
-                stream=None):
+                stream=None, tape: Tape | None = None):
     """The same on the volume lattice origin + (i+1/2, j+1/2, k+1/2) * step."""
     p = p or params()
     out = out or alloc_out(nx * ny * nz)
+    _, tp = _tape_arg(field, p, tape)
     _check(_lib.fqsl_qmap_volume(field.handle, _vec3(origin), _vec3(step), nx, ny, nz, C.byref(p),
-                                 C.byref(_out_struct(out)), _stream(stream)))
+                                 C.byref(_out_struct(out)), tp, _stream(stream)))
     return out
 
 
@@ -328,11 +381,19 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
-def backward(field: Field, dQ=None, dTw=None, dB=None, dtype=None, stream=None):
-    """Accumulate (d(Q,Tw)/dB)^T (dQ, dTw) of the field's last taped plane map
-    (qmap_plane with params(tape=1)) into dB (a B-shaped CUDA tensor; allocated
-    as zeros of ``dtype``, default float32, when not given). dQ, dTw: CUDA
-    float64 tensors of the map's seed count, or None."""
+def _tape_of(field, tape):
+    t = tape if tape is not None else getattr(field, "last_tape", None)
+    if t is None:
+        raise RuntimeError("no taped map: trace one with params(tape=1) first")
+    return t
+
+
+def backward(field: Field, dQ=None, dTw=None, dB=None, dtype=None, stream=None, tape: Tape | None = None):
+    """Accumulate (d(Q,Tw)/dB)^T (dQ, dTw) of the taped map in ``tape``
+    (default: the field's last taped map) into dB (a B-shaped CUDA tensor;
+    allocated as zeros of ``dtype``, default float32, when not given). dQ, dTw:
+    CUDA float64 tensors of the map's seed count, or None."""
+    t = _tape_of(field, tape)
     nx, ny, nz = field.n
     if dB is None:
         dB = torch.zeros((nz, ny, nx, 3), dtype=dtype or torch.float32, device="cuda")
@@ -342,28 +403,22 @@ def backward(field: Field, dQ=None, dTw=None, dB=None, dtype=None, stream=None):
         raise ValueError("dB must be float32 or float64")
     dQ = None if dQ is None else dQ.to(torch.float64).contiguous()
     dTw = None if dTw is None else dTw.to(torch.float64).contiguous()
-    _check(_lib.fqsl_backward(field.handle, _ptr(dQ), _ptr(dTw), C.c_void_p(dB.data_ptr()),
+    _check(_lib.fqsl_backward(field.handle, t.handle, _ptr(dQ), _ptr(dTw), C.c_void_p(dB.data_ptr()),
                               F32 if dB.dtype == torch.float32 else F64, _stream(stream)))
     return dB
 
 
-def tape_id(field: Field) -> int:
-    """Number of the field's current taped map (0 if none)."""
-    v = C.c_ulonglong()
-    _check(_lib.fqsl_tape_id(field.handle, C.byref(v)))
-    return int(v.value)
-
-
-def tape_export(field: Field, n_seeds: int, cap: int = 4096, stream=None):
-    """The step sequence of the field's last taped plane map (fqsl_tape_export):
-    dict of CUDA tensors nsteps (2n), code (2n), hx (2n), h (2n, cap); half-line
-    2 s + e is end e + 1 of seed s."""
+def tape_export(field: Field, n_seeds: int, cap: int = 4096, stream=None, tape: Tape | None = None):
+    """The step sequence of a taped map (default: the field's last;
+    fqsl_tape_export): dict of CUDA tensors nsteps (2n), code (2n), hx (2n),
+    h (2n, cap); half-line 2 s + e is end e + 1 of seed s."""
+    t = _tape_of(field, tape)
     dev = "cuda"
     m = 2 * n_seeds
     out = dict(nsteps=torch.empty(m, dtype=torch.int32, device=dev), code=torch.empty(m, dtype=torch.int32, device=dev),
                hx=torch.empty(m, dtype=torch.float64, device=dev),
                h=torch.zeros((m, max(cap, 1)), dtype=torch.float64, device=dev))
-    _check(_lib.fqsl_tape_export(field.handle, cap, _ptr(out["nsteps"]), _ptr(out["code"]), _ptr(out["hx"]),
+    _check(_lib.fqsl_tape_export(t.handle, cap, _ptr(out["nsteps"]), _ptr(out["code"]), _ptr(out["hx"]),
                                  _ptr(out["h"]), _stream(stream)))
     return out
 
@@ -390,26 +445,28 @@ def loss_logq_tw(Q, Tw, Q_target, Tw_target, status=None, w_tw: float = 0.1, str
 class QTwPlane(torch.autograd.Function):
     """(Q, Tw) of a plane map as a differentiable function of B:
     ``Q, Tw = QTwPlane.apply(B, field, origin, u, v, nu, nv, p)``. The forward
-    repacks B into ``field`` and traces the map with the step tape; the backward
-    runs fqsl_backward (frozen step sequence; Method I). Q of rotated or
-    NaN seeds carries no gradient."""
+    packs B into ``field`` (unless the field already holds this very tensor
+    unchanged) and traces the map into a tape of its own; the backward runs
+    fqsl_backward on that tape (frozen step sequence; Method I). Several maps of
+    one field (other planes) can therefore sit in one graph. Q of rotated or NaN
+    seeds carries no gradient."""
 
     @staticmethod
     def forward(ctx, B, field, origin, u, v, nu, nv, p=None):
         p = p or params()
         q = Params.from_buffer_copy(p)
         q.tape = 1
-        field.update(B.detach())
-        out = qmap_plane(field, origin, u, v, nu, nv, q)
+        key = (B.data_ptr(), B._version, tuple(B.shape), B.dtype)
+        if getattr(field, "_packed_from", None) != key:
+            field.update(B.detach())
+            field._packed_from = key
+        ctx.tape = Tape()
+        out = qmap_plane(field, origin, u, v, nu, nv, q, tape=ctx.tape)
         ctx.field = field
-        ctx.tape = tape_id(field)
         ctx.b_dtype = B.dtype
         return out["Q"], out["Tw"]
 
     @staticmethod
     def backward(ctx, gQ, gTw):
-        if tape_id(ctx.field) != ctx.tape:
-            raise RuntimeError("QTwPlane.backward: the field traced another taped map after this one; "
-                               "use one Field per differentiable map")
-        dB = backward(ctx.field, gQ, gTw, dtype=ctx.b_dtype)
+        dB = backward(ctx.field, gQ, gTw, dtype=ctx.b_dtype, tape=ctx.tape)
         return dB, None, None, None, None, None, None, None

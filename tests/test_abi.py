@@ -26,7 +26,7 @@ def declared_symbols(header="fqsl.h", api="FQSL_API"):
 def test_header_declares_entry_points():
     names = declared_symbols()
     for n in ("fqsl_field_create", "fqsl_qmap_plane", "fqsl_qmap_volume", "fqsl_twist", "fqsl_field_destroy",
-              "fqsl_last_error"):
+              "fqsl_last_error", "fqsl_backward", "fqsl_tape_destroy"):
         assert n in names
 
 
@@ -91,7 +91,15 @@ def test_host_argument_errors(lib):
     assert lib.fqsl_field_create(fake, 0, big, big, big, o, d, 1, None, C.byref(h)) == 1
     assert b"too large" in lib.fqsl_last_error()
     lib.fqsl_qmap_plane.restype = C.c_int
-    assert lib.fqsl_qmap_plane(None, o, o, o, C.c_longlong(1), C.c_longlong(1), None, None, None) == 1
+    assert lib.fqsl_qmap_plane(None, o, o, o, C.c_longlong(1), C.c_longlong(1), None, None, None, None) == 1
+    # the tape handle's entry points refuse NULL handles on the host
+    lib.fqsl_tape_destroy.restype = C.c_int
+    lib.fqsl_backward.restype = C.c_int
+    lib.fqsl_tape_export.restype = C.c_int
+    assert lib.fqsl_tape_destroy(None) == 1
+    assert lib.fqsl_backward(None, None, None, None, C.c_void_p(4096), 0, None) == 1
+    assert lib.fqsl_tape_export(None, 0, C.c_void_p(4096), C.c_void_p(4096), C.c_void_p(4096), None, None) == 1
+    assert b"NULL tape" in lib.fqsl_last_error()
 
 
 def test_stretched_grid_argument_errors(lib):

@@ -336,11 +336,24 @@ def test_autograd_function(fq, small):
 
 
 def test_backward_argument_errors(fq, small):
+    import ctypes as C
+
+    from paper_2208_12569_gb300 import fqsl as raw
+
     B, _, grid = small
     field = _field(fq, B, grid)
-    with pytest.raises(fq.FqslError) as ei:
+    with pytest.raises(RuntimeError, match="no taped map"):
         fq.backward(field, None, None)
-    assert ei.value.status == 1 and "taped" in str(ei.value)
+    dB = torch.zeros(B.shape, dtype=torch.float64, device="cuda")
+    assert raw._lib.fqsl_backward(field.handle, None, None, None, C.c_void_p(dB.data_ptr()), fq.F64, None) == 1
+    assert b"NULL tape" in raw._lib.fqsl_last_error()
+    # params.tape = 1 needs somewhere to put the tape
+    p = fq.params(tape=1)
+    out = fq.alloc_out(PLANE16[3] * PLANE16[4])
+    assert raw._lib.fqsl_qmap_plane(field.handle, raw._vec3(PLANE16[0]), raw._vec3(PLANE16[1]),
+                                    raw._vec3(PLANE16[2]), PLANE16[3], PLANE16[4], C.byref(p),
+                                    C.byref(raw._out_struct(out)), None, None) == 1
+    assert b"tape_or_null" in raw._lib.fqsl_last_error()
     with pytest.raises(fq.FqslError) as ei:
         fq.qmap_plane(field, *PLANE16, fq.params(tape=1, method=2))
     assert ei.value.status == 5
@@ -412,17 +425,80 @@ def test_volume_gradient_matches_oracle(fq, small, scheme):
 def test_backward_refuses_a_stale_tape(fq, small):
     B, _, grid = small
     field = _field(fq, B, grid)
-    assert fq.tape_id(field) == 0
-    fq.qmap_plane(field, *PLANE16, fq.params(tape=1))
-    assert fq.tape_id(field) == 1
-    fq.qmap_plane(field, *PLANE16, fq.params())  # an untaped map leaves the tape
-    assert fq.tape_id(field) == 1
-    fq.qmap_plane(field, *PLANE16, fq.params(tape=1))
-    assert fq.tape_id(field) == 2
+    t = fq.Tape()
+    fq.qmap_plane(field, *PLANE16, fq.params(tape=1), tape=t)
+    fq.qmap_plane(field, *PLANE16, fq.params())  # an untaped map leaves the tape alone
+    fq.backward(field, None, None, tape=t)
+    field.check()
     field.update(torch.from_numpy(B).cuda())
     with pytest.raises(fq.FqslError) as ei:
-        fq.backward(field, None, None)
+        fq.backward(field, None, None, tape=t)
     assert ei.value.status == 1 and "updated" in str(ei.value)
+    # a tape recorded on another field is refused
+    other = _field(fq, B, grid)
+    t2 = fq.Tape()
+    fq.qmap_plane(other, *PLANE16, fq.params(tape=1), tape=t2)
+    with pytest.raises(fq.FqslError) as ei:
+        fq.backward(field, None, None, tape=t2)
+    assert ei.value.status == 1 and "another field" in str(ei.value)
+    # a tape outlives its field for export (and is released on its own)
+    other.close()
+    ex = fq.tape_export(None, PLANE16[3] * PLANE16[4], cap=0, tape=t2)
+    assert int(ex["nsteps"].sum()) > 0
+    t.close()
+    t2.close()
+
+
+def test_two_taped_maps_on_one_field(fq, small):
+    """Two taped maps of one field held at once in their own tapes (Q on two
+    planes in one loss): each backward, taken in reverse order, gives that
+    map's FP64 gradient equal to the oracle adjoint; an untaped map, a third
+    taped map in another tape and the first backward in between change nothing."""
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    w = {}
+    tapes = {}
+    for name, plane, seed in (("z0", PLANE16, 31), ("xz", XZ, 32)):
+        w[name] = _weights(seed, plane[3] * plane[4])
+        tapes[name] = fq.Tape()
+        fq.qmap_plane(field, *plane, fq.params(precision="f64", tape=1), tape=tapes[name])
+    fq.qmap_plane(field, *PATCH, fq.params(precision="f64"))
+    t3 = fq.Tape()
+    fq.qmap_plane(field, *PATCH, fq.params(precision="f32", tape=1), tape=t3)
+    grads = {}
+    for name in ("xz", "z0"):
+        wq, wt = w[name]
+        dB = fq.backward(field, torch.from_numpy(wq).cuda(), torch.from_numpy(wt).cuda(), dtype=torch.float64,
+                         tape=tapes[name])
+        field.check()
+        grads[name] = dB.cpu().numpy()
+    for name, plane in (("z0", PLANE16), ("xz", XZ)):
+        ref, _ = adj.vjp(B, grid, *plane, *w[name], oracle.params())
+        assert np.linalg.norm(ref) > 0
+        assert _rel(grads[name], ref) < 1e-10, name
+    # the same weights again on the same tape: the same gradient
+    wq, wt = w["z0"]
+    again = fq.backward(field, torch.from_numpy(wq).cuda(), torch.from_numpy(wt).cuda(), dtype=torch.float64,
+                        tape=tapes["z0"]).cpu().numpy()
+    assert _rel(again, grads["z0"]) < 1e-13
+    for t in (*tapes.values(), t3):
+        t.close()
+
+
+def test_autograd_two_planes_in_one_loss(fq, small):
+    # QTwPlane keeps its own tape: Q on two planes of one field in one graph
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    p = fq.params(precision="f64")
+    Bv = torch.from_numpy(B).cuda().requires_grad_(True)
+    (wq1, wt1), (wq2, wt2) = _weights(41, PLANE16[3] * PLANE16[4]), _weights(42, XZ[3] * XZ[4])
+    Q1, Tw1 = fq.QTwPlane.apply(Bv, field, *PLANE16, p)
+    Q2, Tw2 = fq.QTwPlane.apply(Bv, field, *XZ, p)
+    c = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
+    torch.autograd.backward([Q1, Tw1, Q2, Tw2], [c(wq1), c(wt1), c(wq2), c(wt2)])
+    r1, _ = adj.vjp(B, grid, *PLANE16, wq1, wt1, oracle.params())
+    r2, _ = adj.vjp(B, grid, *XZ, wq2, wt2, oracle.params())
+    assert _rel(Bv.grad.cpu().numpy(), r1 + r2) < 1e-10
 
 
 def test_full_size_workload_sampled(fq):
