@@ -701,6 +701,19 @@ cudaError_t launch_trace_m2(fqsl_field f, const fqsl_params *p, const TraceArgs 
                                     : launch_trace_dev_f32(a, p->gradb_way, (int)grid, kTraceBlock, s);
 }
 
+// Does the plane x_a = x (a plane lattice's S0 normal to axis a) lie on a
+// face of the box? On a uniform grid its index coordinate is 0 or n - 1; on a
+// stretched grid x is the first or the last node coordinate. (The tracer
+// decides rotation seed by seed; this only spares the rotated-S0 buffers and
+// launch of a face plane.)
+bool on_box_face(const FieldView &g, int a, double x)
+{
+    if (g.rect) return x == g.lo64[a] || x == g.hi64[a];
+    const int na = a == 0 ? g.nx : (a == 1 ? g.ny : g.nz);
+    const double xi = (x - g.o[a]) / g.d[a];
+    return xi == 0.0 || xi == (double)(na - 1);
+}
+
 void cross(const double *a, const double *b, double *c)
 {
     c[0] = a[1] * b[2] - a[2] * b[1];
@@ -1054,10 +1067,7 @@ fqsl_status fqsl_qmap_plane(fqsl_field f, const double origin[3], const double u
     lat.normal_axis = zeros == 2 ? axis : -1;
     bool face_plane = false;
     if (lat.normal_axis >= 0) {
-        const int a = lat.normal_axis;
-        const int na = a == 0 ? f->g.nx : (a == 1 ? f->g.ny : f->g.nz);
-        const double xi = (origin[a] - f->g.o[a]) / f->g.d[a];
-        face_plane = (xi == 0.0) || (xi == (double)(na - 1));
+        face_plane = on_box_face(f->g, lat.normal_axis, origin[lat.normal_axis]);
     }
     return run_qmap(f, lat, p, out, (cudaStream_t)cuda_stream, face_plane, who, tape_or_null);
 }
@@ -1229,10 +1239,7 @@ extern "C" fqsl_status fqsl_qmap_plane_static(fqsl_field f, const double origin[
     lat.normal_axis = zeros == 2 ? axis : -1;
     bool face_plane = false;
     if (lat.normal_axis >= 0) {
-        const int a = lat.normal_axis;
-        const int na = a == 0 ? f->g.nx : (a == 1 ? f->g.ny : f->g.nz);
-        const double xi = (origin[a] - f->g.o[a]) / f->g.d[a];
-        face_plane = (xi == 0.0) || (xi == (double)(na - 1));
+        face_plane = on_box_face(f->g, lat.normal_axis, origin[lat.normal_axis]);
     }
     const long long n = nu * nv;
     index_lattice(f, lat);
@@ -1362,10 +1369,7 @@ fqsl_status plane_lattice(const fqsl_field f, const fqsl_plane &pl, const fqsl_p
     lat.normal_axis = zeros == 2 ? axis : -1;
     bool face_plane = false;
     if (lat.normal_axis >= 0) {
-        const int a = lat.normal_axis;
-        const int na = a == 0 ? f->g.nx : (a == 1 ? f->g.ny : f->g.nz);
-        const double xi = (origin[a] - f->g.o[a]) / f->g.d[a];
-        face_plane = (xi == 0.0) || (xi == (double)(na - 1));
+        face_plane = on_box_face(f->g, lat.normal_axis, origin[lat.normal_axis]);
     }
     index_lattice(f, lat);
     lat.tiles_u = (lat.n1 + kTileU - 1) / kTileU;
