@@ -42,14 +42,14 @@ __device__ __forceinline__ void face_axes(int face, int &r0, int &r1)
 
 // B_ax at index position p (traced precision), its gradient in index
 // coordinates, and the scatter of bnb * e_ax onto the nodes
-template <typename T, typename AccT>
+template <typename T, typename AccT, bool RECT = false>
 __device__ __forceinline__ double bn_vjp(const FieldView &f, const T p[3], int ax, double bnb, double g[3], AccT *acc)
 {
-    const Cell<T> c = cell_of(f, p[0], p[1], p[2]);
+    const Cell<T> c = cellg<RECT>(f, p[0], p[1], p[2]);
     g[0] = g[1] = g[2] = 0.0;
     if (!cell_ok(f, c.base)) return 0.0;
     T V[6], dV[3][6];
-    interp_d(f, c, V, dV);
+    interp_d<T, RECT>(f, c, V, dV);
     g[0] = (double)dV[0][ax];
     g[1] = (double)dV[1][ax];
     g[2] = (double)dV[2][ax];
@@ -61,7 +61,16 @@ __device__ __forceinline__ double bn_vjp(const FieldView &f, const T p[3], int a
     return (double)V[ax];
 }
 
-template <typename T, typename AccT, typename TT>
+// the state coordinates of a physical seed position (a stretched grid's FP64
+// state is the physical position itself)
+template <typename T, bool RECT>
+__device__ __forceinline__ T seed_state(const FieldView &f, double r, int a)
+{
+    if constexpr (RECT && sizeof(T) == 8) return (T)r;
+    else return (T)((r - f.o[a]) / f.d[a]);
+}
+
+template <typename T, typename AccT, typename TT, bool RECT = false>
 __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
 {
     const Lattice &G = A.lat;
@@ -153,8 +162,8 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
             for (int a = 0; a < 3; a++) pe[e][a] = (T)XE[4 * (2 * idx + e) + a];
         double g1[3], g2[3];
         const int ax1 = fe2[0] >> 1, ax2 = fe2[1] >> 1;
-        const double bn1 = bn_vjp<T, AccT>(f, pe[0], ax1, 0.0, g1, acc);
-        const double bn2 = bn_vjp<T, AccT>(f, pe[1], ax2, 0.0, g2, acc);
+        const double bn1 = bn_vjp<T, AccT, RECT>(f, pe[0], ax1, 0.0, g1, acc);
+        const double bn2 = bn_vjp<T, AccT, RECT>(f, pe[1], ax2, 0.0, g2, acc);
         const double bn0 = R.bn0[idx];
         const double sc = fabs(bn1 * bn2) / (bn0 * bn0);
         const double Nb = qb * sc, sb = qb * N;
@@ -188,8 +197,8 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
         const double bn1b = sb * sg1 * fabs(bn2) / (bn0 * bn0);
         const double bn2b = sb * sg2 * fabs(bn1) / (bn0 * bn0);
         const double bn0b = -2.0 * sb * fabs(bn1 * bn2) / (bn0 * bn0 * bn0);
-        bn_vjp<T, AccT>(f, pe[0], ax1, bn1b, g1, acc);
-        bn_vjp<T, AccT>(f, pe[1], ax2, bn2b, g2, acc);
+        bn_vjp<T, AccT, RECT>(f, pe[0], ax1, bn1b, g1, acc);
+        bn_vjp<T, AccT, RECT>(f, pe[1], ax2, bn2b, g2, acc);
         for (int a = 0; a < 3; a++) {
             atomicAdd(A.xbar + 3 * (2 * idx + 0) + a, bn1b * g1[a]);
             atomicAdd(A.xbar + 3 * (2 * idx + 1) + a, bn2b * g2[a]);
@@ -203,17 +212,18 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
             p0[1] = (T)sd.y;
             p0[2] = (T)sd.z;
         } else {
-            // the FP64 tracer's seed: (r0 - o)/d as written
+            // the FP64 tracer's seed: (r0 - o)/d as written (on a stretched
+            // grid the physical seed)
             double r0[3];
             trace::lattice_seed(G, i, j, k, r0);
-            for (int a = 0; a < 3; a++) p0[a] = (T)((r0[a] - f.o[a]) / f.d[a]);
+            for (int a = 0; a < 3; a++) p0[a] = seed_state<T, RECT>(f, r0[a], a);
         }
-        const Cell<T> c0 = cell_of(f, p0[0], p0[1], p0[2]);
+        const Cell<T> c0 = cellg<RECT>(f, p0[0], p0[1], p0[2]);
         if (!cell_ok(f, c0.base)) continue;
         double nb[3] = {G.n0[0], G.n0[1], G.n0[2]};
         if (rot) {
             T V[6], dV[3][6];
-            interp_d(f, c0, V, dV);
+            interp_d<T, RECT>(f, c0, V, dV);
             const double B0[3] = {(double)V[0], (double)V[1], (double)V[2]};
             const double nB = sqrt(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
             if (!(nB > 0.0)) continue;
@@ -229,7 +239,7 @@ __global__ void __launch_bounds__(128) k_q_vjp(const AdjArgs A)
 // seeds (pass B) are carried back through the frame to B at the seed's cell.
 // u = t/|t| with t = bhat x e_m (m: the smallest |bhat_m|, held fixed), v =
 // bhat x u. One thread per rotated seed.
-template <typename T, typename AccT>
+template <typename T, typename AccT, bool RECT = false>
 __global__ void __launch_bounds__(128) k_frame_vjp(const AdjArgs A)
 {
     const Lattice &G = A.lat;
@@ -257,13 +267,14 @@ __global__ void __launch_bounds__(128) k_frame_vjp(const AdjArgs A)
             continue;
         }
         const long long i = idx % G.n1, j = (idx / G.n1) % G.n2, k = idx / (G.n1 * G.n2);
-        double r0[3], xi[3];
+        double r0[3];
+        T xi[3];
         trace::lattice_seed(G, i, j, k, r0);
-        for (int a = 0; a < 3; a++) xi[a] = (r0[a] - f.o[a]) / f.d[a];
-        const Cell<T> c = cell_of(f, (T)xi[0], (T)xi[1], (T)xi[2]);
+        for (int a = 0; a < 3; a++) xi[a] = seed_state<T, RECT>(f, r0[a], a);
+        const Cell<T> c = cellg<RECT>(f, xi[0], xi[1], xi[2]);
         if (!cell_ok(f, c.base)) continue;
         T V[6], dV[3][6];
-        interp_d(f, c, V, dV);
+        interp_d<T, RECT>(f, c, V, dV);
         const double B0[3] = {(double)V[0], (double)V[1], (double)V[2]};
         const double nB = sqrt(B0[0] * B0[0] + B0[1] * B0[1] + B0[2] * B0[2]);
         if (!(nB > 0.0)) continue;
@@ -370,6 +381,65 @@ __global__ void __launch_bounds__(256) k_curl_adjoint(const AccT *__restrict__ a
         const AccT by = p[1] + DT[0][2] - DT[2][0];
         const AccT bz = p[2] + DT[1][0] - DT[0][1];
         using W = decltype(AccT{} + OutT{});  // the wider of the two
+        dB[3 * node + 0] = (OutT)((W)dB[3 * node + 0] + (W)bx);
+        dB[3 * node + 1] = (OutT)((W)dB[3 * node + 1] + (W)by);
+        dB[3 * node + 2] = (OutT)((W)dB[3 * node + 2] + (W)bz);
+    }
+}
+
+// The same on a stretched grid: the curl grid's derivative along an axis of n
+// nodes at row i is the three-point stencil of a non-uniform axis with the
+// coefficients co[3 i ..] (field.cu): interior rows on nodes i-1, i, i+1; row 0
+// on nodes 0, 1, 2 (third coefficient negated); row n-1 on nodes n-3, n-2, n-1
+// (second negated); (f1 - f0)/(x1 - x0) on an axis of 2 nodes. Coefficient of
+// node jn in row i:
+__device__ __forceinline__ double stencil_rect(int i, int jn, int n, const double *__restrict__ X,
+                                               const double *__restrict__ co)
+{
+    if (n == 2) return (jn == 1 ? 1.0 : -1.0) / (X[1] - X[0]);
+    const double c0 = co[3 * i], c1 = co[3 * i + 1], c2 = co[3 * i + 2];
+    if (i == 0) return jn == 0 ? c0 : (jn == 1 ? c1 : (jn == 2 ? -c2 : 0.0));
+    if (i == n - 1) return jn == n - 3 ? c0 : (jn == n - 2 ? -c1 : (jn == n - 1 ? c2 : 0.0));
+    return jn == i - 1 ? c0 : (jn == i ? c1 : (jn == i + 1 ? c2 : 0.0));
+}
+
+template <typename AccT, typename OutT>
+__global__ void __launch_bounds__(256) k_curl_adjoint_rect(const AccT *__restrict__ acc, const FieldView g,
+                                                           OutT *__restrict__ dB)
+{
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const long long total = (long long)nx * ny * nz;
+    const long long sy = nx, sz = (long long)nx * ny;
+    for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < total;
+         node += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(node % nx), iy = (int)((node / nx) % ny), iz = (int)(node / sz);
+        const int n[3] = {nx, ny, nz}, idx[3] = {ix, iy, iz};
+        const long long stride[3] = {1, sy, sz};
+        // DT[axis][c] = (D_axis^T dJ_c)(node): the rows whose stencil reaches this node
+        AccT DT[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            AccT t0 = 0, t1 = 0, t2 = 0;
+            const int j0 = idx[a], na = n[a];
+            const int lo = j0 - 2 < 0 ? 0 : j0 - 2, hi = j0 + 2 > na - 1 ? na - 1 : j0 + 2;
+            for (int i = lo; i <= hi; i++) {
+                const AccT cf = (AccT)stencil_rect(i, j0, na, g.x64[a], g.dco[a]);
+                if (cf == (AccT)0) continue;
+                const AccT *q = acc + 8 * (node + (long long)(i - j0) * stride[a]);
+                t0 += cf * q[3];
+                t1 += cf * q[4];
+                t2 += cf * q[5];
+            }
+            DT[a][0] = t0;
+            DT[a][1] = t1;
+            DT[a][2] = t2;
+        }
+        // Jx = Dy Bz - Dz By, Jy = Dz Bx - Dx Bz, Jz = Dx By - Dy Bx
+        const AccT *p = acc + 8 * node;
+        const AccT bx = p[0] + DT[2][1] - DT[1][2];
+        const AccT by = p[1] + DT[0][2] - DT[2][0];
+        const AccT bz = p[2] + DT[1][0] - DT[0][1];
+        using W = decltype(AccT{} + OutT{});
         dB[3 * node + 0] = (OutT)((W)dB[3 * node + 0] + (W)bx);
         dB[3 * node + 1] = (OutT)((W)dB[3 * node + 1] + (W)by);
         dB[3 * node + 2] = (OutT)((W)dB[3 * node + 2] + (W)bz);
@@ -491,10 +561,20 @@ void q_vjp_mode(const AdjArgs &a, int mode, unsigned g, cudaStream_t s)
     else adj::k_q_vjp<double, double, TT><<<g, 128, 0, s>>>(a);
 }
 
-template <typename T, typename AccT>
+// stretched grids: the forward's state convention (FP64 physical, FP32
+// relative to the first node) is the reverse sweep's, so the tape and the
+// sweep share their precision (the host enforces it)
+void q_vjp_rect(const AdjArgs &a, int mode, unsigned g, cudaStream_t s)
+{
+    if (mode == 0) adj::k_q_vjp<float, float, float, true><<<g, 128, 0, s>>>(a);
+    else if (mode == 1) adj::k_q_vjp<float, double, float, true><<<g, 128, 0, s>>>(a);
+    else adj::k_q_vjp<double, double, double, true><<<g, 128, 0, s>>>(a);
+}
+
+template <typename T, typename AccT, bool RECT = false>
 void frame_pass(const AdjArgs &a, cudaStream_t s)
 {
-    if (a.rot_count) adj::k_frame_vjp<T, AccT><<<adj::grid_for(a.n, 128, 4), 128, 0, s>>>(a);
+    if (a.rot_count) adj::k_frame_vjp<T, AccT, RECT><<<adj::grid_for(a.n, 128, 4), 128, 0, s>>>(a);
 }
 
 template <typename TT>
@@ -509,14 +589,21 @@ void reverse_mode(const AdjArgs &a, int mode, cudaStream_t s)
 cudaError_t launch_q_vjp(const AdjArgs &a, int mode, bool tape_f64, cudaStream_t s)
 {
     const unsigned g = adj::grid_for(a.n, 128, 16);
-    if (tape_f64) q_vjp_mode<double>(a, mode, g, s);
+    if (a.f.rect) q_vjp_rect(a, mode, g, s);
+    else if (tape_f64) q_vjp_mode<double>(a, mode, g, s);
     else q_vjp_mode<float>(a, mode, g, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reverse(const AdjArgs &a, int mode, bool tape_f64, cudaStream_t s)
 {
-    if (a.chunks > 0) {
+    if (a.chunks > 0 && a.f.rect) {
+        const cudaError_t e = launch_reverse_rect(a, mode, s);
+        if (e != cudaSuccess) return e;
+        if (mode == 0) frame_pass<float, float, true>(a, s);
+        else if (mode == 1) frame_pass<float, double, true>(a, s);
+        else frame_pass<double, double, true>(a, s);
+    } else if (a.chunks > 0) {
         if (a.p.scheme == 1) {
             const cudaError_t e = launch_reverse_rk38(a, mode, tape_f64, s);
             if (e != cudaSuccess) return e;
@@ -538,6 +625,20 @@ cudaError_t launch_curl_adjoint(const void *acc, bool acc64, const FieldView &g,
 {
     const long long total = (long long)g.nx * g.ny * g.nz;
     const unsigned grid = adj::grid_for(total, 256, 8);
+    if (g.rect) {
+        if (acc64) {
+            if (dt == FQSL_F32)
+                adj::k_curl_adjoint_rect<double, float><<<grid, 256, 0, s>>>((const double *)acc, g, (float *)dB);
+            else
+                adj::k_curl_adjoint_rect<double, double><<<grid, 256, 0, s>>>((const double *)acc, g, (double *)dB);
+        } else {
+            if (dt == FQSL_F32)
+                adj::k_curl_adjoint_rect<float, float><<<grid, 256, 0, s>>>((const float *)acc, g, (float *)dB);
+            else
+                adj::k_curl_adjoint_rect<float, double><<<grid, 256, 0, s>>>((const float *)acc, g, (double *)dB);
+        }
+        return cudaGetLastError();
+    }
     if (acc64) {
         if (dt == FQSL_F32)
             adj::k_curl_adjoint<double, float><<<grid, 256, 0, s>>>((const double *)acc, g.nx, g.ny, g.nz, g.d[0],

@@ -47,10 +47,14 @@ __device__ __forceinline__ bool cell_ok(const FieldView &f, long long base)
 // ---------------------------------------------------------------------------
 // Cell and fractions as the tracer's gather forms them: cell = floor(xi)
 // clamped to [0, n-2]; weight of corner (m, q, p) = prod of (frac or 1-frac).
+// On a stretched grid (Sec. 2.2) the cell is the one the tracer's search finds
+// (a discrete choice, not differentiated) and the weights are Eq. w0's in
+// physical coordinates, whose derivative along axis a is -+ 1/width_a.
 template <typename T>
 struct Cell {
     long long base;  // node of corner (0, 0, 0)
     T w0[3], w1[3];  // weights of the lower and upper corner along each axis
+    T rw[3];         // stretched grid: 1 / width of the cell along each axis
 };
 
 __device__ __forceinline__ Cell<float> cell_of(const FieldView &f, float x, float y, float z)
@@ -82,6 +86,73 @@ __device__ __forceinline__ Cell<double> cell_of(const FieldView &f, double x, do
     return c;
 }
 
+// stretched grid, FP32: the forward's cell records {x_c, x_{c+1}, 1/width}
+// relative to the first node; the lower corner's weight (x_{c+1} - x)/width
+__device__ __forceinline__ Cell<float> cell_of_rect(const FieldView &f, float x, float y, float z)
+{
+    trace::RectCells<float> rc;
+    trace::rect_cells(f, x, y, z, rc);
+    Cell<float> c;
+    c.base = ((long long)rc.c[2] * f.ny + rc.c[1]) * f.nx + rc.c[0];
+    const float p[3] = {x, y, z};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        c.w0[a] = (rc.r[a].y - p[a]) * rc.r[a].z;
+        c.w1[a] = 1.f - c.w0[a];
+        c.rw[a] = rc.r[a].z;
+    }
+    return c;
+}
+
+// stretched grid, FP64: physical coordinates, Eqs. w0, w1 as the forward
+// evaluates them
+__device__ __forceinline__ Cell<double> cell_of_rect(const FieldView &f, double x, double y, double z)
+{
+    trace::RectCells<double> rc;
+    trace::rect_cells(f, x, y, z, rc);
+    Cell<double> c;
+    c.base = ((long long)rc.c[2] * f.ny + rc.c[1]) * f.nx + rc.c[0];
+    const double p[3] = {x, y, z};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double2 cr = rc.r[a];
+        c.w0[a] = (cr.y - p[a]) / (cr.y - cr.x);
+        c.w1[a] = 1.0 - c.w0[a];
+        c.rw[a] = 1.0 / (cr.y - cr.x);
+    }
+    return c;
+}
+
+template <bool RECT, typename T>
+__device__ __forceinline__ Cell<T> cellg(const FieldView &f, T x, T y, T z)
+{
+    if constexpr (RECT) return cell_of_rect(f, x, y, z);
+    else return cell_of(f, x, y, z);
+}
+
+// The step's scale per axis, fixed at its start (the tracer's step_dd): FP64
+// the spacing or, on a stretched grid, the widths of the start point's cell;
+// FP32 their reciprocals.
+template <bool RECT, typename T>
+__device__ __forceinline__ void step_scale(const FieldView &f, T x, T y, T z, T dd[3])
+{
+    if constexpr (RECT) {
+        trace::RectCells<T> rc;
+        trace::rect_cells(f, x, y, z, rc);
+        trace::dd_of(rc, dd);
+    } else {
+        trace::step_dd<T, false>(f, x, y, z, dd);
+    }
+}
+
+// 1 / scale: bt_a = B_a rho_a
+template <typename T>
+__device__ __forceinline__ T rho_of(T dd)
+{
+    if constexpr (sizeof(T) == 8) return (T)1 / dd;
+    else return dd;
+}
+
 __device__ __forceinline__ void load6(const FieldView &f, long long node, float v[6])
 {
     trace::load_rec32((const char *)f.rec + (size_t)node * 32u, v[0], v[1], v[2], v[3], v[4], v[5]);
@@ -92,8 +163,9 @@ __device__ __forceinline__ void load6(const FieldView &f, long long node, double
     trace::load_node(f, node, v[0], v[1], v[2], v[3], v[4], v[5]);
 }
 
-// node of corner (m, q, p) and its weight and weight gradient
-template <typename T>
+// node of corner (m, q, p) and its weight and weight gradient (in state
+// coordinates: index units, or physical on a stretched grid)
+template <typename T, bool RECT = false>
 __device__ __forceinline__ long long corner(const FieldView &f, const Cell<T> &c, int m, int q, int p, T &w, T dw[3])
 {
     const T wx = m ? c.w1[0] : c.w0[0];
@@ -103,11 +175,16 @@ __device__ __forceinline__ long long corner(const FieldView &f, const Cell<T> &c
     dw[0] = (m ? (T)1 : (T)-1) * wy * wz;
     dw[1] = (q ? (T)1 : (T)-1) * wx * wz;
     dw[2] = (p ? (T)1 : (T)-1) * wx * wy;
+    if constexpr (RECT) {
+        dw[0] *= c.rw[0];
+        dw[1] *= c.rw[1];
+        dw[2] *= c.rw[2];
+    }
     return c.base + (long long)p * f.nx * f.ny + (long long)q * f.nx + m;
 }
 
 // V = (B, curl B) at the cell position and dV[a][c] = d V_c / d xi_a
-template <typename T>
+template <typename T, bool RECT = false>
 __device__ __forceinline__ void interp_d(const FieldView &f, const Cell<T> &c, T V[6], T dV[3][6])
 {
 #pragma unroll
@@ -122,7 +199,7 @@ __device__ __forceinline__ void interp_d(const FieldView &f, const Cell<T> &c, T
 #pragma unroll
             for (int p = 0; p < 2; p++) {
                 T w, dw[3], v[6];
-                const long long node = corner(f, c, m, q, p, w, dw);
+                const long long node = corner<T, RECT>(f, c, m, q, p, w, dw);
                 load6(f, node, v);
 #pragma unroll
                 for (int k = 0; k < 6; k++) {
@@ -196,17 +273,61 @@ struct V3 {
 // Stage VJP. ax < 0: the adjoints of F and dtw are
 // (kb, twb); ax >= 0 (exit step): kb and twb are the adjoints of K = F/F_ax
 // and dtw/F_ax, converted with the stage's own F_ax. All-zero adjoints
-// return at once.
-template <typename T, typename AccT>
-__device__ __forceinline__ V3<T> stage_vjp(const FieldView &f, T sgn, T px, T py, T pz, int ax, T kb0, T kb1, T kb2,
-                                        T twb, AccT *acc)
+// return at once. RECT (stretched grid, Sec. 2.3): F = sgn B/|bt| with bt_a =
+// B_a/D_a, D (dd) the widths of the step's start cell, held fixed.
+template <typename T, typename AccT, bool RECT = false>
+__device__ __forceinline__ V3<T> stage_vjp(const FieldView &f, const T dd[3], T sgn, T px, T py, T pz, int ax, T kb0,
+                                           T kb1, T kb2, T twb, AccT *acc)
 {
     V3<T> r = {(T)0, (T)0, (T)0};
     if (kb0 == (T)0 && kb1 == (T)0 && kb2 == (T)0 && twb == (T)0) return r;
-    const Cell<T> c = cell_of(f, px, py, pz);
+    const Cell<T> c = cellg<RECT>(f, px, py, pz);
     if (!cell_ok(f, c.base)) return r;
     T V[6], dV[3][6];
-    interp_d(f, c, V, dV);
+    interp_d<T, RECT>(f, c, V, dV);
+    if constexpr (RECT) {
+        const T rho[3] = {rho_of(dd[0]), rho_of(dd[1]), rho_of(dd[2])};
+        const T bt[3] = {V[0] * rho[0], V[1] * rho[1], V[2] * rho[2]};
+        const T bb = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
+        const T BB = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+        const T nbt = sqrt(bb), m = sqrt(BB);
+        const T c4 = (T)12.566370614359172 * m * nbt;  // 4 pi |B| |bt|
+        const T JB = V[3] * V[0] + V[4] * V[1] + V[5] * V[2];
+        const T dtw = JB / c4;
+        const T F[3] = {sgn * V[0] / nbt, sgn * V[1] / nbt, sgn * V[2] / nbt};
+        T Fb[3] = {kb0, kb1, kb2}, dtwb = twb;
+        if (ax >= 0) {
+            const T fa = F[ax];
+            const T g = (kb0 * F[0] + kb1 * F[1] + kb2 * F[2] + twb * dtw) / (fa * fa);
+            Fb[0] = kb0 / fa;
+            Fb[1] = kb1 / fa;
+            Fb[2] = kb2 / fa;
+            Fb[ax] -= g;
+            dtwb = twb / fa;
+        }
+        // F_a = sgn B_a / |bt|: Bbar_j = sgn (Fbar_j / |bt| - (Fbar . B) rho_j^2 B_j / |bt|^3)
+        const T FB = Fb[0] * V[0] + Fb[1] * V[1] + Fb[2] * V[2];
+        T Vb[6];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const T r2 = rho[a] * rho[a] * V[a];
+            Vb[a] = sgn * (Fb[a] / nbt - FB * r2 / (nbt * bb)) + dtwb * (V[3 + a] / c4 - dtw * V[a] / BB - dtw * r2 / bb);
+            Vb[3 + a] = dtwb * V[a] / c4;
+        }
+        T pb[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            T sacc = (T)0;
+#pragma unroll
+            for (int k = 0; k < 6; k++) sacc += dV[a][k] * Vb[k];
+            pb[a] = sacc;
+        }
+        scatter(f, c, Vb, acc);
+        r.x = pb[0];
+        r.y = pb[1];
+        r.z = pb[2];
+        return r;
+    }
     const T rd[3] = {inv_spacing<T>(f, 0), inv_spacing<T>(f, 1), inv_spacing<T>(f, 2)};
     const T bt[3] = {V[0] * rd[0], V[1] * rd[1], V[2] * rd[2]};
     const T bb = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
@@ -257,18 +378,25 @@ struct Rhs {
     T F[3], dl, dtw;
 };
 
-// right-hand side in the tracer's own form (the same function the forward ran)
-__device__ __forceinline__ Rhs<float> rhs_fwd(const FieldView &f, float sgn, float x, float y, float z)
+// right-hand side in the tracer's own form (the same function the forward
+// ran; dd: the step's scale from step_scale, used on a stretched grid)
+template <bool RECT = false>
+__device__ __forceinline__ Rhs<float> rhs_fwd(const FieldView &f, const float dd[3], float sgn, float x, float y,
+                                              float z)
 {
     float o[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    if (cell_ok(f, cell_of(f, x, y, z).base)) trace::rhs(f, f.rd, sgn, x, y, z, o);
+    if constexpr (RECT) trace::rhs_rect(f, dd, sgn, x, y, z, o);
+    else if (cell_ok(f, cell_of(f, x, y, z).base)) trace::rhs(f, f.rd, sgn, x, y, z, o);
     return Rhs<float>{{o[0], o[1], o[2]}, o[3], o[4]};
 }
 
-__device__ __forceinline__ Rhs<double> rhs_fwd(const FieldView &f, double sgn, double x, double y, double z)
+template <bool RECT = false>
+__device__ __forceinline__ Rhs<double> rhs_fwd(const FieldView &f, const double dd[3], double sgn, double x, double y,
+                                               double z)
 {
     double o[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    if (cell_ok(f, cell_of(f, x, y, z).base)) trace::rhs(f, f.d, sgn, x, y, z, o);
+    if constexpr (RECT) trace::rhs_rect(f, dd, sgn, x, y, z, o);
+    else if (cell_ok(f, cell_of(f, x, y, z).base)) trace::rhs(f, f.d, sgn, x, y, z, o);
     return Rhs<double>{{o[0], o[1], o[2]}, o[3], o[4]};
 }
 
@@ -279,8 +407,9 @@ __device__ __forceinline__ Rhs<double> rhs_fwd(const FieldView &f, double sgn, d
 // is the ax index coordinate (h = target - x_ax, RHS divided by its ax
 // component). Writes the end state and, per stage, the (divided) derivative
 // and Tw integrand k[s] = {F (3), dtw}.
-template <typename T, int SCH>
-__device__ __forceinline__ void advance(const FieldView &f, T sgn, const T x[3], T h, int ax, T x4[3], T k[5][4])
+template <typename T, int SCH, bool RECT = false>
+__device__ __forceinline__ void advance(const FieldView &f, const T dd[3], T sgn, const T x[3], T h, int ax, T x4[3],
+                                        T k[5][4])
 {
     constexpr bool kF64 = sizeof(T) == 8;
     T a4[3] = {0, 0, 0};
@@ -294,7 +423,7 @@ __device__ __forceinline__ void advance(const FieldView &f, T sgn, const T x[3],
             py += c * k[r][1];
             pz += c * k[r][2];
         }
-        const Rhs<T> o = rhs_fwd(f, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz);
+        const Rhs<T> o = rhs_fwd<RECT>(f, dd, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz);
         T F[4] = {o.F[0], o.F[1], o.F[2], o.dtw};
         if (ax >= 0) {
             const T fa = o.F[ax];
@@ -323,12 +452,13 @@ __device__ __forceinline__ void advance(const FieldView &f, T sgn, const T x[3],
 // keeping them per step): on entry xb is the adjoint of the end state and wb
 // that of the Tw increment; on exit xb is the adjoint of x through the stages
 // and, for the exit step (ax >= 0), *db the adjoint of its length h.
-template <typename T, typename AccT, int SCH>
+template <typename T, typename AccT, int SCH, bool RECT = false>
 __device__ __forceinline__ void step_reverse(const FieldView &f, T sgn, const T x[3], T h, int ax, T xb[3], T wb,
                                              T *db, AccT *acc)
 {
-    T k[5][4], x4[3];
-    advance<T, SCH>(f, sgn, x, h, ax, x4, k);
+    T k[5][4], x4[3], dd[3];
+    step_scale<RECT>(f, x[0], x[1], x[2], dd);
+    advance<T, SCH, RECT>(f, dd, sgn, x, h, ax, x4, k);
     T kb[5][3];
     T d = 0;
 #pragma unroll
@@ -349,8 +479,8 @@ __device__ __forceinline__ void step_reverse(const FieldView &f, T sgn, const T 
             py += c * k[r][1];
             pz += c * k[r][2];
         }
-        const V3<T> pb = stage_vjp<T, AccT>(f, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz, ax, kb[s][0],
-                                            kb[s][1], kb[s][2], h * Stages<T, SCH>::b(s) * wb, acc);
+        const V3<T> pb = stage_vjp<T, AccT, RECT>(f, dd, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz, ax,
+                                                  kb[s][0], kb[s][1], kb[s][2], h * Stages<T, SCH>::b(s) * wb, acc);
         xin[0] += pb.x;
         xin[1] += pb.y;
         xin[2] += pb.z;
@@ -389,11 +519,11 @@ __device__ __forceinline__ void step_reverse(const FieldView &f, T sgn, const T 
 // V, dV/dxi at p and, from them, F, dtw and their position Jacobians:
 // Jm[i][j] = dF_i/dp_j, g[j] = d dtw/dp_j. Returns false (values zero) when the
 // cell check fails.
-template <typename T>
-__device__ __forceinline__ bool stage_jac(const FieldView &f, T sgn, T px, T py, T pz, T F[3], T &dtw, T Jm[3][3],
-                                          T g[3])
+template <typename T, bool RECT = false>
+__device__ __forceinline__ bool stage_jac(const FieldView &f, const T dd[3], T sgn, T px, T py, T pz, T F[3], T &dtw,
+                                          T Jm[3][3], T g[3])
 {
-    const Cell<T> c = cell_of(f, px, py, pz);
+    const Cell<T> c = cellg<RECT>(f, px, py, pz);
     if (!cell_ok(f, c.base)) {
 #pragma unroll
         for (int i = 0; i < 3; i++) {
@@ -404,7 +534,36 @@ __device__ __forceinline__ bool stage_jac(const FieldView &f, T sgn, T px, T py,
         return false;
     }
     T V[6], dV[3][6];
-    interp_d(f, c, V, dV);
+    interp_d<T, RECT>(f, c, V, dV);
+    if constexpr (RECT) {
+        // F = sgn B/|bt|, bt_a = B_a rho_a (rho = 1/D of the step's start cell):
+        // dF_i/dp_j = sgn (dB_i/dp_j - B_i q_j / |bt|^2) / |bt|, q_j = sum_b rho_b^2 B_b dB_b/dp_j
+        const T rho[3] = {rho_of(dd[0]), rho_of(dd[1]), rho_of(dd[2])};
+        const T bt[3] = {V[0] * rho[0], V[1] * rho[1], V[2] * rho[2]};
+        const T bb = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
+        const T BB = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+        const T nbt = sqrt(bb), m = sqrt(BB);
+        const T c4 = (T)12.566370614359172 * m * nbt;
+        const T JB = V[3] * V[0] + V[4] * V[1] + V[5] * V[2];
+        dtw = JB / c4;
+        T dB[3], dJ[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            F[a] = sgn * V[a] / nbt;
+            dB[a] = V[3 + a] / c4 - dtw * V[a] / BB - dtw * rho[a] * rho[a] * V[a] / bb;
+            dJ[a] = V[a] / c4;
+        }
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const T q = rho[0] * rho[0] * V[0] * dV[j][0] + rho[1] * rho[1] * V[1] * dV[j][1] +
+                        rho[2] * rho[2] * V[2] * dV[j][2];
+#pragma unroll
+            for (int i = 0; i < 3; i++) Jm[i][j] = sgn * (dV[j][i] - V[i] * q / bb) / nbt;
+            g[j] = dB[0] * dV[j][0] + dB[1] * dV[j][1] + dB[2] * dV[j][2] + dJ[0] * dV[j][3] + dJ[1] * dV[j][4] +
+                   dJ[2] * dV[j][5];
+        }
+        return true;
+    }
     const T rd[3] = {inv_spacing<T>(f, 0), inv_spacing<T>(f, 1), inv_spacing<T>(f, 2)};
     const T bt[3] = {V[0] * rd[0], V[1] * rd[1], V[2] * rd[2]};
     const T bb = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
@@ -436,11 +595,12 @@ __device__ __forceinline__ bool stage_jac(const FieldView &f, T sgn, T px, T py,
 
 // Reverse of an accepted step whose stage derivatives k are known (from
 // pass A1): xb in = adjoint of the end state, out = adjoint of x.
-template <typename T, typename AccT, int SCH>
+template <typename T, typename AccT, int SCH, bool RECT = false>
 __device__ __forceinline__ void step_reverse_k(const FieldView &f, T sgn, const T x[3], T h, const T k[5][3], T xb[3],
                                                T wb, AccT *acc)
 {
-    T kb[5][3];
+    T kb[5][3], dd[3];
+    step_scale<RECT>(f, x[0], x[1], x[2], dd);
 #pragma unroll
     for (int s = 0; s < Stages<T, SCH>::N; s++)
 #pragma unroll
@@ -455,8 +615,8 @@ __device__ __forceinline__ void step_reverse_k(const FieldView &f, T sgn, const 
             py += c * k[r][1];
             pz += c * k[r][2];
         }
-        const V3<T> pb = stage_vjp<T, AccT>(f, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz, -1, kb[s][0],
-                                            kb[s][1], kb[s][2], h * Stages<T, SCH>::b(s) * wb, acc);
+        const V3<T> pb = stage_vjp<T, AccT, RECT>(f, dd, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz, -1,
+                                                  kb[s][0], kb[s][1], kb[s][2], h * Stages<T, SCH>::b(s) * wb, acc);
         xb[0] += pb.x;
         xb[1] += pb.y;
         xb[2] += pb.z;
@@ -521,7 +681,7 @@ __device__ __forceinline__ bool chunk_of(const AdjArgs &A, long long c, long lon
 
 // pass A1: the states and stage derivatives of every chunk, from its
 // checkpoint (the only sequential recompute)
-template <typename T, typename TT, int SCH>
+template <typename T, typename TT, int SCH, bool RECT = false>
 __global__ void __launch_bounds__(128) k_adj_states(const AdjArgs A)
 {
     const Tape &tp = A.tape;
@@ -564,8 +724,9 @@ __global__ void __launch_bounds__(128) k_adj_states(const AdjArgs A)
         wx[1] = x[1];
         wx[2] = x[2];
         for (int i = 0; i < n; i++) {
-            T x4[3], kt[5][4];
-            advance<T, SCH>(A.f, (T)sg, x, (T)H[c * K + i], -1, x4, kt);
+            T x4[3], kt[5][4], dd[3];
+            step_scale<RECT>(A.f, x[0], x[1], x[2], dd);
+            advance<T, SCH, RECT>(A.f, dd, (T)sg, x, (T)H[c * K + i], -1, x4, kt);
 #pragma unroll
             for (int s = 0; s < Stages<T, SCH>::N; s++)
 #pragma unroll
@@ -601,7 +762,7 @@ __device__ __forceinline__ bool step_of(const AdjArgs &A, long long t, long long
 }
 
 // pass A2: each step's Jacobian J^T and Tw gradient (one thread per step)
-template <typename T, typename TT, int SCH>
+template <typename T, typename TT, int SCH, bool RECT = false>
 __global__ void __launch_bounds__(128) k_adj_jac(const AdjArgs A)
 {
     const int K = A.tape.k;
@@ -625,6 +786,9 @@ __global__ void __launch_bounds__(128) k_adj_jac(const AdjArgs A)
         for (int s = 0; s < Stages<T, SCH>::N; s++)
 #pragma unroll
             for (int a = 0; a < 3; a++) k[s][a] = wk[3 * s + a];
+        // the step's scale, fixed at its start (stretched grid: its start cell)
+        T dd[3];
+        step_scale<RECT>(A.f, x[0], x[1], x[2], dd);
         // tangents: P_s = d p_s / d x = I + h sum_r a_sr D_r, D_s = dF(p_s)/dp P_s
         T D[5][3][3], Ds[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gs[3] = {0, 0, 0};
 #pragma unroll
@@ -643,7 +807,7 @@ __global__ void __launch_bounds__(128) k_adj_jac(const AdjArgs A)
                     for (int b = 0; b < 3; b++) P[a][b] += h * cc * D[r][a][b];
             }
             T F[3], dtw, Jm[3][3], g[3];
-            stage_jac(A.f, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz, F, dtw, Jm, g);
+            stage_jac<T, RECT>(A.f, dd, sgn, x[0] + h * px, x[1] + h * py, x[2] + h * pz, F, dtw, Jm, g);
             const T b4 = Stages<T, SCH>::b(s);
 #pragma unroll
             for (int a = 0; a < 3; a++)
@@ -667,7 +831,7 @@ __global__ void __launch_bounds__(128) k_adj_jac(const AdjArgs A)
 
 // pass B: per half-line, the exit step's VJP and the recurrence over its
 // steps; an extra line's half-line also keeps the adjoint of its seed
-template <typename T, typename AccT, typename TT, int SCH>
+template <typename T, typename AccT, typename TT, int SCH, bool RECT = false>
 __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
 {
     const Tape &tp = A.tape;
@@ -704,7 +868,8 @@ __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
         const T sgn = (T)hd.w;
         const int face = code - (chord ? kTapeChord : (clamped ? kTapeExitClamped : kTapeExit));
         const int fax = face >> 1;
-        const T target = (face & 1) ? (T)((fax == 0 ? f.nx : (fax == 1 ? f.ny : f.nz)) - 1) : (T)0;
+        // the face in state coordinates (physical on a stretched grid)
+        const T target = (face & 1) ? trace::hi_of<T, RECT>(f, fax) : trace::lo_of<T, RECT>(f, fax);
         T xb[3];
 #pragma unroll
         for (int a = 0; a < 3; a++) xb[a] = (T)A.xbar[3 * hl + a];
@@ -719,7 +884,9 @@ __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
         if (chord) {
             // end = x + t0 (x4 - x), t0 = (target - x_ax)/(x4_ax - x_ax); Tw gains t0 of the step's increment
             h = (T)((const TT *)tp.xe)[4 * hl + 3];
-            advance<T, SCH>(f, sgn, x, h, -1, x4, kt);
+            T dd[3];
+            step_scale<RECT>(f, x[0], x[1], x[2], dd);
+            advance<T, SCH, RECT>(f, dd, sgn, x, h, -1, x4, kt);
             T dtw = 0;
 #pragma unroll
             for (int s = 0; s < Stages<T, SCH>::N; s++) dtw += Stages<T, SCH>::b(s) * kt[s][3];
@@ -749,7 +916,9 @@ __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
                 // dependence on x_ax remains: d = K(x) . yb + twK(x) wbar
                 // no earlier step: a lattice seed's adjoint is not needed
                 if (hd.y == 0 && tp.prev[hd.x] < 0 && hl < 2 * A.n) continue;
-                const Rhs<T> o = rhs_fwd(f, sgn, x[0], x[1], x[2]);
+                T dd[3];
+                step_scale<RECT>(f, x[0], x[1], x[2], dd);
+                const Rhs<T> o = rhs_fwd<RECT>(f, dd, sgn, x[0], x[1], x[2]);
                 const T fa = o.F[fax];
                 d = (o.F[0] * yb[0] + o.F[1] * yb[1] + o.F[2] * yb[2] + o.dtw * wb) / fa;
                 y[0] = yb[0];
@@ -758,15 +927,17 @@ __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
                 y[fax] -= d;
                 zero = true;
             } else if (clamped) {
-                advance<T, SCH>(f, sgn, x, h, ax, x4, kt);
-                const int nn[3] = {f.nx, f.ny, f.nz};
+                T dd[3];
+                step_scale<RECT>(f, x[0], x[1], x[2], dd);
+                advance<T, SCH, RECT>(f, dd, sgn, x, h, ax, x4, kt);
 #pragma unroll
                 for (int b = 0; b < 3; b++)
-                    if (b != fax && (x4[b] < (T)0 || x4[b] > (T)(nn[b] - 1))) yb[b] = (T)0;
+                    if (b != fax && (x4[b] < trace::lo_of<T, RECT>(f, b) || x4[b] > trace::hi_of<T, RECT>(f, b)))
+                        yb[b] = (T)0;
             }
         }
         if (!zero) {
-            step_reverse<T, AccT, SCH>(f, sgn, x, h, ax, yb, ws, ax >= 0 ? &d : (T *)nullptr, acc);
+            step_reverse<T, AccT, SCH, RECT>(f, sgn, x, h, ax, yb, ws, ax >= 0 ? &d : (T *)nullptr, acc);
 #pragma unroll
             for (int a = 0; a < 3; a++) y[a] = yb[a] + keep[a];
             if (ax >= 0) y[fax] -= d;  // h = target - x_ax
@@ -806,7 +977,7 @@ __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
 
 // pass C: the stage VJPs of every step, given its end-state adjoint (one
 // thread per step)
-template <typename T, typename AccT, typename TT, int SCH>
+template <typename T, typename AccT, typename TT, int SCH, bool RECT = false>
 __global__ void __launch_bounds__(128) k_adj_rev(const AdjArgs A)
 {
     const int K = A.tape.k;
@@ -829,7 +1000,7 @@ __global__ void __launch_bounds__(128) k_adj_rev(const AdjArgs A)
         for (int s = 0; s < Stages<T, SCH>::N; s++)
 #pragma unroll
             for (int a = 0; a < 3; a++) ks[s][a] = wk[3 * s + a];
-        step_reverse_k<T, AccT, SCH>(A.f, (T)sg, WX + (c * (K + 1) + i) * 3, (T)H[j], ks, yb, (T)w, acc);
+        step_reverse_k<T, AccT, SCH, RECT>(A.f, (T)sg, WX + (c * (K + 1) + i) * 3, (T)H[j], ks, yb, (T)w, acc);
     }
 }
 
@@ -853,16 +1024,16 @@ inline unsigned grid_for(long long n, int per_block, int cap_per_sm)
 }
 
 // the reverse sweep's passes A1, A2, B, C of a taped map traced with stage scheme SCH
-template <typename T, typename AccT, typename TT, int SCH>
+template <typename T, typename AccT, typename TT, int SCH, bool RECT = false>
 void reverse_passes(const AdjArgs &a, cudaStream_t s)
 {
     const unsigned gc = grid_for(a.chunks, 128, 16);
     const unsigned gs = grid_for(a.chunks * a.tape.k, 128, 16);
     const unsigned gl = grid_for(2 * a.n, 128, 16);
-    k_adj_states<T, TT, SCH><<<gc, 128, 0, s>>>(a);
-    k_adj_jac<T, TT, SCH><<<gs, 128, 0, s>>>(a);
-    k_adj_lines<T, AccT, TT, SCH><<<gl, 128, 0, s>>>(a);
-    k_adj_rev<T, AccT, TT, SCH><<<gs, 128, 0, s>>>(a);
+    k_adj_states<T, TT, SCH, RECT><<<gc, 128, 0, s>>>(a);
+    k_adj_jac<T, TT, SCH, RECT><<<gs, 128, 0, s>>>(a);
+    k_adj_lines<T, AccT, TT, SCH, RECT><<<gl, 128, 0, s>>>(a);
+    k_adj_rev<T, AccT, TT, SCH, RECT><<<gs, 128, 0, s>>>(a);
 }
 
 }  // namespace adj

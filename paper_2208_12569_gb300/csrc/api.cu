@@ -524,7 +524,16 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
             return fail(FQSL_ERR_ARG, "%s: need 0 <= step_min <= step", who);
     }
     if (p->qperp && p->method != 2) return fail(FQSL_ERR_UNSUPPORTED, "%s: Q_perp needs Method II", who);
-    if (f->g.rect && p->tape) return fail(FQSL_ERR_UNSUPPORTED, "%s: no step tape on a stretched grid", who);
+    if (f->g.rect && p->tape) {
+        // the stretched-grid tape: RKF45, with the reverse sweep in the taped
+        // state's precision (FP64 physical positions, FP32 relative ones)
+        if (p->scheme == 1)
+            return fail(FQSL_ERR_UNSUPPORTED, "%s: no step tape of the fixed-step scheme on a stretched grid", who);
+        const int rp = p->reverse_precision < 0 ? p->precision : p->reverse_precision;
+        if ((rp == FQSL_F64) != (p->precision == FQSL_F64))
+            return fail(FQSL_ERR_UNSUPPORTED, "%s: on a stretched grid the reverse sweep runs in the taped map's "
+                                              "state precision (FP64 with FP64, FP32 or FP32_ACC64 with FP32)", who);
+    }
     return FQSL_OK;
 }
 
@@ -816,7 +825,9 @@ int tape_blocks_per_sm(fqsl_field f, int precision, int src, int p_scheme)
 {
     int &c = f->blocks_cache_tape[p_scheme][precision][src == kSrcExtra ? 1 : 0];
     const bool acc64 = precision == FQSL_F32_ACC64;
-    if (!c && p_scheme == 1)
+    if (!c && f->g.rect)
+        c = precision == FQSL_F64 ? trace_tape_rect_blocks_per_sm_f64(src) : trace_tape_rect_blocks_per_sm_f32(src, acc64);
+    else if (!c && p_scheme == 1)
         c = precision == FQSL_F64 ? trace_tape_rk38_blocks_per_sm_f64(src) : trace_tape_rk38_blocks_per_sm_f32(src, acc64);
     else if (!c)
         c = precision == FQSL_F64 ? trace_tape_blocks_per_sm_f64(src) : trace_tape_blocks_per_sm_f32(src, acc64);
@@ -827,6 +838,9 @@ cudaError_t launch_tape(const TraceArgs &a, const fqsl_params *p, int src, long 
 {
     if (grid < 1) grid = 1;
     const bool acc64 = p->precision == FQSL_F32_ACC64;
+    if (a.f.rect)
+        return p->precision == FQSL_F64 ? launch_trace_tape_rect_f64(a, src, (int)grid, s)
+                                        : launch_trace_tape_rect_f32(a, src, (int)grid, s, acc64);
     if (p->scheme == 1)
         return p->precision == FQSL_F64 ? launch_trace_tape_rk38_f64(a, src, (int)grid, s)
                                         : launch_trace_tape_rk38_f32(a, src, (int)grid, s, acc64);

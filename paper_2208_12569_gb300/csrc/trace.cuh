@@ -1435,7 +1435,6 @@ template <typename T, int SRC, bool ACC, int DEV = 0, bool BATCH = false, bool T
           int SCH = 0>
 __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs &BA)
 {
-    static_assert(!(RECT && TAPE), "stretched grids: no tape");
     constexpr bool SPLIT = TAPE && SRC == kSrcLattice;
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -1504,7 +1503,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                         // items come in 32-lane groups: a tile's direction 0,
                         // then the same tile's direction 1
                         const long long g = item >> 5;
-                        active = init_lattice<T, ACC, DEV>(E, L, ((g >> 1) << 5) | (item & 31), (g & 1) == 0);
+                        active = init_lattice<T, ACC, DEV, RECT>(E, L, ((g >> 1) << 5) | (item & 31), (g & 1) == 0);
                         if (active && (g & 1)) L.end = 1;
                     } else {
                         active = init_lattice<T, ACC, DEV, RECT>(E, L, item);

@@ -47,6 +47,13 @@ int blocks(int src)
     return b > 0 ? b : 1;
 }
 
+// the adjoint's forward pass: lattice or extra lines writing the step tape
+template <int SRC, bool ACC>
+__global__ void __launch_bounds__(kBlock, FQSL_TRACE_F32_MINB) k_trace_tape_rect_f32(const TraceArgs A)
+{
+    trace::trace_body<float, SRC, ACC, 0, false, true, true>(A, BatchArgs{});
+}
+
 __global__ void __launch_bounds__(256) k_seed_prep_rect_f32(const TraceArgs A, long long n)
 {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
@@ -76,6 +83,31 @@ int trace_dev_rect_blocks_per_sm_f32(int way)
     int b = 0;
     if (way == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_dev_rect_f32<1>, kBlock, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_dev_rect_f32<2>, kBlock, 0);
+    return b > 0 ? b : 1;
+}
+
+cudaError_t launch_trace_tape_rect_f32(const TraceArgs &a, int src, int grid, cudaStream_t s, bool acc64)
+{
+    if (src == kSrcExtra) {
+        if (acc64) k_trace_tape_rect_f32<kSrcExtra, true><<<grid, kBlock, 0, s>>>(a);
+        else k_trace_tape_rect_f32<kSrcExtra, false><<<grid, kBlock, 0, s>>>(a);
+    } else {
+        if (acc64) k_trace_tape_rect_f32<kSrcLattice, true><<<grid, kBlock, 0, s>>>(a);
+        else k_trace_tape_rect_f32<kSrcLattice, false><<<grid, kBlock, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+int trace_tape_rect_blocks_per_sm_f32(int src, bool acc64)
+{
+    int b = 0;
+    if (src == kSrcExtra) {
+        if (acc64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_rect_f32<kSrcExtra, true>, kBlock, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_rect_f32<kSrcExtra, false>, kBlock, 0);
+    } else {
+        if (acc64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_rect_f32<kSrcLattice, true>, kBlock, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_rect_f32<kSrcLattice, false>, kBlock, 0);
+    }
     return b > 0 ? b : 1;
 }
 

@@ -20,7 +20,29 @@ __global__ void __launch_bounds__(kBlock) k_trace_dev_rect_f64(const TraceArgs A
 {
     trace::trace_body<double, kSrcLattice, true, WAY, false, false, true>(A, BatchArgs{});
 }
+
+// the adjoint's forward pass: lattice or extra lines writing the step tape
+template <int SRC>
+__global__ void __launch_bounds__(kBlock, FQSL_TRACE_F64_MINB) k_trace_tape_rect_f64(const TraceArgs A)
+{
+    trace::trace_body<double, SRC, true, 0, false, true, true>(A, BatchArgs{});
+}
 }  // namespace
+
+cudaError_t launch_trace_tape_rect_f64(const TraceArgs &a, int src, int grid, cudaStream_t s)
+{
+    if (src == kSrcExtra) k_trace_tape_rect_f64<kSrcExtra><<<grid, kBlock, 0, s>>>(a);
+    else k_trace_tape_rect_f64<kSrcLattice><<<grid, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int trace_tape_rect_blocks_per_sm_f64(int src)
+{
+    int b = 0;
+    if (src == kSrcExtra) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_rect_f64<kSrcExtra>, kBlock, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_rect_f64<kSrcLattice>, kBlock, 0);
+    return b > 0 ? b : 1;
+}
 
 cudaError_t launch_trace_dev_rect_f64(const TraceArgs &a, int way, int grid, cudaStream_t s)
 {

@@ -322,3 +322,144 @@ def test_strongly_stretched_axes_bitwise(fq, oracle_lib):
     assert np.array_equal(g32["status"] & oracle.BAD, r["status"] & oracle.BAD)
     rel = q_rel(g32, r)
     assert np.median(rel[np.isfinite(rel)]) < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# The discrete adjoint on a stretched grid (reading R16 under the frozen step
+# sequence of R13): each step's start-cell widths held fixed, Eq. w0 weights
+# in physical coordinates, the non-uniform three-point curl stencils; against
+# the adjoint oracle's stretched replay (oracle/adjoint.py)
+# ---------------------------------------------------------------------------
+ADJ_N = (24, 22, 16)
+ADJ_HI = (ADJ_N[0] - 1.0, ADJ_N[1] - 1.0, ADJ_N[2] - 1.0)
+ADJ_Z0 = ((0.0, 0.0, 0.0), (ADJ_HI[0] / 12, 0.0, 0.0), (0.0, ADJ_HI[1] / 12, 0.0), 12, 12)
+# an interior xz plane: seeds where |By/B| < 0.05 rotate S0
+ADJ_XZ = ((0.0, ADJ_HI[1] * 0.41, 0.0), (ADJ_HI[0] / 14, 0.0, 0.0), (0.0, 0.0, ADJ_HI[2] / 9), 14, 9)
+
+
+@pytest.fixture(scope="module")
+def adj_mono():
+    grid = synth.stretched_grid(ADJ_N, (0.0, 0.0, 0.0), ADJ_HI, (1.03, 1.02, 1.05))
+    ch = synth.random_charges(np.random.default_rng(5), 6, ((0.0, ADJ_HI[0]), (0.0, ADJ_HI[1])), depth=(2.0, 5.0))
+    return synth.monopole_cube(grid, ch, dtype=np.float64), grid
+
+
+def _gpu_grad(fq, B, grid, plane, wq, wt, dtype=torch.float64, **kw):
+    field = _field(fq, B, grid)
+    t = fq.Tape()
+    out = fq.qmap_plane(field, *plane, fq.params(tape=1, **kw), tape=t)
+    st = out["status"].cpu().numpy()
+    dB = fq.backward(field, torch.from_numpy(wq).cuda(), torch.from_numpy(wt).cuda(), dtype=dtype, tape=t)
+    field.check()
+    g = dB.cpu().numpy().astype(np.float64)
+    t.close()
+    return g, st, field
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("plane", [ADJ_Z0, ADJ_XZ], ids=["z0_plane", "interior_xz_plane"])
+def test_stretched_fp64_gradient_matches_oracle_adjoint(fq, oracle_lib, adj_mono, plane):
+    adj = pytest.importorskip("oracle.adjoint")
+    B, grid = adj_mono
+    m = plane[3] * plane[4]
+    rng = np.random.default_rng(13)
+    wq, wt = rng.standard_normal(m), rng.standard_normal(m)
+    g, st, _ = _gpu_grad(fq, B, grid, plane, wq, wt, precision="f64")
+    ref, log = adj.vjp(B, grid, *plane, wq, wt, oracle.params())
+    assert np.array_equal(st & oracle.BAD, log["status"] & oracle.BAD)
+    assert np.linalg.norm(ref) > 0
+    assert _rel(g, ref) < 1e-10
+    assert np.abs(g - ref).max() < 1e-10 * np.abs(ref).max()
+    if plane is ADJ_XZ:
+        assert (st & fq.LINE_ROTATED).sum() > 0
+
+
+def test_stretched_rotated_seeds_gradient_matches_oracle(fq, oracle_lib, adj_mono):
+    # weights on the usable rotated seeds only: the extra lines, their seed
+    # adjoints and the frame VJP carry the whole gradient
+    adj = pytest.importorskip("oracle.adjoint")
+    B, grid = adj_mono
+    ref_map = oracle.plane(B, grid, *ADJ_XZ, oracle.params())
+    rot = ((ref_map["status"] & oracle.ROTATED) != 0) & np.isfinite(ref_map["Q"])
+    assert rot.sum() >= 3
+    wq = np.where(rot, 1.0 / np.where(rot, ref_map["Q"], 1.0), 0.0)
+    g, _, _ = _gpu_grad(fq, B, grid, ADJ_XZ, wq, 0.0 * wq, precision="f64")
+    ref, _ = adj.vjp(B, grid, *ADJ_XZ, wq, 0.0 * wq, oracle.params())
+    assert np.linalg.norm(ref) > 0
+    assert _rel(g, ref) < 1e-10
+
+
+def test_stretched_fp64_tape_is_the_oracle_step_sequence(fq, oracle_lib, adj_mono):
+    adj = pytest.importorskip("oracle.adjoint")
+    B, grid = adj_mono
+    field = _field(fq, B, grid)
+    t = fq.Tape()
+    fq.qmap_plane(field, *ADJ_Z0, fq.params(precision="f64", tape=1), tape=t)
+    m = ADJ_Z0[3] * ADJ_Z0[4]
+    ex = {k: v.cpu().numpy() for k, v in fq.tape_export(field, m, cap=2048, tape=t).items()}
+    log = adj.lattice_log(B, grid, *ADJ_Z0, oracle.params())
+    code, hh = adj.half_lines(log)
+    for hl in range(2 * m):
+        c = code[hl][code[hl] >= 0]
+        if (log["status"][hl // 2] & oracle.BAD) != 0:
+            assert ex["nsteps"][hl] == 0 and ex["code"][hl] == -1
+            continue
+        n = int(ex["nsteps"][hl])
+        assert n == len(c) - 1 and np.all(c[:-1] == 0)
+        assert ex["code"][hl] == c[-1]
+        assert np.array_equal(ex["h"][hl, :n], hh[hl, :n])
+    t.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "f32acc64"])
+def test_stretched_gradient_orthogonal_to_B(fq, oracle_lib, adj_mono, precision):
+    # B -> c B leaves the frozen-sequence map unchanged, so <J^T w, B> = 0
+    B, grid = adj_mono
+    m = ADJ_Z0[3] * ADJ_Z0[4]
+    rng = np.random.default_rng(17)
+    g, _, _ = _gpu_grad(fq, B, grid, ADJ_Z0, rng.standard_normal(m), rng.standard_normal(m), precision=precision)
+    tol = 1e-11 if precision == "f64" else 1e-4
+    assert abs(np.sum(g * B)) < tol * np.linalg.norm(g) * np.linalg.norm(B)
+
+
+def test_stretched_fp32_gradient_against_oracle(fq, oracle_lib, adj_mono):
+    # the FP32 tracer takes its own step sequence (its controller amplifies
+    # rounding), and the frozen-sequence derivative follows it: the bound is
+    # stated, as on uniform grids
+    adj = pytest.importorskip("oracle.adjoint")
+    B, grid = adj_mono
+    m = ADJ_Z0[3] * ADJ_Z0[4]
+    rng = np.random.default_rng(19)
+    wq, wt = rng.standard_normal(m), rng.standard_normal(m)
+    g, _, _ = _gpu_grad(fq, B, grid, ADJ_Z0, wq, wt, dtype=torch.float32, precision="f32")
+    ref, _ = adj.vjp(B, grid, *ADJ_Z0, wq, wt, oracle.params())
+    assert _rel(g, ref) < 0.25
+
+
+def test_stretched_hyperbolic_closed_form(fq):
+    # B = (x, -y, 1) on a stretched grid over [-1, 1]^2 x [0, 1]: Q = e^2 + e^-2
+    # on top exits and dQ/da = 2 (e^2 - e^-2) along dB = (x, -y, 0)
+    grid = synth.stretched_grid((33, 33, 17), (-1.0, -1.0, 0.0), (1.0, 1.0, 1.0), (1.04, 1.04, 1.06))
+    B = synth.analytic_cube("hyperbolic", grid)
+    x, y, z = (np.asarray(c) for c in grid.coords)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    dB = np.stack([X, -Y, 0 * X], -1)
+    plane = ((-0.3, -0.3, 0.0), (0.1, 0.0, 0.0), (0.0, 0.1, 0.0), 6, 6)
+    w = np.random.default_rng(3).uniform(0.5, 1.5, 36)
+    g, st, _ = _gpu_grad(fq, B, grid, plane, w, 0 * w, precision="f64", tol=1e-10)
+    assert np.all(st & fq.LINE_BAD == 0)
+    closed = 2.0 * (math.exp(2.0) - math.exp(-2.0))
+    np.testing.assert_allclose(np.sum(g * dB), np.sum(w) * closed, rtol=1e-6)
+
+
+def test_stretched_tape_refusals(fq, adj_mono):
+    B, grid = adj_mono
+    field = _field(fq, B, grid)
+    for kw in (dict(scheme=1), dict(precision="f64", reverse_precision="f32"),
+               dict(precision="f32", reverse_precision="f64")):
+        with pytest.raises(fq.FqslError) as ei:
+            fq.qmap_plane(field, *ADJ_Z0, fq.params(tape=1, **kw), tape=fq.Tape())
+        assert ei.value.status == 5
