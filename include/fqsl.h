@@ -200,10 +200,10 @@ FQSL_API fqsl_status fqsl_field_create(const void *B_dev, fqsl_dtype b_dtype, lo
  * Handles made here serve fqsl_qmap_plane, fqsl_qmap_volume,
  * fqsl_qmap_plane_static and fqsl_twist with Method I and Method II (way 2
  * offsets +-eps_way2 cells of the trial's start cell) and both schemes, and
- * the step tape of RKF45 maps (fqsl_backward differentiates them with each
- * step's start-cell widths held fixed, and with the reverse sweep in the
+ * the step tape of either scheme (fqsl_backward differentiates the map with
+ * each step's start-cell widths held fixed, and with the reverse sweep in the
  * taped map's state precision: FP64 with FP64, FP32 or FP32_ACC64 with FP32);
- * the fixed-step scheme's tape and batches return FQSL_ERR_UNSUPPORTED. Errors:
+ * batches return FQSL_ERR_UNSUPPORTED. Errors:
  * FQSL_ERR_ARG (null pointers, sizes, flags, coordinates not strictly
  * increasing or not finite, coordinates that collapse in float when
  * FQSL_PACK_F32 is asked for), FQSL_ERR_OOM, FQSL_ERR_CUDA. */

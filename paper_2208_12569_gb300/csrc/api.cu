@@ -525,10 +525,8 @@ fqsl_status check_params(const fqsl_field f, const fqsl_params *p, const char *w
     }
     if (p->qperp && p->method != 2) return fail(FQSL_ERR_UNSUPPORTED, "%s: Q_perp needs Method II", who);
     if (f->g.rect && p->tape) {
-        // the stretched-grid tape: RKF45, with the reverse sweep in the taped
-        // state's precision (FP64 physical positions, FP32 relative ones)
-        if (p->scheme == 1)
-            return fail(FQSL_ERR_UNSUPPORTED, "%s: no step tape of the fixed-step scheme on a stretched grid", who);
+        // the stretched-grid tape: the reverse sweep runs in the taped state's
+        // precision (FP64 physical positions, FP32 relative ones)
         const int rp = p->reverse_precision < 0 ? p->precision : p->reverse_precision;
         if ((rp == FQSL_F64) != (p->precision == FQSL_F64))
             return fail(FQSL_ERR_UNSUPPORTED, "%s: on a stretched grid the reverse sweep runs in the taped map's "
@@ -825,7 +823,10 @@ int tape_blocks_per_sm(fqsl_field f, int precision, int src, int p_scheme)
 {
     int &c = f->blocks_cache_tape[p_scheme][precision][src == kSrcExtra ? 1 : 0];
     const bool acc64 = precision == FQSL_F32_ACC64;
-    if (!c && f->g.rect)
+    if (!c && f->g.rect && p_scheme == 1)
+        c = precision == FQSL_F64 ? trace_tape_rect_rk38_blocks_per_sm_f64(src)
+                                  : trace_tape_rect_rk38_blocks_per_sm_f32(src, acc64);
+    else if (!c && f->g.rect)
         c = precision == FQSL_F64 ? trace_tape_rect_blocks_per_sm_f64(src) : trace_tape_rect_blocks_per_sm_f32(src, acc64);
     else if (!c && p_scheme == 1)
         c = precision == FQSL_F64 ? trace_tape_rk38_blocks_per_sm_f64(src) : trace_tape_rk38_blocks_per_sm_f32(src, acc64);
@@ -838,6 +839,9 @@ cudaError_t launch_tape(const TraceArgs &a, const fqsl_params *p, int src, long 
 {
     if (grid < 1) grid = 1;
     const bool acc64 = p->precision == FQSL_F32_ACC64;
+    if (a.f.rect && p->scheme == 1)
+        return p->precision == FQSL_F64 ? launch_trace_tape_rect_rk38_f64(a, src, (int)grid, s)
+                                        : launch_trace_tape_rect_rk38_f32(a, src, (int)grid, s, acc64);
     if (a.f.rect)
         return p->precision == FQSL_F64 ? launch_trace_tape_rect_f64(a, src, (int)grid, s)
                                         : launch_trace_tape_rect_f32(a, src, (int)grid, s, acc64);

@@ -226,8 +226,8 @@ cudaError_t launch_q_vjp(const AdjArgs &a, int mode, bool tape_f64, cudaStream_t
 cudaError_t launch_reverse(const AdjArgs &a, int mode, bool tape_f64, cudaStream_t s);
 // passes A1, A2, B, C for a map traced with the fixed-step scheme (adjoint_rk38.cu)
 cudaError_t launch_reverse_rk38(const AdjArgs &a, int mode, bool tape_f64, cudaStream_t s);
-// passes A1, A2, B, C for an RKF45 map on a stretched grid (adjoint_rect.cu;
-// the tape is in the sweep's state precision)
+// passes A1, A2, B, C for a map on a stretched grid, either scheme
+// (adjoint_rect.cu; the tape is in the sweep's state precision)
 cudaError_t launch_reverse_rect(const AdjArgs &a, int mode, cudaStream_t s);
 cudaError_t launch_curl_adjoint(const void *acc, bool acc64, const FieldView &g, void *dB, fqsl_dtype dt,
                                 cudaStream_t s);
@@ -250,6 +250,10 @@ cudaError_t launch_trace_tape_rect_f32(const TraceArgs &a, int src, int grid, cu
 cudaError_t launch_trace_tape_rect_f64(const TraceArgs &a, int src, int grid, cudaStream_t s);
 int trace_tape_rect_blocks_per_sm_f32(int src, bool acc64);
 int trace_tape_rect_blocks_per_sm_f64(int src);
+cudaError_t launch_trace_tape_rect_rk38_f32(const TraceArgs &a, int src, int grid, cudaStream_t s, bool acc64);
+cudaError_t launch_trace_tape_rect_rk38_f64(const TraceArgs &a, int src, int grid, cudaStream_t s);
+int trace_tape_rect_rk38_blocks_per_sm_f32(int src, bool acc64);
+int trace_tape_rect_rk38_blocks_per_sm_f64(int src);
 int trace_tape_blocks_per_sm_f32(int src, bool acc64);
 int trace_tape_blocks_per_sm_f64(int src);
 // the same with the fixed-step scheme (trace_rk38_f32.cu, trace_rk38_f64.cu)

@@ -23,6 +23,13 @@ __global__ void __launch_bounds__(kBlock) k_trace_dev_rect_rk38_f32(const TraceA
     trace::trace_body<float, kSrcLattice, false, WAY, false, false, true, 1>(A, BatchArgs{});
 }
 
+// the adjoint's forward pass: lattice or extra lines writing the step tape
+template <int SRC, bool ACC>
+__global__ void __launch_bounds__(kBlock, FQSL_TRACE_F32_MINB) k_trace_tape_rect_rk38_f32(const TraceArgs A)
+{
+    trace::trace_body<float, SRC, ACC, 0, false, true, true, 1>(A, BatchArgs{});
+}
+
 template <bool ACC>
 void launch(const TraceArgs &a, int src, int grid, cudaStream_t s)
 {
@@ -53,6 +60,36 @@ cudaError_t launch_trace_rect_rk38_f32(const TraceArgs &a, int src, int grid, cu
 }
 
 int trace_rect_rk38_blocks_per_sm_f32(int src, bool acc64) { return acc64 ? blocks<true>(src) : blocks<false>(src); }
+
+cudaError_t launch_trace_tape_rect_rk38_f32(const TraceArgs &a, int src, int grid, cudaStream_t s, bool acc64)
+{
+    if (src == kSrcExtra) {
+        if (acc64) k_trace_tape_rect_rk38_f32<kSrcExtra, true><<<grid, kBlock, 0, s>>>(a);
+        else k_trace_tape_rect_rk38_f32<kSrcExtra, false><<<grid, kBlock, 0, s>>>(a);
+    } else {
+        if (acc64) k_trace_tape_rect_rk38_f32<kSrcLattice, true><<<grid, kBlock, 0, s>>>(a);
+        else k_trace_tape_rect_rk38_f32<kSrcLattice, false><<<grid, kBlock, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+int trace_tape_rect_rk38_blocks_per_sm_f32(int src, bool acc64)
+{
+    int b = 0;
+    if (src == kSrcExtra) {
+        if (acc64)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_rect_rk38_f32<kSrcExtra, true>, kBlock, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_rect_rk38_f32<kSrcExtra, false>, kBlock, 0);
+    } else {
+        if (acc64)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_rect_rk38_f32<kSrcLattice, true>, kBlock, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_rect_rk38_f32<kSrcLattice, false>, kBlock,
+                                                          0);
+    }
+    return b > 0 ? b : 1;
+}
 
 cudaError_t launch_trace_dev_rect_rk38_f32(const TraceArgs &a, int way, int grid, cudaStream_t s)
 {

@@ -19,7 +19,31 @@ __global__ void __launch_bounds__(kBlock) k_trace_dev_rect_rk38_f64(const TraceA
 {
     trace::trace_body<double, kSrcLattice, true, WAY, false, false, true, 1>(A, BatchArgs{});
 }
+
+// the adjoint's forward pass: lattice or extra lines writing the step tape
+template <int SRC>
+__global__ void __launch_bounds__(kBlock) k_trace_tape_rect_rk38_f64(const TraceArgs A)
+{
+    trace::trace_body<double, SRC, true, 0, false, true, true, 1>(A, BatchArgs{});
+}
 }  // namespace
+
+cudaError_t launch_trace_tape_rect_rk38_f64(const TraceArgs &a, int src, int grid, cudaStream_t s)
+{
+    if (src == kSrcExtra) k_trace_tape_rect_rk38_f64<kSrcExtra><<<grid, kBlock, 0, s>>>(a);
+    else k_trace_tape_rect_rk38_f64<kSrcLattice><<<grid, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int trace_tape_rect_rk38_blocks_per_sm_f64(int src)
+{
+    int b = 0;
+    if (src == kSrcExtra)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_rect_rk38_f64<kSrcExtra>, kBlock, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trace_tape_rect_rk38_f64<kSrcLattice>, kBlock, 0);
+    return b > 0 ? b : 1;
+}
 
 cudaError_t launch_trace_rect_rk38_f64(const TraceArgs &a, int src, int grid, cudaStream_t s)
 {

@@ -242,7 +242,9 @@ def test_unsupported_modes(fq, mono):
     B, grid = mono
     field = _field(fq, B, grid)
     args = ((0.0, 0.0, 0.0), (1.0, 0, 0), (0, 1.0, 0), 4, 4)
-    for kw in (dict(tape=1), dict(method=2, gradb_way=1)):
+    # Method II way 1 needs the gradient grid (not packed here); the step tape
+    # is defined on stretched grids (tested below)
+    for kw in (dict(method=2, gradb_way=1),):
         with pytest.raises(fq.FqslError) as ei:
             fq.qmap_plane(field, *args, fq.params(**kw))
         assert ei.value.status == 5, kw
@@ -458,8 +460,24 @@ def test_stretched_hyperbolic_closed_form(fq):
 def test_stretched_tape_refusals(fq, adj_mono):
     B, grid = adj_mono
     field = _field(fq, B, grid)
-    for kw in (dict(scheme=1), dict(precision="f64", reverse_precision="f32"),
-               dict(precision="f32", reverse_precision="f64")):
+    for kw in (dict(precision="f64", reverse_precision="f32"), dict(precision="f32", reverse_precision="f64")):
         with pytest.raises(fq.FqslError) as ei:
             fq.qmap_plane(field, *ADJ_Z0, fq.params(tape=1, **kw), tape=fq.Tape())
         assert ei.value.status == 5
+
+
+@pytest.mark.parametrize("plane", [ADJ_Z0, ADJ_XZ], ids=["z0_plane", "interior_xz_plane"])
+def test_stretched_fixed_step_fp64_gradient_matches_oracle(fq, oracle_lib, adj_mono, plane):
+    # the fixed-step 3/8 rule (Sec. 2.3, Eq. step) on the stretched grid: steps
+    # in cells of each trial's start cell, the step of each line frozen
+    adj = pytest.importorskip("oracle.adjoint")
+    B, grid = adj_mono
+    m = plane[3] * plane[4]
+    rng = np.random.default_rng(23)
+    wq, wt = rng.standard_normal(m), rng.standard_normal(m)
+    kw = dict(scheme=1, step=0.3, step_min=0.05, max_steps=10 ** 6)
+    g, st, _ = _gpu_grad(fq, B, grid, plane, wq, wt, precision="f64", **kw)
+    ref, log = adj.vjp(B, grid, *plane, wq, wt, oracle.params(**kw))
+    assert np.array_equal(st & oracle.BAD, log["status"] & oracle.BAD)
+    assert np.linalg.norm(ref) > 0
+    assert _rel(g, ref) < 1e-10

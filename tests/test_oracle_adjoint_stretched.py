@@ -106,3 +106,24 @@ def test_gradient_matches_free_retrace_differences(mono):
     err = np.abs(np.array(err))
     assert err.max() < 1e-2 * flat.max()
     assert np.median(err / flat[pick]) < 1e-2
+
+
+@pytest.mark.parametrize("plane", [Z0, XZ], ids=["z0_plane", "interior_xz_plane"])
+def test_fixed_step_replay_and_invariance(mono, plane):
+    # the fixed-step 3/8 rule on the stretched grid (steps in cells of each
+    # trial's start cell): the replay reproduces the C oracle's map, and the
+    # frozen-sequence gradient is orthogonal to B
+    B, grid = mono
+    p = oracle.params(scheme=1, step=0.3, step_min=0.05, max_steps=10 ** 6)
+    ref = oracle.plane(B, grid, *plane, p)
+    log = adj.lattice_log(B, grid, *plane, p)
+    Q, Tw, usable, _ = adj.qmap_t(torch.tensor(B), grid, *plane, log)
+    us = usable.numpy()
+    assert us.sum() > 90
+    np.testing.assert_allclose(Q.numpy()[us], ref["Q"][us], rtol=1e-11)
+    np.testing.assert_allclose(Tw.numpy()[us], ref["Tw"][us], rtol=0, atol=1e-12)
+    m = plane[3] * plane[4]
+    rng = np.random.default_rng(9)
+    g, _ = adj.vjp(B, grid, *plane, rng.standard_normal(m), rng.standard_normal(m), p, log=log)
+    assert np.linalg.norm(g) > 0
+    assert abs(np.sum(g * B)) < 1e-12 * np.linalg.norm(g) * np.linalg.norm(B)
