@@ -62,8 +62,8 @@ NUM_SMS = 152
 # DRAM bytes (read + write) of one k_trace_f32 launch on this workload, from
 # an ncu capture of that kernel on this map, valid while the tracer sources
 # hash to TRACE_F32_SRC_HASH.
-TRACE_F32_DRAM_BYTES = 308.370176e6 + 59.896576e6
-TRACE_F32_SRC_HASH = "0b43cd71e2326598"
+TRACE_F32_DRAM_BYTES = 308.553728e6 + 59.336704e6
+TRACE_F32_SRC_HASH = "070d776e3ee31082"
 
 
 def _trace_src_hash():
@@ -986,6 +986,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--only-f32", action="store_true",
                     help="time only the FP32 map (no FP64, e2e or CPU legs); used for ncu captures")
+    ap.add_argument("--probes-only", action="store_true",
+                    help="run only the roofline probes and print their ceilings (for profiling them)")
     ap.add_argument("--no-probes", action="store_true",
                     help="plane workload: skip the roofline probes (the roofline then uses nominal peaks)")
     ap.add_argument("--only-f64", action="store_true",
@@ -1006,6 +1008,12 @@ def main():
             run_reference_adjoint(args)
         else:
             run_reference(args)
+        return
+    if args.probes_only:
+        # the roofline probes alone (a small command for profiling them)
+        import torch
+
+        print(json.dumps({"ceilings": measure_ceilings(torch.device("cuda", 0))}), flush=True)
         return
     if args.workload == "adjoint":
         run_adjoint(args)
