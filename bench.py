@@ -880,6 +880,56 @@ def run_adjoint(args, emit=True):
         return g.cpu().numpy()
 
     rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
+    # the same differentiation step on a stretched grid over the same box (the
+    # same sources and tube; horizontal widths growing 1 % per cell from the
+    # middle, vertical 2 % per cell upward): FP32 gradient time, FP64 gradient
+    # against the oracle's stretched adjoint on the same seed sample
+    Bs, Bts, grid_s = synth.adjoint_cubes(seed=SEED, n=ADJ_CUBE, ratios=(1.01, 1.01, 1.02))
+    Bsd = torch.from_numpy(Bs).to(dev)
+    hi = grid_s.hi
+    plane_s = ((0.0, 0.0, 0.0), (hi[0] / ADJ_SEEDS, 0.0, 0.0), (0.0, hi[1] / ADJ_SEEDS, 0.0), ADJ_SEEDS, ADJ_SEEDS)
+    fs32 = fq.Field(Bsd, coords=grid_s.coords, pack=("f32",))
+    fs64 = fq.Field(Bsd, coords=grid_s.coords, pack=("f64",))
+    ftgs = fq.Field(torch.from_numpy(Bts).to(dev), coords=grid_s.coords, pack=("f32",))
+    tgs = fq.qmap_plane(ftgs, *plane_s, fq.params(precision="f32", tol=TOL))
+    outs_ = fq.alloc_out(n, device=dev)
+
+    def step_s(g):
+        fs32.update(Bsd)
+        fq.qmap_plane(fs32, *plane_s, p32, out=outs_)
+        fq.loss_logq_tw(outs_["Q"], outs_["Tw"], tgs["Q"], tgs["Tw"], outs_["status"], 0.1, out=lbuf)
+        g.zero_()
+        fq.backward(fs32, lbuf["dQ"], lbuf["dTw"], g)
+
+    for _ in range(args.warmup):
+        step_s(dB)
+    torch.cuda.synchronize()
+    mss = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step_s(dB)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mss.append(e0.elapsed_time(e1))
+    fs64.update(Bsd)
+    fq.qmap_plane(fs64, *plane_s, p64, out=outs_)
+    gs = torch.zeros(Bsd.shape, dtype=torch.float64, device=dev)
+    fq.backward(fs64, WQ, WT, gs)
+    fs64.check()
+    Bs64 = Bs.astype(np.float64)
+    t0 = time.perf_counter()
+    ref_s, _ = oadj.vjp_sample(Bs64, grid_s, *plane_s, sample, wq, wt, oracle.params(tol=TOL))
+    ora_s_s = time.perf_counter() - t0
+    stretched = {"value": float(np.mean(mss)) / 1000.0, "unit": "s/grad", "dtype": "f32",
+                 "note": "the same step on a stretched grid over the same box (x, y widths x1.01 per cell from "
+                         "the middle, z widths x1.02 per cell upward)",
+                 "cell_width_range": [float(min(np.diff(grid_s.axis(a)).min() for a in range(3))),
+                                      float(max(np.diff(grid_s.axis(a)).max() for a in range(3)))],
+                 "error_vs_oracle": {"f64": rel(gs.cpu().numpy(), ref_s)}, "oracle_sample_s": ora_s_s}
+    for fl in (fs32, fs64, ftgs):
+        fl.close()
     t0 = time.perf_counter()
     ref_fx, _ = oadj.vjp_sample(B64, grid, *plane, sample, wq, wt, oracle.params(scheme=1))
     ora_fx_s = time.perf_counter() - t0
@@ -898,6 +948,26 @@ def run_adjoint(args, emit=True):
     alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     achieved = trials * FLOPS_PER_TRIAL / (t_fwd / 1000.0) / 1e12
     rev_tflops = acc_steps * REV_FLOPS_PER_STEP / (t_rev / 1000.0) / 1e12
+    ceil = getattr(args, "ceilings", None)
+    # the taped tracer against the measured gather and FMA ceilings (the same
+    # work per trial as the map's tracer), else the nominal FP32 issue rate
+    if ceil:
+        tg = trials * GATHER_BYTES_PER_TRIAL / (t_fwd / 1000.0) / 1e12
+        fg, fa = tg / ceil["gather_walk_TBs"], achieved / ceil["fma_f32_TFLOPs"]
+        adj_roof = {"bound": "gather" if fg >= fa else "alu", "achieved": tg if fg >= fa else achieved,
+                    "peak": ceil["gather_walk_TBs"] if fg >= fa else ceil["fma_f32_TFLOPs"],
+                    "unit": "TB/s" if fg >= fa else "TFLOP/s", "frac": max(fg, fa), "traffic": None,
+                    "gather": {"achieved_TBs": tg, "ceiling_TBs": ceil["gather_walk_TBs"], "frac": fg},
+                    "alu": {"achieved_TFLOPs": achieved, "ceiling_TFLOPs": ceil["fma_f32_TFLOPs"], "frac": fa},
+                    "peak_source": "measured on this GPU by the probes (fqsl_probe_gather, fqsl_probe_fma)"}
+    else:
+        adj_roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak, "traffic": None,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, peak_kind)}
+    adj_roof["kernel"] = "taped lattice tracer k_trace_tape_f32 (%d B, %d flops per trial)" % (
+        GATHER_BYTES_PER_TRIAL, FLOPS_PER_TRIAL)
+    adj_roof["note"] = ("latency-bound: the longest direction of a line is a chain of dependent gathers "
+                        "(the longest line takes 236 trial steps against a mean of 14)")
     s32 = float(np.mean(ms32)) / 1000.0
     line = {"metric": ADJ_METRIC, "value": s32, "unit": "s/grad", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * s32, "higher_is_better": False, "scaling": "weak",
@@ -909,16 +979,13 @@ def run_adjoint(args, emit=True):
             "fp64": {"value": float(np.mean(ms64)) / 1000.0, "unit": "s/grad"},
             "kernels_ms": {"forward_taped_trace_f32": t_fwd, "reverse_sweep_f32": t_rev, "curl_transpose": t_curl},
             "work": {"trial_steps": trials, "accepted_steps": acc_steps, "accepted_per_half_line": acc_steps / (2 * n)},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": achieved / alu_peak, "traffic": None,
-                         "kernel": "taped lattice tracer k_trace_tape_f32 (trial steps x %d flops)" % FLOPS_PER_TRIAL,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, peak_kind),
-                         "note": "latency-bound: the longest direction of a line is a chain of dependent gathers"},
+            "roofline": adj_roof,
             "reverse_sweep": {"ms": t_rev, "passes": "A1 states, A2 Jacobians, B per-line recurrence, C VJP + scatter",
                               "achieved_TFLOPs": rev_tflops, "frac_of_alu_peak": rev_tflops / alu_peak,
                               "gather_TBs": acc_steps * REV_GATHER_BYTES_PER_STEP / (t_rev / 1000.0) / 1e12,
                               "scatter_GBs": acc_steps * REV_SCATTER_BYTES_PER_STEP / (t_rev / 1000.0) / 1e9},
             "error_vs_oracle": errs,
+            "stretched": stretched,
             "fixed_step": {"value": float(np.mean(msfx)) / 1000.0, "unit": "s/grad", "dtype": "f32",
                            "note": "the same differentiation step with the 3/8-rule scheme (step_perp = 3 "
                                    "cells scaled per line by |Bn0/B|, step_min 0.15)",
@@ -1270,11 +1337,11 @@ def main():
             "gpu_launches": 3 * args.steps, "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_adjoint:
         # the metric's second part: seconds per gradient of the differentiation workload
-        a = run_adjoint(argparse.Namespace(steps=args.steps, warmup=args.warmup, fp64_steps=args.fp64_steps),
-                        emit=False)
+        a = run_adjoint(argparse.Namespace(steps=args.steps, warmup=args.warmup, fp64_steps=args.fp64_steps,
+                                           ceilings=ceilings), emit=False)
         line["adjoint"] = {k: a[k] for k in ("metric", "value", "unit", "ms_per_step", "higher_is_better", "config",
                                              "fp64", "kernels_ms", "error_vs_oracle", "e2e", "cpu_baseline",
-                                             "roofline", "reverse_sweep", "loss", "fixed_step")}
+                                             "roofline", "reverse_sweep", "loss", "fixed_step", "stretched")}
     if rank == 0 and ws == 1 and not args.no_batch:
         # the batched uneven workload (48 cubes, one graph-captured autotuned launch)
         bt = run_batch(argparse.Namespace(steps=args.steps, warmup=args.warmup), emit=False)

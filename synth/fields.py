@@ -281,7 +281,9 @@ def twist_tube_cube(grid: Grid, charges, turns: float = 1.5, radius_cells: float
     yc = 0.5 * (y[0] + y[-1])
     H = z[-1] - z[0]
     q = 2.0 * math.pi * turns / H
-    R = radius_cells * grid.spacing[0]
+    # a stretched grid has no spacing: its mean x width stands in
+    dx = grid.spacing[0] if hasattr(grid, "spacing") else (x[-1] - x[0]) / (len(x) - 1)
+    R = radius_cells * dx
     Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
     xp = X - xc
     yp = Y - yc
@@ -336,13 +338,18 @@ def batch_specs(seed: int = 2208, count: int = 48, seeds_uv=(512, 256)):
 
 
 def adjoint_cubes(seed: int = 2208, n=(128, 128, 64), count: int = 24, turns: float = 1.5,
-                  radius_cells: float = 10.0, rel: float = 0.05, dtype=np.float32):
+                  radius_cells: float = 10.0, rel: float = 0.05, dtype=np.float32, ratios=None):
     """The differentiation workload: a monopole potential field (``count``
     buried sources, depths 4..16 cells scaled by nx/128, unit spacing) plus a
     vertical rigid-twist tube (``turns`` over the box height, radius
     ``radius_cells``), and the target cube: the same sources with strengths
-    scaled by (1 + rel N(0,1)) under the same tube. Returns (B, B_target, grid)."""
+    scaled by (1 + rel N(0,1)) under the same tube. With ``ratios`` the same
+    sources are sampled on a stretched grid over the same box (stretched_grid's
+    axes: horizontal widths growing by ratios[0], ratios[1] per cell from the
+    middle, vertical by ratios[2] upward). Returns (B, B_target, grid)."""
     grid = Grid(tuple(n), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    if ratios is not None:
+        grid = stretched_grid(n, (0.0, 0.0, 0.0), tuple(float(k - 1) for k in n), ratios)
     rng = np.random.default_rng(seed)
     s = n[0] / 128.0
     ch = random_charges(rng, count, ((0.0, n[0] - 1.0), (0.0, n[1] - 1.0)), depth=(4.0 * s, 16.0 * s))
