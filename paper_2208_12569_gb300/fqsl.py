@@ -168,6 +168,7 @@ class Field:
         self._h = h
         self.n = (nx, ny, nz)
         self._keep = B  # the packing kernel reads B asynchronously
+        self._free_tapes = []  # handles of released pooled tapes (see Tape)
 
     @property
     def handle(self):
@@ -201,6 +202,9 @@ class Field:
         if t is not None:
             t.close()
             self._default_tape = None
+        for h in getattr(self, "_free_tapes", ()):
+            _lib.fqsl_tape_destroy(h)
+        self._free_tapes = []
         if getattr(self, "_h", None):
             _lib.fqsl_field_destroy(self._h)
             self._h = None
@@ -234,10 +238,16 @@ def _out_struct(out):
 class Tape:
     """A taped map (fqsl_tape): made by the first qmap_plane / qmap_volume call
     with params(tape=1) that is given it, re-recorded by later ones, read by
-    backward() and tape_export(); its device memory is released by close()."""
+    backward() and tape_export(); its device memory is released by close().
+    A tape made with ``pool=field`` hands its C handle (and the device memory
+    it holds) back to that field when it is garbage-collected, for the next
+    pooled tape to reuse; the field releases pooled handles when it closes."""
 
-    def __init__(self):
+    def __init__(self, pool=None):
         self._h = C.c_void_p()
+        self._pool = pool
+        if pool is not None and getattr(pool, "_free_tapes", None):
+            self._h = pool._free_tapes.pop()
 
     @property
     def handle(self):
@@ -252,7 +262,12 @@ class Tape:
 
     def __del__(self):
         try:
-            self.close()
+            pool = getattr(self, "_pool", None)
+            if self._h and pool is not None and getattr(pool, "_h", None):
+                pool._free_tapes.append(self._h)  # reused by the field's next pooled tape
+                self._h = C.c_void_p()
+            else:
+                self.close()
         except Exception:
             pass
 
@@ -460,7 +475,7 @@ class QTwPlane(torch.autograd.Function):
         if getattr(field, "_packed_from", None) != key:
             field.update(B.detach())
             field._packed_from = key
-        ctx.tape = Tape()
+        ctx.tape = Tape(pool=field)  # a released graph's tape is reused by the next forward
         out = qmap_plane(field, origin, u, v, nu, nv, q, tape=ctx.tape)
         ctx.field = field
         ctx.b_dtype = B.dtype

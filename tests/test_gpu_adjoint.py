@@ -485,6 +485,27 @@ def test_two_taped_maps_on_one_field(fq, small):
         t.close()
 
 
+def test_autograd_reuses_released_tapes(fq, small):
+    # a QTwPlane forward whose graph was released hands its tape back to the
+    # field: a training loop reuses one tape (and its device memory)
+    import gc
+
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    Bv = torch.from_numpy(B).cuda().requires_grad_(True)
+    handles = set()
+    for _ in range(3):
+        Q, Tw = fq.QTwPlane.apply(Bv, field, *PLANE16, fq.params(precision="f64"))
+        torch.autograd.backward([Q], [torch.ones_like(Q)])
+        del Q, Tw
+        gc.collect()
+        assert len(field._free_tapes) == 1
+        handles.add(field._free_tapes[0].value)
+    assert len(handles) == 1
+    field.close()
+    assert field._free_tapes == []
+
+
 def test_autograd_two_planes_in_one_loss(fq, small):
     # QTwPlane keeps its own tape: Q on two planes of one field in one graph
     B, _, grid = small
