@@ -476,7 +476,9 @@ class QTwPlane(torch.autograd.Function):
             field.update(B.detach())
             field._packed_from = key
         ctx.tape = Tape(pool=field)  # a released graph's tape is reused by the next forward
+        prev = getattr(field, "last_tape", None)
         out = qmap_plane(field, origin, u, v, nu, nv, q, tape=ctx.tape)
+        field.last_tape = prev  # only the graph holds this tape
         ctx.field = field
         ctx.b_dtype = B.dtype
         return out["Q"], out["Tw"]
