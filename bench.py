@@ -935,6 +935,7 @@ def run_adjoint(args, emit=True):
     ora_fx_s = time.perf_counter() - t0
     errs_fx = {"f64": rel(gpu_vjp(fq.params(precision="f64", tape=1, scheme=1)), ref_fx),
                "f32": rel(gpu_vjp(fq.params(precision="f32", tape=1, scheme=1)), ref_fx)}
+    fd = fd_directional(fq, field64, Bd, grid, plane, tgt, g32, g64, n, dev)
     errs = {"f64": rel(gpu_vjp(p64), ref),
             "f64_forward_f32_reverse": rel(gpu_vjp(fq.params(precision="f64", tol=TOL, tape=1,
                                                              reverse_precision="f32")), ref),
@@ -985,6 +986,7 @@ def run_adjoint(args, emit=True):
                               "gather_TBs": acc_steps * REV_GATHER_BYTES_PER_STEP / (t_rev / 1000.0) / 1e12,
                               "scatter_GBs": acc_steps * REV_SCATTER_BYTES_PER_STEP / (t_rev / 1000.0) / 1e9},
             "error_vs_oracle": errs,
+            "fd_directional": fd,
             "stretched": stretched,
             "fixed_step": {"value": float(np.mean(msfx)) / 1000.0, "unit": "s/grad", "dtype": "f32",
                            "note": "the same differentiation step with the 3/8-rule scheme (step_perp = 3 "
@@ -1004,6 +1006,66 @@ def run_adjoint(args, emit=True):
     for fl in (field, field64, fieldx, ftgt):
         fl.close()
     return line
+
+
+def loss_masked(Q, Tw, Qt, Twt, mask, w_tw=0.1):
+    """The differentiation workload's loss over a fixed set of seeds (numpy,
+    float64): mean of (log10 Q - log10 Qt)^2 + w_tw (Tw - Twt)^2."""
+    return float(np.mean((np.log10(Q[mask]) - np.log10(Qt[mask])) ** 2 + w_tw * (Tw[mask] - Twt[mask]) ** 2))
+
+
+def fd_directional(fq, field64, Bd, grid, plane, tgt, g32, g64, n, dev, ndir=4, eps=(1e-3, 2e-3)):
+    """The frozen-sequence gradients (FP32 and FP64 loss gradients of the
+    differentiation workload) along smooth directions dB -- the field of one
+    extra buried source pair, scaled to rms(dB) = rms(B) -- against central
+    differences of the loss of freely re-traced FP64 maps at the same
+    tolerance (B +- eps dB, each map traced afresh, its own step sequence),
+    over the usable seeds of the unperturbed map."""
+    import torch
+
+    import synth
+
+    p = fq.params(precision="f64", tol=TOL)
+    B = Bd.double().cpu().numpy()
+    Qt, Twt = tgt["Q"].cpu().numpy(), tgt["Tw"].cpu().numpy()
+
+    def traced(Bx):
+        field64.update(torch.from_numpy(Bx.astype(np.float32)).to(dev) if Bd.dtype == torch.float32
+                       else torch.from_numpy(Bx).to(dev))
+        o = fq.qmap_plane(field64, *plane, p)
+        return {k: o[k].cpu().numpy() for k in ("Q", "Tw", "status")}
+
+    o0 = traced(B)
+    bad = fq.LINE_BAD | fq.LINE_MIXED
+    mask = (np.isfinite(o0["Q"]) & np.isfinite(o0["Tw"]) & np.isfinite(Qt) & np.isfinite(Twt) & (o0["Q"] > 0)
+            & (Qt > 0) & ((o0["status"] & bad) == 0))
+    rng = np.random.default_rng(SEED + 11)
+    nx, ny = grid.n[0], grid.n[1]
+    rows = []
+    for _ in range(ndir):
+        ch = synth.random_charges(rng, 2, ((0.0, nx - 1.0), (0.0, ny - 1.0)), depth=(4.0, 16.0))
+        dB = synth.monopole_cube(grid, ch, dtype=np.float64)
+        dB *= np.sqrt(np.mean(B * B) / np.mean(dB * dB))
+        fds = []
+        for e in eps:
+            op, om = traced(B + e * dB), traced(B - e * dB)
+            ok = mask & np.isfinite(op["Q"]) & np.isfinite(om["Q"]) & (op["Q"] > 0) & (om["Q"] > 0)
+            fds.append((loss_masked(op["Q"], op["Tw"], Qt, Twt, ok) - loss_masked(om["Q"], om["Tw"], Qt, Twt, ok))
+                       / (2.0 * e))
+        d64, d32 = float(np.sum(g64 * dB)), float(np.sum(g32 * dB))
+        rows.append({"fd": fds, "f64": d64, "f32": d32,
+                     "rel_err_f64": abs(d64 - fds[0]) / abs(fds[0]), "rel_err_f32": abs(d32 - fds[0]) / abs(fds[0]),
+                     "fd_eps_spread": abs(fds[1] - fds[0]) / abs(fds[0]),
+                     "f32_vs_f64": abs(d32 - d64) / abs(d64)})
+    traced(B)  # leave the field holding B
+    return {"directions": rows, "eps": list(eps), "usable_seeds": int(mask.sum()),
+            "median_rel_err_f64": float(np.median([r["rel_err_f64"] for r in rows])),
+            "median_rel_err_f32": float(np.median([r["rel_err_f32"] for r in rows])),
+            "max_f32_vs_f64": float(max(r["f32_vs_f64"] for r in rows)),
+            "stable_directions": [i for i, r in enumerate(rows) if r["fd_eps_spread"] < 0.05],
+            "note": "directional derivative of the loss along the field of a buried source pair (rms = rms B); "
+                    "central differences of FP64 maps re-traced afresh at the same tolerance, at eps and 2 eps "
+                    "(their spread shows how far the free map is from smooth at this tolerance)"}
 
 
 def run_reference_adjoint(args):
@@ -1341,7 +1403,8 @@ def main():
                                            ceilings=ceilings), emit=False)
         line["adjoint"] = {k: a[k] for k in ("metric", "value", "unit", "ms_per_step", "higher_is_better", "config",
                                              "fp64", "kernels_ms", "error_vs_oracle", "e2e", "cpu_baseline",
-                                             "roofline", "reverse_sweep", "loss", "fixed_step", "stretched")}
+                                             "roofline", "reverse_sweep", "loss", "fixed_step", "stretched",
+                                             "fd_directional")}
     if rank == 0 and ws == 1 and not args.no_batch:
         # the batched uneven workload (48 cubes, one graph-captured autotuned launch)
         bt = run_batch(argparse.Namespace(steps=args.steps, warmup=args.warmup), emit=False)
