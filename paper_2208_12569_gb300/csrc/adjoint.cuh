@@ -680,7 +680,8 @@ __device__ __forceinline__ bool chunk_of(const AdjArgs &A, long long c, long lon
 }
 
 // pass A1: the states and stage derivatives of every chunk, from its
-// checkpoint (the only sequential recompute)
+// checkpoint (the only sequential recompute), unless the forward kept them
+// (AdjArgs::stored); either way the list of live steps
 template <typename T, typename TT, int SCH, bool RECT = false>
 __global__ void __launch_bounds__(128) k_adj_states(const AdjArgs A)
 {
@@ -717,6 +718,7 @@ __global__ void __launch_bounds__(128) k_adj_states(const AdjArgs A)
         base = __shfl_sync(mask, base, 0) + (unsigned long long)(inc - v);
         if (!live) continue;
         for (int i = 0; i < n; i++) A.steps[base + i] = (int32_t)(c * K + i);
+        if (A.stored) continue;  // the forward kept the states and stage derivatives
         T x[3] = {(T)X[4 * c], (T)X[4 * c + 1], (T)X[4 * c + 2]};
         T *wx = WX + c * (K + 1) * 3;
         T *wk = WK + c * K * 15;

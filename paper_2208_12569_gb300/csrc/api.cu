@@ -763,8 +763,14 @@ struct TapeLayout {
 
 constexpr int kDefaultTapeChunk = 16;
 
+// The taped forward also keeps every accepted step's states and stage
+// derivatives for the reverse sweep (sparing its recompute) when the reverse
+// runs in the tape's precision class and the arrays, sized for the whole pool,
+// stay within this budget.
+constexpr size_t kKeepBudget = (size_t)4 << 30;
+
 TapeLayout tape_layout(char *base, long long n, bool rot, bool f32, long long pool, int k, size_t nodes,
-                       bool acc64)
+                       bool acc64, bool keep)
 {
     TapeLayout t{};
     t.s = layout(base, n, rot, true, f32);
@@ -781,6 +787,8 @@ TapeLayout tape_layout(char *base, long long n, bool rot, bool f32, long long po
     t.tape.head = c.take<int4>((size_t)t.halves);
     t.tape.xe = c.take<char>((size_t)t.halves * 4 * ts);
     t.tape.owner = c.take<int32_t>((size_t)pool);
+    t.tape.wx = keep ? c.take<char>((size_t)pool * (k + 1) * 3 * ts) : nullptr;
+    t.tape.wk = keep ? c.take<char>((size_t)pool * k * 15 * ts) : nullptr;
     t.xbar = c.take<double>((size_t)(3 * t.halves));
     t.xseed = rot ? c.take<double>((size_t)(24 * n)) : nullptr;
     t.sums = c.take<double>(2);
@@ -799,7 +807,10 @@ TapeLayout tape_layout_of(const fqsl_tape t, char *base, long long pool)
     const fqsl_params &p = t->p;
     const long long n = t->lat.n1 * t->lat.n2 * t->lat.n3;
     const int k = p.tape_chunk > 0 ? p.tape_chunk : kDefaultTapeChunk;
-    return tape_layout(base, n, t->lat.allow_rot, p.precision != FQSL_F64, pool, k, t->nodes, acc64_of(p));
+    const size_t ts = p.precision == FQSL_F64 ? 8 : 4;
+    const bool same = (reverse_precision_of(p) == FQSL_F64) == (p.precision == FQSL_F64);
+    const bool keep = same && (size_t)pool * (size_t)(18 * k + 3) * ts <= kKeepBudget;
+    return tape_layout(base, n, t->lat.allow_rot, p.precision != FQSL_F64, pool, k, t->nodes, acc64_of(p), keep);
 }
 
 fqsl_status ensure_tape_buf(fqsl_tape t, size_t bytes)
@@ -1626,11 +1637,13 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, fqsl_tape tp, const double *d
     const bool acc64 = acc64_of(p);
     const int mode = rp == FQSL_F64 ? 2 : (acc64 ? 1 : 0);
     const bool tape_f64 = p.precision == FQSL_F64;
-    // per-step work arrays of the reverse sweep for the chunks in use
+    // per-step work arrays of the reverse sweep for the chunks in use (the
+    // states and stage derivatives are the tape's own when the forward kept them)
     const int K = tl.tape.k;
     const size_t rs = rp == FQSL_F64 ? 8 : 4;
-    const size_t bx = align_up((size_t)used * (K + 1) * 3 * rs), bj = align_up((size_t)used * K * 12 * rs),
-                 bk = align_up((size_t)used * K * 15 * rs), bb = align_up((size_t)used * K * 3 * rs),
+    const bool stored = tl.tape.wx != nullptr;
+    const size_t bx = stored ? 0 : align_up((size_t)used * (K + 1) * 3 * rs), bj = align_up((size_t)used * K * 12 * rs),
+                 bk = stored ? 0 : align_up((size_t)used * K * 15 * rs), bb = align_up((size_t)used * K * 3 * rs),
                  bi = align_up((size_t)used * sizeof(int4)), bs = align_up((size_t)used * K * sizeof(int32_t));
     const size_t wbytes = bx + bj + bk + bb + bi + bs;
     if (wbytes > tp->work_cap) {
@@ -1675,9 +1688,10 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, fqsl_tape tp, const double *d
         a.xseed = tl.xseed;
     }
     a.chunks = (long long)used;
-    a.wx = tp->work;
+    a.stored = stored ? 1 : 0;
+    a.wx = stored ? tl.tape.wx : tp->work;
     a.wj = (char *)tp->work + bx;
-    a.wk = (char *)tp->work + bx + bj;
+    a.wk = stored ? tl.tape.wk : (char *)tp->work + bx + bj;
     a.wb = (char *)tp->work + bx + bj + bk;
     a.cinfo = (int4 *)((char *)tp->work + bx + bj + bk + bb);
     a.steps = (int32_t *)((char *)tp->work + bx + bj + bk + bb + bi);

@@ -156,6 +156,12 @@ struct Tape {
     int32_t *owner;             // [cap] half-line of each chunk
     long long hl_base;          // half-line of a launch's line 0: 0 for lattice lines,
                                 // 2 n for the extra lines of rotated seeds (item = 4 slot + q)
+    // Optional (NULL = not kept): the states and stage derivatives of every
+    // accepted step as the forward computed them, in the reverse sweep's
+    // layout, so that it need not recompute them from the checkpoints:
+    //   wx [cap][k + 1][3] T: state at each step of a chunk and after its last
+    //   wk [cap][k][15] T: position derivatives of stages 0..4 of each step
+    void *wx, *wk;
 };
 
 struct TraceArgs {
@@ -216,6 +222,7 @@ struct AdjArgs {
     //   [chunk][k][3] adjoint of each step's end state
     long long chunks;
     void *wx, *wj, *wk, *wb;
+    int stored;                // wx, wk hold the forward's values (pass A1 only lists the steps)
     int4 *cinfo;               // [chunks] {steps, orientation, half-line, live} (pass A1)
     int32_t *steps;            // [chunks * k] live steps c k + i, compacted (pass A1)
     unsigned long long *nsteps;  // number of entries in steps

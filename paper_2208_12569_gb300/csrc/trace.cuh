@@ -975,18 +975,41 @@ __device__ __forceinline__ bool tape_chunk(const Tape &tp, Lane<T> &L)
     x[1] = L.y;
     x[2] = L.z;
     x[3] = (T)0;
+    if (tp.wx) {
+        T *w = (T *)tp.wx + c * (long long)(tp.k + 1) * 3;
+        w[0] = L.x;
+        w[1] = L.y;
+        w[2] = L.z;
+    }
     L.tcur = (int)c;
     L.tn = 0;
     return true;
 }
 
-// An accepted step of size h from the current state.
-template <typename T>
-__device__ __forceinline__ void tape_step(const Tape &tp, Lane<T> &L, T h)
+// An accepted step of size h from the current state; ns stages' position
+// derivatives k0, k1, k2 and the end state (x1, y1, z1) are kept too when the
+// tape holds them (Tape::wx, wk).
+template <typename T, int NS>
+__device__ __forceinline__ void tape_step(const Tape &tp, Lane<T> &L, T h, const T k0[], const T k1[], const T k2[],
+                                          T x1, T y1, T z1)
 {
     if (L.tcur == -2) return;
     if ((L.tcur < 0 || L.tn == tp.k) && !tape_chunk(tp, L)) return;
-    ((T *)tp.h)[(long long)L.tcur * tp.k + L.tn] = h;
+    const long long j = (long long)L.tcur * tp.k + L.tn;
+    ((T *)tp.h)[j] = h;
+    if (tp.wx) {
+        T *wk = (T *)tp.wk + j * 15;
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+            wk[3 * s + 0] = k0[s];
+            wk[3 * s + 1] = k1[s];
+            wk[3 * s + 2] = k2[s];
+        }
+        T *wx = (T *)tp.wx + ((long long)L.tcur * (tp.k + 1) + L.tn + 1) * 3;
+        wx[0] = x1;
+        wx[1] = y1;
+        wx[2] = z1;
+    }
     L.tn++;
 }
 
@@ -1626,10 +1649,14 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                     for (int c = 0; c < NS; c++) o[c] *= inv;
                 }
             }
-            if (s < NST - 1) {
+            // (the 3/8 rule's last stage is kept too when the tape holds the
+            // stage derivatives: all four enter its solution)
+            if (s < NST - 1 || (TAPE && SCH != 0)) {
                 k0[s] = o[0];
                 k1[s] = o[1];
                 k2[s] = o[2];
+            }
+            if (s < NST - 1) {
                 if constexpr (DEV != 0) {
 #pragma unroll
                     for (int c = 0; c < 6; c++) kd[s][c] = o[5 + c];
@@ -1722,7 +1749,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A0, const BatchArgs 
                 hn = hn < hmin ? hmin : (hn > hmax ? hmax : hn);
             }
             if (inside<T, RECT>(f, nx, ny, nz)) {
-                if constexpr (TAPE) tape_step(A.tape, L, hh);
+                if constexpr (TAPE) tape_step<T, SCH ? NST : NST - 1>(A.tape, L, hh, k0, k1, k2, nx, ny, nz);
                 L.x = nx;
                 L.y = ny;
                 L.z = nz;
