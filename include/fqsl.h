@@ -404,7 +404,9 @@ FQSL_API fqsl_status fqsl_tape_destroy(fqsl_tape tape);
  * none). Writes *loss_dev and dQ_dev[s], dTw_dev[s] = d loss / d Q[s], Tw[s]
  * (0 for seeds not usable; loss_dev, dQ_dev, dTw_dev may be NULL). sums_dev:
  * double[2] scratch of the caller. All pointers are device pointers of n
- * elements (status_dev may be NULL). Errors: FQSL_ERR_ARG, FQSL_ERR_CUDA. */
+ * elements (status_dev may be NULL). dQ_dev and dTw_dev may be Q_dev and
+ * Tw_dev themselves (in place); other partial overlaps of outputs and inputs
+ * are not allowed. Errors: FQSL_ERR_ARG, FQSL_ERR_CUDA. */
 FQSL_API fqsl_status fqsl_loss_logq_tw(long long n, const double *Q_dev, const double *Tw_dev,
                                        const double *Qt_dev, const double *Twt_dev, const uint8_t *status_dev,
                                        double w_tw, double *sums_dev, double *loss_dev, double *dQ_dev,

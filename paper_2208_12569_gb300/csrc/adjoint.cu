@@ -457,14 +457,23 @@ __device__ __forceinline__ bool usable(long long s, const double *Q, const doubl
     return isfinite(q) && isfinite(qt) && isfinite(t) && isfinite(tt) && q > 0.0 && qt > 0.0;
 }
 
+// The misfit sums; with lq_out/dt_out (the gradient's buffers) each usable
+// seed's log-Q difference and Tw difference are kept there for k_loss_grad,
+// so that the FP64 logarithms (the costly part on GB300's FP64 pipe) are
+// taken once.
 __global__ void __launch_bounds__(256) k_loss_sum(long long n, const double *Q, const double *Tw, const double *Qt,
-                                                  const double *Twt, const uint8_t *st, double wtw, double *sums)
+                                                  const double *Twt, const uint8_t *st, double wtw, double *sums,
+                                                  double *lq_out, double *dt_out)
 {
     double s = 0.0, c = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         if (usable(i, Q, Tw, Qt, Twt, st)) {
             const double lq = log10(Q[i]) - log10(Qt[i]);
             const double dt = Tw[i] - Twt[i];
+            if (lq_out) {
+                lq_out[i] = lq;
+                dt_out[i] = dt;
+            }
             s += lq * lq + wtw * dt * dt;
             c += 1.0;
         }
@@ -492,7 +501,8 @@ __global__ void __launch_bounds__(256) k_loss_sum(long long n, const double *Q, 
 
 __global__ void __launch_bounds__(256) k_loss_grad(long long n, const double *Q, const double *Tw, const double *Qt,
                                                    const double *Twt, const uint8_t *st, double wtw,
-                                                   const double *sums, double *loss, double *dQ, double *dTw)
+                                                   const double *sums, double *loss, double *dQ, double *dTw,
+                                                   bool keep)
 {
     const double cnt = sums[1] > 0.0 ? sums[1] : 1.0;
     if (blockIdx.x == 0 && threadIdx.x == 0 && loss) *loss = sums[0] / cnt;
@@ -500,9 +510,11 @@ __global__ void __launch_bounds__(256) k_loss_grad(long long n, const double *Q,
          i += (long long)gridDim.x * blockDim.x) {
         double gq = 0.0, gt = 0.0;
         if (usable(i, Q, Tw, Qt, Twt, st)) {
-            const double lq = log10(Q[i]) - log10(Qt[i]);
+            // dQ, dTw hold k_loss_sum's differences when it kept them
+            const double lq = keep ? dQ[i] : log10(Q[i]) - log10(Qt[i]);
+            const double dt = keep ? dTw[i] : Tw[i] - Twt[i];
             gq = 2.0 * lq / (Q[i] * 2.302585092994046 * cnt);
-            gt = 2.0 * wtw * (Tw[i] - Twt[i]) / cnt;
+            gt = 2.0 * wtw * dt / cnt;
         }
         if (dQ) dQ[i] = gq;
         if (dTw) dTw[i] = gt;
@@ -673,8 +685,13 @@ cudaError_t launch_loss(long long n, const double *Q, const double *Tw, const do
     cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), s);
     if (e != cudaSuccess) return e;
     const unsigned g = adj::grid_for(n, 256, 4);
-    adj::k_loss_sum<<<g, 256, 0, s>>>(n, Q, Tw, Qt, Twt, st, wtw, sums);
-    adj::k_loss_grad<<<g, 256, 0, s>>>(n, Q, Tw, Qt, Twt, st, wtw, sums, loss, dQ, dTw);
+    // (not when an output buffer is also an input: the kept differences would
+    // overwrite it before k_loss_grad reads it)
+    const double *ins[4] = {Q, Tw, Qt, Twt};
+    bool keep = dQ && dTw && dQ != dTw;
+    for (const double *in : ins) keep = keep && in != dQ && in != dTw;
+    adj::k_loss_sum<<<g, 256, 0, s>>>(n, Q, Tw, Qt, Twt, st, wtw, sums, keep ? dQ : nullptr, keep ? dTw : nullptr);
+    adj::k_loss_grad<<<g, 256, 0, s>>>(n, Q, Tw, Qt, Twt, st, wtw, sums, loss, dQ, dTw, keep);
     return cudaGetLastError();
 }
 

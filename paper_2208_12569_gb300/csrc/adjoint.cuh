@@ -679,6 +679,50 @@ __device__ __forceinline__ bool chunk_of(const AdjArgs &A, long long c, long lon
     return true;
 }
 
+// A kept state and a step's stage derivatives (the layouts of Tape::wx, wk)
+// in 16-byte read-only loads.
+__device__ __forceinline__ void load_state(const float *p, float x[3])
+{
+    const float4 q = __ldg((const float4 *)p);
+    x[0] = q.x;
+    x[1] = q.y;
+    x[2] = q.z;
+}
+__device__ __forceinline__ void load_state(const double *p, double x[3])
+{
+    const double2 a = __ldg((const double2 *)p), b = __ldg((const double2 *)p + 1);
+    x[0] = a.x;
+    x[1] = a.y;
+    x[2] = b.x;
+}
+template <typename T, int NS>
+__device__ __forceinline__ void load_stages(const T *p, T k[5][3])
+{
+    constexpr int N = (3 * NS + 3) / 4 * 4;  // values to load: the stages, rounded up to whole float4
+    T v[kStageStride];
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < N; q += 4) {
+            const float4 a = __ldg((const float4 *)(p + q));
+            v[q] = a.x;
+            v[q + 1] = a.y;
+            v[q + 2] = a.z;
+            v[q + 3] = a.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; q += 2) {
+            const double2 a = __ldg((const double2 *)(p + q));
+            v[q] = a.x;
+            v[q + 1] = a.y;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; s++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) k[s][a] = v[3 * s + a];
+}
+
 // pass A1: the states and stage derivatives of every chunk, from its
 // checkpoint (the only sequential recompute), unless the forward kept them
 // (AdjArgs::stored); either way the list of live steps
@@ -720,24 +764,24 @@ __global__ void __launch_bounds__(128) k_adj_states(const AdjArgs A)
         for (int i = 0; i < n; i++) A.steps[base + i] = (int32_t)(c * K + i);
         if (A.stored) continue;  // the forward kept the states and stage derivatives
         T x[3] = {(T)X[4 * c], (T)X[4 * c + 1], (T)X[4 * c + 2]};
-        T *wx = WX + c * (K + 1) * 3;
-        T *wk = WK + c * K * 15;
-        wx[0] = x[0];
-        wx[1] = x[1];
-        wx[2] = x[2];
+        T *wx = WX + c * (K + 1) * kStateStride;
+        T *wk = WK + c * K * kStageStride;
+        trace::store_state(wx, x[0], x[1], x[2]);
         for (int i = 0; i < n; i++) {
             T x4[3], kt[5][4], dd[3];
             step_scale<RECT>(A.f, x[0], x[1], x[2], dd);
             advance<T, SCH, RECT>(A.f, dd, (T)sg, x, (T)H[c * K + i], -1, x4, kt);
+            T v[kStageStride];
+#pragma unroll
+            for (int q = 0; q < kStageStride; q++) v[q] = (T)0;
 #pragma unroll
             for (int s = 0; s < Stages<T, SCH>::N; s++)
 #pragma unroll
-                for (int a = 0; a < 3; a++) wk[15 * i + 3 * s + a] = kt[s][a];
+                for (int a = 0; a < 3; a++) v[3 * s + a] = kt[s][a];
+            trace::store_vec<T, kStageStride>(wk + kStageStride * i, v);
 #pragma unroll
-            for (int a = 0; a < 3; a++) {
-                x[a] = x4[a];
-                wx[3 * (i + 1) + a] = x4[a];
-            }
+            for (int a = 0; a < 3; a++) x[a] = x4[a];
+            trace::store_state(wx + kStateStride * (i + 1), x[0], x[1], x[2]);
         }
     }
 }
@@ -779,15 +823,11 @@ __global__ void __launch_bounds__(128) k_adj_jac(const AdjArgs A)
         int i, sg;
         double w;
         if (!step_of(A, t, j, c, i, sg, w)) continue;
-        const T *x = WX + (c * (K + 1) + i) * 3;
-        const T *wk = WK + j * 15;
+        T x[3], k[5][3];
+        load_state(WX + (c * (K + 1) + i) * kStateStride, x);
+        load_stages<T, Stages<T, SCH>::N>(WK + j * kStageStride, k);
         const T h = (T)H[j];
         const T sgn = (T)sg;
-        T k[5][3];
-#pragma unroll
-        for (int s = 0; s < Stages<T, SCH>::N; s++)
-#pragma unroll
-            for (int a = 0; a < 3; a++) k[s][a] = wk[3 * s + a];
         // the step's scale, fixed at its start (stretched grid: its start cell)
         T dd[3];
         step_scale<RECT>(A.f, x[0], x[1], x[2], dd);
@@ -833,6 +873,46 @@ __global__ void __launch_bounds__(128) k_adj_jac(const AdjArgs A)
 
 // pass B: per half-line, the exit step's VJP and the recurrence over its
 // steps; an extra line's half-line also keeps the adjoint of its seed
+// One step of pass B's recurrence: store the step's end-state adjoint y, then
+// y <- J^T y + g wbar (J = {J^T row-major (9), g (3)}).
+// The 12 values of a step's pass-A2 record (16-byte aligned: records are 48 or
+// 96 bytes from an aligned base) in 16-byte read-only loads.
+template <typename T>
+__device__ __forceinline__ void load_jrec(const T *p, T J[12])
+{
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int v = 0; v < 3; v++) {
+            const float4 q = __ldg((const float4 *)p + v);
+            J[4 * v + 0] = q.x;
+            J[4 * v + 1] = q.y;
+            J[4 * v + 2] = q.z;
+            J[4 * v + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < 6; v++) {
+            const double2 q = __ldg((const double2 *)p + v);
+            J[2 * v + 0] = q.x;
+            J[2 * v + 1] = q.y;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void adj_rec_step(const T J[12], T wb, T y[3], T *out)
+{
+    out[0] = y[0];
+    out[1] = y[1];
+    out[2] = y[2];
+    const T z0 = J[0] * y[0] + J[1] * y[1] + J[2] * y[2] + J[9] * wb;
+    const T z1 = J[3] * y[0] + J[4] * y[1] + J[5] * y[2] + J[10] * wb;
+    const T z2 = J[6] * y[0] + J[7] * y[1] + J[8] * y[2] + J[11] * wb;
+    y[0] = z0;
+    y[1] = z1;
+    y[2] = z2;
+}
+
 template <typename T, typename AccT, typename TT, int SCH, bool RECT = false>
 __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
 {
@@ -876,8 +956,8 @@ __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
 #pragma unroll
         for (int a = 0; a < 3; a++) xb[a] = (T)A.xbar[3 * hl + a];
         // the exiting step from the state after the last accepted step
-        const T *xn = WX + ((long long)hd.x * (K + 1) + hd.y) * 3;
-        const T x[3] = {xn[0], xn[1], xn[2]};
+        T x[3];
+        load_state(WX + ((long long)hd.x * (K + 1) + hd.y) * kStateStride, x);
         T h, d = 0, ws = wb;
         int ax = -1;
         T yb[3] = {xb[0], xb[1], xb[2]}, keep[3] = {0, 0, 0}, y[3];
@@ -946,24 +1026,28 @@ __global__ void __launch_bounds__(128) k_adj_lines(const AdjArgs A)
         }
         // the accepted steps, last first: store each step's end-state adjoint,
         // then xbar_i = J_i^T xbar_{i+1} + g_i wbar
+        // (the Jacobians were written by pass A2 and are read-only here: their
+        // loads go ahead of the chain, four steps at a time)
         int c = hd.x, n = hd.y;
         for (;;) {
-            const T *wj = WJ + (long long)c * K * 12;
-            T *wbp = WB + (long long)c * K * 3;
-#pragma unroll 4
-            for (int i = n - 1; i >= 0; i--) {
-                wbp[3 * i + 0] = y[0];
-                wbp[3 * i + 1] = y[1];
-                wbp[3 * i + 2] = y[2];
-                const T *J = wj + 12 * i;
-                const T z0 = J[0] * y[0] + J[1] * y[1] + J[2] * y[2] + J[9] * wb;
-                const T z1 = J[3] * y[0] + J[4] * y[1] + J[5] * y[2] + J[10] * wb;
-                const T z2 = J[6] * y[0] + J[7] * y[1] + J[8] * y[2] + J[11] * wb;
-                y[0] = z0;
-                y[1] = z1;
-                y[2] = z2;
-            }
+            const T *__restrict__ wj = WJ + (long long)c * K * 12;
+            T *__restrict__ wbp = WB + (long long)c * K * 3;
             const int pc = tp.prev[c];
+            int i = n - 1;
+            for (; i >= 3; i -= 4) {
+                T Jb[4][12];
+#pragma unroll
+                for (int u = 0; u < 4; u++) load_jrec(wj + 12 * (i - u), Jb[u]);
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    adj_rec_step(Jb[u], wb, y, wbp + 3 * (i - u));
+                }
+            }
+            for (; i >= 0; i--) {
+                T Jr[12];
+                load_jrec(wj + 12 * i, Jr);
+                adj_rec_step(Jr, wb, y, wbp + 3 * i);
+            }
             if (pc < 0 || pc >= c) break;  // chunks of a half-line are taken in increasing order
             c = pc;
             n = K;
@@ -995,14 +1079,11 @@ __global__ void __launch_bounds__(128) k_adj_rev(const AdjArgs A)
         int i, sg;
         double w;
         if (!step_of(A, t, j, c, i, sg, w)) continue;
-        const T *wk = WK + j * 15;
         T yb[3] = {WB[3 * j], WB[3 * j + 1], WB[3 * j + 2]};
-        T ks[5][3];
-#pragma unroll
-        for (int s = 0; s < Stages<T, SCH>::N; s++)
-#pragma unroll
-            for (int a = 0; a < 3; a++) ks[s][a] = wk[3 * s + a];
-        step_reverse_k<T, AccT, SCH, RECT>(A.f, (T)sg, WX + (c * (K + 1) + i) * 3, (T)H[j], ks, yb, (T)w, acc);
+        T x[3], ks[5][3];
+        load_state(WX + (c * (K + 1) + i) * kStateStride, x);
+        load_stages<T, Stages<T, SCH>::N>(WK + j * kStageStride, ks);
+        step_reverse_k<T, AccT, SCH, RECT>(A.f, (T)sg, x, (T)H[j], ks, yb, (T)w, acc);
     }
 }
 

@@ -787,8 +787,8 @@ TapeLayout tape_layout(char *base, long long n, bool rot, bool f32, long long po
     t.tape.head = c.take<int4>((size_t)t.halves);
     t.tape.xe = c.take<char>((size_t)t.halves * 4 * ts);
     t.tape.owner = c.take<int32_t>((size_t)pool);
-    t.tape.wx = keep ? c.take<char>((size_t)pool * (k + 1) * 3 * ts) : nullptr;
-    t.tape.wk = keep ? c.take<char>((size_t)pool * k * 15 * ts) : nullptr;
+    t.tape.wx = keep ? c.take<char>((size_t)pool * (k + 1) * kStateStride * ts) : nullptr;
+    t.tape.wk = keep ? c.take<char>((size_t)pool * k * kStageStride * ts) : nullptr;
     t.xbar = c.take<double>((size_t)(3 * t.halves));
     t.xseed = rot ? c.take<double>((size_t)(24 * n)) : nullptr;
     t.sums = c.take<double>(2);
@@ -809,7 +809,8 @@ TapeLayout tape_layout_of(const fqsl_tape t, char *base, long long pool)
     const int k = p.tape_chunk > 0 ? p.tape_chunk : kDefaultTapeChunk;
     const size_t ts = p.precision == FQSL_F64 ? 8 : 4;
     const bool same = (reverse_precision_of(p) == FQSL_F64) == (p.precision == FQSL_F64);
-    const bool keep = same && (size_t)pool * (size_t)(18 * k + 3) * ts <= kKeepBudget;
+    const size_t per_chunk = (size_t)((k + 1) * kStateStride + k * kStageStride) * ts;
+    const bool keep = same && (size_t)pool * per_chunk <= kKeepBudget;
     return tape_layout(base, n, t->lat.allow_rot, p.precision != FQSL_F64, pool, k, t->nodes, acc64_of(p), keep);
 }
 
@@ -1642,8 +1643,9 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, fqsl_tape tp, const double *d
     const int K = tl.tape.k;
     const size_t rs = rp == FQSL_F64 ? 8 : 4;
     const bool stored = tl.tape.wx != nullptr;
-    const size_t bx = stored ? 0 : align_up((size_t)used * (K + 1) * 3 * rs), bj = align_up((size_t)used * K * 12 * rs),
-                 bk = stored ? 0 : align_up((size_t)used * K * 15 * rs), bb = align_up((size_t)used * K * 3 * rs),
+    const size_t bx = stored ? 0 : align_up((size_t)used * (K + 1) * kStateStride * rs),
+                 bj = align_up((size_t)used * K * 12 * rs),
+                 bk = stored ? 0 : align_up((size_t)used * K * kStageStride * rs), bb = align_up((size_t)used * K * 3 * rs),
                  bi = align_up((size_t)used * sizeof(int4)), bs = align_up((size_t)used * K * sizeof(int32_t));
     const size_t wbytes = bx + bj + bk + bb + bi + bs;
     if (wbytes > tp->work_cap) {

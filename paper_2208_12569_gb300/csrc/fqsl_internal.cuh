@@ -159,10 +159,17 @@ struct Tape {
     // Optional (NULL = not kept): the states and stage derivatives of every
     // accepted step as the forward computed them, in the reverse sweep's
     // layout, so that it need not recompute them from the checkpoints:
-    //   wx [cap][k + 1][3] T: state at each step of a chunk and after its last
-    //   wk [cap][k][15] T: position derivatives of stages 0..4 of each step
+    //   wx [cap][k + 1][kStateStride] T: state {x, y, z, 0} at each step of a
+    //      chunk and after its last
+    //   wk [cap][k][kStageStride] T: position derivatives of stages 0..4 of
+    //      each step (stage s at 3 s, zero padding at 15)
+    // (padded so that each state and each step's record is written and read
+    // with 16-byte vector accesses)
     void *wx, *wk;
 };
+
+constexpr int kStateStride = 4;
+constexpr int kStageStride = 16;
 
 struct TraceArgs {
     FieldView f;
@@ -217,9 +224,10 @@ struct AdjArgs {
     const unsigned *rot_count; // rotated seeds of the taped map
     double *xseed;             // [8 n][3] adjoint of each extra half-line's seed (index coordinates)
     // per-step work arrays of the reverse sweep, for chunks 0..chunks-1 (T):
-    //   wx [chunk][k + 1][3] states, wj [chunk][k][12] step Jacobian J^T (9)
-    //   and Tw gradient (3), wk [chunk][k][15] stage derivatives, wb
-    //   [chunk][k][3] adjoint of each step's end state
+    //   wx [chunk][k + 1][kStateStride] states, wj [chunk][k][12] step
+    //   Jacobian J^T (9) and Tw gradient (3), wk [chunk][k][kStageStride]
+    //   stage derivatives (the layouts of Tape::wx, wk), wb [chunk][k][3]
+    //   adjoint of each step's end state
     long long chunks;
     void *wx, *wj, *wk, *wb;
     int stored;                // wx, wk hold the forward's values (pass A1 only lists the steps)

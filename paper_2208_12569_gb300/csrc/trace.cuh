@@ -958,6 +958,30 @@ __device__ __forceinline__ void write_end32(const LineRecs &R, long long line, i
 // ---------------------------------------------------------------------------
 // step tape (adjoint forward pass; see Tape)
 // ---------------------------------------------------------------------------
+// 16-byte vector stores of the kept states and stage derivatives (addresses
+// 16-byte aligned: the arrays are, and their strides are multiples of 16 B).
+__device__ __forceinline__ void store_state(float *p, float x, float y, float z)
+{
+    *(float4 *)p = make_float4(x, y, z, 0.f);
+}
+__device__ __forceinline__ void store_state(double *p, double x, double y, double z)
+{
+    ((double2 *)p)[0] = make_double2(x, y);
+    ((double2 *)p)[1] = make_double2(z, 0.0);
+}
+// the first N (a multiple of 4) values of v
+template <typename T, int N>
+__device__ __forceinline__ void store_vec(T *p, const T v[])
+{
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < N; q += 4) *(float4 *)(p + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; q += 2) *(double2 *)(p + q) = make_double2(v[q], v[q + 1]);
+    }
+}
+
 // Open a new chunk whose checkpoint is the current state. Returns false when
 // the pool is exhausted (the half-line is then no longer taped).
 template <typename T>
@@ -975,12 +999,7 @@ __device__ __forceinline__ bool tape_chunk(const Tape &tp, Lane<T> &L)
     x[1] = L.y;
     x[2] = L.z;
     x[3] = (T)0;
-    if (tp.wx) {
-        T *w = (T *)tp.wx + c * (long long)(tp.k + 1) * 3;
-        w[0] = L.x;
-        w[1] = L.y;
-        w[2] = L.z;
-    }
+    if (tp.wx) store_state((T *)tp.wx + c * (long long)(tp.k + 1) * kStateStride, L.x, L.y, L.z);
     L.tcur = (int)c;
     L.tn = 0;
     return true;
@@ -998,17 +1017,17 @@ __device__ __forceinline__ void tape_step(const Tape &tp, Lane<T> &L, T h, const
     const long long j = (long long)L.tcur * tp.k + L.tn;
     ((T *)tp.h)[j] = h;
     if (tp.wx) {
-        T *wk = (T *)tp.wk + j * 15;
+        T v[kStageStride];
 #pragma unroll
         for (int s = 0; s < NS; s++) {
-            wk[3 * s + 0] = k0[s];
-            wk[3 * s + 1] = k1[s];
-            wk[3 * s + 2] = k2[s];
+            v[3 * s + 0] = k0[s];
+            v[3 * s + 1] = k1[s];
+            v[3 * s + 2] = k2[s];
         }
-        T *wx = (T *)tp.wx + ((long long)L.tcur * (tp.k + 1) + L.tn + 1) * 3;
-        wx[0] = x1;
-        wx[1] = y1;
-        wx[2] = z1;
+#pragma unroll
+        for (int q = 3 * NS; q < kStageStride; q++) v[q] = (T)0;
+        store_vec<T, (3 * NS + 3) / 4 * 4>((T *)tp.wk + j * kStageStride, v);
+        store_state((T *)tp.wx + ((long long)L.tcur * (tp.k + 1) + L.tn + 1) * kStateStride, x1, y1, z1);
     }
     L.tn++;
 }

@@ -300,6 +300,27 @@ def test_loss_kernel_matches_oracle_loss(fq, small):
     np.testing.assert_allclose(dTw.cpu().numpy(), Tw.grad.numpy(), rtol=1e-12, atol=1e-300)
 
 
+def test_loss_in_place_buffers(fq, small):
+    # dQ, dTw given as the Q and Tw inputs themselves (the kernel keeps its
+    # log-Q differences in the output buffers only when they are not inputs):
+    # the same loss and gradient as with separate buffers, bit for bit
+    B, Bt, grid = small
+    field = _field(fq, B, grid)
+    ftgt = _field(fq, Bt, grid)
+    p = fq.params(precision="f64")
+    out = fq.qmap_plane(field, *PLANE16, p)
+    tgt = fq.qmap_plane(ftgt, *PLANE16, p)
+    loss, dQ, dTw = fq.loss_logq_tw(out["Q"], out["Tw"], tgt["Q"], tgt["Tw"], out["status"], 0.1)
+    Qi, Twi = out["Q"].clone(), out["Tw"].clone()
+    buf = dict(sums=torch.empty(2, dtype=torch.float64, device="cuda"),
+               loss=torch.empty((), dtype=torch.float64, device="cuda"), dQ=Qi, dTw=Twi)
+    loss2, dQ2, dTw2 = fq.loss_logq_tw(Qi, Twi, tgt["Q"], tgt["Tw"], out["status"], 0.1, out=buf)
+    assert dQ2.data_ptr() == Qi.data_ptr()
+    assert float(loss2) == float(loss)
+    assert torch.equal(dQ2, dQ) and torch.equal(dTw2, dTw)
+    assert int((dQ != 0).sum()) > 200
+
+
 @pytest.mark.parametrize("plane", [PLANE16, XZ], ids=["z0_plane", "interior_xz_plane"])
 def test_loss_gradient_end_to_end_matches_oracle(fq, small, plane):
     # loss -> dQ, dTw (loss kernel) -> dB (fqsl_backward), FP64, against the
