@@ -360,15 +360,19 @@ FQSL_API fqsl_status fqsl_qmap_plane_static(fqsl_field field, const double origi
  *                    on B at the seed. NaN or infinite weights count as 0.
  *   dB_dev           B-shaped array (layout of fqsl_field_create) of db_dtype
  *                    (FQSL_F32 or FQSL_F64), accumulated into, not cleared.
- * The state is recomputed from checkpoints every params->tape_chunk accepted
- * steps, in the taped call's params->reverse_precision (default: its
- * precision); the node adjoints accumulate in float (FQSL_F32) or double
+ * The reverse sweep runs in the taped call's params->reverse_precision
+ * (default: its precision). When that is the tape's precision class and the
+ * pool's per-step arrays fit 4 GiB, the taped call kept every accepted step's
+ * state and stage derivatives; otherwise they are recomputed from the
+ * checkpoints taken every params->tape_chunk accepted steps. The node
+ * adjoints accumulate in float (FQSL_F32) or double
   * (FQSL_F32_ACC64, FQSL_F64). The field must not be updated between the
  * taped call and this one; other maps of the field (taped into other tapes or
- * not) may run in between. The call synchronises cuda_stream once (to confirm
- * that the tape's chunk pool sufficed; if it did not, it traces the map again
- * into the same tape with a larger pool), so it cannot be captured in a CUDA
- * graph. The tape keeps its map: fqsl_backward may run on it again with other
+ * not) may run in between. The call waits on the host until the taped
+ * call's tracers have finished (not for later work on the stream), to read
+ * how many chunks of the tape's pool they used; if the pool did not suffice, it
+ * traces the map again into the same tape with a larger pool. It therefore
+ * cannot be captured in a CUDA graph. The tape keeps its map: fqsl_backward may run on it again with other
  * weights. With timing enabled, fqsl_field_times reports ms[0] = reverse
  * sweep, ms[1] = 0, ms[2] = curl transpose. Errors: FQSL_ERR_ARG (NULL field
  * or tape, a tape of another field or without a complete map, the field

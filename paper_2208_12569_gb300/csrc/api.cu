@@ -101,6 +101,11 @@ struct fqsl_tape_s {
     size_t cap = 0;
     void *work = nullptr;  // per-step arrays of the reverse sweep
     size_t work_cap = 0;
+    // the chunks the last taped call used, copied to pinned host memory as
+    // soon as its tracers finish (used_ev), so that fqsl_backward waits for
+    // the tracers only, not for what the stream runs after them
+    unsigned long long *used_host = nullptr;
+    cudaEvent_t used_ev = nullptr;
 };
 
 namespace {
@@ -988,6 +993,26 @@ fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params
         }
         if (e != cudaSuccess) return cuda_fail(e, who);
     }
+    if (tape) {
+        // the chunk count, for fqsl_backward's pool check
+        if (!tape->used_host) {
+            e = cudaHostAlloc((void **)&tape->used_host, sizeof(unsigned long long), cudaHostAllocDefault);
+            if (e != cudaSuccess) {
+                tape->used_host = nullptr;
+                return cuda_fail(e, who);
+            }
+        }
+        if (!tape->used_ev) {
+            e = cudaEventCreateWithFlags(&tape->used_ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) {
+                tape->used_ev = nullptr;
+                return cuda_fail(e, who);
+            }
+        }
+        e = cudaMemcpyAsync(tape->used_host, tl.ctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaEventRecord(tape->used_ev, stream);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+    }
     mark(f, 2, stream);
     AssembleArgs g{};
     g.f = a.f;
@@ -1031,6 +1056,8 @@ void release_tape(fqsl_tape t)
     if (!t) return;
     cudaFree(t->buf);
     cudaFree(t->work);
+    if (t->used_host) cudaFreeHost(t->used_host);
+    if (t->used_ev) cudaEventDestroy(t->used_ev);
     delete t;
 }
 
@@ -1618,10 +1645,11 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, fqsl_tape tp, const double *d
     // same map again with a larger pool (the map is deterministic)
     unsigned long long used = 0;
     for (int attempt = 0;; attempt++) {
-        TapeLayout tl = tape_layout_of(tp, (char *)tp->buf, tp->pool);
-        cudaError_t e = cudaMemcpyAsync(&used, tl.ctr, sizeof used, cudaMemcpyDeviceToHost, stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        // the taped call copied its chunk count once its tracers finished
+        if (!tp->used_ev || !tp->used_host) return fail(FQSL_ERR_ARG, "%s: the tape holds no complete taped map", who);
+        cudaError_t e = cudaEventSynchronize(tp->used_ev);
         if (e != cudaSuccess) return cuda_fail(e, who);
+        used = *(volatile unsigned long long *)tp->used_host;
         if (used <= (unsigned long long)tp->pool) break;
         if (attempt >= 2) return fail(FQSL_ERR_CUDA, "%s: step tape pool still exhausted after re-tracing", who);
         tp->pool = (long long)(used + used / 4 + 1024);
