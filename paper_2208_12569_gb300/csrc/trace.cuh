@@ -1913,7 +1913,9 @@ __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
     const Lattice &G = A.lat;
     const FieldView &f = A.f;
     const LineRecs &R = A.rec;
-    const long long i = idx % G.n1, j = (idx / G.n1) % G.n2, k = idx / (G.n1 * G.n2);
+    // 32-bit index arithmetic (a lattice holds fewer than 2^31 seeds)
+    const unsigned u = (unsigned)idx, n1 = (unsigned)G.n1, n12 = (unsigned)(G.n1 * G.n2);
+    const unsigned k = u / n12, rem = u - k * n12, j = rem / n1, i = rem - j * n1;
     const double fi = (double)i + 0.5, fj = (double)j + 0.5, fk = (double)k + 0.5;
     double xi[3];
 #pragma unroll
