@@ -1315,46 +1315,56 @@ def main():
     e2e_serial = n * ws / (float(np.mean(e2e_ms)) / 1000.0)
     assert np.array_equal(np.isnan(Qh.numpy()), np.isnan(res32["Q"]))
 
-    # the same, pipelined as a serving loop would run it: two field handles
-    # and two device copies of B alternate, and step k's host-to-device copy
-    # (copy stream) overlaps step k-1's repack and map (compute stream). Every
-    # step still copies its B in, repacks, maps and reads Q and Tw back; the
-    # timed region spans all K steps.
+    # the same, pipelined as a serving loop would run it: two field handles,
+    # two device copies of B and two output sets alternate. Step k's
+    # host-to-device copy and repack (upload stream) overlap step k-1's map
+    # (compute stream), and its device-to-host copy of Q and Tw (download
+    # stream) overlaps step k+1's map. Every step still copies its B in,
+    # repacks, maps and reads Q and Tw back; L2 is flushed before every map;
+    # the timed region spans all K steps.
     fields = [field32, fq.Field(Bd, grid.origin, grid.spacing, pack=("f32",))]
     Bdevs = [Bdev, torch.empty_like(Bd)]
     outs = [out, fq.alloc_out(n, device=dev)]
     Qhs = [Qh, torch.empty(n, dtype=torch.float64).pin_memory()]
     Twhs = [Twh, torch.empty(n, dtype=torch.float64).pin_memory()]
-    s_copy, s_comp = torch.cuda.Stream(), torch.cuda.Stream()
-    used = [torch.cuda.Event(), torch.cuda.Event()]  # the compute stream is done with Bdevs[b]
-    loaded = [torch.cuda.Event(), torch.cuda.Event()]  # Bdevs[b] holds this step's B
+    s_up, s_comp, s_down = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    mapped = [torch.cuda.Event(), torch.cuda.Event()]  # the map of fields[b] into outs[b] is done
+    loaded = [torch.cuda.Event(), torch.cuda.Event()]  # fields[b] holds this step's records
+    copied = [torch.cuda.Event(), torch.cuda.Event()]  # outs[b] has been read back
     for b in range(2):
-        used[b].record(s_comp)
+        mapped[b].record(s_comp)
+        copied[b].record(s_down)
 
     def pipe_step(k):
         b = k % 2
-        with torch.cuda.stream(s_copy):
-            s_copy.wait_event(used[b])
-            Bdevs[b].copy_(Bh, non_blocking=True)
-            loaded[b].record(s_copy)
+        with torch.cuda.stream(s_up):
+            Bdevs[b].copy_(Bh, non_blocking=True)  # Bdevs[b]: last read by this stream's repack
+            s_up.wait_event(mapped[b])  # the map two steps back is done with fields[b]
+            fields[b].update(Bdevs[b], stream=s_up)
+            loaded[b].record(s_up)
         with torch.cuda.stream(s_comp):
             s_comp.wait_event(loaded[b])
+            s_comp.wait_event(copied[b])
             flush.fill_(1.0)
-            fields[b].update(Bdevs[b], stream=s_comp)
-            used[b].record(s_comp)
             fq.qmap_plane(fields[b], (0.0, 0.0, 0.0), u, v, NU, NV, p32, out=outs[b], stream=s_comp)
+            mapped[b].record(s_comp)
+        with torch.cuda.stream(s_down):
+            s_down.wait_event(mapped[b])
             Qhs[b].copy_(outs[b]["Q"], non_blocking=True)
             Twhs[b].copy_(outs[b]["Tw"], non_blocking=True)
+            copied[b].record(s_down)
 
     for k in range(args.warmup):
         pipe_step(k)
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(s_copy)
+    p0.record(s_up)
     s_comp.wait_event(p0)
+    s_down.wait_event(p0)
     for k in range(args.warmup, args.warmup + args.steps):
         pipe_step(k)
-    s_comp.wait_stream(s_copy)
+    s_comp.wait_stream(s_up)
+    s_comp.wait_stream(s_down)
     p1.record(s_comp)
     torch.cuda.synchronize()
     e2e_pipe_ms = p0.elapsed_time(p1) / args.steps
@@ -1393,8 +1403,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": "Q+Tw values/s", "ms_per_step": e2e_pipe_ms,
                     "h2d_bytes_per_step": int(B.nbytes), "d2h_bytes_per_step": int(2 * n * 8),
                     "note": "per step: H2D of B from pinned memory, repack (curl), map, D2H of Q and Tw; "
-                            "pipelined over two streams (step k's copy overlaps step k-1's map), "
-                            "L2 flushed each step",
+                            "pipelined over three streams (step k's copy and repack overlap step k-1's map, "
+                            "its read-back step k+1's map), L2 flushed before each map",
                     "serial": {"value": e2e_serial, "ms_per_step": float(np.mean(e2e_ms))}},
             "gpu_launches": 3 * args.steps, "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_adjoint:
