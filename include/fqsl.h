@@ -361,10 +361,12 @@ FQSL_API fqsl_status fqsl_qmap_plane_static(fqsl_field field, const double origi
  *   dB_dev           B-shaped array (layout of fqsl_field_create) of db_dtype
  *                    (FQSL_F32 or FQSL_F64), accumulated into, not cleared.
  * The reverse sweep runs in the taped call's params->reverse_precision
- * (default: its precision). When that is the tape's precision class and the
- * pool's per-step arrays fit 4 GiB, the taped call kept every accepted step's
- * state and stage derivatives; otherwise they are recomputed from the
- * checkpoints taken every params->tape_chunk accepted steps. The node
+ * (default: its precision). When that is the tape's precision class, the
+ * taped call kept every accepted step's state and stage derivatives for as
+ * many chunks as the tape's previous backward call needed (two per direction
+ * at first; at most 4 GiB); otherwise, or when the map took more chunks, they
+ * are recomputed from the checkpoints taken every params->tape_chunk accepted
+ * steps. The node
  * adjoints accumulate in float (FQSL_F32) or double
   * (FQSL_F32_ACC64, FQSL_F64). The field must not be updated between the
  * taped call and this one; other maps of the field (taped into other tapes or

@@ -97,6 +97,8 @@ struct fqsl_tape_s {
     bool face_plane = false;
     size_t nodes = 0;      // the field's node count (size of the adjoint node grid)
     long long pool = 0;    // tape chunks of the next taped call
+    long long keep_cap = 0;   // chunks whose states the taped call keeps (Tape::wcap; 0: first guess)
+    long long keep_want = 0;  // what the last backward call needed (applied at the next taped call)
     void *buf = nullptr;
     size_t cap = 0;
     void *work = nullptr;  // per-step arrays of the reverse sweep
@@ -775,7 +777,7 @@ constexpr int kDefaultTapeChunk = 16;
 constexpr size_t kKeepBudget = (size_t)4 << 30;
 
 TapeLayout tape_layout(char *base, long long n, bool rot, bool f32, long long pool, int k, size_t nodes,
-                       bool acc64, bool keep)
+                       bool acc64, bool keep, long long wcap)
 {
     TapeLayout t{};
     t.s = layout(base, n, rot, true, f32);
@@ -792,8 +794,9 @@ TapeLayout tape_layout(char *base, long long n, bool rot, bool f32, long long po
     t.tape.head = c.take<int4>((size_t)t.halves);
     t.tape.xe = c.take<char>((size_t)t.halves * 4 * ts);
     t.tape.owner = c.take<int32_t>((size_t)pool);
-    t.tape.wx = keep ? c.take<char>((size_t)pool * (k + 1) * kStateStride * ts) : nullptr;
-    t.tape.wk = keep ? c.take<char>((size_t)pool * k * kStageStride * ts) : nullptr;
+    t.tape.wx = keep ? c.take<char>((size_t)wcap * (k + 1) * kStateStride * ts) : nullptr;
+    t.tape.wk = keep ? c.take<char>((size_t)wcap * k * kStageStride * ts) : nullptr;
+    t.tape.wcap = keep ? wcap : 0;
     t.xbar = c.take<double>((size_t)(3 * t.halves));
     t.xseed = rot ? c.take<double>((size_t)(24 * n)) : nullptr;
     t.sums = c.take<double>(2);
@@ -815,8 +818,10 @@ TapeLayout tape_layout_of(const fqsl_tape t, char *base, long long pool)
     const size_t ts = p.precision == FQSL_F64 ? 8 : 4;
     const bool same = (reverse_precision_of(p) == FQSL_F64) == (p.precision == FQSL_F64);
     const size_t per_chunk = (size_t)((k + 1) * kStateStride + k * kStageStride) * ts;
-    const bool keep = same && (size_t)pool * per_chunk <= kKeepBudget;
-    return tape_layout(base, n, t->lat.allow_rot, p.precision != FQSL_F64, pool, k, t->nodes, acc64_of(p), keep);
+    const long long wcap = t->keep_cap < 1 ? 1 : (t->keep_cap > pool ? pool : t->keep_cap);
+    const bool keep = same && (size_t)wcap * per_chunk <= kKeepBudget;
+    return tape_layout(base, n, t->lat.allow_rot, p.precision != FQSL_F64, pool, k, t->nodes, acc64_of(p), keep,
+                       wcap);
 }
 
 fqsl_status ensure_tape_buf(fqsl_tape t, size_t bytes)
@@ -898,6 +903,10 @@ fqsl_status run_qmap_locked(fqsl_field f, const Lattice &lat0, const fqsl_params
         // first guess: 128 accepted steps per direction on average
         const long long guess = 2 * n * (128 / k + 1) + 1024;
         if (tape->pool < guess) tape->pool = guess;
+        // the kept states: two chunks per direction at first, then what the
+        // last backward call needed
+        if (tape->keep_cap < 1) tape->keep_cap = 4 * n + 1024;
+        if (tape->keep_want > tape->keep_cap) tape->keep_cap = tape->keep_want;
         fqsl_status st = ensure_tape_buf(tape, tape_layout_of(tape, nullptr, tape->pool).bytes);
         if (st != FQSL_OK) return st;
         tl = tape_layout_of(tape, (char *)tape->buf, tape->pool);
@@ -1670,7 +1679,10 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, fqsl_tape tp, const double *d
     // states and stage derivatives are the tape's own when the forward kept them)
     const int K = tl.tape.k;
     const size_t rs = rp == FQSL_F64 ? 8 : 4;
-    const bool stored = tl.tape.wx != nullptr;
+    const bool stored = tl.tape.wx != nullptr && (long long)used <= tl.tape.wcap;
+    // the next taped call keeps as many chunks as this map used, with room
+    const long long want = (long long)(used + used / 4 + 1024);
+    if (want > tp->keep_want) tp->keep_want = want;
     const size_t bx = stored ? 0 : align_up((size_t)used * (K + 1) * kStateStride * rs),
                  bj = align_up((size_t)used * K * 12 * rs),
                  bk = stored ? 0 : align_up((size_t)used * K * kStageStride * rs), bb = align_up((size_t)used * K * 3 * rs),

@@ -164,8 +164,10 @@ struct Tape {
     //   wk [cap][k][kStageStride] T: position derivatives of stages 0..4 of
     //      each step (stage s at 3 s, zero padding at 15)
     // (padded so that each state and each step's record is written and read
-    // with 16-byte vector accesses)
+    // with 16-byte vector accesses). They hold chunks [0, wcap) only; a map
+    // that takes more chunks is recomputed from its checkpoints instead.
     void *wx, *wk;
+    long long wcap;
 };
 
 constexpr int kStateStride = 4;

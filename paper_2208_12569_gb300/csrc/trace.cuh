@@ -999,7 +999,7 @@ __device__ __forceinline__ bool tape_chunk(const Tape &tp, Lane<T> &L)
     x[1] = L.y;
     x[2] = L.z;
     x[3] = (T)0;
-    if (tp.wx) store_state((T *)tp.wx + c * (long long)(tp.k + 1) * kStateStride, L.x, L.y, L.z);
+    if (tp.wx && (long long)c < tp.wcap) store_state((T *)tp.wx + c * (long long)(tp.k + 1) * kStateStride, L.x, L.y, L.z);
     L.tcur = (int)c;
     L.tn = 0;
     return true;
@@ -1016,7 +1016,7 @@ __device__ __forceinline__ void tape_step(const Tape &tp, Lane<T> &L, T h, const
     if ((L.tcur < 0 || L.tn == tp.k) && !tape_chunk(tp, L)) return;
     const long long j = (long long)L.tcur * tp.k + L.tn;
     ((T *)tp.h)[j] = h;
-    if (tp.wx) {
+    if (tp.wx && L.tcur < tp.wcap) {
         T v[kStageStride];
 #pragma unroll
         for (int s = 0; s < NS; s++) {

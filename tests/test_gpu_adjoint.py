@@ -280,6 +280,22 @@ def test_tape_pool_grows_when_exhausted(fq, small):
     assert _rel(g1, ref) < 1e-10
 
 
+def test_kept_states_grow_to_the_map(fq, small):
+    # one step per chunk: the first taped call keeps the states of two chunks
+    # per direction, fewer than the map takes, so its backward recomputes them
+    # from the checkpoints; the next taped call on the same tape keeps every
+    # chunk the first one used. Both gradients equal the oracle adjoint.
+    B, _, grid = small
+    field = _field(fq, B, grid)
+    m = PLANE16[3] * PLANE16[4]
+    wq, wt = _weights(23, m)
+    g1, _ = _gpu_vjp(fq, field, PLANE16, wq, wt, precision="f64", tape_chunk=1)
+    g2, _ = _gpu_vjp(fq, field, PLANE16, wq, wt, precision="f64", tape_chunk=1)
+    assert _rel(g2, g1) < 1e-12
+    ref, _ = adj.vjp(B, grid, *PLANE16, wq, wt, oracle.params())
+    assert _rel(g1, ref) < 1e-10 and _rel(g2, ref) < 1e-10
+
+
 def test_loss_kernel_matches_oracle_loss(fq, small):
     B, Bt, grid = small
     field = _field(fq, B, grid)
