@@ -73,15 +73,13 @@ __device__ __forceinline__ Cell<float> cell_of(const FieldView &f, float x, floa
 
 __device__ __forceinline__ Cell<double> cell_of(const FieldView &f, double x, double y, double z)
 {
-    const double cx = trace::clampcell<double>(floor(x), f.nx);
-    const double cy = trace::clampcell<double>(floor(y), f.ny);
-    const double cz = trace::clampcell<double>(floor(z), f.nz);
+    const int cx = trace::cell_floor64(x, f.nx), cy = trace::cell_floor64(y, f.ny), cz = trace::cell_floor64(z, f.nz);
     Cell<double> c;
     c.base = ((long long)cz * f.ny + (long long)cy) * f.nx + (long long)cx;
     // the FP64 gather forms omega_0 = (c+1) - xi and omega_1 = 1 - omega_0
-    c.w0[0] = (cx + 1.0) - x;
-    c.w0[1] = (cy + 1.0) - y;
-    c.w0[2] = (cz + 1.0) - z;
+    c.w0[0] = trace::int_f64(cx + 1) - x;
+    c.w0[1] = trace::int_f64(cy + 1) - y;
+    c.w0[2] = trace::int_f64(cz + 1) - z;
     for (int a = 0; a < 3; a++) c.w1[a] = 1.0 - c.w0[a];
     return c;
 }

@@ -260,6 +260,7 @@ fqsl_status fqsl_field_create(const void *B_dev, fqsl_dtype b_dtype, long long n
         f->g.d[a] = spacing[a];
         f->g.rd[a] = (float)(1.0 / spacing[a]);
     }
+    f->g.unit = spacing[0] == 1.0 && spacing[1] == 1.0 && spacing[2] == 1.0;
     return finish_create(f, B_dev, b_dtype, flags, cuda_stream, out, who);
 }
 

@@ -33,6 +33,7 @@ struct FieldView {
     double d[3];  // spacing
     float cmax[3];            // largest cell index per axis, n - 2, as float
     float rd[3];              // 1 / spacing, as float
+    int unit;                 // spacing (1, 1, 1): FP64 divisions by it are skipped (exact either way)
     unsigned sy32, sz32;      // FP32 record byte strides along y and z
     const void *grad;         // grad(B/|B|) node records (Method II way 1) or NULL:
                               // FP32 48 B {g0..g8, 0, 0, 0}, FP64 80 B {g0..g8, 0}

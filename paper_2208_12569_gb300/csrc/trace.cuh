@@ -147,18 +147,32 @@ __device__ __forceinline__ void load_node(const FieldView &f, long long node, do
     jz = c.y;
 }
 
-template <typename T>
-__device__ __forceinline__ T tfloor(T v);
-template <>
-__device__ __forceinline__ float tfloor<float>(float v) { return floorf(v); }
-template <>
-__device__ __forceinline__ double tfloor<double>(double v) { return floor(v); }
 
-template <typename T>
-__device__ __forceinline__ T clampcell(T c, int n)
+// FP64 cells on the integer pipe (GB300's FP64 pipe is the FP64 tracer's
+// bound, and it would also run the floor, clamps and conversions): the cell
+// min(max(floor(x), 0), n - 2) as an integer (NaN and x < 0 give 0,
+// x >= n - 2 and +inf give n - 2), read off the double's exponent and mantissa.
+__device__ __forceinline__ int cell_floor64(double x, int n)
 {
-    // fmax/fmin return the non-NaN operand: a NaN position maps to cell 0
-    return fmin(fmax(c, (T)0), (T)(n - 2));
+    const long long u = __double_as_longlong(x);
+    const int top = n - 2;
+    if (u < 0) return 0;  // sign set: negative, -0, a negative NaN
+    const int e = (int)(u >> 52);
+    if (e == 0x7ff) return (u & 0xfffffffffffffLL) ? 0 : top;  // NaN, +inf
+    if (e < 1023) return 0;                                    // [0, 1)
+    if (e >= 1023 + 31) return top;
+    const unsigned long long m = ((unsigned long long)u & 0xfffffffffffffULL) | (1ULL << 52);
+    const long long c = (long long)(m >> (52 - (e - 1023)));
+    return c > top ? top : (int)c;
+}
+
+// an integer in [0, 2^31) as the double of the same value (exact)
+__device__ __forceinline__ double int_f64(int c)
+{
+    if (c <= 0) return 0.0;
+    const int p = 31 - __clz(c);
+    const unsigned long long m = ((unsigned long long)c << (52 - p)) & 0xfffffffffffffULL;
+    return __longlong_as_double((long long)(((unsigned long long)(p + 1023) << 52) | m));
 }
 
 // One 32-byte FP32 node record in a single 256-bit read-only load (records are
@@ -248,13 +262,13 @@ __device__ __forceinline__ void gather(const FieldView &f, float x, float y, flo
 __device__ __forceinline__ void gather(const FieldView &f, double x, double y, double z, double B[3], double J[3],
                                        bool wj = true)
 {
-    const double c[3] = {clampcell<double>(floor(x), f.nx), clampcell<double>(floor(y), f.ny),
-                         clampcell<double>(floor(z), f.nz)};
+    // (c + 1 as a double is exact, so int_f64(c + 1) is the c + 1.0 of the form)
+    const int c[3] = {cell_floor64(x, f.nx), cell_floor64(y, f.ny), cell_floor64(z, f.nz)};
     const double xi[3] = {x, y, z};
     double w[3][2];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        w[a][0] = (c[a] + 1.0) - xi[a];
+        w[a][0] = int_f64(c[a] + 1) - xi[a];
         w[a][1] = 1.0 - w[a][0];
     }
     const long long sy = f.nx, sz = (long long)f.nx * f.ny;
@@ -523,7 +537,8 @@ __device__ __forceinline__ bool rhs(const FieldView &f, const double d[3], doubl
 {
     double B[3], J[3];
     gather(f, x, y, z, B, J);
-    const double bt[3] = {B[0] / d[0], B[1] / d[1], B[2] / d[2]};
+    // (on a unit-spacing grid B_a / 1 = B_a exactly: no division)
+    const double bt[3] = {f.unit ? B[0] : B[0] / d[0], f.unit ? B[1] : B[1] / d[1], f.unit ? B[2] : B[2] / d[2]};
     const double bb = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
     const double BB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
     if (!(bb > 0.0) || !(bb < INFINITY)) return false;
@@ -675,15 +690,14 @@ __device__ __forceinline__ void gather_grad_cell(const FieldView &f, const long 
 
 __device__ __forceinline__ void gather_grad(const FieldView &f, double x, double y, double z, double G[3][3])
 {
-    const double cf[3] = {clampcell<double>(floor(x), f.nx), clampcell<double>(floor(y), f.ny),
-                          clampcell<double>(floor(z), f.nz)};
+    const int cf[3] = {cell_floor64(x, f.nx), cell_floor64(y, f.ny), cell_floor64(z, f.nz)};
     const double xi[3] = {x, y, z};
     long long c[3];
     double w[3][2];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        c[a] = (long long)cf[a];
-        w[a][0] = (cf[a] + 1.0) - xi[a];
+        c[a] = cf[a];
+        w[a][0] = int_f64(cf[a] + 1) - xi[a];
         w[a][1] = 1.0 - w[a][0];
     }
     gather_grad_cell(f, c, w, G);
