@@ -1651,31 +1651,66 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, fqsl_tape tp, const double *d
     if (tp->gen != f->gen)
         return fail(FQSL_ERR_ARG, "%s: the field was updated after the taped map (trace it again)", who);
     const fqsl_params p = tp->p;
-    // the pool of the taped call must have held every chunk; if not, trace the
-    // same map again with a larger pool (the map is deterministic)
-    unsigned long long used = 0;
-    for (int attempt = 0;; attempt++) {
-        // the taped call copied its chunk count once its tracers finished
-        if (!tp->used_ev || !tp->used_host) return fail(FQSL_ERR_ARG, "%s: the tape holds no complete taped map", who);
-        cudaError_t e = cudaEventSynchronize(tp->used_ev);
-        if (e != cudaSuccess) return cuda_fail(e, who);
-        used = *(volatile unsigned long long *)tp->used_host;
-        if (used <= (unsigned long long)tp->pool) break;
-        if (attempt >= 2) return fail(FQSL_ERR_CUDA, "%s: step tape pool still exhausted after re-tracing", who);
-        tp->pool = (long long)(used + used / 4 + 1024);
-        const Lattice lat = tp->lat;
-        const fqsl_out none{};
-        fqsl_status st = run_qmap_locked(f, lat, &p, &none, stream, tp->face_plane, tp, who);
-        if (st != FQSL_OK) return st;
-    }
-    TapeLayout tl = tape_layout_of(tp, (char *)tp->buf, tp->pool);
-    const Lattice &lat = tp->lat;
-    const long long n = lat.n1 * lat.n2 * lat.n3;
     const size_t nodes = (size_t)f->g.nx * f->g.ny * f->g.nz;
     const int rp = reverse_precision_of(p);
     const bool acc64 = acc64_of(p);
     const int mode = rp == FQSL_F64 ? 2 : (acc64 ? 1 : 0);
     const bool tape_f64 = p.precision == FQSL_F64;
+    // The pool of the taped call must have held every chunk; if not, trace the
+    // same map again with a larger pool (the map is deterministic). The clears
+    // of the adjoint buffers and the Q-assembly VJP do not depend on the chunk
+    // count, so they are queued before the host waits for the taped call's
+    // tracers: the GPU has them to run while the host wakes and launches the
+    // reverse sweep.
+    unsigned long long used = 0;
+    TapeLayout tl{};
+    AdjArgs a{};
+    for (int attempt = 0;; attempt++) {
+        if (!tp->used_ev || !tp->used_host) return fail(FQSL_ERR_ARG, "%s: the tape holds no complete taped map", who);
+        tl = tape_layout_of(tp, (char *)tp->buf, tp->pool);
+        const Lattice &lat = tp->lat;
+        const long long n = lat.n1 * lat.n2 * lat.n3;
+        cudaError_t e = cudaMemsetAsync(tl.xbar, 0, (size_t)(3 * tl.halves) * sizeof(double), stream);
+        if (e == cudaSuccess && tl.xseed) e = cudaMemsetAsync(tl.xseed, 0, (size_t)(24 * n) * sizeof(double), stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(tl.acc, 0, nodes * 8 * (acc64 ? 8 : 4), stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(tl.ctr + 1, 0, sizeof(unsigned long long), stream);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+        a = AdjArgs{};
+        a.f = f->g;
+        a.f.rec = rp == FQSL_F64 ? f->rec64 : f->rec32;
+        a.f.grad = nullptr;
+        a.f.err = f->counters + 4;  // the field's record of failed index checks (fqsl_field_check)
+        a.p = dev_params(&p);
+        a.lat = lat;
+        a.rec = tl.s.rec;
+        a.prep = tl.s.prep;
+        a.tape = tl.tape;
+        a.dQ = dQ_dev;
+        a.dTw = dTw_dev;
+        a.xbar = tl.xbar;
+        a.acc = tl.acc;
+        a.n = n;
+        if (lat.allow_rot) {
+            a.ext = tl.s.ext;
+            a.rot_slot = tl.s.rot_slot;
+            a.rot_seed = tl.s.rot_seed;
+            a.rot_count = (const unsigned *)(tl.ctr + 4);
+            a.xseed = tl.xseed;
+        }
+        e = launch_q_vjp(a, mode, tape_f64, stream);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+        // the taped call copied its chunk count once its tracers finished
+        e = cudaEventSynchronize(tp->used_ev);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+        used = *(volatile unsigned long long *)tp->used_host;
+        if (used <= (unsigned long long)tp->pool) break;
+        if (attempt >= 2) return fail(FQSL_ERR_CUDA, "%s: step tape pool still exhausted after re-tracing", who);
+        tp->pool = (long long)(used + used / 4 + 1024);
+        const Lattice lat0 = tp->lat;
+        const fqsl_out none{};
+        fqsl_status st = run_qmap_locked(f, lat0, &p, &none, stream, tp->face_plane, tp, who);
+        if (st != FQSL_OK) return st;
+    }
     // per-step work arrays of the reverse sweep for the chunks in use (the
     // states and stage derivatives are the tape's own when the forward kept them)
     const int K = tl.tape.k;
@@ -1703,33 +1738,6 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, fqsl_tape tp, const double *d
         }
         tp->work_cap = wbytes;
     }
-    cudaError_t e = cudaMemsetAsync(tl.xbar, 0, (size_t)(3 * tl.halves) * sizeof(double), stream);
-    if (e == cudaSuccess && tl.xseed) e = cudaMemsetAsync(tl.xseed, 0, (size_t)(24 * n) * sizeof(double), stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tl.acc, 0, nodes * 8 * (acc64 ? 8 : 4), stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tl.ctr + 1, 0, sizeof(unsigned long long), stream);
-    if (e != cudaSuccess) return cuda_fail(e, who);
-    AdjArgs a{};
-    a.f = f->g;
-    a.f.rec = rp == FQSL_F64 ? f->rec64 : f->rec32;
-    a.f.grad = nullptr;
-    a.f.err = f->counters + 4;  // the field's record of failed index checks (fqsl_field_check)
-    a.p = dev_params(&p);
-    a.lat = lat;
-    a.rec = tl.s.rec;
-    a.prep = tl.s.prep;
-    a.tape = tl.tape;
-    a.dQ = dQ_dev;
-    a.dTw = dTw_dev;
-    a.xbar = tl.xbar;
-    a.acc = tl.acc;
-    a.n = n;
-    if (lat.allow_rot) {
-        a.ext = tl.s.ext;
-        a.rot_slot = tl.s.rot_slot;
-        a.rot_seed = tl.s.rot_seed;
-        a.rot_count = (const unsigned *)(tl.ctr + 4);
-        a.xseed = tl.xseed;
-    }
     a.chunks = (long long)used;
     a.stored = stored ? 1 : 0;
     a.wx = stored ? tl.tape.wx : tp->work;
@@ -1739,8 +1747,7 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, fqsl_tape tp, const double *d
     a.cinfo = (int4 *)((char *)tp->work + bx + bj + bk + bb);
     a.steps = (int32_t *)((char *)tp->work + bx + bj + bk + bb + bi);
     a.nsteps = tl.ctr + 1;  // cleared above
-    e = launch_q_vjp(a, mode, tape_f64, stream);
-    if (e != cudaSuccess) return cuda_fail(e, who);
+    cudaError_t e = cudaSuccess;
     mark(f, 0, stream);
     e = launch_reverse(a, mode, tape_f64, stream);
     if (e != cudaSuccess) return cuda_fail(e, who);
