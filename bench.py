@@ -1170,7 +1170,12 @@ def main():
     torch.cuda.set_device(dev)
     import __graft_entry__
 
-    __graft_entry__._builder().build()
+    # one rank builds (a no-op when the library is current); the others wait
+    # rather than compile into the same build folder at once
+    if rank == 0:
+        __graft_entry__._builder().build()
+    if dist:
+        dist.barrier()
     import paper_2208_12569_gb300 as fq
 
     B, grid, u, v = c2_inputs(rank)
