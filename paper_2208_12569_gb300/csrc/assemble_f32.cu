@@ -165,10 +165,11 @@ __device__ __forceinline__ void assemble_one_f32(const AssembleArgs &A, long lon
 
 namespace {
 
-// (3 blocks of 256 per SM: the kernel is bound by the FP64 pipe's latency, and
-// the compiler's unconstrained choice, 86 registers, fits only 2: 0.170 ms
-// against 0.141 ms on the 1024^2 map)
-__global__ void __launch_bounds__(256, 3) k_assemble_f32(const AssembleArgs A)
+// (4 blocks of 256 per SM, 64 registers: the kernel waits on the FP64 pipe and
+// on the neighbouring lines' records. On the 1024^2 map: 0.123 ms, against
+// 0.141 ms at 3 blocks, 0.137 ms at 5 and 6, and 0.170 ms with the compiler's
+// unconstrained 86 registers, which fit only 2)
+__global__ void __launch_bounds__(256, 4) k_assemble_f32(const AssembleArgs A)
 {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < A.n;
          idx += (long long)gridDim.x * blockDim.x)
@@ -270,7 +271,7 @@ __device__ __forceinline__ int batch_entry(const long long *__restrict__ base, i
     return lo;
 }
 
-__global__ void __launch_bounds__(256, 3) k_batch_assemble_f32(const AssembleArgs *__restrict__ desc,
+__global__ void __launch_bounds__(256, 4) k_batch_assemble_f32(const AssembleArgs *__restrict__ desc,
                                                             const long long *__restrict__ nbase, int nent)
 {
     const long long total = nbase[nent];
