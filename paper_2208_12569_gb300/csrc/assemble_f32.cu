@@ -17,37 +17,6 @@
 namespace fqsl {
 namespace {
 
-// float -> double, exactly, on the integer pipe: the assembly is bound by
-// GB300's narrow FP64 pipe, which also runs the hardware conversion. Normal
-// numbers move their exponent from bias 127 to 1023 and their mantissa to the
-// top of the double's; subnormals are normalised by their leading one; zeros,
-// infinities and NaNs keep their class.
-__device__ __forceinline__ double f2d(float f)
-{
-    const unsigned b = __float_as_uint(f);
-    const unsigned sign = b & 0x80000000u;
-    const unsigned e = (b >> 23) & 0xffu;
-    const unsigned m = b & 0x7fffffu;
-    unsigned hi, lo;
-    if (e == 0xffu) {
-        hi = sign | 0x7ff00000u | (m >> 3);
-        lo = m << 29;
-    } else if (e != 0u) {
-        hi = sign | ((e + 896u) << 20) | (m >> 3);
-        lo = m << 29;
-    } else if (m == 0u) {
-        hi = sign;
-        lo = 0u;
-    } else {
-        // m 2^-149 with its leading one at bit p: 1.f 2^(p - 149)
-        const int p = 31 - __clz(m);
-        const unsigned mm = (m << (23 - p)) & 0x7fffffu;
-        hi = sign | ((unsigned)(p + 874) << 20) | (mm >> 3);
-        lo = mm << 29;
-    }
-    return __hiloint2double((int)hi, (int)lo);
-}
-
 // the two non-normal axes of a face, in increasing order
 __device__ __forceinline__ void face_axes(int face, int &r0, int &r1)
 {
@@ -62,7 +31,7 @@ __device__ __forceinline__ double bn_at(const FieldView &f, const float *xi, int
     if (f.rect) trace::gather_rect(f, xi[0], xi[1], xi[2], B, J);
     else trace::gather(f, xi[0], xi[1], xi[2], B, J);
     const int a = face >> 1;
-    return f2d(a == 0 ? B[0] : (a == 1 ? B[1] : B[2]));
+    return trace::f2d(a == 0 ? B[0] : (a == 1 ? B[1] : B[2]));
 }
 
 }  // namespace
@@ -119,9 +88,9 @@ __device__ __forceinline__ void assemble_one_f32(const AssembleArgs &A, long lon
                         cm = (e == 0 ? NR->xi1 : NR->xi2) + 3 * nid[M];
                     for (int r = 0; r < 2; r++) {
                         const int a = ra[r];
-                        if (cp && cm) Jm[e][r][s] = f2d(cp[a] - cm[a]) * (0.5 * scs[a]);
-                        else if (cp) Jm[e][r][s] = f2d(cp[a] - c0[a]) * scs[a];
-                        else if (cm) Jm[e][r][s] = f2d(c0[a] - cm[a]) * scs[a];
+                        if (cp && cm) Jm[e][r][s] = trace::f2d(cp[a] - cm[a]) * (0.5 * scs[a]);
+                        else if (cp) Jm[e][r][s] = trace::f2d(cp[a] - c0[a]) * scs[a];
+                        else if (cm) Jm[e][r][s] = trace::f2d(c0[a] - cm[a]) * scs[a];
                         else mixed = true;
                     }
                 }
@@ -146,16 +115,16 @@ __device__ __forceinline__ void assemble_one_f32(const AssembleArgs &A, long lon
             double tw = NAN, len = NAN;
             if (!bad) {
                 const float4 k0 = R.kacc[2 * idx], k1 = R.kacc[2 * idx + 1];
-                len = (f2d(k0.x) - f2d(k0.y)) + (f2d(k1.x) - f2d(k1.y));
-                tw = (f2d(k0.z) - f2d(k0.w)) + (f2d(k1.z) - f2d(k1.w));
+                len = (trace::f2d(k0.x) - trace::f2d(k0.y)) + (trace::f2d(k1.x) - trace::f2d(k1.y));
+                tw = (trace::f2d(k0.z) - trace::f2d(k0.w)) + (trace::f2d(k1.z) - trace::f2d(k1.w));
             }
             if (o.Tw) o.Tw[idx] = tw;
             if (o.length) o.length[idx] = len;
         }
         if (o.r1)
-            for (int c = 0; c < 3; c++) o.r1[3 * idx + c] = fma(f.d[c], f2d(x1[c]), f.o[c]);
+            for (int c = 0; c < 3; c++) o.r1[3 * idx + c] = fma(f.d[c], trace::f2d(x1[c]), f.o[c]);
         if (o.r2)
-            for (int c = 0; c < 3; c++) o.r2[3 * idx + c] = fma(f.d[c], f2d(x2[c]), f.o[c]);
+            for (int c = 0; c < 3; c++) o.r2[3 * idx + c] = fma(f.d[c], trace::f2d(x2[c]), f.o[c]);
         if (o.face1) o.face1[idx] = (int8_t)f1;
         if (o.face2) o.face2[idx] = (int8_t)f2;
         if (o.status) o.status[idx] = (uint8_t)st;
@@ -228,16 +197,16 @@ __global__ void __launch_bounds__(256) k_assemble_m2_f32(const AssembleArgs A)
             double tw = NAN, len = NAN;
             if (!bad) {
                 const float4 k0 = R.kacc[2 * idx], k1 = R.kacc[2 * idx + 1];
-                len = (f2d(k0.x) - f2d(k0.y)) + (f2d(k1.x) - f2d(k1.y));
-                tw = (f2d(k0.z) - f2d(k0.w)) + (f2d(k1.z) - f2d(k1.w));
+                len = (trace::f2d(k0.x) - trace::f2d(k0.y)) + (trace::f2d(k1.x) - trace::f2d(k1.y));
+                tw = (trace::f2d(k0.z) - trace::f2d(k0.w)) + (trace::f2d(k1.z) - trace::f2d(k1.w));
             }
             if (o.Tw) o.Tw[idx] = tw;
             if (o.length) o.length[idx] = len;
         }
         if (o.r1)
-            for (int c = 0; c < 3; c++) o.r1[3 * idx + c] = fma(f.d[c], f2d(x1[c]), f.o[c]);
+            for (int c = 0; c < 3; c++) o.r1[3 * idx + c] = fma(f.d[c], trace::f2d(x1[c]), f.o[c]);
         if (o.r2)
-            for (int c = 0; c < 3; c++) o.r2[3 * idx + c] = fma(f.d[c], f2d(x2[c]), f.o[c]);
+            for (int c = 0; c < 3; c++) o.r2[3 * idx + c] = fma(f.d[c], trace::f2d(x2[c]), f.o[c]);
         if (o.face1) o.face1[idx] = (int8_t)f1;
         if (o.face2) o.face2[idx] = (int8_t)f2;
         if (o.status) o.status[idx] = (uint8_t)st;

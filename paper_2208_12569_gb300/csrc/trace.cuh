@@ -166,6 +166,37 @@ __device__ __forceinline__ int cell_floor64(double x, int n)
     return c > top ? top : (int)c;
 }
 
+// float -> double, exactly, on the integer pipe (GB300's narrow FP64 pipe
+// would also run the hardware conversion). Normal
+// numbers move their exponent from bias 127 to 1023 and their mantissa to the
+// top of the double's; subnormals are normalised by their leading one; zeros,
+// infinities and NaNs keep their class.
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned sign = b & 0x80000000u;
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned m = b & 0x7fffffu;
+    unsigned hi, lo;
+    if (e == 0xffu) {
+        hi = sign | 0x7ff00000u | (m >> 3);
+        lo = m << 29;
+    } else if (e != 0u) {
+        hi = sign | ((e + 896u) << 20) | (m >> 3);
+        lo = m << 29;
+    } else if (m == 0u) {
+        hi = sign;
+        lo = 0u;
+    } else {
+        // m 2^-149 with its leading one at bit p: 1.f 2^(p - 149)
+        const int p = 31 - __clz(m);
+        const unsigned mm = (m << (23 - p)) & 0x7fffffu;
+        hi = sign | ((unsigned)(p + 874) << 20) | (mm >> 3);
+        lo = mm << 29;
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
 // an integer in [0, 2^31) as the double of the same value (exact)
 __device__ __forceinline__ double int_f64(int c)
 {
@@ -173,6 +204,15 @@ __device__ __forceinline__ double int_f64(int c)
     const int p = 31 - __clz(c);
     const unsigned long long m = ((unsigned long long)c << (52 - p)) & 0xfffffffffffffULL;
     return __longlong_as_double((long long)(((unsigned long long)(p + 1023) << 52) | m));
+}
+
+// i + 1/2 as a double (exact): (2i + 1) made a double by its bits, halved
+// by its exponent
+__device__ __forceinline__ double half_odd(unsigned i)
+{
+    if (i >= (1u << 30)) return (double)i + 0.5;
+    const double d = int_f64((int)(2u * i + 1u));
+    return __longlong_as_double(__double_as_longlong(d) - (1LL << 52));
 }
 
 // One 32-byte FP32 node record in a single 256-bit read-only load (records are
@@ -1930,7 +1970,7 @@ __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
     // 32-bit index arithmetic (a lattice holds fewer than 2^31 seeds)
     const unsigned u = (unsigned)idx, n1 = (unsigned)G.n1, n12 = (unsigned)(G.n1 * G.n2);
     const unsigned k = u / n12, rem = u - k * n12, j = rem / n1, i = rem - j * n1;
-    const double fi = (double)i + 0.5, fj = (double)j + 0.5, fk = (double)k + 0.5;
+    const double fi = half_odd(i), fj = half_odd(j), fk = half_odd(k);
     double xi[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) xi[a] = fma(fk, G.xa3[a], fma(fj, G.xa2[a], fma(fi, G.xa1[a], G.xo[a])));
@@ -1954,7 +1994,7 @@ __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
             const float bn = B0[0] * (float)G.n0[0] + B0[1] * (float)G.n0[1] + B0[2] * (float)G.n0[2];
             if (bn < 0.f) fl |= kSeedNegS0;
             if (A.p.method == 2) {
-                bn0 = (double)nB;
+                bn0 = f2d(nB);
             } else {
                 const float ratio = fabsf(bn) / nB;
                 bool on_face = false;
@@ -1964,18 +2004,18 @@ __device__ __forceinline__ void seed_prep_f32(const TraceArgs &A, long long idx)
                 }
                 if (G.allow_rot && ratio < (float)A.p.rot && !on_face) {
                     fl |= kSeedRotated;
-                    bn0 = (double)nB;
+                    bn0 = f2d(nB);
                     const unsigned slot = atomicAdd(A.q.rot_count, 1u);
                     A.q.rot_seed[slot] = (int32_t)idx;
                     A.q.rot_slot[idx] = (int32_t)slot + 1;
                 } else if (A.p.scheme == 1) {
-                    bn0 = (double)bn;
-                    tol = fmax(A.p.step * (double)ratio, A.p.step_min);  // Eq. step
+                    bn0 = f2d(bn);
+                    tol = fmax(A.p.step * f2d(ratio), A.p.step_min);  // Eq. step
                 } else {
-                    bn0 = (double)bn;
+                    bn0 = f2d(bn);
                     const float xr = fmaxf(ratio, (float)A.p.rot);
                     const float g = A.p.texp == 1.5 ? xr * sqrtf(xr) : __powf(xr, (float)A.p.texp);
-                    tol = A.p.tol * (double)g;
+                    tol = A.p.tol * f2d(g);
                 }
             }
         }
