@@ -423,6 +423,13 @@ FQSL_API fqsl_status fqsl_loss_logq_tw(long long n, const double *Q_dev, const d
  * record is cleared. */
 FQSL_API fqsl_status fqsl_field_check(fqsl_field field, void *cuda_stream);
 
+/* Testing aid (the paper has no counterpart): every later device allocation
+ * the library makes that is larger than `bytes` fails as if the device were
+ * out of memory, so that callers' and the library's out-of-memory paths can
+ * be exercised without exhausting the GPU. 0 removes the cap (the default).
+ * Process-wide; allocations already made are kept. */
+FQSL_API void fqsl_debug_alloc_cap(unsigned long long bytes);
+
 #ifdef __cplusplus
 }
 #endif

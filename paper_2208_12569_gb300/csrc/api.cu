@@ -37,6 +37,21 @@ fqsl_status cuda_fail(cudaError_t e, const char *what)
     return fail(FQSL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Every device allocation of the library goes through dev_malloc, so that a
+// test can make one fail as out of memory on demand (fqsl_debug_alloc_cap):
+// the failure paths run without exhausting the GPU.
+std::atomic<unsigned long long> g_alloc_cap{0};
+
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    const unsigned long long cap = g_alloc_cap.load();
+    if (cap != 0 && (unsigned long long)bytes > cap) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 bool finite3(const double *v) { return v && isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
 
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -184,13 +199,13 @@ fqsl_status finish_create(fqsl_field f, const void *B_dev, fqsl_dtype b_dtype, u
 {
     const size_t nodes = (size_t)f->g.nodes;
     cudaError_t e = cudaSuccess;
-    if (flags & FQSL_PACK_F32) e = cudaMalloc(&f->rec32, nodes * 32);
-    if (e == cudaSuccess && (flags & FQSL_PACK_F64)) e = cudaMalloc(&f->rec64, nodes * 64);
+    if (flags & FQSL_PACK_F32) e = dev_malloc((void **)&f->rec32, nodes * 32);
+    if (e == cudaSuccess && (flags & FQSL_PACK_F64)) e = dev_malloc((void **)&f->rec64, nodes * 64);
     if (e == cudaSuccess && (flags & FQSL_PACK_GRADB)) {
-        if (f->rec32) e = cudaMalloc(&f->grad32, nodes * 48);
-        if (e == cudaSuccess && f->rec64) e = cudaMalloc(&f->grad64, nodes * 80);
+        if (f->rec32) e = dev_malloc((void **)&f->grad32, nodes * 48);
+        if (e == cudaSuccess && f->rec64) e = dev_malloc((void **)&f->grad64, nodes * 80);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&f->counters, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = dev_malloc((void **)&f->counters, 8 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_field(f);
@@ -235,6 +250,8 @@ void fqsl_params_default(fqsl_params *p)
 }
 
 const char *fqsl_version(void) { return "fqsl 0.1.0 (sm_103a)"; }
+
+void fqsl_debug_alloc_cap(unsigned long long bytes) { g_alloc_cap.store(bytes); }
 
 const char *fqsl_last_error(void) { return g_err.c_str(); }
 
@@ -370,7 +387,7 @@ fqsl_status fqsl_field_create_rect(const void *B_dev, fqsl_dtype b_dtype, long l
     const size_t s0 = align_up(x64.size() * sizeof(double)), s1 = align_up(cell64.size() * sizeof(double2)),
                  s2 = align_up(cell32.size() * sizeof(float4)), s3 = align_up(bkt.size() * sizeof(int)),
                  s4 = align_up(bk32.size() * sizeof(float4)), s5 = align_up(dco.size() * sizeof(double));
-    cudaError_t e = cudaMalloc(&f->rect_buf, s0 + s1 + s2 + s3 + s4 + s5);
+    cudaError_t e = dev_malloc((void **)&f->rect_buf, s0 + s1 + s2 + s3 + s4 + s5);
     if (e != cudaSuccess) {
         delete f;
         cudaGetLastError();
@@ -647,7 +664,7 @@ fqsl_status ensure_scratch(fqsl_field f, size_t bytes)
     cudaFree(f->scratch);
     f->scratch = nullptr;
     f->scratch_cap = 0;
-    e = cudaMalloc(&f->scratch, bytes);
+    e = dev_malloc((void **)&f->scratch, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_fail(e, "scratch allocation");
@@ -833,7 +850,7 @@ fqsl_status ensure_tape_buf(fqsl_tape t, size_t bytes)
     cudaFree(t->buf);
     t->buf = nullptr;
     t->cap = 0;
-    e = cudaMalloc(&t->buf, bytes);
+    e = dev_malloc((void **)&t->buf, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_fail(e, "tape buffer allocation");
@@ -1517,7 +1534,7 @@ extern "C" fqsl_status fqsl_batch_create(const fqsl_field *fields, const fqsl_pl
     const size_t rc_off = align_up(xb_off + (n + 1) * sizeof(long long));
     const size_t hd_off = align_up(rc_off + n * sizeof(unsigned));
     const size_t total = align_up(hd_off + 4 * sizeof(unsigned long long));
-    cudaError_t e = cudaMalloc(&b->mem, total);
+    cudaError_t e = dev_malloc((void **)&b->mem, total);
     if (e != cudaSuccess) {
         delete b;
         cudaGetLastError();
@@ -1730,7 +1747,7 @@ extern "C" fqsl_status fqsl_backward(fqsl_field f, fqsl_tape tp, const double *d
             cudaFree(tp->work);
             tp->work = nullptr;
             tp->work_cap = 0;
-            e0 = cudaMalloc(&tp->work, wbytes);
+            e0 = dev_malloc((void **)&tp->work, wbytes);
         }
         if (e0 != cudaSuccess) {
             cudaGetLastError();

@@ -23,7 +23,7 @@ EXPORTS = ("fqsl_params_default", "fqsl_version", "fqsl_last_error", "fqsl_field
            "fqsl_qmap_plane", "fqsl_qmap_volume", "fqsl_twist", "fqsl_field_check", "fqsl_field_set_timing",
            "fqsl_field_times", "fqsl_field_update", "fqsl_qmap_plane_static", "fqsl_batch_create", "fqsl_batch_run",
            "fqsl_batch_destroy", "fqsl_backward", "fqsl_loss_logq_tw", "fqsl_tape_export",
-           "fqsl_tape_destroy", "fqsl_field_create_rect")
+           "fqsl_tape_destroy", "fqsl_field_create_rect", "fqsl_debug_alloc_cap")
 STATIC_MAX_SEEDS = 65536
 
 
@@ -85,9 +85,11 @@ def load(path: str = LIB_PATH):
     lib.fqsl_tape_export.argtypes = [P, C.c_int, P, P, P, P, P]
     lib.fqsl_tape_destroy.argtypes = [P]
     lib.fqsl_loss_logq_tw.argtypes = [C.c_longlong, P, P, P, P, P, C.c_double, P, P, P, P, P]
+    lib.fqsl_debug_alloc_cap.argtypes = [C.c_ulonglong]
     for name in EXPORTS:
-        if name not in ("fqsl_params_default", "fqsl_version", "fqsl_last_error"):
+        if name not in ("fqsl_params_default", "fqsl_version", "fqsl_last_error", "fqsl_debug_alloc_cap"):
             getattr(lib, name).restype = C.c_int
+    lib.fqsl_debug_alloc_cap.restype = None
     return lib
 
 
@@ -96,6 +98,13 @@ _lib = load()
 
 def version() -> str:
     return _lib.fqsl_version().decode()
+
+
+def debug_alloc_cap(nbytes: int) -> None:
+    """Testing aid (fqsl_debug_alloc_cap): later device allocations of the
+    library larger than ``nbytes`` fail as out of memory (FqslError status 3);
+    0 removes the cap."""
+    _lib.fqsl_debug_alloc_cap(int(nbytes))
 
 
 def _check(status):
