@@ -63,7 +63,7 @@ NUM_SMS = 152
 # an ncu capture of that kernel on this map, valid while the tracer sources
 # hash to TRACE_F32_SRC_HASH.
 TRACE_F32_DRAM_BYTES = 309.030656e6 + 59.771648e6
-TRACE_F32_SRC_HASH = "6e97bb38f9defdc0"
+TRACE_F32_SRC_HASH = "ef0edbdcc5075cb6"
 
 
 def _trace_src_hash():
@@ -252,11 +252,11 @@ def _dist():
     return ws, rank, local
 
 
-def c2_inputs(rank: int = 0, cube=CUBE):
+def monopole24_inputs(rank: int = 0, cube=CUBE):
     """Rank r maps its own cube: the same shape, sources seeded with 2208 + r."""
     import synth
 
-    B, grid, _ = synth.c2_monopole(seed=SEED + rank, n=cube)
+    B, grid, _ = synth.monopole24_cube(seed=SEED + rank, n=cube)
     u = (float(cube[0] - 1) / NU, 0.0, 0.0)
     v = (0.0, float(cube[1] - 1) / NV, 0.0)
     return B, grid, u, v
@@ -319,7 +319,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    B, grid, u, v = c2_inputs(0)
+    B, grid, u, v = monopole24_inputs(0)
     import oracle
 
     oracle.build()
@@ -488,10 +488,10 @@ RECT_WORKLOAD = "monopole24_stretched256x256x128_f32_z0plane_1024x1024_methodI_r
 
 
 def run_stretched(args, emit=True):
-    """The C2 map on a stretched grid (Sec. 2.2-2.3): the same 24 monopoles
+    """The 24-monopole map on a stretched grid (Sec. 2.2-2.3): the same 24 monopoles
     sampled on 256x256x128 nodes over the same box, horizontal cells growing
     1 % per cell from the middle to the edges and vertical cells 2 % per cell
-    upward; 1024x1024 seeds on z=0. FP32 and FP64, next to the uniform C2 map
+    upward; 1024x1024 seeds on z=0. FP32 and FP64, next to the uniform map
     (the paper reports 45-80 % of the uniform speed for its binary search);
     error against the oracle on a seeded sample."""
     import torch
@@ -504,7 +504,7 @@ def run_stretched(args, emit=True):
     import paper_2208_12569_gb300 as fq
 
     dev = torch.device("cuda", 0)
-    B, grid, _ = synth.c2_stretched(seed=SEED, n=CUBE)
+    B, grid, _ = synth.monopole24_stretched(seed=SEED, n=CUBE)
     Bd = torch.from_numpy(B).to(dev)
     u = ((CUBE[0] - 1.0) / NU, 0.0, 0.0)
     v = (0.0, (CUBE[1] - 1.0) / NV, 0.0)
@@ -539,8 +539,8 @@ def run_stretched(args, emit=True):
         res[prec] = {"value": n / (ms / 1000.0), "unit": "Q+Tw values/s", "ms_per_step": ms, "trace_ms": tr,
                      "mean_trials_per_line": float(o["steps"].astype(np.int64).sum()) / n, "out": o}
     fr.close()
-    # the uniform C2 map in the same run, for the ratio
-    Bu, ugrid, uu, vu = c2_inputs(0)
+    # the uniform 256x256x128 map in the same run, for the ratio
+    Bu, ugrid, uu, vu = monopole24_inputs(0)
     Bud = torch.from_numpy(Bu).to(dev)
     fu = fq.Field(Bud, ugrid.origin, ugrid.spacing, pack=("f32",))
     fu.set_timing(True)
@@ -558,7 +558,7 @@ def run_stretched(args, emit=True):
             "fp64": {k: res["f64"][k] for k in ("value", "ms_per_step", "trace_ms")},
             "kernels_ms": {"trace_f32": res["f32"]["trace_ms"]},
             "work": {"mean_trials_per_line": res["f32"]["mean_trials_per_line"]},
-            "uniform_c2_f32": {"value": n / (ms_u / 1000.0), "ms_per_step": ms_u, "trace_ms": tr_u,
+            "uniform_f32": {"value": n / (ms_u / 1000.0), "ms_per_step": ms_u, "trace_ms": tr_u,
                                "stretched_over_uniform": ms_u / res["f32"]["ms_per_step"]},
             "gpu_launches": 3 * args.steps}
     if emit and not args.no_cpu_baseline:
@@ -1178,7 +1178,7 @@ def main():
         dist.barrier()
     import paper_2208_12569_gb300 as fq
 
-    B, grid, u, v = c2_inputs(rank)
+    B, grid, u, v = monopole24_inputs(rank)
     Bd = torch.from_numpy(B).to(dev)
     field32 = fq.Field(Bd, grid.origin, grid.spacing, pack=("f32",))
     field64 = fq.Field(Bd, grid.origin, grid.spacing, pack=("f64",))
@@ -1437,7 +1437,7 @@ def main():
         st = run_stretched(argparse.Namespace(steps=args.steps, warmup=args.warmup, fp64_steps=args.fp64_steps,
                                               no_cpu_baseline=True), emit=False)
         line["stretched"] = {k: st[k] for k in ("value", "unit", "ms_per_step", "config", "f32_acc64", "fp64",
-                                                "kernels_ms", "work", "uniform_c2_f32")}
+                                                "kernels_ms", "work", "uniform_f32")}
     ref = sample = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, sample, ref = cpu_baseline(B, grid, u, v)

@@ -42,9 +42,10 @@
 // Resident 128-thread blocks per SM asked of the FP64 RKF45 tracers (not the
 // Method II or fixed-step ones): their latency (FP64 divisions and square
 // roots on GB300's narrow FP64 pipe) wants warps more than registers. 8 blocks
-// (64 registers, the rest spilled to L1) measured fastest: 92.5 ms per C2 map
-// against 108.9 ms at 168 registers and 3 blocks. The fixed-step FP64 map
-// measured slower with it (8.5 against 8.9 M Q+Tw/s) and keeps its registers.
+// (64 registers, the rest spilled to L1) measured fastest: 92.5 ms per
+// 1024x1024 map of the 256x256x128 monopole cube against 108.9 ms at 168
+// registers and 3 blocks. The fixed-step FP64 map measured slower with it
+// (8.5 against 8.9 M Q+Tw/s) and keeps its registers.
 #ifndef FQSL_TRACE_F64_MINB
 #define FQSL_TRACE_F64_MINB 8
 #endif

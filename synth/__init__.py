@@ -11,7 +11,7 @@ from .fields import (  # noqa: F401
     RectGrid,
     stretched_axis,
     stretched_grid,
-    c2_stretched,
+    monopole24_stretched,
     analytic_cube,
     monopole_cube,
     random_charges,
@@ -21,8 +21,8 @@ from .fields import (  # noqa: F401
     perturbed_charges,
     random_smooth_cube,
     batch_specs,
-    C1_GRID,
-    c2_monopole,
+    ANALYTIC_GRID,
+    monopole24_cube,
     large_monopole,
     adjoint_cubes,
 )

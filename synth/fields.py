@@ -102,10 +102,10 @@ def _grid_from_box(n, lo, hi):
     return Grid(tuple(int(k) for k in n), tuple(float(v) for v in lo), sp)
 
 
-C1_GRID = _grid_from_box((64, 64, 64), (-1.0, -1.0, 0.0), (1.0, 1.0, 1.0))
+ANALYTIC_GRID = _grid_from_box((64, 64, 64), (-1.0, -1.0, 0.0), (1.0, 1.0, 1.0))
 
 
-def analytic_cube(kind: str, grid: Grid = C1_GRID, q: float = 2.0 * math.pi,
+def analytic_cube(kind: str, grid: Grid = ANALYTIC_GRID, q: float = 2.0 * math.pi,
                   dtype=np.float64):
     """Sample an analytic field at the nodes of ``grid``.
 
@@ -219,9 +219,9 @@ def monopole_cube(grid: Grid, charges, dtype=np.float32, device=None):
     return out
 
 
-def c2_stretched(seed: int = 2208, n=(256, 256, 128), count: int = 24, dtype=np.float32,
+def monopole24_stretched(seed: int = 2208, n=(256, 256, 128), count: int = 24, dtype=np.float32,
                  ratios=(1.01, 1.01, 1.02)):
-    """The 24-monopole field of c2_monopole (same sources) sampled on a
+    """The 24-monopole field of monopole24_cube (same sources) sampled on a
     stretched grid over the same box: horizontal cells growing by ratios[0],
     ratios[1] per cell from the middle to the edges, vertical cells by
     ratios[2] per cell upward. Returns (B, RectGrid, charges)."""
@@ -232,7 +232,7 @@ def c2_stretched(seed: int = 2208, n=(256, 256, 128), count: int = 24, dtype=np.
     return monopole_cube(grid, ch, dtype=dtype), grid, ch
 
 
-def c2_monopole(seed: int = 2208, n=(256, 256, 128), count: int = 24, dtype=np.float32,
+def monopole24_cube(seed: int = 2208, n=(256, 256, 128), count: int = 24, dtype=np.float32,
                 device=None):
     """Synthetic active-region potential field: ``count`` buried monopoles,
     unit spacing, origin 0, depths 4..16 cells. Returns (B, grid, charges)."""

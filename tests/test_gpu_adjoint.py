@@ -226,7 +226,7 @@ def _mesh(grid):
 @pytest.mark.parametrize("precision,rtol", [("f64", 1e-5), ("f32", 1e-3)])
 def test_hyperbolic_closed_form(fq, precision, rtol):
     # B = (x, -y, 1): sum_s w_s dQ_s/da along dB = (x, -y, 0) = sum w * 2L(e^2L - e^-2L)
-    grid = synth.C1_GRID
+    grid = synth.ANALYTIC_GRID
     B = synth.analytic_cube("hyperbolic", grid)
     field = _field(fq, B if precision == "f64" else B.astype(np.float32), grid)
     X, Y, Z = _mesh(grid)
@@ -241,7 +241,7 @@ def test_hyperbolic_closed_form(fq, precision, rtol):
 @pytest.mark.parametrize("precision,rtol", [("f64", 1e-3), ("f32", 2e-3)])
 def test_rotation_closed_form(fq, precision, rtol):
     # B = (-q y, q x, 1): sum_s w_s dTw_s/dq along dB = (-y, x, 0)
-    grid = synth.C1_GRID
+    grid = synth.ANALYTIC_GRID
     q = 2.0 * math.pi
     B = synth.analytic_cube("rotation", grid, q=q)
     field = _field(fq, B if precision == "f64" else B.astype(np.float32), grid)
@@ -701,7 +701,7 @@ def test_fixed_step_fp32_forward_gradient_against_oracle(fq, small, precision):
 def test_fixed_step_hyperbolic_closed_form(fq, precision, rtol):
     # B = (x, -y, 1), the closed form of the hyperbolic test above, through the
     # 3/8 rule at 0.2 cells (its footpoints are exact to 1e-7 there)
-    grid = synth.C1_GRID
+    grid = synth.ANALYTIC_GRID
     B = synth.analytic_cube("hyperbolic", grid)
     field = _field(fq, B if precision == "f64" else B.astype(np.float32), grid)
     X, Y, Z = _mesh(grid)

@@ -39,7 +39,7 @@ def _check_fp32(g, r):
     assert np.median(rel[np.isfinite(rel)]) < 1e-3
 
 
-def test_c3_batch_full_size_sampled(fq):
+def test_batch48_full_size_sampled(fq):
     dev = torch.device("cuda", 0)
     specs = synth.batch_specs(seed=2208)
     cubes = [synth.monopole_cube(sp["grid"], sp["charges"], dtype=np.float32, device=dev) for sp in specs]
@@ -70,7 +70,7 @@ def test_c3_batch_full_size_sampled(fq):
         f.close()
 
 
-def test_c5_large_volume_full_size_sampled(fq):
+def test_large_volume_full_size_sampled(fq):
     dev = torch.device("cuda", 0)
     n = (1024, 1024, 512)
     Bd, grid, _ = synth.large_monopole(n=n, device=dev)

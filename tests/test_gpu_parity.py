@@ -39,13 +39,13 @@ def _gpu_plane(fq, field, origin, u, v, nu, nv, **kw):
     return to_np(out)
 
 
-G1 = synth.C1_GRID
+G1 = synth.ANALYTIC_GRID
 D1 = 2.0 / 128
 
 
 @pytest.mark.parametrize("kind", ["hyperbolic", "rotation", "uniform", "shear", "expanding"])
 @pytest.mark.parametrize("tol", [1e-10, 10 ** -3.2])
-def test_c1_analytic_fp64_parity(fq, oracle_lib, kind, tol):
+def test_analytic_fp64_parity(fq, oracle_lib, kind, tol):
     """Analytic 64^3 fields, 128x128 cell-centred seeds on z=0."""
     B = synth.analytic_cube(kind)
     field = _field(fq, B, G1)
@@ -57,7 +57,7 @@ def test_c1_analytic_fp64_parity(fq, oracle_lib, kind, tol):
     assert_bitwise(g, r)
 
 
-def test_c1_closed_forms_on_gpu(fq, oracle_lib):
+def test_analytic_closed_forms_on_gpu(fq, oracle_lib):
     """The closed forms themselves, on the FP64 and FP32 paths."""
     X, Y = np.meshgrid(-1 + (np.arange(128) + 0.5) * D1, -1 + (np.arange(128) + 0.5) * D1, indexing="xy")
     X, Y = X.ravel(), Y.ravel()
@@ -218,11 +218,11 @@ def test_argument_errors(fq):
     assert ei.value.status == 1
 
 
-def test_c2_full_size_sampled_parity(fq, oracle_lib):
+def test_monopole_full_size_sampled_parity(fq, oracle_lib):
     """The benchmark workload at full size (256x256x128 FP32 monopole cube,
     1024x1024 seeds on z=0) in the benchmark's launch configuration; the oracle
     recomputes a seeded random sample of seeds one by one."""
-    B, grid, _ = synth.c2_monopole()
+    B, grid, _ = synth.monopole24_cube()
     field = _field(fq, B, grid)
     n = 1024
     args = ((0.0, 0.0, 0.0), (255.0 / n, 0, 0), (0, 255.0 / n, 0), n, n)
@@ -242,7 +242,7 @@ def test_c2_full_size_sampled_parity(fq, oracle_lib):
     assert np.percentile(rel[np.isfinite(rel)], 99) < 0.06
 
 
-def test_c2_fp32_accuracy_against_the_converged_map(fq, oracle_lib):
+def test_monopole_fp32_accuracy_against_the_converged_map(fq, oracle_lib):
     """FP32 against the map itself: on the full-size benchmark map, both the
     FP32 and the FP64 map at the benchmark tolerance (10^-3.2) are compared
     with the oracle's map at tol_perp = 1e-10 on a seeded sample. FP64 at that
@@ -250,7 +250,7 @@ def test_c2_fp32_accuracy_against_the_converged_map(fq, oracle_lib):
     sequence than the converged one); FP32's error against the converged map
     must stay within twice FP64's, at the median and the 99th percentile, so
     that float rounding does not set the map's accuracy."""
-    B, grid, _ = synth.c2_monopole()
+    B, grid, _ = synth.monopole24_cube()
     field = _field(fq, B, grid)
     n = 1024
     args = ((0.0, 0.0, 0.0), (255.0 / n, 0, 0), (0, 255.0 / n, 0), n, n)
@@ -332,12 +332,12 @@ def test_method2_volume_fp64_bitwise(fq, oracle_lib, mono):
 
 
 @pytest.mark.parametrize("way,qperp", [(1, 0), (2, 0), (1, 1)], ids=["way1", "way2", "way1_qperp"])
-def test_method2_c2_full_size_sampled(fq, oracle_lib, way, qperp):
+def test_method2_monopole_full_size_sampled(fq, oracle_lib, way, qperp):
     """Method II (and Q_perp) on the benchmark's full-size map (256x256x128
     FP32 monopole cube, 1024x1024 seeds on z=0) in the launch the benchmark
     times: FP64 bit-identical to the oracle on a seeded sample of seeds, each
     recomputed on its own, and the FP32 error stated."""
-    B, grid, _ = synth.c2_monopole()
+    B, grid, _ = synth.monopole24_cube()
     field = _field_m2(fq, B, grid)
     n = 1024
     args = ((0.0, 0.0, 0.0), (255.0 / n, 0, 0), (0, 255.0 / n, 0), n, n)

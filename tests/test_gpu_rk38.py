@@ -13,7 +13,7 @@ from parity import assert_bitwise, assert_fp64_parity, q_rel, to_np, tw_rel
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-G1 = synth.C1_GRID
+G1 = synth.ANALYTIC_GRID
 E2 = math.e ** 2 + math.e ** -2
 
 
@@ -112,12 +112,12 @@ def test_closed_form_on_gpu(fq, oracle_lib):
         np.testing.assert_allclose(g["Q"], E2, rtol=bound)
 
 
-def test_c2_full_size_sampled(fq, oracle_lib):
-    """The fixed-step map the benchmark times (C2: 256x256x128 FP32 monopole
+def test_monopole_full_size_sampled(fq, oracle_lib):
+    """The fixed-step map the benchmark times (the 256x256x128 FP32 monopole
     cube, 1024x1024 seeds on z=0, step_perp = 3 cells scaled by Eq. step) at
     full size: FP64 bit-identical to the oracle on a seeded sample of seeds,
     FP32 error stated."""
-    B, grid, _ = synth.c2_monopole()
+    B, grid, _ = synth.monopole24_cube()
     field = _field(fq, B, grid)
     n = 1024
     args = ((0.0, 0.0, 0.0), (255.0 / n, 0, 0), (0, 255.0 / n, 0), n, n)

@@ -257,7 +257,7 @@ def test_full_size_stretched_workload_sampled(fq, oracle_lib):
     """The stretched benchmark workload at full size (the 256x256x128 monopole
     field on a stretched grid, 1024x1024 seeds on z=0) in the benchmark's
     launch configuration; the oracle recomputes a seeded sample of seeds."""
-    B, grid, _ = synth.c2_stretched()
+    B, grid, _ = synth.monopole24_stretched()
     field = _field(fq, B, grid)
     n = 1024
     args = ((0.0, 0.0, 0.0), (255.0 / n, 0, 0), (0, 255.0 / n, 0), n, n)

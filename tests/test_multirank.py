@@ -32,7 +32,7 @@ def _rank(rank, world, port, out):
 
     dist.init_process_group("gloo", rank=rank, world_size=world)
     ws, r, local = bench._dist()
-    B, grid, u, v = bench.c2_inputs(r, cube=(16, 12, 8))
+    B, grid, u, v = bench.monopole24_inputs(r, cube=(16, 12, 8))
     # a made-up per-rank step time: the slower rank sets the job's time
     ms_local = 2.0 + r
     ms, value = bench.job_rate(ms_local, 1000, dist, "cpu")

@@ -20,7 +20,7 @@ adj = pytest.importorskip("oracle.adjoint")
 SMALL = dict(n=(24, 24, 24), count=6, radius_cells=4.0, dtype=np.float64)
 PLANE16 = ((0.0, 0.0, 0.0), (23.0 / 16, 0.0, 0.0), (0.0, 23.0 / 16, 0.0), 16, 16)
 PLANE8 = ((0.0, 0.0, 0.0), (23.0 / 8, 0.0, 0.0), (0.0, 23.0 / 8, 0.0), 8, 8)
-# a 6x6 patch of the C1 grid's z=0 plane around the axis (every line leaves
+# a 6x6 patch of the analytic grid's z=0 plane around the axis (every line leaves
 # through the top for the hyperbolic and rotation fields)
 PATCH = ((-0.3, -0.3, 0.0), (0.1, 0.0, 0.0), (0.0, 0.1, 0.0), 6, 6)
 
@@ -104,7 +104,7 @@ def test_hyperbolic_field_closed_form():
     # B = (a x, -a y, 1): footpoints (x e^{aL}, y e^{-aL}) on top (L = 1), so
     # Q = e^{2aL} + e^{-2aL} and dQ/da = 2L (e^{2aL} - e^{-2aL}) along
     # dB = (x, -y, 0) (linear, hence exactly interpolated).
-    grid = synth.C1_GRID
+    grid = synth.ANALYTIC_GRID
     p = oracle.params()
     B = synth.analytic_cube("hyperbolic", grid)
     X, Y, Z = _mesh(grid)
@@ -124,7 +124,7 @@ def test_rotation_field_closed_form():
     # B = (-q y, q x, 1): a line at radius r keeps it, J = (0, 0, 2q), so
     # Tw = q L / (2 pi sqrt(1 + q^2 r^2)) and dTw/dq = L (1 + q^2 r^2)^(-3/2) / (2 pi)
     # along dB = (-y, x, 0); the footpoint map stays a rotation (dQ/dq = 0).
-    grid = synth.C1_GRID
+    grid = synth.ANALYTIC_GRID
     q = 2.0 * math.pi
     p = oracle.params()
     B = synth.analytic_cube("rotation", grid, q=q)

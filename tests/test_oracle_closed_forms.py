@@ -13,7 +13,7 @@ import pytest
 import oracle
 import synth
 
-G1 = synth.C1_GRID
+G1 = synth.ANALYTIC_GRID
 E2 = math.e ** 2 + math.e ** -2
 
 

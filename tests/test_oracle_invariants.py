@@ -51,7 +51,7 @@ def test_q_constant_along_line_exact_field(oracle_lib):
     interior point (Eq. D+-2 makes Q independent of S0) equals Method I on the
     bottom face at the line's footpoint and on the top face at the other one."""
     B = synth.analytic_cube("linear")
-    grid = synth.C1_GRID
+    grid = synth.ANALYTIC_GRID
     rng = np.random.default_rng(5)
     seeds = rng.uniform([-0.4, -0.4, 0.2], [0.4, 0.4, 0.8], size=(12, 3))
     p = oracle.params(method=1, tol=1e-12)
@@ -104,7 +104,7 @@ def test_method2_q_constant_along_analytic_line(oracle_lib):
         for x0, y0 in ((0.1, 0.2), (-0.2, -0.5)):
             r = np.array([x0 * np.exp(z0), y0 * np.exp(-z0), z0])
             lo = r - np.array([5e-4, 5e-4, 0.0])  # the single seed sits at lo + (a1 + a2)/2 = r
-            o = oracle.qmap(B, synth.C1_GRID, lo, (1e-3, 0, 0), (0, 1e-3, 0), counts=(1, 1, 1), p=p)
+            o = oracle.qmap(B, synth.ANALYTIC_GRID, lo, (1e-3, 0, 0), (0, 1e-3, 0), counts=(1, 1, 1), p=p)
             assert abs(o["Q"][0] / e2 - 1) < 1e-8
 
 

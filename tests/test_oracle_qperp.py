@@ -21,7 +21,7 @@ import numpy as np
 import oracle
 import synth
 
-G1 = synth.C1_GRID
+G1 = synth.ANALYTIC_GRID
 E2 = math.e ** 2 + math.e ** -2
 
 
