@@ -84,57 +84,123 @@ def _measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def _smi_gpu_id(dev_index: int) -> str:
+    """The nvidia-smi id of a CUDA device: its UUID (CUDA and NVML number
+    visible devices differently when CUDA_VISIBLE_DEVICES is set), else the
+    index."""
+    try:
+        import torch
+
+        u = str(torch.cuda.get_device_properties(dev_index).uuid)
+        u = u[4:] if u.startswith("GPU-") else u
+        if len(u) == 36 and all(c in "0123456789abcdef-" for c in u.lower()):
+            return "GPU-" + u
+    except Exception:
+        pass
+    return str(dev_index)
+
+
 class ClockSampler:
-    """nvidia-smi clocks/throttle sampling during the timed region."""
+    """nvidia-smi clocks/throttle sampling during the timed region. start()
+    returns once the sampler has written its first line, so sampling is under
+    way when the region begins; stop() keeps the samples stamped between the
+    two calls. If the region is shorter than the sampling interval and holds
+    no sample, the last sample before it and the first after it stand in
+    (``bracketing``)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, gpu_index: int, smi: str = "nvidia-smi"):
+        self.ids = [_smi_gpu_id(gpu_index)]
+        if self.ids[0] != str(gpu_index):
+            self.ids.append(str(gpu_index))
+        self.smi = smi
         self.proc = None
         self.lines = []
+        self.t0 = None
+
+    def _spawn(self, gid):
+        self.lines = []
+        self.proc = subprocess.Popen([self.smi, "-i", gid, "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
+                                     stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        deadline = time.monotonic() + 5.0
+        while not self.lines and time.monotonic() < deadline and self.proc.poll() is None:
+            time.sleep(0.002)
+        return bool(self.lines)
 
     def start(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except OSError:
-            self.proc = None
+        self.proc = None
+        for gid in self.ids:
+            try:
+                if self._spawn(gid):
+                    break
+            except OSError:
+                self.proc = None
+                break
+            self._kill()
+        self.t0 = time.monotonic()
+
+    def mark(self):
+        """The timed region begins now (start() may run before the warm-up,
+        so that the GPU does not idle between the warm-up and the region
+        while the sampler starts)."""
+        self.t0 = time.monotonic()
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
-    def stop(self):
+    def _kill(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.t.join(timeout=2)
-        sm, mx, reasons = [], [], set()
+
+    @staticmethod
+    def _parse(ln):
+        parts = [p.strip() for p in ln.split(",")]
+        if len(parts) < 9:
+            return None
+        try:
+            sm, mx = float(parts[1]), float(parts[2])
+        except ValueError:
+            return None
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return sm, mx, {nm for nm, v in zip(names, parts[5:9]) if v.lower().startswith("active")}
+
+    def stop(self):
+        t1 = time.monotonic()
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        # one more interval, so that a sample after the region exists
+        time.sleep(2 * self.INTERVAL_MS / 1000.0)
+        self._kill()
+        stamped = [(t, r) for t, r in ((t, self._parse(ln)) for t, ln in self.lines) if r is not None]
+        inside = [r for t, r in stamped if self.t0 <= t <= t1]
+        bracketing = not inside
+        if bracketing:
+            before = [r for t, r in stamped if t < self.t0][-1:]
+            after = [r for t, r in stamped if t > t1][:1]
+            inside = before + after
+        sm = [r[0] for r in inside]
+        mx = [r[1] for r in inside]
+        reasons = set().union(*[r[2] for r in inside]) if inside else set()
+        out = {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+               "reasons": sorted(reasons), "samples": 0 if bracketing else len(sm),
+               "interval_ms": self.INTERVAL_MS, "region_ms": round((t1 - self.t0) * 1000.0, 1)}
+        if bracketing:
+            out["bracketing"] = len(sm)
+        return out
 
 
 def roofline(trials, trace_ms, trace64_ms, ceil, work_src):
@@ -809,11 +875,12 @@ def run_adjoint(args, emit=True):
         field.set_timing(False)
         return float(np.mean(fwd)), float(np.mean(rev)), float(np.mean(curlt))
 
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     for _ in range(args.warmup):
         step(p32, Bd, dB)
     torch.cuda.synchronize()
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
+    clocks.mark()
     ms32 = timed(p32, dB, args.steps)
     clk = clocks.stop()
     loss32 = float(lbuf["loss"])
@@ -1222,14 +1289,15 @@ def main():
                               "kernels_ms": {"trace_f64": float(np.mean([k[0] for k in kern]))},
                               "config": {"workload": WORKLOAD}, "partial": "only-f64"}), flush=True)
         return
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     for _ in range(args.warmup):
         step(p32)
     field32.check()
-    clocks = ClockSampler(torch.cuda.current_device())
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.mark()
     ms32, kern32 = timed(p32, args.steps)
     if dist:
         dist.barrier()

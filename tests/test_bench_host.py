@@ -1,7 +1,10 @@
 """Host-side bookkeeping of bench.py that needs no GPU: the roofline fraction
 and its binding unit, the error statistics against the oracle, the masked
-loss of the finite-difference check, and the whole-job rate."""
+loss of the finite-difference check, the whole-job rate, and the clock
+sampler (against a stand-in for nvidia-smi's query loop)."""
 import math
+import sys
+import time
 
 import numpy as np
 import pytest
@@ -59,3 +62,42 @@ def test_loss_masked():
 def test_job_rate_single_process():
     ms, rate = bench.job_rate(2.0, 1000)
     assert ms == 2.0 and math.isclose(rate, 1000 / 2e-3)
+
+
+def _fake_smi(tmp_path, line):
+    """An executable that prints ``line`` every -lms milliseconds, as
+    nvidia-smi's query loop does."""
+    p = tmp_path / "fake-smi"
+    p.write_text("#!%s\n" % sys.executable + "import sys, time\n"
+                 "ms = int(sys.argv[sys.argv.index('-lms') + 1])\n"
+                 "while True:\n"
+                 "    print(%r, flush=True)\n"
+                 "    time.sleep(ms / 1000.0)\n" % line)
+    p.chmod(0o755)
+    return str(p)
+
+
+def test_clock_sampler_keeps_the_samples_of_the_region(tmp_path):
+    smi = _fake_smi(tmp_path, "0, 1980, 2070, 412.5, 0x4, Not Active, Not Active, Not Active, Active")
+    c = bench.ClockSampler(0, smi=smi)
+    c.start()
+    time.sleep(0.1)  # before the region: not counted
+    c.mark()
+    time.sleep(0.2)
+    out = c.stop()
+    assert out["sm_mhz"] == 1980.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+    assert 3 <= out["samples"] <= 0.2 / (bench.ClockSampler.INTERVAL_MS / 1000.0) + 2
+    assert "bracketing" not in out and 190 <= out["region_ms"] < 400
+
+
+def test_clock_sampler_short_region_and_missing_tool(tmp_path):
+    smi = _fake_smi(tmp_path, "0, 2070, 2070, 300.0, 0x0, Not Active, Active, Not Active, Not Active")
+    c = bench.ClockSampler(0, smi=smi)
+    c.start()
+    out = c.stop()  # a region shorter than the interval: the samples around it stand in
+    assert out["samples"] == 0 and out["bracketing"] >= 1
+    assert out["sm_mhz"] == 2070.0 and out["reasons"] == ["hw_thermal_slowdown"]
+    c = bench.ClockSampler(0, smi=str(tmp_path / "absent"))
+    c.start()
+    assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
