@@ -125,3 +125,102 @@ def test_stretched_grid_argument_errors(lib):
     assert create(good, good, tiny, 1) == 1 and b"float" in lib.fqsl_last_error()
     assert create(good, good, good, 0) == 1
     assert lib.fqsl_field_create_rect(None, 0, n, n, n, good, good, good, 1, None, C.byref(h)) == 1
+
+
+# (field, bad value, phrase of the message): each violates one documented
+# range of fqsl_params and is refused before the field handle is read
+BAD_PARAMS = [
+    ("method", 3, b"method"), ("gradb_way", 0, b"gradb_way"), ("precision", 7, b"precision"),
+    ("tol", 0.0, b"tol must be"), ("tol", float("nan"), b"tol must be"), ("tol", float("inf"), b"tol must be"),
+    ("h_min", 0.0, b"h_min"), ("h0", 10.0, b"h_min <= h0 <= h_max"), ("h_max", float("inf"), b"h_max"),
+    ("max_steps", 0, b"max_steps"), ("max_steps", 3 * 10 ** 9, b"max_steps"), ("rot_thresh", 1.0, b"rot_thresh"),
+    ("rot_thresh", -0.1, b"rot_thresh"), ("tol_exp", -1.0, b"tol_exp"), ("graze", 0.0, b"graze"),
+    ("graze", 1.0, b"graze"), ("eps_way2", 0.5, b"eps_way2"), ("refill_lanes", 33, b"refill_lanes"),
+    ("refill_lanes", -1, b"refill_lanes"), ("sync_dirs", 2, b"sync_dirs"), ("chunk_tiles", 65, b"chunk_tiles"),
+    ("blocks_per_sm", 65, b"blocks_per_sm"), ("tape", 2, b"tape must be"), ("tape_chunk", 33, b"tape_chunk"),
+    ("reverse_precision", 5, b"reverse_precision"),
+]
+
+
+@pytest.mark.parametrize("name,value,phrase", BAD_PARAMS)
+def test_params_out_of_range_are_refused_on_the_host(lib, name, value, phrase):
+    import paper_2208_12569_gb300 as fq
+    from paper_2208_12569_gb300 import fqsl as fqm
+
+    lib.fqsl_qmap_plane.restype = C.c_int
+    lib.fqsl_qmap_volume.restype = C.c_int
+    lib.fqsl_twist.restype = C.c_int
+    lib.fqsl_last_error.restype = C.c_char_p
+    p = fq.params()
+    setattr(p, name, value)
+    fake = C.c_void_p(4096)  # never read: the parameters are checked first
+    o = (C.c_double * 3)(0, 0, 0)
+    e = (C.c_double * 3)(1, 0, 0)
+    f = (C.c_double * 3)(0, 1, 0)
+    out = fqm.Out()
+    ll = C.c_longlong
+    assert lib.fqsl_qmap_plane(fake, o, e, f, ll(4), ll(4), C.byref(p), C.byref(out), None, None) == 1
+    assert phrase in lib.fqsl_last_error()
+    assert lib.fqsl_qmap_volume(fake, o, e, ll(2), ll(2), ll(2), C.byref(p), C.byref(out), None, None) == 1
+    assert phrase in lib.fqsl_last_error()
+    assert lib.fqsl_twist(fake, C.c_void_p(4096), ll(1), C.byref(p), C.byref(out), None) == 1
+    assert phrase in lib.fqsl_last_error()
+
+
+def test_every_entry_point_refuses_null_handles(lib):
+    """Each entry point that takes a handle or output array refuses NULL with
+    FQSL_ERR_ARG and a message, before any CUDA call."""
+    import paper_2208_12569_gb300 as fq
+    from paper_2208_12569_gb300 import fqsl as fqm
+
+    lib.fqsl_last_error.restype = C.c_char_p
+    p = fq.params()
+    out = fqm.Out()
+    o = (C.c_double * 3)(0, 0, 0)
+    ll = C.c_longlong
+    plane = fqm.Plane()
+    fake = C.c_void_p(4096)
+    calls = {
+        "fqsl_field_update": lambda: lib.fqsl_field_update(None, fake, 0, None),
+        "fqsl_field_destroy": lambda: lib.fqsl_field_destroy(None),
+        "fqsl_field_set_timing": lambda: lib.fqsl_field_set_timing(None, 1),
+        "fqsl_field_times": lambda: lib.fqsl_field_times(None, (C.c_float * 3)()),
+        "fqsl_field_check": lambda: lib.fqsl_field_check(None, None),
+        "fqsl_qmap_volume": lambda: lib.fqsl_qmap_volume(None, o, o, ll(1), ll(1), ll(1), C.byref(p), C.byref(out),
+                                                         None, None),
+        "fqsl_twist": lambda: lib.fqsl_twist(None, fake, ll(1), C.byref(p), C.byref(out), None),
+        "fqsl_qmap_plane_static": lambda: lib.fqsl_qmap_plane_static(None, o, o, o, ll(1), ll(1), C.byref(p),
+                                                                     C.byref(out), None),
+        "fqsl_batch_create": lambda: lib.fqsl_batch_create(None, C.byref(plane), C.byref(out), 1, C.byref(p),
+                                                           C.byref(C.c_void_p())),
+        "fqsl_batch_run": lambda: lib.fqsl_batch_run(None, None),
+        "fqsl_batch_destroy": lambda: lib.fqsl_batch_destroy(None),
+        "fqsl_loss_logq_tw": lambda: lib.fqsl_loss_logq_tw(ll(4), None, fake, fake, fake, None, C.c_double(0.1),
+                                                           fake, None, None, None, None),
+    }
+    for name, call in calls.items():
+        getattr(lib, name).restype = C.c_int
+        assert call() == 1, name
+        assert lib.fqsl_last_error(), name
+    # the batch's other arguments
+    lib.fqsl_batch_create.restype = C.c_int
+    h = C.c_void_p(fake.value)
+    assert lib.fqsl_batch_create(C.byref(fake), C.byref(plane), C.byref(out), 1, C.byref(p), None) == 1
+    assert lib.fqsl_batch_create(C.byref(fake), C.byref(plane), C.byref(out), 0, C.byref(p), C.byref(h)) == 1
+    assert h.value is None  # *out is cleared on refusal
+    assert lib.fqsl_batch_create(C.byref(fake), C.byref(plane), C.byref(out), 1, None, C.byref(h)) == 1
+    p2 = fq.params(method=2)
+    lib.fqsl_batch_create(C.byref(fake), C.byref(plane), C.byref(out), 1, C.byref(p2), C.byref(h))
+    assert b"Method I" in lib.fqsl_last_error()
+    # the loss: a negative count and a non-finite weight
+    lib.fqsl_loss_logq_tw.restype = C.c_int
+    assert lib.fqsl_loss_logq_tw(ll(-1), fake, fake, fake, fake, None, C.c_double(0.1), fake, None, None, None,
+                                 None) == 1
+    assert lib.fqsl_loss_logq_tw(ll(4), fake, fake, fake, fake, None, C.c_double(float("nan")), fake, None, None,
+                                 None, None) == 1
+    assert b"w_tw" in lib.fqsl_last_error()
+    # the tape export: a negative cap and NULL outputs
+    lib.fqsl_tape_export.restype = C.c_int
+    assert lib.fqsl_tape_export(fake, -1, fake, fake, fake, fake, None) == 1
+    assert lib.fqsl_tape_export(fake, 4, fake, fake, fake, None, None) == 1
+    assert b"NULL output" in lib.fqsl_last_error()
