@@ -61,7 +61,8 @@ typedef enum {
     FQSL_ERR_ARG = 1,         /* invalid argument; nothing was launched */
     FQSL_ERR_CUDA = 2,        /* a CUDA runtime call failed (message has the CUDA error) */
     FQSL_ERR_OOM = 3,         /* device memory could not be allocated */
-    FQSL_ERR_TIMEOUT = 4,     /* a bounded device loop gave up (see fqsl_field_check) */
+    FQSL_ERR_TIMEOUT = 4,     /* reserved: no kernel of this library waits on anything; every device loop
+                                 is bounded (a line that uses max_steps ends with FQSL_LINE_MAXSTEPS) */
     FQSL_ERR_UNSUPPORTED = 5  /* valid request the library does not implement */
 } fqsl_status;
 
@@ -419,8 +420,10 @@ FQSL_API fqsl_status fqsl_loss_logq_tw(long long n, const double *Q_dev, const d
                                        double *dTw_dev, void *cuda_stream);
 
 /* Synchronise cuda_stream and report device-side failures recorded by earlier
- * calls on this field (FQSL_ERR_TIMEOUT if a bounded loop gave up). The
- * record is cleared. */
+ * calls on this field: the reverse sweep's kernels check every index they
+ * form and record, instead of making the access, the first that is out of
+ * range and the number of such checks (FQSL_ERR_CUDA, the message names the
+ * first check and its value). The record is cleared. */
 FQSL_API fqsl_status fqsl_field_check(fqsl_field field, void *cuda_stream);
 
 /* Testing aid (the paper has no counterpart): every later device allocation
