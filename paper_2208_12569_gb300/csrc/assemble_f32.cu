@@ -1,17 +1,20 @@
 // q_assemble for the FP32 tracers: the FP32 tracer leaves index-space
 // footpoints, exit faces and compensated length/Tw partial sums; this kernel
-// forms, in FP64 and with every thread of a warp busy, the physical
-// footpoints, Bn at both ends (trilinear B of the FP32 records, Sec. 2.2), the
-// length and Tw totals (Eq. tw), and Method I's Q (Eqs. D+-2, D+-3, Q+- with
-// |det D| -> |Bn1/Bn2|, Eq. Bn1): J_e = d(face coordinates)/d(S0
+// forms, with every thread of a warp busy, the physical footpoints, the length
+// and Tw totals (Eq. tw) and Method I's Q (Eqs. D+-2, D+-3, Q+- with
+// |det D| -> |Bn1/Bn2|, Eq. Bn1) in FP64: J_e = d(face coordinates)/d(S0
 // coordinates) by central differences when both neighbours end on the
 // centre's face, one-sided when one does, NaN and FQSL_LINE_MIXED otherwise.
 // Neighbouring footpoints are differenced in index space first (exact for
-// nearby values in float) and scaled by the spacing in FP64. On a stretched
+// nearby values in float) and scaled by the spacing in FP64. Bn at both ends
+// is trilinear in the FP32 records (Sec. 2.2), and the factor |Bn1 Bn2|/Bn0^2
+// is formed as two correctly rounded float quotients (its inputs are floats;
+// GB300's FP64 pipe is the kernel's bound). On a stretched
 // grid the FP32 state is the physical position relative to the first node
 // (the field view's origin, with unit spacing), so the same forms apply.
 #include <math.h>
 
+#include "bits.cuh"
 #include "trace.cuh"
 
 namespace fqsl {
@@ -25,13 +28,14 @@ __device__ __forceinline__ void face_axes(int face, int &r0, int &r1)
     r1 = (a == 2) ? 1 : 2;
 }
 
-__device__ __forceinline__ double bn_at(const FieldView &f, const float *xi, int face)
+// Bn of a footpoint on its exit face, trilinear in the FP32 records
+__device__ __forceinline__ float bn_at(const FieldView &f, const float *xi, int face)
 {
     float B[3], J[3];
     if (f.rect) trace::gather_rect(f, xi[0], xi[1], xi[2], B, J);
     else trace::gather(f, xi[0], xi[1], xi[2], B, J);
     const int a = face >> 1;
-    return trace::f2d(a == 0 ? B[0] : (a == 1 ? B[1] : B[2]));
+    return a == 0 ? B[0] : (a == 1 ? B[1] : B[2]);
 }
 
 }  // namespace
@@ -88,7 +92,8 @@ __device__ __forceinline__ void assemble_one_f32(const AssembleArgs &A, long lon
                         cm = (e == 0 ? NR->xi1 : NR->xi2) + 3 * nid[M];
                     for (int r = 0; r < 2; r++) {
                         const int a = ra[r];
-                        if (cp && cm) Jm[e][r][s] = trace::f2d(cp[a] - cm[a]) * (0.5 * scs[a]);
+                        // (the halving is exact in float: one FP64 multiply per entry)
+                        if (cp && cm) Jm[e][r][s] = trace::f2d(0.5f * (cp[a] - cm[a])) * scs[a];
                         else if (cp) Jm[e][r][s] = trace::f2d(cp[a] - c0[a]) * scs[a];
                         else if (cm) Jm[e][r][s] = trace::f2d(c0[a] - cm[a]) * scs[a];
                         else mixed = true;
@@ -105,8 +110,13 @@ __device__ __forceinline__ void assemble_one_f32(const AssembleArgs &A, long lon
                         const double m = Jm[1][r][0] * adj[0][s] + Jm[1][r][1] * adj[1][s];
                         norm2 += m * m;
                     }
-                const double bn0 = R.bn0[idx];
-                Q = norm2 * fabs(bn_at(f, x1, f1) * bn_at(f, x2, f2)) / (bn0 * bn0);
+                // |Bn1 Bn2| / Bn0^2 as the product of two float quotients
+                // (correctly rounded; Bn0 holds the seed pre-pass's float
+                // value, and Bn1, Bn2 are float gathers), widened exactly:
+                // relative error below 2^-23, on the FP32 pipe
+                const float b0 = bits::narrow_exact(R.bn0[idx]);
+                const float q1 = bn_at(f, x1, f1) / b0, q2 = bn_at(f, x2, f2) / b0;
+                Q = norm2 * fabs(trace::f2d(q1) * trace::f2d(q2));
             }
         }
         const fqsl_out &o = A.out;
@@ -165,9 +175,10 @@ __global__ void __launch_bounds__(256) k_assemble_m2_f32(const AssembleArgs A)
                 float Bf[3], Jf[3];
                 if (f.rect) trace::gather_rect(f, xe[0], xe[1], xe[2], Bf, Jf);
                 else trace::gather(f, xe[0], xe[1], xe[2], Bf, Jf);
-                const double B[3] = {Bf[0], Bf[1], Bf[2]};
+                const double B[3] = {trace::f2d(Bf[0]), trace::f2d(Bf[1]), trace::f2d(Bf[2])};
                 const float *dv = R.dev32 + 12 * idx + 6 * e;
-                const double U[3] = {dv[0], dv[1], dv[2]}, V[3] = {dv[3], dv[4], dv[5]};
+                const double U[3] = {trace::f2d(dv[0]), trace::f2d(dv[1]), trace::f2d(dv[2])},
+                             V[3] = {trace::f2d(dv[3]), trace::f2d(dv[4]), trace::f2d(dv[5])};
                 double ru, rv;
                 if (A.qperp) {
                     // Q_perp: the end plane perpendicular to B
